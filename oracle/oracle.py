@@ -1,0 +1,445 @@
+"""KIFMM oracle: plain FP64 CPU reference of the long-range force evaluation.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+benchmark's CPU-baseline / reference legs import this module; the GPU library
+never does, and the two share no code (inputs come from ``workloads``).
+
+It follows the paper's outline of the kernel-independent FMM (Sec. 2.2): an
+adaptive octree with at most M points per leaf, an upward pass producing
+equivalent densities on surfaces around each box, M2L between boxes in each
+other's far zone but not in their parents', a downward pass, and the leaf
+evaluation of far field plus near field.  The details the paper leaves open
+are taken from the original KIFMM (Ying, Biros & Zorin 2004, cited in
+Sec. 2.2) and fixed as follows:
+
+* Kernel: K(x, y) = 1/(4 pi |x - y|), the normalisation of Eq. 3; pairs at
+  zero distance contribute nothing.  Outputs are pot_i = sum_j K q_j and its
+  gradient; the physical potential is ``coef`` times that (coef = 1 gives
+  Eq. 3 units, 1/eps0 SI Coulomb, -4 pi G gravity with masses as charges,
+  which is Eq. 4 read as attractive).
+* Surfaces: box centre c, half-width h, points c + alpha h (-1 + 2 (i,j,k)/(p-1))
+  with at least one index on the boundary, lexicographic; n_s = 6(p-1)^2 + 2.
+  alpha = 1.05 (upward equivalent, downward check), 2.95 (upward check,
+  downward equivalent).
+* Pseudo-inverse: SVD, singular values below eps * sigma_max dropped; the
+  threshold must not lie within a factor 1.1 of any sigma_i / sigma_max (gap
+  check), so that any backward-stable SVD truncates the same modes.  It is
+  applied as V (Sigma^-1 (U^T b)), never as an explicit matrix.
+* Tree: root cube from the per-axis minimum and the largest extent; 21-bit
+  quantisation, Morton order x-highest; stable sort; split while
+  count > M and level < max_depth; only non-empty children exist; canonical
+  node order (level, Morton prefix).
+* Lists: U, V, W, X of the adaptive KIFMM, classified from their definitions.
+
+Parity status: every function here is pinned by tests under tests/ against
+closed forms, invariants or brute force (see the test module docstrings).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+_LOCK = threading.Lock()
+
+ALPHA_UE = 1.05
+ALPHA_UC = 2.95
+ALPHA_DE = 2.95
+ALPHA_DC = 1.05
+BITS = 21
+
+
+def build() -> str:
+    """Compile the oracle's C core (gcc, OpenMP, no FMA contraction)."""
+    return _lib()._name
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        out_dir = os.path.join(_HERE, "_build")
+        os.makedirs(out_dir, exist_ok=True)
+        so = os.path.join(out_dir, "liborc.so")
+        src = os.path.join(_HERE, "kifmm_oracle.c")
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            tmp = so + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                                   "-ffp-contract=off", src, "-o", tmp, "-lm"])
+            os.replace(tmp, so)
+        lib = ctypes.CDLL(so)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        lib.orc_direct.argtypes = [I64, P, P, I64, P, P, P]
+        lib.orc_bbox.argtypes = [I64, P, P, P]
+        lib.orc_morton.argtypes = [I64, P, P, ctypes.c_double, P]
+        lib.orc_list_counts.argtypes = [I64, P, P, P, P, ctypes.c_int, P]
+        lib.orc_list_fill.argtypes = [I64, P, P, P, P, ctypes.c_int, P, P]
+        lib.orc_list_of.argtypes = [I64, P, P, P, P, ctypes.c_int, I64, P, I64]
+        lib.orc_list_of.restype = I64
+        lib.orc_fmm_evaluate.argtypes = [P]
+        lib.orc_fmm_struct_size.restype = ctypes.c_int
+        _LIB = lib
+        return lib
+
+
+def _p(a):
+    return a.ctypes.data if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Direct sum (Sec. 1: all pairs; Eq. 1 with the Laplace kernel, Eq. 3 units)
+# ---------------------------------------------------------------------------
+def direct(x, q, targets=None):
+    """pot, grad at ``targets`` (default: the sources) from all sources,
+    zero-distance pairs excluded."""
+    lib = _lib()
+    x = _f64(x).reshape(-1, 3)
+    q = _f64(q).reshape(-1)
+    t = x if targets is None else _f64(targets).reshape(-1, 3)
+    pot = np.empty(t.shape[0])
+    grad = np.empty((t.shape[0], 3))
+    lib.orc_direct(x.shape[0], _p(x), _p(q), t.shape[0], _p(t), _p(pot), _p(grad))
+    return pot, grad
+
+
+# ---------------------------------------------------------------------------
+# Morton keys and the adaptive octree (Sec. 2.2, first step)
+# ---------------------------------------------------------------------------
+def bbox(x):
+    lib = _lib()
+    x = _f64(x).reshape(-1, 3)
+    lo = np.empty(3)
+    side = np.empty(1)
+    lib.orc_bbox(x.shape[0], _p(x), _p(lo), _p(side))
+    return lo, float(side[0])
+
+
+def morton(x, lo, side):
+    lib = _lib()
+    x = _f64(x).reshape(-1, 3)
+    lo = _f64(lo)
+    keys = np.empty(x.shape[0], dtype=np.uint64)
+    lib.orc_morton(x.shape[0], _p(x), _p(lo), float(side), _p(keys))
+    return keys
+
+
+def deinterleave(prefix: int, level: int):
+    """Integer box coordinates (x, y, z) of a Morton prefix of ``level`` digits."""
+    c = [0, 0, 0]
+    for b in range(level):
+        digit = (prefix >> (3 * b)) & 7
+        c[0] |= ((digit >> 2) & 1) << b
+        c[1] |= ((digit >> 1) & 1) << b
+        c[2] |= (digit & 1) << b
+    return c
+
+
+def build_tree(keys_sorted, leaf_cap: int, max_depth: int):
+    """Adaptive octree over sorted keys: a box splits while it holds more than
+    ``leaf_cap`` points and its level is below ``max_depth``; only non-empty
+    children are created.  Nodes come out in canonical (level, prefix) order
+    with each node's children contiguous."""
+    keys_sorted = np.asarray(keys_sorted, dtype=np.uint64)
+    n = keys_sorted.shape[0]
+    level, prefix, first, count, parent = [0], [0], [0], [n], [-1]
+    child_first, nchild = [], []
+    begin = 0
+    while begin < len(level):
+        end = len(level)
+        for b in range(begin, end):
+            lev = level[b]
+            if count[b] > leaf_cap and lev < max_depth:
+                shift = np.uint64(3 * (BITS - lev - 1))
+                lo_i = first[b]
+                sub = keys_sorted[lo_i:lo_i + count[b]]
+                digits = ((sub >> shift) & np.uint64(7)).astype(np.int64)
+                child_first.append(len(level))
+                nc = 0
+                for o in range(8):
+                    a = int(np.searchsorted(digits, o, side="left"))
+                    e = int(np.searchsorted(digits, o, side="right"))
+                    if e > a:
+                        level.append(lev + 1)
+                        prefix.append((prefix[b] << 3) | o)
+                        first.append(lo_i + a)
+                        count.append(e - a)
+                        parent.append(b)
+                        nc += 1
+                nchild.append(nc)
+            else:
+                child_first.append(-1)
+                nchild.append(0)
+        begin = end
+    nb = len(level)
+    coord = np.array([deinterleave(prefix[b], level[b]) for b in range(nb)], dtype=np.int64).reshape(nb, 3)
+    tree = {
+        "level": np.array(level, dtype=np.int32),
+        "prefix": np.array(prefix, dtype=np.uint64),
+        "coord": coord,
+        "first": np.array(first, dtype=np.int64),
+        "count": np.array(count, dtype=np.int64),
+        "parent": np.array(parent, dtype=np.int32),
+        "child_first": np.array(child_first, dtype=np.int64),
+        "nchild": np.array(nchild, dtype=np.int64),
+    }
+    tree["isleaf"] = (tree["nchild"] == 0).astype(np.int32)
+    tree["nb"] = nb
+    tree["max_level"] = int(tree["level"].max())
+    return tree
+
+
+def sort_and_tree(x, leaf_cap: int, max_depth: int):
+    """Root cube, keys, stable sort (ties by input index) and the octree."""
+    lo, side = bbox(x)
+    keys = morton(x, lo, side)
+    perm = np.argsort(keys, kind="stable")
+    tree = build_tree(keys[perm], leaf_cap, max_depth)
+    tree.update(lo=lo, side=side, keys=keys, perm=perm)
+    return tree
+
+
+# ---------------------------------------------------------------------------
+# Interaction lists (Sec. 2.2, third step; adaptive U/V/W/X of Ying et al.)
+# ---------------------------------------------------------------------------
+LIST_KINDS = {"U": 0, "V": 1, "W": 2, "X": 3}
+
+
+def lists(tree):
+    """CSR lists {kind: (ptr, idx)} for every node, sources in node order."""
+    lib = _lib()
+    nb = tree["nb"]
+    args = (nb, _p(tree["level"]), _p(tree["coord"]), _p(tree["parent"]), _p(tree["isleaf"]))
+    out = {}
+    for name, k in LIST_KINDS.items():
+        counts = np.empty(nb, dtype=np.int64)
+        lib.orc_list_counts(*args, k, _p(counts))
+        ptr = np.zeros(nb + 1, dtype=np.int64)
+        np.cumsum(counts, out=ptr[1:])
+        idx = np.empty(int(ptr[-1]), dtype=np.int64)
+        lib.orc_list_fill(*args, k, _p(ptr), _p(idx))
+        out[name] = (ptr, idx)
+    return out
+
+
+def list_of(tree, kind: str, t: int):
+    """One target's list (used to check sampled boxes of large trees)."""
+    lib = _lib()
+    nb = tree["nb"]
+    args = (nb, _p(tree["level"]), _p(tree["coord"]), _p(tree["parent"]), _p(tree["isleaf"]))
+    n = lib.orc_list_of(*args, LIST_KINDS[kind], t, None, 0)
+    out = np.empty(max(n, 1), dtype=np.int64)
+    lib.orc_list_of(*args, LIST_KINDS[kind], t, _p(out), n)
+    return out[:n]
+
+
+# ---------------------------------------------------------------------------
+# Surfaces and translation operators (Sec. 2.2: densities on equivalent
+# surfaces; operators are matrices computed automatically for the kernel)
+# ---------------------------------------------------------------------------
+def surface(p: int):
+    """Unit-cube surface grid: (-1 + 2 (i,j,k)/(p-1)) with at least one index
+    on the boundary, lexicographic in (i, j, k)."""
+    pts = []
+    for i in range(p):
+        for j in range(p):
+            for k in range(p):
+                if i in (0, p - 1) or j in (0, p - 1) or k in (0, p - 1):
+                    pts.append((-1 + 2 * i / (p - 1), -1 + 2 * j / (p - 1), -1 + 2 * k / (p - 1)))
+    return np.array(pts, dtype=np.float64)
+
+
+def kernel_matrix(targets, sources):
+    d = targets[:, None, :] - sources[None, :, :]
+    r = np.sqrt(np.sum(d * d, axis=-1))
+    with np.errstate(divide="ignore"):
+        k = np.where(r > 0, 1.0 / (4.0 * np.pi * r), 0.0)
+    return k
+
+
+def m2l_offsets():
+    """The 316 relative positions d in {-3..3}^3 minus {-1..1}^3, in
+    lexicographic order (index = position in this list)."""
+    out = []
+    for a in range(-3, 4):
+        for b in range(-3, 4):
+            for c in range(-3, 4):
+                if -1 <= a <= 1 and -1 <= b <= 1 and -1 <= c <= 1:
+                    continue
+                out.append((a, b, c))
+    return np.array(out, dtype=np.int64)
+
+
+def child_offset(o: int):
+    """Centre of child octant o = 4x + 2y + z of a half-width-1 parent."""
+    return np.array([0.5 if (o >> 2) & 1 else -0.5, 0.5 if (o >> 1) & 1 else -0.5,
+                     0.5 if o & 1 else -0.5])
+
+
+class PinvGapError(ValueError):
+    pass
+
+
+def svd_pinv_factors(k, eps: float):
+    """Truncated SVD pseudo-inverse factors (U, sinv, V) with pinv = V diag(sinv) U^T."""
+    u, s, vh = np.linalg.svd(k)
+    rel = s / s[0]
+    near = np.logical_and(rel > eps / 1.1, rel < eps * 1.1)
+    if np.any(near):
+        raise PinvGapError(f"singular value within a factor 1.1 of eps={eps:g}: {rel[near]}")
+    sinv = np.where(rel >= eps, 1.0 / s, 0.0)
+    return np.ascontiguousarray(u), sinv, np.ascontiguousarray(vh.T), s
+
+
+def operators(p: int, eps: float = 1e-12):
+    """Unit-box (half-width 1) matrices; a box of half-width h scales them by 1/h."""
+    S = surface(p)
+    ns = S.shape[0]
+    ops = {"p": p, "ns": ns, "surf": S, "eps": eps}
+    ops["up"] = svd_pinv_factors(kernel_matrix(ALPHA_UC * S, ALPHA_UE * S), eps)
+    ops["dn"] = svd_pinv_factors(kernel_matrix(ALPHA_DC * S, ALPHA_DE * S), eps)
+    ops["m2m"] = np.stack([kernel_matrix(ALPHA_UC * S, child_offset(o) + 0.5 * ALPHA_UE * S)
+                           for o in range(8)])
+    ops["l2l"] = np.stack([kernel_matrix(child_offset(o) + 0.5 * ALPHA_DC * S, ALPHA_DE * S)
+                           for o in range(8)])
+    ops["m2l"] = np.stack([kernel_matrix(ALPHA_DC * S, 2.0 * d + ALPHA_UE * S) for d in m2l_offsets()])
+    return ops
+
+
+# ---------------------------------------------------------------------------
+# KIFMM evaluation
+# ---------------------------------------------------------------------------
+class _Fmm(ctypes.Structure):
+    _fields_ = [
+        ("nb", ctypes.c_int64),
+        ("level", ctypes.c_void_p), ("coord", ctypes.c_void_p), ("parent", ctypes.c_void_p),
+        ("isleaf", ctypes.c_void_p), ("first", ctypes.c_void_p), ("count", ctypes.c_void_p),
+        ("child_first", ctypes.c_void_p), ("nchild", ctypes.c_void_p),
+        ("max_level", ctypes.c_int32),
+        ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
+        ("x", ctypes.c_void_p), ("q", ctypes.c_void_p),
+        ("u_ptr", ctypes.c_void_p), ("u_idx", ctypes.c_void_p),
+        ("v_ptr", ctypes.c_void_p), ("v_idx", ctypes.c_void_p),
+        ("w_ptr", ctypes.c_void_p), ("w_idx", ctypes.c_void_p),
+        ("x_ptr", ctypes.c_void_p), ("x_idx", ctypes.c_void_p),
+        ("ns", ctypes.c_int),
+        ("surf", ctypes.c_void_p),
+        ("a_ue", ctypes.c_double), ("a_uc", ctypes.c_double),
+        ("a_de", ctypes.c_double), ("a_dc", ctypes.c_double),
+        ("m2m", ctypes.c_void_p), ("m2l", ctypes.c_void_p), ("l2l", ctypes.c_void_p),
+        ("up_u", ctypes.c_void_p), ("up_sinv", ctypes.c_void_p), ("up_v", ctypes.c_void_p),
+        ("dn_u", ctypes.c_void_p), ("dn_sinv", ctypes.c_void_p), ("dn_v", ctypes.c_void_p),
+        ("q_up", ctypes.c_void_p), ("d_chk", ctypes.c_void_p), ("q_dn", ctypes.c_void_p),
+        ("pot", ctypes.c_void_p), ("grad", ctypes.c_void_p),
+    ]
+
+
+def kifmm(x, q, p: int = 6, leaf_cap: int = 64, max_depth: int = 20, eps: float = 1e-12,
+          ops=None, tree=None, lst=None):
+    """Potential and gradient (user order, Eq. 3 units) of every particle from
+    all others, by the KIFMM.  Returns (pot, grad, info) where info holds the
+    tree, lists and the intermediate densities (canonical node order)."""
+    lib = _lib()
+    x = _f64(x).reshape(-1, 3)
+    q = _f64(q).reshape(-1)
+    n = x.shape[0]
+    if tree is None:
+        tree = sort_and_tree(x, leaf_cap, max_depth)
+    if lst is None:
+        lst = lists(tree)
+    if ops is None:
+        ops = operators(p, eps)
+    perm = tree["perm"]
+    xs = np.ascontiguousarray(x[perm])
+    qsrt = np.ascontiguousarray(q[perm])
+    nb, ns = tree["nb"], ops["ns"]
+    q_up = np.zeros((nb, ns))
+    d_chk = np.zeros((nb, ns))
+    q_dn = np.zeros((nb, ns))
+    pot_s = np.zeros(n)
+    grad_s = np.zeros((n, 3))
+    keep = [xs, qsrt]
+    f = _Fmm()
+    f.nb = nb
+    for name in ("level", "coord", "parent", "isleaf", "first", "count", "child_first", "nchild"):
+        arr = np.ascontiguousarray(tree[name])
+        keep.append(arr)
+        setattr(f, name, arr.ctypes.data)
+    f.max_level = tree["max_level"]
+    for d in range(3):
+        f.lo[d] = tree["lo"][d]
+    f.side = tree["side"]
+    f.x, f.q = xs.ctypes.data, qsrt.ctypes.data
+    for name in ("U", "V", "W", "X"):
+        ptr, idx = lst[name]
+        idx = idx if idx.size else np.zeros(1, dtype=np.int64)
+        keep += [ptr, idx]
+        setattr(f, name.lower() + "_ptr", ptr.ctypes.data)
+        setattr(f, name.lower() + "_idx", idx.ctypes.data)
+    f.ns = ns
+    mats = {k: np.ascontiguousarray(ops[k]) for k in ("surf", "m2m", "m2l", "l2l")}
+    keep += list(mats.values())
+    f.surf, f.m2m, f.m2l, f.l2l = (mats[k].ctypes.data for k in ("surf", "m2m", "m2l", "l2l"))
+    f.a_ue, f.a_uc, f.a_de, f.a_dc = ALPHA_UE, ALPHA_UC, ALPHA_DE, ALPHA_DC
+    uu, us, uv, _ = ops["up"]
+    du, ds, dv, _ = ops["dn"]
+    keep += [uu, us, uv, du, ds, dv]
+    f.up_u, f.up_sinv, f.up_v = uu.ctypes.data, us.ctypes.data, uv.ctypes.data
+    f.dn_u, f.dn_sinv, f.dn_v = du.ctypes.data, ds.ctypes.data, dv.ctypes.data
+    f.q_up, f.d_chk, f.q_dn = q_up.ctypes.data, d_chk.ctypes.data, q_dn.ctypes.data
+    f.pot, f.grad = pot_s.ctypes.data, grad_s.ctypes.data
+    assert ctypes.sizeof(f) == lib.orc_fmm_struct_size()
+    lib.orc_fmm_evaluate(ctypes.byref(f))
+    pot = np.empty(n)
+    grad = np.empty((n, 3))
+    pot[perm] = pot_s
+    grad[perm] = grad_s
+    info = {"tree": tree, "lists": lst, "ops": ops, "q_up": q_up, "d_chk": d_chk, "q_dn": q_dn}
+    return pot, grad, info
+
+
+# ---------------------------------------------------------------------------
+# Derived quantities
+# ---------------------------------------------------------------------------
+def energy(q, pot, coef: float = 1.0):
+    """Long-range potential energy U = 1/2 coef sum_i q_i pot_i (Sec. 2.4)."""
+    return 0.5 * coef * float(np.dot(np.asarray(q, dtype=np.float64), np.asarray(pot, dtype=np.float64)))
+
+
+def forces(q, grad, coef: float = 1.0):
+    """Per-particle force F_i = -coef q_i grad_i (Eq. 3 for coef = 1)."""
+    return -coef * np.asarray(q, dtype=np.float64)[:, None] * np.asarray(grad, dtype=np.float64)
+
+
+def clump_reduce(x, q, grad, offsets, ref, coef: float = 1.0):
+    """Clump force and torque (Sec. 2.4): sums over each clump's pebbles of
+    F_k and (x_k - X_c) x F_k about the reference point X_c."""
+    x = _f64(x).reshape(-1, 3)
+    f = forces(q, grad, coef)
+    ref = _f64(ref).reshape(-1, 3)
+    nc = ref.shape[0]
+    F = np.zeros((nc, 3))
+    T = np.zeros((nc, 3))
+    for c in range(nc):
+        for k in range(int(offsets[c]), int(offsets[c + 1])):
+            F[c] += f[k]
+            T[c] += np.cross(x[k] - ref[c], f[k])
+    return F, T
+
+
+def rel_l2(a, b):
+    """||a - b||_2 / ||b||_2 in FP64 over all entries."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a - b))
