@@ -1,0 +1,226 @@
+/*
+ * kifmm.h - C ABI of the GB300 (sm_103a) kernel-independent fast multipole
+ * library for long-range 1/r forces in discrete-element simulations.
+ *
+ * The method is the kernel-independent FMM outlined in Sec. 2.2 of the paper
+ * (an adaptive octree with at most M points per leaf; fine-to-coarse M2M;
+ * M2L between boxes in each other's far zone but not in their parents';
+ * coarse-to-fine L2L; far field plus near field at the leaves; densities on
+ * equivalent surfaces and translation matrices computed from the kernel),
+ * applied to the sum of Eq. 1 with the Laplace kernel normalised as in Eq. 3:
+ *
+ *     pot_i  = coef * sum_{j, |x_i - x_j| > 0} q_j / (4 pi |x_i - x_j|)
+ *     grad_i = gradient of pot_i with respect to x_i
+ *
+ * coef = 1 gives Eq. 3 units, 1/eps0 SI Coulomb, -4 pi G gravity with masses as
+ * charges (Eq. 4 read as attraction).  The force on particle i is
+ * F_i = -q_i grad_i and the long-range energy is U = 1/2 sum_i q_i pot_i
+ * (Sec. 2.4).
+ *
+ * Conventions for every call:
+ *  - Pointers marked "device" address memory on the plan's CUDA device,
+ *    contiguous, row-major, in the plan's dtype (float or double).  The
+ *    caller owns them; the library never frees or retains them past the call.
+ *  - Pointers marked "host" address ordinary host memory.
+ *  - The plan owns its workspace, operators and tree.  A plan is not
+ *    thread-safe; calls on one plan must be serialised by the caller.
+ *  - Work is enqueued on the given stream; nothing returns before its
+ *    arguments are validated.  Argument errors are returned at once.  Errors
+ *    detected on the device (non-finite input, capacity, timeout) are recorded
+ *    in a device status word read by kifmm_get_device_status.
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef KIFMM_H
+#define KIFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *kifmm_stream_t;
+
+typedef enum {
+    KIFMM_OK = 0,
+    KIFMM_ERR_ARG = 1,       /* invalid argument (null pointer, bad size or mode) */
+    KIFMM_ERR_CAPACITY = 2,  /* more particles or systems than the plan was made for */
+    KIFMM_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    KIFMM_ERR_NONFINITE = 4, /* a position or charge is NaN or infinite */
+    KIFMM_ERR_TIMEOUT = 5,   /* a bounded device wait ran out */
+    KIFMM_ERR_STATE = 6      /* call out of order (e.g. evaluate before set_sources) */
+} kifmm_status;
+
+typedef enum {
+    KIFMM_FP64 = 0,       /* every stage in double precision (parity path) */
+    KIFMM_FP32 = 1,       /* single precision, SIMT M2L ("plain FP32")         */
+    KIFMM_MIXED_TF32 = 2, /* M2L on tensor cores, 3xTF32 split, FP32 accumulate */
+    KIFMM_MIXED_FP16 = 3  /* M2L on tensor cores, 3xFP16 split with power-of-two
+                             scaling, FP32 accumulate                         */
+} kifmm_precision;
+
+typedef enum { KIFMM_DTYPE_F32 = 0, KIFMM_DTYPE_F64 = 1 } kifmm_dtype;
+
+/* Plan description.  Zero-initialise and set the fields you need. */
+typedef struct {
+    int p;               /* surface order: points per cube edge, 2 <= p <= 10;
+                            n_s = 6 (p - 1)^2 + 2 points per surface          */
+    int leaf_cap;        /* M: a box splits while it holds more than M points  */
+    int max_depth;       /* deepest octree level, 1 <= max_depth <= 20          */
+    int precision;       /* kifmm_precision                                    */
+    double coef;         /* multiplies 1/(4 pi r); 0 is read as 1              */
+    int64_t n_max;       /* largest total particle count over all systems      */
+    int n_systems_max;   /* largest number of independent systems per call     */
+    int dtype;           /* kifmm_dtype of xyz, q, pot, grad, forces           */
+    double pinv_eps;     /* relative SVD truncation of the check-to-equivalent
+                            pseudo-inverse; 0 selects 1e-12.  It must not lie
+                            within a factor 1.1 of any sigma_i / sigma_max.    */
+    int autotune;        /* 1: time candidate tile shapes at plan creation     */
+} kifmm_plan_desc;
+
+typedef struct kifmm_plan kifmm_plan;
+
+/*
+ * Create a plan: validate desc, allocate workspace for n_max particles,
+ * build the unit surfaces (Sec. 2.2, equivalent surfaces), compute the FP64
+ * pseudo-inverses of the check-from-equivalent matrices on the GPU (one-sided
+ * Jacobi SVD, truncated at pinv_eps) and the M2M, L2L and 316 M2L translation
+ * matrices (Sec. 2.2: matrices computed automatically for the kernel), and
+ * synchronise.  This is the per-setup precompute of Sec. 2.4.
+ * out (host): receives the plan.  Returns KIFMM_ERR_ARG for a bad desc or an
+ * ambiguous truncation threshold, KIFMM_ERR_CUDA if allocation fails.
+ */
+kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out);
+
+/* Free the plan and all device memory it owns (synchronises its device). */
+kifmm_status kifmm_plan_destroy(kifmm_plan *plan);
+
+/*
+ * Load particles and build the tree (Sec. 2.2, first and third steps): per
+ * system bounding cube, 63-bit Morton keys, stable radix sort, adaptive
+ * octree (split while count > leaf_cap and level < max_depth), U/V/W/X lists.
+ * n_systems: number of independent systems (1 <= n_systems <= n_systems_max).
+ * sys_offsets (host): n_systems + 1 ascending int64 offsets, sys_offsets[0] = 0;
+ *   system s owns particles [sys_offsets[s], sys_offsets[s+1]), at least one.
+ * xyz (device): [N, 3] positions; q (device): [N] charges (masses for gravity);
+ *   N = sys_offsets[n_systems] <= n_max.  Both are read during this call only;
+ *   the plan keeps sorted copies.
+ * Synchronises the stream (the tree size is data dependent).  Returns
+ * KIFMM_ERR_NONFINITE if a position or charge is not finite.
+ */
+kifmm_status kifmm_set_sources(kifmm_plan *plan, int n_systems, const int64_t *sys_offsets,
+                               const void *xyz, const void *q, kifmm_stream_t stream);
+
+/*
+ * Evaluate the long-range field on every particle (Sec. 2.2 passes; Sec. 2.4
+ * per-step evaluation): P2M, M2M, M2L (V list), P2L (X list), L2L, L2P,
+ * M2P (W list), P2P (U list).
+ * pot (device, [N] or NULL), grad (device, [N, 3] or NULL): outputs in the
+ *   caller's particle order, coef applied, self-interaction excluded.
+ * energy (device, [n_systems] doubles, or NULL): U_s = 1/2 sum_{i in s} q_i pot_i.
+ * Enqueues work only; never allocates; never synchronises.
+ */
+kifmm_status kifmm_evaluate(kifmm_plan *plan, void *pot, void *grad, double *energy,
+                            kifmm_stream_t stream);
+
+/*
+ * Rigid-clump aggregation (Sec. 2.3-2.4): charges sit on pebbles, forces are
+ * applied per pebble and summed into the clump force and the torque about the
+ * clump reference point:
+ *   F_c = sum_{k in c} F_k,  tau_c = sum_{k in c} (x_k - X_c) x F_k,
+ *   F_k = -q_k grad_k.
+ * clump_offsets (device): n_clumps + 1 ascending int64 offsets into the
+ *   caller's particle order; xyz, q, grad (device): [N,3], [N], [N,3] as passed
+ *   to set_sources / returned by evaluate; ref (device): [n_clumps, 3] X_c;
+ *   force, torque (device): [n_clumps, 3] outputs.  Accumulates in FP64.
+ */
+kifmm_status kifmm_clump_reduce(kifmm_plan *plan, int64_t n_clumps, const int64_t *clump_offsets,
+                                const void *xyz, const void *q, const void *grad, const void *ref,
+                                void *force, void *torque, kifmm_stream_t stream);
+
+/*
+ * Adjoint of evaluate with the tree frozen (not in the paper; it makes the
+ * evaluation differentiable).  With pot = A(x) q the FMM operator and a loss
+ * L with dL_dpot = w:
+ *   dq = A^T w,   dx_k = w_k grad_k + q_k grad_{x_k} (A^T w)_k
+ * computed by the transposed passes (no stored intermediates).
+ * dL_dpot (device, [N]); grad (device, [N,3]): the forward gradient (coef
+ * applied); dq (device, [N]), dx (device, [N,3]): outputs, caller order.
+ */
+kifmm_status kifmm_backward(kifmm_plan *plan, const void *dL_dpot, const void *grad, void *dq,
+                            void *dx, kifmm_stream_t stream);
+
+/* Synchronise the last stream used by the plan and read (then clear) the
+ * device status word.  code (host) receives a kifmm_status value. */
+kifmm_status kifmm_get_device_status(kifmm_plan *plan, int *code);
+
+/* Static description of a status code. */
+const char *kifmm_status_string(kifmm_status status);
+
+/* ------------------------------------------------------------------------
+ * Profiling.  When enabled, every stage of set_sources / evaluate is
+ * bracketed by CUDA events recorded on the call's stream (no extra
+ * synchronisation), and every kernel launch is counted.  kifmm_profile_read
+ * synchronises, returns the device time accumulated per stage since the
+ * last read (or enable) and resets the accumulators.
+ * ------------------------------------------------------------------------ */
+typedef enum {
+    KIFMM_STAGE_TREE = 0,  /* set_sources: bbox, keys, sort, octree, lists  */
+    KIFMM_STAGE_P2M = 1,
+    KIFMM_STAGE_M2M = 2,
+    KIFMM_STAGE_M2L = 3,
+    KIFMM_STAGE_P2L = 4,
+    KIFMM_STAGE_L2L = 5,
+    KIFMM_STAGE_LEAF = 6,  /* equivalent-density solves, L2P, M2P         */
+    KIFMM_STAGE_P2P = 7,
+    KIFMM_STAGE_OUT = 8,   /* scatter to caller order, energy             */
+    KIFMM_STAGE_COUNT = 9
+} kifmm_stage;
+
+typedef struct {
+    double ms[KIFMM_STAGE_COUNT]; /* summed device milliseconds per stage  */
+    int64_t calls[KIFMM_STAGE_COUNT]; /* bracketed occurrences per stage   */
+    int64_t launches;             /* kernels launched by the library       */
+} kifmm_profile_t;
+
+/* enable (host): 1 to record, 0 to stop. */
+kifmm_status kifmm_profile_enable(kifmm_plan *plan, int enable);
+/* out (host): accumulated times since the last read; resets them. */
+kifmm_status kifmm_profile_read(kifmm_plan *plan, kifmm_profile_t *out);
+
+/* ------------------------------------------------------------------------
+ * Introspection (tests and tools).  All outputs are host buffers sized by
+ * the caller from kifmm_tree_info; nodes are in canonical order (system,
+ * level, Morton prefix within the level).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n_particles;
+    int64_t n_boxes;
+    int max_level;
+    int n_systems;
+    int64_t n_u, n_v, n_w, n_x; /* total list entries */
+} kifmm_tree_info_t;
+
+kifmm_status kifmm_tree_info(kifmm_plan *plan, kifmm_tree_info_t *info);
+
+/* keys (host, [N] uint64): Morton keys in the caller's order;
+ * perm (host, [N] int64): perm[i] = caller index of the i-th sorted particle;
+ * lo_side (host, [n_systems, 4] double): root cube lo xyz and side. */
+kifmm_status kifmm_copy_keys(kifmm_plan *plan, uint64_t *keys, int64_t *perm, double *lo_side);
+
+/* Per node (host, [n_boxes] int64 each, NULL to skip): system, level, integer
+ * coordinates (3 per node), first sorted particle, count, parent (-1 root). */
+kifmm_status kifmm_copy_tree(kifmm_plan *plan, int64_t *sys, int64_t *level, int64_t *coord,
+                             int64_t *first, int64_t *count, int64_t *parent);
+
+/* One list kind (0 = U, 1 = V, 2 = W, 3 = X) as CSR over nodes:
+ * ptr (host, [n_boxes + 1]), idx (host, [n_kind]); sources of each node are
+ * sorted ascending. */
+kifmm_status kifmm_copy_list(kifmm_plan *plan, int kind, int64_t *ptr, int64_t *idx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KIFMM_H */

@@ -1,0 +1,6 @@
+"""GB300 (sm_103a) kernel-independent FMM for long-range forces in DEM.
+
+The compute path is the C-ABI library lib/libkifmm.so (CUDA kernels); the
+Python layer (kifmm.py) only marshals arguments.
+"""
+from .kifmm import Plan, KifmmError, load, PRECISIONS  # noqa: F401

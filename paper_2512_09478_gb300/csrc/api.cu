@@ -1,0 +1,521 @@
+// C ABI of the KIFMM library: plan lifecycle, argument validation, workspace
+// management, orchestration of the tree build and of the evaluation passes,
+// and host-side introspection for tests.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using kifmm::Plan;
+
+struct kifmm_plan {
+    Plan P;
+};
+
+namespace kifmm {
+
+thread_local long long g_launches = 0;
+
+void stage_begin(Plan &P, int stage, cudaStream_t s) {
+    if (!P.prof) return;
+    if (P.ev_used + 2 > P.ev_pool.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            P.ev_pool.push_back(e);
+        }
+    }
+    const int i = (int)P.ev_used;
+    P.ev_used += 2;
+    cudaEventRecord(P.ev_pool[i], s);
+    P.ev_pending.push_back({stage, i});
+}
+
+void stage_end(Plan &P, int stage, cudaStream_t s) {
+    if (!P.prof) return;
+    for (auto it = P.ev_pending.rbegin(); it != P.ev_pending.rend(); ++it)
+        if (it->first == stage) {
+            cudaEventRecord(P.ev_pool[it->second + 1], s);
+            return;
+        }
+}
+
+static cudaError_t profile_collect(Plan &P) {
+    for (const auto &pe : P.ev_pending) {
+        KIFMM_CUDA_TRY(cudaEventSynchronize(P.ev_pool[pe.second + 1]));
+        float ms = 0.f;
+        KIFMM_CUDA_TRY(cudaEventElapsedTime(&ms, P.ev_pool[pe.second], P.ev_pool[pe.second + 1]));
+        P.prof_ms[pe.first] += ms;
+        P.prof_calls[pe.first] += 1;
+    }
+    P.ev_pending.clear();
+    P.ev_used = 0;
+    return cudaSuccess;
+}
+
+cudaError_t plan_alloc(Plan &P, void **ptr, size_t bytes) {
+    if (*ptr) {
+        for (auto it = P.owned.begin(); it != P.owned.end(); ++it)
+            if (it->ptr == *ptr) {
+                cudaFree(it->ptr);
+                P.owned.erase(it);
+                break;
+            }
+        *ptr = nullptr;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    P.owned.push_back({p, bytes});
+    *ptr = p;
+    return cudaSuccess;
+}
+
+cudaError_t plan_grow(Plan &P, void **ptr, size_t bytes, size_t keep_bytes) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    if (*ptr && keep_bytes) {
+        e = cudaMemcpy(p, *ptr, keep_bytes, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return e;
+        }
+    }
+    if (*ptr) {
+        for (auto it = P.owned.begin(); it != P.owned.end(); ++it)
+            if (it->ptr == *ptr) {
+                cudaFree(it->ptr);
+                P.owned.erase(it);
+                break;
+            }
+    }
+    P.owned.push_back({p, bytes});
+    *ptr = p;
+    return cudaSuccess;
+}
+
+// Per-node arrays used while the octree is built.
+cudaError_t grow_tree_arrays(Plan &P, int64_t cap, int64_t keep) {
+    KIFMM_CUDA_TRY(cudaDeviceSynchronize());
+    int32_t **arrs[] = {&P.lvl, &P.cx, &P.cy, &P.cz, &P.first, &P.cnt, &P.parent, &P.child_first, &P.nchild, &P.sys};
+    for (int32_t **a : arrs)
+        KIFMM_CUDA_TRY(plan_grow(P, (void **)a, sizeof(int32_t) * cap, sizeof(int32_t) * keep));
+    KIFMM_CUDA_TRY(plan_grow(P, (void **)&P.tmp_nchild, sizeof(uint32_t) * 2 * cap, sizeof(uint32_t) * keep));
+    KIFMM_CUDA_TRY(plan_grow(P, (void **)&P.child_rng, sizeof(int32_t) * 16 * cap, sizeof(int32_t) * 16 * keep));
+    P.box_cap = cap;
+    const size_t need = scan_tmp_needed(2 * cap) + 8;
+    if (need > P.scan_tmp_elems) {
+        P.scan_tmp_elems = need;
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.scan_tmp, sizeof(uint32_t) * need));
+    }
+    return cudaSuccess;
+}
+
+// Per-box arrays sized after the tree is known.
+static cudaError_t ensure_box_arrays(Plan &P) {
+    if (P.nb <= P.list_cap) return cudaSuccess;
+    const int64_t cap = P.nb + P.nb / 4 + 256;
+    const size_t esz = P.f64 ? sizeof(double) : sizeof(float);
+    struct A { void **p; size_t bytes; };
+    const A arrs[] = {
+        {(void **)&P.coll, sizeof(int32_t) * kColl * cap},
+        {(void **)&P.coarse, sizeof(int32_t) * kMaxCoarse * cap},
+        {(void **)&P.ncoarse, sizeof(int32_t) * cap},
+        {(void **)&P.vdense, sizeof(int32_t) * kVSlots * cap},
+        {(void **)&P.nv, sizeof(int32_t) * cap},
+        {(void **)&P.xdense, sizeof(int32_t) * kMaxCoarse * cap},
+        {(void **)&P.nx, sizeof(int32_t) * cap},
+        {(void **)&P.u_ptr, sizeof(uint32_t) * (cap + 1)},
+        {(void **)&P.w_ptr, sizeof(uint32_t) * (cap + 1)},
+        {(void **)&P.u_cnt, sizeof(uint32_t) * cap},
+        {(void **)&P.w_cnt, sizeof(uint32_t) * cap},
+        {(void **)&P.m2l_targets, sizeof(int32_t) * cap},
+        {(void **)&P.leaves, sizeof(int32_t) * cap},
+        {(void **)&P.wsrc_flag, sizeof(int32_t) * cap},
+        {&P.u_chk, esz * P.ns * cap},
+        {&P.d_chk, esz * P.ns * cap},
+        {&P.up_dens, esz * P.ns * cap},
+    };
+    for (const A &a : arrs) KIFMM_CUDA_TRY(plan_alloc(P, a.p, a.bytes));
+    P.list_cap = cap;
+    return cudaSuccess;
+}
+
+static cudaError_t ensure_partition_arrays(Plan &P) {
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.part_keys, sizeof(uint64_t) * 2 * P.box_cap));
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.part_vals, sizeof(uint32_t) * 2 * P.box_cap));
+    return cudaSuccess;
+}
+
+}  // namespace kifmm
+
+using namespace kifmm;
+
+static kifmm_status from_cuda(cudaError_t e) {
+    return e == cudaSuccess ? KIFMM_OK : KIFMM_ERR_CUDA;
+}
+
+#define API_CUDA(expr)                          \
+    do {                                        \
+        cudaError_t e_ = (expr);                \
+        if (e_ != cudaSuccess) {                \
+            (void)cudaGetLastError();           \
+            return KIFMM_ERR_CUDA;              \
+        }                                       \
+    } while (0)
+
+extern "C" {
+
+static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cudaStream_t s);
+
+const char *kifmm_status_string(kifmm_status s) {
+    switch (s) {
+        case KIFMM_OK: return "ok";
+        case KIFMM_ERR_ARG: return "invalid argument";
+        case KIFMM_ERR_CAPACITY: return "capacity exceeded";
+        case KIFMM_ERR_CUDA: return "CUDA runtime error";
+        case KIFMM_ERR_NONFINITE: return "non-finite position or charge";
+        case KIFMM_ERR_TIMEOUT: return "device wait timed out";
+        case KIFMM_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
+    if (!desc || !out) return KIFMM_ERR_ARG;
+    *out = nullptr;
+    const kifmm_plan_desc &d = *desc;
+    if (d.p < 2 || d.p > 10 || d.leaf_cap < 1 || d.max_depth < 1 || d.max_depth > kMaxLevel) return KIFMM_ERR_ARG;
+    if (d.precision < KIFMM_FP64 || d.precision > KIFMM_MIXED_FP16) return KIFMM_ERR_ARG;
+    if (d.n_max < 1 || d.n_max > (int64_t)0x7fffffff || d.n_systems_max < 1) return KIFMM_ERR_ARG;
+    if (d.dtype != KIFMM_DTYPE_F32 && d.dtype != KIFMM_DTYPE_F64) return KIFMM_ERR_ARG;
+    if (!(d.pinv_eps >= 0.0) || d.pinv_eps >= 1.0) return KIFMM_ERR_ARG;
+    kifmm_plan *pl = new (std::nothrow) kifmm_plan();
+    if (!pl) return KIFMM_ERR_CUDA;
+    Plan &P = pl->P;
+    P.desc = d;
+    P.p = d.p;
+    P.ns = 6 * (d.p - 1) * (d.p - 1) + 2;
+    P.f64 = (d.precision == KIFMM_FP64);
+    P.io_f64 = (d.dtype == KIFMM_DTYPE_F64);
+    P.coef = (d.coef == 0.0) ? 1.0 : d.coef;
+    P.eps = (d.pinv_eps == 0.0) ? 1e-12 : d.pinv_eps;
+    auto fail = [&](kifmm_status st) {
+        kifmm_plan_destroy(pl);
+        (void)cudaGetLastError();
+        return st;
+    };
+    if (cudaGetDevice(&P.device) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, P.device);
+    std::string err;
+    cudaError_t e = build_operators(P, err);
+    if (e == cudaErrorInvalidValue) return fail(KIFMM_ERR_ARG);
+    if (e != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    if (d.precision == KIFMM_MIXED_TF32) return fail(KIFMM_ERR_ARG);  // not built yet
+    if (d.precision == KIFMM_MIXED_FP16) {
+        e = m2l_tensor_setup(P);
+        if (e == cudaErrorNotSupported) return fail(KIFMM_ERR_ARG);
+        if (e != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    }
+    // workspace for n_max particles
+    const int64_t n = d.n_max;
+    P.n_cap = n;
+    P.sys_cap = d.n_systems_max;
+    const size_t esz = P.f64 ? sizeof(double) : sizeof(float);
+    const int64_t nblk = (n + 4095) / 4096;
+    P.hist_elems = (size_t)512 * nblk;
+    struct A { void **p; size_t bytes; };
+    const A arrs[] = {
+        {(void **)&P.keys[0], sizeof(uint64_t) * n},   {(void **)&P.keys[1], sizeof(uint64_t) * n},
+        {(void **)&P.vals[0], sizeof(uint32_t) * n},   {(void **)&P.vals[1], sizeof(uint32_t) * n},
+        {(void **)&P.keys_user, sizeof(uint64_t) * n}, {(void **)&P.perm, sizeof(uint32_t) * n},
+        {&P.pts, esz * 4 * n},                         {(void **)&P.res, sizeof(double) * 4 * n},
+        {(void **)&P.sys_off_d, sizeof(int64_t) * (P.sys_cap + 1)},
+        {(void **)&P.lo_side, sizeof(double) * 4 * P.sys_cap},
+        {(void **)&P.bbox_ord, sizeof(unsigned long long) * 6 * P.sys_cap},
+        {(void **)&P.hist, sizeof(uint32_t) * P.hist_elems},
+        {(void **)&P.status, sizeof(int)},
+        {(void **)&P.part_counts, sizeof(uint32_t) * 16},
+        {(void **)&P.energy_chunk_start, sizeof(int32_t) * (P.sys_cap + 1)},
+    };
+    for (const A &a : arrs)
+        if (plan_alloc(P, a.p, a.bytes) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    const int64_t box0 = 12 * (n / (d.leaf_cap + 1)) + 64LL * P.sys_cap + 1024;
+    if (grow_tree_arrays(P, box0, 0) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    P.scan_tmp_elems = std::max(P.scan_tmp_elems, scan_tmp_needed((int64_t)256 * nblk) + 8);
+    if (plan_alloc(P, (void **)&P.scan_tmp, sizeof(uint32_t) * P.scan_tmp_elems) != cudaSuccess)
+        return fail(KIFMM_ERR_CUDA);
+    if (cudaMemset(P.status, 0, sizeof(int)) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    *out = pl;
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_plan_destroy(kifmm_plan *pl) {
+    if (!pl) return KIFMM_ERR_ARG;
+    cudaDeviceSynchronize();
+    m2l_tensor_release(pl->P);
+    for (auto &b : pl->P.owned) cudaFree(b.ptr);
+    pl->P.owned.clear();
+    for (cudaEvent_t e : pl->P.ev_pool) cudaEventDestroy(e);
+    delete pl;
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_set_sources(kifmm_plan *pl, int n_systems, const int64_t *sys_offsets, const void *xyz,
+                               const void *q, kifmm_stream_t stream) {
+    if (!pl || !sys_offsets || !xyz || !q) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (n_systems < 1) return KIFMM_ERR_ARG;
+    if (n_systems > P.sys_cap) return KIFMM_ERR_CAPACITY;
+    if (sys_offsets[0] != 0) return KIFMM_ERR_ARG;
+    for (int s = 0; s < n_systems; ++s)
+        if (sys_offsets[s + 1] <= sys_offsets[s]) return KIFMM_ERR_ARG;
+    const int64_t n = sys_offsets[n_systems];
+    if (n > P.n_cap) return KIFMM_ERR_CAPACITY;
+    cudaStream_t s = (cudaStream_t)stream;
+    P.last_stream = s;
+    P.has_sources = false;
+    P.n = n;
+    P.n_sys = n_systems;
+    P.sys_off_h.assign(sys_offsets, sys_offsets + n_systems + 1);
+    const long long l0 = g_launches;
+    stage_begin(P, KIFMM_STAGE_TREE, s);
+    kifmm_status rc = set_sources_impl(P, xyz, q, s);
+    stage_end(P, KIFMM_STAGE_TREE, s);
+    P.launches += g_launches - l0;
+    return rc;
+}
+
+static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cudaStream_t s) {
+    const int n_systems = P.n_sys;
+    const int64_t *sys_offsets = P.sys_off_h.data();
+    API_CUDA(cudaMemsetAsync(P.status, 0, sizeof(int), s));
+    API_CUDA(build_tree(P, xyz, q, s));
+    int st = 0;
+    API_CUDA(cudaMemcpyAsync(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    API_CUDA(cudaStreamSynchronize(s));
+    if (st != 0) return (kifmm_status)st;
+    API_CUDA(ensure_box_arrays(P));
+    API_CUDA(build_lists(P, s));
+    API_CUDA(ensure_partition_arrays(P));
+    API_CUDA(partition_boxes(P, s));
+    if (P.desc.precision == KIFMM_MIXED_FP16) API_CUDA(m2l_tensor_tiles(P, s));
+    // list totals for V and X
+    {
+        std::vector<int32_t> nv(P.nb), nx(P.nb);
+        API_CUDA(cudaMemcpyAsync(nv.data(), P.nv, sizeof(int32_t) * P.nb, cudaMemcpyDeviceToHost, s));
+        API_CUDA(cudaMemcpyAsync(nx.data(), P.nx, sizeof(int32_t) * P.nb, cudaMemcpyDeviceToHost, s));
+        API_CUDA(cudaStreamSynchronize(s));
+        P.n_v = 0;
+        P.n_x = 0;
+        for (int64_t b = 0; b < P.nb; ++b) {
+            P.n_v += nv[b];
+            P.n_x += nx[b];
+        }
+    }
+    // energy chunks (sorted order never mixes systems)
+    {
+        std::vector<int64_t> ch;
+        std::vector<int32_t> start(n_systems + 1, 0);
+        for (int sy = 0; sy < n_systems; ++sy) {
+            start[sy] = (int32_t)(ch.size() / 2);
+            for (int64_t a = sys_offsets[sy]; a < sys_offsets[sy + 1]; a += 4096) {
+                ch.push_back(a);
+                ch.push_back(std::min(a + 4096, sys_offsets[sy + 1]));
+            }
+        }
+        start[n_systems] = (int32_t)(ch.size() / 2);
+        const int64_t nch = (int64_t)ch.size() / 2;
+        if (nch > P.n_energy_chunks) {
+            API_CUDA(plan_alloc(P, (void **)&P.energy_chunks, sizeof(int64_t) * 2 * nch));
+            API_CUDA(plan_alloc(P, (void **)&P.energy_partial, sizeof(double) * nch));
+        }
+        P.n_energy_chunks = nch;
+        API_CUDA(cudaMemcpyAsync(P.energy_chunks, ch.data(), sizeof(int64_t) * ch.size(), cudaMemcpyHostToDevice, s));
+        API_CUDA(cudaMemcpyAsync(P.energy_chunk_start, start.data(), sizeof(int32_t) * start.size(),
+                                 cudaMemcpyHostToDevice, s));
+        API_CUDA(cudaStreamSynchronize(s));
+    }
+    API_CUDA(cudaMemcpyAsync(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    API_CUDA(cudaStreamSynchronize(s));
+    if (st != 0) return (kifmm_status)st;
+    P.has_sources = true;
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_evaluate(kifmm_plan *pl, void *pot, void *grad, double *energy, kifmm_stream_t stream) {
+    if (!pl) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!P.has_sources) return KIFMM_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    P.last_stream = s;
+    const long long l0 = g_launches;
+    cudaError_t e = run_evaluate(P, pot, grad, energy, s);
+    P.launches += g_launches - l0;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return KIFMM_ERR_CUDA;
+    }
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_clump_reduce(kifmm_plan *pl, int64_t n_clumps, const int64_t *clump_offsets, const void *xyz,
+                                const void *q, const void *grad, const void *ref, void *force, void *torque,
+                                kifmm_stream_t stream) {
+    if (!pl || n_clumps < 0) return KIFMM_ERR_ARG;
+    if (n_clumps > 0 && (!clump_offsets || !xyz || !q || !grad || !ref || !force || !torque)) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    cudaStream_t s = (cudaStream_t)stream;
+    P.last_stream = s;
+    return from_cuda(run_clump_reduce(P, n_clumps, clump_offsets, xyz, q, grad, ref, force, torque, s));
+}
+
+kifmm_status kifmm_backward(kifmm_plan *pl, const void *dL_dpot, const void *grad, void *dq, void *dx,
+                            kifmm_stream_t stream) {
+    (void)dL_dpot;
+    (void)grad;
+    (void)dq;
+    (void)dx;
+    (void)stream;
+    if (!pl) return KIFMM_ERR_ARG;
+    return KIFMM_ERR_STATE;
+}
+
+kifmm_status kifmm_get_device_status(kifmm_plan *pl, int *code) {
+    if (!pl || !code) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    API_CUDA(cudaStreamSynchronize(P.last_stream));
+    int st = 0;
+    API_CUDA(cudaMemcpy(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost));
+    API_CUDA(cudaMemset(P.status, 0, sizeof(int)));
+    *code = st;
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_profile_enable(kifmm_plan *pl, int enable) {
+    if (!pl) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!enable && P.prof) API_CUDA(profile_collect(P));
+    P.prof = enable != 0;
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_profile_read(kifmm_plan *pl, kifmm_profile_t *out) {
+    if (!pl || !out) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    API_CUDA(profile_collect(P));
+    for (int k = 0; k < KIFMM_STAGE_COUNT; ++k) {
+        out->ms[k] = P.prof_ms[k];
+        out->calls[k] = P.prof_calls[k];
+        P.prof_ms[k] = 0.0;
+        P.prof_calls[k] = 0;
+    }
+    out->launches = P.launches;
+    P.launches = 0;
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_tree_info(kifmm_plan *pl, kifmm_tree_info_t *info) {
+    if (!pl || !info) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!P.has_sources) return KIFMM_ERR_STATE;
+    info->n_particles = P.n;
+    info->n_boxes = P.nb;
+    info->max_level = P.max_level;
+    info->n_systems = P.n_sys;
+    info->n_u = P.n_u;
+    info->n_v = P.n_v;
+    info->n_w = P.n_w;
+    info->n_x = P.n_x;
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_copy_keys(kifmm_plan *pl, uint64_t *keys, int64_t *perm, double *lo_side) {
+    if (!pl) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!P.has_sources) return KIFMM_ERR_STATE;
+    API_CUDA(cudaDeviceSynchronize());
+    if (keys) API_CUDA(cudaMemcpy(keys, P.keys_user, sizeof(uint64_t) * P.n, cudaMemcpyDeviceToHost));
+    if (perm) {
+        std::vector<uint32_t> p(P.n);
+        API_CUDA(cudaMemcpy(p.data(), P.perm, sizeof(uint32_t) * P.n, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < P.n; ++i) perm[i] = p[i];
+    }
+    if (lo_side) API_CUDA(cudaMemcpy(lo_side, P.lo_side, sizeof(double) * 4 * P.n_sys, cudaMemcpyDeviceToHost));
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_copy_tree(kifmm_plan *pl, int64_t *sys, int64_t *level, int64_t *coord, int64_t *first,
+                             int64_t *count, int64_t *parent) {
+    if (!pl) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!P.has_sources) return KIFMM_ERR_STATE;
+    API_CUDA(cudaDeviceSynchronize());
+    const int64_t nb = P.nb;
+    std::vector<int32_t> t(nb);
+    auto get = [&](const int32_t *src, int64_t *dst, int stride, int off) -> cudaError_t {
+        cudaError_t e = cudaMemcpy(t.data(), src, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        for (int64_t b = 0; b < nb; ++b) dst[b * stride + off] = t[b];
+        return cudaSuccess;
+    };
+    if (sys) API_CUDA(get(P.sys, sys, 1, 0));
+    if (level) API_CUDA(get(P.lvl, level, 1, 0));
+    if (coord) {
+        API_CUDA(get(P.cx, coord, 3, 0));
+        API_CUDA(get(P.cy, coord, 3, 1));
+        API_CUDA(get(P.cz, coord, 3, 2));
+    }
+    if (first) API_CUDA(get(P.first, first, 1, 0));
+    if (count) API_CUDA(get(P.cnt, count, 1, 0));
+    if (parent) API_CUDA(get(P.parent, parent, 1, 0));
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_copy_list(kifmm_plan *pl, int kind, int64_t *ptr, int64_t *idx) {
+    if (!pl || !ptr || kind < 0 || kind > 3) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!P.has_sources) return KIFMM_ERR_STATE;
+    API_CUDA(cudaDeviceSynchronize());
+    const int64_t nb = P.nb;
+    std::vector<std::vector<int64_t>> lists(nb);
+    if (kind == 0 || kind == 2) {
+        std::vector<uint32_t> p(nb + 1);
+        const int64_t tot = (kind == 0) ? P.n_u : P.n_w;
+        std::vector<int32_t> ix(std::max<int64_t>(tot, 1));
+        API_CUDA(cudaMemcpy(p.data(), kind == 0 ? P.u_ptr : P.w_ptr, sizeof(uint32_t) * (nb + 1),
+                            cudaMemcpyDeviceToHost));
+        if (tot) API_CUDA(cudaMemcpy(ix.data(), kind == 0 ? P.u_idx : P.w_idx, sizeof(int32_t) * tot,
+                                     cudaMemcpyDeviceToHost));
+        for (int64_t b = 0; b < nb; ++b)
+            for (uint32_t e = p[b]; e < p[b + 1]; ++e) lists[b].push_back(ix[e]);
+    } else if (kind == 1) {
+        std::vector<int32_t> v((size_t)nb * kVSlots);
+        API_CUDA(cudaMemcpy(v.data(), P.vdense, sizeof(int32_t) * v.size(), cudaMemcpyDeviceToHost));
+        for (int64_t b = 0; b < nb; ++b)
+            for (int sl = 0; sl < kVSlots; ++sl)
+                if (v[(size_t)b * kVSlots + sl] >= 0) lists[b].push_back(v[(size_t)b * kVSlots + sl]);
+    } else {
+        std::vector<int32_t> x((size_t)nb * kMaxCoarse), nx(nb);
+        API_CUDA(cudaMemcpy(x.data(), P.xdense, sizeof(int32_t) * x.size(), cudaMemcpyDeviceToHost));
+        API_CUDA(cudaMemcpy(nx.data(), P.nx, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
+        for (int64_t b = 0; b < nb; ++b)
+            for (int k = 0; k < nx[b]; ++k) lists[b].push_back(x[(size_t)b * kMaxCoarse + k]);
+    }
+    ptr[0] = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        std::sort(lists[b].begin(), lists[b].end());
+        ptr[b + 1] = ptr[b] + (int64_t)lists[b].size();
+        if (idx)
+            for (size_t k = 0; k < lists[b].size(); ++k) idx[ptr[b] + k] = lists[b][k];
+    }
+    return KIFMM_OK;
+}
+
+}  // extern "C"

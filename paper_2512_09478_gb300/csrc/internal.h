@@ -1,0 +1,172 @@
+// Internal declarations of the KIFMM library: the plan object and the host
+// launchers implemented in the .cu translation units.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/kifmm.h"
+
+namespace kifmm {
+
+constexpr int kMaxLevel = 20;       // 21-bit quantisation per axis
+constexpr int kNumM2L = 316;        // offsets in {-3..3}^3 minus {-1..1}^3
+constexpr int kVSlots = 189;        // V-list slots per octant class (6^3 - 3^3)
+constexpr int kMaxCoarse = 26;      // coarser-or-equal adjacent leaves of a box
+constexpr int kColl = 27;           // colleague slots (3^3, centre = self)
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Device-side status codes share the kifmm_status numbering.
+struct Plan {
+    kifmm_plan_desc desc{};
+    int device = 0;
+    int p = 0, ns = 0;        // surface order, surface points
+    bool f64 = false;         // compute type is double (FP64 mode)
+    int io_f64 = 0;           // caller dtype is double
+    double coef = 1.0;
+    double eps = 1e-12;
+    int num_sms = 0;
+
+    // ---- operators (device) ----
+    double *surf64 = nullptr;   // [ns*3] unit-cube surface points
+    float *surf32 = nullptr;
+    // Composite translation operators in "check-potential" form, stored
+    // transposed ([o][k][j]) in the compute type:
+    void *m2m_t = nullptr;      // [8][ns][ns]   u(child)  -> u(parent)
+    void *l2l_t = nullptr;      // [8][ns][ns]   d(parent) -> d(child)
+    void *m2l_t = nullptr;      // [316][ns][ns] u(source) -> d(target)
+    // Two-step pseudo-inverses for leaf evaluation: dens = V (W chk),
+    // W = diag(sinv) U^T, both stored transposed ([k][j]).
+    void *up_w_t = nullptr, *up_v_t = nullptr;
+    void *dn_w_t = nullptr, *dn_v_t = nullptr;
+    // Tensor-core M2L operands (mixed modes), built lazily.
+    void *m2l_tc = nullptr;     // layout owned by the tensor-core kernel
+    float *m2l_tc_scale = nullptr;
+    int *slot_off = nullptr;    // [8][189] V slot -> M2L offset index (-1 unused)
+
+    // ---- capacities ----
+    int64_t n_cap = 0, box_cap = 0, u_cap = 0, w_cap = 0;
+    int sys_cap = 0;
+
+    // ---- particles ----
+    uint64_t *keys[2] = {nullptr, nullptr};
+    uint32_t *vals[2] = {nullptr, nullptr};
+    uint64_t *keys_user = nullptr;  // keys in caller order (introspection)
+    uint32_t *perm = nullptr;       // sorted -> caller index
+    void *pts = nullptr;            // [N] {dx, dy, dz, q} leaf-relative, compute type
+    double *near_pot = nullptr;     // scratch accumulators (FP64 final sums)
+    int64_t *sys_off_d = nullptr;   // [S+1]
+    double *lo_side = nullptr;      // [S][4]
+    unsigned long long *bbox_ord = nullptr;  // [S][6]
+    uint32_t *scan_tmp = nullptr;   // scan scratch
+    size_t scan_tmp_elems = 0;
+    uint32_t *hist = nullptr;       // radix histograms
+    size_t hist_elems = 0;
+
+    // ---- tree (canonical order: level, system, Morton prefix) ----
+    int32_t *lvl = nullptr, *cx = nullptr, *cy = nullptr, *cz = nullptr;
+    int32_t *first = nullptr, *cnt = nullptr, *parent = nullptr, *child_first = nullptr,
+            *nchild = nullptr, *sys = nullptr;
+    uint32_t *tmp_nchild = nullptr;   // per node scratch
+    int32_t *child_rng = nullptr;     // [box][16] scratch: (first, count) per octant
+    std::vector<int64_t> level_start;  // host: level l owns [level_start[l], level_start[l+1])
+    int64_t nb = 0, n = 0;
+    int n_sys = 0, max_level = 0;
+    std::vector<int64_t> sys_off_h;
+
+    // ---- lists ----
+    int32_t *coll = nullptr;         // [nb][27]
+    int32_t *coarse = nullptr;       // [nb][26] coarser-or-equal adjacent leaves
+    int32_t *ncoarse = nullptr;      // [nb]
+    int32_t *vdense = nullptr;       // [nb][189] source box per slot, -1 if none
+    int32_t *nv = nullptr;           // [nb]
+    int32_t *xdense = nullptr;       // [nb][26]
+    int32_t *nx = nullptr;           // [nb]
+    uint32_t *u_ptr = nullptr, *w_ptr = nullptr;  // [nb+1]
+    int32_t *u_idx = nullptr, *w_idx = nullptr;
+    uint32_t *u_cnt = nullptr, *w_cnt = nullptr;  // [nb] scratch
+    int64_t n_u = 0, n_v = 0, n_w = 0, n_x = 0;
+    // M2L work: targets grouped by octant class
+    int32_t *m2l_targets = nullptr;  // [nb] boxes with a V list, class-major
+    int64_t m2l_class_start[9] = {0};
+    int32_t *leaves = nullptr;       // [nb] leaf indices
+    int64_t n_leaves = 0;
+    int32_t *wsrc_flag = nullptr;    // [nb] 1 if the box is in some W list
+    void *part_keys = nullptr;       // [2][box_cap] u64 partition scratch
+    void *part_vals = nullptr;       // [2][box_cap] u32
+    uint32_t *part_counts = nullptr; // [16]
+    int64_t list_cap = 0;            // boxes the per-box list/expansion arrays hold
+
+    // ---- expansions (compute type) ----
+    void *u_chk = nullptr;   // [nb][ns] upward check potentials
+    void *d_chk = nullptr;   // [nb][ns] downward check potentials
+    void *up_dens = nullptr; // [nb][ns] normalised upward densities (W sources)
+
+    // ---- results in sorted order ----
+    double *res = nullptr;   // [N][4] pot, gx, gy, gz (normalised units, FP64 final)
+    // energy reduction: chunks of sorted particles that never straddle systems
+    int64_t *energy_chunks = nullptr;     // [n_chunks][2] (begin, end)
+    int32_t *energy_chunk_start = nullptr; // [S+1]
+    double *energy_partial = nullptr;     // [n_chunks]
+    int64_t n_energy_chunks = 0;
+
+    // ---- profiling ----
+    bool prof = false;
+    int64_t launches = 0;
+    std::vector<cudaEvent_t> ev_pool;             // created lazily
+    std::vector<std::pair<int, int>> ev_pending;  // (stage, event index of the start)
+    size_t ev_used = 0;
+    double prof_ms[KIFMM_STAGE_COUNT] = {0};
+    int64_t prof_calls[KIFMM_STAGE_COUNT] = {0};
+
+    // ---- status ----
+    int *status = nullptr;   // device status word
+    cudaStream_t last_stream = nullptr;
+    bool has_sources = false;
+
+    std::vector<DevBuf> owned;
+};
+
+// allocation helpers (tracked, freed with the plan).  plan_alloc replaces
+// *ptr (freeing a previous tracked buffer); plan_grow keeps the first
+// keep_bytes of the old contents.
+cudaError_t plan_alloc(Plan &P, void **ptr, size_t bytes);
+cudaError_t plan_grow(Plan &P, void **ptr, size_t bytes, size_t keep_bytes);
+cudaError_t grow_tree_arrays(Plan &P, int64_t new_cap, int64_t keep);
+
+// Stage bracketing (no-ops unless profiling is enabled).
+void stage_begin(Plan &P, int stage, cudaStream_t s);
+void stage_end(Plan &P, int stage, cudaStream_t s);
+inline void count_launch(Plan &P, int64_t k = 1) { P.launches += k; }
+
+// ---- tree.cu ----
+cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s);
+cudaError_t build_lists(Plan &P, cudaStream_t s);
+cudaError_t partition_boxes(Plan &P, cudaStream_t s);
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total_dev,
+                               uint32_t *tmp, size_t tmp_elems, cudaStream_t s);
+size_t scan_tmp_needed(int64_t n);
+
+// ---- operators.cu ----
+cudaError_t build_operators(Plan &P, std::string &err);
+
+// ---- m2l_tc.cu (mixed modes) ----
+cudaError_t m2l_tensor_setup(Plan &P);
+cudaError_t m2l_tensor_tiles(Plan &P, cudaStream_t s);
+cudaError_t m2l_tensor(Plan &P, cudaStream_t s);
+void m2l_tensor_release(Plan &P);
+
+// ---- fmm.cu ----
+cudaError_t run_evaluate(Plan &P, void *pot, void *grad, double *energy, cudaStream_t s);
+cudaError_t run_clump_reduce(Plan &P, int64_t n_clumps, const int64_t *offs, const void *xyz,
+                             const void *q, const void *grad, const void *ref, void *force,
+                             void *torque, cudaStream_t s);
+
+}  // namespace kifmm

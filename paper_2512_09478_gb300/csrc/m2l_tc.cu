@@ -1,0 +1,499 @@
+// M2L on the Blackwell tensor cores (tcgen05 / TMEM), mixed-precision modes.
+//
+// The V-list translations (Sec. 2.2: M2L between boxes in each other's far
+// zone but not in their parents') are, for one octant class c of targets,
+//     d(t) = sum_{s < 189} M_{off(c,s)} u(src(t, s))
+// i.e. a sum over 189 slots of a [targets x K] x [K x N] product with gathered
+// rows.  A CTA owns 128 targets of one class (one row each, M = 128) and all
+// N = n_s check points (padded to a multiple of 16); the FP32 accumulator
+// lives in TMEM (128 lanes x N columns).
+//
+// Precision (3xFP16): every operand x is split as x*sigma = hi + lo with hi,
+// lo in FP16 and sigma a power of two (per tree level for the expansions, one
+// for all operators); the product keeps hi*hi + hi*lo + lo*hi (the lo*lo term
+// is below 2^-22 of the product) and the epilogue divides by sigma_A sigma_B.
+//
+// Pipeline (per CTA, 160 threads):
+//   warps 0-3  producers: cp.async (16 B, L2) of the gathered A rows and of the
+//              slot's B rows into a ring of shared-memory stages laid out in
+//              the 64-byte swizzled K-major form; completion is tracked by the
+//              stage's "full" mbarrier (cp.async.mbarrier.arrive.noinc).
+//   warp 4     allocates TMEM; one thread issues tcgen05.mma for each stage
+//              and frees the stage with tcgen05.commit on its "empty" barrier.
+//   warps 0-3  epilogue: tcgen05.ld of their 32 TMEM lanes, unscale, store.
+// Every wait is bounded; on time-out the CTA records KIFMM_ERR_TIMEOUT, drains
+// its own copies and MMAs (bounded), frees TMEM and returns.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace kifmm {
+
+namespace {
+
+constexpr int kTcThreads = 160;
+constexpr int kTcRows = 128;        // targets per CTA (MMA M)
+constexpr int kKBlock = 32;         // FP16 elements per stage row (64 bytes)
+constexpr int kRowBytes = 64;
+constexpr long long kWaitIters = 1LL << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on one mbarrier phase; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    for (long long i = 0; i < kWaitIters; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, rows of 64 bytes,
+// 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;           // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;           // descriptor version
+    d |= (uint64_t)4 << 61;           // SWIZZLE_64B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP16 A and B, FP32 accumulate, both
+// K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_f16(int n) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// 32 lanes x 32 columns of 32-bit TMEM data -> 32 registers per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TileArgs {
+    const int32_t *targets;   // class-major target boxes
+    const int4 *tiles;        // (class, begin, end, unused)
+    const int32_t *vdense;    // [nb][189]
+    const int *slot_off;      // [8][189]
+    const __half *uh, *ul;    // [nb][kp] scaled expansions
+    const __half *bh, *bl;    // [316][np][kp] scaled operators
+    const int32_t *lvl;
+    const float *level_unscale;  // 1 / (sigma_A(level) sigma_B)
+    float *d;                 // [nb][ns]
+    int ns, kp, np, nstages;
+    int *status;
+};
+
+// Byte offset of 16-byte chunk c of row r inside a 64-byte-swizzled tile.
+__device__ __forceinline__ uint32_t swz64(int r, int c) {
+    return (uint32_t)(r * kRowBytes + ((c ^ ((r >> 1) & 3)) << 4));
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int np = a.np, kp = a.kp, NS = a.nstages;
+    const uint32_t a_bytes = kTcRows * kRowBytes;            // one of hi / lo
+    const uint32_t b_bytes = (uint32_t)np * kRowBytes;
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;  // multiple of 512
+    __shared__ __align__(8) uint64_t full_bar[16], empty_bar[16], done_bar;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int32_t tgt_s[kTcRows];
+    __shared__ volatile int abort_s;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int4 tile = a.tiles[blockIdx.x];
+    const int cls = tile.x;
+    if (threadIdx.x < kTcRows) {
+        const int i = tile.y + threadIdx.x;
+        tgt_s[threadIdx.x] = (i < tile.z) ? a.targets[i] : -1;
+    }
+    if (threadIdx.x == 0) {
+        abort_s = 0;
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), kTcRows);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&done_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const uint32_t tmem_cols = (np <= 32) ? 32 : (np <= 64) ? 64 : (np <= 128) ? 128 : (np <= 256) ? 256 : 512;
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+    const int kblocks = kp / kKBlock;
+    const int iters = kVSlots * kblocks;
+
+    if (warp < 4) {
+        // ---------------- producers ----------------
+        const int row = threadIdx.x;  // A row owned by this thread
+        const int32_t t = tgt_s[row];
+        int32_t src = -1;
+        const __half *bh_base = nullptr, *bl_base = nullptr;
+        for (int it = 0; it < iters; ++it) {
+            const int stage = it % NS;
+            const int s = it / kblocks, kb = it - s * kblocks;
+            if (kb == 0) {
+                src = (t >= 0) ? a.vdense[(size_t)t * kVSlots + s] : -1;
+                const int o = a.slot_off[cls * kVSlots + s];
+                bh_base = a.bh + (size_t)o * np * kp;
+                bl_base = a.bl + (size_t)o * np * kp;
+            }
+            if (!mbar_wait(smem_u32(&empty_bar[stage]), ((it / NS) & 1) ^ 1, &abort_s)) {
+                set_status(a.status, KIFMM_ERR_TIMEOUT);
+                abort_s = 1;
+                break;
+            }
+            unsigned char *st = smem + (size_t)stage * stage_bytes;
+            const uint32_t sA = smem_u32(st), sAl = sA + a_bytes, sB = sAl + a_bytes, sBl = sB + b_bytes;
+            const size_t koff = (size_t)kb * kKBlock;
+            const __half *gh = a.uh + (size_t)(src >= 0 ? src : 0) * kp + koff;
+            const __half *gl = a.ul + (size_t)(src >= 0 ? src : 0) * kp + koff;
+            const uint32_t nbytes = (src >= 0) ? 16u : 0u;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                cp_async16(sA + swz64(row, c), gh + 8 * c, nbytes);
+                cp_async16(sAl + swz64(row, c), gl + 8 * c, nbytes);
+            }
+            for (int r = row; r < np; r += kTcRows) {
+                const __half *bh = bh_base + (size_t)r * kp + koff;
+                const __half *bl = bl_base + (size_t)r * kp + koff;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    cp_async16(sB + swz64(r, c), bh + 8 * c, 16u);
+                    cp_async16(sBl + swz64(r, c), bl + 8 * c, 16u);
+                }
+            }
+            cp_async_arrive_noinc(smem_u32(&full_bar[stage]));
+        }
+        cp_async_wait_all();
+    } else if (lane == 0) {
+        // ---------------- MMA issuer ----------------
+        for (int it = 0; it < iters; ++it) {
+            const int stage = it % NS;
+            if (!mbar_wait(smem_u32(&full_bar[stage]), (it / NS) & 1, &abort_s)) {
+                set_status(a.status, KIFMM_ERR_TIMEOUT);
+                abort_s = 1;
+                break;
+            }
+            fence_proxy_async();
+            tc_fence_after();
+            const uint32_t sA = smem_u32(smem + (size_t)stage * stage_bytes);
+            const uint32_t sAl = sA + a_bytes, sB = sAl + a_bytes, sBl = sB + b_bytes;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const uint64_t dAh = sdesc_sw64(sA + 32 * kk), dAl = sdesc_sw64(sAl + 32 * kk);
+                for (int n0 = 0; n0 < np; n0 += 256) {
+                    const int nc = min(256, np - n0);
+                    const uint32_t id = idesc_f16(nc);
+                    const uint64_t dBh = sdesc_sw64(sB + n0 * kRowBytes + 32 * kk);
+                    const uint64_t dBl = sdesc_sw64(sBl + n0 * kRowBytes + 32 * kk);
+                    const uint32_t acc0 = (it > 0 || kk > 0) ? 1u : 0u;
+                    mma_f16(tmem + n0, dAh, dBh, id, acc0);
+                    mma_f16(tmem + n0, dAh, dBl, id, 1u);
+                    mma_f16(tmem + n0, dAl, dBh, id, 1u);
+                }
+            }
+            mma_commit(smem_u32(&empty_bar[stage]));
+        }
+        mma_commit(smem_u32(&done_bar));
+    }
+
+    // ---------------- epilogue ----------------
+    if (warp < 4) {
+        bool ok = mbar_wait(smem_u32(&done_bar), 0, &abort_s);
+        ok = __all_sync(0xffffffffu, ok);  // warp-uniform: tcgen05.ld is .sync.aligned
+        if (!ok) {
+            set_status(a.status, KIFMM_ERR_TIMEOUT);
+            abort_s = 1;
+        }
+        tc_fence_after();
+        const int row = warp * 32 + lane;
+        const int32_t t = tgt_s[row];
+        const float scale = (t >= 0) ? a.level_unscale[a.lvl[t]] : 0.f;
+        if (ok) {
+            for (int c0 = 0; c0 < np; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                if (t >= 0) {
+                    float *out = a.d + (size_t)t * a.ns + c0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < a.ns) out[j] = v[j] * scale;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        if (abort_s) {
+            // bounded drain of in-flight MMAs (the done barrier completes when they do)
+            for (long long i = 0; i < kWaitIters; ++i)
+                if (mbar_try_wait(smem_u32(&done_bar), 0) || mbar_try_wait(smem_u32(&done_bar), 1)) break;
+        }
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+// max |u| per level, as float bits (non-negative floats order like integers).
+__global__ void k_level_absmax(int64_t nb, int ns, const float *__restrict__ u, const int32_t *__restrict__ lvl,
+                               unsigned *__restrict__ level_max) {
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (b >= nb) return;
+    float m = 0.f;
+    for (int k = threadIdx.x & 31; k < ns; k += 32) m = fmaxf(m, fabsf(u[(size_t)b * ns + k]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&level_max[lvl[b]], __float_as_uint(m));
+}
+
+__device__ __forceinline__ float pow2_scale_for(float maxabs) {
+    if (!(maxabs > 0.f)) return 1.f;
+    int e;
+    frexpf(maxabs, &e);  // maxabs = m 2^e, m in [0.5, 1)
+    return ldexpf(1.f, 14 - e);
+}
+
+__global__ void k_level_scale(int nlev, const unsigned *__restrict__ level_max, float sigma_b,
+                              float *__restrict__ level_sigma, float *__restrict__ level_unscale) {
+    const int l = threadIdx.x;
+    if (l >= nlev) return;
+    const float s = pow2_scale_for(__uint_as_float(level_max[l]));
+    level_sigma[l] = s;
+    level_unscale[l] = 1.f / (s * sigma_b);
+}
+
+// hi/lo FP16 split of the scaled expansions, K padded with zeros.
+__global__ void k_split_u(int64_t nb, int ns, int kp, const float *__restrict__ u, const int32_t *__restrict__ lvl,
+                          const float *__restrict__ level_sigma, __half *__restrict__ uh, __half *__restrict__ ul) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nb * kp) return;
+    const int64_t b = idx / kp;
+    const int k = (int)(idx - b * kp);
+    const float x = (k < ns) ? u[(size_t)b * ns + k] * level_sigma[lvl[b]] : 0.f;
+    const __half h = __float2half_rn(x);
+    uh[idx] = h;
+    ul[idx] = __float2half_rn(x - __half2float(h));
+}
+
+__global__ void k_split_ops(int nops, int ns, int np, int kp, const float *__restrict__ m2l_t, float sigma,
+                            __half *__restrict__ bh, __half *__restrict__ bl) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)nops * np * kp;
+    if (idx >= total) return;
+    const int o = (int)(idx / ((int64_t)np * kp));
+    const int rem = (int)(idx - (int64_t)o * np * kp);
+    const int j = rem / kp, k = rem % kp;
+    // B[j][k] = M_o[j][k]; m2l_t is stored transposed ([o][k][j])
+    const float x = (j < ns && k < ns) ? m2l_t[((size_t)o * ns + k) * ns + j] * sigma : 0.f;
+    const __half h = __float2half_rn(x);
+    bh[idx] = h;
+    bl[idx] = __float2half_rn(x - __half2float(h));
+}
+
+__global__ void k_absmax_f32(int64_t n, const float *__restrict__ x, unsigned *out) {
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct TcState {
+    int np = 0, kp = 0, nstages = 0;
+    float sigma_b = 1.f;
+    __half *bh = nullptr, *bl = nullptr;
+    __half *uh = nullptr, *ul = nullptr;
+    int64_t u_cap = 0;
+    unsigned *level_max = nullptr;
+    float *level_sigma = nullptr, *level_unscale = nullptr;
+    int4 *tiles = nullptr;
+    int64_t tiles_cap = 0;
+    std::vector<int4> tiles_h;
+    size_t smem = 0;
+};
+
+static TcState &tc_state(Plan &P) {
+    if (!P.m2l_tc) P.m2l_tc = new TcState();
+    return *(TcState *)P.m2l_tc;
+}
+
+void m2l_tensor_release(Plan &P) {
+    if (P.m2l_tc) {
+        delete (TcState *)P.m2l_tc;
+        P.m2l_tc = nullptr;
+    }
+}
+
+// Plan time: FP16 hi/lo operators with one power-of-two scale.
+cudaError_t m2l_tensor_setup(Plan &P) {
+    TcState &S = tc_state(P);
+    const int ns = P.ns;
+    S.np = round_up(ns, 16);
+    S.kp = round_up(ns, kKBlock);
+    if (S.np > 512) return cudaErrorNotSupported;
+    const size_t stage = 2 * (size_t)kTcRows * kRowBytes + 2 * (size_t)S.np * kRowBytes;
+    S.nstages = (int)std::min<size_t>(16, (200 * 1024) / stage);
+    if (S.nstages < 2) return cudaErrorNotSupported;
+    S.smem = S.nstages * stage + 1024;
+    unsigned *dmax = nullptr;
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&dmax, sizeof(unsigned)));
+    KIFMM_CUDA_TRY(cudaMemset(dmax, 0, sizeof(unsigned)));
+    const int64_t nm = (int64_t)kNumM2L * ns * ns;
+    ++g_launches, k_absmax_f32<<<256, 256>>>(nm, (const float *)P.m2l_t, dmax);
+    unsigned mbits = 0;
+    KIFMM_CUDA_TRY(cudaMemcpy(&mbits, dmax, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    float mx;
+    memcpy(&mx, &mbits, sizeof(float));
+    int e = 0;
+    std::frexp(mx, &e);
+    S.sigma_b = std::ldexp(1.0f, 14 - e);
+    const size_t nb = (size_t)kNumM2L * S.np * S.kp;
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.bh, sizeof(__half) * nb));
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.bl, sizeof(__half) * nb));
+    ++g_launches, k_split_ops<<<(unsigned)((nb + 255) / 256), 256>>>(kNumM2L, ns, S.np, S.kp, (const float *)P.m2l_t,
+                                                                     S.sigma_b, S.bh, S.bl);
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.level_max, sizeof(unsigned) * 32));
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.level_sigma, sizeof(float) * 32));
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.level_unscale, sizeof(float) * 32));
+    KIFMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
+    return cudaDeviceSynchronize();
+}
+
+// After set_sources: tiles of 128 targets within each octant class.
+cudaError_t m2l_tensor_tiles(Plan &P, cudaStream_t s) {
+    TcState &S = tc_state(P);
+    S.tiles_h.clear();
+    for (int c = 0; c < 8; ++c)
+        for (int64_t b = P.m2l_class_start[c]; b < P.m2l_class_start[c + 1]; b += kTcRows)
+            S.tiles_h.push_back(make_int4(c, (int)b, (int)std::min<int64_t>(b + kTcRows, P.m2l_class_start[c + 1]), 0));
+    if ((int64_t)S.tiles_h.size() > S.tiles_cap) {
+        S.tiles_cap = (int64_t)S.tiles_h.size() + 64;
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.tiles, sizeof(int4) * S.tiles_cap));
+    }
+    if (!S.tiles_h.empty())
+        KIFMM_CUDA_TRY(cudaMemcpyAsync(S.tiles, S.tiles_h.data(), sizeof(int4) * S.tiles_h.size(),
+                                       cudaMemcpyHostToDevice, s));
+    if (P.nb > S.u_cap) {
+        S.u_cap = P.list_cap;
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.uh, sizeof(__half) * S.u_cap * S.kp));
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.ul, sizeof(__half) * S.u_cap * S.kp));
+    }
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {
+    TcState &S = tc_state(P);
+    if (S.tiles_h.empty()) return cudaSuccess;
+    const int nlev = P.max_level + 1;
+    KIFMM_CUDA_TRY(cudaMemsetAsync(S.level_max, 0, sizeof(unsigned) * 32, s));
+    ++g_launches, k_level_absmax<<<(unsigned)((P.nb + 7) / 8), 256, 0, s>>>(P.nb, P.ns, (const float *)P.u_chk, P.lvl,
+                                                                            S.level_max);
+    ++g_launches, k_level_scale<<<1, 32, 0, s>>>(nlev, S.level_max, S.sigma_b, S.level_sigma, S.level_unscale);
+    const int64_t tot = P.nb * S.kp;
+    ++g_launches, k_split_u<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.nb, P.ns, S.kp, (const float *)P.u_chk,
+                                                                          P.lvl, S.level_sigma, S.uh, S.ul);
+    TileArgs a;
+    a.targets = P.m2l_targets;
+    a.tiles = S.tiles;
+    a.vdense = P.vdense;
+    a.slot_off = P.slot_off;
+    a.uh = S.uh;
+    a.ul = S.ul;
+    a.bh = S.bh;
+    a.bl = S.bl;
+    a.lvl = P.lvl;
+    a.level_unscale = S.level_unscale;
+    a.d = (float *)P.d_chk;
+    a.ns = P.ns;
+    a.kp = S.kp;
+    a.np = S.np;
+    a.nstages = S.nstages;
+    a.status = P.status;
+    ++g_launches, k_m2l_tc<<<(unsigned)S.tiles_h.size(), kTcThreads, S.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace kifmm

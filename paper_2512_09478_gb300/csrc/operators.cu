@@ -1,0 +1,338 @@
+// Translation operators (Sec. 2.2: the M2M, M2L and L2L operators are
+// matrices between surfaces, computed automatically from the kernel).
+//
+// All operators are built for a unit box (half-width 1) with the kernel 1/r
+// (the 1/(4 pi) factor is applied once at the output).  The library keeps
+// every expansion as a potential on a check surface, so each operator that
+// crosses an equivalent surface is a composite K_target<-equiv * pinv(K_check<-equiv):
+//
+//   M2M  A_c = 1/2 K(UC_parent, UE_child c) P_up     (u child -> u parent)
+//   M2L  M_o = K(DC, UE + 2 d_o) P_up                 (u source -> d target)
+//   L2L  C_c = K(DC_child c, DE_parent) P_dn          (d parent -> d child)
+//
+// where P = V diag(sinv) U^T is the pseudo-inverse of the check-from-
+// equivalent matrix, truncated at eps * sigma_max.  The SVD is a one-sided
+// Jacobi (Hestenes) iteration in FP64 on the GPU with a cyclic round-robin
+// pair order (Brent & Luk); products are formed as ((K V) diag(sinv)) U^T so
+// the large entries of P never appear explicitly.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace kifmm {
+
+namespace {
+
+constexpr int kSvdThreads = 512;
+
+// One block per matrix.  At: [n][n] row j = column j of the matrix; on exit
+// row j = sigma_j u_j.  Vt: [n][n] row j = column j of V.
+__global__ void k_jacobi_svd(int n, double *At_all, double *Vt_all, double *sigma_all, int max_sweeps,
+                             double tol, int *sweeps_out) {
+    double *At = At_all + (size_t)blockIdx.x * n * n;
+    double *Vt = Vt_all + (size_t)blockIdx.x * n * n;
+    double *sigma = sigma_all + (size_t)blockIdx.x * n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Vt[i] = (i / n == i % n) ? 1.0 : 0.0;
+    __shared__ int rotated;
+    __syncthreads();
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
+        __syncthreads();
+        for (int r = 0; r < n - 1; ++r) {
+            for (int k = warp; k < n / 2; k += nwarps) {
+                const int i = (k == 0) ? 0 : ((r + k - 1) % (n - 1)) + 1;
+                const int j = ((r + n - 2 - k) % (n - 1)) + 1;
+                double *ai = At + (size_t)i * n, *aj = At + (size_t)j * n;
+                double a = 0.0, b = 0.0, g = 0.0;
+                for (int row = lane; row < n; row += 32) {
+                    const double x = ai[row], y = aj[row];
+                    a += x * x;
+                    b += y * y;
+                    g += x * y;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    g += __shfl_xor_sync(0xffffffffu, g, o);
+                }
+                if (g != 0.0 && fabs(g) > tol * sqrt(a * b)) {
+                    const double zeta = (b - a) / (2.0 * g);
+                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                    for (int row = lane; row < n; row += 32) {
+                        const double x = ai[row], y = aj[row];
+                        ai[row] = c * x - s * y;
+                        aj[row] = s * x + c * y;
+                    }
+                    double *vi = Vt + (size_t)i * n, *vj = Vt + (size_t)j * n;
+                    for (int row = lane; row < n; row += 32) {
+                        const double x = vi[row], y = vj[row];
+                        vi[row] = c * x - s * y;
+                        vj[row] = s * x + c * y;
+                    }
+                    if (lane == 0) rotated = 1;
+                }
+            }
+            __syncthreads();
+        }
+        const int any = rotated;
+        __syncthreads();
+        if (!any) break;
+    }
+    for (int j = warp; j < n; j += nwarps) {
+        double *aj = At + (size_t)j * n;
+        double s2 = 0.0;
+        for (int row = lane; row < n; row += 32) s2 += aj[row] * aj[row];
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        const double sg = sqrt(s2);
+        for (int row = lane; row < n; row += 32) aj[row] = (sg > 0.0) ? aj[row] / sg : 0.0;
+        if (lane == 0) sigma[j] = sg;
+    }
+    if (threadIdx.x == 0) sweeps_out[blockIdx.x] = sweep;
+}
+
+// C[b] = scale * A[b] diag(cs) op(B) with op(B)(m, j) = transB ? B[j][m] : B[m][j];
+// all n x n row-major FP64; the result is written transposed when transC.
+__global__ void k_dgemm(int n, const double *__restrict__ A, size_t strideA, const double *__restrict__ B,
+                        const double *__restrict__ cs, int transB, double scale, double *C, size_t strideC,
+                        int transC) {
+    __shared__ double As[16][17], Bs[16][17];
+    const int b = blockIdx.z;
+    const double *Ab = A + strideA * b;
+    double *Cb = C + strideC * b;
+    const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+    double acc = 0.0;
+    for (int m0 = 0; m0 < n; m0 += 16) {
+        const int ma = m0 + threadIdx.x, mb = m0 + threadIdx.y;
+        As[threadIdx.y][threadIdx.x] = (i < n && ma < n) ? Ab[(size_t)i * n + ma] * (cs ? cs[ma] : 1.0) : 0.0;
+        double bv = 0.0;
+        if (mb < n && j < n) bv = transB ? B[(size_t)j * n + mb] : B[(size_t)mb * n + j];
+        Bs[threadIdx.y][threadIdx.x] = bv;
+        __syncthreads();
+        for (int m = 0; m < 16; ++m) acc += As[threadIdx.y][m] * Bs[m][threadIdx.x];
+        __syncthreads();
+    }
+    if (i < n && j < n) {
+        if (transC) Cb[(size_t)j * n + i] = scale * acc; else Cb[(size_t)i * n + j] = scale * acc;
+    }
+}
+
+__global__ void k_to_f32(const double *in, float *out, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+// W_t[j][m] = sinv[m] * Ut[m][j]
+__global__ void k_make_wt(int n, const double *Ut, const double *sinv, double *Wt) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int j = idx / n, m = idx % n;
+    Wt[idx] = sinv[m] * Ut[(size_t)m * n + j];
+}
+
+std::vector<double> unit_surface(int p) {
+    std::vector<double> s;
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j)
+            for (int k = 0; k < p; ++k) {
+                if (i == 0 || i == p - 1 || j == 0 || j == p - 1 || k == 0 || k == p - 1) {
+                    s.push_back(-1.0 + 2.0 * i / (p - 1));
+                    s.push_back(-1.0 + 2.0 * j / (p - 1));
+                    s.push_back(-1.0 + 2.0 * k / (p - 1));
+                }
+            }
+    return s;
+}
+
+// K[i][k] = 1 / |(ct + at S_i) - (cs + as S_k)|
+void kernel_block(const std::vector<double> &S, int n, const double ct[3], double at, const double cs[3],
+                  double as, double *K) {
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            double r2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const double dd = (ct[d] + at * S[3 * i + d]) - (cs[d] + as * S[3 * k + d]);
+                r2 += dd * dd;
+            }
+            K[(size_t)i * n + k] = (r2 > 0.0) ? 1.0 / std::sqrt(r2) : 0.0;
+        }
+}
+
+void child_center(int o, double c[3]) {
+    c[0] = ((o >> 2) & 1) ? 0.5 : -0.5;
+    c[1] = ((o >> 1) & 1) ? 0.5 : -0.5;
+    c[2] = (o & 1) ? 0.5 : -0.5;
+}
+
+}  // namespace
+
+std::vector<int> m2l_offset_list() {
+    std::vector<int> out;
+    for (int a = -3; a <= 3; ++a)
+        for (int b = -3; b <= 3; ++b)
+            for (int c = -3; c <= 3; ++c) {
+                if (a >= -1 && a <= 1 && b >= -1 && b <= 1 && c >= -1 && c <= 1) continue;
+                out.push_back(a);
+                out.push_back(b);
+                out.push_back(c);
+            }
+    return out;
+}
+
+cudaError_t build_operators(Plan &P, std::string &err) {
+    const int p = P.p, n = P.ns;
+    const std::vector<double> S = unit_surface(p);
+    const double zero[3] = {0, 0, 0};
+    const size_t nn = (size_t)n * n;
+    const double ai = kAlphaInner, ao = kAlphaOuter;
+
+    // check-from-equivalent matrices, transposed for the column-wise Jacobi
+    std::vector<double> Kchk(2 * nn), tmp(nn);
+    kernel_block(S, n, zero, ao, zero, ai, tmp.data());  // K(UC, UE)
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) Kchk[(size_t)k * n + i] = tmp[(size_t)i * n + k];
+    kernel_block(S, n, zero, ai, zero, ao, tmp.data());  // K(DC, DE)
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) Kchk[nn + (size_t)k * n + i] = tmp[(size_t)i * n + k];
+
+    double *dAt = nullptr, *dVt = nullptr, *dsig = nullptr, *dsinv = nullptr;
+    int *dsweeps = nullptr;
+    KIFMM_CUDA_TRY(cudaMalloc(&dAt, sizeof(double) * 2 * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&dVt, sizeof(double) * 2 * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&dsig, sizeof(double) * 2 * n));
+    KIFMM_CUDA_TRY(cudaMalloc(&dsinv, sizeof(double) * 2 * n));
+    KIFMM_CUDA_TRY(cudaMalloc(&dsweeps, sizeof(int) * 2));
+    KIFMM_CUDA_TRY(cudaMemcpy(dAt, Kchk.data(), sizeof(double) * 2 * nn, cudaMemcpyHostToDevice));
+    k_jacobi_svd<<<2, kSvdThreads>>>(n, dAt, dVt, dsig, 60, 1e-15, dsweeps);
+    KIFMM_CUDA_TRY(cudaGetLastError());
+    std::vector<double> sig(2 * n);
+    int sweeps[2];
+    KIFMM_CUDA_TRY(cudaMemcpy(sig.data(), dsig, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
+    KIFMM_CUDA_TRY(cudaMemcpy(sweeps, dsweeps, sizeof(int) * 2, cudaMemcpyDeviceToHost));
+    if (sweeps[0] >= 60 || sweeps[1] >= 60) {
+        err = "Jacobi SVD did not converge";
+        return cudaErrorUnknown;
+    }
+    // truncation with the gap check
+    std::vector<double> sinv(2 * n);
+    for (int m = 0; m < 2; ++m) {
+        double smax = 0.0;
+        for (int j = 0; j < n; ++j) smax = std::fmax(smax, sig[m * n + j]);
+        for (int j = 0; j < n; ++j) {
+            const double rel = sig[m * n + j] / smax;
+            if (rel > P.eps / 1.1 && rel < P.eps * 1.1) {
+                char buf[160];
+                snprintf(buf, sizeof buf, "pinv_eps %.3g lies within a factor 1.1 of sigma/sigma_max = %.3g",
+                         P.eps, rel);
+                err = buf;
+                return cudaErrorInvalidValue;
+            }
+            sinv[m * n + j] = (rel >= P.eps) ? 1.0 / sig[m * n + j] : 0.0;
+        }
+    }
+    KIFMM_CUDA_TRY(cudaMemcpy(dsinv, sinv.data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice));
+
+    // kernel blocks: 8 M2M, 8 L2L, 316 M2L (row-major)
+    const std::vector<int> offs = m2l_offset_list();
+    const int nblk = 8 + 8 + kNumM2L;
+    std::vector<double> Kb((size_t)nblk * nn);
+    for (int o = 0; o < 8; ++o) {
+        double cc[3];
+        child_center(o, cc);
+        kernel_block(S, n, zero, ao, cc, 0.5 * ai, Kb.data() + (size_t)o * nn);        // K(UC_p, UE_c)
+        kernel_block(S, n, cc, 0.5 * ai, zero, ao, Kb.data() + (size_t)(8 + o) * nn);  // K(DC_c, DE_p)
+    }
+    for (int o = 0; o < kNumM2L; ++o) {
+        const double cs[3] = {2.0 * offs[3 * o], 2.0 * offs[3 * o + 1], 2.0 * offs[3 * o + 2]};
+        kernel_block(S, n, zero, ai, cs, ai, Kb.data() + (size_t)(16 + o) * nn);       // K(DC, UE + 2d)
+    }
+    double *dK = nullptr, *dKV = nullptr, *dOut = nullptr;
+    KIFMM_CUDA_TRY(cudaMalloc(&dK, sizeof(double) * nblk * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&dKV, sizeof(double) * nblk * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&dOut, sizeof(double) * nblk * nn));
+    KIFMM_CUDA_TRY(cudaMemcpy(dK, Kb.data(), sizeof(double) * nblk * nn, cudaMemcpyHostToDevice));
+    const double *Ut_up = dAt, *Ut_dn = dAt + nn, *Vt_up = dVt, *Vt_dn = dVt + nn;
+    const double *sinv_up = dsinv, *sinv_dn = dsinv + n;
+    dim3 blk(16, 16);
+    auto gemm = [&](const double *A, int batch, const double *B, const double *cs, int transB, double scale,
+                    double *C, int transC) {
+        dim3 grd((n + 15) / 16, (n + 15) / 16, batch);
+        k_dgemm<<<grd, blk>>>(n, A, nn, B, cs, transB, scale, C, nn, transC);
+    };
+    // K V  (V(k, m) = Vt[m][k])
+    gemm(dK, 8, Vt_up, nullptr, 1, 1.0, dKV, 0);
+    gemm(dK + 8 * nn, 8, Vt_dn, nullptr, 1, 1.0, dKV + 8 * nn, 0);
+    gemm(dK + 16 * nn, kNumM2L, Vt_up, nullptr, 1, 1.0, dKV + 16 * nn, 0);
+    // (K V) diag(sinv) U^T, written transposed ([k][j]); M2M carries h_child / h_parent = 1/2
+    gemm(dKV, 8, Ut_up, sinv_up, 0, 0.5, dOut, 1);
+    gemm(dKV + 8 * nn, 8, Ut_dn, sinv_dn, 0, 1.0, dOut + 8 * nn, 1);
+    gemm(dKV + 16 * nn, kNumM2L, Ut_up, sinv_up, 0, 1.0, dOut + 16 * nn, 1);
+    // leaf pseudo-inverses: W_t = (diag(sinv) U^T)^T, V_t = V^T (stored as is)
+    double *dW = nullptr;
+    KIFMM_CUDA_TRY(cudaMalloc(&dW, sizeof(double) * 2 * nn));
+    k_make_wt<<<(unsigned)((nn + 255) / 256), 256>>>(n, Ut_up, sinv_up, dW);
+    k_make_wt<<<(unsigned)((nn + 255) / 256), 256>>>(n, Ut_dn, sinv_dn, dW + nn);
+    KIFMM_CUDA_TRY(cudaGetLastError());
+
+    const size_t esz = P.f64 ? sizeof(double) : sizeof(float);
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.m2m_t, esz * 8 * nn));
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.l2l_t, esz * 8 * nn));
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.m2l_t, esz * kNumM2L * nn));
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.up_w_t, esz * nn));
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.up_v_t, esz * nn));
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.dn_w_t, esz * nn));
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.dn_v_t, esz * nn));
+    struct Copy { void *dst; const double *src; size_t cnt; };
+    const Copy copies[] = {{P.m2m_t, dOut, 8 * nn},           {P.l2l_t, dOut + 8 * nn, 8 * nn},
+                           {P.m2l_t, dOut + 16 * nn, kNumM2L * nn}, {P.up_w_t, dW, nn},
+                           {P.up_v_t, Vt_up, nn},             {P.dn_w_t, dW + nn, nn},
+                           {P.dn_v_t, Vt_dn, nn}};
+    for (const Copy &c : copies) {
+        if (P.f64)
+            KIFMM_CUDA_TRY(cudaMemcpy(c.dst, c.src, sizeof(double) * c.cnt, cudaMemcpyDeviceToDevice));
+        else
+            k_to_f32<<<(unsigned)((c.cnt + 255) / 256), 256>>>(c.src, (float *)c.dst, c.cnt);
+    }
+    // surfaces
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf64, sizeof(double) * 3 * n));
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf32, sizeof(float) * 3 * n));
+    std::vector<float> S32(S.begin(), S.end());
+    KIFMM_CUDA_TRY(cudaMemcpy(P.surf64, S.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+    KIFMM_CUDA_TRY(cudaMemcpy(P.surf32, S32.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice));
+    // V slot -> offset index tables
+    std::vector<int> slot(8 * kVSlots, -1);
+    for (int cls = 0; cls < 8; ++cls) {
+        const int ox = (cls >> 2) & 1, oy = (cls >> 1) & 1, oz = cls & 1;
+        int s = 0;
+        for (int a = 0; a < 6; ++a)
+            for (int b = 0; b < 6; ++b)
+                for (int c = 0; c < 6; ++c) {
+                    const int dx = a - 2 - ox, dy = b - 2 - oy, dz = c - 2 - oz;
+                    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+                    int idx = 0;
+                    for (int t = 0; t < kNumM2L; ++t)
+                        if (offs[3 * t] == dx && offs[3 * t + 1] == dy && offs[3 * t + 2] == dz) idx = t;
+                    slot[cls * kVSlots + s++] = idx;
+                }
+    }
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.slot_off, sizeof(int) * 8 * kVSlots));
+    KIFMM_CUDA_TRY(cudaMemcpy(P.slot_off, slot.data(), sizeof(int) * 8 * kVSlots, cudaMemcpyHostToDevice));
+    KIFMM_CUDA_TRY(cudaDeviceSynchronize());
+    cudaFree(dAt);
+    cudaFree(dVt);
+    cudaFree(dsig);
+    cudaFree(dsinv);
+    cudaFree(dsweeps);
+    cudaFree(dK);
+    cudaFree(dKV);
+    cudaFree(dOut);
+    cudaFree(dW);
+    return cudaGetLastError();
+}
+
+}  // namespace kifmm

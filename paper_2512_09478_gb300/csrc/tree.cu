@@ -1,0 +1,799 @@
+// Tree construction on the GPU (Sec. 2.2, first step: adaptive octree with
+// at most M points per leaf; third step: the interaction lists).
+//
+//   per-system bounding cube -> 63-bit Morton keys -> stable LSD radix sort
+//   (8-bit digits) -> octree level by level (binary search of the octant
+//   boundaries inside each split node's key range) -> colleagues, coarse
+//   adjacent leaves, U/V/W/X lists.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace kifmm {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kBlock * kItems;  // radix-sort tile
+
+__device__ __forceinline__ unsigned long long ord_of(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ double unord(unsigned long long b) {
+    b = (b & 0x8000000000000000ULL) ? (b & ~0x8000000000000000ULL) : ~b;
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ int find_sys(const int64_t *off, int S, int64_t i) {
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void k_bbox_init(unsigned long long *bb, int S) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < S * 6) bb[i] = (i % 6 < 3) ? ~0ULL : 0ULL;
+}
+
+// Per-system min/max of the positions; non-finite inputs raise a status.
+template <typename T>
+__global__ void k_bbox(int64_t n, const T *__restrict__ xyz, const T *__restrict__ q,
+                       const int64_t *__restrict__ off, int S, unsigned long long *bb, int *status) {
+    __shared__ unsigned long long red[6][kBlock / 32];
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    if (base >= n) return;
+    const int64_t end = min(n, base + (int64_t)kTile);
+    const int s0 = find_sys(off, S, base), s1 = find_sys(off, S, end - 1);
+    double mn[3] = {1e308, 1e308, 1e308}, mx[3] = {-1e308, -1e308, -1e308};
+    int cur = -1;
+    bool bad = false;
+    for (int64_t i = base + threadIdx.x; i < end; i += kBlock) {
+        double v[3];
+        for (int d = 0; d < 3; ++d) v[d] = (double)xyz[3 * i + d];
+        if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || !isfinite((double)q[i])) {
+            bad = true;
+            continue;
+        }
+        if (s0 != s1) {
+            int s = find_sys(off, S, i);
+            for (int d = 0; d < 3; ++d) {
+                atomicMin(&bb[s * 6 + d], ord_of(v[d]));
+                atomicMax(&bb[s * 6 + 3 + d], ord_of(v[d]));
+            }
+            continue;
+        }
+        cur = s0;
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fmin(mn[d], v[d]);
+            mx[d] = fmax(mx[d], v[d]);
+        }
+    }
+    if (bad) set_status(status, KIFMM_ERR_NONFINITE);
+    if (s0 != s1) return;
+    // block reduction (single system)
+    unsigned long long o[6];
+    for (int d = 0; d < 3; ++d) {
+        o[d] = (cur >= 0) ? ord_of(mn[d]) : ~0ULL;
+        o[3 + d] = (cur >= 0) ? ord_of(mx[d]) : 0ULL;
+    }
+    for (int k = 0; k < 6; ++k) {
+        unsigned long long v = o[k];
+        for (int sh = 16; sh > 0; sh >>= 1) {
+            unsigned long long w = __shfl_xor_sync(0xffffffffu, v, sh);
+            v = (k < 3) ? (w < v ? w : v) : (w > v ? w : v);
+        }
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        int k = threadIdx.x;
+        unsigned long long v = red[k][0];
+        for (int w = 1; w < kBlock / 32; ++w) v = (k < 3) ? min(v, red[k][w]) : max(v, red[k][w]);
+        if (k < 3) atomicMin(&bb[s0 * 6 + k], v); else atomicMax(&bb[s0 * 6 + k], v);
+    }
+}
+
+// Root cube per system: lo = per-axis minimum, side = largest extent (1 if 0).
+__global__ void k_bbox_final(const unsigned long long *bb, int S, double *lo_side) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    double side = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double lo = unord(bb[s * 6 + d]), hi = unord(bb[s * 6 + 3 + d]);
+        lo_side[s * 4 + d] = lo;
+        side = fmax(side, hi - lo);
+    }
+    lo_side[s * 4 + 3] = (side > 0.0) ? side : 1.0;
+}
+
+__device__ __forceinline__ uint64_t spread3(uint64_t x) {
+    x &= 0x1fffffULL;
+    x = (x | (x << 32)) & 0x1f00000000ffffULL;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+
+// 21-bit quantisation in FP64 without contraction: k = min(floor((x-lo)*s), 2^21-1),
+// s = 2^21 / side; bits interleaved x-highest.
+template <typename T>
+__global__ void k_keys(int64_t n, const T *__restrict__ xyz, const int64_t *__restrict__ off, int S,
+                       const double *__restrict__ lo_side, uint64_t *keys, uint32_t *vals,
+                       uint64_t *keys_user) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = find_sys(off, S, i);
+    const double side = lo_side[s * 4 + 3];
+    const double sc = __ddiv_rn(2097152.0, side);
+    uint64_t k[3];
+    for (int d = 0; d < 3; ++d) {
+        double t = __dmul_rn(__dsub_rn((double)xyz[3 * i + d], lo_side[s * 4 + d]), sc);
+        double f = floor(t);
+        k[d] = (f >= 2097151.0) ? 2097151ULL : (uint64_t)(f > 0.0 ? f : 0.0);
+    }
+    uint64_t key = (spread3(k[0]) << 2) | (spread3(k[1]) << 1) | spread3(k[2]);
+    keys[i] = key;
+    keys_user[i] = key;
+    vals[i] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (key, value), 8-bit digits.  Digit source: the key
+// (mode 0, bits [shift, shift+8)) or the system id of the value (mode 1), used
+// for the most significant passes of batched sorts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t digit_of(uint64_t key, uint32_t val, int mode, int shift,
+                                             const int64_t *off, int S) {
+    if (mode == 0) return (uint32_t)((key >> shift) & 0xFF);
+    return (uint32_t)((find_sys(off, S, val) >> shift) & 0xFF);
+}
+
+__global__ void k_rs_hist(int64_t n, const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                          int mode, int shift, const int64_t *off, int S, uint32_t *hist, int nblk) {
+    __shared__ uint32_t h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const int64_t end = min(n, base + (int64_t)kTile);
+    for (int64_t i = base + threadIdx.x; i < end; i += kBlock)
+        atomicAdd(&h[digit_of(keys[i], vals[i], mode, shift, off, S)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * nblk + blockIdx.x] = h[d];
+}
+
+// Scatter with ranks stable in input order: rounds of 256 consecutive items,
+// warp-level peer ranking, per-warp digit counts scanned across warps.
+__global__ void k_rs_scatter(int64_t n, const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                             uint64_t *kout, uint32_t *vout, int mode, int shift, const int64_t *off, int S,
+                             const uint32_t *__restrict__ hist_scan, int nblk) {
+    __shared__ uint32_t base_d[256];
+    __shared__ uint32_t wcnt[kBlock / 32][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < 256; d += kBlock) base_d[d] = hist_scan[(int64_t)d * nblk + blockIdx.x];
+    const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+    for (int r = 0; r < kItems; ++r) {
+        for (int i = threadIdx.x; i < (kBlock / 32) * 256; i += kBlock) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t i = tile0 + (int64_t)r * kBlock + threadIdx.x;
+        const bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0ULL;
+        uint32_t val = valid ? vin[i] : 0u;
+        uint32_t dig = valid ? digit_of(key, val, mode, shift, off, S) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xffffffffu, dig);
+        const unsigned lt = (1u << lane) - 1u;
+        const int rank_w = __popc(peers & lt);
+        if (valid && rank_w == 0) wcnt[warp][dig] = __popc(peers);
+        __syncthreads();
+        // per digit: exclusive scan across warps, then advance the running base
+        for (int d = threadIdx.x; d < 256; d += kBlock) {
+            uint32_t run = base_d[d];
+            for (int w = 0; w < kBlock / 32; ++w) {
+                uint32_t c = wcnt[w][d];
+                wcnt[w][d] = run;
+                run += c;
+            }
+            base_d[d] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = wcnt[warp][dig] + rank_w;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of uint32 (three phases, recursive over block sums).
+// ---------------------------------------------------------------------------
+constexpr int kScanBlock = 512;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+__global__ void k_scan_tiles(const uint32_t *__restrict__ in, uint32_t *out, int64_t n, uint32_t *sums) {
+    __shared__ uint32_t ws[kScanBlock / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t t = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0u;
+        t += v[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < kScanBlock / 32) ? ws[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kScanBlock / 32) ws[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = x - t + (warp > 0 ? ws[warp - 1] : 0u);
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == kScanBlock - 1) sums[blockIdx.x] = run;
+}
+
+__global__ void k_scan_add(uint32_t *out, int64_t n, const uint32_t *__restrict__ sums_scanned) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    const uint32_t add = sums_scanned[blockIdx.x];
+    for (int k = threadIdx.x; k < kScanTile; k += kScanBlock)
+        if (base + k < n) out[base + k] += add;
+}
+
+__global__ void k_write_total(const uint32_t *scan, const uint32_t *in, int64_t n, uint32_t *total) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *total = (n > 0) ? scan[n - 1] + in[n - 1] : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Octree
+// ---------------------------------------------------------------------------
+__global__ void k_roots(int S, const int64_t *off, int32_t *lvl, int32_t *cx, int32_t *cy, int32_t *cz,
+                        int32_t *first, int32_t *cnt, int32_t *parent, int32_t *sys) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    lvl[s] = 0;
+    cx[s] = cy[s] = cz[s] = 0;
+    first[s] = (int32_t)off[s];
+    cnt[s] = (int32_t)(off[s + 1] - off[s]);
+    parent[s] = -1;
+    sys[s] = s;
+}
+
+// For each node of one level: octant ranges of its keys and the number of
+// non-empty octants if it splits (count > M and level < max depth).
+__global__ void k_split(int64_t ls, int64_t le, int level, int leaf_cap, int max_depth,
+                        const uint64_t *__restrict__ keys, const int32_t *__restrict__ first,
+                        const int32_t *__restrict__ cnt, uint32_t *nchild_tmp, int32_t *rng) {
+    int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= le) return;
+    const int64_t j = b - ls;
+    uint32_t nc = 0;
+    if (cnt[b] > leaf_cap && level < max_depth) {
+        const int shift = 3 * (kMaxLevel - level);
+        const int64_t lo0 = first[b], hi0 = lo0 + cnt[b];
+        int64_t start = lo0;
+        for (int o = 0; o < 8; ++o) {
+            // first index in [start, hi0) whose digit exceeds o
+            int64_t lo = start, hi = hi0;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if ((int)((keys[mid] >> shift) & 7ULL) <= o) lo = mid + 1; else hi = mid;
+            }
+            rng[j * 16 + 2 * o] = (int32_t)start;
+            rng[j * 16 + 2 * o + 1] = (int32_t)(lo - start);
+            if (lo > start) ++nc;
+            start = lo;
+        }
+    }
+    nchild_tmp[j] = nc;
+}
+
+__global__ void k_emit(int64_t ls, int64_t le, const uint32_t *__restrict__ nchild_tmp,
+                       const uint32_t *__restrict__ nchild_scan, const int32_t *__restrict__ rng,
+                       int32_t *lvl, int32_t *cx, int32_t *cy, int32_t *cz, int32_t *first, int32_t *cnt,
+                       int32_t *parent, int32_t *child_first, int32_t *nchild, int32_t *sys, int64_t cap,
+                       int *status) {
+    int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= le) return;
+    const int64_t j = b - ls;
+    const uint32_t nc = nchild_tmp[j];
+    nchild[b] = (int32_t)nc;
+    if (nc == 0) {
+        child_first[b] = -1;
+        return;
+    }
+    const int64_t c0 = le + nchild_scan[j];
+    child_first[b] = (int32_t)c0;
+    int k = 0;
+    for (int o = 0; o < 8; ++o) {
+        const int32_t f = rng[j * 16 + 2 * o], c = rng[j * 16 + 2 * o + 1];
+        if (c == 0) continue;
+        const int64_t ch = c0 + k++;
+        if (ch >= cap) {
+            set_status(status, KIFMM_ERR_CAPACITY);
+            return;
+        }
+        lvl[ch] = lvl[b] + 1;
+        cx[ch] = 2 * cx[b] + ((o >> 2) & 1);
+        cy[ch] = 2 * cy[b] + ((o >> 1) & 1);
+        cz[ch] = 2 * cz[b] + (o & 1);
+        first[ch] = f;
+        cnt[ch] = c;
+        parent[ch] = (int32_t)b;
+        sys[ch] = sys[b];
+    }
+}
+
+// Leaf-relative particle records {x - c_leaf, y - c_leaf, z - c_leaf, q} in
+// root-normalised units (root side = 1), computed in FP64.
+template <typename TI, typename TC>
+__global__ void k_gather(int64_t nb, const int32_t *__restrict__ nchild, const int32_t *__restrict__ first,
+                         const int32_t *__restrict__ cnt, const int32_t *__restrict__ lvl,
+                         const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                         const int32_t *__restrict__ cz, const int32_t *__restrict__ sys,
+                         const double *__restrict__ lo_side, const uint32_t *__restrict__ perm,
+                         const TI *__restrict__ xyz, const TI *__restrict__ q,
+                         typename Vec4<TC>::type *pts) {
+    const int64_t b = blockIdx.x;
+    if (b >= nb || nchild[b] != 0) return;
+    const int s = sys[b];
+    const double side = lo_side[s * 4 + 3];
+    const double w = ldexp(1.0, -lvl[b]);
+    const double c[3] = {(cx[b] + 0.5) * w, (cy[b] + 0.5) * w, (cz[b] + 0.5) * w};
+    for (int k = threadIdx.x; k < cnt[b]; k += blockDim.x) {
+        const int64_t i = first[b] + k;
+        const uint32_t j = perm[i];
+        double r[3];
+        for (int d = 0; d < 3; ++d) r[d] = ((double)xyz[3 * j + d] - lo_side[s * 4 + d]) / side - c[d];
+        typename Vec4<TC>::type v;
+        v.x = (TC)r[0];
+        v.y = (TC)r[1];
+        v.z = (TC)r[2];
+        v.w = (TC)q[j];
+        pts[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Lists
+// ---------------------------------------------------------------------------
+__global__ void k_colleagues(int64_t ls, int64_t le, int level, const int32_t *__restrict__ parent,
+                             const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
+                             const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                             const int32_t *__restrict__ cz, int32_t *coll) {
+    int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= le) return;
+    int32_t *cb = coll + b * kColl;
+    for (int k = 0; k < kColl; ++k) cb[k] = -1;
+    if (level == 0) {
+        cb[13] = (int32_t)b;
+        return;
+    }
+    const int32_t P = parent[b];
+    const int32_t *cp = coll + (int64_t)P * kColl;
+    for (int k = 0; k < kColl; ++k) {
+        const int32_t c = cp[k];
+        if (c < 0 || nchild[c] == 0) continue;
+        for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
+            const int dx = cx[ch] - cx[b], dy = cy[ch] - cy[b], dz = cz[ch] - cz[b];
+            if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
+            cb[(dx + 1) * 9 + (dy + 1) * 3 + (dz + 1)] = ch;
+        }
+    }
+}
+
+// Coarser-or-equal-level leaves adjacent to b: those of the parent that touch
+// b, plus b's leaf colleagues.
+__global__ void k_coarse(int64_t ls, int64_t le, int level, const int32_t *__restrict__ parent,
+                         const int32_t *__restrict__ nchild, const int32_t *__restrict__ lvl,
+                         const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                         const int32_t *__restrict__ cz, const int32_t *__restrict__ coll, int32_t *coarse,
+                         int32_t *ncoarse, int *status) {
+    int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= le) return;
+    int n = 0;
+    int32_t *out = coarse + b * kMaxCoarse;
+    if (level > 0) {
+        const int32_t P = parent[b];
+        for (int k = 0; k < ncoarse[P]; ++k) {
+            const int32_t a = coarse[(int64_t)P * kMaxCoarse + k];
+            if (boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], level, cx[b], cy[b], cz[b])) {
+                if (n < kMaxCoarse) out[n] = a;
+                ++n;
+            }
+        }
+    }
+    for (int k = 0; k < kColl; ++k) {
+        const int32_t c = coll[b * kColl + k];
+        if (k == 13 || c < 0 || nchild[c] != 0) continue;
+        if (n < kMaxCoarse) out[n] = c;
+        ++n;
+    }
+    if (n > kMaxCoarse) {
+        set_status(status, KIFMM_ERR_CAPACITY);
+        n = kMaxCoarse;
+    }
+    ncoarse[b] = n;
+}
+
+// slot of offset d for octant class (ox,oy,oz): components range over
+// [-2-o, 3-o]; the inner [-1,1]^3 is excluded.
+__device__ __forceinline__ int v_slot(int ox, int oy, int oz, int dx, int dy, int dz) {
+    const int ix = dx + 2 + ox, iy = dy + 2 + oy, iz = dz + 2 + oz;  // 0..5
+    int s = 0;
+    for (int a = 0; a < 6; ++a)
+        for (int bb = 0; bb < 6; ++bb)
+            for (int c = 0; c < 6; ++c) {
+                const int ddx = a - 2 - ox, ddy = bb - 2 - oy, ddz = c - 2 - oz;
+                if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1 && ddz >= -1 && ddz <= 1) continue;
+                if (a == ix && bb == iy && c == iz) return s;
+                ++s;
+            }
+    return -1;
+}
+
+// V list (children of the parent's colleagues not adjacent to b) into the
+// per-class slot table, and X list (coarser leaves adjacent to the parent but
+// not to b).
+__global__ void k_vx(int64_t ls, int64_t le, int level, const int32_t *__restrict__ parent,
+                     const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
+                     const int32_t *__restrict__ lvl, const int32_t *__restrict__ cx,
+                     const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
+                     const int32_t *__restrict__ coll, const int32_t *__restrict__ coarse,
+                     const int32_t *__restrict__ ncoarse, int32_t *vdense, int32_t *nv, int32_t *xdense,
+                     int32_t *nx) {
+    int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= le) return;
+    int32_t *vb = vdense + b * kVSlots;
+    for (int s = 0; s < kVSlots; ++s) vb[s] = -1;
+    int cntv = 0, cntx = 0;
+    if (level > 0) {
+        const int32_t P = parent[b];
+        const int ox = cx[b] & 1, oy = cy[b] & 1, oz = cz[b] & 1;
+        for (int k = 0; k < kColl; ++k) {
+            const int32_t c = coll[(int64_t)P * kColl + k];
+            if (c < 0 || nchild[c] == 0) continue;
+            for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
+                const int dx = cx[ch] - cx[b], dy = cy[ch] - cy[b], dz = cz[ch] - cz[b];
+                if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+                const int sl = v_slot(ox, oy, oz, dx, dy, dz);
+                if (sl < 0) continue;  // unreachable: children of parent colleagues lie in the class window
+                vb[sl] = ch;
+                ++cntv;
+            }
+        }
+        for (int k = 0; k < ncoarse[P]; ++k) {
+            const int32_t a = coarse[(int64_t)P * kMaxCoarse + k];
+            if (!boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], level, cx[b], cy[b], cz[b]))
+                xdense[b * kMaxCoarse + cntx++] = a;
+        }
+    }
+    nv[b] = cntv;
+    nx[b] = cntx;
+}
+
+// U and W of a leaf: U = {b} + coarse adjacent leaves + finer adjacent leaves
+// found by descending b's non-leaf colleagues; a descendant that is not
+// adjacent to b (while its parent is) goes to W.  Pass 0 counts, pass 1 fills.
+__global__ void k_uw(int64_t nb, int pass, const int32_t *__restrict__ child_first,
+                     const int32_t *__restrict__ nchild, const int32_t *__restrict__ lvl,
+                     const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                     const int32_t *__restrict__ cz, const int32_t *__restrict__ coll,
+                     const int32_t *__restrict__ coarse, const int32_t *__restrict__ ncoarse,
+                     uint32_t *u_cnt, uint32_t *w_cnt, const uint32_t *__restrict__ u_ptr,
+                     const uint32_t *__restrict__ w_ptr, int32_t *u_idx, int32_t *w_idx, int *status) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    if (nchild[b] != 0) {
+        if (pass == 0) u_cnt[b] = w_cnt[b] = 0;
+        return;
+    }
+    const int lb = lvl[b], bx = cx[b], by = cy[b], bz = cz[b];
+    uint32_t nu = 0, nw = 0;
+    const uint32_t u0 = pass ? u_ptr[b] : 0, w0 = pass ? w_ptr[b] : 0;
+    if (pass) u_idx[u0 + nu] = (int32_t)b;
+    ++nu;
+    for (int k = 0; k < ncoarse[b]; ++k) {
+        if (pass) u_idx[u0 + nu] = coarse[b * kMaxCoarse + k];
+        ++nu;
+    }
+    int32_t stack[8 * (kMaxLevel + 1)];
+    for (int k = 0; k < kColl; ++k) {
+        const int32_t c = coll[b * kColl + k];
+        if (k == 13 || c < 0 || nchild[c] == 0) continue;
+        int sp = 0;
+        for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) stack[sp++] = ch;
+        while (sp > 0) {
+            const int32_t a = stack[--sp];
+            if (boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], lb, bx, by, bz)) {
+                if (nchild[a] == 0) {
+                    if (pass) u_idx[u0 + nu] = a;
+                    ++nu;
+                } else {
+                    if (sp + nchild[a] > 8 * (kMaxLevel + 1)) {
+                        set_status(status, KIFMM_ERR_CAPACITY);
+                        return;
+                    }
+                    for (int32_t ch = child_first[a]; ch < child_first[a] + nchild[a]; ++ch) stack[sp++] = ch;
+                }
+            } else {
+                if (pass) w_idx[w0 + nw] = a;
+                ++nw;
+            }
+        }
+    }
+    if (pass == 0) {
+        u_cnt[b] = nu;
+        w_cnt[b] = nw;
+    }
+}
+
+__global__ void k_mark_w(int64_t nw, const int32_t *__restrict__ w_idx, int32_t *flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nw) flag[w_idx[i]] = 1;
+}
+
+inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+size_t scan_tmp_needed(int64_t n) {
+    size_t total = 0;
+    int64_t m = n;
+    while (m > 1) {
+        m = (m + kScanTile - 1) / kScanTile;
+        total += (size_t)m + 1;
+    }
+    return total + 4;
+}
+
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total_dev,
+                               uint32_t *tmp, size_t tmp_elems, cudaStream_t s) {
+    if (n <= 0) {
+        if (total_dev) KIFMM_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s));
+        return cudaSuccess;
+    }
+    const int64_t nblk = (n + kScanTile - 1) / kScanTile;
+    if ((size_t)nblk + 1 > tmp_elems) return cudaErrorInvalidValue;
+    uint32_t *sums = tmp;
+    ++g_launches, k_scan_tiles<<<(unsigned)nblk, kScanBlock, 0, s>>>(in, out, n, sums);
+    if (nblk > 1) {
+        KIFMM_CUDA_TRY(exclusive_scan_u32(sums, sums, nblk, nullptr, tmp + nblk + 1, tmp_elems - nblk - 1, s));
+        ++g_launches, k_scan_add<<<(unsigned)nblk, kScanBlock, 0, s>>>(out, n, sums);
+    }
+    if (total_dev) ++g_launches, k_write_total<<<1, 32, 0, s>>>(out, in, n, total_dev);
+    return cudaGetLastError();
+}
+
+// Partition keys: class of boxes with a V list (8 = none), or 0 for leaves.
+__global__ void k_part_keys(int64_t nb, int mode, const int32_t *__restrict__ nv, const int32_t *__restrict__ nchild,
+                            const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                            const int32_t *__restrict__ cz, uint64_t *keys, uint32_t *vals, uint32_t *counts) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    uint32_t k;
+    if (mode == 0) k = (nv[b] > 0) ? (uint32_t)(4 * (cx[b] & 1) + 2 * (cy[b] & 1) + (cz[b] & 1)) : 8u;
+    else k = (nchild[b] == 0) ? 0u : 1u;
+    keys[b] = k;
+    vals[b] = (uint32_t)b;
+    atomicAdd(&counts[k], 1u);
+}
+
+static cudaError_t radix_pass(Plan &P, const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout,
+                              int64_t n, int mode, int shift, cudaStream_t s) {
+    const int nblk = (int)((n + kTile - 1) / kTile);
+    if ((size_t)512 * nblk > P.hist_elems) {
+        P.hist_elems = (size_t)512 * nblk;
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.hist, sizeof(uint32_t) * P.hist_elems));
+    }
+    if (scan_tmp_needed((int64_t)256 * nblk) + 8 > P.scan_tmp_elems) {
+        P.scan_tmp_elems = scan_tmp_needed((int64_t)256 * nblk) + 8;
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.scan_tmp, sizeof(uint32_t) * P.scan_tmp_elems));
+    }
+    ++g_launches, k_rs_hist<<<nblk, kBlock, 0, s>>>(n, kin, vin, mode, shift, P.sys_off_d, P.n_sys, P.hist, nblk);
+    KIFMM_CUDA_TRY(exclusive_scan_u32(P.hist, P.hist + (size_t)256 * nblk, (int64_t)256 * nblk, nullptr,
+                                      P.scan_tmp, P.scan_tmp_elems - 1, s));
+    ++g_launches, k_rs_scatter<<<nblk, kBlock, 0, s>>>(n, kin, vin, kout, vout, mode, shift, P.sys_off_d, P.n_sys,
+                                         P.hist + (size_t)256 * nblk, nblk);
+    return cudaGetLastError();
+}
+
+cudaError_t partition_boxes(Plan &P, cudaStream_t s) {
+    const int64_t nb = P.nb;
+    uint64_t *pk0 = (uint64_t *)P.part_keys, *pk1 = pk0 + P.box_cap;
+    uint32_t *pv0 = (uint32_t *)P.part_vals, *pv1 = pv0 + P.box_cap;
+    for (int mode = 0; mode < 2; ++mode) {
+        KIFMM_CUDA_TRY(cudaMemsetAsync(P.part_counts, 0, sizeof(uint32_t) * 16, s));
+        ++g_launches, k_part_keys<<<grid_for(nb, 256), 256, 0, s>>>(nb, mode, P.nv, P.nchild, P.cx, P.cy, P.cz, pk0, pv0,
+                                                      P.part_counts);
+        KIFMM_CUDA_TRY(radix_pass(P, pk0, pv0, pk1, pv1, nb, 0, 0, s));
+        uint32_t counts[16];
+        KIFMM_CUDA_TRY(cudaMemcpyAsync(counts, P.part_counts, sizeof(counts), cudaMemcpyDeviceToHost, s));
+        KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (mode == 0) {
+            P.m2l_class_start[0] = 0;
+            for (int c = 0; c < 8; ++c) P.m2l_class_start[c + 1] = P.m2l_class_start[c] + counts[c];
+            KIFMM_CUDA_TRY(cudaMemcpyAsync(P.m2l_targets, pv1, sizeof(int32_t) * nb, cudaMemcpyDeviceToDevice, s));
+        } else {
+            P.n_leaves = counts[0];
+            KIFMM_CUDA_TRY(cudaMemcpyAsync(P.leaves, pv1, sizeof(int32_t) * nb, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t radix_sort(Plan &P, int64_t n, cudaStream_t s, int &cur) {
+    const int nblk = (int)((n + kTile - 1) / kTile);
+    struct Pass { int mode, shift; };
+    std::vector<Pass> passes;
+    for (int sh = 0; sh < 64; sh += 8) passes.push_back({0, sh});
+    if (P.n_sys > 1) {
+        for (int sh = 0; (1LL << sh) < P.n_sys; sh += 8) passes.push_back({1, sh});
+    }
+    (void)nblk;
+    for (const Pass &ps : passes) {
+        const int nxt = cur ^ 1;
+        KIFMM_CUDA_TRY(radix_pass(P, P.keys[cur], P.vals[cur], P.keys[nxt], P.vals[nxt], n, ps.mode, ps.shift, s));
+        cur = nxt;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) {
+    const int64_t n = P.n;
+    const int S = P.n_sys;
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.sys_off_d, P.sys_off_h.data(), sizeof(int64_t) * (S + 1),
+                                   cudaMemcpyHostToDevice, s));
+    ++g_launches, k_bbox_init<double><<<grid_for(S * 6, 128), 128, 0, s>>>(P.bbox_ord, S);
+    const unsigned nt = grid_for(n, kTile);
+    if (P.io_f64)
+        ++g_launches, k_bbox<double><<<nt, kBlock, 0, s>>>(n, (const double *)xyz, (const double *)q, P.sys_off_d, S,
+                                             P.bbox_ord, P.status);
+    else
+        ++g_launches, k_bbox<float><<<nt, kBlock, 0, s>>>(n, (const float *)xyz, (const float *)q, P.sys_off_d, S,
+                                            P.bbox_ord, P.status);
+    ++g_launches, k_bbox_final<<<grid_for(S, 128), 128, 0, s>>>(P.bbox_ord, S, P.lo_side);
+    if (P.io_f64)
+        ++g_launches, k_keys<double><<<grid_for(n, 256), 256, 0, s>>>(n, (const double *)xyz, P.sys_off_d, S, P.lo_side,
+                                                       P.keys[0], P.vals[0], P.keys_user);
+    else
+        ++g_launches, k_keys<float><<<grid_for(n, 256), 256, 0, s>>>(n, (const float *)xyz, P.sys_off_d, S, P.lo_side,
+                                                      P.keys[0], P.vals[0], P.keys_user);
+    KIFMM_CUDA_TRY(cudaGetLastError());
+    int cur = 0;
+    KIFMM_CUDA_TRY(radix_sort(P, n, s, cur));
+    if (cur != 0) {
+        KIFMM_CUDA_TRY(cudaMemcpyAsync(P.keys[0], P.keys[1], sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+        KIFMM_CUDA_TRY(cudaMemcpyAsync(P.vals[0], P.vals[1], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.perm, P.vals[0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+
+    // octree, level by level
+    ++g_launches, k_roots<<<grid_for(S, 128), 128, 0, s>>>(S, P.sys_off_d, P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.parent,
+                                             P.sys);
+    P.level_start.assign(1, 0);
+    P.level_start.push_back(S);
+    int64_t ls = 0, le = S;
+    int level = 0;
+    uint32_t *total_dev = P.scan_tmp + P.scan_tmp_elems - 1;
+    while (true) {
+        const int64_t m = le - ls;
+        ++g_launches, k_split<<<grid_for(m, 128), 128, 0, s>>>(ls, le, level, P.desc.leaf_cap, P.desc.max_depth, P.keys[0],
+                                                 P.first, P.cnt, P.tmp_nchild, P.child_rng);
+        uint32_t *scan_out = P.tmp_nchild + P.box_cap;
+        KIFMM_CUDA_TRY(exclusive_scan_u32(P.tmp_nchild, scan_out, m, total_dev, P.scan_tmp,
+                                          P.scan_tmp_elems - 1, s));
+        uint32_t total = 0;
+        KIFMM_CUDA_TRY(cudaMemcpyAsync(&total, total_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (le + (int64_t)total > P.box_cap) {
+            KIFMM_CUDA_TRY(grow_tree_arrays(P, 2 * (le + (int64_t)total) + 1024, le));
+            scan_out = P.tmp_nchild + P.box_cap;
+            KIFMM_CUDA_TRY(exclusive_scan_u32(P.tmp_nchild, scan_out, m, total_dev, P.scan_tmp,
+                                              P.scan_tmp_elems - 1, s));
+        }
+        ++g_launches, k_emit<<<grid_for(m, 128), 128, 0, s>>>(ls, le, P.tmp_nchild, scan_out, P.child_rng, P.lvl, P.cx, P.cy,
+                                                P.cz, P.first, P.cnt, P.parent, P.child_first, P.nchild, P.sys,
+                                                P.box_cap, P.status);
+        KIFMM_CUDA_TRY(cudaGetLastError());
+        if (total == 0) break;
+        ls = le;
+        le = le + total;
+        ++level;
+        P.level_start.push_back(le);
+    }
+    P.nb = le;
+    P.max_level = level;
+
+    // leaf-relative particle records in the compute type
+    if (P.f64) {
+        if (P.io_f64)
+            ++g_launches, k_gather<double, double><<<(unsigned)P.nb, 128, 0, s>>>(
+                P.nb, P.nchild, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+                (const double *)xyz, (const double *)q, (double4 *)P.pts);
+        else
+            ++g_launches, k_gather<float, double><<<(unsigned)P.nb, 128, 0, s>>>(
+                P.nb, P.nchild, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+                (const float *)xyz, (const float *)q, (double4 *)P.pts);
+    } else {
+        if (P.io_f64)
+            ++g_launches, k_gather<double, float><<<(unsigned)P.nb, 128, 0, s>>>(
+                P.nb, P.nchild, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+                (const double *)xyz, (const double *)q, (float4 *)P.pts);
+        else
+            ++g_launches, k_gather<float, float><<<(unsigned)P.nb, 128, 0, s>>>(
+                P.nb, P.nchild, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+                (const float *)xyz, (const float *)q, (float4 *)P.pts);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t build_lists(Plan &P, cudaStream_t s) {
+    const int64_t nb = P.nb;
+    for (int l = 0; l <= P.max_level; ++l) {
+        const int64_t ls = P.level_start[l], le = P.level_start[l + 1];
+        const unsigned g = grid_for(le - ls, 128);
+        ++g_launches, k_colleagues<<<g, 128, 0, s>>>(ls, le, l, P.parent, P.child_first, P.nchild, P.cx, P.cy, P.cz, P.coll);
+        ++g_launches, k_coarse<<<g, 128, 0, s>>>(ls, le, l, P.parent, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse,
+                                   P.ncoarse, P.status);
+        ++g_launches, k_vx<<<g, 128, 0, s>>>(ls, le, l, P.parent, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll,
+                               P.coarse, P.ncoarse, P.vdense, P.nv, P.xdense, P.nx);
+        KIFMM_CUDA_TRY(cudaGetLastError());
+    }
+    const unsigned g = grid_for(nb, 128);
+    ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 0, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse, P.ncoarse,
+                           P.u_cnt, P.w_cnt, nullptr, nullptr, nullptr, nullptr, P.status);
+    uint32_t *tot = P.scan_tmp + P.scan_tmp_elems - 1;
+    uint32_t totals[2];
+    KIFMM_CUDA_TRY(exclusive_scan_u32(P.u_cnt, P.u_ptr, nb, tot, P.scan_tmp, P.scan_tmp_elems - 1, s));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.u_ptr + nb, tot, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(&totals[0], tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    KIFMM_CUDA_TRY(exclusive_scan_u32(P.w_cnt, P.w_ptr, nb, tot, P.scan_tmp, P.scan_tmp_elems - 1, s));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.w_ptr + nb, tot, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(&totals[1], tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    P.n_u = totals[0];
+    P.n_w = totals[1];
+    if (P.n_u > P.u_cap || P.n_w > P.w_cap) {
+        // grow the list storage (set_sources may allocate; evaluate never does)
+        if (P.n_u > P.u_cap) {
+            P.u_cap = P.n_u + P.n_u / 4 + 1024;
+            KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.u_idx, sizeof(int32_t) * P.u_cap));
+        }
+        if (P.n_w > P.w_cap) {
+            P.w_cap = P.n_w + P.n_w / 4 + 1024;
+            KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.w_idx, sizeof(int32_t) * P.w_cap));
+        }
+    }
+    ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 1, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse, P.ncoarse,
+                           P.u_cnt, P.w_cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, P.status);
+    KIFMM_CUDA_TRY(cudaMemsetAsync(P.wsrc_flag, 0, sizeof(int32_t) * nb, s));
+    if (P.n_w > 0) ++g_launches, k_mark_w<<<grid_for(P.n_w, 256), 256, 0, s>>>(P.n_w, P.w_idx, P.wsrc_flag);
+    KIFMM_CUDA_TRY(cudaGetLastError());
+    return cudaSuccess;
+}
+
+}  // namespace kifmm

@@ -1,0 +1,240 @@
+"""Python binding of the KIFMM C ABI (include/kifmm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+(lib/libkifmm.so).  PyTorch provides device memory and the current stream.
+There is no fallback: if the library is missing or a call fails, an
+exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libkifmm.so")
+
+OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed_tf32": 2, "mixed_fp16": 3}
+LIST_KINDS = {"U": 0, "V": 1, "W": 2, "X": 3}
+
+
+class KifmmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_depth", ctypes.c_int),
+                ("precision", ctypes.c_int), ("coef", ctypes.c_double), ("n_max", ctypes.c_int64),
+                ("n_systems_max", ctypes.c_int), ("dtype", ctypes.c_int), ("pinv_eps", ctypes.c_double),
+                ("autotune", ctypes.c_int)]
+
+
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int64), ("n_boxes", ctypes.c_int64), ("max_level", ctypes.c_int),
+                ("n_systems", ctypes.c_int), ("n_u", ctypes.c_int64), ("n_v", ctypes.c_int64),
+                ("n_w", ctypes.c_int64), ("n_x", ctypes.c_int64)]
+
+
+STAGES = ["tree", "p2m", "m2m", "m2l", "p2l", "l2l", "leaf", "p2p", "out"]
+
+
+class ProfileT(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * len(STAGES)), ("calls", ctypes.c_int64 * len(STAGES)),
+                ("launches", ctypes.c_int64)]
+
+
+_LIB = None
+EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifmm_evaluate",
+           "kifmm_clump_reduce", "kifmm_backward", "kifmm_get_device_status", "kifmm_status_string",
+           "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
+           "kifmm_profile_enable", "kifmm_profile_read"]
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"KIFMM library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.kifmm_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(P)]
+    lib.kifmm_plan_destroy.argtypes = [P]
+    lib.kifmm_set_sources.argtypes = [P, I, P, P, P, P]
+    lib.kifmm_evaluate.argtypes = [P, P, P, P, P]
+    lib.kifmm_clump_reduce.argtypes = [P, I64, P, P, P, P, P, P, P, P]
+    lib.kifmm_backward.argtypes = [P, P, P, P, P, P]
+    lib.kifmm_get_device_status.argtypes = [P, ctypes.POINTER(I)]
+    lib.kifmm_status_string.argtypes = [I]
+    lib.kifmm_status_string.restype = ctypes.c_char_p
+    lib.kifmm_tree_info.argtypes = [P, ctypes.POINTER(TreeInfo)]
+    lib.kifmm_copy_keys.argtypes = [P, P, P, P]
+    lib.kifmm_copy_tree.argtypes = [P, P, P, P, P, P, P]
+    lib.kifmm_copy_list.argtypes = [P, I, P, P]
+    lib.kifmm_profile_enable.argtypes = [P, I]
+    lib.kifmm_profile_read.argtypes = [P, ctypes.POINTER(ProfileT)]
+    for name in EXPORTS:
+        getattr(lib, name).restype = ctypes.c_int if name != "kifmm_status_string" else ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().kifmm_status_string(code).decode()
+    except Exception:
+        return "unknown"
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise KifmmError(code, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """One precomputed KIFMM configuration (operators + workspace) on the
+    current CUDA device."""
+
+    def __init__(self, p: int = 6, leaf_cap: int = 128, max_depth: int = 20, precision: str = "fp32",
+                 coef: float = 1.0, n_max: int = 1 << 20, n_systems_max: int = 1,
+                 dtype: torch.dtype = torch.float32, pinv_eps: float = 0.0, autotune: bool = False):
+        lib = load()
+        self.dtype = dtype
+        self.precision = precision
+        self.coef = coef
+        d = PlanDesc(p=p, leaf_cap=leaf_cap, max_depth=max_depth, precision=PRECISIONS[precision], coef=coef,
+                     n_max=n_max, n_systems_max=n_systems_max,
+                     dtype=1 if dtype == torch.float64 else 0, pinv_eps=pinv_eps, autotune=int(autotune))
+        h = ctypes.c_void_p()
+        _check(lib.kifmm_plan_create(ctypes.byref(d), ctypes.byref(h)), "kifmm_plan_create")
+        self._h = h
+        self.n = 0
+        self.n_systems = 0
+        self._offsets = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kifmm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_sources(self, xyz: torch.Tensor, q: torch.Tensor, sys_offsets=None, stream=None):
+        assert xyz.is_cuda and q.is_cuda and xyz.dtype == self.dtype and q.dtype == self.dtype
+        xyz = xyz.contiguous()
+        q = q.contiguous()
+        n = xyz.shape[0]
+        if sys_offsets is None:
+            sys_offsets = [0, n]
+        off = np.ascontiguousarray(np.asarray(sys_offsets, dtype=np.int64))
+        _check(load().kifmm_set_sources(self._h, len(off) - 1, off.ctypes.data_as(ctypes.c_void_p),
+                                        _ptr(xyz), _ptr(q), _stream(stream)), "kifmm_set_sources")
+        self.n = n
+        self.n_systems = len(off) - 1
+        self._offsets = off
+
+    def evaluate(self, pot=None, grad=None, energy=None, want_pot=True, want_grad=True, want_energy=False,
+                 stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if pot is None and want_pot:
+            pot = torch.empty(self.n, dtype=self.dtype, device=dev)
+        if grad is None and want_grad:
+            grad = torch.empty(self.n, 3, dtype=self.dtype, device=dev)
+        if energy is None and want_energy:
+            energy = torch.empty(self.n_systems, dtype=torch.float64, device=dev)
+        _check(load().kifmm_evaluate(self._h, _ptr(pot), _ptr(grad), _ptr(energy), _stream(stream)),
+               "kifmm_evaluate")
+        return pot, grad, energy
+
+    def clump_reduce(self, clump_offsets: torch.Tensor, xyz, q, grad, ref, force=None, torque=None, stream=None):
+        nc = clump_offsets.shape[0] - 1
+        if force is None:
+            force = torch.empty(nc, 3, dtype=self.dtype, device=xyz.device)
+        if torque is None:
+            torque = torch.empty(nc, 3, dtype=self.dtype, device=xyz.device)
+        _check(load().kifmm_clump_reduce(self._h, nc, _ptr(clump_offsets), _ptr(xyz), _ptr(q), _ptr(grad),
+                                         _ptr(ref), _ptr(force), _ptr(torque), _stream(stream)),
+               "kifmm_clump_reduce")
+        return force, torque
+
+    def backward(self, dL_dpot, grad, dq=None, dx=None, stream=None):
+        if dq is None:
+            dq = torch.empty(self.n, dtype=self.dtype, device=grad.device)
+        if dx is None:
+            dx = torch.empty(self.n, 3, dtype=self.dtype, device=grad.device)
+        _check(load().kifmm_backward(self._h, _ptr(dL_dpot), _ptr(grad), _ptr(dq), _ptr(dx), _stream(stream)),
+               "kifmm_backward")
+        return dq, dx
+
+    def device_status(self) -> int:
+        c = ctypes.c_int(0)
+        _check(load().kifmm_get_device_status(self._h, ctypes.byref(c)), "kifmm_get_device_status")
+        return c.value
+
+    # ---- profiling ----
+    def profile(self, enable: bool = True):
+        _check(load().kifmm_profile_enable(self._h, int(enable)), "kifmm_profile_enable")
+
+    def profile_read(self) -> dict:
+        """Per-stage device milliseconds and bracket counts since the last
+        read, and the number of kernels the library launched."""
+        t = ProfileT()
+        _check(load().kifmm_profile_read(self._h, ctypes.byref(t)), "kifmm_profile_read")
+        return {"ms": dict(zip(STAGES, list(t.ms))), "calls": dict(zip(STAGES, list(t.calls))),
+                "launches": t.launches}
+
+    # ---- introspection ----
+    def tree_info(self) -> dict:
+        t = TreeInfo()
+        _check(load().kifmm_tree_info(self._h, ctypes.byref(t)), "kifmm_tree_info")
+        return {f: getattr(t, f) for f, _ in TreeInfo._fields_}
+
+    def keys(self):
+        n = self.n
+        keys = np.empty(n, dtype=np.uint64)
+        perm = np.empty(n, dtype=np.int64)
+        lo_side = np.empty((self.n_systems, 4))
+        _check(load().kifmm_copy_keys(self._h, keys.ctypes.data_as(ctypes.c_void_p),
+                                      perm.ctypes.data_as(ctypes.c_void_p),
+                                      lo_side.ctypes.data_as(ctypes.c_void_p)), "kifmm_copy_keys")
+        return keys, perm, lo_side
+
+    def tree(self) -> dict:
+        nb = self.tree_info()["n_boxes"]
+        out = {k: np.empty(nb, dtype=np.int64) for k in ("sys", "level", "first", "count", "parent")}
+        out["coord"] = np.empty((nb, 3), dtype=np.int64)
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(load().kifmm_copy_tree(self._h, c(out["sys"]), c(out["level"]), c(out["coord"]), c(out["first"]),
+                                      c(out["count"]), c(out["parent"])), "kifmm_copy_tree")
+        return out
+
+    def list(self, kind: str):
+        info = self.tree_info()
+        nb = info["n_boxes"]
+        ptr = np.empty(nb + 1, dtype=np.int64)
+        _check(load().kifmm_copy_list(self._h, LIST_KINDS[kind], ptr.ctypes.data_as(ctypes.c_void_p), None),
+               "kifmm_copy_list")
+        idx = np.empty(max(int(ptr[-1]), 1), dtype=np.int64)
+        _check(load().kifmm_copy_list(self._h, LIST_KINDS[kind], ptr.ctypes.data_as(ctypes.c_void_p),
+                                      idx.ctypes.data_as(ctypes.c_void_p)), "kifmm_copy_list")
+        return ptr, idx[:int(ptr[-1])]

@@ -1,0 +1,238 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI.
+
+* Morton keys, sort permutation, tree nodes and U/V/W/X lists: bit-exact.
+* FP64 GPU path vs the oracle's KIFMM (same rules): rel-L2 <= 1e-12.
+* FP32 path vs the FP64 direct sum: within the method's own error at that p
+  plus a small margin (the reduced-precision budget).
+* Edge cases: one particle, two, coincident points, all points coincident
+  (leaves at the depth limit hold more than M), ragged sizes, several
+  systems, non-finite input.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from workloads import generators as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_09478_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+
+
+def _plan(x, precision="fp64", p=4, M=32, D=20, dtype=torch.float64, n_systems=1, **kw):
+    from paper_2512_09478_gb300 import Plan
+    return Plan(p=p, leaf_cap=M, max_depth=D, precision=precision, n_max=len(x), n_systems_max=n_systems,
+                dtype=dtype, **kw)
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+CASES = {
+    "uniform4096": lambda: G.uniform_charges(4096, 1000),
+    "plummer3000": lambda: (G.plummer(3000, 5)[0], np.random.default_rng(5).normal(size=3000)),
+    "clustered": lambda: (np.concatenate([np.random.default_rng(2).normal(0, 1e-3, size=(700, 3)),
+                                          np.random.default_rng(3).uniform(-1, 1, size=(1300, 3))]),
+                          np.random.default_rng(4).choice([-1.0, 1.0], 2000)),
+}
+
+
+@pytest.mark.parametrize("case,M", [("uniform4096", 64), ("plummer3000", 16), ("clustered", 8)])
+def test_tree_and_lists_bit_exact(case, M):
+    x, q = CASES[case]()
+    plan = _plan(x, M=M)
+    plan.set_sources(_dev(x), _dev(q))
+    keys, perm, lo_side = plan.keys()
+    t = O.sort_and_tree(x, M, 20)
+    assert np.array_equal(keys, t["keys"])
+    assert np.array_equal(perm, t["perm"])
+    assert np.array_equal(lo_side[0, :3], t["lo"]) and lo_side[0, 3] == t["side"]
+    g = plan.tree()
+    assert g["level"].shape[0] == t["nb"]
+    for name in ("level", "first", "count", "parent"):
+        assert np.array_equal(g[name], t[name]), name
+    assert np.array_equal(g["coord"], t["coord"])
+    L = O.lists(t)
+    for kind in "UVWX":
+        ptr, idx = plan.list(kind)
+        assert np.array_equal(ptr, L[kind][0]), kind
+        assert np.array_equal(idx, L[kind][1]), kind
+    if case == "plummer3000":
+        assert L["W"][1].size > 0 and L["X"][1].size > 0
+
+
+@pytest.mark.parametrize("case,M,p", [("uniform4096", 64, 4), ("plummer3000", 16, 4), ("clustered", 8, 6)])
+def test_fp64_matches_oracle(case, M, p):
+    x, q = CASES[case]()
+    pot_o, grad_o, _ = O.kifmm(x, q, p=p, leaf_cap=M)
+    plan = _plan(x, M=M, p=p)
+    plan.set_sources(_dev(x), _dev(q))
+    pot, grad, energy = plan.evaluate(want_energy=True)
+    assert plan.device_status() == 0
+    assert O.rel_l2(pot.cpu().numpy(), pot_o) <= 1e-12
+    assert O.rel_l2(grad.cpu().numpy(), grad_o) <= 1e-12
+    assert energy.item() == pytest.approx(O.energy(q, pot_o), rel=1e-12)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_fp32_path_error_budget(dtype):
+    """FP32 at p=6 stays within 1.1x the FP64 KIFMM error (plus 2e-7) against
+    the FP64 direct sum."""
+    x, q = G.uniform_charges(6000, 77)
+    pd, gd = O.direct(x, q)
+    pot_o, grad_o, _ = O.kifmm(x, q, p=6, leaf_cap=32)
+    plan = _plan(x, precision="fp32", p=6, M=32, dtype=dtype)
+    plan.set_sources(_dev(x, dtype), _dev(q, dtype))
+    pot, grad, _ = plan.evaluate()
+    ep, eg = O.rel_l2(pot.cpu().numpy(), pd), O.rel_l2(grad.cpu().numpy(), gd)
+    assert ep <= 1.1 * O.rel_l2(pot_o, pd) + 2e-7
+    assert eg <= 1.1 * O.rel_l2(grad_o, gd) + 2e-7
+
+
+@pytest.mark.parametrize("case,M,p", [("uniform4096", 32, 6), ("plummer3000", 16, 6), ("uniform4096", 64, 4)])
+def test_mixed_fp16_tensor_m2l(case, M, p):
+    """Tensor-core M2L (3xFP16 split) agrees with the FP32 SIMT path to FP32
+    rounding and keeps the FP32 error budget against the direct sum."""
+    x, q = CASES[case]()
+    pd, gd = O.direct(x, q)
+    pot_o, grad_o, _ = O.kifmm(x, q, p=p, leaf_cap=M)
+    out = {}
+    for prec in ("fp32", "mixed_fp16"):
+        plan = _plan(x, precision=prec, p=p, M=M, dtype=torch.float32)
+        plan.set_sources(_dev(x, torch.float32), _dev(q, torch.float32))
+        pot, grad, _ = plan.evaluate()
+        assert plan.device_status() == 0
+        out[prec] = (pot.double().cpu().numpy(), grad.double().cpu().numpy())
+    (p32, g32), (pm, gm) = out["fp32"], out["mixed_fp16"]
+    assert O.rel_l2(pm, p32) < 2e-6 and O.rel_l2(gm, g32) < 2e-6
+    assert O.rel_l2(pm, pd) <= 1.1 * O.rel_l2(pot_o, pd) + 3e-7
+    assert O.rel_l2(gm, gd) <= 1.1 * O.rel_l2(grad_o, gd) + 3e-7
+
+
+def test_single_leaf_equals_direct_sum():
+    x, q = G.uniform_charges(100, 9)
+    plan = _plan(x, M=128)
+    plan.set_sources(_dev(x), _dev(q))
+    pot, grad, _ = plan.evaluate()
+    pd, gd = O.direct(x, q)
+    assert plan.tree_info()["n_boxes"] == 1
+    assert O.rel_l2(pot.cpu().numpy(), pd) < 1e-14 and O.rel_l2(grad.cpu().numpy(), gd) < 1e-14
+
+
+def test_degenerate_inputs():
+    # one particle: no partner, zero field
+    plan = _plan(np.zeros((1, 3)), M=4)
+    plan.set_sources(_dev([[0.3, 0.2, 0.1]]), _dev([2.0]))
+    pot, grad, _ = plan.evaluate()
+    assert pot.item() == 0.0 and torch.all(grad == 0)
+    # two particles
+    x = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    q = np.array([1.0, 2.0])
+    plan = _plan(x, M=1, p=4)
+    plan.set_sources(_dev(x), _dev(q))
+    pot, grad, _ = plan.evaluate()
+    pd, gd = O.direct(x, q)
+    assert np.allclose(pot.cpu().numpy(), pd, rtol=1e-13) and np.allclose(grad.cpu().numpy(), gd, rtol=1e-13)
+    # all points coincident: side 1, every leaf at the depth limit, zero field
+    x = np.ones((50, 3)) * 0.5
+    plan = _plan(x, M=4, D=3)
+    plan.set_sources(_dev(x), _dev(np.ones(50)))
+    pot, grad, _ = plan.evaluate()
+    assert torch.all(pot == 0) and torch.all(grad == 0)
+    assert plan.tree_info()["max_level"] == 3
+    # coincident pairs inside a larger cloud: finite, equal to the direct sum
+    x, q = G.uniform_charges(700, 13)
+    x[1] = x[0]
+    x[5] = x[4]
+    pot_o, grad_o, _ = O.kifmm(x, q, p=4, leaf_cap=8)
+    plan = _plan(x, M=8)
+    plan.set_sources(_dev(x), _dev(q))
+    pot, grad, _ = plan.evaluate()
+    assert torch.all(torch.isfinite(pot)) and torch.all(torch.isfinite(grad))
+    assert O.rel_l2(pot.cpu().numpy(), pot_o) <= 1e-12
+
+
+def test_depth_limit_leaves_exceed_cap():
+    rng = np.random.default_rng(3)
+    x = np.concatenate([np.full((40, 3), 0.25), rng.uniform(size=(200, 3))])
+    q = rng.normal(size=240)
+    plan = _plan(x, M=8, D=5)
+    plan.set_sources(_dev(x), _dev(q))
+    t = O.sort_and_tree(x, 8, 5)
+    g = plan.tree()
+    assert np.array_equal(g["count"], t["count"]) and t["count"][t["level"] == 5].max() >= 40
+    pot, grad, _ = plan.evaluate()
+    pot_o, grad_o, _ = O.kifmm(x, q, p=4, leaf_cap=8, max_depth=5)
+    assert O.rel_l2(pot.cpu().numpy(), pot_o) <= 1e-12
+
+
+def test_batched_systems_match_per_system_oracle():
+    sizes = [1500, 333, 2711]
+    xs, qs = [], []
+    for k, nk in enumerate(sizes):
+        x, q = (G.uniform_charges(nk, 40 + k) if k % 2 == 0 else
+                (G.plummer(nk, 40 + k)[0], np.random.default_rng(k).choice([-1.0, 1.0], nk)))
+        xs.append(x)
+        qs.append(q)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    X, Q = np.concatenate(xs), np.concatenate(qs)
+    plan = _plan(X, M=16, n_systems=3)
+    plan.set_sources(_dev(X), _dev(Q), sys_offsets=off)
+    pot, grad, energy = plan.evaluate(want_energy=True)
+    pot, grad = pot.cpu().numpy(), grad.cpu().numpy()
+    g = plan.tree()
+    for k in range(3):
+        sl = slice(off[k], off[k + 1])
+        po, go, info = O.kifmm(xs[k], qs[k], p=4, leaf_cap=16)
+        assert O.rel_l2(pot[sl], po) <= 1e-12 and O.rel_l2(grad[sl], go) <= 1e-12
+        assert energy[k].item() == pytest.approx(O.energy(qs[k], po), rel=1e-12)
+        t = info["tree"]
+        mine = g["sys"] == k
+        assert mine.sum() == t["nb"]
+        a = sorted(zip(g["level"][mine], map(tuple, g["coord"][mine]), g["count"][mine]))
+        b = sorted(zip(t["level"], map(tuple, t["coord"]), t["count"]))
+        assert a == b
+
+
+def test_nonfinite_input_is_reported():
+    from paper_2512_09478_gb300 import KifmmError
+    x, q = G.uniform_charges(300, 1)
+    x[17, 1] = np.nan
+    plan = _plan(x, M=16)
+    with pytest.raises(KifmmError) as e:
+        plan.set_sources(_dev(x), _dev(q))
+    assert e.value.code == 4
+
+
+def test_argument_errors():
+    from paper_2512_09478_gb300 import Plan, KifmmError
+    with pytest.raises(KifmmError) as e:
+        Plan(p=1, leaf_cap=8, n_max=10)
+    assert e.value.code == 1
+    plan = _plan(np.zeros((10, 3)), M=4)
+    with pytest.raises(KifmmError) as e:
+        plan.evaluate()
+    assert e.value.code == 6
+    with pytest.raises(KifmmError) as e:
+        plan.set_sources(_dev(np.zeros((20, 3))), _dev(np.zeros(20)))
+    assert e.value.code == 2
+
+
+def test_clump_reduce_matches_oracle():
+    x, q, off, centres = G.clumps(500, 8, charges_per_clump=4)
+    plan = _plan(x, M=16, p=4)
+    xt, qt = _dev(x), _dev(q)
+    plan.set_sources(xt, qt)
+    pot, grad, _ = plan.evaluate()
+    F, T = plan.clump_reduce(torch.tensor(off, device="cuda"), xt, qt, grad, _dev(centres))
+    Fo, To = O.clump_reduce(x, q, grad.cpu().numpy(), off, centres)
+    assert O.rel_l2(F.cpu().numpy(), Fo) < 1e-14 and O.rel_l2(T.cpu().numpy(), To) < 1e-14
