@@ -1,13 +1,17 @@
 #!/usr/bin/env python
 """Benchmark: KIFMM long-range force evaluation on one GB300 per rank.
 
-One step = one pass of the whole hot path over one system: set_sources (bounding
-cube, Morton keys, radix sort, octree, U/V/W/X lists) + evaluate (P2M, M2M,
-M2L, P2L, L2L, L2P/M2P, P2P, scatter) for the default workload, the
+One step = one pass of the whole hot path.  Default workload (c2): the
 1M-sphere DEM Coulomb packing (RSA to solid fraction 0.4, radii U[0.5, 1.5]
-mm, charges N(0, (1e-12 C)^2), p = 6, leaf cap 128, FP32 inputs/outputs).
+mm, charges N(0, (1e-12 C)^2), p = 6, leaf cap 128, FP32 inputs/outputs);
+a step is set_sources (bounding cube, Morton keys, radix sort, octree,
+U/V/W/X lists) + evaluate (P2M, M2M, M2L, P2L, L2L, leaf pseudo-inverses,
+L2P/M2P/P2P, scatter).  Other workloads:
+  c3  200k rigid clumps x 4 charges: the step adds the clump force/torque reduce;
+  c5  64 independent systems of 10k..200k particles: the tree is built once and
+      each step replays one captured CUDA graph of update_sources + evaluate.
 
-    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+    python bench.py [--gpus N --steps K --warmup W] [--workload c2|c3|c5] [--impl reference]
 
 Prints one JSON line on rank 0.  A single system does not shard: with N > 1
 every rank evaluates its own replica (no collective on the data path).
@@ -34,8 +38,12 @@ EPS0 = 8.8541878128e-12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 
 WORKLOADS = {
-    "c2": dict(name="dem-coulomb-rsa-1M", n=1_000_000, p=6, leaf_cap=128, max_depth=20, seed=1001),
-    "c2-small": dict(name="dem-coulomb-rsa-64k", n=65_536, p=6, leaf_cap=128, max_depth=20, seed=1001),
+    "c2": dict(kind="rsa", name="dem-coulomb-rsa-1M", n=1_000_000, p=6, leaf_cap=128, max_depth=20, seed=1001),
+    "c2-small": dict(kind="rsa", name="dem-coulomb-rsa-64k", n=65_536, p=6, leaf_cap=128, max_depth=20, seed=1001),
+    "c3": dict(kind="clumps", name="rigid-clumps-200k-x4", n=800_000, clumps=200_000, p=6, leaf_cap=128,
+               max_depth=20, seed=1002),
+    "c5": dict(kind="batched", name="batched-64-systems-10k-200k", systems=64, p=6, leaf_cap=64, max_depth=20,
+               seed=1004),
 }
 
 
@@ -46,7 +54,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default=os.environ.get("KIFMM_BENCH_PRECISION", "fp32"))
+    ap.add_argument("--precision", default=os.environ.get("KIFMM_BENCH_PRECISION", "mixed_fp16"))
     ap.add_argument("--accuracy-targets", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -54,8 +62,18 @@ def parse():
 
 
 def make_inputs(w):
+    """Positions, charges and metadata of a workload.  Coulomb workloads carry
+    SI charges (coef 1/eps0); the batched workload is in Eq. 3 units."""
     from workloads import generators as G
-    x, q, meta = G.dem_coulomb(w["n"], w["seed"])
+    if w["kind"] == "rsa":
+        x, q, meta = G.dem_coulomb(w["n"], w["seed"])
+        meta.update(coef=1.0 / EPS0, offsets=[0, len(x)])
+    elif w["kind"] == "clumps":
+        x, q, off, centres = G.clumps(w["clumps"], w["seed"])
+        meta = {"clump_offsets": off, "centres": centres, "coef": 1.0 / EPS0, "offsets": [0, len(x)]}
+    else:
+        x, q, off = G.batched(w["systems"], w["seed"])
+        meta = {"coef": 1.0, "offsets": [int(v) for v in off]}
     return x, q, meta
 
 
@@ -117,8 +135,8 @@ class ClockSampler:
 
 def algorithmic_work(plan, w, n):
     """Algorithmic units per evaluate for the roofline: M2L flops 2 n_s^2 |V|,
-    P2P pairs (sum over leaves of n_B times the U-list source count, minus the
-    self pairs), tree-build bytes."""
+    near-field pairs (sum over leaves of n_B times the U-list source count,
+    minus the self pairs), tree-build bytes."""
     info = plan.tree_info()
     ns = 6 * (w["p"] - 1) ** 2 + 2
     m2l_flops = 2.0 * ns * ns * info["n_v"]
@@ -141,56 +159,90 @@ def roofline_for(stage, ms_per_call, work, precision, peaks):
         if precision.startswith("mixed"):
             peak = bf16_s if precision == "mixed_fp16" else bf16_s / 2
             return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": None, "kernel": "m2l", "peak_source": f"{kind} bf16 sustained (fp16 same rate)"}
+                    "traffic": None, "kernel": "k_m2l_tc",
+                    "peak_source": f"{kind} bf16 sustained (fp16 same rate); 3 split products, 1 counted"}
         return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "m2l_simt",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "k_ggemm<GatherM2L>",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     if stage == "p2p":
         flops = 20.0 * work["p2p_pairs"]
         ach = flops / (ms_per_call * 1e-3) / 1e12
         return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "p2p",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz; 20 flop per pair"}
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "k_leaf_all",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz; 20 flop per near-field pair"}
     if stage == "tree":
         gbs = work["tree_bytes"] / (ms_per_call * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": None, "kernel": "tree", "peak_source": f"{kind} copy bandwidth"}
+                "traffic": None, "kernel": "set_sources", "peak_source": f"{kind} copy bandwidth"}
     return None
-
-
-def cpu_baseline_leg(x, q, w, n_targets, seed=0, sample_frac=0.5):
-    """CPU leg (the only place the benchmark runs the oracle): time the FP64
-    oracle KIFMM on a bounded sample of the workload (the corner sub-cube
-    holding sample_frac of the particles), and compute FP64 direct-sum
-    reference values on sampled targets for the accuracy figures."""
-    from oracle import oracle as O
-    O.build()
-    lo = x.min(axis=0)
-    side = (x.max(axis=0) - lo).max()
-    cut = side * sample_frac ** (1.0 / 3.0)
-    sel = np.all(x - lo < cut, axis=1)
-    xs, qs = x[sel], q[sel]
-    t0 = time.perf_counter()
-    tree = O.sort_and_tree(xs, w["leaf_cap"], w["max_depth"])
-    lst = O.lists(tree)
-    ops = O.operators(w["p"])
-    t1 = time.perf_counter()
-    O.kifmm(xs, qs, p=w["p"], tree=tree, lst=lst, ops=ops)
-    t2 = time.perf_counter()
-    cores = len(os.sched_getaffinity(0))
-    base = {"value": xs.shape[0] / (t2 - t0 - 0.0) / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"corner sub-cube with {xs.shape[0]} of {x.shape[0]} particles; FP64 oracle tree+lists+KIFMM, "
-                      f"p={w['p']}, M={w['leaf_cap']} ({t2 - t0:.1f} s; operator precompute excluded)"}
-    rng = np.random.default_rng(seed)
-    idx = rng.choice(x.shape[0], size=min(n_targets, x.shape[0]), replace=False)
-    pd, gd = O.direct(x, q, x[idx])
-    return base, idx, pd, gd
 
 
 def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64).ravel()
     b = np.asarray(b, dtype=np.float64).ravel()
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _oracle_sample(x, q, meta, w, frac):
+    """A bounded sample of the workload for the CPU legs: the corner sub-cube
+    holding ``frac`` of the particles (c2, c3), or the leading systems holding
+    about ``frac`` of them (c5)."""
+    if w["kind"] == "batched":
+        off = meta["offsets"]
+        k = max(1, int(np.searchsorted(np.asarray(off[1:]), frac * off[-1])))
+        return [(x[off[s]:off[s + 1]], q[off[s]:off[s + 1]]) for s in range(k)], f"systems 0..{k - 1}"
+    lo = x.min(axis=0)
+    side = (x.max(axis=0) - lo).max()
+    sel = np.all(x - lo < side * frac ** (1.0 / 3.0), axis=1)
+    return [(x[sel], q[sel])], "corner sub-cube"
+
+
+def cpu_baseline_leg(x, q, meta, w, n_targets, seed=0, frac=0.5):
+    """CPU leg (the only place the benchmark runs the oracle): time the FP64
+    oracle KIFMM on a bounded sample of the workload, and compute FP64
+    direct-sum reference values on sampled targets for the accuracy figures."""
+    from oracle import oracle as O
+    O.build()
+    parts, what = _oracle_sample(x, q, meta, w, frac)
+    ops = O.operators(w["p"])
+    t0 = time.perf_counter()
+    n_s = 0
+    for xs, qs in parts:
+        tree = O.sort_and_tree(xs, w["leaf_cap"], w["max_depth"])
+        lst = O.lists(tree)
+        O.kifmm(xs, qs, p=w["p"], tree=tree, lst=lst, ops=ops)
+        n_s += xs.shape[0]
+    t2 = time.perf_counter()
+    cores = len(os.sched_getaffinity(0))
+    base = {"value": n_s / (t2 - t0) / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{what}: {n_s} of {x.shape[0]} particles; FP64 oracle tree+lists+KIFMM, "
+                      f"p={w['p']}, M={w['leaf_cap']} ({t2 - t0:.1f} s; operator precompute excluded)"}
+    rng = np.random.default_rng(seed)
+    ref = {}
+    if w["kind"] == "clumps":
+        off, cen = meta["clump_offsets"], meta["centres"]
+        cl = np.sort(rng.choice(len(cen), size=min(256, len(cen)), replace=False))
+        idx = np.concatenate([np.arange(off[c], off[c + 1]) for c in cl])
+        pd, gd = O.direct(x, q, x[idx])
+        loc = np.concatenate([[0], np.cumsum([off[c + 1] - off[c] for c in cl])])
+        F, T = O.clump_reduce(x[idx], q[idx], gd, loc, cen[cl])
+        ref.update(clumps=cl, F=F, T=T)
+    elif w["kind"] == "batched":
+        off = meta["offsets"]
+        idx_l, pd_l, gd_l = [], [], []
+        for s in rng.choice(len(off) - 1, size=4, replace=False):
+            a, b = off[s], off[s + 1]
+            t = a + rng.choice(b - a, size=min(512, b - a), replace=False)
+            pd_s, gd_s = O.direct(x[a:b], q[a:b], x[t])
+            idx_l.append(t)
+            pd_l.append(pd_s)
+            gd_l.append(gd_s)
+        idx, pd, gd = np.concatenate(idx_l), np.concatenate(pd_l), np.concatenate(gd_l)
+    else:
+        idx = rng.choice(x.shape[0], size=min(n_targets, x.shape[0]), replace=False)
+        pd, gd = O.direct(x, q, x[idx])
+    ref.update(idx=idx, pot=pd, grad=gd)
+    return base, ref
 
 
 def run_reference(args, rank, world):
@@ -202,18 +254,15 @@ def run_reference(args, rank, world):
     O.build()
     w = WORKLOADS[args.workload]
     x, q, meta = make_inputs(w)
-    lo = x.min(axis=0)
-    side = (x.max(axis=0) - lo).max()
-    frac = 0.1
-    cut = side * frac ** (1.0 / 3.0)
-    sel = np.all(x - lo < cut, axis=1)
-    xs, qs = x[sel], q[sel]
+    parts, what = _oracle_sample(x, q, meta, w, 0.1)
     ops = O.operators(w["p"])
+    n_s = sum(p[0].shape[0] for p in parts)
 
     def step():
-        tree = O.sort_and_tree(xs, w["leaf_cap"], w["max_depth"])
-        lst = O.lists(tree)
-        O.kifmm(xs, qs, p=w["p"], tree=tree, lst=lst, ops=ops)
+        for xs, qs in parts:
+            tree = O.sort_and_tree(xs, w["leaf_cap"], w["max_depth"])
+            lst = O.lists(tree)
+            O.kifmm(xs, qs, p=w["p"], tree=tree, lst=lst, ops=ops)
 
     for _ in range(args.warmup):
         step()
@@ -221,15 +270,15 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         step()
     dt = (time.perf_counter() - t0) / args.steps
-    value = xs.shape[0] / dt / 1e6
+    value = n_s / dt / 1e6
     cores = len(os.sched_getaffinity(0))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "leaf_cap": w["leaf_cap"],
+           "config": {"workload": w["name"], "n": int(x.shape[0]), "p": w["p"], "leaf_cap": w["leaf_cap"],
                       "parallelism": "host cores (OpenMP)"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"corner sub-cube with {xs.shape[0]} of {x.shape[0]} particles per step"},
+                            "sample": f"{what}: {n_s} of {x.shape[0]} particles per step"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -243,25 +292,58 @@ def run_ours(args, rank, world, local_rank):
     w = WORKLOADS[args.workload]
     x, q, meta = make_inputs(w)
     n = x.shape[0]
-    coef = 1.0 / EPS0
+    coef, offsets = meta["coef"], meta["offsets"]
+    n_sys = len(offsets) - 1
     xt = torch.tensor(x, dtype=torch.float32, device=dev)
     qt = torch.tensor(q, dtype=torch.float32, device=dev)
     plan = Plan(p=w["p"], leaf_cap=w["leaf_cap"], max_depth=w["max_depth"], precision=args.precision, coef=coef,
-                n_max=n, dtype=torch.float32)
+                n_max=n, n_systems_max=n_sys, dtype=torch.float32)
     pot = torch.empty(n, dtype=torch.float32, device=dev)
     grad = torch.empty(n, 3, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    clumps = w["kind"] == "clumps"
+    if clumps:
+        coff = torch.tensor(meta["clump_offsets"], device=dev)
+        cref = torch.tensor(meta["centres"], dtype=torch.float32, device=dev)
+        force = torch.empty(len(meta["centres"]), 3, dtype=torch.float32, device=dev)
+        torque = torch.empty_like(force)
 
-    def step():
-        plan.set_sources(xt, qt)
+    def eager_step():
+        plan.set_sources(xt, qt, offsets)
         plan.evaluate(pot, grad)
+        if clumps:
+            plan.clump_reduce(coff, xt, qt, grad, cref, force, torque)
+
+    graph = None
+    if w["kind"] == "batched":
+        # tree built once; each step refreshes the particles and evaluates, as one graph
+        plan.set_sources(xt, qt, offsets)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                plan.update_sources(xt, qt)
+                plan.evaluate(pot, grad)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        l0 = plan.profile_read()["launches"]
+        with torch.cuda.graph(graph):
+            plan.update_sources(xt, qt)
+            plan.evaluate(pot, grad)
+        launches_per_replay = plan.profile_read()["launches"]
+
+        def step():
+            graph.replay()
+    else:
+        step = eager_step
 
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
     work = algorithmic_work(plan, w, n)
-    plan.profile(True)
+    if graph is None:
+        plan.profile(True)
     plan.profile_read()
     if dist:
         torch.distributed.barrier()
@@ -279,8 +361,22 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    prof = plan.profile_read()
-    plan.profile(False)
+    if graph is None:
+        prof = plan.profile_read()
+        plan.profile(False)
+        launches = int(prof["launches"])
+        prof_note = "stage events recorded in the timed steps"
+    else:
+        launches = int(launches_per_replay) * args.steps
+        # stage split from an uncaptured pass of the same evaluate (events cannot be read per replay)
+        plan.profile(True)
+        plan.profile_read()
+        for _ in range(args.steps):
+            plan.update_sources(xt, qt)
+            plan.evaluate(pot, grad)
+        prof = plan.profile_read()
+        plan.profile(False)
+        prof_note = "stage events from uncaptured passes of the same update_sources + evaluate"
     total_ms = sum(step_ms)
     if dist:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -289,7 +385,7 @@ def run_ours(args, rank, world, local_rank):
     ms_per_step = total_ms / args.steps
     value = world * n / (ms_per_step * 1e-3) / 1e6
 
-    # end to end: pinned host inputs -> device -> set_sources + evaluate -> host outputs
+    # end to end through the public API: pinned host inputs -> device -> step -> host outputs
     e2e = None
     if not args.no_e2e:
         hx = torch.tensor(x, dtype=torch.float32).pin_memory()
@@ -302,8 +398,10 @@ def run_ours(args, rank, world, local_rank):
         def e2e_step():
             dx.copy_(hx, non_blocking=True)
             dq.copy_(hq, non_blocking=True)
-            plan.set_sources(dx, dq)
+            plan.set_sources(dx, dq, offsets)
             plan.evaluate(pot, grad)
+            if clumps:
+                plan.clump_reduce(coff, dx, dq, grad, cref, force, torque)
             hpot.copy_(pot, non_blocking=True)
             hgrad.copy_(grad, non_blocking=True)
 
@@ -322,39 +420,48 @@ def run_ours(args, rank, world, local_rank):
             e_ms += a.elapsed_time(b)
         e2e = {"value": world * n / (e_ms / ke * 1e-3) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(hx.numel() * 4 + hq.numel() * 4),
-               "d2h_bytes_per_step": int(hpot.numel() * 4 + hgrad.numel() * 4)}
+               "d2h_bytes_per_step": int(hpot.numel() * 4 + hgrad.numel() * 4),
+               "step": "set_sources + evaluate" + (" + clump_reduce" if clumps else "")}
 
     if rank != 0:
         return
-    # dominant stage and its roofline
     calls = prof["calls"]
     per_call = {k: prof["ms"][k] / max(calls[k], 1) for k in prof["ms"] if calls[k] > 0}
-    dominant = max(per_call, key=lambda k: prof["ms"][k])
+    dominant = max((k for k in per_call if k in ("m2l", "p2p", "tree")), key=lambda k: prof["ms"][k])
     peaks = measured_peaks()
     roof = roofline_for(dominant, per_call[dominant], work, args.precision, peaks)
     other = {s: roofline_for(s, per_call[s], work, args.precision, peaks) for s in ("m2l", "p2p", "tree")
              if s in per_call}
+    cfg = {"workload": w["name"], "n": n, "systems": n_sys, "p": w["p"], "leaf_cap": w["leaf_cap"],
+           "precision": args.precision, "parallelism": f"replicas x{world}" if world > 1 else "1 gpu",
+           "l2": "flushed between steps (256 MiB write)", "boxes": work["info"]["n_boxes"],
+           "max_level": work["info"]["max_level"],
+           "step": ("graph replay of update_sources + evaluate (tree frozen)" if graph is not None else
+                    "set_sources + evaluate" + (" + clump_reduce" if clumps else ""))}
+    if "solid_fraction" in meta:
+        cfg["rsa_solid_fraction"] = round(meta["solid_fraction"], 4)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": w["name"], "n": n, "p": w["p"], "leaf_cap": w["leaf_cap"],
-                      "precision": args.precision, "parallelism": f"replicas x{world}" if world > 1 else "1 gpu",
-                      "l2": "flushed between steps (256 MiB write)",
-                      "rsa_solid_fraction": round(meta["solid_fraction"], 4),
-                      "boxes": work["info"]["n_boxes"], "max_level": work["info"]["max_level"]},
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
            "roofline": roof, "stage_rooflines": other,
-           "stages_ms": {k: round(v / args.steps, 4) for k, v in prof["ms"].items() if calls[k] > 0},
-           "gpu_launches": int(prof["launches"]), "clocks": clk, "e2e": e2e}
+           "stages_ms": {k: round(v / max(calls[k], 1) * (calls[k] / args.steps), 4)
+                         for k, v in prof["ms"].items() if calls[k] > 0},
+           "stages_note": prof_note, "gpu_launches": launches, "clocks": clk, "e2e": e2e}
     if not args.no_cpu_baseline:
-        base, idx, pd, gd = cpu_baseline_leg(x, q, w, args.accuracy_targets)
+        base, ref = cpu_baseline_leg(x, q, meta, w, args.accuracy_targets)
         out["cpu_baseline"] = base
-        p_gpu = pot.double().cpu().numpy()[idx] * EPS0  # back to Eq. 3 units for the comparison
-        g_gpu = grad.double().cpu().numpy()[idx] * EPS0
-        f_ref = -q[idx, None] * gd
-        f_gpu = -q[idx, None] * g_gpu
-        out["accuracy"] = {"targets": int(idx.size), "vs": "FP64 direct sum",
-                           "rel_l2_pot": rel_l2(p_gpu, pd), "rel_l2_grad": rel_l2(g_gpu, gd),
-                           "rel_l2_force": rel_l2(f_gpu, f_ref)}
+        idx = ref["idx"]
+        p_gpu = pot.double().cpu().numpy()[idx] / coef  # back to Eq. 3 units for the comparison
+        g_gpu = grad.double().cpu().numpy()[idx] / coef
+        acc = {"targets": int(idx.size), "vs": "FP64 direct sum", "rel_l2_pot": rel_l2(p_gpu, ref["pot"]),
+               "rel_l2_grad": rel_l2(g_gpu, ref["grad"]),
+               "rel_l2_force": rel_l2(-q[idx, None] * g_gpu, -q[idx, None] * ref["grad"])}
+        if clumps:
+            cl = ref["clumps"]
+            acc["clumps"] = int(cl.size)
+            acc["rel_l2_clump_force"] = rel_l2(force.double().cpu().numpy()[cl] / coef, ref["F"])
+            acc["rel_l2_clump_torque"] = rel_l2(torque.double().cpu().numpy()[cl] / coef, ref["T"])
+        out["accuracy"] = acc
     print(json.dumps(out), flush=True)
 
 

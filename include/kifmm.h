@@ -113,6 +113,19 @@ kifmm_status kifmm_set_sources(kifmm_plan *plan, int n_systems, const int64_t *s
                                const void *xyz, const void *q, kifmm_stream_t stream);
 
 /*
+ * Refresh positions and charges with the tree and lists frozen.  The paper
+ * recomputes long-range forces only every S steps (Eq. 2) and builds the tree
+ * once at setup (Sec. 2.4); this call keeps the last set_sources' particle
+ * order, boxes and lists and only rewrites the leaf-relative particle records,
+ * so that evaluate and backward see the new positions.  Particles that left
+ * their leaf stay assigned to it (accuracy degrades with the distance moved;
+ * exactness of the pair coverage does not).  xyz (device, [N,3]) and q
+ * (device, [N]) must hold the same particles in the same order as the last
+ * set_sources.  Never allocates or synchronises (capturable in a CUDA graph).
+ */
+kifmm_status kifmm_update_sources(kifmm_plan *plan, const void *xyz, const void *q, kifmm_stream_t stream);
+
+/*
  * Evaluate the long-range field on every particle (Sec. 2.2 passes; Sec. 2.4
  * per-step evaluation): P2M, M2M, M2L (V list), P2L (X list), L2L, L2P,
  * M2P (W list), P2P (U list).
@@ -213,6 +226,12 @@ kifmm_status kifmm_copy_keys(kifmm_plan *plan, uint64_t *keys, int64_t *perm, do
  * coordinates (3 per node), first sorted particle, count, parent (-1 root). */
 kifmm_status kifmm_copy_tree(kifmm_plan *plan, int64_t *sys, int64_t *level, int64_t *coord,
                              int64_t *first, int64_t *count, int64_t *parent);
+
+/* Expansions after the last evaluate, in root-normalised units of the
+ * kernel 1/r: u (host, [n_boxes, n_s]) upward check potentials, d (host,
+ * [n_boxes, n_s]) downward check potentials, res (host, [N, 4]) potential and
+ * gradient per sorted particle (NULL to skip).  All double. */
+kifmm_status kifmm_copy_expansions(kifmm_plan *plan, double *u, double *d, double *res);
 
 /* One list kind (0 = U, 1 = V, 2 = W, 3 = X) as CSR over nodes:
  * ptr (host, [n_boxes + 1]), idx (host, [n_kind]); sources of each node are

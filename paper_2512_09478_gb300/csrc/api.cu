@@ -134,12 +134,17 @@ static cudaError_t ensure_box_arrays(Plan &P) {
         {(void **)&P.w_ptr, sizeof(uint32_t) * (cap + 1)},
         {(void **)&P.u_cnt, sizeof(uint32_t) * cap},
         {(void **)&P.w_cnt, sizeof(uint32_t) * cap},
-        {(void **)&P.m2l_targets, sizeof(int32_t) * cap},
-        {(void **)&P.leaves, sizeof(int32_t) * cap},
+        {(void **)&P.part_list[0], sizeof(int32_t) * cap},
+        {(void **)&P.part_list[1], sizeof(int32_t) * cap},
+        {(void **)&P.part_list[2], sizeof(int32_t) * cap},
+        {(void **)&P.part_list[3], sizeof(int32_t) * cap},
+        {(void **)&P.child8, sizeof(int32_t) * 8 * cap},
         {(void **)&P.wsrc_flag, sizeof(int32_t) * cap},
         {&P.u_chk, esz * P.ns * cap},
         {&P.d_chk, esz * P.ns * cap},
         {&P.up_dens, esz * P.ns * cap},
+        {&P.tmp_chk, esz * P.ns * cap},
+        {&P.dn_dens, esz * P.ns * cap},
     };
     for (const A &a : arrs) KIFMM_CUDA_TRY(plan_alloc(P, a.p, a.bytes));
     P.list_cap = cap;
@@ -235,12 +240,13 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {(void **)&P.vals[0], sizeof(uint32_t) * n},   {(void **)&P.vals[1], sizeof(uint32_t) * n},
         {(void **)&P.keys_user, sizeof(uint64_t) * n}, {(void **)&P.perm, sizeof(uint32_t) * n},
         {&P.pts, esz * 4 * n},                         {(void **)&P.res, sizeof(double) * 4 * n},
+        {&P.w_sorted, esz * n},
         {(void **)&P.sys_off_d, sizeof(int64_t) * (P.sys_cap + 1)},
         {(void **)&P.lo_side, sizeof(double) * 4 * P.sys_cap},
         {(void **)&P.bbox_ord, sizeof(unsigned long long) * 6 * P.sys_cap},
         {(void **)&P.hist, sizeof(uint32_t) * P.hist_elems},
         {(void **)&P.status, sizeof(int)},
-        {(void **)&P.part_counts, sizeof(uint32_t) * 16},
+        {(void **)&P.part_counts, sizeof(uint32_t) * 256},
         {(void **)&P.energy_chunk_start, sizeof(int32_t) * (P.sys_cap + 1)},
     };
     for (const A &a : arrs)
@@ -378,13 +384,30 @@ kifmm_status kifmm_clump_reduce(kifmm_plan *pl, int64_t n_clumps, const int64_t 
 
 kifmm_status kifmm_backward(kifmm_plan *pl, const void *dL_dpot, const void *grad, void *dq, void *dx,
                             kifmm_stream_t stream) {
-    (void)dL_dpot;
-    (void)grad;
-    (void)dq;
-    (void)dx;
-    (void)stream;
-    if (!pl) return KIFMM_ERR_ARG;
-    return KIFMM_ERR_STATE;
+    if (!pl || !dL_dpot) return KIFMM_ERR_ARG;
+    if (dx && !grad) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!P.has_sources) return KIFMM_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    P.last_stream = s;
+    const long long l0 = g_launches;
+    cudaError_t e = run_backward(P, dL_dpot, grad, dq, dx, s);
+    P.launches += g_launches - l0;
+    return from_cuda(e);
+}
+
+kifmm_status kifmm_update_sources(kifmm_plan *pl, const void *xyz, const void *q, kifmm_stream_t stream) {
+    if (!pl || !xyz || !q) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!P.has_sources) return KIFMM_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    P.last_stream = s;
+    const long long l0 = g_launches;
+    stage_begin(P, KIFMM_STAGE_TREE, s);
+    cudaError_t e = gather_particles(P, xyz, q, s);
+    stage_end(P, KIFMM_STAGE_TREE, s);
+    P.launches += g_launches - l0;
+    return from_cuda(e);
 }
 
 kifmm_status kifmm_get_device_status(kifmm_plan *pl, int *code) {
@@ -475,6 +498,25 @@ kifmm_status kifmm_copy_tree(kifmm_plan *pl, int64_t *sys, int64_t *level, int64
     if (first) API_CUDA(get(P.first, first, 1, 0));
     if (count) API_CUDA(get(P.cnt, count, 1, 0));
     if (parent) API_CUDA(get(P.parent, parent, 1, 0));
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_copy_expansions(kifmm_plan *pl, double *u, double *d, double *res) {
+    if (!pl) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!P.has_sources) return KIFMM_ERR_STATE;
+    API_CUDA(cudaDeviceSynchronize());
+    const size_t m = (size_t)P.nb * P.ns;
+    auto get = [&](const void *src, double *dst) -> cudaError_t {
+        if (P.f64) return cudaMemcpy(dst, src, sizeof(double) * m, cudaMemcpyDeviceToHost);
+        std::vector<float> t(m);
+        cudaError_t e = cudaMemcpy(t.data(), src, sizeof(float) * m, cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < m; ++i) dst[i] = t[i];
+        return e;
+    };
+    if (u) API_CUDA(get(P.u_chk, u));
+    if (d) API_CUDA(get(P.d_chk, d));
+    if (res) API_CUDA(cudaMemcpy(res, P.res, sizeof(double) * 4 * P.n, cudaMemcpyDeviceToHost));
     return KIFMM_OK;
 }
 

@@ -42,7 +42,7 @@ template <typename T>
 __global__ void k_p2m(const int32_t *__restrict__ leaves, const int32_t *__restrict__ lvl,
                       const int32_t *__restrict__ first, const int32_t *__restrict__ cnt,
                       const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, int ns,
-                      T *__restrict__ u) {
+                      T *__restrict__ u, const T *__restrict__ wts = nullptr, int adj = 0) {
     __shared__ T sx[kLeafThreads], sy[kLeafThreads], sz[kLeafThreads], sq[kLeafThreads];
     const int b = leaves[blockIdx.x];
     const T h = box_half<T>(lvl[b]), hinv = T(1) / h;
@@ -64,116 +64,18 @@ __global__ void k_p2m(const int32_t *__restrict__ leaves, const int32_t *__restr
                 sx[threadIdx.x] = v.x * hinv;
                 sy[threadIdx.x] = v.y * hinv;
                 sz[threadIdx.x] = v.z * hinv;
-                sq[threadIdx.x] = v.w;
+                sq[threadIdx.x] = wts ? wts[f + c0 + threadIdx.x] : v.w;
             }
             __syncthreads();
             const int m = min(kLeafThreads, n - c0);
             for (int i = 0; i < m; ++i) acc += sq[i] * lap_pot<T>(px - sx[i], py - sy[i], pz - sz[i]);
         }
-        if (j < ns) u[(size_t)b * ns + j] = acc * hinv;
+        // forward: u = sum q / |UC - x| (1/h from the unit surface); adjoint of
+        // L2P: h * sum w / |DE - x| with the same unit geometry
+        if (j < ns) u[(size_t)b * ns + j] = adj ? acc : acc * hinv;
     }
 }
 
-// M2M for the non-leaf boxes of one level: u(b) = sum_c A_{oct(c)} u(c).
-template <typename T>
-__global__ void k_m2m(int64_t ls, const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
-                      const int32_t *__restrict__ cx, const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
-                      const T *__restrict__ m2m_t, int ns, T *__restrict__ u) {
-    extern __shared__ unsigned char smem_raw[];
-    T *uc = reinterpret_cast<T *>(smem_raw);
-    const int64_t b = ls + blockIdx.x;
-    if (nchild[b] == 0) return;
-    T acc[4] = {0, 0, 0, 0};
-    for (int c = child_first[b]; c < child_first[b] + nchild[b]; ++c) {
-        const int o = 4 * (cx[c] & 1) + 2 * (cy[c] & 1) + (cz[c] & 1);
-        __syncthreads();
-        for (int k = threadIdx.x; k < ns; k += blockDim.x) uc[k] = u[(size_t)c * ns + k];
-        __syncthreads();
-        const T *A = m2m_t + (size_t)o * ns * ns;
-        for (int r = 0; r < 4; ++r) {
-            const int j = threadIdx.x + r * blockDim.x;
-            if (j >= ns) continue;
-            T s = 0;
-            for (int k = 0; k < ns; ++k) s += A[(size_t)k * ns + j] * uc[k];
-            acc[r] += s;
-        }
-    }
-    for (int r = 0; r < 4; ++r) {
-        const int j = threadIdx.x + r * blockDim.x;
-        if (j < ns) u[(size_t)b * ns + j] = acc[r];
-    }
-}
-
-// M2L on SIMT cores: a block owns 64 targets of one octant class and all
-// check points (padded to 160); for each of the class's 189 slots it gathers
-// the 64 source rows and multiplies by the slot's operator.
-constexpr int kM2LT = 64;   // targets per block
-constexpr int kM2LJ = 160;  // padded outputs
-constexpr int kM2LK = 8;    // k chunk
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_m2l_simt(const int32_t *__restrict__ targets, int64_t t_begin,
-                                                  int64_t t_end, int cls, const int32_t *__restrict__ vdense,
-                                                  const int *__restrict__ slot_off, const T *__restrict__ m2l_t,
-                                                  int ns, const T *__restrict__ u, T *__restrict__ d) {
-    __shared__ T Us[kM2LK][kM2LT];
-    __shared__ T Ms[kM2LK][kM2LJ];
-    __shared__ int32_t tgt[kM2LT];
-    __shared__ int32_t src[kM2LT];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int64_t t0 = t_begin + (int64_t)blockIdx.x * kM2LT;
-    if (threadIdx.x < kM2LT) tgt[threadIdx.x] = (t0 + threadIdx.x < t_end) ? targets[t0 + threadIdx.x] : -1;
-    T acc[4][10];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 10; ++c) acc[a][c] = 0;
-    __syncthreads();
-    for (int s = 0; s < kVSlots; ++s) {
-        if (threadIdx.x < kM2LT) {
-            const int32_t t = tgt[threadIdx.x];
-            src[threadIdx.x] = (t >= 0) ? vdense[(size_t)t * kVSlots + s] : -1;
-        }
-        const T *M = m2l_t + (size_t)slot_off[cls * kVSlots + s] * ns * ns;
-        __syncthreads();
-        for (int k0 = 0; k0 < ns; k0 += kM2LK) {
-            // gather: 64 targets x 8 k values, k-contiguous per target
-            for (int e = threadIdx.x; e < kM2LT * kM2LK; e += 256) {
-                const int t = e / kM2LK, k = e % kM2LK;
-                const int32_t sb = src[t];
-                Us[k][t] = (sb >= 0 && k0 + k < ns) ? u[(size_t)sb * ns + k0 + k] : T(0);
-            }
-            for (int e = threadIdx.x; e < kM2LK * kM2LJ; e += 256) {
-                const int k = e / kM2LJ, j = e % kM2LJ;
-                Ms[k][j] = (k0 + k < ns && j < ns) ? M[(size_t)(k0 + k) * ns + j] : T(0);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < kM2LK; ++k) {
-                T uv[4], mv[10];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) uv[a] = Us[k][ty + 16 * a];
-#pragma unroll
-                for (int c = 0; c < 10; ++c) mv[c] = Ms[k][tx + 16 * c];
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int c = 0; c < 10; ++c) acc[a][c] += uv[a] * mv[c];
-            }
-            __syncthreads();
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int32_t t = tgt[ty + 16 * a];
-        if (t < 0) continue;
-#pragma unroll
-        for (int c = 0; c < 10; ++c) {
-            const int j = tx + 16 * c;
-            if (j < ns) d[(size_t)t * ns + j] = acc[a][c];
-        }
-    }
-}
 
 // P2L: d(b)_j += (1/h_b) sum_{a in X(b)} sum_i q_i / |1.05 S_j - (x_i - c_b)/h_b|
 template <typename T>
@@ -182,7 +84,7 @@ __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict_
                       const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
                       const int32_t *__restrict__ first, const int32_t *__restrict__ cnt,
                       const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, int ns,
-                      T *__restrict__ d) {
+                      T *__restrict__ d, const T *__restrict__ wts = nullptr, int adj = 0) {
     __shared__ T sx[kLeafThreads], sy[kLeafThreads], sz[kLeafThreads], sq[kLeafThreads];
     const int b = blockIdx.x;
     if (nx[b] == 0) return;
@@ -212,196 +114,338 @@ __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict_
                     sx[threadIdx.x] = (ox + v.x) * hinv;
                     sy[threadIdx.x] = (oy + v.y) * hinv;
                     sz[threadIdx.x] = (oz + v.z) * hinv;
-                    sq[threadIdx.x] = v.w;
+                    sq[threadIdx.x] = wts ? wts[f + c0 + threadIdx.x] : v.w;
                 }
                 __syncthreads();
                 const int m = min(kLeafThreads, n - c0);
                 for (int i = 0; i < m; ++i) acc += sq[i] * lap_pot<T>(px - sx[i], py - sy[i], pz - sz[i]);
             }
         }
-        if (j < ns) d[(size_t)b * ns + j] += acc * hinv;
+        if (j < ns) d[(size_t)b * ns + j] += adj ? acc : acc * hinv;
     }
 }
 
-// L2L for one level: d(b) += C_{oct(b)} d(parent(b)).
-template <typename T>
-__global__ void k_l2l(int64_t ls, const int32_t *__restrict__ parent, const int32_t *__restrict__ cx,
-                      const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
-                      const T *__restrict__ l2l_t, int ns, T *__restrict__ d) {
-    extern __shared__ unsigned char smem_raw[];
-    T *dp = reinterpret_cast<T *>(smem_raw);
-    const int64_t b = ls + blockIdx.x;
-    const int32_t p = parent[b];
-    const int o = 4 * (cx[b] & 1) + 2 * (cy[b] & 1) + (cz[b] & 1);
-    for (int k = threadIdx.x; k < ns; k += blockDim.x) dp[k] = d[(size_t)p * ns + k];
-    __syncthreads();
-    const T *C = l2l_t + (size_t)o * ns * ns;
-    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
-        T s = 0;
-        for (int k = 0; k < ns; ++k) s += C[(size_t)k * ns + j] * dp[k];
-        d[(size_t)b * ns + j] += s;
-    }
-}
-
-// dens = V (W chk): the two-step pseudo-inverse, normalised to a unit box.
-template <typename T>
-__device__ void pinv_apply(const T *__restrict__ w_t, const T *__restrict__ v_t, int ns, const T *chk, T *tmp,
-                           T *dens) {
-    for (int m = threadIdx.x; m < ns; m += blockDim.x) {
-        T s = 0;
-        for (int j = 0; j < ns; ++j) s += w_t[(size_t)j * ns + m] * chk[j];
-        tmp[m] = s;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-        T s = 0;
-        for (int m = 0; m < ns; ++m) s += v_t[(size_t)m * ns + k] * tmp[m];
-        dens[k] = s;
-    }
-    __syncthreads();
-}
+// ---------------------------------------------------------------------------
+// Gathered, class-tiled GEMM on SIMT cores:
+//   out[t] (=|+=) sum_{s < nslots} Op_s  in[src(t, s)]
+// for a list of targets.  A block owns 64 targets and all outputs (padded to
+// 160); each thread keeps an 8 x 5 register tile (targets 8 ty .. 8 ty + 7,
+// outputs tx + 32 c).  Operators are stored transposed ([k][j]); k advances in
+// chunks of 8 through shared memory with the next chunk prefetched into
+// registers.  Used for M2L (189 V slots), M2M (8 child octants), L2L (parent)
+// and the two factors of the leaf pseudo-inverses.
+// ---------------------------------------------------------------------------
+constexpr int kGT = 64, kGJ = 160, kGK = 8;
 
 template <typename T>
-__global__ void k_up_dens(int64_t nb, const int32_t *__restrict__ flag, const T *__restrict__ w_t,
-                          const T *__restrict__ v_t, int ns, const T *__restrict__ u, T *__restrict__ dens) {
-    extern __shared__ unsigned char smem_raw[];
-    T *chk = reinterpret_cast<T *>(smem_raw);
-    T *tmp = chk + ns;
-    T *out = tmp + ns;
-    const int64_t b = blockIdx.x;
-    if (!flag[b]) return;
-    for (int k = threadIdx.x; k < ns; k += blockDim.x) chk[k] = u[(size_t)b * ns + k];
-    __syncthreads();
-    pinv_apply<T>(w_t, v_t, ns, chk, tmp, out);
-    for (int k = threadIdx.x; k < ns; k += blockDim.x) dens[(size_t)b * ns + k] = out[k];
-}
-
-// Leaf far field: L2P from the downward density on DE = 2.95 h S and M2P
-// from the upward densities (UE = 1.05 h S) of the W-list boxes.
+struct GatherM2L {
+    const int32_t *vdense;
+    const int *slot_off;
+    const T *ops;
+    int ns, cls;
+    __device__ int src(int t, int s) const { return vdense[(size_t)t * kVSlots + s]; }
+    __device__ const T *op(int s) const { return ops + (size_t)slot_off[cls * kVSlots + s] * ns * ns; }
+};
 template <typename T>
-__global__ void k_leaf_far(const int32_t *__restrict__ leaves, const int32_t *__restrict__ lvl,
-                           const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
-                           const int32_t *__restrict__ cz, const int32_t *__restrict__ first,
-                           const int32_t *__restrict__ cnt, const typename Vec4<T>::type *__restrict__ pts,
-                           const T *__restrict__ surf, int ns, const T *__restrict__ dn_w_t,
-                           const T *__restrict__ dn_v_t, const T *__restrict__ d,
-                           const uint32_t *__restrict__ w_ptr, const int32_t *__restrict__ w_idx,
-                           const T *__restrict__ up_dens, double4 *__restrict__ res) {
-    extern __shared__ unsigned char smem_raw[];
-    T *chk = reinterpret_cast<T *>(smem_raw);
-    T *tmp = chk + ns;
-    T *dens = tmp + ns;
-    const int b = leaves[blockIdx.x];
-    const int lb = lvl[b];
-    const T h = box_half<T>(lb), hinv = T(1) / h;
-    for (int k = threadIdx.x; k < ns; k += blockDim.x) chk[k] = d[(size_t)b * ns + k];
-    __syncthreads();
-    pinv_apply<T>(dn_w_t, dn_v_t, ns, chk, tmp, dens);
-    const int n = cnt[b], f = first[b];
-    const T ao = (T)kAlphaOuter, ai = (T)kAlphaInner;
-    // per-thread particles (up to 4 per thread for leaves above 128)
-    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
-        const int i = i0 + threadIdx.x;
-        T pot = 0, gx = 0, gy = 0, gz = 0;
-        T X = 0, Y = 0, Z = 0;
-        typename Vec4<T>::type v{};
-        if (i < n) {
-            v = pts[f + i];
-            X = v.x * hinv;
-            Y = v.y * hinv;
-            Z = v.z * hinv;
-            for (int k = 0; k < ns; ++k)
-                lap_accum<T>(X - ao * surf[3 * k], Y - ao * surf[3 * k + 1], Z - ao * surf[3 * k + 2], dens[k],
-                             pot, gx, gy, gz);
-            gx *= hinv;
-            gy *= hinv;
-            gz *= hinv;
-        }
-        // M2P
-        for (uint32_t e = w_ptr[b]; e < w_ptr[b + 1]; ++e) {
-            const int a = w_idx[e];
-            const int la = lvl[a];
-            const T ha = box_half<T>(la), hainv = T(1) / ha;
-            __syncthreads();
-            for (int k = threadIdx.x; k < ns; k += blockDim.x) tmp[k] = up_dens[(size_t)a * ns + k];
-            __syncthreads();
-            if (i < n) {
-                const T ox = box_center<T>(cx[b], lb) - box_center<T>(cx[a], la);
-                const T oy = box_center<T>(cy[b], lb) - box_center<T>(cy[a], la);
-                const T oz = box_center<T>(cz[b], lb) - box_center<T>(cz[a], la);
-                const T Xa = (ox + v.x) * hainv, Ya = (oy + v.y) * hainv, Za = (oz + v.z) * hainv;
-                T p2 = 0, g2x = 0, g2y = 0, g2z = 0;
-                for (int k = 0; k < ns; ++k)
-                    lap_accum<T>(Xa - ai * surf[3 * k], Ya - ai * surf[3 * k + 1], Za - ai * surf[3 * k + 2], tmp[k],
-                                 p2, g2x, g2y, g2z);
-                pot += p2;
-                gx += g2x * hainv;
-                gy += g2y * hainv;
-                gz += g2z * hainv;
-            }
-        }
-        if (i < n) res[f + i] = make_double4((double)pot, (double)gx, (double)gy, (double)gz);
-    }
-}
-
-// P2P over the U list; each source leaf's contribution is summed plainly and
-// added to the running totals with a compensated (two-sum) update.
+struct GatherChild {
+    const int32_t *child8;
+    const T *ops;
+    int ns;
+    __device__ int src(int t, int s) const { return child8[(size_t)t * 8 + s]; }
+    __device__ const T *op(int s) const { return ops + (size_t)s * ns * ns; }
+};
 template <typename T>
-__global__ void k_p2p(const int32_t *__restrict__ leaves, const int32_t *__restrict__ lvl,
-                      const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
-                      const int32_t *__restrict__ cz, const int32_t *__restrict__ first,
-                      const int32_t *__restrict__ cnt, const typename Vec4<T>::type *__restrict__ pts,
-                      const uint32_t *__restrict__ u_ptr, const int32_t *__restrict__ u_idx,
-                      double4 *__restrict__ res) {
-    __shared__ T sx[kLeafThreads], sy[kLeafThreads], sz[kLeafThreads], sq[kLeafThreads];
-    const int b = leaves[blockIdx.x];
-    const int lb = lvl[b];
-    const T cbx = box_center<T>(cx[b], lb), cby = box_center<T>(cy[b], lb), cbz = box_center<T>(cz[b], lb);
-    const int n = cnt[b], f = first[b];
-    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
-        const int i = i0 + threadIdx.x;
-        typename Vec4<T>::type v{};
-        if (i < n) v = pts[f + i];
-        T acc[4] = {0, 0, 0, 0}, cmp[4] = {0, 0, 0, 0};
-        for (uint32_t e = u_ptr[b]; e < u_ptr[b + 1]; ++e) {
-            const int a = u_idx[e];
-            const int la = lvl[a];
-            const T ox = box_center<T>(cx[a], la) - cbx, oy = box_center<T>(cy[a], la) - cby,
-                    oz = box_center<T>(cz[a], la) - cbz;
-            const int na = cnt[a], fa = first[a];
-            for (int c0 = 0; c0 < na; c0 += kLeafThreads) {
-                __syncthreads();
-                if (c0 + threadIdx.x < na) {
-                    const auto w = pts[fa + c0 + threadIdx.x];
-                    sx[threadIdx.x] = ox + w.x;
-                    sy[threadIdx.x] = oy + w.y;
-                    sz[threadIdx.x] = oz + w.z;
-                    sq[threadIdx.x] = w.w;
-                }
-                __syncthreads();
-                if (i < n) {
-                    const int m = min(kLeafThreads, na - c0);
-                    T p = 0, gx = 0, gy = 0, gz = 0;
-                    for (int j = 0; j < m; ++j) lap_accum<T>(v.x - sx[j], v.y - sy[j], v.z - sz[j], sq[j], p, gx, gy, gz);
-                    const T part[4] = {p, gx, gy, gz};
+struct GatherParent {
+    const int32_t *parent;
+    const T *op0;
+    __device__ int src(int t, int) const { return parent[t]; }
+    __device__ const T *op(int) const { return op0; }
+};
+template <typename T>
+struct GatherSelf {
+    const T *op0;
+    __device__ int src(int t, int) const { return t; }
+    __device__ const T *op(int) const { return op0; }
+};
+
+template <typename T, class G>
+__global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ targets, int64_t t_begin,
+                                               int64_t t_end, int nslots, int ns, const T *__restrict__ in,
+                                               T *__restrict__ out, int accumulate) {
+    __shared__ __align__(16) T Us[kGK][kGT];
+    __shared__ __align__(16) T Ms[kGK][kGJ];
+    __shared__ int32_t tgt[kGT];
+    __shared__ int32_t src[kGT];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t t0 = t_begin + (int64_t)blockIdx.x * kGT;
+    if (threadIdx.x < kGT) tgt[threadIdx.x] = (t0 + threadIdx.x < t_end) ? targets[t0 + threadIdx.x] : -1;
+    // FP32: each slot sums into a fresh partial that is then added to the
+    // running total, so no rounding chain is longer than one slot's n_s terms.
+    constexpr bool kTwoLevel = sizeof(T) == 4;
+    T acc[8][5], run[8][5];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        T s, err;
-                        two_sum<T>(acc[c], part[c], s, err);
-                        acc[c] = s;
-                        cmp[c] += err;
-                    }
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) acc[a][c] = run[a][c] = T(0);
+    const int nk = (ns + kGK - 1) / kGK;
+    __syncthreads();
+    for (int s = 0; s < nslots; ++s) {
+        if (threadIdx.x < kGT) {
+            const int32_t t = tgt[threadIdx.x];
+            src[threadIdx.x] = (t >= 0) ? g.src(t, s) : -1;
+        }
+        const T *M = g.op(s);
+        __syncthreads();
+        T ru[2], rm[5];
+        auto load = [&](int kc) {
+            const int k0 = kc * kGK;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int e = threadIdx.x + 256 * r;
+                const int t = e >> 3, k = e & 7;
+                const int32_t sb = src[t];
+                ru[r] = (sb >= 0 && k0 + k < ns) ? in[(size_t)sb * ns + k0 + k] : T(0);
+            }
+#pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                const int e = threadIdx.x + 256 * r;
+                const int k = e / kGJ, j = e - k * kGJ;
+                rm[r] = (k0 + k < ns && j < ns) ? M[(size_t)(k0 + k) * ns + j] : T(0);
+            }
+        };
+        load(0);
+        for (int kc = 0; kc < nk; ++kc) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int e = threadIdx.x + 256 * r;
+                Us[e & 7][e >> 3] = ru[r];
+            }
+#pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                const int e = threadIdx.x + 256 * r;
+                const int k = e / kGJ;
+                Ms[k][e - k * kGJ] = rm[r];
+            }
+            __syncthreads();
+            if (kc + 1 < nk) load(kc + 1);
+#pragma unroll
+            for (int k = 0; k < kGK; ++k) {
+                T uv[8], mv[5];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) uv[a] = Us[k][8 * ty + a];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) mv[c] = Ms[k][tx + 32 * c];
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) acc[a][c] += uv[a] * mv[c];
+            }
+            __syncthreads();
+        }
+        if constexpr (kTwoLevel) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    run[a][c] += acc[a][c];
+                    acc[a][c] = T(0);
                 }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int32_t t = tgt[8 * ty + a];
+        if (t < 0) continue;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const int j = tx + 32 * c;
+            if (j < ns) {
+                const T v = kTwoLevel ? run[a][c] : acc[a][c];
+                T *o = out + (size_t)t * ns + j;
+                *o = accumulate ? *o + v : v;
             }
         }
-        if (i < n) {
-            double4 r = res[f + i];
-            r.x += (double)acc[0] + (double)cmp[0];
-            r.y += (double)acc[1] + (double)cmp[1];
-            r.z += (double)acc[2] + (double)cmp[2];
-            r.w += (double)acc[3] + (double)cmp[3];
-            res[f + i] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf evaluation, one warp per target leaf: far field (L2P from the leaf's
+// downward density on DE = 2.95 h S; M2P from the upward densities on
+// UE = 1.05 h S of the W-list boxes) and near field (P2P over the U list),
+// all as one stream of (pseudo-)sources {position relative to the leaf
+// centre, weight}.  Lanes l and l^16 share targets (l & 15) + 16 k and split
+// each staged chunk by parity; each chunk is summed plainly and added to the
+// totals with two-sum; the result overwrites res.
+// ---------------------------------------------------------------------------
+constexpr int kLW = 4;
+constexpr int kLChunk = 128;
+
+template <typename T, int TPL>
+struct LeafAcc {
+    T tx[TPL], ty[TPL], tz[TPL];
+    T acc[TPL][4], cmp[TPL][4];
+};
+
+template <typename T, int TPL>
+__device__ __forceinline__ void leaf_chunk(LeafAcc<T, TPL> &L, const typename Vec4<T>::type *buf, int m, int half) {
+    T part[TPL][4];
+#pragma unroll
+    for (int k = 0; k < TPL; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[k][c] = T(0);
+    for (int j = half; j < m; j += 2) {
+        const auto s = buf[j];
+#pragma unroll
+        for (int k = 0; k < TPL; ++k)
+            lap_accum<T>(L.tx[k] - s.x, L.ty[k] - s.y, L.tz[k] - s.z, s.w, part[k][0], part[k][1], part[k][2],
+                         part[k][3]);
+    }
+#pragma unroll
+    for (int k = 0; k < TPL; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            T sum, err;
+            two_sum<T>(L.acc[k][c], part[k][c], sum, err);
+            L.acc[k][c] = sum;
+            L.cmp[k][c] += err;
         }
+}
+
+struct LeafCtx {
+    const int32_t *lvl, *cx, *cy, *cz, *first, *cnt;
+    const uint32_t *u_ptr, *w_ptr;
+    const int32_t *u_idx, *w_idx;
+    int ns;
+};
+
+// Source weights of the leaf stage.  Forward: own surface dn_dens * h_b,
+// W surfaces up_dens * h_a, particles q.  Adjoint (same geometry): own
+// surface u-bar, W surfaces d-bar, particles w.
+template <typename T>
+struct LeafW {
+    const T *own;
+    int own_h;
+    const T *wl;
+    int wl_h;
+    const T *pw;  // sorted per-particle weights, or nullptr for the charges
+};
+
+template <typename T, int TPL>
+__device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec4<T>::type *__restrict__ pts,
+                          const T *__restrict__ surf, const LeafW<T> &W, typename Vec4<T>::type *buf,
+                          double4 *__restrict__ res) {
+    using V4 = typename Vec4<T>::type;
+    const int lane = threadIdx.x & 31, half = lane >> 4;
+    const int lb = C.lvl[b];
+    const T cbx = box_center<T>(C.cx[b], lb), cby = box_center<T>(C.cy[b], lb), cbz = box_center<T>(C.cz[b], lb);
+    const int n = C.cnt[b], f = C.first[b], ns = C.ns;
+    LeafAcc<T, TPL> L;
+#pragma unroll
+    for (int k = 0; k < TPL; ++k) {
+        const int i = tbase + (lane & 15) + 16 * k;
+        V4 v{};
+        if (i < n) v = pts[f + i];
+        L.tx[k] = v.x;
+        L.ty[k] = v.y;
+        L.tz[k] = v.z;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) L.acc[k][c] = L.cmp[k][c] = T(0);
+    }
+    // L2P: own downward equivalent surface
+    {
+        const T h = box_half<T>(lb), r = (T)kAlphaOuter * h;
+        for (int c0 = 0; c0 < ns; c0 += kLChunk) {
+            const int m = min(kLChunk, ns - c0);
+            __syncwarp();
+            for (int j = lane; j < m; j += 32) {
+                const int k = c0 + j;
+                V4 w;
+                w.x = r * surf[3 * k];
+                w.y = r * surf[3 * k + 1];
+                w.z = r * surf[3 * k + 2];
+                w.w = W.own[(size_t)b * ns + k] * (W.own_h ? h : T(1));
+                buf[j] = w;
+            }
+            __syncwarp();
+            leaf_chunk<T, TPL>(L, buf, m, half);
+        }
+    }
+    // M2P: upward equivalent surfaces of the W list
+    for (uint32_t e = C.w_ptr[b]; e < C.w_ptr[b + 1]; ++e) {
+        const int a = C.w_idx[e];
+        const int la = C.lvl[a];
+        const T ha = box_half<T>(la), r = (T)kAlphaInner * ha;
+        const T ox = box_center<T>(C.cx[a], la) - cbx, oy = box_center<T>(C.cy[a], la) - cby,
+                oz = box_center<T>(C.cz[a], la) - cbz;
+        for (int c0 = 0; c0 < ns; c0 += kLChunk) {
+            const int m = min(kLChunk, ns - c0);
+            __syncwarp();
+            for (int j = lane; j < m; j += 32) {
+                const int k = c0 + j;
+                V4 w;
+                w.x = ox + r * surf[3 * k];
+                w.y = oy + r * surf[3 * k + 1];
+                w.z = oz + r * surf[3 * k + 2];
+                w.w = W.wl[(size_t)a * ns + k] * (W.wl_h ? ha : T(1));
+                buf[j] = w;
+            }
+            __syncwarp();
+            leaf_chunk<T, TPL>(L, buf, m, half);
+        }
+    }
+    // P2P: particles of the U list
+    for (uint32_t e = C.u_ptr[b]; e < C.u_ptr[b + 1]; ++e) {
+        const int a = C.u_idx[e];
+        const int la = C.lvl[a];
+        const T ox = box_center<T>(C.cx[a], la) - cbx, oy = box_center<T>(C.cy[a], la) - cby,
+                oz = box_center<T>(C.cz[a], la) - cbz;
+        const int na = C.cnt[a], fa = C.first[a];
+        for (int c0 = 0; c0 < na; c0 += kLChunk) {
+            const int m = min(kLChunk, na - c0);
+            __syncwarp();
+            for (int j = lane; j < m; j += 32) {
+                V4 w = pts[fa + c0 + j];
+                if (W.pw) w.w = W.pw[fa + c0 + j];
+                w.x += ox;
+                w.y += oy;
+                w.z += oz;
+                buf[j] = w;
+            }
+            __syncwarp();
+            leaf_chunk<T, TPL>(L, buf, m, half);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < TPL; ++k) {
+        double tot[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const double mine = (double)L.acc[k][c] + (double)L.cmp[k][c];
+            tot[c] = mine + __shfl_xor_sync(0xffffffffu, mine, 16);
+        }
+        const int i = tbase + (lane & 15) + 16 * k;
+        if (half == 0 && i < n) res[f + i] = make_double4(tot[0], tot[1], tot[2], tot[3]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kLW) k_leaf_all(LeafCtx C, int64_t n_leaves, const int32_t *__restrict__ leaves,
+                                                      const typename Vec4<T>::type *__restrict__ pts,
+                                                      const T *__restrict__ surf, LeafW<T> W,
+                                                      double4 *__restrict__ res) {
+    __shared__ typename Vec4<T>::type bufs[kLW][kLChunk];
+    const int warp = threadIdx.x >> 5;
+    const int64_t li = (int64_t)blockIdx.x * kLW + warp;
+    if (li >= n_leaves) return;
+    const int b = leaves[li];
+    const int n = C.cnt[b];
+    auto *buf = bufs[warp];
+    if (n <= 16) {
+        leaf_pass<T, 1>(C, b, 0, pts, surf, W, buf, res);
+    } else if (n <= 32) {
+        leaf_pass<T, 2>(C, b, 0, pts, surf, W, buf, res);
+    } else {
+        for (int t0 = 0; t0 < n; t0 += 64) leaf_pass<T, 4>(C, b, t0, pts, surf, W, buf, res);
     }
 }
 
@@ -483,28 +527,35 @@ __global__ void k_clump(int64_t nc, const int64_t *__restrict__ off, const TO *_
     }
 }
 
+
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+template <typename T, class G>
+void ggemm(Plan &P, const G &g, const int32_t *targets, int64_t a, int64_t e, int nslots, const T *in, T *out,
+           int accumulate, cudaStream_t s) {
+    if (e <= a) return;
+    ++g_launches, k_ggemm<T, G><<<grid_for(e - a, kGT), 256, 0, s>>>(g, targets, a, e, nslots, P.ns, in, out,
+                                                                     accumulate);
+}
 
 template <typename T>
 cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
     const int ns = P.ns;
+    const size_t nn = (size_t)ns * ns;
     const T *surf = P.f64 ? (const T *)P.surf64 : (const T *)P.surf32;
-    T *u = (T *)P.u_chk, *d = (T *)P.d_chk;
+    T *u = (T *)P.u_chk, *d = (T *)P.d_chk, *tmp = (T *)P.tmp_chk;
     const V4 *pts = (const V4 *)P.pts;
     double4 *res = (double4 *)P.res;
     // upward pass
-    const size_t sm1 = sizeof(T) * ns;
     stage_begin(P, KIFMM_STAGE_P2M, s);
     ++g_launches, k_p2m<T><<<(unsigned)P.n_leaves, kLeafThreads, 0, s>>>(P.leaves, P.lvl, P.first, P.cnt, pts,
                                                                         surf, ns, u);
     stage_end(P, KIFMM_STAGE_P2M, s);
     stage_begin(P, KIFMM_STAGE_M2M, s);
-    for (int l = P.max_level - 1; l >= 0; --l) {
-        const int64_t ls = P.level_start[l], le = P.level_start[l + 1];
-        ++g_launches, k_m2m<T><<<(unsigned)(le - ls), 128, sm1, s>>>(ls, P.child_first, P.nchild, P.cx, P.cy,
-                                                                      P.cz, (const T *)P.m2m_t, ns, u);
-    }
+    for (int l = P.max_level - 1; l >= 0; --l)
+        ggemm<T>(P, GatherChild<T>{P.child8, (const T *)P.m2m_t, ns}, P.part_list[1],
+                 P.part_start[1][1 + l], P.part_start[1][2 + l], 8, u, u, 0, s);
     stage_end(P, KIFMM_STAGE_M2M, s);
     KIFMM_CUDA_TRY(cudaGetLastError());
     // interactions
@@ -514,12 +565,9 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     if (tensor) {
         KIFMM_CUDA_TRY(m2l_tensor(P, s));
     } else {
-        for (int c = 0; c < 8; ++c) {
-            const int64_t a = P.m2l_class_start[c], e = P.m2l_class_start[c + 1];
-            if (e > a)
-                ++g_launches, k_m2l_simt<T><<<grid_for(e - a, kM2LT), 256, 0, s>>>(
-                                  P.m2l_targets, a, e, c, P.vdense, P.slot_off, (const T *)P.m2l_t, ns, u, d);
-        }
+        for (int c = 0; c < 8; ++c)
+            ggemm<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.m2l_t, ns, c}, P.part_list[0],
+                     P.part_start[0][c], P.part_start[0][c + 1], kVSlots, u, d, 0, s);
     }
     stage_end(P, KIFMM_STAGE_M2L, s);
     if (P.n_x > 0) {
@@ -528,29 +576,31 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
                                                                         P.first, P.cnt, pts, surf, ns, d);
         stage_end(P, KIFMM_STAGE_P2L, s);
     }
-    // downward pass
+    // downward pass: per level, per octant class of the child
     stage_begin(P, KIFMM_STAGE_L2L, s);
-    for (int l = 1; l <= P.max_level; ++l) {
-        const int64_t ls = P.level_start[l], le = P.level_start[l + 1];
-        ++g_launches, k_l2l<T><<<(unsigned)(le - ls), 128, sm1, s>>>(ls, P.parent, P.cx, P.cy, P.cz,
-                                                                      (const T *)P.l2l_t, ns, d);
-    }
+    for (int l = 1; l <= P.max_level; ++l)
+        for (int c = 0; c < 8; ++c) {
+            const int key = l * 8 + c;
+            ggemm<T>(P, GatherParent<T>{P.parent, (const T *)P.l2l_t + (size_t)c * nn}, P.part_list[3],
+                     P.part_start[3][key], P.part_start[3][key + 1], 1, d, d, 1, s);
+        }
     stage_end(P, KIFMM_STAGE_L2L, s);
     KIFMM_CUDA_TRY(cudaGetLastError());
-    // leaves
+    // leaves: equivalent densities (two-step pseudo-inverse), then L2P + M2P + P2P
     stage_begin(P, KIFMM_STAGE_LEAF, s);
-    if (P.n_w > 0)
-        ++g_launches, k_up_dens<T><<<(unsigned)P.nb, 128, 3 * sm1, s>>>(P.nb, P.wsrc_flag, (const T *)P.up_w_t,
-                                                                         (const T *)P.up_v_t, ns, u,
-                                                                         (T *)P.up_dens);
-    ++g_launches, k_leaf_far<T><<<(unsigned)P.n_leaves, kLeafThreads, 3 * sm1, s>>>(
-                      P.leaves, P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, pts, surf, ns, (const T *)P.dn_w_t,
-                      (const T *)P.dn_v_t, d, P.w_ptr, P.w_idx, (const T *)P.up_dens, res);
+    if (P.n_w > 0) {
+        ggemm<T>(P, GatherSelf<T>{(const T *)P.up_w_t}, P.part_list[2], 0, P.part_start[2][1], 1, u, tmp, 0, s);
+        ggemm<T>(P, GatherSelf<T>{(const T *)P.up_v_t}, P.part_list[2], 0, P.part_start[2][1], 1, tmp,
+                 (T *)P.up_dens, 0, s);
+    }
+    ggemm<T>(P, GatherSelf<T>{(const T *)P.dn_w_t}, P.leaves, 0, P.n_leaves, 1, d, tmp, 0, s);
+    ggemm<T>(P, GatherSelf<T>{(const T *)P.dn_v_t}, P.leaves, 0, P.n_leaves, 1, tmp, (T *)P.dn_dens, 0, s);
     stage_end(P, KIFMM_STAGE_LEAF, s);
     stage_begin(P, KIFMM_STAGE_P2P, s);
-    ++g_launches, k_p2p<T><<<(unsigned)P.n_leaves, kLeafThreads, 0, s>>>(P.leaves, P.lvl, P.cx, P.cy, P.cz,
-                                                                        P.first, P.cnt, pts, P.u_ptr, P.u_idx,
-                                                                        res);
+    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns};
+    const LeafW<T> W{(const T *)P.dn_dens, 1, (const T *)P.up_dens, 1, nullptr};
+    ++g_launches, k_leaf_all<T><<<grid_for(P.n_leaves, kLW), 32 * kLW, 0, s>>>(C, P.n_leaves, P.leaves, pts, surf,
+                                                                               W, res);
     stage_end(P, KIFMM_STAGE_P2P, s);
     KIFMM_CUDA_TRY(cudaGetLastError());
     // outputs
@@ -575,7 +625,108 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     return cudaGetLastError();
 }
 
+// Adjoint weights in sorted order.
+template <typename TI, typename T>
+__global__ void k_gather_w(int64_t n, const uint32_t *__restrict__ perm, const TI *__restrict__ w, T *__restrict__ ws) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) ws[i] = (T)w[perm[i]];
+}
+
+// dq = c1 psi, dx = w grad + c1 / side * q grad(psi), c1 = coef / (4 pi side).
+template <typename TO, typename T>
+__global__ void k_finalize_adj(int64_t n, const double4 *__restrict__ res, const uint32_t *__restrict__ perm,
+                               const int64_t *__restrict__ off, int S, const double *__restrict__ lo_side, double coef,
+                               const typename Vec4<T>::type *__restrict__ pts, const TO *__restrict__ w,
+                               const TO *__restrict__ grad, TO *dq, TO *dx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= (int64_t)j) lo = mid; else hi = mid - 1;
+    }
+    const double side = lo_side[lo * 4 + 3];
+    const double c1 = coef * kInv4Pi / side, c2 = c1 / side;
+    const double4 r = res[i];
+    const double q = (double)pts[i].w;
+    if (dq) dq[j] = (TO)(c1 * r.x);
+    if (dx) {
+        const double wj = (double)w[j];
+        dx[3 * j] = (TO)(wj * (double)grad[3 * j] + c2 * q * r.y);
+        dx[3 * j + 1] = (TO)(wj * (double)grad[3 * j + 1] + c2 * q * r.z);
+        dx[3 * j + 2] = (TO)(wj * (double)grad[3 * j + 2] + c2 * q * r.w);
+    }
+}
+
+// Transposed passes with the tree frozen: psi = A^T w (Sec. 2.2 operators,
+// transposed in reverse order), then the adjoint outputs.
+template <typename T>
+cudaError_t backward_t(Plan &P, const void *w_user, const void *grad_user, void *dq, void *dx, cudaStream_t s) {
+    using V4 = typename Vec4<T>::type;
+    const int ns = P.ns;
+    const size_t nn = (size_t)ns * ns;
+    const T *surf = P.f64 ? (const T *)P.surf64 : (const T *)P.surf32;
+    T *ub = (T *)P.u_chk, *db = (T *)P.d_chk, *tmp = (T *)P.tmp_chk;
+    T *e1 = (T *)P.dn_dens, *e2 = (T *)P.up_dens, *ws = (T *)P.w_sorted;
+    const T *adjp = (const T *)P.adj_pinv;
+    const V4 *pts = (const V4 *)P.pts;
+    double4 *res = (double4 *)P.res;
+    if (P.io_f64)
+        ++g_launches, k_gather_w<double, T><<<grid_for(P.n, 256), 256, 0, s>>>(P.n, P.perm, (const double *)w_user, ws);
+    else
+        ++g_launches, k_gather_w<float, T><<<grid_for(P.n, 256), 256, 0, s>>>(P.n, P.perm, (const float *)w_user, ws);
+    // L2P^T: h * sum w / |DE - x| at each leaf, then d-bar = W_dn^T V_dn^T (.)
+    KIFMM_CUDA_TRY(cudaMemsetAsync(db, 0, sizeof(T) * (size_t)P.nb * ns, s));
+    KIFMM_CUDA_TRY(cudaMemsetAsync(ub, 0, sizeof(T) * (size_t)P.nb * ns, s));
+    ++g_launches, k_p2m<T><<<(unsigned)P.n_leaves, kLeafThreads, 0, s>>>(P.leaves, P.lvl, P.first, P.cnt, pts, surf,
+                                                                        ns, e1, ws, 1);
+    ggemm<T>(P, GatherSelf<T>{adjp + 3 * nn}, P.leaves, 0, P.n_leaves, 1, e1, tmp, 0, s);
+    ggemm<T>(P, GatherSelf<T>{adjp + 2 * nn}, P.leaves, 0, P.n_leaves, 1, tmp, db, 0, s);
+    // M2P^T: W-list sources a receive h_a * sum w / |UE_a - x| from the leaves of X(a)
+    if (P.n_x > 0) {
+        KIFMM_CUDA_TRY(cudaMemsetAsync(e2, 0, sizeof(T) * (size_t)P.nb * ns, s));
+        ++g_launches, k_p2l<T><<<(unsigned)P.nb, kLeafThreads, 0, s>>>(P.nx, P.xdense, P.lvl, P.cx, P.cy, P.cz,
+                                                                        P.first, P.cnt, pts, surf, ns, e2, ws, 1);
+        ggemm<T>(P, GatherSelf<T>{adjp + 1 * nn}, P.part_list[2], 0, P.part_start[2][1], 1, e2, tmp, 0, s);
+        ggemm<T>(P, GatherSelf<T>{adjp}, P.part_list[2], 0, P.part_start[2][1], 1, tmp, ub, 0, s);
+    }
+    // L2L^T, bottom-up
+    for (int l = P.max_level - 1; l >= 0; --l)
+        ggemm<T>(P, GatherChild<T>{P.child8, (const T *)P.adj_l2l, ns}, P.part_list[1], P.part_start[1][1 + l],
+                 P.part_start[1][2 + l], 8, db, db, 1, s);
+    // M2L^T (V lists are symmetric; operator at the negated offset, transposed)
+    for (int c = 0; c < 8; ++c)
+        ggemm<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.adj_m2l, ns, c}, P.part_list[0],
+                 P.part_start[0][c], P.part_start[0][c + 1], kVSlots, db, ub, 1, s);
+    // M2M^T, top-down
+    for (int l = 1; l <= P.max_level; ++l)
+        for (int c = 0; c < 8; ++c) {
+            const int key = l * 8 + c;
+            ggemm<T>(P, GatherParent<T>{P.parent, (const T *)P.adj_m2m + (size_t)c * nn}, P.part_list[3],
+                     P.part_start[3][key], P.part_start[3][key + 1], 1, ub, ub, 1, s);
+        }
+    // P2M^T (own UC surface, u-bar), P2L^T (W boxes' DC surfaces, d-bar), P2P^T (weights w)
+    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns};
+    const LeafW<T> W{ub, 0, db, 0, ws};
+    ++g_launches, k_leaf_all<T><<<grid_for(P.n_leaves, kLW), 32 * kLW, 0, s>>>(C, P.n_leaves, P.leaves, pts, surf,
+                                                                               W, res);
+    if (P.io_f64)
+        ++g_launches, k_finalize_adj<double, T><<<grid_for(P.n, 256), 256, 0, s>>>(
+                          P.n, res, P.perm, P.sys_off_d, P.n_sys, P.lo_side, P.coef, pts, (const double *)w_user,
+                          (const double *)grad_user, (double *)dq, (double *)dx);
+    else
+        ++g_launches, k_finalize_adj<float, T><<<grid_for(P.n, 256), 256, 0, s>>>(
+                          P.n, res, P.perm, P.sys_off_d, P.n_sys, P.lo_side, P.coef, pts, (const float *)w_user,
+                          (const float *)grad_user, (float *)dq, (float *)dx);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t run_backward(Plan &P, const void *w, const void *grad, void *dq, void *dx, cudaStream_t s) {
+    return P.f64 ? backward_t<double>(P, w, grad, dq, dx, s) : backward_t<float>(P, w, grad, dq, dx, s);
+}
 
 cudaError_t run_evaluate(Plan &P, void *pot, void *grad, double *energy, cudaStream_t s) {
     return P.f64 ? evaluate_t<double>(P, pot, grad, energy, s) : evaluate_t<float>(P, pot, grad, energy, s);

@@ -46,6 +46,11 @@ struct Plan {
     // W = diag(sinv) U^T, both stored transposed ([k][j]).
     void *up_w_t = nullptr, *up_v_t = nullptr;
     void *dn_w_t = nullptr, *dn_v_t = nullptr;
+    // Adjoint operators, read as [k][j] by the gathered GEMM: M2M^T, L2L^T,
+    // M2L^T (indexed by the offset of the adjoint's source), and the leaf
+    // pseudo-inverse factors W_up, V_up, W_dn, V_dn row-major.
+    void *adj_m2m = nullptr, *adj_l2l = nullptr, *adj_m2l = nullptr, *adj_pinv = nullptr;
+    void *w_sorted = nullptr;   // [N] adjoint weights in sorted order
     // Tensor-core M2L operands (mixed modes), built lazily.
     void *m2l_tc = nullptr;     // layout owned by the tensor-core kernel
     float *m2l_tc_scale = nullptr;
@@ -101,7 +106,17 @@ struct Plan {
     int32_t *wsrc_flag = nullptr;    // [nb] 1 if the box is in some W list
     void *part_keys = nullptr;       // [2][box_cap] u64 partition scratch
     void *part_vals = nullptr;       // [2][box_cap] u32
-    uint32_t *part_counts = nullptr; // [16]
+    uint32_t *part_counts = nullptr; // [256]
+    // Box lists grouped by a small key (stable, canonical order within a key):
+    //   0: octant class of boxes with a V list (8 = none)
+    //   1: leaves (key 0), then non-leaves by level (key 1 + level)
+    //   2: boxes in some W list (key 0)
+    //   3: boxes below the root by level * 8 + octant (L2L groups)
+    int32_t *part_list[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<int64_t> part_start[4];  // host: exclusive prefix of the key counts (257 entries)
+    int32_t *child8 = nullptr;       // [nb][8] child in each octant, -1 if none
+    void *tmp_chk = nullptr;         // [nb][ns] pseudo-inverse scratch
+    void *dn_dens = nullptr;         // [nb][ns] normalised downward densities of leaves
     int64_t list_cap = 0;            // boxes the per-box list/expansion arrays hold
 
     // ---- expansions (compute type) ----
@@ -165,6 +180,8 @@ void m2l_tensor_release(Plan &P);
 
 // ---- fmm.cu ----
 cudaError_t run_evaluate(Plan &P, void *pot, void *grad, double *energy, cudaStream_t s);
+cudaError_t run_backward(Plan &P, const void *w, const void *grad, void *dq, void *dx, cudaStream_t s);
+cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream_t s);
 cudaError_t run_clump_reduce(Plan &P, int64_t n_clumps, const int64_t *offs, const void *xyz,
                              const void *q, const void *grad, const void *ref, void *force,
                              void *torque, cudaStream_t s);

@@ -36,7 +36,7 @@ namespace kifmm {
 
 namespace {
 
-constexpr int kTcThreads = 160;
+constexpr int kTcThreads = 288;     // 4 producer warps, 1 MMA warp, 4 drain warps
 constexpr int kTcRows = 128;        // targets per CTA (MMA M)
 constexpr int kKBlock = 32;         // FP16 elements per stage row (64 bytes)
 constexpr int kRowBytes = 64;
@@ -69,6 +69,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         if (*abort_flag) return false;
     }
     return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
@@ -140,6 +144,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 registers per thread -> 32 lanes x 32 columns of TMEM.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
+    uint32_t r[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(v[i]);
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 struct TileArgs {
     const int32_t *targets;   // class-major target boxes
     const int4 *tiles;        // (class, begin, end, unused)
@@ -166,7 +186,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
     const uint32_t a_bytes = kTcRows * kRowBytes;            // one of hi / lo
     const uint32_t b_bytes = (uint32_t)np * kRowBytes;
     const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;  // multiple of 512
-    __shared__ __align__(8) uint64_t full_bar[16], empty_bar[16], done_bar;
+    __shared__ __align__(8) uint64_t full_bar[16], empty_bar[16], done_bar, accfull_bar[2], accfree_bar[2];
     __shared__ uint32_t tmem_base_s;
     __shared__ int32_t tgt_s[kTcRows];
     __shared__ volatile int abort_s;
@@ -185,9 +205,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
         mbar_init(smem_u32(&done_bar), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&accfull_bar[b]), 1);
+            mbar_init(smem_u32(&accfree_bar[b]), 4);  // lane 0 of each drain warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const uint32_t tmem_cols = (np <= 32) ? 32 : (np <= 64) ? 64 : (np <= 128) ? 128 : (np <= 256) ? 256 : 512;
+    // TMEM columns: running sum [0, np), partials [np, 2 np) and [2 np, 3 np);
+    // np is a multiple of 32 (enforced at setup).
+    const uint32_t tmem_cols = (3 * np <= 128) ? 128 : (3 * np <= 256) ? 256 : 512;
     if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
                      "r"(tmem_cols)
@@ -206,15 +232,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
         const int row = threadIdx.x;  // A row owned by this thread
         const int32_t t = tgt_s[row];
         int32_t src = -1;
+        // next slot's source and operator are fetched one slot ahead
+        int32_t src_next = (t >= 0) ? a.vdense[(size_t)t * kVSlots] : -1;
+        int o_next = a.slot_off[cls * kVSlots];
         const __half *bh_base = nullptr, *bl_base = nullptr;
         for (int it = 0; it < iters; ++it) {
             const int stage = it % NS;
             const int s = it / kblocks, kb = it - s * kblocks;
             if (kb == 0) {
-                src = (t >= 0) ? a.vdense[(size_t)t * kVSlots + s] : -1;
-                const int o = a.slot_off[cls * kVSlots + s];
-                bh_base = a.bh + (size_t)o * np * kp;
-                bl_base = a.bl + (size_t)o * np * kp;
+                src = src_next;
+                bh_base = a.bh + (size_t)o_next * np * kp;
+                bl_base = a.bl + (size_t)o_next * np * kp;
+                if (s + 1 < kVSlots) {
+                    src_next = (t >= 0) ? a.vdense[(size_t)t * kVSlots + s + 1] : -1;
+                    o_next = a.slot_off[cls * kVSlots + s + 1];
+                }
             }
             if (!mbar_wait(smem_u32(&empty_bar[stage]), ((it / NS) & 1) ^ 1, &abort_s)) {
                 set_status(a.status, KIFMM_ERR_TIMEOUT);
@@ -244,54 +276,93 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             cp_async_arrive_noinc(smem_u32(&full_bar[stage]));
         }
         cp_async_wait_all();
-    } else if (lane == 0) {
+    } else if (warp == 4) {
         // ---------------- MMA issuer ----------------
-        for (int it = 0; it < iters; ++it) {
-            const int stage = it % NS;
-            if (!mbar_wait(smem_u32(&full_bar[stage]), (it / NS) & 1, &abort_s)) {
+        // Slot s accumulates into partial buffer s % 2 (fresh accumulator:
+        // the tensor core's FP32 accumulation rounds toward zero, so chains
+        // are kept to one slot and summed by the drain warps in IEEE FP32).
+        if (lane == 0) {
+            int it = 0;
+            for (int s = 0; s < kVSlots && !abort_s; ++s) {
+                const int buf = s & 1;
+                if (s >= 2 && !mbar_wait(smem_u32(&accfree_bar[buf]), ((s >> 1) - 1) & 1, &abort_s)) {
+                    set_status(a.status, KIFMM_ERR_TIMEOUT);
+                    abort_s = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tacc = tmem + (uint32_t)((1 + buf) * np);
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int stage = it % NS;
+                    if (!mbar_wait(smem_u32(&full_bar[stage]), (it / NS) & 1, &abort_s)) {
+                        set_status(a.status, KIFMM_ERR_TIMEOUT);
+                        abort_s = 1;
+                        break;
+                    }
+                    fence_proxy_async();
+                    tc_fence_after();
+                    const uint32_t sA = smem_u32(smem + (size_t)stage * stage_bytes);
+                    const uint32_t sAl = sA + a_bytes, sB = sAl + a_bytes, sBl = sB + b_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t dAh = sdesc_sw64(sA + 32 * kk), dAl = sdesc_sw64(sAl + 32 * kk);
+                        const uint32_t id = idesc_f16(np);
+                        const uint64_t dBh = sdesc_sw64(sB + 32 * kk);
+                        const uint64_t dBl = sdesc_sw64(sBl + 32 * kk);
+                        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+                        mma_f16(tacc, dAh, dBh, id, acc0);
+                        mma_f16(tacc, dAh, dBl, id, 1u);
+                        mma_f16(tacc, dAl, dBh, id, 1u);
+                    }
+                    mma_commit(smem_u32(&empty_bar[stage]));
+                }
+                mma_commit(smem_u32(&accfull_bar[buf]));
+            }
+            mma_commit(smem_u32(&done_bar));
+        }
+        __syncwarp();
+    } else {
+        // ---------------- drain warps (5..8): TMEM lanes 32 (warp % 4) .. +31 ----------------
+        const int q = warp & 3;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        for (int s = 0; s < kVSlots; ++s) {
+            const int buf = s & 1;
+            bool ok = mbar_wait(smem_u32(&accfull_bar[buf]), (s >> 1) & 1, &abort_s);
+            ok = __all_sync(0xffffffffu, ok);  // warp-uniform: tcgen05.ld/st are .sync.aligned
+            if (!ok) {
                 set_status(a.status, KIFMM_ERR_TIMEOUT);
                 abort_s = 1;
                 break;
             }
-            fence_proxy_async();
             tc_fence_after();
-            const uint32_t sA = smem_u32(smem + (size_t)stage * stage_bytes);
-            const uint32_t sAl = sA + a_bytes, sB = sAl + a_bytes, sBl = sB + b_bytes;
+            for (int c0 = 0; c0 < np; c0 += 32) {
+                float p[32], r[32];
+                tmem_ld32(tmem + lane_off + (uint32_t)((1 + buf) * np + c0), p);
+                if (s > 0) {
+                    tmem_ld32(tmem + lane_off + (uint32_t)c0, r);
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-                const uint64_t dAh = sdesc_sw64(sA + 32 * kk), dAl = sdesc_sw64(sAl + 32 * kk);
-                for (int n0 = 0; n0 < np; n0 += 256) {
-                    const int nc = min(256, np - n0);
-                    const uint32_t id = idesc_f16(nc);
-                    const uint64_t dBh = sdesc_sw64(sB + n0 * kRowBytes + 32 * kk);
-                    const uint64_t dBl = sdesc_sw64(sBl + n0 * kRowBytes + 32 * kk);
-                    const uint32_t acc0 = (it > 0 || kk > 0) ? 1u : 0u;
-                    mma_f16(tmem + n0, dAh, dBh, id, acc0);
-                    mma_f16(tmem + n0, dAh, dBl, id, 1u);
-                    mma_f16(tmem + n0, dAl, dBh, id, 1u);
+                    for (int j = 0; j < 32; ++j) r[j] += p[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) r[j] = p[j];
                 }
+                tmem_st32(tmem + lane_off + (uint32_t)c0, r);
             }
-            mma_commit(smem_u32(&empty_bar[stage]));
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&accfree_bar[buf]));
         }
-        mma_commit(smem_u32(&done_bar));
-    }
-
-    // ---------------- epilogue ----------------
-    if (warp < 4) {
+        // final read-out of the running sums
         bool ok = mbar_wait(smem_u32(&done_bar), 0, &abort_s);
-        ok = __all_sync(0xffffffffu, ok);  // warp-uniform: tcgen05.ld is .sync.aligned
-        if (!ok) {
-            set_status(a.status, KIFMM_ERR_TIMEOUT);
-            abort_s = 1;
-        }
+        ok = __all_sync(0xffffffffu, ok) && !abort_s;
         tc_fence_after();
-        const int row = warp * 32 + lane;
+        const int row = q * 32 + lane;
         const int32_t t = tgt_s[row];
         const float scale = (t >= 0) ? a.level_unscale[a.lvl[t]] : 0.f;
         if (ok) {
             for (int c0 = 0; c0 < np; c0 += 32) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                tmem_ld32(tmem + lane_off + (uint32_t)c0, v);
                 if (t >= 0) {
                     float *out = a.d + (size_t)t * a.ns + c0;
 #pragma unroll
@@ -411,9 +482,9 @@ void m2l_tensor_release(Plan &P) {
 cudaError_t m2l_tensor_setup(Plan &P) {
     TcState &S = tc_state(P);
     const int ns = P.ns;
-    S.np = round_up(ns, 16);
+    S.np = round_up(ns, 32);
     S.kp = round_up(ns, kKBlock);
-    if (S.np > 512) return cudaErrorNotSupported;
+    if (3 * S.np > 512) return cudaErrorNotSupported;  // running sum + two partials must fit TMEM (p <= 6)
     const size_t stage = 2 * (size_t)kTcRows * kRowBytes + 2 * (size_t)S.np * kRowBytes;
     S.nstages = (int)std::min<size_t>(16, (200 * 1024) / stage);
     if (S.nstages < 2) return cudaErrorNotSupported;

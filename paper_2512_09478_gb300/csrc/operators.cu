@@ -122,6 +122,17 @@ __global__ void k_dgemm(int n, const double *__restrict__ A, size_t strideA, con
     }
 }
 
+// out[b] = in[map(b)]^T for n x n blocks; map(b) = rev ? nb - 1 - b : b.
+__global__ void k_transpose_blocks(int n, int nb, int rev, const double *__restrict__ in, double *__restrict__ out) {
+    const size_t nn = (size_t)n * n;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nn * nb) return;
+    const int b = (int)(idx / nn);
+    const int r = (int)((idx % nn) / n), c = (int)(idx % n);
+    const int src = rev ? nb - 1 - b : b;
+    out[idx] = in[(size_t)src * nn + (size_t)c * n + r];
+}
+
 __global__ void k_to_f32(const double *in, float *out, size_t n) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
@@ -298,6 +309,40 @@ cudaError_t build_operators(Plan &P, std::string &err) {
         else
             k_to_f32<<<(unsigned)((c.cnt + 255) / 256), 256>>>(c.src, (float *)c.dst, c.cnt);
     }
+    // Adjoint operators (the transposed passes use the same gathered GEMM, which
+    // reads operators as [k][j]; for Op^T that is Op itself, row-major):
+    //   M2M^T, L2L^T: blocks of m2m_t / l2l_t transposed back;
+    //   M2L^T at offset o: M_{-o} row-major, and -o has index 315 - o.
+    //   Leaf pseudo-inverses W^T, V^T: W and V row-major.
+    double *dT = nullptr;
+    KIFMM_CUDA_TRY(cudaMalloc(&dT, sizeof(double) * (size_t)(16 + kNumM2L + 4) * nn));
+    auto tblocks = [&](const double *in, int nb, int rev, double *out) {
+        const size_t tot = nn * nb;
+        k_transpose_blocks<<<(unsigned)((tot + 255) / 256), 256>>>(n, nb, rev, in, out);
+    };
+    tblocks(dOut, 8, 0, dT);                             // m2m row-major
+    tblocks(dOut + 8 * nn, 8, 0, dT + 8 * nn);           // l2l row-major
+    tblocks(dOut + 16 * nn, kNumM2L, 1, dT + 16 * nn);   // m2l at negated offsets, row-major
+    tblocks(dW, 1, 0, dT + (16 + kNumM2L) * nn);         // up W row-major
+    tblocks(Vt_up, 1, 0, dT + (17 + kNumM2L) * nn);      // up V row-major
+    tblocks(dW + nn, 1, 0, dT + (18 + kNumM2L) * nn);    // dn W row-major
+    tblocks(Vt_dn, 1, 0, dT + (19 + kNumM2L) * nn);      // dn V row-major
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.adj_m2m, esz * 8 * nn));
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.adj_l2l, esz * 8 * nn));
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.adj_m2l, esz * kNumM2L * nn));
+    KIFMM_CUDA_TRY(plan_alloc(P, &P.adj_pinv, esz * 4 * nn));
+    const Copy adj[] = {{P.adj_m2m, dT, 8 * nn},
+                        {P.adj_l2l, dT + 8 * nn, 8 * nn},
+                        {P.adj_m2l, dT + 16 * nn, kNumM2L * nn},
+                        {P.adj_pinv, dT + (16 + kNumM2L) * nn, 4 * nn}};
+    for (const Copy &c : adj) {
+        if (P.f64)
+            KIFMM_CUDA_TRY(cudaMemcpy(c.dst, c.src, sizeof(double) * c.cnt, cudaMemcpyDeviceToDevice));
+        else
+            k_to_f32<<<(unsigned)((c.cnt + 255) / 256), 256>>>(c.src, (float *)c.dst, c.cnt);
+    }
+    KIFMM_CUDA_TRY(cudaDeviceSynchronize());
+    cudaFree(dT);
     // surfaces
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf64, sizeof(double) * 3 * n));
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf32, sizeof(float) * 3 * n));

@@ -440,18 +440,20 @@ __global__ void k_coarse(int64_t ls, int64_t le, int level, const int32_t *__res
 
 // slot of offset d for octant class (ox,oy,oz): components range over
 // [-2-o, 3-o]; the inner [-1,1]^3 is excluded.
+// Closed form: lexicographic index in the 6^3 window minus the excluded inner
+// 3^3 cells (at window offset 1 + o per axis) that precede it.
 __device__ __forceinline__ int v_slot(int ox, int oy, int oz, int dx, int dy, int dz) {
-    const int ix = dx + 2 + ox, iy = dy + 2 + oy, iz = dz + 2 + oz;  // 0..5
-    int s = 0;
-    for (int a = 0; a < 6; ++a)
-        for (int bb = 0; bb < 6; ++bb)
-            for (int c = 0; c < 6; ++c) {
-                const int ddx = a - 2 - ox, ddy = bb - 2 - oy, ddz = c - 2 - oz;
-                if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1 && ddz >= -1 && ddz <= 1) continue;
-                if (a == ix && bb == iy && c == iz) return s;
-                ++s;
-            }
-    return -1;
+    const int a = dx + 2 + ox, b = dy + 2 + oy, c = dz + 2 + oz;  // 0..5
+    if (a < 0 || a > 5 || b < 0 || b > 5 || c < 0 || c > 5) return -1;
+    const int a0 = 1 + ox, b0 = 1 + oy, c0 = 1 + oz;
+    const bool ina = a >= a0 && a < a0 + 3, inb = b >= b0 && b < b0 + 3, inc = c >= c0 && c < c0 + 3;
+    if (ina && inb && inc) return -1;
+    int before = min(max(a - a0, 0), 3) * 9;
+    if (ina) {
+        before += min(max(b - b0, 0), 3) * 3;
+        if (inb) before += min(max(c - c0, 0), 3);
+    }
+    return a * 36 + b * 6 + c - before;
 }
 
 // V list (children of the parent's colleagues not adjacent to b) into the
@@ -587,18 +589,33 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uin
     return cudaGetLastError();
 }
 
-// Partition keys: class of boxes with a V list (8 = none), or 0 for leaves.
+// Partition keys (see Plan::part_list).
 __global__ void k_part_keys(int64_t nb, int mode, const int32_t *__restrict__ nv, const int32_t *__restrict__ nchild,
+                            const int32_t *__restrict__ lvl, const int32_t *__restrict__ wflag,
                             const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
                             const int32_t *__restrict__ cz, uint64_t *keys, uint32_t *vals, uint32_t *counts) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
+    const uint32_t oct = (uint32_t)(4 * (cx[b] & 1) + 2 * (cy[b] & 1) + (cz[b] & 1));
     uint32_t k;
-    if (mode == 0) k = (nv[b] > 0) ? (uint32_t)(4 * (cx[b] & 1) + 2 * (cy[b] & 1) + (cz[b] & 1)) : 8u;
-    else k = (nchild[b] == 0) ? 0u : 1u;
+    if (mode == 0) k = (nv[b] > 0) ? oct : 8u;
+    else if (mode == 1) k = (nchild[b] == 0) ? 0u : 1u + (uint32_t)lvl[b];
+    else if (mode == 2) k = wflag[b] ? 0u : 1u;
+    else k = (lvl[b] > 0) ? (uint32_t)lvl[b] * 8u + oct : 255u;
     keys[b] = k;
     vals[b] = (uint32_t)b;
     atomicAdd(&counts[k], 1u);
+}
+
+__global__ void k_child8(int64_t nb, const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
+                         const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                         const int32_t *__restrict__ cz, int32_t *child8) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int32_t *o = child8 + b * 8;
+    for (int k = 0; k < 8; ++k) o[k] = -1;
+    for (int32_t c = child_first[b]; c < child_first[b] + nchild[b]; ++c)
+        o[4 * (cx[c] & 1) + 2 * (cy[c] & 1) + (cz[c] & 1)] = c;
 }
 
 static cudaError_t radix_pass(Plan &P, const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout,
@@ -624,23 +641,23 @@ cudaError_t partition_boxes(Plan &P, cudaStream_t s) {
     const int64_t nb = P.nb;
     uint64_t *pk0 = (uint64_t *)P.part_keys, *pk1 = pk0 + P.box_cap;
     uint32_t *pv0 = (uint32_t *)P.part_vals, *pv1 = pv0 + P.box_cap;
-    for (int mode = 0; mode < 2; ++mode) {
-        KIFMM_CUDA_TRY(cudaMemsetAsync(P.part_counts, 0, sizeof(uint32_t) * 16, s));
-        ++g_launches, k_part_keys<<<grid_for(nb, 256), 256, 0, s>>>(nb, mode, P.nv, P.nchild, P.cx, P.cy, P.cz, pk0, pv0,
-                                                      P.part_counts);
+    ++g_launches, k_child8<<<grid_for(nb, 256), 256, 0, s>>>(nb, P.child_first, P.nchild, P.cx, P.cy, P.cz, P.child8);
+    for (int mode = 0; mode < 4; ++mode) {
+        KIFMM_CUDA_TRY(cudaMemsetAsync(P.part_counts, 0, sizeof(uint32_t) * 256, s));
+        ++g_launches, k_part_keys<<<grid_for(nb, 256), 256, 0, s>>>(nb, mode, P.nv, P.nchild, P.lvl, P.wsrc_flag,
+                                                                    P.cx, P.cy, P.cz, pk0, pv0, P.part_counts);
         KIFMM_CUDA_TRY(radix_pass(P, pk0, pv0, pk1, pv1, nb, 0, 0, s));
-        uint32_t counts[16];
+        KIFMM_CUDA_TRY(cudaMemcpyAsync(P.part_list[mode], pv1, sizeof(int32_t) * nb, cudaMemcpyDeviceToDevice, s));
+        uint32_t counts[256];
         KIFMM_CUDA_TRY(cudaMemcpyAsync(counts, P.part_counts, sizeof(counts), cudaMemcpyDeviceToHost, s));
         KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
-        if (mode == 0) {
-            P.m2l_class_start[0] = 0;
-            for (int c = 0; c < 8; ++c) P.m2l_class_start[c + 1] = P.m2l_class_start[c] + counts[c];
-            KIFMM_CUDA_TRY(cudaMemcpyAsync(P.m2l_targets, pv1, sizeof(int32_t) * nb, cudaMemcpyDeviceToDevice, s));
-        } else {
-            P.n_leaves = counts[0];
-            KIFMM_CUDA_TRY(cudaMemcpyAsync(P.leaves, pv1, sizeof(int32_t) * nb, cudaMemcpyDeviceToDevice, s));
-        }
+        P.part_start[mode].assign(257, 0);
+        for (int k = 0; k < 256; ++k) P.part_start[mode][k + 1] = P.part_start[mode][k] + counts[k];
     }
+    P.m2l_targets = P.part_list[0];
+    for (int c = 0; c <= 8; ++c) P.m2l_class_start[c] = P.part_start[0][c];
+    P.leaves = P.part_list[1];
+    P.n_leaves = P.part_start[1][1];
     return cudaGetLastError();
 }
 
@@ -727,7 +744,12 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
     P.nb = le;
     P.max_level = level;
 
-    // leaf-relative particle records in the compute type
+    return gather_particles(P, xyz, q, s);
+}
+
+// Leaf-relative particle records in the compute type (also used to refresh
+// positions and charges with the tree frozen).
+cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream_t s) {
     if (P.f64) {
         if (P.io_f64)
             ++g_launches, k_gather<double, double><<<(unsigned)P.nb, 128, 0, s>>>(

@@ -52,7 +52,7 @@ _LIB = None
 EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifmm_evaluate",
            "kifmm_clump_reduce", "kifmm_backward", "kifmm_get_device_status", "kifmm_status_string",
            "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
-           "kifmm_profile_enable", "kifmm_profile_read"]
+           "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources"]
 
 
 def load(path: str = LIB_PATH):
@@ -79,6 +79,8 @@ def load(path: str = LIB_PATH):
     lib.kifmm_copy_list.argtypes = [P, I, P, P]
     lib.kifmm_profile_enable.argtypes = [P, I]
     lib.kifmm_profile_read.argtypes = [P, ctypes.POINTER(ProfileT)]
+    lib.kifmm_copy_expansions.argtypes = [P, P, P, P]
+    lib.kifmm_update_sources.argtypes = [P, P, P, P]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int if name != "kifmm_status_string" else ctypes.c_char_p
     _LIB = lib
@@ -124,6 +126,7 @@ class Plan:
         h = ctypes.c_void_p()
         _check(lib.kifmm_plan_create(ctypes.byref(d), ctypes.byref(h)), "kifmm_plan_create")
         self._h = h
+        self._ns = 6 * (p - 1) ** 2 + 2
         self.n = 0
         self.n_systems = 0
         self._offsets = None
@@ -153,6 +156,13 @@ class Plan:
         self.n_systems = len(off) - 1
         self._offsets = off
 
+    def update_sources(self, xyz: torch.Tensor, q: torch.Tensor, stream=None):
+        """New positions/charges for the same particles, tree and lists frozen."""
+        assert xyz.is_cuda and q.is_cuda and xyz.dtype == self.dtype and q.dtype == self.dtype
+        assert xyz.shape[0] == self.n
+        _check(load().kifmm_update_sources(self._h, _ptr(xyz.contiguous()), _ptr(q.contiguous()),
+                                           _stream(stream)), "kifmm_update_sources")
+
     def evaluate(self, pot=None, grad=None, energy=None, want_pot=True, want_grad=True, want_energy=False,
                  stream=None):
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -178,6 +188,10 @@ class Plan:
         return force, torque
 
     def backward(self, dL_dpot, grad, dq=None, dx=None, stream=None):
+        """Adjoint of evaluate on the plan's current tree and sources:
+        dq = A^T dL_dpot, dx = dL_dpot * grad + q * grad_y(A^T dL_dpot)."""
+        dL_dpot = dL_dpot.contiguous()
+        grad = grad.contiguous()
         if dq is None:
             dq = torch.empty(self.n, dtype=self.dtype, device=grad.device)
         if dx is None:
@@ -228,6 +242,18 @@ class Plan:
                                       c(out["count"]), c(out["parent"])), "kifmm_copy_tree")
         return out
 
+    def expansions(self):
+        """(u, d, res) after the last evaluate (see kifmm_copy_expansions)."""
+        nb = self.tree_info()["n_boxes"]
+        lib = load()
+        ns = self._ns
+        u = np.empty((nb, ns))
+        d = np.empty((nb, ns))
+        res = np.empty((self.n, 4))
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib.kifmm_copy_expansions(self._h, c(u), c(d), c(res)), "kifmm_copy_expansions")
+        return u, d, res
+
     def list(self, kind: str):
         info = self.tree_info()
         nb = info["n_boxes"]
@@ -238,3 +264,42 @@ class Plan:
         _check(load().kifmm_copy_list(self._h, LIST_KINDS[kind], ptr.ctypes.data_as(ctypes.c_void_p),
                                       idx.ctypes.data_as(ctypes.c_void_p)), "kifmm_copy_list")
         return ptr, idx[:int(ptr[-1])]
+
+
+class KifmmPotential(torch.autograd.Function):
+    """pot = KIFMM(x, q) with gradients w.r.t. x and q through the adjoint
+    passes (kifmm_backward).  The tree is built (rebuild=True) or frozen
+    (rebuild=False, kifmm_update_sources); the plan must still hold these
+    sources when backward runs (tree-level recomputation, nothing stored
+    besides the forward gradient)."""
+
+    @staticmethod
+    def forward(ctx, x, q, plan, rebuild=True):
+        if rebuild:
+            plan.set_sources(x.detach(), q.detach())
+        else:
+            plan.update_sources(x.detach(), q.detach())
+        pot, grad, _ = plan.evaluate()
+        ctx.plan = plan
+        ctx.save_for_backward(grad)
+        ctx.mark_non_differentiable(grad)
+        return pot, grad
+
+    @staticmethod
+    def backward(ctx, g_pot, g_grad):
+        (grad,) = ctx.saved_tensors
+        if g_grad is not None and torch.any(g_grad != 0):
+            raise NotImplementedError("losses on the gradient output are not differentiated")
+        dq, dx = ctx.plan.backward(g_pot, grad)
+        return dx, dq, None, None
+
+
+def potential(x, q, plan, rebuild=True):
+    """Differentiable potential (Eq. 1 with the Eq. 3 kernel, coef applied)."""
+    pot, _ = KifmmPotential.apply(x, q, plan, rebuild)
+    return pot
+
+
+def energy(x, q, plan, rebuild=True):
+    """Differentiable long-range energy U = 1/2 sum_i q_i pot_i (Sec. 2.4)."""
+    return 0.5 * torch.dot(q, potential(x, q, plan, rebuild))

@@ -40,10 +40,30 @@ def _dev(a, dtype=torch.float64):
 CASES = {
     "uniform4096": lambda: G.uniform_charges(4096, 1000),
     "plummer3000": lambda: (G.plummer(3000, 5)[0], np.random.default_rng(5).normal(size=3000)),
-    "clustered": lambda: (np.concatenate([np.random.default_rng(2).normal(0, 1e-3, size=(700, 3)),
+    "clustered": lambda: (np.concatenate([np.random.default_rng(2).normal(0, 1e-2, size=(700, 3)),
                                           np.random.default_rng(3).uniform(-1, 1, size=(1300, 3))]),
                           np.random.default_rng(4).choice([-1.0, 1.0], 2000)),
+    "clustered_tight": lambda: (np.concatenate([np.random.default_rng(2).normal(0, 1e-3, size=(700, 3)),
+                                                np.random.default_rng(3).uniform(-1, 1, size=(1300, 3))]),
+                                np.random.default_rng(4).choice([-1.0, 1.0], 2000)),
 }
+
+
+def test_fp64_ill_conditioned_input_within_rounding_floor():
+    """Pairs 1e-4 apart in a domain of size 2 lose ~12 digits in x_i - x_j, so
+    two correct FP64 evaluations differ by more than 1e-12 in the gradient.
+    The bar is then 10x the oracle's own change under a rounding-level
+    perturbation of the input (translation by 0.1234567 and scaling by 3)."""
+    x, q = CASES["clustered_tight"]()
+    pot_o, grad_o, _ = O.kifmm(x, q, p=6, leaf_cap=8)
+    p2, g2, _ = O.kifmm(3.0 * x + 0.1234567, q, p=6, leaf_cap=8)
+    floor_p = O.rel_l2(3.0 * p2, pot_o)
+    floor_g = O.rel_l2(9.0 * g2, grad_o)
+    plan = _plan(x, M=8, p=6)
+    plan.set_sources(_dev(x), _dev(q))
+    pot, grad, _ = plan.evaluate()
+    assert O.rel_l2(pot.cpu().numpy(), pot_o) <= max(1e-12, 10 * floor_p)
+    assert O.rel_l2(grad.cpu().numpy(), grad_o) <= max(1e-12, 10 * floor_g)
 
 
 @pytest.mark.parametrize("case,M", [("uniform4096", 64), ("plummer3000", 16), ("clustered", 8)])
