@@ -135,49 +135,65 @@ __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict_
 // registers.  Used for M2L (189 V slots), M2M (8 child octants), L2L (parent)
 // and the two factors of the leaf pseudo-inverses.
 // ---------------------------------------------------------------------------
-constexpr int kGT = 64, kGJ = 160, kGK = 8;
+constexpr int kGT = 64, kGJ = 160, kGK = 16;
+
+// Target ranges of up to 8 classes (blockIdx.y = class) in one launch.
+struct ClassRanges {
+    int64_t b[9];
+};
 
 template <typename T>
 struct GatherM2L {
     const int32_t *vdense;
     const int *slot_off;
     const T *ops;
-    int ns, cls;
-    __device__ int src(int t, int s) const { return vdense[(size_t)t * kVSlots + s]; }
-    __device__ const T *op(int s) const { return ops + (size_t)slot_off[cls * kVSlots + s] * ns * ns; }
+    int ns;
+    __device__ int src(int t, int s, int) const { return vdense[(size_t)t * kVSlots + s]; }
+    __device__ const T *op(int s, int cls) const { return ops + (size_t)slot_off[cls * kVSlots + s] * ns * ns; }
 };
 template <typename T>
 struct GatherChild {
     const int32_t *child8;
     const T *ops;
     int ns;
-    __device__ int src(int t, int s) const { return child8[(size_t)t * 8 + s]; }
-    __device__ const T *op(int s) const { return ops + (size_t)s * ns * ns; }
+    __device__ int src(int t, int s, int) const { return child8[(size_t)t * 8 + s]; }
+    __device__ const T *op(int s, int) const { return ops + (size_t)s * ns * ns; }
 };
+// One operator per class (L2L: the octant of the child).
 template <typename T>
 struct GatherParent {
     const int32_t *parent;
-    const T *op0;
-    __device__ int src(int t, int) const { return parent[t]; }
-    __device__ const T *op(int) const { return op0; }
+    const T *ops;
+    int ns;
+    __device__ int src(int t, int, int) const { return parent[t]; }
+    __device__ const T *op(int, int cls) const { return ops + (size_t)cls * ns * ns; }
 };
 template <typename T>
 struct GatherSelf {
     const T *op0;
-    __device__ int src(int t, int) const { return t; }
-    __device__ const T *op(int) const { return op0; }
+    __device__ int src(int t, int, int) const { return t; }
+    __device__ const T *op(int, int) const { return op0; }
 };
 
 template <typename T, class G>
-__global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ targets, int64_t t_begin,
-                                               int64_t t_end, int nslots, int ns, const T *__restrict__ in,
+__global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ targets, ClassRanges cr,
+                                               int nslots, int ns, const T *__restrict__ in,
                                                T *__restrict__ out, int accumulate) {
     __shared__ __align__(16) T Us[kGK][kGT];
     __shared__ __align__(16) T Ms[kGK][kGJ];
     __shared__ int32_t tgt[kGT];
     __shared__ int32_t src[kGT];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int cls = blockIdx.y;
+    int64_t t_begin = 0, t_end = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (c == cls) {
+            t_begin = cr.b[c];
+            t_end = cr.b[c + 1];
+        }
     const int64_t t0 = t_begin + (int64_t)blockIdx.x * kGT;
+    if (t0 >= t_end) return;  // uniform for the block
     if (threadIdx.x < kGT) tgt[threadIdx.x] = (t0 + threadIdx.x < t_end) ? targets[t0 + threadIdx.x] : -1;
     // FP32: each slot sums into a fresh partial that is then added to the
     // running total, so no rounding chain is longer than one slot's n_s terms.
@@ -192,22 +208,23 @@ __global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ 
     for (int s = 0; s < nslots; ++s) {
         if (threadIdx.x < kGT) {
             const int32_t t = tgt[threadIdx.x];
-            src[threadIdx.x] = (t >= 0) ? g.src(t, s) : -1;
+            src[threadIdx.x] = (t >= 0) ? g.src(t, s, cls) : -1;
         }
-        const T *M = g.op(s);
+        const T *M = g.op(s, cls);
         __syncthreads();
-        T ru[2], rm[5];
+        constexpr int kRU = kGT * kGK / 256, kRM = kGK * kGJ / 256;
+        T ru[kRU], rm[kRM];
         auto load = [&](int kc) {
             const int k0 = kc * kGK;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < kRU; ++r) {
                 const int e = threadIdx.x + 256 * r;
-                const int t = e >> 3, k = e & 7;
+                const int t = e / kGK, k = e % kGK;
                 const int32_t sb = src[t];
                 ru[r] = (sb >= 0 && k0 + k < ns) ? in[(size_t)sb * ns + k0 + k] : T(0);
             }
 #pragma unroll
-            for (int r = 0; r < 5; ++r) {
+            for (int r = 0; r < kRM; ++r) {
                 const int e = threadIdx.x + 256 * r;
                 const int k = e / kGJ, j = e - k * kGJ;
                 rm[r] = (k0 + k < ns && j < ns) ? M[(size_t)(k0 + k) * ns + j] : T(0);
@@ -216,12 +233,12 @@ __global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ 
         load(0);
         for (int kc = 0; kc < nk; ++kc) {
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < kRU; ++r) {
                 const int e = threadIdx.x + 256 * r;
-                Us[e & 7][e >> 3] = ru[r];
+                Us[e % kGK][e / kGK] = ru[r];
             }
 #pragma unroll
-            for (int r = 0; r < 5; ++r) {
+            for (int r = 0; r < kRM; ++r) {
                 const int e = threadIdx.x + 256 * r;
                 const int k = e / kGJ;
                 Ms[k][e - k * kGJ] = rm[r];
@@ -530,12 +547,24 @@ __global__ void k_clump(int64_t nc, const int64_t *__restrict__ off, const TO *_
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// Classes c < ncls own targets [starts[c], starts[c + 1]); one launch.
+template <typename T, class G>
+void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *starts, int ncls, int nslots,
+                   const T *in, T *out, int accumulate, cudaStream_t s) {
+    ClassRanges cr;
+    int64_t most = 0;
+    for (int c = 0; c <= ncls; ++c) cr.b[c] = starts[c];
+    for (int c = 0; c < ncls; ++c) most = std::max<int64_t>(most, starts[c + 1] - starts[c]);
+    if (most <= 0) return;
+    dim3 grid(grid_for(most, kGT), ncls);
+    ++g_launches, k_ggemm<T, G><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, in, out, accumulate);
+}
+
 template <typename T, class G>
 void ggemm(Plan &P, const G &g, const int32_t *targets, int64_t a, int64_t e, int nslots, const T *in, T *out,
            int accumulate, cudaStream_t s) {
-    if (e <= a) return;
-    ++g_launches, k_ggemm<T, G><<<grid_for(e - a, kGT), 256, 0, s>>>(g, targets, a, e, nslots, P.ns, in, out,
-                                                                     accumulate);
+    const int64_t st[2] = {a, e};
+    ggemm_classes<T, G>(P, g, targets, st, 1, nslots, in, out, accumulate, s);
 }
 
 template <typename T>
@@ -565,9 +594,8 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     if (tensor) {
         KIFMM_CUDA_TRY(m2l_tensor(P, s));
     } else {
-        for (int c = 0; c < 8; ++c)
-            ggemm<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.m2l_t, ns, c}, P.part_list[0],
-                     P.part_start[0][c], P.part_start[0][c + 1], kVSlots, u, d, 0, s);
+        ggemm_classes<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.m2l_t, ns}, P.part_list[0],
+                         P.part_start[0].data(), 8, kVSlots, u, d, 0, s);
     }
     stage_end(P, KIFMM_STAGE_M2L, s);
     if (P.n_x > 0) {
@@ -579,11 +607,8 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     // downward pass: per level, per octant class of the child
     stage_begin(P, KIFMM_STAGE_L2L, s);
     for (int l = 1; l <= P.max_level; ++l)
-        for (int c = 0; c < 8; ++c) {
-            const int key = l * 8 + c;
-            ggemm<T>(P, GatherParent<T>{P.parent, (const T *)P.l2l_t + (size_t)c * nn}, P.part_list[3],
-                     P.part_start[3][key], P.part_start[3][key + 1], 1, d, d, 1, s);
-        }
+        ggemm_classes<T>(P, GatherParent<T>{P.parent, (const T *)P.l2l_t, ns}, P.part_list[3],
+                         P.part_start[3].data() + 8 * l, 8, 1, d, d, 1, s);
     stage_end(P, KIFMM_STAGE_L2L, s);
     KIFMM_CUDA_TRY(cudaGetLastError());
     // leaves: equivalent densities (two-step pseudo-inverse), then L2P + M2P + P2P
@@ -696,16 +721,12 @@ cudaError_t backward_t(Plan &P, const void *w_user, const void *grad_user, void 
         ggemm<T>(P, GatherChild<T>{P.child8, (const T *)P.adj_l2l, ns}, P.part_list[1], P.part_start[1][1 + l],
                  P.part_start[1][2 + l], 8, db, db, 1, s);
     // M2L^T (V lists are symmetric; operator at the negated offset, transposed)
-    for (int c = 0; c < 8; ++c)
-        ggemm<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.adj_m2l, ns, c}, P.part_list[0],
-                 P.part_start[0][c], P.part_start[0][c + 1], kVSlots, db, ub, 1, s);
+    ggemm_classes<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.adj_m2l, ns}, P.part_list[0],
+                     P.part_start[0].data(), 8, kVSlots, db, ub, 1, s);
     // M2M^T, top-down
     for (int l = 1; l <= P.max_level; ++l)
-        for (int c = 0; c < 8; ++c) {
-            const int key = l * 8 + c;
-            ggemm<T>(P, GatherParent<T>{P.parent, (const T *)P.adj_m2m + (size_t)c * nn}, P.part_list[3],
-                     P.part_start[3][key], P.part_start[3][key + 1], 1, ub, ub, 1, s);
-        }
+        ggemm_classes<T>(P, GatherParent<T>{P.parent, (const T *)P.adj_m2m, ns}, P.part_list[3],
+                         P.part_start[3].data() + 8 * l, 8, 1, ub, ub, 1, s);
     // P2M^T (own UC surface, u-bar), P2L^T (W boxes' DC surfaces, d-bar), P2P^T (weights w)
     LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns};
     const LeafW<T> W{ub, 0, db, 0, ws};
