@@ -164,6 +164,31 @@ kifmm_status kifmm_clump_reduce(kifmm_plan *plan, int64_t n_clumps, const int64_
 kifmm_status kifmm_backward(kifmm_plan *plan, const void *dL_dpot, const void *grad, void *dq,
                             void *dx, kifmm_stream_t stream);
 
+/*
+ * Long-range energy U = 1/2 sum_i q_i pot_i without allocating anything.
+ * The paper has no counterpart: this is a convenience for callers that cannot
+ * allocate device memory where they need the energy — a DEM step recorded into
+ * a CUDA graph (cudaMalloc cannot be captured), an application whose device
+ * memory belongs to its own pool, a time-critical loop that must not enter an
+ * allocator.  It runs the same deterministic chunked reduction as the energy
+ * output of kifmm_evaluate, with its partial sums in a fixed array of 16384
+ * doubles (128 KiB) that lives in the library's device image; every GPU that
+ * loads the library keeps that array until the process exits.
+ * n: number of particles, at most 67,108,864 (16384 chunks of 4096); larger n
+ *   returns KIFMM_ERR_CAPACITY without launching anything.
+ * dtype: kifmm_dtype of q and pot.  q, pot (device, [n]): charges and the
+ *   potential returned by kifmm_evaluate.  energy (device, one double): output.
+ * No cudaMalloc/cudaFree or other allocation happens.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  All calls
+ * on a device share the array and it keeps the last call's partials: every
+ * partial a call reads is written earlier in the same call, so nothing needs
+ * clearing, but calls that overlap on the GPU (different streams, no ordering)
+ * race on it.
+ */
+kifmm_status kifmm_energy_noalloc(int64_t n, int dtype, const void *q, const void *pot, double *energy,
+                                  kifmm_stream_t stream);
+
 /* Synchronise the last stream used by the plan and read (then clear) the
  * device status word.  code (host) receives a kifmm_status value. */
 kifmm_status kifmm_get_device_status(kifmm_plan *plan, int *code);

@@ -266,6 +266,25 @@ class Plan:
         return ptr, idx[:int(ptr[-1])]
 
 
+def energy_noalloc(q: torch.Tensor, pot: torch.Tensor, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """U = 1/2 sum q pot through kifmm_energy_noalloc (the library allocates
+    nothing; ``out`` is a one-element float64 device tensor, created here if
+    not given)."""
+    lib = load()
+    if not hasattr(lib, "_noalloc_typed"):
+        lib.kifmm_energy_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p]
+        lib.kifmm_energy_noalloc.restype = ctypes.c_int
+        lib._noalloc_typed = True
+    assert q.is_cuda and pot.is_cuda and q.dtype == pot.dtype and q.numel() == pot.numel()
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=q.device)
+    dt = 1 if q.dtype == torch.float64 else 0
+    _check(lib.kifmm_energy_noalloc(q.numel(), dt, _ptr(q.contiguous()), _ptr(pot.contiguous()), _ptr(out),
+                                    _stream(stream)), "kifmm_energy_noalloc")
+    return out
+
+
 class KifmmPotential(torch.autograd.Function):
     """pot = KIFMM(x, q) with gradients w.r.t. x and q through the adjoint
     passes (kifmm_backward).  The tree is built (rebuild=True) or frozen
