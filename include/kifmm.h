@@ -77,6 +77,12 @@ typedef struct {
                             pseudo-inverse; 0 selects 1e-12.  It must not lie
                             within a factor 1.1 of any sigma_i / sigma_max.    */
     int autotune;        /* 1: time candidate tile shapes at plan creation     */
+    int direct_max;      /* a W/X interaction whose finer box (the W member,
+                            or the owner of the X list) is a leaf holding at
+                            most this many points is summed directly, as a
+                            U-list (P2P) entry: the original KIFMM's cost rule
+                            for the adaptive lists (Sec. 2.2).  0 selects n_s;
+                            a negative value keeps every W/X interaction.      */
 } kifmm_plan_desc;
 
 typedef struct kifmm_plan kifmm_plan;

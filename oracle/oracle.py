@@ -29,7 +29,9 @@ Sec. 2.2) and fixed as follows:
   quantisation, Morton order x-highest; stable sort; split while
   count > M and level < max_depth; only non-empty children exist; canonical
   node order (level, Morton prefix).
-* Lists: U, V, W, X of the adaptive KIFMM, classified from their definitions.
+* Lists: U, V, W, X of the adaptive KIFMM, classified from their definitions;
+  a W/X interaction whose finer box is a leaf with at most n_s points is
+  summed directly (moved to U), the original KIFMM's cost rule.
 
 Parity status: every function here is pinned by tests under tests/ against
 closed forms, invariants or brute force (see the test module docstrings).
@@ -232,6 +234,56 @@ def lists(tree):
     return out
 
 
+def direct_threshold(ns: int, direct_max: int = 0) -> int:
+    """Particle count up to which a W/X box is evaluated directly: n_s by
+    default (direct_max = 0), none when direct_max < 0."""
+    if direct_max < 0:
+        return -1
+    return ns if direct_max == 0 else int(direct_max)
+
+
+def effective_lists(tree, lst, thr: int):
+    """Lists as evaluated: a W or X interaction whose finer box (the W member,
+    or the X list's owner) is a leaf holding at most ``thr`` particles is
+    evaluated directly, so its source moves to the U list.
+
+    This is the original KIFMM's cost rule (Ying, Biros & Zorin 2004, the
+    adaptive lists cited in Sec. 2.2): M2P costs n_s evaluations per target
+    and P2L n_s per source, so a box with fewer points than its equivalent
+    surface is cheaper, and exact, to sum point by point.  The rule is the
+    same from both sides of a pair (A in W(B) iff B in X(A)), so U stays
+    symmetric and X stays the transpose of W."""
+    if thr < 0:
+        return lst
+    nb = tree["nb"]
+    leaf = tree["isleaf"].astype(bool)
+    cnt = tree["count"]
+    small = leaf & (cnt <= thr)
+
+    def rows(kind):
+        ptr, idx = lst[kind]
+        return [idx[ptr[b]:ptr[b + 1]] for b in range(nb)]
+
+    U, V, W, X = (rows(k) for k in "UVWX")
+    U2, W2, X2 = [], [], []
+    for b in range(nb):
+        w_keep = [a for a in W[b] if not small[a]]
+        w_move = [a for a in W[b] if small[a]]
+        x_move = list(X[b]) if small[b] else []
+        x_keep = [] if small[b] else list(X[b])
+        U2.append(sorted(list(U[b]) + w_move + x_move))
+        W2.append(w_keep)
+        X2.append(x_keep)
+
+    def csr(r):
+        ptr = np.zeros(nb + 1, dtype=np.int64)
+        ptr[1:] = np.cumsum([len(v) for v in r])
+        idx = np.array([a for v in r for a in v], dtype=np.int64)
+        return ptr, idx
+
+    return {"U": csr(U2), "V": lst["V"], "W": csr(W2), "X": csr(X2)}
+
+
 def list_of(tree, kind: str, t: int):
     """One target's list (used to check sampled boxes of large trees)."""
     lib = _lib()
@@ -345,10 +397,13 @@ class _Fmm(ctypes.Structure):
 
 
 def kifmm(x, q, p: int = 6, leaf_cap: int = 64, max_depth: int = 20, eps: float = 1e-12,
-          ops=None, tree=None, lst=None):
+          ops=None, tree=None, lst=None, direct_max: int = 0):
     """Potential and gradient (user order, Eq. 3 units) of every particle from
-    all others, by the KIFMM.  Returns (pot, grad, info) where info holds the
-    tree, lists and the intermediate densities (canonical node order)."""
+    all others, by the KIFMM.  ``lst`` (if given) holds the lists as
+    classified; W/X interactions of small leaves are then moved to U by
+    effective_lists (threshold from direct_threshold(n_s, direct_max)).
+    Returns (pot, grad, info) where info holds the tree, the lists as
+    evaluated and the intermediate densities (canonical node order)."""
     lib = _lib()
     x = _f64(x).reshape(-1, 3)
     q = _f64(q).reshape(-1)
@@ -359,6 +414,7 @@ def kifmm(x, q, p: int = 6, leaf_cap: int = 64, max_depth: int = 20, eps: float 
         lst = lists(tree)
     if ops is None:
         ops = operators(p, eps)
+    lst = effective_lists(tree, lst, direct_threshold(ops["ns"], direct_max))
     perm = tree["perm"]
     xs = np.ascontiguousarray(x[perm])
     qsrt = np.ascontiguousarray(q[perm])

@@ -210,6 +210,7 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     P.io_f64 = (d.dtype == KIFMM_DTYPE_F64);
     P.coef = (d.coef == 0.0) ? 1.0 : d.coef;
     P.eps = (d.pinv_eps == 0.0) ? 1e-12 : d.pinv_eps;
+    P.direct_thr = (d.direct_max < 0) ? -1 : (d.direct_max == 0 ? P.ns : d.direct_max);
     auto fail = [&](kifmm_status st) {
         kifmm_plan_destroy(pl);
         (void)cudaGetLastError();
@@ -246,7 +247,8 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {(void **)&P.bbox_ord, sizeof(unsigned long long) * 6 * P.sys_cap},
         {(void **)&P.hist, sizeof(uint32_t) * P.hist_elems},
         {(void **)&P.status, sizeof(int)},
-        {(void **)&P.part_counts, sizeof(uint32_t) * 256},
+        {(void **)&P.part_counts, sizeof(uint32_t) * 4 * 256},
+        {(void **)&P.list_totals, sizeof(unsigned long long) * 4},
         {(void **)&P.energy_chunk_start, sizeof(int32_t) * (P.sys_cap + 1)},
     };
     for (const A &a : arrs)
@@ -302,29 +304,14 @@ static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cu
     const int n_systems = P.n_sys;
     const int64_t *sys_offsets = P.sys_off_h.data();
     API_CUDA(cudaMemsetAsync(P.status, 0, sizeof(int), s));
+    // Non-finite inputs still quantise to valid keys, so the tree and lists
+    // build regardless; the status is read once at the end.
     API_CUDA(build_tree(P, xyz, q, s));
-    int st = 0;
-    API_CUDA(cudaMemcpyAsync(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    API_CUDA(cudaStreamSynchronize(s));
-    if (st != 0) return (kifmm_status)st;
     API_CUDA(ensure_box_arrays(P));
     API_CUDA(build_lists(P, s));
     API_CUDA(ensure_partition_arrays(P));
     API_CUDA(partition_boxes(P, s));
     if (P.desc.precision == KIFMM_MIXED_FP16) API_CUDA(m2l_tensor_tiles(P, s));
-    // list totals for V and X
-    {
-        std::vector<int32_t> nv(P.nb), nx(P.nb);
-        API_CUDA(cudaMemcpyAsync(nv.data(), P.nv, sizeof(int32_t) * P.nb, cudaMemcpyDeviceToHost, s));
-        API_CUDA(cudaMemcpyAsync(nx.data(), P.nx, sizeof(int32_t) * P.nb, cudaMemcpyDeviceToHost, s));
-        API_CUDA(cudaStreamSynchronize(s));
-        P.n_v = 0;
-        P.n_x = 0;
-        for (int64_t b = 0; b < P.nb; ++b) {
-            P.n_v += nv[b];
-            P.n_x += nx[b];
-        }
-    }
     // energy chunks (sorted order never mixes systems)
     {
         std::vector<int64_t> ch;
@@ -346,8 +333,8 @@ static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cu
         API_CUDA(cudaMemcpyAsync(P.energy_chunks, ch.data(), sizeof(int64_t) * ch.size(), cudaMemcpyHostToDevice, s));
         API_CUDA(cudaMemcpyAsync(P.energy_chunk_start, start.data(), sizeof(int32_t) * start.size(),
                                  cudaMemcpyHostToDevice, s));
-        API_CUDA(cudaStreamSynchronize(s));
     }
+    int st = 0;
     API_CUDA(cudaMemcpyAsync(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     API_CUDA(cudaStreamSynchronize(s));
     if (st != 0) return (kifmm_status)st;

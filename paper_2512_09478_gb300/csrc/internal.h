@@ -32,6 +32,7 @@ struct Plan {
     int io_f64 = 0;           // caller dtype is double
     double coef = 1.0;
     double eps = 1e-12;
+    int direct_thr = -1;      // W/X of leaves with at most this many points go to U (-1: none)
     int num_sms = 0;
 
     // ---- operators (device) ----
@@ -106,7 +107,8 @@ struct Plan {
     int32_t *wsrc_flag = nullptr;    // [nb] 1 if the box is in some W list
     void *part_keys = nullptr;       // [2][box_cap] u64 partition scratch
     void *part_vals = nullptr;       // [2][box_cap] u32
-    uint32_t *part_counts = nullptr; // [256]
+    uint32_t *part_counts = nullptr; // [4][256]
+    unsigned long long *list_totals = nullptr;  // [4] V and X list sizes
     // Box lists grouped by a small key (stable, canonical order within a key):
     //   0: octant class of boxes with a V list (8 = none)
     //   1: leaves (key 0), then non-leaves by level (key 1 + level)

@@ -283,31 +283,35 @@ __global__ void k_roots(int S, const int64_t *off, int32_t *lvl, int32_t *cx, in
 
 // For each node of one level: octant ranges of its keys and the number of
 // non-empty octants if it splits (count > M and level < max depth).
+// One warp per node; lanes 0..7 search in parallel for the end of octant o
+// (first index in the node's range whose digit exceeds o).
 __global__ void k_split(int64_t ls, int64_t le, int level, int leaf_cap, int max_depth,
                         const uint64_t *__restrict__ keys, const int32_t *__restrict__ first,
                         const int32_t *__restrict__ cnt, uint32_t *nchild_tmp, int32_t *rng) {
-    int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (b >= le) return;
     const int64_t j = b - ls;
-    uint32_t nc = 0;
-    if (cnt[b] > leaf_cap && level < max_depth) {
+    const bool split = cnt[b] > leaf_cap && level < max_depth;
+    int64_t end = 0;
+    const int64_t lo0 = first[b], hi0 = lo0 + cnt[b];
+    if (split && lane < 8) {
         const int shift = 3 * (kMaxLevel - level);
-        const int64_t lo0 = first[b], hi0 = lo0 + cnt[b];
-        int64_t start = lo0;
-        for (int o = 0; o < 8; ++o) {
-            // first index in [start, hi0) whose digit exceeds o
-            int64_t lo = start, hi = hi0;
-            while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
-                if ((int)((keys[mid] >> shift) & 7ULL) <= o) lo = mid + 1; else hi = mid;
-            }
-            rng[j * 16 + 2 * o] = (int32_t)start;
-            rng[j * 16 + 2 * o + 1] = (int32_t)(lo - start);
-            if (lo > start) ++nc;
-            start = lo;
+        int64_t lo = lo0, hi = hi0;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int)((keys[mid] >> shift) & 7ULL) <= lane) lo = mid + 1; else hi = mid;
         }
+        end = lo;
     }
-    nchild_tmp[j] = nc;
+    const int64_t start = __shfl_up_sync(0xffffffffu, end, 1);
+    const int64_t s0 = (lane == 0) ? lo0 : start;
+    const unsigned nonempty = __ballot_sync(0xffffffffu, split && lane < 8 && end > s0);
+    if (split && lane < 8) {
+        rng[j * 16 + 2 * lane] = (int32_t)s0;
+        rng[j * 16 + 2 * lane + 1] = (int32_t)(end - s0);
+    }
+    if (lane == 0) nchild_tmp[j] = split ? (uint32_t)__popc(nonempty) : 0u;
 }
 
 __global__ void k_emit(int64_t ls, int64_t le, const uint32_t *__restrict__ nchild_tmp,
@@ -386,7 +390,7 @@ __global__ void k_colleagues(int64_t ls, int64_t le, int level, const int32_t *_
     int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= le) return;
     int32_t *cb = coll + b * kColl;
-    for (int k = 0; k < kColl; ++k) cb[k] = -1;
+    // cb was set to -1 by a memset of the whole array before the first level
     if (level == 0) {
         cb[13] = (int32_t)b;
         return;
@@ -456,20 +460,25 @@ __device__ __forceinline__ int v_slot(int ox, int oy, int oz, int dx, int dy, in
     return a * 36 + b * 6 + c - before;
 }
 
+// A leaf holding at most thr points: its W/X interactions are summed directly.
+__device__ __forceinline__ bool direct_box(const int32_t *nchild, const int32_t *cnt, int thr, int32_t b) {
+    return thr >= 0 && nchild[b] == 0 && cnt[b] <= thr;
+}
+
 // V list (children of the parent's colleagues not adjacent to b) into the
 // per-class slot table, and X list (coarser leaves adjacent to the parent but
-// not to b).
-__global__ void k_vx(int64_t ls, int64_t le, int level, const int32_t *__restrict__ parent,
+// not to b; empty when b itself is a direct-sum leaf, see k_uw).
+__global__ void k_vx(int64_t ls, int64_t le, int level, int thr, const int32_t *__restrict__ parent,
                      const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
+                     const int32_t *__restrict__ cnt,
                      const int32_t *__restrict__ lvl, const int32_t *__restrict__ cx,
                      const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
                      const int32_t *__restrict__ coll, const int32_t *__restrict__ coarse,
                      const int32_t *__restrict__ ncoarse, int32_t *vdense, int32_t *nv, int32_t *xdense,
-                     int32_t *nx) {
+                     int32_t *nx, unsigned long long *totals) {
     int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= le) return;
-    int32_t *vb = vdense + b * kVSlots;
-    for (int s = 0; s < kVSlots; ++s) vb[s] = -1;
+    int32_t *vb = vdense + b * kVSlots;  // preset to -1 by a memset
     int cntv = 0, cntx = 0;
     if (level > 0) {
         const int32_t P = parent[b];
@@ -486,20 +495,28 @@ __global__ void k_vx(int64_t ls, int64_t le, int level, const int32_t *__restric
                 ++cntv;
             }
         }
-        for (int k = 0; k < ncoarse[P]; ++k) {
-            const int32_t a = coarse[(int64_t)P * kMaxCoarse + k];
-            if (!boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], level, cx[b], cy[b], cz[b]))
-                xdense[b * kMaxCoarse + cntx++] = a;
+        if (!direct_box(nchild, cnt, thr, (int32_t)b)) {
+            for (int k = 0; k < ncoarse[P]; ++k) {
+                const int32_t a = coarse[(int64_t)P * kMaxCoarse + k];
+                if (!boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], level, cx[b], cy[b], cz[b]))
+                    xdense[b * kMaxCoarse + cntx++] = a;
+            }
         }
     }
     nv[b] = cntv;
+    if (cntv) atomicAdd(&totals[0], (unsigned long long)cntv);
+    if (cntx) atomicAdd(&totals[1], (unsigned long long)cntx);
     nx[b] = cntx;
 }
 
 // U and W of a leaf: U = {b} + coarse adjacent leaves + finer adjacent leaves
 // found by descending b's non-leaf colleagues; a descendant that is not
-// adjacent to b (while its parent is) goes to W.  Pass 0 counts, pass 1 fills.
-__global__ void k_uw(int64_t nb, int pass, const int32_t *__restrict__ child_first,
+// adjacent to b (while its parent is) goes to W, or to U when it is a
+// direct-sum leaf.  When b itself is a direct-sum leaf, its X list (coarser
+// leaves adjacent to the parent, not to b) goes to U as well.  Pass 0 counts,
+// pass 1 fills.
+__global__ void k_uw(int64_t nb, int pass, int thr, const int32_t *__restrict__ parent,
+                     const int32_t *__restrict__ cnt, const int32_t *__restrict__ child_first,
                      const int32_t *__restrict__ nchild, const int32_t *__restrict__ lvl,
                      const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
                      const int32_t *__restrict__ cz, const int32_t *__restrict__ coll,
@@ -521,6 +538,15 @@ __global__ void k_uw(int64_t nb, int pass, const int32_t *__restrict__ child_fir
         if (pass) u_idx[u0 + nu] = coarse[b * kMaxCoarse + k];
         ++nu;
     }
+    if (lb > 0 && direct_box(nchild, cnt, thr, (int32_t)b)) {
+        const int32_t P = parent[b];
+        for (int k = 0; k < ncoarse[P]; ++k) {
+            const int32_t a = coarse[(int64_t)P * kMaxCoarse + k];
+            if (boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], lb, bx, by, bz)) continue;
+            if (pass) u_idx[u0 + nu] = a;
+            ++nu;
+        }
+    }
     int32_t stack[8 * (kMaxLevel + 1)];
     for (int k = 0; k < kColl; ++k) {
         const int32_t c = coll[b * kColl + k];
@@ -540,6 +566,9 @@ __global__ void k_uw(int64_t nb, int pass, const int32_t *__restrict__ child_fir
                     }
                     for (int32_t ch = child_first[a]; ch < child_first[a] + nchild[a]; ++ch) stack[sp++] = ch;
                 }
+            } else if (direct_box(nchild, cnt, thr, a)) {
+                if (pass) u_idx[u0 + nu] = a;
+                ++nu;
             } else {
                 if (pass) w_idx[w0 + nw] = a;
                 ++nw;
@@ -642,17 +671,21 @@ cudaError_t partition_boxes(Plan &P, cudaStream_t s) {
     uint64_t *pk0 = (uint64_t *)P.part_keys, *pk1 = pk0 + P.box_cap;
     uint32_t *pv0 = (uint32_t *)P.part_vals, *pv1 = pv0 + P.box_cap;
     ++g_launches, k_child8<<<grid_for(nb, 256), 256, 0, s>>>(nb, P.child_first, P.nchild, P.cx, P.cy, P.cz, P.child8);
+    KIFMM_CUDA_TRY(cudaMemsetAsync(P.part_counts, 0, sizeof(uint32_t) * 4 * 256, s));
     for (int mode = 0; mode < 4; ++mode) {
-        KIFMM_CUDA_TRY(cudaMemsetAsync(P.part_counts, 0, sizeof(uint32_t) * 256, s));
         ++g_launches, k_part_keys<<<grid_for(nb, 256), 256, 0, s>>>(nb, mode, P.nv, P.nchild, P.lvl, P.wsrc_flag,
-                                                                    P.cx, P.cy, P.cz, pk0, pv0, P.part_counts);
+                                                                    P.cx, P.cy, P.cz, pk0, pv0,
+                                                                    P.part_counts + 256 * mode);
         KIFMM_CUDA_TRY(radix_pass(P, pk0, pv0, pk1, pv1, nb, 0, 0, s));
         KIFMM_CUDA_TRY(cudaMemcpyAsync(P.part_list[mode], pv1, sizeof(int32_t) * nb, cudaMemcpyDeviceToDevice, s));
-        uint32_t counts[256];
-        KIFMM_CUDA_TRY(cudaMemcpyAsync(counts, P.part_counts, sizeof(counts), cudaMemcpyDeviceToHost, s));
-        KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    // one synchronisation for the four key histograms
+    uint32_t counts[4][256];
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(counts, P.part_counts, sizeof(counts), cudaMemcpyDeviceToHost, s));
+    KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int mode = 0; mode < 4; ++mode) {
         P.part_start[mode].assign(257, 0);
-        for (int k = 0; k < 256; ++k) P.part_start[mode][k + 1] = P.part_start[mode][k] + counts[k];
+        for (int k = 0; k < 256; ++k) P.part_start[mode][k + 1] = P.part_start[mode][k] + counts[mode][k];
     }
     P.m2l_targets = P.part_list[0];
     for (int c = 0; c <= 8; ++c) P.m2l_class_start[c] = P.part_start[0][c];
@@ -717,7 +750,7 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
     uint32_t *total_dev = P.scan_tmp + P.scan_tmp_elems - 1;
     while (true) {
         const int64_t m = le - ls;
-        ++g_launches, k_split<<<grid_for(m, 128), 128, 0, s>>>(ls, le, level, P.desc.leaf_cap, P.desc.max_depth, P.keys[0],
+        ++g_launches, k_split<<<grid_for(m, 4), 128, 0, s>>>(ls, le, level, P.desc.leaf_cap, P.desc.max_depth, P.keys[0],
                                                  P.first, P.cnt, P.tmp_nchild, P.child_rng);
         uint32_t *scan_out = P.tmp_nchild + P.box_cap;
         KIFMM_CUDA_TRY(exclusive_scan_u32(P.tmp_nchild, scan_out, m, total_dev, P.scan_tmp,
@@ -774,31 +807,41 @@ cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream
 
 cudaError_t build_lists(Plan &P, cudaStream_t s) {
     const int64_t nb = P.nb;
+    KIFMM_CUDA_TRY(cudaMemsetAsync(P.coll, 0xFF, sizeof(int32_t) * kColl * nb, s));
+    KIFMM_CUDA_TRY(cudaMemsetAsync(P.vdense, 0xFF, sizeof(int32_t) * kVSlots * nb, s));
+    KIFMM_CUDA_TRY(cudaMemsetAsync(P.list_totals, 0, sizeof(unsigned long long) * 4, s));
     for (int l = 0; l <= P.max_level; ++l) {
         const int64_t ls = P.level_start[l], le = P.level_start[l + 1];
         const unsigned g = grid_for(le - ls, 128);
-        ++g_launches, k_colleagues<<<g, 128, 0, s>>>(ls, le, l, P.parent, P.child_first, P.nchild, P.cx, P.cy, P.cz, P.coll);
-        ++g_launches, k_coarse<<<g, 128, 0, s>>>(ls, le, l, P.parent, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse,
-                                   P.ncoarse, P.status);
-        ++g_launches, k_vx<<<g, 128, 0, s>>>(ls, le, l, P.parent, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll,
-                               P.coarse, P.ncoarse, P.vdense, P.nv, P.xdense, P.nx);
+        ++g_launches, k_colleagues<<<g, 128, 0, s>>>(ls, le, l, P.parent, P.child_first, P.nchild, P.cx, P.cy, P.cz,
+                                                     P.coll);
+        ++g_launches, k_coarse<<<g, 128, 0, s>>>(ls, le, l, P.parent, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll,
+                                                 P.coarse, P.ncoarse, P.status);
+        ++g_launches, k_vx<<<g, 128, 0, s>>>(ls, le, l, P.direct_thr, P.parent, P.child_first, P.nchild, P.cnt,
+                                             P.lvl, P.cx, P.cy, P.cz,
+                                             P.coll, P.coarse, P.ncoarse, P.vdense, P.nv, P.xdense, P.nx,
+                                             P.list_totals);
         KIFMM_CUDA_TRY(cudaGetLastError());
     }
     const unsigned g = grid_for(nb, 128);
-    ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 0, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse, P.ncoarse,
-                           P.u_cnt, P.w_cnt, nullptr, nullptr, nullptr, nullptr, P.status);
-    uint32_t *tot = P.scan_tmp + P.scan_tmp_elems - 1;
-    uint32_t totals[2];
-    KIFMM_CUDA_TRY(exclusive_scan_u32(P.u_cnt, P.u_ptr, nb, tot, P.scan_tmp, P.scan_tmp_elems - 1, s));
-    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.u_ptr + nb, tot, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    KIFMM_CUDA_TRY(cudaMemcpyAsync(&totals[0], tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 0, P.direct_thr, P.parent, P.cnt, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse,
+                                         P.ncoarse, P.u_cnt, P.w_cnt, nullptr, nullptr, nullptr, nullptr, P.status);
+    // two scans, totals in the last two scratch words; one synchronisation for all list sizes
+    uint32_t *tot_u = P.scan_tmp + P.scan_tmp_elems - 1, *tot_w = P.scan_tmp + P.scan_tmp_elems - 2;
+    KIFMM_CUDA_TRY(exclusive_scan_u32(P.u_cnt, P.u_ptr, nb, tot_u, P.scan_tmp, P.scan_tmp_elems - 2, s));
+    KIFMM_CUDA_TRY(exclusive_scan_u32(P.w_cnt, P.w_ptr, nb, tot_w, P.scan_tmp, P.scan_tmp_elems - 2, s));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.u_ptr + nb, tot_u, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.w_ptr + nb, tot_w, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    uint32_t uw[2];
+    unsigned long long vx[4];
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(&uw[0], tot_u, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(&uw[1], tot_w, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(vx, P.list_totals, sizeof(vx), cudaMemcpyDeviceToHost, s));
     KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
-    KIFMM_CUDA_TRY(exclusive_scan_u32(P.w_cnt, P.w_ptr, nb, tot, P.scan_tmp, P.scan_tmp_elems - 1, s));
-    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.w_ptr + nb, tot, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    KIFMM_CUDA_TRY(cudaMemcpyAsync(&totals[1], tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
-    P.n_u = totals[0];
-    P.n_w = totals[1];
+    P.n_u = uw[0];
+    P.n_w = uw[1];
+    P.n_v = (int64_t)vx[0];
+    P.n_x = (int64_t)vx[1];
     if (P.n_u > P.u_cap || P.n_w > P.w_cap) {
         // grow the list storage (set_sources may allocate; evaluate never does)
         if (P.n_u > P.u_cap) {
@@ -810,8 +853,8 @@ cudaError_t build_lists(Plan &P, cudaStream_t s) {
             KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.w_idx, sizeof(int32_t) * P.w_cap));
         }
     }
-    ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 1, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse, P.ncoarse,
-                           P.u_cnt, P.w_cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, P.status);
+    ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 1, P.direct_thr, P.parent, P.cnt, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse,
+                                         P.ncoarse, P.u_cnt, P.w_cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, P.status);
     KIFMM_CUDA_TRY(cudaMemsetAsync(P.wsrc_flag, 0, sizeof(int32_t) * nb, s));
     if (P.n_w > 0) ++g_launches, k_mark_w<<<grid_for(P.n_w, 256), 256, 0, s>>>(P.n_w, P.w_idx, P.wsrc_flag);
     KIFMM_CUDA_TRY(cudaGetLastError());

@@ -31,7 +31,7 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("precision", ctypes.c_int), ("coef", ctypes.c_double), ("n_max", ctypes.c_int64),
                 ("n_systems_max", ctypes.c_int), ("dtype", ctypes.c_int), ("pinv_eps", ctypes.c_double),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("direct_max", ctypes.c_int)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -115,14 +115,15 @@ class Plan:
 
     def __init__(self, p: int = 6, leaf_cap: int = 128, max_depth: int = 20, precision: str = "fp32",
                  coef: float = 1.0, n_max: int = 1 << 20, n_systems_max: int = 1,
-                 dtype: torch.dtype = torch.float32, pinv_eps: float = 0.0, autotune: bool = False):
+                 dtype: torch.dtype = torch.float32, pinv_eps: float = 0.0, autotune: bool = False,
+                 direct_max: int = 0):
         lib = load()
         self.dtype = dtype
         self.precision = precision
         self.coef = coef
         d = PlanDesc(p=p, leaf_cap=leaf_cap, max_depth=max_depth, precision=PRECISIONS[precision], coef=coef,
                      n_max=n_max, n_systems_max=n_systems_max,
-                     dtype=1 if dtype == torch.float64 else 0, pinv_eps=pinv_eps, autotune=int(autotune))
+                     dtype=1 if dtype == torch.float64 else 0, pinv_eps=pinv_eps, autotune=int(autotune), direct_max=direct_max)
         h = ctypes.c_void_p()
         _check(lib.kifmm_plan_create(ctypes.byref(d), ctypes.byref(h)), "kifmm_plan_create")
         self._h = h

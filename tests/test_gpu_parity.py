@@ -66,10 +66,14 @@ def test_fp64_ill_conditioned_input_within_rounding_floor():
     assert O.rel_l2(grad.cpu().numpy(), grad_o) <= max(1e-12, 10 * floor_g)
 
 
+@pytest.mark.parametrize("direct_max", [0, -1])
 @pytest.mark.parametrize("case,M", [("uniform4096", 64), ("plummer3000", 16), ("clustered", 8)])
-def test_tree_and_lists_bit_exact(case, M):
+def test_tree_and_lists_bit_exact(case, M, direct_max):
+    """Keys, permutation, tree and lists as evaluated (direct_max = 0: W/X of
+    leaves with at most n_s points summed directly) or as classified
+    (direct_max = -1)."""
     x, q = CASES[case]()
-    plan = _plan(x, M=M)
+    plan = _plan(x, M=M, direct_max=direct_max)
     plan.set_sources(_dev(x), _dev(q))
     keys, perm, lo_side = plan.keys()
     t = O.sort_and_tree(x, M, 20)
@@ -81,13 +85,16 @@ def test_tree_and_lists_bit_exact(case, M):
     for name in ("level", "first", "count", "parent"):
         assert np.array_equal(g[name], t[name]), name
     assert np.array_equal(g["coord"], t["coord"])
-    L = O.lists(t)
+    raw = O.lists(t)
+    L = O.effective_lists(t, raw, O.direct_threshold(6 * 3 * 3 + 2, direct_max))  # p = 4: n_s = 56
     for kind in "UVWX":
         ptr, idx = plan.list(kind)
         assert np.array_equal(ptr, L[kind][0]), kind
         assert np.array_equal(idx, L[kind][1]), kind
     if case == "plummer3000":
-        assert L["W"][1].size > 0 and L["X"][1].size > 0
+        assert raw["W"][1].size > 0 and raw["X"][1].size > 0
+        if direct_max == 0:
+            assert L["U"][1].size > raw["U"][1].size  # some W/X moved to U
 
 
 @pytest.mark.parametrize("case,M,p", [("uniform4096", 64, 4), ("plummer3000", 16, 4), ("clustered", 8, 6)])

@@ -129,11 +129,14 @@ def _descendant_leaves(t, b):
     return out
 
 
+@pytest.mark.parametrize("thr", [-1, 6, 56])
 @pytest.mark.parametrize("shape,n,M", [("plummer", 1500, 8), ("uniform", 900, 6), ("clustered", 700, 4)])
-def test_lists_cover_every_pair_exactly_once(shape, n, M):
+def test_lists_cover_every_pair_exactly_once(shape, n, M, thr):
     """Every ordered (target leaf, source leaf) pair is accounted for exactly
     once by U(B), W(B) (source inside a W box) or V/X of an ancestor-or-self
-    of B (source inside that box): the sum then counts each interaction once."""
+    of B (source inside that box): the sum then counts each interaction once.
+    Holds for the lists as classified (thr = -1) and as evaluated, with W/X
+    interactions of leaves holding at most thr points moved to U."""
     if shape == "plummer":
         x, _ = G.plummer(n, 5)
     elif shape == "uniform":
@@ -142,7 +145,8 @@ def test_lists_cover_every_pair_exactly_once(shape, n, M):
         rng = np.random.default_rng(5)
         x = np.concatenate([rng.normal(0, 0.01, size=(n // 2, 3)), rng.uniform(-1, 1, size=(n - n // 2, 3))])
     t = O.sort_and_tree(x, M, 20)
-    L = O.lists(t)
+    raw = O.lists(t)
+    L = O.effective_lists(t, raw, thr)
     leaves = np.nonzero(t["isleaf"])[0]
     pos = {b: i for i, b in enumerate(leaves)}
     desc = {b: _descendant_leaves(t, b) for b in range(t["nb"])}
@@ -164,14 +168,30 @@ def test_lists_cover_every_pair_exactly_once(shape, n, M):
                     for a in desc[A]:
                         cover[pos[a]] += 1
         assert np.all(cover == 1), (B, np.nonzero(cover != 1)[0][:10])
-    assert L["W"][1].size > 0 or shape == "uniform"
+    assert raw["W"][1].size > 0 or shape == "uniform"
+    # every U entry is a leaf, and a moved entry is a W/X pair of a small leaf
+    assert np.all(t["isleaf"][L["U"][1]] == 1)
+    small = (t["isleaf"] == 1) & (t["count"] <= thr)
+    for b in range(t["nb"]):
+        Wr = set(members_raw("W", raw, b))
+        Xr = set(members_raw("X", raw, b))
+        moved = set(L["U"][1][L["U"][0][b]:L["U"][0][b + 1]]) - set(members_raw("U", raw, b))
+        assert moved == {a for a in Wr if small[a]} | (Xr if small[b] else set())
 
 
-def test_lists_duality():
-    """U and V are symmetric relations and X is the transpose of W."""
+def members_raw(kind, L, b):
+    ptr, idx = L[kind]
+    return [int(a) for a in idx[ptr[b]:ptr[b + 1]]]
+
+
+@pytest.mark.parametrize("thr", [-1, 8, 56])
+def test_lists_duality(thr):
+    """U and V are symmetric relations and X is the transpose of W, for the
+    lists as classified and as evaluated (the direct-sum rule is the same
+    from both sides of a W/X pair)."""
     x, _ = G.plummer(1200, 9)
     t = O.sort_and_tree(x, 8, 20)
-    L = O.lists(t)
+    L = O.effective_lists(t, O.lists(t), thr)
 
     def pairs(kind):
         ptr, idx = L[kind]
@@ -181,7 +201,7 @@ def test_lists_duality():
     assert U == {(a, b) for b, a in U}
     assert V == {(a, b) for b, a in V}
     assert X == {(a, b) for b, a in W}
-    assert len(W) > 0
+    assert len(W) > 0 or thr >= 8
     # V members are never adjacent: offsets stay within the 316 M2L offsets
     offs = {tuple(d) for d in O.m2l_offsets()}
     for b, a in V:
