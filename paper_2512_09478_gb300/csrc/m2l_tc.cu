@@ -14,10 +14,13 @@
 // is below 2^-22 of the product) and the epilogue divides by sigma_A sigma_B.
 //
 // Pipeline (per CTA, 160 threads):
-//   warps 0-3  producers: cp.async (16 B, L2) of the gathered A rows and of the
-//              slot's B rows into a ring of shared-memory stages laid out in
-//              the 64-byte swizzled K-major form; completion is tracked by the
-//              stage's "full" mbarrier (cp.async.mbarrier.arrive.noinc).
+//   warps 0-3  producers: cp.async (16 B, four threads per 64-byte row) of the
+//              gathered A rows into a ring of shared-memory stages laid out in
+//              the 64-byte swizzled K-major form; the slot's B block is stored
+//              in global memory already in that form and arrives by one bulk
+//              (TMA) copy per operand half.  Completion is tracked by the
+//              stage's "full" mbarrier (cp.async.mbarrier.arrive.noinc plus the
+//              bulk copies' byte count).
 //   warp 4     allocates TMEM; one thread issues tcgen05.mma for each stage
 //              and frees the stage with tcgen05.commit on its "empty" barrier.
 //   warps 0-3  epilogue: tcgen05.ld of their 32 TMEM lanes, unscale, store.
@@ -73,6 +76,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bulk (TMA, non-tensor) copy global -> shared, completion counted in bytes on
+// an mbarrier.  Addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
@@ -166,7 +181,7 @@ struct TileArgs {
     const int32_t *vdense;    // [nb][189]
     const int *slot_off;      // [8][189]
     const __half *uh, *ul;    // [nb][kp] scaled expansions
-    const __half *bh, *bl;    // [316][np][kp] scaled operators
+    const __half *bh, *bl;    // [316][kp/32][np][32] scaled operators, K-block-major, 64-byte swizzled
     const int32_t *lvl;
     const float *level_unscale;  // 1 / (sigma_A(level) sigma_B)
     float *d;                 // [nb][ns]
@@ -190,6 +205,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
     __shared__ uint32_t tmem_base_s;
     __shared__ int32_t tgt_s[kTcRows];
     __shared__ volatile int abort_s;
+    __shared__ volatile int abort_zero;  // never set: a wait on it runs to its bound
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int4 tile = a.tiles[blockIdx.x];
@@ -200,8 +216,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
     }
     if (threadIdx.x == 0) {
         abort_s = 0;
+        abort_zero = 0;
         for (int s = 0; s < NS; ++s) {
-            mbar_init(smem_u32(&full_bar[s]), kTcRows);
+            mbar_init(smem_u32(&full_bar[s]), kTcRows + 1);  // 128 cp.async arrivals + the bulk-copy leader
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
         mbar_init(smem_u32(&done_bar), 1);
@@ -229,24 +246,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
 
     if (warp < 4) {
         // ---------------- producers ----------------
-        const int row = threadIdx.x;  // A row owned by this thread
-        const int32_t t = tgt_s[row];
-        int32_t src = -1;
-        // next slot's source and operator are fetched one slot ahead
-        int32_t src_next = (t >= 0) ? a.vdense[(size_t)t * kVSlots] : -1;
-        int o_next = a.slot_off[cls * kVSlots];
-        const __half *bh_base = nullptr, *bl_base = nullptr;
+        // Thread t copies 16-byte chunk (t & 3) of rows (t >> 2) + 32 i, so
+        // each warp instruction reads eight whole 64-byte rows.
+        const int ch = threadIdx.x & 3, r0 = threadIdx.x >> 2;
+        int32_t tg[4], src[4], src_next[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            tg[i] = tgt_s[r0 + 32 * i];
+            src[i] = -1;
+            src_next[i] = (tg[i] >= 0) ? a.vdense[(size_t)tg[i] * kVSlots] : -1;
+        }
+        const bool leader = threadIdx.x == 0;
+        int o_cur = 0, last_it = -1;
         for (int it = 0; it < iters; ++it) {
             const int stage = it % NS;
             const int s = it / kblocks, kb = it - s * kblocks;
             if (kb == 0) {
-                src = src_next;
-                bh_base = a.bh + (size_t)o_next * np * kp;
-                bl_base = a.bl + (size_t)o_next * np * kp;
-                if (s + 1 < kVSlots) {
-                    src_next = (t >= 0) ? a.vdense[(size_t)t * kVSlots + s + 1] : -1;
-                    o_next = a.slot_off[cls * kVSlots + s + 1];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    src[i] = src_next[i];
+                    if (s + 1 < kVSlots) src_next[i] = (tg[i] >= 0) ? a.vdense[(size_t)tg[i] * kVSlots + s + 1] : -1;
                 }
+                if (leader) o_cur = a.slot_off[cls * kVSlots + s];
             }
             if (!mbar_wait(smem_u32(&empty_bar[stage]), ((it / NS) & 1) ^ 1, &abort_s)) {
                 set_status(a.status, KIFMM_ERR_TIMEOUT);
@@ -255,27 +276,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             }
             unsigned char *st = smem + (size_t)stage * stage_bytes;
             const uint32_t sA = smem_u32(st), sAl = sA + a_bytes, sB = sAl + a_bytes, sBl = sB + b_bytes;
-            const size_t koff = (size_t)kb * kKBlock;
-            const __half *gh = a.uh + (size_t)(src >= 0 ? src : 0) * kp + koff;
-            const __half *gl = a.ul + (size_t)(src >= 0 ? src : 0) * kp + koff;
-            const uint32_t nbytes = (src >= 0) ? 16u : 0u;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                cp_async16(sA + swz64(row, c), gh + 8 * c, nbytes);
-                cp_async16(sAl + swz64(row, c), gl + 8 * c, nbytes);
+            const uint32_t fb = smem_u32(&full_bar[stage]);
+            if (leader) {
+                const size_t boff = ((size_t)o_cur * kblocks + kb) * (size_t)np * kKBlock;
+                mbar_arrive_expect_tx(fb, 2 * b_bytes);
+                bulk_g2s(sB, a.bh + boff, b_bytes, fb);
+                bulk_g2s(sBl, a.bl + boff, b_bytes, fb);
+                last_it = it;
             }
-            for (int r = row; r < np; r += kTcRows) {
-                const __half *bh = bh_base + (size_t)r * kp + koff;
-                const __half *bl = bl_base + (size_t)r * kp + koff;
+            const size_t koff = (size_t)kb * kKBlock + 8 * ch;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    cp_async16(sB + swz64(r, c), bh + 8 * c, 16u);
-                    cp_async16(sBl + swz64(r, c), bl + 8 * c, 16u);
-                }
+            for (int i = 0; i < 4; ++i) {
+                const int r = r0 + 32 * i;
+                const size_t g = (size_t)(src[i] >= 0 ? src[i] : 0) * kp + koff;
+                const uint32_t nbytes = (src[i] >= 0) ? 16u : 0u;
+                cp_async16(sA + swz64(r, ch), a.uh + g, nbytes);
+                cp_async16(sAl + swz64(r, ch), a.ul + g, nbytes);
             }
-            cp_async_arrive_noinc(smem_u32(&full_bar[stage]));
+            cp_async_arrive_noinc(fb);
         }
         cp_async_wait_all();
+        if (leader && abort_s && last_it >= 0) {
+            // the last bulk copies must land before the CTA's shared memory
+            // goes away; the bounded wait outlasts them even when other
+            // producers stopped before arriving on that stage
+            (void)mbar_wait(smem_u32(&full_bar[last_it % NS]), (last_it / NS) & 1, &abort_zero);
+        }
     } else if (warp == 4) {
         // ---------------- MMA issuer ----------------
         // Slot s accumulates into partial buffer s % 2 (fresh accumulator:
@@ -425,15 +451,23 @@ __global__ void k_split_u(int64_t nb, int ns, int kp, const float *__restrict__ 
     ul[idx] = __float2half_rn(x - __half2float(h));
 }
 
+// Operator B[j][k] = M_o[j][k] (m2l_t is stored transposed, [o][k][j]) split
+// into FP16 hi/lo and stored K-block-major: block (o, kb) holds rows j < np of
+// 32 elements in the 64-byte swizzled K-major form (16-byte chunk c of row j
+// at chunk position c ^ ((j >> 1) & 3)), so one linear copy of the block
+// lands in shared memory ready for the tensor core.
 __global__ void k_split_ops(int nops, int ns, int np, int kp, const float *__restrict__ m2l_t, float sigma,
                             __half *__restrict__ bh, __half *__restrict__ bl) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)nops * np * kp;
     if (idx >= total) return;
-    const int o = (int)(idx / ((int64_t)np * kp));
-    const int rem = (int)(idx - (int64_t)o * np * kp);
-    const int j = rem / kp, k = rem % kp;
-    // B[j][k] = M_o[j][k]; m2l_t is stored transposed ([o][k][j])
+    const int kblocks = kp / kKBlock;
+    const int64_t blk = idx / ((int64_t)np * kKBlock);  // o * kblocks + kb
+    const int rem = (int)(idx - blk * np * kKBlock);
+    const int o = (int)(blk / kblocks), kb = (int)(blk - (int64_t)o * kblocks);
+    const int j = rem / kKBlock, pos = rem % kKBlock;   // pos: swizzled position in the row
+    const int c = (pos >> 3) ^ ((j >> 1) & 3), e = pos & 7;
+    const int k = kb * kKBlock + c * 8 + e;
     const float x = (j < ns && k < ns) ? m2l_t[((size_t)o * ns + k) * ns + j] * sigma : 0.f;
     const __half h = __float2half_rn(x);
     bh[idx] = h;
