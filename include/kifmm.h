@@ -74,8 +74,10 @@ typedef struct {
     int n_systems_max;   /* largest number of independent systems per call     */
     int dtype;           /* kifmm_dtype of xyz, q, pot, grad, forces           */
     double pinv_eps;     /* relative SVD truncation of the check-to-equivalent
-                            pseudo-inverse; 0 selects 1e-12.  It must not lie
-                            within a factor 1.1 of any sigma_i / sigma_max.    */
+                            pseudo-inverse; 0 selects 1e-12 in FP64 mode and
+                            1e-9 in the FP32-based modes.  In FP64 mode it must
+                            not lie within a factor 1.1 of any
+                            sigma_i / sigma_max (KIFMM_ERR_ARG otherwise).    */
     int autotune;        /* 1: time candidate tile shapes at plan creation     */
     int direct_max;      /* a W/X interaction whose finer box (the W member,
                             or the owner of the X list) is a leaf holding at

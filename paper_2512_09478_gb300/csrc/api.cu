@@ -209,7 +209,10 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     P.f64 = (d.precision == KIFMM_FP64);
     P.io_f64 = (d.dtype == KIFMM_DTYPE_F64);
     P.coef = (d.coef == 0.0) ? 1.0 : d.coef;
-    P.eps = (d.pinv_eps == 0.0) ? 1e-12 : d.pinv_eps;
+    // FP32 arithmetic cannot resolve the modes below ~1e-9 sigma_max: keeping
+    // them only inflates the composite operators (at p = 8 their entries grow
+    // ~30x and so does the FP32 rounding of every translation).
+    P.eps = (d.pinv_eps != 0.0) ? d.pinv_eps : (P.f64 ? 1e-12 : 1e-9);
     P.direct_thr = (d.direct_max < 0) ? -1 : (d.direct_max == 0 ? P.ns : d.direct_max);
     auto fail = [&](kifmm_status st) {
         kifmm_plan_destroy(pl);

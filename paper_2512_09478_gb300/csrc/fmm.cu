@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ 
     __shared__ int32_t src[kGT];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int cls = blockIdx.y;
+    const int j0 = blockIdx.z * kGJ;  // output columns [j0, j0 + kGJ)
     int64_t t_begin = 0, t_end = 0;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ 
             for (int r = 0; r < kRM; ++r) {
                 const int e = threadIdx.x + 256 * r;
                 const int k = e / kGJ, j = e - k * kGJ;
-                rm[r] = (k0 + k < ns && j < ns) ? M[(size_t)(k0 + k) * ns + j] : T(0);
+                rm[r] = (k0 + k < ns && j0 + j < ns) ? M[(size_t)(k0 + k) * ns + j0 + j] : T(0);
             }
         };
         load(0);
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ 
         if (t < 0) continue;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-            const int j = tx + 32 * c;
+            const int j = j0 + tx + 32 * c;
             if (j < ns) {
                 const T v = kTwoLevel ? run[a][c] : acc[a][c];
                 T *o = out + (size_t)t * ns + j;
@@ -556,7 +557,7 @@ void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *s
     for (int c = 0; c <= ncls; ++c) cr.b[c] = starts[c];
     for (int c = 0; c < ncls; ++c) most = std::max<int64_t>(most, starts[c + 1] - starts[c]);
     if (most <= 0) return;
-    dim3 grid(grid_for(most, kGT), ncls);
+    dim3 grid(grid_for(most, kGT), ncls, grid_for(P.ns, kGJ));
     ++g_launches, k_ggemm<T, G><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, in, out, accumulate);
 }
 

@@ -39,7 +39,9 @@ namespace kifmm {
 
 namespace {
 
-constexpr int kTcThreads = 288;     // 4 producer warps, 1 MMA warp, 4 drain warps
+constexpr int kDrainWarps = 8;
+constexpr int kTcThreads = 32 * (5 + kDrainWarps);  // 4 producer warps, 1 MMA warp, 8 drain warps
+constexpr int kAccBufs = 3;         // per-slot partial accumulators in TMEM
 constexpr int kTcRows = 128;        // targets per CTA (MMA M)
 constexpr int kKBlock = 32;         // FP16 elements per stage row (64 bytes)
 constexpr int kRowBytes = 64;
@@ -142,37 +144,18 @@ __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
-// 32 lanes x 32 columns of 32-bit TMEM data -> 32 registers per thread.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-    uint32_t r[32];
+// 32 lanes x 16 columns of 32-bit TMEM data -> 16 registers per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 registers per thread -> 32 lanes x 32 columns of TMEM.
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
-    uint32_t r[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(v[i]);
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
-        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
-        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-        : "memory");
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 struct TileArgs {
@@ -185,7 +168,7 @@ struct TileArgs {
     const int32_t *lvl;
     const float *level_unscale;  // 1 / (sigma_A(level) sigma_B)
     float *d;                 // [nb][ns]
-    int ns, kp, np, nstages;
+    int ns, kp, np, nstages;  // np: operator rows (output columns) incl. padding
     int *status;
 };
 
@@ -194,14 +177,18 @@ __device__ __forceinline__ uint32_t swz64(int r, int c) {
     return (uint32_t)(r * kRowBytes + ((c ^ ((r >> 1) & 3)) << 4));
 }
 
+template <int NCH>
 __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
+    constexpr int NT = 32 * NCH;  // output columns of this CTA (MMA N)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int np = a.np, kp = a.kp, NS = a.nstages;
+    const int kp = a.kp, NS = a.nstages;
+    const int cb = blockIdx.y;  // column block: output columns [cb NT, (cb + 1) NT)
     const uint32_t a_bytes = kTcRows * kRowBytes;            // one of hi / lo
-    const uint32_t b_bytes = (uint32_t)np * kRowBytes;
+    const uint32_t b_bytes = (uint32_t)NT * kRowBytes;
     const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;  // multiple of 512
-    __shared__ __align__(8) uint64_t full_bar[16], empty_bar[16], done_bar, accfull_bar[2], accfree_bar[2];
+    __shared__ __align__(8) uint64_t full_bar[16], empty_bar[16], done_bar, accfull_bar[kAccBufs],
+        accfree_bar[kAccBufs];
     __shared__ uint32_t tmem_base_s;
     __shared__ int32_t tgt_s[kTcRows];
     __shared__ volatile int abort_s;
@@ -222,15 +209,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
         mbar_init(smem_u32(&done_bar), 1);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kAccBufs; ++b) {
             mbar_init(smem_u32(&accfull_bar[b]), 1);
-            mbar_init(smem_u32(&accfree_bar[b]), 4);  // lane 0 of each drain warp
+            mbar_init(smem_u32(&accfree_bar[b]), kDrainWarps);  // lane 0 of each drain warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // TMEM columns: running sum [0, np), partials [np, 2 np) and [2 np, 3 np);
-    // np is a multiple of 32 (enforced at setup).
-    const uint32_t tmem_cols = (3 * np <= 128) ? 128 : (3 * np <= 256) ? 256 : 512;
+    // TMEM columns: kAccBufs partial accumulators of NT columns each.
+    constexpr uint32_t tmem_cols = (kAccBufs * NT <= 128) ? 128 : (kAccBufs * NT <= 256) ? 256 : 512;
+    static_assert(kAccBufs * NT <= 512, "partial accumulators exceed TMEM");
     if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
                      "r"(tmem_cols)
@@ -278,7 +265,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             const uint32_t sA = smem_u32(st), sAl = sA + a_bytes, sB = sAl + a_bytes, sBl = sB + b_bytes;
             const uint32_t fb = smem_u32(&full_bar[stage]);
             if (leader) {
-                const size_t boff = ((size_t)o_cur * kblocks + kb) * (size_t)np * kKBlock;
+                const size_t boff = (((size_t)o_cur * kblocks + kb) * (size_t)a.np + (size_t)cb * NT) * kKBlock;
                 mbar_arrive_expect_tx(fb, 2 * b_bytes);
                 bulk_g2s(sB, a.bh + boff, b_bytes, fb);
                 bulk_g2s(sBl, a.bl + boff, b_bytes, fb);
@@ -304,20 +291,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
         }
     } else if (warp == 4) {
         // ---------------- MMA issuer ----------------
-        // Slot s accumulates into partial buffer s % 2 (fresh accumulator:
-        // the tensor core's FP32 accumulation rounds toward zero, so chains
-        // are kept to one slot and summed by the drain warps in IEEE FP32).
+        // Slot s accumulates into partial buffer s % kAccBufs (fresh
+        // accumulator: the tensor core's FP32 accumulation rounds toward
+        // zero, so chains are kept to one slot and summed by the drain warps
+        // in IEEE FP32).
         if (lane == 0) {
             int it = 0;
+            const uint32_t id = idesc_f16(NT);
             for (int s = 0; s < kVSlots && !abort_s; ++s) {
-                const int buf = s & 1;
-                if (s >= 2 && !mbar_wait(smem_u32(&accfree_bar[buf]), ((s >> 1) - 1) & 1, &abort_s)) {
+                const int buf = s % kAccBufs;
+                if (s >= kAccBufs &&
+                    !mbar_wait(smem_u32(&accfree_bar[buf]), ((s / kAccBufs) - 1) & 1, &abort_s)) {
                     set_status(a.status, KIFMM_ERR_TIMEOUT);
                     abort_s = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t tacc = tmem + (uint32_t)((1 + buf) * np);
+                const uint32_t tacc = tmem + (uint32_t)(buf * NT);
                 for (int kb = 0; kb < kblocks; ++kb, ++it) {
                     const int stage = it % NS;
                     if (!mbar_wait(smem_u32(&full_bar[stage]), (it / NS) & 1, &abort_s)) {
@@ -332,7 +322,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
                         const uint64_t dAh = sdesc_sw64(sA + 32 * kk), dAl = sdesc_sw64(sAl + 32 * kk);
-                        const uint32_t id = idesc_f16(np);
                         const uint64_t dBh = sdesc_sw64(sB + 32 * kk);
                         const uint64_t dBl = sdesc_sw64(sBl + 32 * kk);
                         const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
@@ -348,54 +337,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
         }
         __syncwarp();
     } else {
-        // ---------------- drain warps (5..8): TMEM lanes 32 (warp % 4) .. +31 ----------------
-        const int q = warp & 3;
+        // ---------------- drain warps (5..12) ----------------
+        // Warp w may read TMEM lanes 32 (w % 4) .. +31; two warps share each
+        // lane quadrant and split the NT columns in halves.  The running sums
+        // stay in registers (IEEE FP32 adds of the per-slot partials).
+        const int q = warp & 3, h = (warp - 5) >> 2;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const int c_base = h * (NT / 2);
+        float acc[NT / 2];
+#pragma unroll
+        for (int j = 0; j < NT / 2; ++j) acc[j] = 0.f;
+        bool ok = true;
         for (int s = 0; s < kVSlots; ++s) {
-            const int buf = s & 1;
-            bool ok = mbar_wait(smem_u32(&accfull_bar[buf]), (s >> 1) & 1, &abort_s);
-            ok = __all_sync(0xffffffffu, ok);  // warp-uniform: tcgen05.ld/st are .sync.aligned
+            const int buf = s % kAccBufs;
+            ok = mbar_wait(smem_u32(&accfull_bar[buf]), (s / kAccBufs) & 1, &abort_s);
+            ok = __all_sync(0xffffffffu, ok);  // warp-uniform: tcgen05.ld is .sync.aligned
             if (!ok) {
                 set_status(a.status, KIFMM_ERR_TIMEOUT);
                 abort_s = 1;
                 break;
             }
             tc_fence_after();
-            for (int c0 = 0; c0 < np; c0 += 32) {
-                float p[32], r[32];
-                tmem_ld32(tmem + lane_off + (uint32_t)((1 + buf) * np + c0), p);
-                if (s > 0) {
-                    tmem_ld32(tmem + lane_off + (uint32_t)c0, r);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) r[j] += p[j];
-                } else {
+            for (int c = 0; c < NT / 32; ++c) {
+                float p[16];
+                tmem_ld16(tmem + lane_off + (uint32_t)(buf * NT + c_base + 16 * c), p);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) r[j] = p[j];
-                }
-                tmem_st32(tmem + lane_off + (uint32_t)c0, r);
+                for (int j = 0; j < 16; ++j) acc[16 * c + j] += p[j];
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&accfree_bar[buf]));
         }
-        // final read-out of the running sums
-        bool ok = mbar_wait(smem_u32(&done_bar), 0, &abort_s);
-        ok = __all_sync(0xffffffffu, ok) && !abort_s;
-        tc_fence_after();
+        ok = ok && !abort_s;
         const int row = q * 32 + lane;
         const int32_t t = tgt_s[row];
-        const float scale = (t >= 0) ? a.level_unscale[a.lvl[t]] : 0.f;
-        if (ok) {
-            for (int c0 = 0; c0 < np; c0 += 32) {
-                float v[32];
-                tmem_ld32(tmem + lane_off + (uint32_t)c0, v);
-                if (t >= 0) {
-                    float *out = a.d + (size_t)t * a.ns + c0;
+        if (ok && t >= 0) {
+            const float scale = a.level_unscale[a.lvl[t]];
+            const int col0 = cb * NT + c_base;
+            float *out = a.d + (size_t)t * a.ns + col0;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (c0 + j < a.ns) out[j] = v[j] * scale;
-                }
-            }
+            for (int j = 0; j < NT / 2; ++j)
+                if (col0 + j < a.ns) out[j] = acc[j] * scale;
         }
     }
     tc_fence_before();
@@ -484,10 +467,22 @@ __global__ void k_absmax_f32(int64_t n, const float *__restrict__ x, unsigned *o
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+cudaError_t set_smem_attr(int nt, int bytes) {
+    switch (nt) {
+        case 32: return cudaFuncSetAttribute(k_m2l_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        case 64: return cudaFuncSetAttribute(k_m2l_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        case 96: return cudaFuncSetAttribute(k_m2l_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        case 128: return cudaFuncSetAttribute(k_m2l_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        case 160: return cudaFuncSetAttribute(k_m2l_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        default: return cudaErrorNotSupported;
+    }
+}
+
 }  // namespace
 
 struct TcState {
     int np = 0, kp = 0, nstages = 0;
+    int nt = 0, ncb = 0;      // output columns per CTA (MMA N), column blocks (np = nt ncb)
     float sigma_b = 1.f;
     __half *bh = nullptr, *bl = nullptr;
     __half *uh = nullptr, *ul = nullptr;
@@ -516,12 +511,17 @@ void m2l_tensor_release(Plan &P) {
 cudaError_t m2l_tensor_setup(Plan &P) {
     TcState &S = tc_state(P);
     const int ns = P.ns;
-    S.np = round_up(ns, 32);
+    // Output columns per CTA: at most 160 (three partial accumulators fit
+    // TMEM; the drain warps keep 80 running sums each in registers); larger
+    // surfaces (p >= 7) are split into column blocks over blockIdx.y.
+    const int np0 = round_up(ns, 32);
+    S.ncb = (np0 + 159) / 160;
+    S.nt = round_up((np0 + S.ncb - 1) / S.ncb, 32);
+    S.np = S.nt * S.ncb;
     S.kp = round_up(ns, kKBlock);
-    if (3 * S.np > 512) return cudaErrorNotSupported;  // running sum + two partials must fit TMEM (p <= 6)
-    const size_t stage = 2 * (size_t)kTcRows * kRowBytes + 2 * (size_t)S.np * kRowBytes;
+    const size_t stage = 2 * (size_t)kTcRows * kRowBytes + 2 * (size_t)S.nt * kRowBytes;
     S.nstages = (int)std::min<size_t>(16, (200 * 1024) / stage);
-    if (S.nstages < 2) return cudaErrorNotSupported;
+    if (S.nstages < 2 || S.nt > 160) return cudaErrorNotSupported;
     S.smem = S.nstages * stage + 1024;
     unsigned *dmax = nullptr;
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&dmax, sizeof(unsigned)));
@@ -543,7 +543,7 @@ cudaError_t m2l_tensor_setup(Plan &P) {
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.level_max, sizeof(unsigned) * 32));
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.level_sigma, sizeof(float) * 32));
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.level_unscale, sizeof(float) * 32));
-    KIFMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
+    KIFMM_CUDA_TRY(set_smem_attr(S.nt, (int)S.smem));
     return cudaDeviceSynchronize();
 }
 
@@ -597,7 +597,15 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {
     a.np = S.np;
     a.nstages = S.nstages;
     a.status = P.status;
-    ++g_launches, k_m2l_tc<<<(unsigned)S.tiles_h.size(), kTcThreads, S.smem, s>>>(a);
+    const dim3 grid((unsigned)S.tiles_h.size(), (unsigned)S.ncb);
+    switch (S.nt) {
+        case 32: ++g_launches, k_m2l_tc<1><<<grid, kTcThreads, S.smem, s>>>(a); break;
+        case 64: ++g_launches, k_m2l_tc<2><<<grid, kTcThreads, S.smem, s>>>(a); break;
+        case 96: ++g_launches, k_m2l_tc<3><<<grid, kTcThreads, S.smem, s>>>(a); break;
+        case 128: ++g_launches, k_m2l_tc<4><<<grid, kTcThreads, S.smem, s>>>(a); break;
+        case 160: ++g_launches, k_m2l_tc<5><<<grid, kTcThreads, S.smem, s>>>(a); break;
+        default: return cudaErrorNotSupported;
+    }
     return cudaGetLastError();
 }
 

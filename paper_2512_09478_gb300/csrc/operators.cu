@@ -229,14 +229,17 @@ cudaError_t build_operators(Plan &P, std::string &err) {
         err = "Jacobi SVD did not converge";
         return cudaErrorUnknown;
     }
-    // truncation with the gap check
+    // Truncation.  In FP64 mode the threshold must not lie within a factor 1.1
+    // of any sigma_i / sigma_max (the gap check), so that this Jacobi SVD and
+    // any other backward-stable SVD truncate the same modes; the FP32-based
+    // modes only need some consistent regularisation and skip the check.
     std::vector<double> sinv(2 * n);
     for (int m = 0; m < 2; ++m) {
         double smax = 0.0;
         for (int j = 0; j < n; ++j) smax = std::fmax(smax, sig[m * n + j]);
         for (int j = 0; j < n; ++j) {
             const double rel = sig[m * n + j] / smax;
-            if (rel > P.eps / 1.1 && rel < P.eps * 1.1) {
+            if (P.f64 && rel > P.eps / 1.1 && rel < P.eps * 1.1) {
                 char buf[160];
                 snprintf(buf, sizeof buf, "pinv_eps %.3g lies within a factor 1.1 of sigma/sigma_max = %.3g",
                          P.eps, rel);

@@ -97,7 +97,8 @@ def test_tree_and_lists_bit_exact(case, M, direct_max):
             assert L["U"][1].size > raw["U"][1].size  # some W/X moved to U
 
 
-@pytest.mark.parametrize("case,M,p", [("uniform4096", 64, 4), ("plummer3000", 16, 4), ("clustered", 8, 6)])
+@pytest.mark.parametrize("case,M,p", [("uniform4096", 64, 4), ("plummer3000", 16, 4), ("clustered", 8, 6),
+                                      ("plummer3000", 16, 7), ("uniform4096", 64, 8)])
 def test_fp64_matches_oracle(case, M, p):
     x, q = CASES[case]()
     pot_o, grad_o, _ = O.kifmm(x, q, p=p, leaf_cap=M)
@@ -105,6 +106,7 @@ def test_fp64_matches_oracle(case, M, p):
     plan.set_sources(_dev(x), _dev(q))
     pot, grad, energy = plan.evaluate(want_energy=True)
     assert plan.device_status() == 0
+    print("fp64 p=%d pot %.2e grad %.2e" % (p, O.rel_l2(pot.cpu().numpy(), pot_o), O.rel_l2(grad.cpu().numpy(), grad_o)))
     assert O.rel_l2(pot.cpu().numpy(), pot_o) <= 1e-12
     # At p = 6 the check-to-equivalent pseudo-inverse has condition number
     # 1.1e9; the downward check potentials agree to ~4e-14 (summation order),
@@ -112,7 +114,8 @@ def test_fp64_matches_oracle(case, M, p):
     # amplify that ~50x.  Gradients at p = 6 are held to 5e-12, all else 1e-12.
     grad_tol = 5e-12 if p >= 6 else 1e-12
     assert O.rel_l2(grad.cpu().numpy(), grad_o) <= grad_tol
-    assert energy.item() == pytest.approx(O.energy(q, pot_o), rel=1e-12)
+    # |U - U_o| <= 1/2 |q| |pot - pot_o| (Cauchy-Schwarz), with the pot bound above
+    assert abs(energy.item() - O.energy(q, pot_o)) <= 0.5 * np.linalg.norm(q) * 1e-12 * np.linalg.norm(pot_o)
 
 
 def _rsa(n, seed):
@@ -164,11 +167,13 @@ def test_reduced_precision_close_pairs(prec):
     assert eg <= O.rel_l2(grad_o, gd) + 2 * fg + 3e-7
 
 
-@pytest.mark.parametrize("case,M,p", [("uniform4096", 32, 6), ("plummer3000", 16, 6), ("uniform4096", 64, 4)])
+@pytest.mark.parametrize("case,M,p", [("uniform4096", 32, 6), ("plummer3000", 16, 6), ("uniform4096", 64, 4),
+                                      ("uniform4096", 64, 3), ("plummer3000", 16, 7), ("uniform4096", 64, 8)])
 def test_mixed_fp16_tensor_m2l(case, M, p):
     """Tensor-core M2L (3xFP16 split) agrees with the FP32 SIMT path: the
     downward check potentials match to FP32-level accuracy and the outputs to
-    within the FP32 rounding of the far field."""
+    within the FP32 rounding of the far field.  p = 3..6 run one column block
+    of 32..160 outputs per CTA; p = 7, 8 split the outputs over two."""
     x, q = CASES[case]()
     out = {}
     for prec in ("fp32", "mixed_fp16", "fp64"):
@@ -180,9 +185,37 @@ def test_mixed_fp16_tensor_m2l(case, M, p):
         u, d, res = plan.expansions()
         out[prec] = (d, pot.double().cpu().numpy())
     d64 = out["fp64"][0]
-    assert O.rel_l2(out["mixed_fp16"][0], d64) < 4e-6
-    assert O.rel_l2(out["fp32"][0], d64) < 4e-6
-    assert O.rel_l2(out["mixed_fp16"][1], out["fp64"][1]) < 4e-6
+    e_m, e_32 = O.rel_l2(out["mixed_fp16"][0], d64), O.rel_l2(out["fp32"][0], d64)
+    e_m32 = O.rel_l2(out["mixed_fp16"][0], out["fp32"][0])
+    e_pot = O.rel_l2(out["mixed_fp16"][1], out["fp64"][1])
+    print("p=%d d rel-L2 mixed %.2e fp32 %.2e mixed-vs-fp32 %.2e pot %.2e" % (p, e_m, e_32, e_m32, e_pot))
+    # the same (FP32, pinv_eps 1e-9) operators: the tensor-core M2L is as
+    # accurate as the FP32 SIMT path
+    assert e_m32 < 4e-6
+    # against FP64 (pinv_eps 1e-12): FP32 rounding plus the truncation difference
+    assert e_m < 6e-6 and e_32 < 6e-6
+    assert e_pot < 6e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed_fp16"])
+def test_reduced_precision_gains_from_higher_order(prec):
+    """With the FP32-based modes' regularised pseudo-inverse (pinv_eps 1e-9),
+    raising the surface order from 6 to 8 still buys accuracy (measured
+    against the exact field of the FP32-rounded inputs the device receives)."""
+    x, q = G.uniform_charges(6000, 77)
+    x = x.astype(np.float32).astype(np.float64)  # the exact field of the inputs the device gets
+    q = q.astype(np.float32).astype(np.float64)
+    pd, gd = O.direct(x, q)
+    errs = {}
+    for p in (6, 8):
+        plan = _plan(x, precision=prec, p=p, M=64, dtype=torch.float32)
+        plan.set_sources(_dev(x, torch.float32), _dev(q, torch.float32))
+        pot, grad, _ = plan.evaluate()
+        assert plan.device_status() == 0
+        errs[p] = (O.rel_l2(pot.double().cpu().numpy(), pd), O.rel_l2(grad.double().cpu().numpy(), gd))
+    print(prec, "p=6 pot %.2e grad %.2e | p=8 pot %.2e grad %.2e" % (errs[6] + errs[8]))
+    # gradients gain ~3x; potentials less, as they approach the ~1e-6 FP32 floor
+    assert errs[8][1] < errs[6][1] / 2 and errs[8][0] < errs[6][0]
 
 
 def test_single_leaf_equals_direct_sum():
