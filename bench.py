@@ -44,9 +44,12 @@ WORKLOADS = {
     "c2-64k": dict(kind="rsa", name="dem-coulomb-rsa-64k", n=65_536, p=6, leaf_cap=128, max_depth=20, seed=1001),
     "c3": dict(kind="clumps", name="rigid-clumps-200k-x4", n=800_000, clumps=200_000, p=6, leaf_cap=128,
                max_depth=20, seed=1002),
+    "c4": dict(kind="plummer", name="gravity-plummer-4M", n=4_000_000, p=8, leaf_cap=128, max_depth=12, seed=1003,
+               oracle_frac=0.03, ref_frac=0.005, compare="fp64"),
     "c5": dict(kind="batched", name="batched-64-systems-10k-200k", systems=64, p=6, leaf_cap=64, max_depth=20,
                seed=1004),
 }
+WORKLOADS["c2"]["compare"] = "fp32"
 
 
 def parse():
@@ -60,6 +63,9 @@ def parse():
     ap.add_argument("--accuracy-targets", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare", default="auto",
+                    help="also time this precision on the same workload (auto: the workload's comparison "
+                         "path, none: skip)")
     return ap.parse_args()
 
 
@@ -73,6 +79,10 @@ def make_inputs(w):
     elif w["kind"] == "clumps":
         x, q, off, centres = G.clumps(w["clumps"], w["seed"])
         meta = {"clump_offsets": off, "centres": centres, "coef": 1.0 / EPS0, "offsets": [0, len(x)]}
+    elif w["kind"] == "plummer":
+        # G = 1: masses as charges with coef -4 pi (Eq. 4 read as attractive)
+        x, q = G.plummer(w["n"], w["seed"])
+        meta = {"coef": -4.0 * np.pi, "offsets": [0, len(x)]}
     else:
         x, q, off = G.batched(w["systems"], w["seed"])
         meta = {"coef": 1.0, "offsets": [int(v) for v in off]}
@@ -199,18 +209,24 @@ def _oracle_sample(x, q, meta, w, frac):
         off = meta["offsets"]
         k = max(1, int(np.searchsorted(np.asarray(off[1:]), frac * off[-1])))
         return [(x[off[s]:off[s + 1]], q[off[s]:off[s + 1]]) for s in range(k)], f"systems 0..{k - 1}"
+    if w["kind"] == "plummer":
+        # the central cube holding about frac of the particles
+        r = np.abs(x - np.median(x, axis=0)).max(axis=1)
+        sel = r <= np.quantile(r, frac)
+        return [(x[sel], q[sel])], "central cube"
     lo = x.min(axis=0)
     side = (x.max(axis=0) - lo).max()
     sel = np.all(x - lo < side * frac ** (1.0 / 3.0), axis=1)
     return [(x[sel], q[sel])], "corner sub-cube"
 
 
-def cpu_baseline_leg(x, q, meta, w, n_targets, seed=0, frac=0.5):
+def cpu_baseline_leg(x, q, meta, w, n_targets, seed=0, frac=None):
     """CPU leg (the only place the benchmark runs the oracle): time the FP64
     oracle KIFMM on a bounded sample of the workload, and compute FP64
     direct-sum reference values on sampled targets for the accuracy figures."""
     from oracle import oracle as O
     O.build()
+    frac = w.get("oracle_frac", 0.5) if frac is None else frac
     parts, what = _oracle_sample(x, q, meta, w, frac)
     ops = O.operators(w["p"])
     t0 = time.perf_counter()
@@ -266,7 +282,7 @@ def run_reference(args, rank, world):
     O.build()
     w = WORKLOADS[args.workload]
     x, q, meta = make_inputs(w)
-    parts, what = _oracle_sample(x, q, meta, w, 0.1)
+    parts, what = _oracle_sample(x, q, meta, w, w.get("ref_frac", 0.1))
     ops = O.operators(w["p"])
     n_s = sum(p[0].shape[0] for p in parts)
 
@@ -303,8 +319,17 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w = WORKLOADS[args.workload]
     x, q, meta = make_inputs(w)
-    n = x.shape[0]
+    n_job = x.shape[0]
     coef, offsets = meta["coef"], meta["offsets"]
+    sharded = w["kind"] == "batched" and world > 1
+    if sharded:
+        # whole systems per rank, largest first onto the least-loaded rank; no collective on the data path
+        from paper_2512_09478_gb300 import shard
+        assignment = shard.assign_largest_first(np.diff(offsets), world)
+        x, q, offsets = shard.local_batch(x, q, offsets, assignment[rank])
+    n_sys_job = len(meta["offsets"]) - 1
+    meta = dict(meta, offsets=offsets)
+    n = x.shape[0]
     n_sys = len(offsets) - 1
     xt = torch.tensor(x, dtype=torch.float32, device=dev)
     qt = torch.tensor(q, dtype=torch.float32, device=dev)
@@ -395,7 +420,8 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = t.item()
     ms_per_step = total_ms / args.steps
-    value = world * n / (ms_per_step * 1e-3) / 1e6
+    units = n_job if sharded else world * n  # particles all ranks processed per step
+    value = units / (ms_per_step * 1e-3) / 1e6
 
     # end to end through the public API: pinned host inputs -> device -> step -> host outputs
     e2e = None
@@ -430,7 +456,11 @@ def run_ours(args, rank, world, local_rank):
             b.record(stream)
             torch.cuda.synchronize()
             e_ms += a.elapsed_time(b)
-        e2e = {"value": world * n / (e_ms / ke * 1e-3) / 1e6, "unit": UNIT,
+        if dist:
+            t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_ms = t.item()
+        e2e = {"value": units / (e_ms / ke * 1e-3) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(hx.numel() * 4 + hq.numel() * 4),
                "d2h_bytes_per_step": int(hpot.numel() * 4 + hgrad.numel() * 4),
                "step": "set_sources + evaluate" + (" + clump_reduce" if clumps else "")}
@@ -439,13 +469,16 @@ def run_ours(args, rank, world, local_rank):
         return
     calls = prof["calls"]
     per_call = {k: prof["ms"][k] / max(calls[k], 1) for k in prof["ms"] if calls[k] > 0}
-    dominant = max((k for k in per_call if k in ("m2l", "p2p", "tree")), key=lambda k: prof["ms"][k])
+    # dominant single kernel: the M2L (k_m2l_tc / gathered GEMM) or the leaf kernel
+    dominant = max((k for k in per_call if k in ("m2l", "p2p")), key=lambda k: prof["ms"][k])
     peaks = measured_peaks()
     roof = roofline_for(dominant, per_call[dominant], work, args.precision, peaks)
     other = {s: roofline_for(s, per_call[s], work, args.precision, peaks) for s in ("m2l", "p2p", "tree")
              if s in per_call}
-    cfg = {"workload": w["name"], "n": n, "systems": n_sys, "p": w["p"], "leaf_cap": w["leaf_cap"],
-           "precision": args.precision, "parallelism": f"replicas x{world}" if world > 1 else "1 gpu",
+    cfg = {"workload": w["name"], "n": n_job, "systems": n_sys_job, "p": w["p"], "leaf_cap": w["leaf_cap"],
+           "precision": args.precision,
+           "parallelism": ("1 gpu" if world == 1 else
+                           f"systems sharded over {world} gpus (largest first)" if sharded else f"replicas x{world}"),
            "l2": "flushed between steps (256 MiB write)", "boxes": work["info"]["n_boxes"],
            "max_level": work["info"]["max_level"],
            "step": ("graph replay of update_sources + evaluate (tree frozen)" if graph is not None else
@@ -453,28 +486,89 @@ def run_ours(args, rank, world, local_rank):
     if "solid_fraction" in meta:
         cfg["rsa_solid_fraction"] = round(meta["solid_fraction"], 4)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "strong" if sharded else "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
            "roofline": roof, "stage_rooflines": other,
            "stages_ms": {k: round(v / max(calls[k], 1) * (calls[k] / args.steps), 4)
                          for k, v in prof["ms"].items() if calls[k] > 0},
            "stages_note": prof_note, "gpu_launches": launches, "clocks": clk, "e2e": e2e}
+    ref = None
     if not args.no_cpu_baseline:
         base, ref = cpu_baseline_leg(x, q, meta, w, args.accuracy_targets)
         out["cpu_baseline"] = base
-        idx = ref["idx"]
-        p_gpu = pot.double().cpu().numpy()[idx] / coef  # back to Eq. 3 units for the comparison
-        g_gpu = grad.double().cpu().numpy()[idx] / coef
-        q64 = q.astype(np.float32).astype(np.float64)
-        acc = {"targets": int(idx.size), "vs": "FP64 direct sum over the FP32 inputs", "rel_l2_pot": rel_l2(p_gpu, ref["pot"]),
-               "rel_l2_grad": rel_l2(g_gpu, ref["grad"]),
-               "rel_l2_force": rel_l2(-q64[idx, None] * g_gpu, -q64[idx, None] * ref["grad"])}
+        out["accuracy"] = accuracy_of(ref, q, coef, pot, grad, force if clumps else None,
+                                      torque if clumps else None)
+    cmp_prec = w.get("compare") if args.compare == "auto" else (None if args.compare == "none" else args.compare)
+    if cmp_prec and cmp_prec != args.precision:
+        out["compare"] = compare_leg(args, w, cmp_prec, xt, qt, offsets, coef, n, n / (ms_per_step * 1e-3) / 1e6, stream, flush,
+                                     clumps, (coff, cref) if clumps else None, ref, q)
+    print(json.dumps(out), flush=True)
+
+
+def accuracy_of(ref, q, coef, pot, grad, force=None, torque=None):
+    """rel-L2 of the sampled outputs against the FP64 direct sums in ``ref``."""
+    idx = ref["idx"]
+    p_gpu = pot.double().cpu().numpy()[idx] / coef  # back to Eq. 3 units for the comparison
+    g_gpu = grad.double().cpu().numpy()[idx] / coef
+    q64 = q.astype(np.float32).astype(np.float64)
+    acc = {"targets": int(idx.size), "vs": "FP64 direct sum over the FP32 inputs",
+           "rel_l2_pot": rel_l2(p_gpu, ref["pot"]), "rel_l2_grad": rel_l2(g_gpu, ref["grad"]),
+           "rel_l2_force": rel_l2(-q64[idx, None] * g_gpu, -q64[idx, None] * ref["grad"])}
+    if force is not None:
+        cl = ref["clumps"]
+        acc["clumps"] = int(cl.size)
+        acc["rel_l2_clump_force"] = rel_l2(force.double().cpu().numpy()[cl] / coef, ref["F"])
+        acc["rel_l2_clump_torque"] = rel_l2(torque.double().cpu().numpy()[cl] / coef, ref["T"])
+    return acc
+
+
+def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, clumps, cl, ref, q):
+    """The same step with another precision of the library (plain FP32 SIMT
+    M2L for the DEM workload, the FP64 path for gravity): its throughput,
+    the speedup of the benchmarked precision over it, and its accuracy."""
+    import torch
+    from paper_2512_09478_gb300 import Plan
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = Plan(p=w["p"], leaf_cap=w["leaf_cap"], max_depth=w["max_depth"], precision=prec, coef=coef,
+                n_max=n, n_systems_max=len(offsets) - 1, dtype=dt)
+    x2, q2 = xt.to(dt), qt.to(dt)
+    pot = torch.empty(n, dtype=dt, device=xt.device)
+    grad = torch.empty(n, 3, dtype=dt, device=xt.device)
+    if clumps:
+        coff, cref = cl
+        cref = cref.to(dt)
+        force = torch.empty(cref.shape[0], 3, dtype=dt, device=xt.device)
+        torque = torch.empty_like(force)
+
+    def step():
+        plan.set_sources(x2, q2, offsets)
+        plan.evaluate(pot, grad)
         if clumps:
-            cl = ref["clumps"]
-            acc["clumps"] = int(cl.size)
-            acc["rel_l2_clump_force"] = rel_l2(force.double().cpu().numpy()[cl] / coef, ref["F"])
-            acc["rel_l2_clump_torque"] = rel_l2(torque.double().cpu().numpy()[cl] / coef, ref["T"])
-        out["accuracy"] = acc
+            plan.clump_reduce(coff, x2, q2, grad, cref, force, torque)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    k = 3 if prec == "fp64" else max(3, min(args.steps, 10))
+    ms = 0.0
+    for i in range(k):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+    v = n / (ms / k * 1e-3) / 1e6
+    res = {"precision": prec, "value": v, "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+           "speedup_of_benchmarked": value / v, "io_dtype": "f64" if prec == "fp64" else "f32"}
+    if ref is not None:
+        res["accuracy"] = accuracy_of(ref, q, coef, pot, grad, force if clumps else None,
+                                      torque if clumps else None)
+    return res
+
+
     print(json.dumps(out), flush=True)
 
 

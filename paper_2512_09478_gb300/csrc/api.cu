@@ -145,6 +145,7 @@ static cudaError_t ensure_box_arrays(Plan &P) {
         {&P.up_dens, esz * P.ns * cap},
         {&P.tmp_chk, esz * P.ns * cap},
         {&P.dn_dens, esz * P.ns * cap},
+        {(void **)&P.dbar, sizeof(double) * cap},
     };
     for (const A &a : arrs) KIFMM_CUDA_TRY(plan_alloc(P, a.p, a.bytes));
     P.list_cap = cap;
@@ -505,7 +506,16 @@ kifmm_status kifmm_copy_expansions(kifmm_plan *pl, double *u, double *d, double 
         return e;
     };
     if (u) API_CUDA(get(P.u_chk, u));
-    if (d) API_CUDA(get(P.d_chk, d));
+    if (d) {
+        API_CUDA(get(P.d_chk, d));
+        if (!P.f64) {
+            // FP32-based modes store the mean separately: return the whole check potential
+            std::vector<double> dbar((size_t)P.nb);
+            API_CUDA(cudaMemcpy(dbar.data(), P.dbar, sizeof(double) * P.nb, cudaMemcpyDeviceToHost));
+            for (int64_t b = 0; b < P.nb; ++b)
+                for (int k = 0; k < P.ns; ++k) d[(size_t)b * P.ns + k] += dbar[(size_t)b];
+        }
+    }
     if (res) API_CUDA(cudaMemcpy(res, P.res, sizeof(double) * 4 * P.n, cudaMemcpyDeviceToHost));
     return KIFMM_OK;
 }

@@ -20,6 +20,7 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s);  // m2l_tc.cu
 namespace {
 
 constexpr int kLeafThreads = 128;
+constexpr int kMaxNs = 6 * 9 * 9 + 2;  // n_s at the largest surface order, p = 10
 
 template <typename T>
 __device__ __forceinline__ T box_half(int level) {
@@ -84,8 +85,13 @@ __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict_
                       const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
                       const int32_t *__restrict__ first, const int32_t *__restrict__ cnt,
                       const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, int ns,
-                      T *__restrict__ d, const T *__restrict__ wts = nullptr, int adj = 0) {
+                      T *__restrict__ d, const T *__restrict__ wts = nullptr, int adj = 0,
+                      double *__restrict__ dbar = nullptr) {
+    // With dbar (FP32-based modes) the mean of this box's contribution goes
+    // to dbar and only the mean-free remainder to d.
     __shared__ T sx[kLeafThreads], sy[kLeafThreads], sz[kLeafThreads], sq[kLeafThreads];
+    __shared__ T cv[kMaxNs];
+    __shared__ double red[kLeafThreads / 32];
     const int b = blockIdx.x;
     if (nx[b] == 0) return;
     const int lb = lvl[b];
@@ -121,7 +127,24 @@ __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict_
                 for (int i = 0; i < m; ++i) acc += sq[i] * lap_pot<T>(px - sx[i], py - sy[i], pz - sz[i]);
             }
         }
-        if (j < ns) d[(size_t)b * ns + j] += adj ? acc : acc * hinv;
+        if (j < ns) {
+            const T v = adj ? acc : acc * hinv;
+            if (dbar) cv[j] = v; else d[(size_t)b * ns + j] += v;
+        }
+    }
+    if (dbar) {
+        __syncthreads();
+        double sum = 0.0;
+        for (int j = threadIdx.x; j < ns; j += blockDim.x) sum += (double)cv[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        const double mean = tot / ns;
+        for (int j = threadIdx.x; j < ns; j += blockDim.x) d[(size_t)b * ns + j] += (T)((double)cv[j] - mean);
+        if (threadIdx.x == 0) dbar[b] += mean;
     }
 }
 
@@ -142,14 +165,17 @@ struct ClassRanges {
     int64_t b[9];
 };
 
+// Operator blocks are [k][ld]: ld = n_s, or n_s + 1 when column n_s holds the
+// mean row of a mean-free check-to-check block (FP32-based modes).
 template <typename T>
 struct GatherM2L {
     const int32_t *vdense;
     const int *slot_off;
     const T *ops;
-    int ns;
+    int ns, ld;
     __device__ int src(int t, int s, int) const { return vdense[(size_t)t * kVSlots + s]; }
-    __device__ const T *op(int s, int cls) const { return ops + (size_t)slot_off[cls * kVSlots + s] * ns * ns; }
+    __device__ const T *op(int s, int cls) const { return ops + (size_t)slot_off[cls * kVSlots + s] * ns * ld; }
+    __device__ double mean_base(int, const double *) const { return 0.0; }
 };
 template <typename T>
 struct GatherChild {
@@ -158,27 +184,33 @@ struct GatherChild {
     int ns;
     __device__ int src(int t, int s, int) const { return child8[(size_t)t * 8 + s]; }
     __device__ const T *op(int s, int) const { return ops + (size_t)s * ns * ns; }
+    __device__ double mean_base(int, const double *) const { return 0.0; }
 };
-// One operator per class (L2L: the octant of the child).
+// One operator per class (L2L: the octant of the child); the child inherits
+// the parent's mean.
 template <typename T>
 struct GatherParent {
     const int32_t *parent;
     const T *ops;
-    int ns;
+    int ns, ld;
     __device__ int src(int t, int, int) const { return parent[t]; }
-    __device__ const T *op(int, int cls) const { return ops + (size_t)cls * ns * ns; }
+    __device__ const T *op(int, int cls) const { return ops + (size_t)cls * ns * ld; }
+    __device__ double mean_base(int t, const double *dbar) const { return dbar[parent[t]]; }
 };
 template <typename T>
 struct GatherSelf {
     const T *op0;
     __device__ int src(int t, int, int) const { return t; }
     __device__ const T *op(int, int) const { return op0; }
+    __device__ double mean_base(int, const double *) const { return 0.0; }
 };
 
+// With dbar: output column n_s (operator column n_s, the mean row) goes to
+// dbar[t] (FP64, plus the functor's mean_base) instead of out.
 template <typename T, class G>
 __global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ targets, ClassRanges cr,
-                                               int nslots, int ns, const T *__restrict__ in,
-                                               T *__restrict__ out, int accumulate) {
+                                               int nslots, int ns, int ld, const T *__restrict__ in,
+                                               T *__restrict__ out, int accumulate, double *dbar) {
     __shared__ __align__(16) T Us[kGK][kGT];
     __shared__ __align__(16) T Ms[kGK][kGJ];
     __shared__ int32_t tgt[kGT];
@@ -228,7 +260,7 @@ __global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ 
             for (int r = 0; r < kRM; ++r) {
                 const int e = threadIdx.x + 256 * r;
                 const int k = e / kGJ, j = e - k * kGJ;
-                rm[r] = (k0 + k < ns && j0 + j < ns) ? M[(size_t)(k0 + k) * ns + j0 + j] : T(0);
+                rm[r] = (k0 + k < ns && j0 + j < ld) ? M[(size_t)(k0 + k) * ld + j0 + j] : T(0);
             }
         };
         load(0);
@@ -277,10 +309,12 @@ __global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ 
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
             const int j = j0 + tx + 32 * c;
+            const T v = kTwoLevel ? run[a][c] : acc[a][c];
             if (j < ns) {
-                const T v = kTwoLevel ? run[a][c] : acc[a][c];
                 T *o = out + (size_t)t * ns + j;
                 *o = accumulate ? *o + v : v;
+            } else if (j == ns && dbar) {
+                dbar[t] = (accumulate ? dbar[t] : 0.0) + (double)v + g.mean_base(t, dbar);
             }
         }
     }
@@ -334,6 +368,7 @@ struct LeafCtx {
     const uint32_t *u_ptr, *w_ptr;
     const int32_t *u_idx, *w_idx;
     int ns;
+    const double *dbar;  // per-box mean of the downward check potential, or nullptr
 };
 
 // Source weights of the leaf stage.  Forward: own surface dn_dens * h_b,
@@ -441,6 +476,7 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
             const double mine = (double)L.acc[k][c] + (double)L.cmp[k][c];
             tot[c] = mine + __shfl_xor_sync(0xffffffffu, mine, 16);
         }
+        if (C.dbar) tot[0] += C.dbar[b];  // the constant part of the local expansion
         const int i = tbase + (lane & 15) + 16 * k;
         if (half == 0 && i < n) res[f + i] = make_double4(tot[0], tot[1], tot[2], tot[3]);
     }
@@ -551,14 +587,15 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 // Classes c < ncls own targets [starts[c], starts[c + 1]); one launch.
 template <typename T, class G>
 void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *starts, int ncls, int nslots,
-                   const T *in, T *out, int accumulate, cudaStream_t s) {
+                   const T *in, T *out, int accumulate, cudaStream_t s, int ld = 0, double *dbar = nullptr) {
     ClassRanges cr;
     int64_t most = 0;
     for (int c = 0; c <= ncls; ++c) cr.b[c] = starts[c];
     for (int c = 0; c < ncls; ++c) most = std::max<int64_t>(most, starts[c + 1] - starts[c]);
     if (most <= 0) return;
-    dim3 grid(grid_for(most, kGT), ncls, grid_for(P.ns, kGJ));
-    ++g_launches, k_ggemm<T, G><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, in, out, accumulate);
+    if (ld == 0) ld = P.ns;
+    dim3 grid(grid_for(most, kGT), ncls, grid_for(ld, kGJ));
+    ++g_launches, k_ggemm<T, G><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out, accumulate, dbar);
 }
 
 template <typename T, class G>
@@ -591,25 +628,28 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     // interactions
     stage_begin(P, KIFMM_STAGE_M2L, s);
     KIFMM_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(T) * (size_t)P.nb * ns, s));
+    const bool split_mean = !P.f64;  // FP32-based modes: d = dbar (FP64) + mean-free FP32 vector
+    if (split_mean) KIFMM_CUDA_TRY(cudaMemsetAsync(P.dbar, 0, sizeof(double) * (size_t)P.nb, s));
     const bool tensor = (P.desc.precision == KIFMM_MIXED_TF32 || P.desc.precision == KIFMM_MIXED_FP16);
     if (tensor) {
         KIFMM_CUDA_TRY(m2l_tensor(P, s));
     } else {
-        ggemm_classes<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.m2l_t, ns}, P.part_list[0],
-                         P.part_start[0].data(), 8, kVSlots, u, d, 0, s);
+        ggemm_classes<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.m2l_t, ns, P.op_ld}, P.part_list[0],
+                         P.part_start[0].data(), 8, kVSlots, u, d, 0, s, P.op_ld, split_mean ? P.dbar : nullptr);
     }
     stage_end(P, KIFMM_STAGE_M2L, s);
     if (P.n_x > 0) {
         stage_begin(P, KIFMM_STAGE_P2L, s);
         ++g_launches, k_p2l<T><<<(unsigned)P.nb, kLeafThreads, 0, s>>>(P.nx, P.xdense, P.lvl, P.cx, P.cy, P.cz,
-                                                                        P.first, P.cnt, pts, surf, ns, d);
+                                                                        P.first, P.cnt, pts, surf, ns, d, nullptr,
+                                                                        0, split_mean ? P.dbar : nullptr);
         stage_end(P, KIFMM_STAGE_P2L, s);
     }
     // downward pass: per level, per octant class of the child
     stage_begin(P, KIFMM_STAGE_L2L, s);
     for (int l = 1; l <= P.max_level; ++l)
-        ggemm_classes<T>(P, GatherParent<T>{P.parent, (const T *)P.l2l_t, ns}, P.part_list[3],
-                         P.part_start[3].data() + 8 * l, 8, 1, d, d, 1, s);
+        ggemm_classes<T>(P, GatherParent<T>{P.parent, (const T *)P.l2l_t, ns, P.op_ld}, P.part_list[3],
+                         P.part_start[3].data() + 8 * l, 8, 1, d, d, 1, s, P.op_ld, split_mean ? P.dbar : nullptr);
     stage_end(P, KIFMM_STAGE_L2L, s);
     KIFMM_CUDA_TRY(cudaGetLastError());
     // leaves: equivalent densities (two-step pseudo-inverse), then L2P + M2P + P2P
@@ -623,7 +663,8 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     ggemm<T>(P, GatherSelf<T>{(const T *)P.dn_v_t}, P.leaves, 0, P.n_leaves, 1, tmp, (T *)P.dn_dens, 0, s);
     stage_end(P, KIFMM_STAGE_LEAF, s);
     stage_begin(P, KIFMM_STAGE_P2P, s);
-    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns};
+    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns,
+              split_mean ? P.dbar : nullptr};
     const LeafW<T> W{(const T *)P.dn_dens, 1, (const T *)P.up_dens, 1, nullptr};
     ++g_launches, k_leaf_all<T><<<grid_for(P.n_leaves, kLW), 32 * kLW, 0, s>>>(C, P.n_leaves, P.leaves, pts, surf,
                                                                                W, res);
@@ -722,14 +763,14 @@ cudaError_t backward_t(Plan &P, const void *w_user, const void *grad_user, void 
         ggemm<T>(P, GatherChild<T>{P.child8, (const T *)P.adj_l2l, ns}, P.part_list[1], P.part_start[1][1 + l],
                  P.part_start[1][2 + l], 8, db, db, 1, s);
     // M2L^T (V lists are symmetric; operator at the negated offset, transposed)
-    ggemm_classes<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.adj_m2l, ns}, P.part_list[0],
+    ggemm_classes<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.adj_m2l, ns, ns}, P.part_list[0],
                      P.part_start[0].data(), 8, kVSlots, db, ub, 1, s);
     // M2M^T, top-down
     for (int l = 1; l <= P.max_level; ++l)
-        ggemm_classes<T>(P, GatherParent<T>{P.parent, (const T *)P.adj_m2m, ns}, P.part_list[3],
+        ggemm_classes<T>(P, GatherParent<T>{P.parent, (const T *)P.adj_m2m, ns, ns}, P.part_list[3],
                          P.part_start[3].data() + 8 * l, 8, 1, ub, ub, 1, s);
     // P2M^T (own UC surface, u-bar), P2L^T (W boxes' DC surfaces, d-bar), P2P^T (weights w)
-    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns};
+    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns, nullptr};
     const LeafW<T> W{ub, 0, db, 0, ws};
     ++g_launches, k_leaf_all<T><<<grid_for(P.n_leaves, kLW), 32 * kLW, 0, s>>>(C, P.n_leaves, P.leaves, pts, surf,
                                                                                W, res);

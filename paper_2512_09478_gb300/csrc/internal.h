@@ -41,8 +41,14 @@ struct Plan {
     // Composite translation operators in "check-potential" form, stored
     // transposed ([o][k][j]) in the compute type:
     void *m2m_t = nullptr;      // [8][ns][ns]   u(child)  -> u(parent)
-    void *l2l_t = nullptr;      // [8][ns][ns]   d(parent) -> d(child)
-    void *m2l_t = nullptr;      // [316][ns][ns] u(source) -> d(target)
+    void *l2l_t = nullptr;      // [8][ns][op_ld]   d(parent) -> d(child)
+    void *m2l_t = nullptr;      // [316][ns][op_ld] u(source) -> d(target)
+    // FP32-based modes: l2l_t and m2l_t are mean-free over their outputs,
+    // stored [blk][k][ns + 1] with the mean row in column ns (op_ld = ns + 1;
+    // ns otherwise); d is then the mean-free part and dbar (FP64, per box)
+    // the mean of the downward check potential.
+    int op_ld = 0;
+    double *dbar = nullptr;     // [nb]
     // Two-step pseudo-inverses for leaf evaluation: dens = V (W chk),
     // W = diag(sinv) U^T, both stored transposed ([k][j]).
     void *up_w_t = nullptr, *up_v_t = nullptr;

@@ -168,6 +168,7 @@ struct TileArgs {
     const int32_t *lvl;
     const float *level_unscale;  // 1 / (sigma_A(level) sigma_B)
     float *d;                 // [nb][ns]
+    double *dbar;             // [nb] output column ns (the mean row), or nullptr
     int ns, kp, np, nstages;  // np: operator rows (output columns) incl. padding
     int *status;
 };
@@ -377,8 +378,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             const int col0 = cb * NT + c_base;
             float *out = a.d + (size_t)t * a.ns + col0;
 #pragma unroll
-            for (int j = 0; j < NT / 2; ++j)
+            for (int j = 0; j < NT / 2; ++j) {
                 if (col0 + j < a.ns) out[j] = acc[j] * scale;
+                else if (col0 + j == a.ns && a.dbar) a.dbar[t] = (double)(acc[j] * scale);
+            }
         }
     }
     tc_fence_before();
@@ -434,12 +437,13 @@ __global__ void k_split_u(int64_t nb, int ns, int kp, const float *__restrict__ 
     ul[idx] = __float2half_rn(x - __half2float(h));
 }
 
-// Operator B[j][k] = M_o[j][k] (m2l_t is stored transposed, [o][k][j]) split
+// Operator B[j][k] = M_o[j][k] (m2l_t is stored transposed, [o][k][ld], with
+// the mean row as output j = ns when ld = ns + 1) split
 // into FP16 hi/lo and stored K-block-major: block (o, kb) holds rows j < np of
 // 32 elements in the 64-byte swizzled K-major form (16-byte chunk c of row j
 // at chunk position c ^ ((j >> 1) & 3)), so one linear copy of the block
 // lands in shared memory ready for the tensor core.
-__global__ void k_split_ops(int nops, int ns, int np, int kp, const float *__restrict__ m2l_t, float sigma,
+__global__ void k_split_ops(int nops, int ns, int ld, int np, int kp, const float *__restrict__ m2l_t, float sigma,
                             __half *__restrict__ bh, __half *__restrict__ bl) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)nops * np * kp;
@@ -451,7 +455,7 @@ __global__ void k_split_ops(int nops, int ns, int np, int kp, const float *__res
     const int j = rem / kKBlock, pos = rem % kKBlock;   // pos: swizzled position in the row
     const int c = (pos >> 3) ^ ((j >> 1) & 3), e = pos & 7;
     const int k = kb * kKBlock + c * 8 + e;
-    const float x = (j < ns && k < ns) ? m2l_t[((size_t)o * ns + k) * ns + j] * sigma : 0.f;
+    const float x = (j < ld && k < ns) ? m2l_t[((size_t)o * ns + k) * ld + j] * sigma : 0.f;
     const __half h = __float2half_rn(x);
     bh[idx] = h;
     bl[idx] = __float2half_rn(x - __half2float(h));
@@ -514,7 +518,7 @@ cudaError_t m2l_tensor_setup(Plan &P) {
     // Output columns per CTA: at most 160 (three partial accumulators fit
     // TMEM; the drain warps keep 80 running sums each in registers); larger
     // surfaces (p >= 7) are split into column blocks over blockIdx.y.
-    const int np0 = round_up(ns, 32);
+    const int np0 = round_up(ns + 1, 32);  // room for the mean row (FP32-based modes)
     S.ncb = (np0 + 159) / 160;
     S.nt = round_up((np0 + S.ncb - 1) / S.ncb, 32);
     S.np = S.nt * S.ncb;
@@ -526,7 +530,7 @@ cudaError_t m2l_tensor_setup(Plan &P) {
     unsigned *dmax = nullptr;
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&dmax, sizeof(unsigned)));
     KIFMM_CUDA_TRY(cudaMemset(dmax, 0, sizeof(unsigned)));
-    const int64_t nm = (int64_t)kNumM2L * ns * ns;
+    const int64_t nm = (int64_t)kNumM2L * ns * P.op_ld;
     ++g_launches, k_absmax_f32<<<256, 256>>>(nm, (const float *)P.m2l_t, dmax);
     unsigned mbits = 0;
     KIFMM_CUDA_TRY(cudaMemcpy(&mbits, dmax, sizeof(unsigned), cudaMemcpyDeviceToHost));
@@ -538,7 +542,7 @@ cudaError_t m2l_tensor_setup(Plan &P) {
     const size_t nb = (size_t)kNumM2L * S.np * S.kp;
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.bh, sizeof(__half) * nb));
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.bl, sizeof(__half) * nb));
-    ++g_launches, k_split_ops<<<(unsigned)((nb + 255) / 256), 256>>>(kNumM2L, ns, S.np, S.kp, (const float *)P.m2l_t,
+    ++g_launches, k_split_ops<<<(unsigned)((nb + 255) / 256), 256>>>(kNumM2L, ns, P.op_ld, S.np, S.kp, (const float *)P.m2l_t,
                                                                      S.sigma_b, S.bh, S.bl);
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.level_max, sizeof(unsigned) * 32));
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.level_sigma, sizeof(float) * 32));
@@ -592,6 +596,7 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {
     a.lvl = P.lvl;
     a.level_unscale = S.level_unscale;
     a.d = (float *)P.d_chk;
+    a.dbar = (P.op_ld > P.ns) ? P.dbar : nullptr;
     a.ns = P.ns;
     a.kp = S.kp;
     a.np = S.np;

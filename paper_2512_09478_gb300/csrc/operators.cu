@@ -139,6 +139,32 @@ __global__ void k_to_f32(const double *in, float *out, size_t n) {
 }
 
 // W_t[j][m] = sinv[m] * Ut[m][j]
+// Split each check-to-check block [k][j] (input k, output j) into its mean
+// over the outputs, mean[blk][k] = (1/n) sum_j A[k][j], and the mean-free
+// remainder A[k][j] - mean[blk][k].  One thread per (block, k) row.
+__global__ void k_center_rows(int n, int nb, double *A, double *mean) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (int64_t)nb * n) return;
+    double *row = A + r * n;
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += row[j];
+    const double m = s / n;
+    for (int j = 0; j < n; ++j) row[j] -= m;
+    mean[r] = m;
+}
+
+// [nb][n][n] mean-free blocks + [nb][n] mean rows -> FP32 [nb][n][n + 1]
+// with the mean in column n.
+__global__ void k_pack_mean_col(int n, int nb, const double *__restrict__ A, const double *__restrict__ mean,
+                                float *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ld = n + 1;
+    if (i >= (int64_t)nb * n * ld) return;
+    const int64_t row = i / ld;  // blk * n + k
+    const int j = (int)(i - row * ld);
+    out[i] = (float)((j < n) ? A[row * n + j] : mean[row]);
+}
+
 __global__ void k_make_wt(int n, const double *Ut, const double *sinv, double *Wt) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * n) return;
@@ -346,6 +372,26 @@ cudaError_t build_operators(Plan &P, std::string &err) {
     }
     KIFMM_CUDA_TRY(cudaDeviceSynchronize());
     cudaFree(dT);
+    P.op_ld = n;
+    if (!P.f64) {
+        // FP32-based modes carry the downward check potential as a per-box
+        // mean (FP64 scalar) plus a mean-free FP32 vector: the L2L and M2L
+        // blocks are stored mean-free, [k][n + 1] with the mean row in
+        // column n, so the same GEMMs produce the mean contributions.
+        double *dMean = nullptr;
+        KIFMM_CUDA_TRY(cudaMalloc(&dMean, sizeof(double) * (8 + kNumM2L) * n));
+        const int64_t rows = (int64_t)(8 + kNumM2L) * n;
+        k_center_rows<<<(unsigned)((rows + 255) / 256), 256>>>(n, 8 + kNumM2L, dOut + 8 * nn, dMean);
+        P.op_ld = n + 1;
+        const size_t blk1 = (size_t)n * (n + 1);
+        KIFMM_CUDA_TRY(plan_alloc(P, &P.l2l_t, sizeof(float) * 8 * blk1));
+        KIFMM_CUDA_TRY(plan_alloc(P, &P.m2l_t, sizeof(float) * kNumM2L * blk1));
+        k_pack_mean_col<<<(unsigned)((8 * blk1 + 255) / 256), 256>>>(n, 8, dOut + 8 * nn, dMean, (float *)P.l2l_t);
+        k_pack_mean_col<<<(unsigned)((kNumM2L * blk1 + 255) / 256), 256>>>(n, kNumM2L, dOut + 16 * nn, dMean + 8 * n,
+                                                                         (float *)P.m2l_t);
+        KIFMM_CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(dMean);
+    }
     // surfaces
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf64, sizeof(double) * 3 * n));
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf32, sizeof(float) * 3 * n));

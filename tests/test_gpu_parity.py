@@ -171,9 +171,10 @@ def test_reduced_precision_close_pairs(prec):
                                       ("uniform4096", 64, 3), ("plummer3000", 16, 7), ("uniform4096", 64, 8)])
 def test_mixed_fp16_tensor_m2l(case, M, p):
     """Tensor-core M2L (3xFP16 split) agrees with the FP32 SIMT path: the
-    downward check potentials match to FP32-level accuracy and the outputs to
-    within the FP32 rounding of the far field.  p = 3..6 run one column block
-    of 32..160 outputs per CTA; p = 7, 8 split the outputs over two."""
+    downward check potentials match to FP32-level accuracy, and the
+    potentials are as close to the exact sum as the FP64 path's up to the
+    FP32 floor.  p = 3..6 run one column block of 32..160 outputs per CTA;
+    p = 7, 8 split the outputs over two."""
     x, q = CASES[case]()
     out = {}
     for prec in ("fp32", "mixed_fp16", "fp64"):
@@ -184,17 +185,19 @@ def test_mixed_fp16_tensor_m2l(case, M, p):
         assert plan.device_status() == 0
         u, d, res = plan.expansions()
         out[prec] = (d, pot.double().cpu().numpy())
-    d64 = out["fp64"][0]
-    e_m, e_32 = O.rel_l2(out["mixed_fp16"][0], d64), O.rel_l2(out["fp32"][0], d64)
     e_m32 = O.rel_l2(out["mixed_fp16"][0], out["fp32"][0])
-    e_pot = O.rel_l2(out["mixed_fp16"][1], out["fp64"][1])
-    print("p=%d d rel-L2 mixed %.2e fp32 %.2e mixed-vs-fp32 %.2e pot %.2e" % (p, e_m, e_32, e_m32, e_pot))
+    pd, _ = O.direct(x, q)
+    pd32, _ = O.direct(x.astype(np.float32).astype(np.float64), q.astype(np.float32).astype(np.float64))
+    e_pm = O.rel_l2(out["mixed_fp16"][1], pd32)
+    e_p64 = O.rel_l2(out["fp64"][1], pd)
+    print("p=%d d mixed-vs-fp32 %.2e | pot vs direct: mixed %.2e fp64 %.2e" % (p, e_m32, e_pm, e_p64))
     # the same (FP32, pinv_eps 1e-9) operators: the tensor-core M2L is as
     # accurate as the FP32 SIMT path
     assert e_m32 < 4e-6
-    # against FP64 (pinv_eps 1e-12): FP32 rounding plus the truncation difference
-    assert e_m < 6e-6 and e_32 < 6e-6
-    assert e_pot < 6e-6
+    # against the exact sum: the FP64 path's method error plus the FP32 floor
+    # (the FP32 modes pass the mean of the local expansion down exactly, which
+    # at low p differs from the plain method by its own approximation error)
+    assert e_pm < e_p64 + 4e-6
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed_fp16"])
