@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--accuracy-targets", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="fixed tile shapes (default: the library tunes them on the first, untimed, evaluate)")
     ap.add_argument("--compare", default="auto",
                     help="also time this precision on the same workload (auto: the workload's comparison "
                          "path, none: skip)")
@@ -334,7 +336,7 @@ def run_ours(args, rank, world, local_rank):
     xt = torch.tensor(x, dtype=torch.float32, device=dev)
     qt = torch.tensor(q, dtype=torch.float32, device=dev)
     plan = Plan(p=w["p"], leaf_cap=w["leaf_cap"], max_depth=w["max_depth"], precision=args.precision, coef=coef,
-                n_max=n, n_systems_max=n_sys, dtype=torch.float32)
+                n_max=n, n_systems_max=n_sys, dtype=torch.float32, autotune=not args.no_autotune)
     pot = torch.empty(n, dtype=torch.float32, device=dev)
     grad = torch.empty(n, 3, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -485,6 +487,9 @@ def run_ours(args, rank, world, local_rank):
                     "set_sources + evaluate" + (" + clump_reduce" if clumps else ""))}
     if "solid_fraction" in meta:
         cfg["rsa_solid_fraction"] = round(meta["solid_fraction"], 4)
+    tun = plan.tuning()
+    cfg["tiles"] = {"autotuned": tun["tuned_leaf"], "m2l_stages": tun["m2l_stages"],
+                    "leaf_tpl_x_groups_per_8_targets": ["%dx%d" % t for t in tun["leaf_tiles"]]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
            "scaling": "strong" if sharded else "weak",
@@ -531,7 +536,7 @@ def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, c
     from paper_2512_09478_gb300 import Plan
     dt = torch.float64 if prec == "fp64" else torch.float32
     plan = Plan(p=w["p"], leaf_cap=w["leaf_cap"], max_depth=w["max_depth"], precision=prec, coef=coef,
-                n_max=n, n_systems_max=len(offsets) - 1, dtype=dt)
+                n_max=n, n_systems_max=len(offsets) - 1, dtype=dt, autotune=not args.no_autotune)
     x2, q2 = xt.to(dt), qt.to(dt)
     pot = torch.empty(n, dtype=dt, device=xt.device)
     grad = torch.empty(n, 3, dtype=dt, device=xt.device)

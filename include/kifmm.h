@@ -78,7 +78,12 @@ typedef struct {
                             1e-9 in the FP32-based modes.  In FP64 mode it must
                             not lie within a factor 1.1 of any
                             sigma_i / sigma_max (KIFMM_ERR_ARG otherwise).    */
-    int autotune;        /* 1: time candidate tile shapes at plan creation     */
+    int autotune;        /* 1: on the first evaluate (outside stream capture),
+                            time the candidate leaf-kernel tilings and
+                            tensor-core M2L pipeline depths on the live tree
+                            and keep the fastest (synchronises once; results
+                            may then differ from an untuned plan's in the
+                            last FP32 bits).  0: fixed defaults.             */
     int direct_max;      /* a W/X interaction whose finer box (the W member,
                             or the owner of the X list) is a leaf holding at
                             most this many points is summed directly, as a
@@ -234,6 +239,21 @@ typedef struct {
 kifmm_status kifmm_profile_enable(kifmm_plan *plan, int enable);
 /* out (host): accumulated times since the last read; resets them. */
 kifmm_status kifmm_profile_read(kifmm_plan *plan, kifmm_profile_t *out);
+
+/* Tile shapes in use (no counterpart in the paper: the benchmark spec asks for
+ * M2L/P2P tile shapes chosen by an autotuner).  tuned: bit 0 leaf kernel,
+ * bit 1 tensor-core M2L.  m2l_stages: shared-memory pipeline depth of the
+ * tensor-core M2L (0 when the plan has none).  Leaf kernel: for a leaf with
+ * r targets still to cover, bucket min((r - 1) / 8, 15) selects leaf_tpl
+ * targets per lane and leaf_groups source groups (a warp covers
+ * 32 / groups * tpl targets per pass).  Host memory; no device work. */
+typedef struct {
+    int tuned;
+    int m2l_stages;
+    int leaf_tpl[16];
+    int leaf_groups[16];
+} kifmm_tuning_t;
+kifmm_status kifmm_get_tuning(kifmm_plan *plan, kifmm_tuning_t *out);
 
 /* ------------------------------------------------------------------------
  * Introspection (tests and tools).  All outputs are host buffers sized by

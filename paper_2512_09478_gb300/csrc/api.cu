@@ -57,6 +57,26 @@ static cudaError_t profile_collect(Plan &P) {
     return cudaSuccess;
 }
 
+LeafTiling leaf_tiling_candidate(int c) {
+    static const int fam[kLeafTilingCandidates][2] = {{4, 2}, {2, 2}, {4, 1}, {2, 1}, {1, 1}, {1, 2}};
+    const int gs = fam[c][0], gm = fam[c][1];
+    LeafTiling t{};
+    for (int i = 0; i < kLeafBuckets; ++i) {
+        const int r = (i == kLeafBuckets - 1) ? 128 : 8 * (i + 1);
+        const int g = (r <= 32) ? gs : (r <= 64 ? gm : 1);
+        const int tpl = std::min(4, std::max(1, (r * g + 31) / 32));
+        t.id[i] = (unsigned char)((g == 4 ? 0 : g == 2 ? 4 : 8) + tpl - 1);
+    }
+    return t;
+}
+
+bool tuning_wanted(const Plan &P, cudaStream_t s) {
+    if (!P.desc.autotune) return false;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st == cudaStreamCaptureStatusNone;
+}
+
 cudaError_t plan_alloc(Plan &P, void **ptr, size_t bytes) {
     if (*ptr) {
         for (auto it = P.owned.begin(); it != P.owned.end(); ++it)
@@ -215,6 +235,7 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     // ~30x and so does the FP32 rounding of every translation).
     P.eps = (d.pinv_eps != 0.0) ? d.pinv_eps : (P.f64 ? 1e-12 : 1e-9);
     P.direct_thr = (d.direct_max < 0) ? -1 : (d.direct_max == 0 ? P.ns : d.direct_max);
+    P.leaf_tile = leaf_tiling_candidate(0);
     auto fail = [&](kifmm_status st) {
         kifmm_plan_destroy(pl);
         (void)cudaGetLastError();
@@ -432,6 +453,18 @@ kifmm_status kifmm_profile_read(kifmm_plan *pl, kifmm_profile_t *out) {
     }
     out->launches = P.launches;
     P.launches = 0;
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_get_tuning(kifmm_plan *pl, kifmm_tuning_t *out) {
+    if (!pl || !out) return KIFMM_ERR_ARG;
+    const Plan &P = pl->P;
+    out->tuned = (P.tuned_leaf ? 1 : 0) | (P.tuned_m2l ? 2 : 0);
+    out->m2l_stages = m2l_tensor_stages(P);
+    for (int i = 0; i < kLeafBuckets; ++i) {
+        out->leaf_tpl[i] = leaf_tile_tpl(P.leaf_tile.id[i]);
+        out->leaf_groups[i] = leaf_tile_groups(P.leaf_tile.id[i]);
+    }
     return KIFMM_OK;
 }
 

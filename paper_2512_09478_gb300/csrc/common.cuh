@@ -60,9 +60,13 @@ struct Vec4<double> {
 
 template <typename T>
 __device__ __forceinline__ T rsqrt_t(T x);
+// FP32: the hardware approximation (rsqrt.approx, relative error below
+// 2^-22.9), flushing subnormal inputs; callers exclude r = 0 themselves.
 template <>
 __device__ __forceinline__ float rsqrt_t<float>(float x) {
-    return rsqrtf(x);
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) {

@@ -158,7 +158,7 @@ __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict_
 // registers.  Used for M2L (189 V slots), M2M (8 child octants), L2L (parent)
 // and the two factors of the leaf pseudo-inverses.
 // ---------------------------------------------------------------------------
-constexpr int kGT = 64, kGJ = 160, kGK = 16;
+constexpr int kGK = 16;
 
 // Target ranges of up to 8 classes (blockIdx.y = class) in one launch.
 struct ClassRanges {
@@ -207,17 +207,20 @@ struct GatherSelf {
 
 // With dbar: output column n_s (operator column n_s, the mean row) goes to
 // dbar[t] (FP64, plus the functor's mean_base) instead of out.
-template <typename T, class G>
-__global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ targets, ClassRanges cr,
-                                               int nslots, int ns, int ld, const T *__restrict__ in,
-                                               T *__restrict__ out, int accumulate, double *dbar) {
-    __shared__ __align__(16) T Us[kGK][kGT];
-    __shared__ __align__(16) T Ms[kGK][kGJ];
-    __shared__ int32_t tgt[kGT];
-    __shared__ int32_t src[kGT];
+// Tile: NTY warps; thread (tx, ty) owns targets RT ty .. RT ty + RT-1 and
+// outputs tx + 32 c (c < RC): TT = NTY RT targets by TJ = 32 RC outputs.
+template <typename T, class G, int NTY, int RT, int RC>
+__global__ void __launch_bounds__(32 * NTY) k_ggemm(G g, const int32_t *__restrict__ targets, ClassRanges cr,
+                                                    int nslots, int ns, int ld, const T *__restrict__ in,
+                                                    T *__restrict__ out, int accumulate, double *dbar) {
+    constexpr int TT = NTY * RT, TJ = 32 * RC, NT = 32 * NTY;
+    __shared__ __align__(16) T Us[kGK][TT];
+    __shared__ __align__(16) T Ms[kGK][TJ];
+    __shared__ int32_t tgt[TT];
+    __shared__ int32_t src[TT];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int cls = blockIdx.y;
-    const int j0 = blockIdx.z * kGJ;  // output columns [j0, j0 + kGJ)
+    const int j0 = blockIdx.z * TJ;  // output columns [j0, j0 + TJ)
     int64_t t_begin = 0, t_end = 0;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
@@ -225,89 +228,92 @@ __global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ 
             t_begin = cr.b[c];
             t_end = cr.b[c + 1];
         }
-    const int64_t t0 = t_begin + (int64_t)blockIdx.x * kGT;
+    const int64_t t0 = t_begin + (int64_t)blockIdx.x * TT;
     if (t0 >= t_end) return;  // uniform for the block
-    if (threadIdx.x < kGT) tgt[threadIdx.x] = (t0 + threadIdx.x < t_end) ? targets[t0 + threadIdx.x] : -1;
+    if (threadIdx.x < TT) tgt[threadIdx.x] = (t0 + threadIdx.x < t_end) ? targets[t0 + threadIdx.x] : -1;
     // FP32: each slot sums into a fresh partial that is then added to the
     // running total, so no rounding chain is longer than one slot's n_s terms.
     constexpr bool kTwoLevel = sizeof(T) == 4;
-    T acc[8][5], run[8][5];
+    T acc[RT][RC], run[RT][RC];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < RT; ++a)
 #pragma unroll
-        for (int c = 0; c < 5; ++c) acc[a][c] = run[a][c] = T(0);
+        for (int c = 0; c < RC; ++c) acc[a][c] = run[a][c] = T(0);
     const int nk = (ns + kGK - 1) / kGK;
     __syncthreads();
     for (int s = 0; s < nslots; ++s) {
-        if (threadIdx.x < kGT) {
+        if (threadIdx.x < TT) {
             const int32_t t = tgt[threadIdx.x];
             src[threadIdx.x] = (t >= 0) ? g.src(t, s, cls) : -1;
         }
         const T *M = g.op(s, cls);
         __syncthreads();
-        constexpr int kRU = kGT * kGK / 256, kRM = kGK * kGJ / 256;
+        constexpr int kRU = (TT * kGK + NT - 1) / NT, kRM = (kGK * TJ + NT - 1) / NT;
         T ru[kRU], rm[kRM];
         auto load = [&](int kc) {
             const int k0 = kc * kGK;
 #pragma unroll
             for (int r = 0; r < kRU; ++r) {
-                const int e = threadIdx.x + 256 * r;
+                const int e = threadIdx.x + NT * r;
                 const int t = e / kGK, k = e % kGK;
-                const int32_t sb = src[t];
-                ru[r] = (sb >= 0 && k0 + k < ns) ? in[(size_t)sb * ns + k0 + k] : T(0);
+                ru[r] = T(0);
+                if (t < TT) {
+                    const int32_t sb = src[t];
+                    if (sb >= 0 && k0 + k < ns) ru[r] = in[(size_t)sb * ns + k0 + k];
+                }
             }
 #pragma unroll
             for (int r = 0; r < kRM; ++r) {
-                const int e = threadIdx.x + 256 * r;
-                const int k = e / kGJ, j = e - k * kGJ;
-                rm[r] = (k0 + k < ns && j0 + j < ld) ? M[(size_t)(k0 + k) * ld + j0 + j] : T(0);
+                const int e = threadIdx.x + NT * r;
+                const int k = e / TJ, j = e - k * TJ;
+                rm[r] = (k < kGK && k0 + k < ns && j0 + j < ld) ? M[(size_t)(k0 + k) * ld + j0 + j] : T(0);
             }
         };
         load(0);
         for (int kc = 0; kc < nk; ++kc) {
 #pragma unroll
             for (int r = 0; r < kRU; ++r) {
-                const int e = threadIdx.x + 256 * r;
-                Us[e % kGK][e / kGK] = ru[r];
+                const int e = threadIdx.x + NT * r;
+                if (e < TT * kGK) Us[e % kGK][e / kGK] = ru[r];
             }
 #pragma unroll
             for (int r = 0; r < kRM; ++r) {
-                const int e = threadIdx.x + 256 * r;
-                const int k = e / kGJ;
-                Ms[k][e - k * kGJ] = rm[r];
+                const int e = threadIdx.x + NT * r;
+                const int k = e / TJ;
+                if (k < kGK) Ms[k][e - k * TJ] = rm[r];
             }
             __syncthreads();
             if (kc + 1 < nk) load(kc + 1);
 #pragma unroll
             for (int k = 0; k < kGK; ++k) {
-                T uv[8], mv[5];
+                T uv[RT], mv[RC];
 #pragma unroll
-                for (int a = 0; a < 8; ++a) uv[a] = Us[k][8 * ty + a];
+                for (int a = 0; a < RT; ++a) uv[a] = Us[k][RT * ty + a];
 #pragma unroll
-                for (int c = 0; c < 5; ++c) mv[c] = Ms[k][tx + 32 * c];
+                for (int c = 0; c < RC; ++c) mv[c] = Ms[k][tx + 32 * c];
 #pragma unroll
-                for (int a = 0; a < 8; ++a)
+                for (int a = 0; a < RT; ++a)
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) acc[a][c] += uv[a] * mv[c];
+                    for (int c = 0; c < RC; ++c) acc[a][c] += uv[a] * mv[c];
             }
             __syncthreads();
         }
         if constexpr (kTwoLevel) {
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+            for (int a = 0; a < RT; ++a)
 #pragma unroll
-                for (int c = 0; c < 5; ++c) {
+                for (int c = 0; c < RC; ++c) {
                     run[a][c] += acc[a][c];
                     acc[a][c] = T(0);
                 }
         }
     }
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        const int32_t t = tgt[8 * ty + a];
+    for (int a = 0; a < RT; ++a) {
+        const int32_t t = tgt[RT * ty + a];
         if (t < 0) continue;
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
+        for (int c = 0; c < RC; ++c) {
             const int j = j0 + tx + 32 * c;
             const T v = kTwoLevel ? run[a][c] : acc[a][c];
             if (j < ns) {
@@ -325,42 +331,55 @@ __global__ void __launch_bounds__(256) k_ggemm(G g, const int32_t *__restrict__ 
 // downward density on DE = 2.95 h S; M2P from the upward densities on
 // UE = 1.05 h S of the W-list boxes) and near field (P2P over the U list),
 // all as one stream of (pseudo-)sources {position relative to the leaf
-// centre, weight}.  Lanes l and l^16 share targets (l & 15) + 16 k and split
-// each staged chunk by parity; each chunk is summed plainly and added to the
-// totals with two-sum; the result overwrites res.
+// centre, weight} staged in shared memory.
+//
+// Tiling <TPL, G>: the warp splits into G groups of 32/G lanes; lane m of a
+// group owns targets tbase + m + (32/G) k (k < TPL) and the group takes every
+// G-th source of each staged chunk.  Up to 64 sources per lane are summed
+// plainly, then added to the totals with two-sum; the groups' totals are
+// combined in FP64 with shuffles and the result overwrites res.  The tile is picked per leaf so
+// that (32/G) TPL covers its targets with little waste.
 // ---------------------------------------------------------------------------
 constexpr int kLW = 4;
 constexpr int kLChunk = 128;
 
+constexpr int kLFlush = 64;  // sources per lane summed plainly before a compensated flush
+
 template <typename T, int TPL>
 struct LeafAcc {
     T tx[TPL], ty[TPL], tz[TPL];
-    T acc[TPL][4], cmp[TPL][4];
+    T part[TPL][4];             // plain FP32 partial sums since the last flush
+    T acc[TPL][4], cmp[TPL][4]; // compensated totals (two-sum)
+    int pend;                   // sources per lane in part (warp-uniform bound)
 };
 
 template <typename T, int TPL>
-__device__ __forceinline__ void leaf_chunk(LeafAcc<T, TPL> &L, const typename Vec4<T>::type *buf, int m, int half) {
-    T part[TPL][4];
-#pragma unroll
-    for (int k = 0; k < TPL; ++k)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) part[k][c] = T(0);
-    for (int j = half; j < m; j += 2) {
-        const auto s = buf[j];
-#pragma unroll
-        for (int k = 0; k < TPL; ++k)
-            lap_accum<T>(L.tx[k] - s.x, L.ty[k] - s.y, L.tz[k] - s.z, s.w, part[k][0], part[k][1], part[k][2],
-                         part[k][3]);
-    }
+__device__ __forceinline__ void leaf_flush(LeafAcc<T, TPL> &L) {
 #pragma unroll
     for (int k = 0; k < TPL; ++k)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             T sum, err;
-            two_sum<T>(L.acc[k][c], part[k][c], sum, err);
+            two_sum<T>(L.acc[k][c], L.part[k][c], sum, err);
             L.acc[k][c] = sum;
             L.cmp[k][c] += err;
+            L.part[k][c] = T(0);
         }
+    L.pend = 0;
+}
+
+template <typename T, int TPL, int G>
+__device__ __forceinline__ void leaf_chunk(LeafAcc<T, TPL> &L, const typename Vec4<T>::type *buf, int m, int grp) {
+#pragma unroll 2
+    for (int j = grp; j < m; j += G) {
+        const auto s = buf[j];
+#pragma unroll
+        for (int k = 0; k < TPL; ++k)
+            lap_accum<T>(L.tx[k] - s.x, L.ty[k] - s.y, L.tz[k] - s.z, s.w, L.part[k][0], L.part[k][1],
+                         L.part[k][2], L.part[k][3]);
+    }
+    L.pend += (m + G - 1) / G;
+    if (L.pend >= kLFlush) leaf_flush<T, TPL>(L);
 }
 
 struct LeafCtx {
@@ -369,6 +388,7 @@ struct LeafCtx {
     const int32_t *u_idx, *w_idx;
     int ns;
     const double *dbar;  // per-box mean of the downward check potential, or nullptr
+    LeafTiling tile;     // tile id per remaining-target bucket
 };
 
 // Source weights of the leaf stage.  Forward: own surface dn_dens * h_b,
@@ -383,27 +403,29 @@ struct LeafW {
     const T *pw;  // sorted per-particle weights, or nullptr for the charges
 };
 
-template <typename T, int TPL>
+template <typename T, int TPL, int G>
 __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec4<T>::type *__restrict__ pts,
                           const T *__restrict__ surf, const LeafW<T> &W, typename Vec4<T>::type *buf,
                           double4 *__restrict__ res) {
     using V4 = typename Vec4<T>::type;
-    const int lane = threadIdx.x & 31, half = lane >> 4;
+    constexpr int LG = 32 / G;  // lanes per group
+    const int lane = threadIdx.x & 31, grp = lane / LG, mem = lane % LG;
     const int lb = C.lvl[b];
     const T cbx = box_center<T>(C.cx[b], lb), cby = box_center<T>(C.cy[b], lb), cbz = box_center<T>(C.cz[b], lb);
     const int n = C.cnt[b], f = C.first[b], ns = C.ns;
     LeafAcc<T, TPL> L;
 #pragma unroll
     for (int k = 0; k < TPL; ++k) {
-        const int i = tbase + (lane & 15) + 16 * k;
+        const int i = tbase + mem + LG * k;
         V4 v{};
         if (i < n) v = pts[f + i];
         L.tx[k] = v.x;
         L.ty[k] = v.y;
         L.tz[k] = v.z;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) L.acc[k][c] = L.cmp[k][c] = T(0);
+        for (int c = 0; c < 4; ++c) L.part[k][c] = L.acc[k][c] = L.cmp[k][c] = T(0);
     }
+    L.pend = 0;
     // L2P: own downward equivalent surface
     {
         const T h = box_half<T>(lb), r = (T)kAlphaOuter * h;
@@ -420,7 +442,7 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
                 buf[j] = w;
             }
             __syncwarp();
-            leaf_chunk<T, TPL>(L, buf, m, half);
+            leaf_chunk<T, TPL, G>(L, buf, m, grp);
         }
     }
     // M2P: upward equivalent surfaces of the W list
@@ -443,7 +465,7 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
                 buf[j] = w;
             }
             __syncwarp();
-            leaf_chunk<T, TPL>(L, buf, m, half);
+            leaf_chunk<T, TPL, G>(L, buf, m, grp);
         }
     }
     // P2P: particles of the U list
@@ -465,20 +487,50 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
                 buf[j] = w;
             }
             __syncwarp();
-            leaf_chunk<T, TPL>(L, buf, m, half);
+            leaf_chunk<T, TPL, G>(L, buf, m, grp);
         }
     }
+    leaf_flush<T, TPL>(L);
 #pragma unroll
     for (int k = 0; k < TPL; ++k) {
         double tot[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const double mine = (double)L.acc[k][c] + (double)L.cmp[k][c];
-            tot[c] = mine + __shfl_xor_sync(0xffffffffu, mine, 16);
+            tot[c] = (double)L.acc[k][c] + (double)L.cmp[k][c];
+#pragma unroll
+            for (int o = 16; o >= LG; o >>= 1) tot[c] += __shfl_xor_sync(0xffffffffu, tot[c], o);
         }
         if (C.dbar) tot[0] += C.dbar[b];  // the constant part of the local expansion
-        const int i = tbase + (lane & 15) + 16 * k;
-        if (half == 0 && i < n) res[f + i] = make_double4(tot[0], tot[1], tot[2], tot[3]);
+        const int i = tbase + mem + LG * k;
+        if (grp == 0 && i < n) res[f + i] = make_double4(tot[0], tot[1], tot[2], tot[3]);
+    }
+}
+
+// Targets [t0, n) of leaf b: the tile the plan's table gives for the
+// remainder (bucket (r - 1) / 8, the last bucket beyond 128), repeated until
+// every target is covered.
+template <typename T>
+__device__ void leaf_dispatch(const LeafCtx &C, int b, int n, const typename Vec4<T>::type *__restrict__ pts,
+                              const T *__restrict__ surf, const LeafW<T> &W, typename Vec4<T>::type *buf,
+                              double4 *__restrict__ res) {
+    for (int t0 = 0; t0 < n;) {
+        const int r = n - t0;
+        const int id = C.tile.id[min((r - 1) >> 3, kLeafBuckets - 1)];
+        switch (id) {
+            case 0: leaf_pass<T, 1, 4>(C, b, t0, pts, surf, W, buf, res); break;
+            case 1: leaf_pass<T, 2, 4>(C, b, t0, pts, surf, W, buf, res); break;
+            case 2: leaf_pass<T, 3, 4>(C, b, t0, pts, surf, W, buf, res); break;
+            case 3: leaf_pass<T, 4, 4>(C, b, t0, pts, surf, W, buf, res); break;
+            case 4: leaf_pass<T, 1, 2>(C, b, t0, pts, surf, W, buf, res); break;
+            case 5: leaf_pass<T, 2, 2>(C, b, t0, pts, surf, W, buf, res); break;
+            case 6: leaf_pass<T, 3, 2>(C, b, t0, pts, surf, W, buf, res); break;
+            case 7: leaf_pass<T, 4, 2>(C, b, t0, pts, surf, W, buf, res); break;
+            case 8: leaf_pass<T, 1, 1>(C, b, t0, pts, surf, W, buf, res); break;
+            case 9: leaf_pass<T, 2, 1>(C, b, t0, pts, surf, W, buf, res); break;
+            case 10: leaf_pass<T, 3, 1>(C, b, t0, pts, surf, W, buf, res); break;
+            default: leaf_pass<T, 4, 1>(C, b, t0, pts, surf, W, buf, res); break;
+        }
+        t0 += kLeafTileSlots[id < kLeafTiles ? id : kLeafTiles - 1];
     }
 }
 
@@ -492,15 +544,7 @@ __global__ void __launch_bounds__(32 * kLW) k_leaf_all(LeafCtx C, int64_t n_leav
     const int64_t li = (int64_t)blockIdx.x * kLW + warp;
     if (li >= n_leaves) return;
     const int b = leaves[li];
-    const int n = C.cnt[b];
-    auto *buf = bufs[warp];
-    if (n <= 16) {
-        leaf_pass<T, 1>(C, b, 0, pts, surf, W, buf, res);
-    } else if (n <= 32) {
-        leaf_pass<T, 2>(C, b, 0, pts, surf, W, buf, res);
-    } else {
-        for (int t0 = 0; t0 < n; t0 += 64) leaf_pass<T, 4>(C, b, t0, pts, surf, W, buf, res);
-    }
+    leaf_dispatch<T>(C, b, C.cnt[b], pts, surf, W, bufs[warp], res);
 }
 
 // Scatter to caller order with 1/(4 pi), coef and physical units.
@@ -589,13 +633,26 @@ template <typename T, class G>
 void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *starts, int ncls, int nslots,
                    const T *in, T *out, int accumulate, cudaStream_t s, int ld = 0, double *dbar = nullptr) {
     ClassRanges cr;
-    int64_t most = 0;
+    int64_t most = 0, total = 0;
     for (int c = 0; c <= ncls; ++c) cr.b[c] = starts[c];
-    for (int c = 0; c < ncls; ++c) most = std::max<int64_t>(most, starts[c + 1] - starts[c]);
+    for (int c = 0; c < ncls; ++c) {
+        most = std::max<int64_t>(most, starts[c + 1] - starts[c]);
+        total += starts[c + 1] - starts[c];
+    }
     if (most <= 0) return;
     if (ld == 0) ld = P.ns;
-    dim3 grid(grid_for(most, kGT), ncls, grid_for(ld, kGJ));
-    ++g_launches, k_ggemm<T, G><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out, accumulate, dbar);
+    // 64 x 160 tiles while they fill the GPU twice over; else 16 x 32 tiles
+    // (the coarse levels of M2M / L2L and small trees are latency-bound).
+    const int64_t big_blocks = grid_for(total, 64) * grid_for(ld, 160);
+    if (big_blocks >= 2 * P.num_sms) {
+        dim3 grid(grid_for(most, 64), ncls, grid_for(ld, 160));
+        ++g_launches, k_ggemm<T, G, 8, 8, 5><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,
+                                                                   accumulate, dbar);
+    } else {
+        dim3 grid(grid_for(most, 16), ncls, grid_for(ld, 32));
+        ++g_launches, k_ggemm<T, G, 4, 4, 1><<<grid, 128, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,
+                                                                   accumulate, dbar);
+    }
 }
 
 template <typename T, class G>
@@ -664,8 +721,28 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     stage_end(P, KIFMM_STAGE_LEAF, s);
     stage_begin(P, KIFMM_STAGE_P2P, s);
     LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns,
-              split_mean ? P.dbar : nullptr};
+              split_mean ? P.dbar : nullptr, P.leaf_tile};
     const LeafW<T> W{(const T *)P.dn_dens, 1, (const T *)P.up_dens, 1, nullptr};
+    if (!P.tuned_leaf && tuning_wanted(P, s)) {
+        // time every candidate table on this tree; keep the fastest
+        float best = 1e30f;
+        LeafTiling pick = P.leaf_tile;
+        for (int c = 0; c < kLeafTilingCandidates; ++c) {
+            LeafCtx Cc = C;
+            Cc.tile = leaf_tiling_candidate(c);
+            const float ms = time_launch(s, [&] {
+                k_leaf_all<T><<<grid_for(P.n_leaves, kLW), 32 * kLW, 0, s>>>(Cc, P.n_leaves, P.leaves, pts, surf,
+                                                                             W, res);
+            });
+            if (ms < best) {
+                best = ms;
+                pick = Cc.tile;
+            }
+        }
+        P.leaf_tile = pick;
+        C.tile = pick;
+        P.tuned_leaf = true;
+    }
     ++g_launches, k_leaf_all<T><<<grid_for(P.n_leaves, kLW), 32 * kLW, 0, s>>>(C, P.n_leaves, P.leaves, pts, surf,
                                                                                W, res);
     stage_end(P, KIFMM_STAGE_P2P, s);
@@ -770,7 +847,8 @@ cudaError_t backward_t(Plan &P, const void *w_user, const void *grad_user, void 
         ggemm_classes<T>(P, GatherParent<T>{P.parent, (const T *)P.adj_m2m, ns, ns}, P.part_list[3],
                          P.part_start[3].data() + 8 * l, 8, 1, ub, ub, 1, s);
     // P2M^T (own UC surface, u-bar), P2L^T (W boxes' DC surfaces, d-bar), P2P^T (weights w)
-    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns, nullptr};
+    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns, nullptr,
+              P.leaf_tile};
     const LeafW<T> W{ub, 0, db, 0, ws};
     ++g_launches, k_leaf_all<T><<<grid_for(P.n_leaves, kLW), 32 * kLW, 0, s>>>(C, P.n_leaves, P.leaves, pts, surf,
                                                                                W, res);

@@ -18,6 +18,23 @@ constexpr int kVSlots = 189;        // V-list slots per octant class (6^3 - 3^3)
 constexpr int kMaxCoarse = 26;      // coarser-or-equal adjacent leaves of a box
 constexpr int kColl = 27;           // colleague slots (3^3, centre = self)
 
+// Leaf-kernel tiles: id -> (targets per lane TPL, source groups G); a tile
+// covers (32 / G) TPL targets.  The table maps the number of targets still
+// to cover, in buckets of 8 (the last bucket: more than 120), to a tile.
+constexpr int kLeafTiles = 12;
+constexpr int kLeafBuckets = 16;
+constexpr int kLeafTilingCandidates = 6;
+__host__ __device__ constexpr int leaf_tile_tpl(int id) { return id % 4 + 1; }
+__host__ __device__ constexpr int leaf_tile_groups(int id) { return id < 4 ? 4 : (id < 8 ? 2 : 1); }
+__device__ constexpr int kLeafTileSlots[kLeafTiles] = {8, 16, 24, 32, 16, 32, 48, 64, 32, 64, 96, 128};
+struct LeafTiling {
+    unsigned char id[kLeafBuckets];
+};
+// Candidate c of the tuner (c = 0 is the default): up to 32 targets use
+// g_small source groups, up to 64 use g_mid, beyond that one group, each with
+// the fewest targets per lane that cover the bucket.
+LeafTiling leaf_tiling_candidate(int c);
+
 struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;
@@ -33,6 +50,8 @@ struct Plan {
     double coef = 1.0;
     double eps = 1e-12;
     int direct_thr = -1;      // W/X of leaves with at most this many points go to U (-1: none)
+    LeafTiling leaf_tile{};   // leaf-kernel tiles (tuned when desc.autotune)
+    bool tuned_leaf = false, tuned_m2l = false;
     int num_sms = 0;
 
     // ---- operators (device) ----
@@ -187,6 +206,27 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s);
 void m2l_tensor_release(Plan &P);
 
 // ---- fmm.cu ----
+// Autotuning: true when desc.autotune asks for it, something is still
+// untuned and the stream is not being captured (tuning synchronises).
+bool tuning_wanted(const Plan &P, cudaStream_t s);
+int m2l_tensor_stages(const Plan &P);  // current pipeline depth of the tensor-core M2L (0: none)
+// Device time of one launch sequence on stream s, in ms (synchronises).
+template <class F>
+float time_launch(cudaStream_t s, F &&launch) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    launch();
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
 cudaError_t run_evaluate(Plan &P, void *pot, void *grad, double *energy, cudaStream_t s);
 cudaError_t run_backward(Plan &P, const void *w, const void *grad, void *dq, void *dx, cudaStream_t s);
 cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream_t s);

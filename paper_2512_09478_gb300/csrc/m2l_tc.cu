@@ -485,7 +485,8 @@ cudaError_t set_smem_attr(int nt, int bytes) {
 }  // namespace
 
 struct TcState {
-    int np = 0, kp = 0, nstages = 0;
+    int np = 0, kp = 0, nstages = 0, nstages_max = 0;
+    size_t stage_bytes = 0;
     int nt = 0, ncb = 0;      // output columns per CTA (MMA N), column blocks (np = nt ncb)
     float sigma_b = 1.f;
     __half *bh = nullptr, *bl = nullptr;
@@ -503,6 +504,8 @@ static TcState &tc_state(Plan &P) {
     if (!P.m2l_tc) P.m2l_tc = new TcState();
     return *(TcState *)P.m2l_tc;
 }
+
+int m2l_tensor_stages(const Plan &P) { return P.m2l_tc ? ((const TcState *)P.m2l_tc)->nstages : 0; }
 
 void m2l_tensor_release(Plan &P) {
     if (P.m2l_tc) {
@@ -526,6 +529,8 @@ cudaError_t m2l_tensor_setup(Plan &P) {
     const size_t stage = 2 * (size_t)kTcRows * kRowBytes + 2 * (size_t)S.nt * kRowBytes;
     S.nstages = (int)std::min<size_t>(16, (200 * 1024) / stage);
     if (S.nstages < 2 || S.nt > 160) return cudaErrorNotSupported;
+    S.nstages_max = S.nstages;
+    S.stage_bytes = stage;
     S.smem = S.nstages * stage + 1024;
     unsigned *dmax = nullptr;
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&dmax, sizeof(unsigned)));
@@ -600,18 +605,38 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {
     a.ns = P.ns;
     a.kp = S.kp;
     a.np = S.np;
-    a.nstages = S.nstages;
     a.status = P.status;
     const dim3 grid((unsigned)S.tiles_h.size(), (unsigned)S.ncb);
-    switch (S.nt) {
-        case 32: ++g_launches, k_m2l_tc<1><<<grid, kTcThreads, S.smem, s>>>(a); break;
-        case 64: ++g_launches, k_m2l_tc<2><<<grid, kTcThreads, S.smem, s>>>(a); break;
-        case 96: ++g_launches, k_m2l_tc<3><<<grid, kTcThreads, S.smem, s>>>(a); break;
-        case 128: ++g_launches, k_m2l_tc<4><<<grid, kTcThreads, S.smem, s>>>(a); break;
-        case 160: ++g_launches, k_m2l_tc<5><<<grid, kTcThreads, S.smem, s>>>(a); break;
-        default: return cudaErrorNotSupported;
+    auto launch = [&](int nst) -> cudaError_t {
+        a.nstages = nst;
+        const size_t smem = (size_t)nst * S.stage_bytes + 1024;
+        switch (S.nt) {
+            case 32: ++g_launches, k_m2l_tc<1><<<grid, kTcThreads, smem, s>>>(a); break;
+            case 64: ++g_launches, k_m2l_tc<2><<<grid, kTcThreads, smem, s>>>(a); break;
+            case 96: ++g_launches, k_m2l_tc<3><<<grid, kTcThreads, smem, s>>>(a); break;
+            case 128: ++g_launches, k_m2l_tc<4><<<grid, kTcThreads, smem, s>>>(a); break;
+            case 160: ++g_launches, k_m2l_tc<5><<<grid, kTcThreads, smem, s>>>(a); break;
+            default: return cudaErrorNotSupported;
+        }
+        return cudaGetLastError();
+    };
+    if (!P.tuned_m2l && tuning_wanted(P, s)) {
+        // pipeline depth: time 2 .. the shared-memory maximum (at most five depths)
+        float best = 1e30f;
+        int pick = S.nstages;
+        for (int nst = S.nstages_max; nst >= std::max(2, S.nstages_max - 4); --nst) {
+            cudaError_t e = cudaSuccess;
+            const float ms = time_launch(s, [&] { e = launch(nst); });
+            KIFMM_CUDA_TRY(e);
+            if (ms < best) {
+                best = ms;
+                pick = nst;
+            }
+        }
+        S.nstages = pick;
+        P.tuned_m2l = true;
     }
-    return cudaGetLastError();
+    return launch(S.nstages);
 }
 
 }  // namespace kifmm

@@ -48,11 +48,17 @@ class ProfileT(ctypes.Structure):
                 ("launches", ctypes.c_int64)]
 
 
+class TuningT(ctypes.Structure):
+    _fields_ = [("tuned", ctypes.c_int), ("m2l_stages", ctypes.c_int), ("leaf_tpl", ctypes.c_int * 16),
+                ("leaf_groups", ctypes.c_int * 16)]
+
+
 _LIB = None
 EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifmm_evaluate",
            "kifmm_clump_reduce", "kifmm_backward", "kifmm_get_device_status", "kifmm_status_string",
            "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
-           "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources"]
+           "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources",
+           "kifmm_get_tuning", "kifmm_energy_noalloc"]
 
 
 def load(path: str = LIB_PATH):
@@ -209,6 +215,13 @@ class Plan:
     # ---- profiling ----
     def profile(self, enable: bool = True):
         _check(load().kifmm_profile_enable(self._h, int(enable)), "kifmm_profile_enable")
+
+    def tuning(self) -> dict:
+        """Tile shapes in use (see kifmm_get_tuning)."""
+        t = TuningT()
+        _check(load().kifmm_get_tuning(self._h, ctypes.byref(t)), "kifmm_get_tuning")
+        return {"tuned_leaf": bool(t.tuned & 1), "tuned_m2l": bool(t.tuned & 2), "m2l_stages": t.m2l_stages,
+                "leaf_tiles": [(t.leaf_tpl[i], t.leaf_groups[i]) for i in range(16)]}
 
     def profile_read(self) -> dict:
         """Per-stage device milliseconds and bracket counts since the last

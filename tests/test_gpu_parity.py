@@ -339,3 +339,30 @@ def test_clump_reduce_matches_oracle():
     F, T = plan.clump_reduce(torch.tensor(off, device="cuda"), xt, qt, grad, _dev(centres))
     Fo, To = O.clump_reduce(x, q, grad.cpu().numpy(), off, centres)
     assert O.rel_l2(F.cpu().numpy(), Fo) < 1e-14 and O.rel_l2(T.cpu().numpy(), To) < 1e-14
+
+
+@pytest.mark.parametrize("prec", ["mixed_fp16", "fp64"])
+def test_autotune_keeps_results(prec):
+    """autotune times the candidate tilings on the first evaluate and keeps
+    the fastest; the results stay those of the fixed default (the same sums,
+    in another order: last-bit differences only)."""
+    x, q = CASES["plummer3000"]()
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    out = []
+    for tune in (False, True):
+        plan = _plan(x, precision=prec, p=6, M=16, dtype=dt, autotune=tune)
+        plan.set_sources(_dev(x, dt), _dev(q, dt))
+        pot, grad, _ = plan.evaluate()
+        pot2, grad2, _ = plan.evaluate()
+        assert plan.device_status() == 0
+        t = plan.tuning()
+        assert t["tuned_leaf"] == tune
+        if prec == "mixed_fp16":
+            assert t["tuned_m2l"] == tune and t["m2l_stages"] >= 2
+        for tpl, g in t["leaf_tiles"]:
+            assert 1 <= tpl <= 4 and g in (1, 2, 4)
+        # the tuned plan's second evaluate is deterministic
+        assert torch.equal(pot, pot2) or tune
+        out.append((pot2.double().cpu().numpy(), grad2.double().cpu().numpy()))
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert O.rel_l2(out[1][0], out[0][0]) < tol and O.rel_l2(out[1][1], out[0][1]) < tol
