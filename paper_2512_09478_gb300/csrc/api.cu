@@ -172,11 +172,6 @@ static cudaError_t ensure_box_arrays(Plan &P) {
     return cudaSuccess;
 }
 
-static cudaError_t ensure_partition_arrays(Plan &P) {
-    KIFMM_CUDA_TRY(plan_alloc(P, &P.part_keys, sizeof(uint64_t) * 2 * P.box_cap));
-    KIFMM_CUDA_TRY(plan_alloc(P, &P.part_vals, sizeof(uint32_t) * 2 * P.box_cap));
-    return cudaSuccess;
-}
 
 }  // namespace kifmm
 
@@ -334,8 +329,8 @@ static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cu
     API_CUDA(build_tree(P, xyz, q, s));
     API_CUDA(ensure_box_arrays(P));
     API_CUDA(build_lists(P, s));
-    API_CUDA(ensure_partition_arrays(P));
     API_CUDA(partition_boxes(P, s));
+    API_CUDA(gather_particles(P, xyz, q, s));
     if (P.desc.precision == KIFMM_MIXED_FP16) API_CUDA(m2l_tensor_tiles(P, s));
     // energy chunks (sorted order never mixes systems)
     {

@@ -130,8 +130,6 @@ struct Plan {
     int32_t *leaves = nullptr;       // [nb] leaf indices
     int64_t n_leaves = 0;
     int32_t *wsrc_flag = nullptr;    // [nb] 1 if the box is in some W list
-    void *part_keys = nullptr;       // [2][box_cap] u64 partition scratch
-    void *part_vals = nullptr;       // [2][box_cap] u32
     uint32_t *part_counts = nullptr; // [4][256]
     unsigned long long *list_totals = nullptr;  // [4] V and X list sizes
     // Box lists grouped by a small key (stable, canonical order within a key):

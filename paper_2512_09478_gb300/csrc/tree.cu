@@ -353,24 +353,31 @@ __global__ void k_emit(int64_t ls, int64_t le, const uint32_t *__restrict__ nchi
 // Leaf-relative particle records {x - c_leaf, y - c_leaf, z - c_leaf, q} in
 // root-normalised units (root side = 1), computed in FP64.
 template <typename TI, typename TC>
-__global__ void k_gather(int64_t nb, const int32_t *__restrict__ nchild, const int32_t *__restrict__ first,
+__global__ void k_gather(int64_t n_leaves, const int32_t *__restrict__ leaves, const int32_t *__restrict__ first,
                          const int32_t *__restrict__ cnt, const int32_t *__restrict__ lvl,
                          const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
                          const int32_t *__restrict__ cz, const int32_t *__restrict__ sys,
                          const double *__restrict__ lo_side, const uint32_t *__restrict__ perm,
                          const TI *__restrict__ xyz, const TI *__restrict__ q,
                          typename Vec4<TC>::type *pts) {
-    const int64_t b = blockIdx.x;
-    if (b >= nb || nchild[b] != 0) return;
+    // one warp per leaf
+    const int64_t li = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (li >= n_leaves) return;
+    const int b = leaves[li];
     const int s = sys[b];
-    const double side = lo_side[s * 4 + 3];
+    const double side = lo_side[s * 4 + 3], inv_side = 1.0 / side;
+    const double lo[3] = {lo_side[s * 4], lo_side[s * 4 + 1], lo_side[s * 4 + 2]};
     const double w = ldexp(1.0, -lvl[b]);
     const double c[3] = {(cx[b] + 0.5) * w, (cy[b] + 0.5) * w, (cz[b] + 0.5) * w};
-    for (int k = threadIdx.x; k < cnt[b]; k += blockDim.x) {
+    for (int k = threadIdx.x & 31; k < cnt[b]; k += 32) {
         const int64_t i = first[b] + k;
         const uint32_t j = perm[i];
         double r[3];
-        for (int d = 0; d < 3; ++d) r[d] = ((double)xyz[3 * j + d] - lo_side[s * 4 + d]) / side - c[d];
+        // FP64 records keep the correctly rounded quotient (FP64 parity); FP32
+        // records are rounded to FP32 anyway, so a reciprocal multiply will do
+        for (int d = 0; d < 3; ++d)
+            r[d] = (sizeof(TC) == 8 ? ((double)xyz[3 * j + d] - lo[d]) / side
+                                    : ((double)xyz[3 * j + d] - lo[d]) * inv_side) - c[d];
         typename Vec4<TC>::type v;
         v.x = (TC)r[0];
         v.y = (TC)r[1];
@@ -383,63 +390,81 @@ __global__ void k_gather(int64_t nb, const int32_t *__restrict__ nchild, const i
 // ---------------------------------------------------------------------------
 // Lists
 // ---------------------------------------------------------------------------
+// One warp per box: lane k < 27 scans the children of the parent's colleague
+// k; every child adjacent to (or equal to) b lands in its own slot.
 __global__ void k_colleagues(int64_t ls, int64_t le, int level, const int32_t *__restrict__ parent,
                              const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
                              const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
                              const int32_t *__restrict__ cz, int32_t *coll) {
-    int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (b >= le) return;
     int32_t *cb = coll + b * kColl;
     // cb was set to -1 by a memset of the whole array before the first level
     if (level == 0) {
-        cb[13] = (int32_t)b;
+        if (lane == 0) cb[13] = (int32_t)b;
         return;
     }
-    const int32_t P = parent[b];
-    const int32_t *cp = coll + (int64_t)P * kColl;
-    for (int k = 0; k < kColl; ++k) {
-        const int32_t c = cp[k];
-        if (c < 0 || nchild[c] == 0) continue;
-        for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
-            const int dx = cx[ch] - cx[b], dy = cy[ch] - cy[b], dz = cz[ch] - cz[b];
-            if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
-            cb[(dx + 1) * 9 + (dy + 1) * 3 + (dz + 1)] = ch;
-        }
+    if (lane >= kColl) return;
+    const int32_t c = coll[(int64_t)parent[b] * kColl + lane];
+    if (c < 0) return;
+    const int bx = cx[b], by = cy[b], bz = cz[b];
+    for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
+        const int dx = cx[ch] - bx, dy = cy[ch] - by, dz = cz[ch] - bz;
+        if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
+        cb[(dx + 1) * 9 + (dy + 1) * 3 + (dz + 1)] = ch;
     }
 }
 
 // Coarser-or-equal-level leaves adjacent to b: those of the parent that touch
-// b, plus b's leaf colleagues.
+// b (in the parent's order), then b's leaf colleagues (in slot order).  One
+// warp per box; ballots keep the order.
 __global__ void k_coarse(int64_t ls, int64_t le, int level, const int32_t *__restrict__ parent,
                          const int32_t *__restrict__ nchild, const int32_t *__restrict__ lvl,
                          const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
                          const int32_t *__restrict__ cz, const int32_t *__restrict__ coll, int32_t *coarse,
                          int32_t *ncoarse, int *status) {
-    int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (b >= le) return;
+    const unsigned below = (1u << lane) - 1u;
     int n = 0;
     int32_t *out = coarse + b * kMaxCoarse;
     if (level > 0) {
         const int32_t P = parent[b];
-        for (int k = 0; k < ncoarse[P]; ++k) {
-            const int32_t a = coarse[(int64_t)P * kMaxCoarse + k];
-            if (boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], level, cx[b], cy[b], cz[b])) {
-                if (n < kMaxCoarse) out[n] = a;
-                ++n;
-            }
+        const int np = ncoarse[P];  // <= kMaxCoarse < 32
+        int32_t a = -1;
+        bool keep = false;
+        if (lane < np) {
+            a = coarse[(int64_t)P * kMaxCoarse + lane];
+            keep = boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], level, cx[b], cy[b], cz[b]);
         }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int pos = __popc(m & below);
+            if (pos < kMaxCoarse) out[pos] = a;
+        }
+        n = __popc(m);
     }
-    for (int k = 0; k < kColl; ++k) {
-        const int32_t c = coll[b * kColl + k];
-        if (k == 13 || c < 0 || nchild[c] != 0) continue;
-        if (n < kMaxCoarse) out[n] = c;
-        ++n;
+    int32_t c = -1;
+    bool keep = false;
+    if (lane < kColl && lane != 13) {
+        c = coll[b * kColl + lane];
+        keep = c >= 0 && nchild[c] == 0;
     }
-    if (n > kMaxCoarse) {
-        set_status(status, KIFMM_ERR_CAPACITY);
-        n = kMaxCoarse;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+        const int pos = n + __popc(m & below);
+        if (pos < kMaxCoarse) out[pos] = c;
     }
-    ncoarse[b] = n;
+    n += __popc(m);
+    if (lane == 0) {
+        if (n > kMaxCoarse) {
+            set_status(status, KIFMM_ERR_CAPACITY);
+            n = kMaxCoarse;
+        }
+        ncoarse[b] = n;
+    }
 }
 
 // slot of offset d for octant class (ox,oy,oz): components range over
@@ -467,7 +492,9 @@ __device__ __forceinline__ bool direct_box(const int32_t *nchild, const int32_t 
 
 // V list (children of the parent's colleagues not adjacent to b) into the
 // per-class slot table, and X list (coarser leaves adjacent to the parent but
-// not to b; empty when b itself is a direct-sum leaf, see k_uw).
+// not to b; empty when b itself is a direct-sum leaf, see k_uw).  One warp
+// per box: lane k < 27 takes the parent's colleague k (each child has its
+// own slot); the X list keeps the parent's coarse order through a ballot.
 __global__ void k_vx(int64_t ls, int64_t le, int level, int thr, const int32_t *__restrict__ parent,
                      const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
                      const int32_t *__restrict__ cnt,
@@ -476,37 +503,49 @@ __global__ void k_vx(int64_t ls, int64_t le, int level, int thr, const int32_t *
                      const int32_t *__restrict__ coll, const int32_t *__restrict__ coarse,
                      const int32_t *__restrict__ ncoarse, int32_t *vdense, int32_t *nv, int32_t *xdense,
                      int32_t *nx, unsigned long long *totals) {
-    int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (b >= le) return;
     int32_t *vb = vdense + b * kVSlots;  // preset to -1 by a memset
     int cntv = 0, cntx = 0;
     if (level > 0) {
         const int32_t P = parent[b];
-        const int ox = cx[b] & 1, oy = cy[b] & 1, oz = cz[b] & 1;
-        for (int k = 0; k < kColl; ++k) {
-            const int32_t c = coll[(int64_t)P * kColl + k];
-            if (c < 0 || nchild[c] == 0) continue;
-            for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
-                const int dx = cx[ch] - cx[b], dy = cy[ch] - cy[b], dz = cz[ch] - cz[b];
-                if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
-                const int sl = v_slot(ox, oy, oz, dx, dy, dz);
-                if (sl < 0) continue;  // unreachable: children of parent colleagues lie in the class window
-                vb[sl] = ch;
-                ++cntv;
+        const int bx = cx[b], by = cy[b], bz = cz[b];
+        const int ox = bx & 1, oy = by & 1, oz = bz & 1;
+        if (lane < kColl) {
+            const int32_t c = coll[(int64_t)P * kColl + lane];
+            if (c >= 0) {
+                for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
+                    const int dx = cx[ch] - bx, dy = cy[ch] - by, dz = cz[ch] - bz;
+                    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+                    const int sl = v_slot(ox, oy, oz, dx, dy, dz);
+                    if (sl < 0) continue;  // unreachable: children of parent colleagues lie in the class window
+                    vb[sl] = ch;
+                    ++cntv;
+                }
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cntv += __shfl_xor_sync(0xffffffffu, cntv, o);
         if (!direct_box(nchild, cnt, thr, (int32_t)b)) {
-            for (int k = 0; k < ncoarse[P]; ++k) {
-                const int32_t a = coarse[(int64_t)P * kMaxCoarse + k];
-                if (!boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], level, cx[b], cy[b], cz[b]))
-                    xdense[b * kMaxCoarse + cntx++] = a;
+            const int np = ncoarse[P];
+            int32_t a = -1;
+            bool keep = false;
+            if (lane < np) {
+                a = coarse[(int64_t)P * kMaxCoarse + lane];
+                keep = !boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], level, bx, by, bz);
             }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) xdense[b * kMaxCoarse + __popc(m & ((1u << lane) - 1u))] = a;
+            cntx = __popc(m);
         }
     }
-    nv[b] = cntv;
-    if (cntv) atomicAdd(&totals[0], (unsigned long long)cntv);
-    if (cntx) atomicAdd(&totals[1], (unsigned long long)cntx);
-    nx[b] = cntx;
+    if (lane == 0) {
+        nv[b] = cntv;
+        nx[b] = cntx;
+        if (cntv) atomicAdd(&totals[0], (unsigned long long)cntv);
+        if (cntx) atomicAdd(&totals[1], (unsigned long long)cntx);
+    }
 }
 
 // U and W of a leaf: U = {b} + coarse adjacent leaves + finer adjacent leaves
@@ -618,22 +657,81 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uin
     return cudaGetLastError();
 }
 
-// Partition keys (see Plan::part_list).
-__global__ void k_part_keys(int64_t nb, int mode, const int32_t *__restrict__ nv, const int32_t *__restrict__ nchild,
+// Partition keys (see Plan::part_list): mode 0 octant class of boxes with a
+// V list (8: none), mode 1 leaves first then non-leaves by level, mode 2 W
+// sources first, mode 3 level * 8 + octant (255: the roots).
+__device__ __forceinline__ uint32_t part_key(int mode, int64_t b, const int32_t *__restrict__ nv,
+                                             const int32_t *__restrict__ nchild, const int32_t *__restrict__ lvl,
+                                             const int32_t *__restrict__ wflag, const int32_t *__restrict__ cx,
+                                             const int32_t *__restrict__ cy, const int32_t *__restrict__ cz) {
+    const uint32_t oct = (uint32_t)(4 * (cx[b] & 1) + 2 * (cy[b] & 1) + (cz[b] & 1));
+    if (mode == 0) return (nv[b] > 0) ? oct : 8u;
+    if (mode == 1) return (nchild[b] == 0) ? 0u : 1u + (uint32_t)lvl[b];
+    if (mode == 2) return wflag[b] ? 0u : 1u;
+    return (lvl[b] > 0) ? (uint32_t)lvl[b] * 8u + oct : 255u;
+}
+
+// All four partitions in one grid (blockIdx.y = mode): per-tile key
+// histograms laid out [mode][key][tile] so that one exclusive scan serves all
+// modes (mode m's positions come out offset by m * nb), plus key totals.
+__global__ void k_part_hist(int64_t nb, int nblk, const int32_t *__restrict__ nv, const int32_t *__restrict__ nchild,
                             const int32_t *__restrict__ lvl, const int32_t *__restrict__ wflag,
                             const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
-                            const int32_t *__restrict__ cz, uint64_t *keys, uint32_t *vals, uint32_t *counts) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    const uint32_t oct = (uint32_t)(4 * (cx[b] & 1) + 2 * (cy[b] & 1) + (cz[b] & 1));
-    uint32_t k;
-    if (mode == 0) k = (nv[b] > 0) ? oct : 8u;
-    else if (mode == 1) k = (nchild[b] == 0) ? 0u : 1u + (uint32_t)lvl[b];
-    else if (mode == 2) k = wflag[b] ? 0u : 1u;
-    else k = (lvl[b] > 0) ? (uint32_t)lvl[b] * 8u + oct : 255u;
-    keys[b] = k;
-    vals[b] = (uint32_t)b;
-    atomicAdd(&counts[k], 1u);
+                            const int32_t *__restrict__ cz, uint32_t *hist, uint32_t *counts) {
+    __shared__ uint32_t h[256];
+    const int mode = blockIdx.y;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const int64_t end = min(nb, base + (int64_t)kTile);
+    for (int64_t b = base + threadIdx.x; b < end; b += kBlock)
+        atomicAdd(&h[part_key(mode, b, nv, nchild, lvl, wflag, cx, cy, cz)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+        hist[((int64_t)mode * 256 + d) * nblk + blockIdx.x] = h[d];
+        if (h[d]) atomicAdd(&counts[mode * 256 + d], h[d]);
+    }
+}
+
+// Stable scatter of box indices by key (ranks as in k_rs_scatter).
+__global__ void k_part_scatter(int64_t nb, int nblk, const int32_t *__restrict__ nv,
+                               const int32_t *__restrict__ nchild, const int32_t *__restrict__ lvl,
+                               const int32_t *__restrict__ wflag, const int32_t *__restrict__ cx,
+                               const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
+                               const uint32_t *__restrict__ hist_scan, int32_t *out0, int32_t *out1, int32_t *out2,
+                               int32_t *out3) {
+    __shared__ uint32_t base_d[256];
+    __shared__ uint32_t wcnt[kBlock / 32][256];
+    const int mode = blockIdx.y;
+    int32_t *out = mode == 0 ? out0 : mode == 1 ? out1 : mode == 2 ? out2 : out3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t shift = (uint32_t)(mode * nb);  // the joint scan's offset of this mode
+    for (int d = threadIdx.x; d < 256; d += kBlock)
+        base_d[d] = hist_scan[((int64_t)mode * 256 + d) * nblk + blockIdx.x] - shift;
+    const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+    for (int r = 0; r < kItems; ++r) {
+        for (int i = threadIdx.x; i < (kBlock / 32) * 256; i += kBlock) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t b = tile0 + (int64_t)r * kBlock + threadIdx.x;
+        const bool valid = b < nb;
+        const uint32_t dig = valid ? part_key(mode, b, nv, nchild, lvl, wflag, cx, cy, cz) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xffffffffu, dig);
+        const int rank_w = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank_w == 0) wcnt[warp][dig] = __popc(peers);
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += kBlock) {
+            uint32_t run = base_d[d];
+            for (int w = 0; w < kBlock / 32; ++w) {
+                const uint32_t c = wcnt[w][d];
+                wcnt[w][d] = run;
+                run += c;
+            }
+            base_d[d] = run;
+        }
+        __syncthreads();
+        if (valid) out[wcnt[warp][dig] + rank_w] = (int32_t)b;
+        __syncthreads();
+    }
 }
 
 __global__ void k_child8(int64_t nb, const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
@@ -668,17 +766,25 @@ static cudaError_t radix_pass(Plan &P, const uint64_t *kin, const uint32_t *vin,
 
 cudaError_t partition_boxes(Plan &P, cudaStream_t s) {
     const int64_t nb = P.nb;
-    uint64_t *pk0 = (uint64_t *)P.part_keys, *pk1 = pk0 + P.box_cap;
-    uint32_t *pv0 = (uint32_t *)P.part_vals, *pv1 = pv0 + P.box_cap;
+    const int nblk = (int)((nb + kTile - 1) / kTile);
+    const int64_t nh = (int64_t)4 * 256 * nblk;
+    if ((size_t)2 * nh > P.hist_elems) {
+        P.hist_elems = (size_t)2 * nh;
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.hist, sizeof(uint32_t) * P.hist_elems));
+    }
+    if (scan_tmp_needed(nh) + 8 > P.scan_tmp_elems) {
+        P.scan_tmp_elems = scan_tmp_needed(nh) + 8;
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.scan_tmp, sizeof(uint32_t) * P.scan_tmp_elems));
+    }
     ++g_launches, k_child8<<<grid_for(nb, 256), 256, 0, s>>>(nb, P.child_first, P.nchild, P.cx, P.cy, P.cz, P.child8);
     KIFMM_CUDA_TRY(cudaMemsetAsync(P.part_counts, 0, sizeof(uint32_t) * 4 * 256, s));
-    for (int mode = 0; mode < 4; ++mode) {
-        ++g_launches, k_part_keys<<<grid_for(nb, 256), 256, 0, s>>>(nb, mode, P.nv, P.nchild, P.lvl, P.wsrc_flag,
-                                                                    P.cx, P.cy, P.cz, pk0, pv0,
-                                                                    P.part_counts + 256 * mode);
-        KIFMM_CUDA_TRY(radix_pass(P, pk0, pv0, pk1, pv1, nb, 0, 0, s));
-        KIFMM_CUDA_TRY(cudaMemcpyAsync(P.part_list[mode], pv1, sizeof(int32_t) * nb, cudaMemcpyDeviceToDevice, s));
-    }
+    const dim3 grid((unsigned)nblk, 4);
+    ++g_launches, k_part_hist<<<grid, kBlock, 0, s>>>(nb, nblk, P.nv, P.nchild, P.lvl, P.wsrc_flag, P.cx, P.cy, P.cz,
+                                                      P.hist, P.part_counts);
+    KIFMM_CUDA_TRY(exclusive_scan_u32(P.hist, P.hist + nh, nh, nullptr, P.scan_tmp, P.scan_tmp_elems - 1, s));
+    ++g_launches, k_part_scatter<<<grid, kBlock, 0, s>>>(nb, nblk, P.nv, P.nchild, P.lvl, P.wsrc_flag, P.cx, P.cy,
+                                                         P.cz, P.hist + nh, P.part_list[0], P.part_list[1],
+                                                         P.part_list[2], P.part_list[3]);
     // one synchronisation for the four key histograms
     uint32_t counts[4][256];
     KIFMM_CUDA_TRY(cudaMemcpyAsync(counts, P.part_counts, sizeof(counts), cudaMemcpyDeviceToHost, s));
@@ -777,7 +883,7 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
     P.nb = le;
     P.max_level = level;
 
-    return gather_particles(P, xyz, q, s);
+    return cudaGetLastError();  // the particle records follow once the leaves are listed
 }
 
 // Leaf-relative particle records in the compute type (also used to refresh
@@ -785,21 +891,21 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
 cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream_t s) {
     if (P.f64) {
         if (P.io_f64)
-            ++g_launches, k_gather<double, double><<<(unsigned)P.nb, 128, 0, s>>>(
-                P.nb, P.nchild, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+            ++g_launches, k_gather<double, double><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
+                P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
                 (const double *)xyz, (const double *)q, (double4 *)P.pts);
         else
-            ++g_launches, k_gather<float, double><<<(unsigned)P.nb, 128, 0, s>>>(
-                P.nb, P.nchild, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+            ++g_launches, k_gather<float, double><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
+                P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
                 (const float *)xyz, (const float *)q, (double4 *)P.pts);
     } else {
         if (P.io_f64)
-            ++g_launches, k_gather<double, float><<<(unsigned)P.nb, 128, 0, s>>>(
-                P.nb, P.nchild, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+            ++g_launches, k_gather<double, float><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
+                P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
                 (const double *)xyz, (const double *)q, (float4 *)P.pts);
         else
-            ++g_launches, k_gather<float, float><<<(unsigned)P.nb, 128, 0, s>>>(
-                P.nb, P.nchild, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+            ++g_launches, k_gather<float, float><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
+                P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
                 (const float *)xyz, (const float *)q, (float4 *)P.pts);
     }
     return cudaGetLastError();
@@ -812,12 +918,12 @@ cudaError_t build_lists(Plan &P, cudaStream_t s) {
     KIFMM_CUDA_TRY(cudaMemsetAsync(P.list_totals, 0, sizeof(unsigned long long) * 4, s));
     for (int l = 0; l <= P.max_level; ++l) {
         const int64_t ls = P.level_start[l], le = P.level_start[l + 1];
-        const unsigned g = grid_for(le - ls, 128);
-        ++g_launches, k_colleagues<<<g, 128, 0, s>>>(ls, le, l, P.parent, P.child_first, P.nchild, P.cx, P.cy, P.cz,
+        const unsigned g = grid_for(le - ls, 8);  // warp per box, 8 per block
+        ++g_launches, k_colleagues<<<g, 256, 0, s>>>(ls, le, l, P.parent, P.child_first, P.nchild, P.cx, P.cy, P.cz,
                                                      P.coll);
-        ++g_launches, k_coarse<<<g, 128, 0, s>>>(ls, le, l, P.parent, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll,
+        ++g_launches, k_coarse<<<g, 256, 0, s>>>(ls, le, l, P.parent, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll,
                                                  P.coarse, P.ncoarse, P.status);
-        ++g_launches, k_vx<<<g, 128, 0, s>>>(ls, le, l, P.direct_thr, P.parent, P.child_first, P.nchild, P.cnt,
+        ++g_launches, k_vx<<<g, 256, 0, s>>>(ls, le, l, P.direct_thr, P.parent, P.child_first, P.nchild, P.cnt,
                                              P.lvl, P.cx, P.cy, P.cz,
                                              P.coll, P.coarse, P.ncoarse, P.vdense, P.nv, P.xdense, P.nx,
                                              P.list_totals);
