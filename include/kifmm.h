@@ -246,12 +246,15 @@ kifmm_status kifmm_profile_read(kifmm_plan *plan, kifmm_profile_t *out);
  * tensor-core M2L (0 when the plan has none).  Leaf kernel: for a leaf with
  * r targets still to cover, bucket min((r - 1) / 8, 15) selects leaf_tpl
  * targets per lane and leaf_groups source groups (a warp covers
- * 32 / groups * tpl targets per pass).  Host memory; no device work. */
+ * 32 / groups * tpl targets per pass).  leaf_small_kernel: 1 when leaves
+ * covered in one pass with tpl <= 2 run in a separate low-register kernel.
+ * Host memory; no device work. */
 typedef struct {
     int tuned;
     int m2l_stages;
     int leaf_tpl[16];
     int leaf_groups[16];
+    int leaf_small_kernel;
 } kifmm_tuning_t;
 kifmm_status kifmm_get_tuning(kifmm_plan *plan, kifmm_tuning_t *out);
 

@@ -58,14 +58,15 @@ static cudaError_t profile_collect(Plan &P) {
 }
 
 LeafTiling leaf_tiling_candidate(int c) {
-    static const int fam[kLeafTilingCandidates][2] = {{4, 2}, {2, 2}, {4, 1}, {2, 1}, {1, 1}, {1, 2}};
-    const int gs = fam[c][0], gm = fam[c][1];
+    static const int fam[kLeafTilingCandidates / 2][2] = {{4, 2}, {2, 2}, {4, 1}, {2, 1}, {1, 1}, {1, 2}};
+    const int gs = fam[c / 2][0], gm = fam[c / 2][1];
     LeafTiling t{};
+    t.small_class = (c % 2 == 0);
     for (int i = 0; i < kLeafBuckets; ++i) {
         const int r = (i == kLeafBuckets - 1) ? 128 : 8 * (i + 1);
         const int g = (r <= 32) ? gs : (r <= 64 ? gm : 1);
         const int tpl = std::min(4, std::max(1, (r * g + 31) / 32));
-        t.id[i] = (unsigned char)((g == 4 ? 0 : g == 2 ? 4 : 8) + tpl - 1);
+        t.set(i, (g == 4 ? 0 : g == 2 ? 4 : 8) + tpl - 1);
     }
     return t;
 }
@@ -457,9 +458,10 @@ kifmm_status kifmm_get_tuning(kifmm_plan *pl, kifmm_tuning_t *out) {
     out->tuned = (P.tuned_leaf ? 1 : 0) | (P.tuned_m2l ? 2 : 0);
     out->m2l_stages = m2l_tensor_stages(P);
     for (int i = 0; i < kLeafBuckets; ++i) {
-        out->leaf_tpl[i] = leaf_tile_tpl(P.leaf_tile.id[i]);
-        out->leaf_groups[i] = leaf_tile_groups(P.leaf_tile.id[i]);
+        out->leaf_tpl[i] = leaf_tile_tpl(P.leaf_tile.get(i));
+        out->leaf_groups[i] = leaf_tile_groups(P.leaf_tile.get(i));
     }
+    out->leaf_small_kernel = P.leaf_tile.small_class;
     return KIFMM_OK;
 }
 

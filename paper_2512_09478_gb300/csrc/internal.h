@@ -23,16 +23,22 @@ constexpr int kColl = 27;           // colleague slots (3^3, centre = self)
 // to cover, in buckets of 8 (the last bucket: more than 120), to a tile.
 constexpr int kLeafTiles = 12;
 constexpr int kLeafBuckets = 16;
-constexpr int kLeafTilingCandidates = 6;
+constexpr int kLeafTilingCandidates = 12;
 __host__ __device__ constexpr int leaf_tile_tpl(int id) { return id % 4 + 1; }
 __host__ __device__ constexpr int leaf_tile_groups(int id) { return id < 4 ? 4 : (id < 8 ? 2 : 1); }
-__device__ constexpr int kLeafTileSlots[kLeafTiles] = {8, 16, 24, 32, 16, 32, 48, 64, 32, 64, 96, 128};
 struct LeafTiling {
-    unsigned char id[kLeafBuckets];
+    unsigned long long packed;  // 4 bits per bucket
+    int small_class;            // 1: leaves with <= 2 targets per lane go to the low-register kernel
+    __host__ __device__ int get(int bucket) const { return (int)((packed >> (4 * bucket)) & 15ULL); }
+    __host__ __device__ int for_targets(int r) const { return get((r - 1) >> 3 < kLeafBuckets ? (r - 1) >> 3 : kLeafBuckets - 1); }
+    void set(int bucket, int id) {
+        packed = (packed & ~(15ULL << (4 * bucket))) | ((unsigned long long)id << (4 * bucket));
+    }
 };
 // Candidate c of the tuner (c = 0 is the default): up to 32 targets use
 // g_small source groups, up to 64 use g_mid, beyond that one group, each with
-// the fewest targets per lane that cover the bucket.
+// the fewest targets per lane that cover the bucket; odd c keep every leaf
+// in the general kernel.
 LeafTiling leaf_tiling_candidate(int c);
 
 struct DevBuf {

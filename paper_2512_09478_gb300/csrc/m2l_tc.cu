@@ -624,9 +624,12 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {
         // pipeline depth: time 2 .. the shared-memory maximum (at most five depths)
         float best = 1e30f;
         int pick = S.nstages;
+        KIFMM_CUDA_TRY(launch(S.nstages));  // warm the caches first
         for (int nst = S.nstages_max; nst >= std::max(2, S.nstages_max - 4); --nst) {
             cudaError_t e = cudaSuccess;
-            const float ms = time_launch(s, [&] { e = launch(nst); });
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2; ++rep)  // best of two
+                ms = std::min(ms, time_launch(s, [&] { e = launch(nst); }));
             KIFMM_CUDA_TRY(e);
             if (ms < best) {
                 best = ms;
