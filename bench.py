@@ -475,6 +475,11 @@ def run_ours(args, rank, world, local_rank):
     dominant = max((k for k in per_call if k in ("m2l", "p2p")), key=lambda k: prof["ms"][k])
     peaks = measured_peaks()
     roof = roofline_for(dominant, per_call[dominant], work, args.precision, peaks)
+    try:
+        from paper_2512_09478_gb300.kifmm import measure_peaks
+        unit_peaks = measure_peaks()  # this device's FMA / rsqrt / tcgen05 rates, for context
+    except Exception as e:  # reported, never fatal for the benchmark line
+        unit_peaks = {"error": str(e)}
     other = {s: roofline_for(s, per_call[s], work, args.precision, peaks) for s in ("m2l", "p2p", "tree")
              if s in per_call}
     cfg = {"workload": w["name"], "n": n_job, "systems": n_sys_job, "p": w["p"], "leaf_cap": w["leaf_cap"],
@@ -498,7 +503,8 @@ def run_ours(args, rank, world, local_rank):
            "roofline": roof, "stage_rooflines": other,
            "stages_ms": {k: round(v / max(calls[k], 1) * (calls[k] / args.steps), 4)
                          for k, v in prof["ms"].items() if calls[k] > 0},
-           "stages_note": prof_note, "gpu_launches": launches, "clocks": clk, "e2e": e2e}
+           "stages_note": prof_note, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
+           "unit_peaks_measured": unit_peaks}
     ref = None
     if not args.no_cpu_baseline:
         base, ref = cpu_baseline_leg(x, q, meta, w, args.accuracy_targets)

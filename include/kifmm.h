@@ -258,6 +258,25 @@ typedef struct {
 } kifmm_tuning_t;
 kifmm_status kifmm_get_tuning(kifmm_plan *plan, kifmm_tuning_t *out);
 
+/* Peak rates of the units the hot path uses, measured on the current device
+ * (no counterpart in the paper: roofline denominators).  FP32 and FP64 FMA
+ * (2 flop each), FP32 reciprocal square roots per second (rsqrt.approx), and
+ * the tcgen05 kind::f16 MMA in the M2L kernel's shape (M = 128, K = 16,
+ * 64-byte swizzled K-major operands) for N = 160 and 256.  Runs for a few
+ * tens of milliseconds on `stream` and synchronises; allocates 68 bytes of
+ * scratch.  Errors: KIFMM_ERR_ARG (out NULL), KIFMM_ERR_CUDA,
+ * KIFMM_ERR_TIMEOUT (an MMA wait ran out; the device stays usable). */
+typedef struct {
+    double fp32_fma_tflops;
+    double fp64_fma_tflops;
+    double rsqrt_per_s;
+    double f16_mma_n160_tflops;
+    double f16_mma_n256_tflops;
+    int sms;
+    double clock_mhz;
+} kifmm_peaks_t;
+kifmm_status kifmm_measure_peaks(kifmm_peaks_t *out, kifmm_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Introspection (tests and tools).  All outputs are host buffers sized by
  * the caller from kifmm_tree_info; nodes are in canonical order (system,

@@ -53,12 +53,18 @@ class TuningT(ctypes.Structure):
                 ("leaf_groups", ctypes.c_int * 16), ("leaf_small_kernel", ctypes.c_int)]
 
 
+class PeaksT(ctypes.Structure):
+    _fields_ = [("fp32_fma_tflops", ctypes.c_double), ("fp64_fma_tflops", ctypes.c_double),
+                ("rsqrt_per_s", ctypes.c_double), ("f16_mma_n160_tflops", ctypes.c_double),
+                ("f16_mma_n256_tflops", ctypes.c_double), ("sms", ctypes.c_int), ("clock_mhz", ctypes.c_double)]
+
+
 _LIB = None
 EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifmm_evaluate",
            "kifmm_clump_reduce", "kifmm_backward", "kifmm_get_device_status", "kifmm_status_string",
            "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
            "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources",
-           "kifmm_get_tuning", "kifmm_energy_noalloc"]
+           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_measure_peaks"]
 
 
 def load(path: str = LIB_PATH):
@@ -337,3 +343,12 @@ def potential(x, q, plan, rebuild=True):
 def energy(x, q, plan, rebuild=True):
     """Differentiable long-range energy U = 1/2 sum_i q_i pot_i (Sec. 2.4)."""
     return 0.5 * torch.dot(q, potential(x, q, plan, rebuild))
+
+
+def measure_peaks() -> dict:
+    """Peak rates of the FP32/FP64 FMA, rsqrt and tcgen05 f16 MMA units of the
+    current device (kifmm_measure_peaks)."""
+    out = PeaksT()
+    _check(load().kifmm_measure_peaks(ctypes.byref(out), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+           "kifmm_measure_peaks")
+    return {f: getattr(out, f) for f, _ in PeaksT._fields_}
