@@ -245,6 +245,8 @@ def _oracle_sample(x, q, meta, w, frac):
         return [(x[sel], q[sel])], "central cube"
     lo = x.min(axis=0)
     side = (x.max(axis=0) - lo).max()
+    if frac >= 1.0:
+        return [(x, q)], "whole workload"
     sel = np.all(x - lo < side * frac ** (1.0 / 3.0), axis=1)
     return [(x[sel], q[sel])], "corner sub-cube"
 
@@ -524,7 +526,6 @@ def run_ours(args, rank, world, local_rank):
         cfg["rsa_solid_fraction"] = round(meta["solid_fraction"], 4)
     tun = plan.tuning()
     cfg["tiles"] = {"autotuned": tun["tuned_leaf"], "m2l_stages": tun["m2l_stages"],
-                    "leaf_small_kernel": tun["leaf_small_kernel"],
                     "leaf_tpl_x_groups_per_8_targets": ["%dx%d" % t for t in tun["leaf_tiles"]]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

@@ -243,18 +243,16 @@ kifmm_status kifmm_profile_read(kifmm_plan *plan, kifmm_profile_t *out);
 /* Tile shapes in use (no counterpart in the paper: the benchmark spec asks for
  * M2L/P2P tile shapes chosen by an autotuner).  tuned: bit 0 leaf kernel,
  * bit 1 tensor-core M2L.  m2l_stages: shared-memory pipeline depth of the
- * tensor-core M2L (0 when the plan has none).  Leaf kernel: for a leaf with
- * r targets still to cover, bucket min((r - 1) / 8, 15) selects leaf_tpl
- * targets per lane and leaf_groups source groups (a warp covers
- * 32 / groups * tpl targets per pass).  leaf_small_kernel: 1 when leaves
- * covered in one pass with tpl <= 2 run in a separate low-register kernel.
+ * tensor-core M2L (0 when the plan has none).  Leaf kernel: a leaf with
+ * r targets is evaluated by the variant of bucket min((r - 1) / 8, 15):
+ * leaf_tpl targets per lane and leaf_groups source groups, in passes of
+ * 32 / groups * tpl targets; each variant is its own kernel.
  * Host memory; no device work. */
 typedef struct {
     int tuned;
     int m2l_stages;
     int leaf_tpl[16];
     int leaf_groups[16];
-    int leaf_small_kernel;
 } kifmm_tuning_t;
 kifmm_status kifmm_get_tuning(kifmm_plan *plan, kifmm_tuning_t *out);
 

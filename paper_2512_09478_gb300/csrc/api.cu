@@ -58,15 +58,14 @@ static cudaError_t profile_collect(Plan &P) {
 }
 
 LeafTiling leaf_tiling_candidate(int c) {
-    static const int fam[kLeafTilingCandidates / 2][2] = {{4, 2}, {2, 2}, {4, 1}, {2, 1}, {1, 1}, {1, 2}};
-    const int gs = fam[c / 2][0], gm = fam[c / 2][1];
+    static const int fam[kLeafTilingCandidates][2] = {{4, 2}, {2, 2}, {4, 1}, {2, 1}, {1, 1}, {1, 2}};
+    const int gs = fam[c][0], gm = fam[c][1];
     LeafTiling t{};
-    t.small_class = (c % 2 == 0);
     for (int i = 0; i < kLeafBuckets; ++i) {
         const int r = (i == kLeafBuckets - 1) ? 128 : 8 * (i + 1);
         const int g = (r <= 32) ? gs : (r <= 64 ? gm : 1);
-        const int tpl = std::min(4, std::max(1, (r * g + 31) / 32));
-        t.set(i, (g == 4 ? 0 : g == 2 ? 4 : 8) + tpl - 1);
+        const int tpl = std::min(2, std::max(1, (r * g + 31) / 32));
+        t.set(i, (g == 4 ? 0 : g == 2 ? 2 : 4) + tpl - 1);
     }
     return t;
 }
@@ -167,6 +166,8 @@ static cudaError_t ensure_box_arrays(Plan &P) {
         {&P.tmp_chk, esz * P.ns * cap},
         {&P.dn_dens, esz * P.ns * cap},
         {(void **)&P.dbar, sizeof(double) * cap},
+        {(void **)&P.leaf_vlist, sizeof(int32_t) * kLeafTiles * cap},
+        {(void **)&P.leaf_vcnt, sizeof(int32_t) * 8},
     };
     for (const A &a : arrs) KIFMM_CUDA_TRY(plan_alloc(P, a.p, a.bytes));
     P.list_cap = cap;
@@ -461,7 +462,6 @@ kifmm_status kifmm_get_tuning(kifmm_plan *pl, kifmm_tuning_t *out) {
         out->leaf_tpl[i] = leaf_tile_tpl(P.leaf_tile.get(i));
         out->leaf_groups[i] = leaf_tile_groups(P.leaf_tile.get(i));
     }
-    out->leaf_small_kernel = P.leaf_tile.small_class;
     return KIFMM_OK;
 }
 

@@ -87,6 +87,20 @@ __device__ __forceinline__ void lap_accum(T rx, T ry, T rz, T w, T &pot, T &gx, 
     gz -= rz * wr3;
 }
 
+// The same without the r = 0 test, for sources that cannot coincide with
+// the target.
+template <typename T>
+__device__ __forceinline__ void lap_accum_nz(T rx, T ry, T rz, T w, T &pot, T &gx, T &gy, T &gz) {
+    const T r2 = rx * rx + ry * ry + rz * rz;
+    const T rinv = rsqrt_t<T>(r2);
+    const T wr = w * rinv;
+    const T wr3 = wr * rinv * rinv;
+    pot += wr;
+    gx -= rx * wr3;
+    gy -= ry * wr3;
+    gz -= rz * wr3;
+}
+
 template <typename T>
 __device__ __forceinline__ T lap_pot(T rx, T ry, T rz) {
     const T r2 = rx * rx + ry * ry + rz * rz;

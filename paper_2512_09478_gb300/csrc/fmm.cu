@@ -329,26 +329,58 @@ __global__ void __launch_bounds__(32 * NTY) k_ggemm(G g, const int32_t *__restri
 // ---------------------------------------------------------------------------
 // Leaf evaluation, one warp per target leaf: far field (L2P from the leaf's
 // downward density on DE = 2.95 h S; M2P from the upward densities on
-// UE = 1.05 h S of the W-list boxes) and near field (P2P over the U list),
-// all as one stream of (pseudo-)sources {position relative to the leaf
-// centre, weight} staged in shared memory.
+// UE = 1.05 h S of the W-list boxes) and near field (P2P over the U list).
+// All of it is one stream of (pseudo-)sources {position relative to the leaf
+// centre, weight}: the segments (own surface, W surfaces, U leaves) are laid
+// end to end, and the stream is staged through shared memory in chunks of
+// 128.  The next chunk's loads are issued before the current chunk is
+// summed, so their latency overlaps the arithmetic.
 //
 // Tiling <TPL, G>: the warp splits into G groups of 32/G lanes; lane m of a
 // group owns targets tbase + m + (32/G) k (k < TPL) and the group takes every
-// G-th source of each staged chunk.  Up to 64 sources per lane are summed
-// plainly, then added to the totals with two-sum; the groups' totals are
-// combined in FP64 with shuffles and the result overwrites res.  The tile is picked per leaf so
-// that (32/G) TPL covers its targets with little waste.
+// G-th source of each chunk.  Up to 64 sources per lane are summed plainly,
+// then added to the totals with two-sum; the groups' totals are combined in
+// FP64 with shuffles and the result overwrites res.  The tile is picked per
+// leaf so that (32/G) TPL covers its targets with little waste.
+//
+// Only the leaf's own particles can sit at distance zero from a target (a
+// particle's own position, or a coincident particle: equal positions have
+// equal keys, hence the same leaf); that segment is summed with the r = 0
+// test, every other one without it.  Distinct particles of different leaves
+// whose separation rounds to zero in the compute type would give a
+// non-finite sum: the kernel reports KIFMM_ERR_NONFINITE for them.
 // ---------------------------------------------------------------------------
-constexpr int kLW = 4;
-constexpr int kLChunk = 128;
+constexpr int kLW = 4;               // warps (target leaves) per block
+constexpr int kLK = 4;               // sources per lane per chunk
+constexpr int kLChunk = 32 * kLK;    // sources per staged chunk
+constexpr int kLFlush = 64;          // sources per lane summed plainly before a compensated flush
+constexpr int kLSeg = 32;            // segments per batch (one per lane)
 
-constexpr int kLFlush = 64;  // sources per lane summed plainly before a compensated flush
+template <typename T>
+__device__ __forceinline__ T pow2(int e);
+template <>
+__device__ __forceinline__ float pow2<float>(int e) {
+    return __int_as_float((127 + e) << 23);
+}
+template <>
+__device__ __forceinline__ double pow2<double>(int e) {
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// c_a - c_b along one axis for boxes (level, integer coordinate): both
+// centres are odd multiples of 2^-(level+1), so the difference is an integer
+// below 2^22 times 2^-(L+1) and exact in FP32.
+template <typename T>
+__device__ __forceinline__ T centre_diff(int ca, int la, int cb, int lb) {
+    const int L = max(la, lb);
+    const int na = (2 * ca + 1) << (L - la), nb = (2 * cb + 1) << (L - lb);
+    return (T)(na - nb) * pow2<T>(-(L + 1));
+}
 
 template <typename T, int TPL>
 struct LeafAcc {
     T tx[TPL], ty[TPL], tz[TPL];
-    T part[TPL][4];             // plain FP32 partial sums since the last flush
+    T part[TPL][4];             // plain partial sums since the last flush
     T acc[TPL][4], cmp[TPL][4]; // compensated totals (two-sum)
     int pend;                   // sources per lane in part (warp-uniform bound)
 };
@@ -368,19 +400,22 @@ __device__ __forceinline__ void leaf_flush(LeafAcc<T, TPL> &L) {
     L.pend = 0;
 }
 
-template <typename T, int TPL, int G>
-__device__ __forceinline__ void leaf_chunk(LeafAcc<T, TPL> &L, const typename Vec4<T>::type *buf, int m, int grp) {
-#pragma unroll 2
-    for (int j = grp; j < m; j += G) {
-        const auto s = buf[j];
-#pragma unroll
-        for (int k = 0; k < TPL; ++k)
-            lap_accum<T>(L.tx[k] - s.x, L.ty[k] - s.y, L.tz[k] - s.z, s.w, L.part[k][0], L.part[k][1],
-                         L.part[k][2], L.part[k][3]);
-    }
-    L.pend += (m + G - 1) / G;
-    if (L.pend >= kLFlush) leaf_flush<T, TPL>(L);
-}
+// One segment of the source stream: positions are r * raw + o (surfaces:
+// unit-surface points; particles: r = 1, raw = position in the source leaf's
+// frame), weights hw * raw weight.
+template <typename T>
+struct LeafSeg {
+    T ox, oy, oz, r, hw;
+    int base;   // first particle, or first weight of the surface
+    int kind;   // 0 own surface, 1 W-list surface, 2 particles
+};
+
+template <typename T>
+struct LeafSmem {
+    typename Vec4<T>::type buf[2][kLChunk];
+    LeafSeg<T> seg[kLSeg];
+    int start[kLSeg];
+};
 
 struct LeafCtx {
     const int32_t *lvl, *cx, *cy, *cz, *first, *cnt;
@@ -389,6 +424,7 @@ struct LeafCtx {
     int ns;
     const double *dbar;  // per-box mean of the downward check potential, or nullptr
     LeafTiling tile;     // tile id per remaining-target bucket
+    int *status;         // device status word
 };
 
 // Source weights of the leaf stage.  Forward: own surface dn_dens * h_b,
@@ -403,15 +439,102 @@ struct LeafW {
     const T *pw;  // sorted per-particle weights, or nullptr for the charges
 };
 
+// Sources j in [lo, hi) of a staged chunk with j = grp (mod G).
+template <typename T, int TPL, int G, bool CHECK>
+__device__ __forceinline__ void leaf_range(LeafAcc<T, TPL> &L, const typename Vec4<T>::type *buf, int lo, int hi,
+                                           int grp) {
+    // sources in flight per iteration: about four pair evaluations per lane
+    constexpr int UNR = (sizeof(T) == 8 || TPL >= 3) ? 1 : (TPL == 2 ? 2 : 4);
+#pragma unroll UNR
+    for (int j = lo + ((grp - lo) & (G - 1)); j < hi; j += G) {
+        const auto s = buf[j];
+#pragma unroll
+        for (int k = 0; k < TPL; ++k) {
+            if constexpr (CHECK)
+                lap_accum<T>(L.tx[k] - s.x, L.ty[k] - s.y, L.tz[k] - s.z, s.w, L.part[k][0], L.part[k][1],
+                             L.part[k][2], L.part[k][3]);
+            else
+                lap_accum_nz<T>(L.tx[k] - s.x, L.ty[k] - s.y, L.tz[k] - s.z, s.w, L.part[k][0], L.part[k][1],
+                                L.part[k][2], L.part[k][3]);
+        }
+    }
+}
+
+// A staged chunk of m sources; [olo, ohi) are the leaf's own particles.
+// Sub-blocks of kLFlush G sources keep every plain partial sum to at most
+// kLFlush terms.
+template <typename T, int TPL, int G>
+__device__ __forceinline__ void leaf_chunk(LeafAcc<T, TPL> &L, const typename Vec4<T>::type *buf, int m, int olo,
+                                           int ohi, int grp) {
+    for (int s0 = 0; s0 < m; s0 += kLFlush * G) {
+        const int s1 = min(m, s0 + kLFlush * G);
+        const int a = max(s0, min(s1, olo)), e = max(a, min(s1, ohi));
+        leaf_range<T, TPL, G, false>(L, buf, s0, a, grp);
+        if (a < e) leaf_range<T, TPL, G, true>(L, buf, a, e, grp);
+        leaf_range<T, TPL, G, false>(L, buf, e, s1, grp);
+        L.pend += (s1 - s0 + G - 1) / G;
+        if (L.pend >= kLFlush) leaf_flush<T, TPL>(L);
+    }
+}
+
+// Loads of chunk c of a batch: lane l takes stream entries c kLChunk + l + 32 i.
+template <typename T>
+__device__ __forceinline__ void leaf_fetch(const LeafSmem<T> &S, int c, int total, int nb,
+                                           const typename Vec4<T>::type *__restrict__ pts,
+                                           const T *__restrict__ surf, const LeafW<T> &W,
+                                           typename Vec4<T>::type (&raw)[kLK], int (&rs)[kLK]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < kLK; ++i) {
+        const int j = c * kLChunk + lane + 32 * i;
+        rs[i] = -1;
+        if (j < total) {
+            int s = 0;
+#pragma unroll
+            for (int step = kLSeg / 2; step > 0; step >>= 1)
+                if (s + step < nb && S.start[s + step] <= j) s += step;
+            const int k = j - S.start[s];
+            const int kind = S.seg[s].kind, base = S.seg[s].base;
+            rs[i] = s;
+            if (kind == 2) {
+                raw[i] = pts[base + k];
+                if (W.pw) raw[i].w = W.pw[base + k];
+            } else {
+                raw[i].x = surf[3 * k];
+                raw[i].y = surf[3 * k + 1];
+                raw[i].z = surf[3 * k + 2];
+                raw[i].w = (kind == 0 ? W.own : W.wl)[base + k];
+            }
+        }
+    }
+}
+
+// Place fetched entries (segment transform applied) in staging buffer slot.
+template <typename T>
+__device__ __forceinline__ void leaf_store(LeafSmem<T> &S, int slot, const typename Vec4<T>::type (&raw)[kLK],
+                                           const int (&rs)[kLK]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < kLK; ++i) {
+        if (rs[i] < 0) continue;
+        const LeafSeg<T> g = S.seg[rs[i]];
+        typename Vec4<T>::type v;
+        v.x = g.r * raw[i].x + g.ox;
+        v.y = g.r * raw[i].y + g.oy;
+        v.z = g.r * raw[i].z + g.oz;
+        v.w = raw[i].w * g.hw;
+        S.buf[slot][lane + 32 * i] = v;
+    }
+}
+
 template <typename T, int TPL, int G>
 __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec4<T>::type *__restrict__ pts,
-                          const T *__restrict__ surf, const LeafW<T> &W, typename Vec4<T>::type *buf,
+                          const T *__restrict__ surf, const LeafW<T> &W, LeafSmem<T> &S,
                           double4 *__restrict__ res) {
     using V4 = typename Vec4<T>::type;
     constexpr int LG = 32 / G;  // lanes per group
     const int lane = threadIdx.x & 31, grp = lane / LG, mem = lane % LG;
-    const int lb = C.lvl[b];
-    const T cbx = box_center<T>(C.cx[b], lb), cby = box_center<T>(C.cy[b], lb), cbz = box_center<T>(C.cz[b], lb);
+    const int lb = C.lvl[b], bx = C.cx[b], by = C.cy[b], bz = C.cz[b];
     const int n = C.cnt[b], f = C.first[b], ns = C.ns;
     LeafAcc<T, TPL> L;
 #pragma unroll
@@ -426,68 +549,68 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
         for (int c = 0; c < 4; ++c) L.part[k][c] = L.acc[k][c] = L.cmp[k][c] = T(0);
     }
     L.pend = 0;
-    // L2P: own downward equivalent surface
-    {
-        const T h = box_half<T>(lb), r = (T)kAlphaOuter * h;
-        for (int c0 = 0; c0 < ns; c0 += kLChunk) {
-            const int m = min(kLChunk, ns - c0);
-            __syncwarp();
-            for (int j = lane; j < m; j += 32) {
-                const int k = c0 + j;
-                V4 w;
-                w.x = r * surf[3 * k];
-                w.y = r * surf[3 * k + 1];
-                w.z = r * surf[3 * k + 2];
-                w.w = W.own[(size_t)b * ns + k] * (W.own_h ? h : T(1));
-                buf[j] = w;
-            }
-            __syncwarp();
-            leaf_chunk<T, TPL, G>(L, buf, m, grp);
+    const uint32_t w0 = C.w_ptr[b], u0 = C.u_ptr[b];
+    const int nw = (int)(C.w_ptr[b + 1] - w0), nu = (int)(C.u_ptr[b + 1] - u0);
+    const int nseg = 1 + nw + nu;
+    for (int sb = 0; sb < nseg; sb += kLSeg) {
+        // lane e describes segment sb + e of (own surface, W list, U list)
+        const int e = sb + lane;
+        LeafSeg<T> d{T(0), T(0), T(0), T(1), T(1), 0, 2};
+        int cnt = 0, own = 0;
+        if (e == 0) {
+            d.r = (T)kAlphaOuter * pow2<T>(-(lb + 1));
+            d.hw = W.own_h ? pow2<T>(-(lb + 1)) : T(1);
+            d.base = b * ns;
+            d.kind = 0;
+            cnt = ns;
+        } else if (e <= nw) {
+            const int a = C.w_idx[w0 + e - 1], la = C.lvl[a];
+            d.ox = centre_diff<T>(C.cx[a], la, bx, lb);
+            d.oy = centre_diff<T>(C.cy[a], la, by, lb);
+            d.oz = centre_diff<T>(C.cz[a], la, bz, lb);
+            d.r = (T)kAlphaInner * pow2<T>(-(la + 1));
+            d.hw = W.wl_h ? pow2<T>(-(la + 1)) : T(1);
+            d.base = a * ns;
+            d.kind = 1;
+            cnt = ns;
+        } else if (e < nseg) {
+            const int a = C.u_idx[u0 + e - 1 - nw], la = C.lvl[a];
+            d.ox = centre_diff<T>(C.cx[a], la, bx, lb);
+            d.oy = centre_diff<T>(C.cy[a], la, by, lb);
+            d.oz = centre_diff<T>(C.cz[a], la, bz, lb);
+            d.base = C.first[a];
+            cnt = C.cnt[a];
+            own = (a == b);
         }
-    }
-    // M2P: upward equivalent surfaces of the W list
-    for (uint32_t e = C.w_ptr[b]; e < C.w_ptr[b + 1]; ++e) {
-        const int a = C.w_idx[e];
-        const int la = C.lvl[a];
-        const T ha = box_half<T>(la), r = (T)kAlphaInner * ha;
-        const T ox = box_center<T>(C.cx[a], la) - cbx, oy = box_center<T>(C.cy[a], la) - cby,
-                oz = box_center<T>(C.cz[a], la) - cbz;
-        for (int c0 = 0; c0 < ns; c0 += kLChunk) {
-            const int m = min(kLChunk, ns - c0);
-            __syncwarp();
-            for (int j = lane; j < m; j += 32) {
-                const int k = c0 + j;
-                V4 w;
-                w.x = ox + r * surf[3 * k];
-                w.y = oy + r * surf[3 * k + 1];
-                w.z = oz + r * surf[3 * k + 2];
-                w.w = W.wl[(size_t)a * ns + k] * (W.wl_h ? ha : T(1));
-                buf[j] = w;
-            }
-            __syncwarp();
-            leaf_chunk<T, TPL, G>(L, buf, m, grp);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-    }
-    // P2P: particles of the U list
-    for (uint32_t e = C.u_ptr[b]; e < C.u_ptr[b + 1]; ++e) {
-        const int a = C.u_idx[e];
-        const int la = C.lvl[a];
-        const T ox = box_center<T>(C.cx[a], la) - cbx, oy = box_center<T>(C.cy[a], la) - cby,
-                oz = box_center<T>(C.cz[a], la) - cbz;
-        const int na = C.cnt[a], fa = C.first[a];
-        for (int c0 = 0; c0 < na; c0 += kLChunk) {
-            const int m = min(kLChunk, na - c0);
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const unsigned own_mask = __ballot_sync(0xffffffffu, own);
+        int olo = 0, ohi = 0;
+        if (own_mask) {
+            const int o = __ffs(own_mask) - 1;
+            ohi = __shfl_sync(0xffffffffu, incl, o);
+            olo = ohi - __shfl_sync(0xffffffffu, cnt, o);
+        }
+        __syncwarp();  // the previous batch is done with seg, start and buf
+        S.seg[lane] = d;
+        S.start[lane] = (e < nseg) ? incl - cnt : total;
+        __syncwarp();
+        const int nb = min(kLSeg, nseg - sb);
+        typename Vec4<T>::type raw[kLK];
+        int rs[kLK];
+        const int nchunks = (total + kLChunk - 1) / kLChunk;
+        for (int c = 0; c < nchunks; ++c) {
+            // double-buffered: the slot written here was last read two chunks ago
+            leaf_fetch<T>(S, c, total, nb, pts, surf, W, raw, rs);
+            leaf_store<T>(S, c & 1, raw, rs);
             __syncwarp();
-            for (int j = lane; j < m; j += 32) {
-                V4 w = pts[fa + c0 + j];
-                if (W.pw) w.w = W.pw[fa + c0 + j];
-                w.x += ox;
-                w.y += oy;
-                w.z += oz;
-                buf[j] = w;
-            }
-            __syncwarp();
-            leaf_chunk<T, TPL, G>(L, buf, m, grp);
+            const int c0 = c * kLChunk;
+            leaf_chunk<T, TPL, G>(L, S.buf[c & 1], min(kLChunk, total - c0), olo - c0, ohi - c0, grp);
         }
     }
     leaf_flush<T, TPL>(L);
@@ -502,87 +625,78 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
         }
         if (C.dbar) tot[0] += C.dbar[b];  // the constant part of the local expansion
         const int i = tbase + mem + LG * k;
-        if (grp == 0 && i < n) res[f + i] = make_double4(tot[0], tot[1], tot[2], tot[3]);
-    }
-}
-
-// Targets [t0, n) of leaf b: the tile the plan's table gives for the
-// remainder (bucket (r - 1) / 8, the last bucket beyond 128), repeated until
-// every target is covered.
-template <typename T>
-__device__ void leaf_dispatch(const LeafCtx &C, int b, int n, const typename Vec4<T>::type *__restrict__ pts,
-                              const T *__restrict__ surf, const LeafW<T> &W, typename Vec4<T>::type *buf,
-                              double4 *__restrict__ res) {
-    for (int t0 = 0; t0 < n;) {
-        const int r = n - t0;
-        const int id = C.tile.for_targets(r);
-        switch (id) {
-            case 0: leaf_pass<T, 1, 4>(C, b, t0, pts, surf, W, buf, res); break;
-            case 1: leaf_pass<T, 2, 4>(C, b, t0, pts, surf, W, buf, res); break;
-            case 2: leaf_pass<T, 3, 4>(C, b, t0, pts, surf, W, buf, res); break;
-            case 3: leaf_pass<T, 4, 4>(C, b, t0, pts, surf, W, buf, res); break;
-            case 4: leaf_pass<T, 1, 2>(C, b, t0, pts, surf, W, buf, res); break;
-            case 5: leaf_pass<T, 2, 2>(C, b, t0, pts, surf, W, buf, res); break;
-            case 6: leaf_pass<T, 3, 2>(C, b, t0, pts, surf, W, buf, res); break;
-            case 7: leaf_pass<T, 4, 2>(C, b, t0, pts, surf, W, buf, res); break;
-            case 8: leaf_pass<T, 1, 1>(C, b, t0, pts, surf, W, buf, res); break;
-            case 9: leaf_pass<T, 2, 1>(C, b, t0, pts, surf, W, buf, res); break;
-            case 10: leaf_pass<T, 3, 1>(C, b, t0, pts, surf, W, buf, res); break;
-            default: leaf_pass<T, 4, 1>(C, b, t0, pts, surf, W, buf, res); break;
+        if (grp == 0 && i < n) {
+            res[f + i] = make_double4(tot[0], tot[1], tot[2], tot[3]);
+            if (!isfinite(tot[0] + tot[1] + tot[2] + tot[3])) set_status(C.status, KIFMM_ERR_NONFINITE);
         }
-        t0 += (32 / leaf_tile_groups(id)) * leaf_tile_tpl(id);
+    }
+}
+// Leaf variants: the tile of a leaf is the plan table's entry for its
+// target count (leaf_variant); one kernel per variant, so each runs with the
+// registers its tile needs.  A leaf is covered in passes of (32 / G) TPL
+// targets.  k_leaf_partition lists the leaves of each variant (order within
+// a list is immaterial: leaves are independent).
+__global__ void k_leaf_partition(int64_t n_leaves, const int32_t *__restrict__ leaves,
+                                 const int32_t *__restrict__ cnt, LeafTiling tile, int64_t cap,
+                                 int32_t *__restrict__ lists, int32_t *__restrict__ counts) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < n_leaves;
+    const int b = valid ? leaves[i] : -1;
+    const int v = valid ? leaf_variant(tile, cnt[b]) : -1;
+#pragma unroll
+    for (int u = 0; u < kLeafTiles; ++u) {
+        const unsigned m = __ballot_sync(0xffffffffu, v == u);
+        if (m == 0) continue;
+        const int leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&counts[u], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (v == u) lists[(int64_t)u * cap + base + __popc(m & ((1u << lane) - 1))] = b;
     }
 }
 
-// A leaf belongs to the small class when the tile for all of its targets has
-// at most two targets per lane and covers it in one pass; the small-class
-// kernel holds only those tiles, so it needs few registers and runs at twice
-// the occupancy of the general kernel.
-__device__ __forceinline__ bool leaf_small_class(const LeafTiling &t, int n) {
-    const int id = t.for_targets(n);
-    return t.small_class && n > 0 && leaf_tile_tpl(id) <= 2 && (32 / leaf_tile_groups(id)) * leaf_tile_tpl(id) >= n;
-}
-
-template <typename T>
-__device__ void leaf_dispatch_small(const LeafCtx &C, int b, int n, const typename Vec4<T>::type *__restrict__ pts,
-                                    const T *__restrict__ surf, const LeafW<T> &W, typename Vec4<T>::type *buf,
-                                    double4 *__restrict__ res) {
-    switch (C.tile.for_targets(n)) {
-        case 0: leaf_pass<T, 1, 4>(C, b, 0, pts, surf, W, buf, res); break;
-        case 1: leaf_pass<T, 2, 4>(C, b, 0, pts, surf, W, buf, res); break;
-        case 4: leaf_pass<T, 1, 2>(C, b, 0, pts, surf, W, buf, res); break;
-        case 5: leaf_pass<T, 2, 2>(C, b, 0, pts, surf, W, buf, res); break;
-        case 8: leaf_pass<T, 1, 1>(C, b, 0, pts, surf, W, buf, res); break;
-        default: leaf_pass<T, 2, 1>(C, b, 0, pts, surf, W, buf, res); break;
-    }
-}
-
-template <typename T, bool SMALL>
-__global__ void __launch_bounds__(32 * kLW, sizeof(T) == 4 ? (SMALL ? 6 : 4) : 1) k_leaf_all(LeafCtx C, int64_t n_leaves,
-                                                                       const int32_t *__restrict__ leaves,
-                                                                       const typename Vec4<T>::type *__restrict__ pts,
-                                                                       const T *__restrict__ surf, LeafW<T> W,
-                                                                       double4 *__restrict__ res) {
-    __shared__ typename Vec4<T>::type bufs[kLW][kLChunk];
+template <typename T, int TPL, int G>
+__global__ void __launch_bounds__(32 * kLW, sizeof(T) == 4 ? (TPL == 1 ? 6 : 5) : 2)
+    k_leaf_all(LeafCtx C, const int32_t *__restrict__ list, const int32_t *__restrict__ count,
+               const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, LeafW<T> W,
+               double4 *__restrict__ res) {
+    __shared__ LeafSmem<T> bufs[kLW];
     const int warp = threadIdx.x >> 5;
-    const int64_t li = (int64_t)blockIdx.x * kLW + warp;
-    if (li >= n_leaves) return;
-    const int b = leaves[li];
-    const int n = C.cnt[b];
-    if (leaf_small_class(C.tile, n) != SMALL) return;  // the other class's launch covers it
-    if constexpr (SMALL)
-        leaf_dispatch_small<T>(C, b, n, pts, surf, W, bufs[warp], res);
-    else
-        leaf_dispatch<T>(C, b, n, pts, surf, W, bufs[warp], res);
+    const int nl = *count;
+    for (int li = blockIdx.x * kLW + warp; li < nl; li += gridDim.x * kLW) {
+        const int b = list[li];
+        const int n = C.cnt[b];
+        for (int t0 = 0; t0 < n; t0 += (32 / G) * TPL) leaf_pass<T, TPL, G>(C, b, t0, pts, surf, W, bufs[warp], res);
+    }
 }
 
-// Both classes of the leaf kernel over all leaves.
+template <typename T, int TPL, int G>
+void leaf_launch_variant(const Plan &P, const LeafCtx &C, int v, const typename Vec4<T>::type *pts, const T *surf,
+                         const LeafW<T> &W, double4 *res, cudaStream_t s) {
+    constexpr int occ = sizeof(T) == 4 ? (TPL == 1 ? 6 : 5) : 2;
+    const int64_t want = (P.n_leaves + kLW - 1) / kLW;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P.num_sms * occ));
+    ++g_launches, k_leaf_all<T, TPL, G><<<g, 32 * kLW, 0, s>>>(C, P.leaf_vlist + (int64_t)v * P.list_cap,
+                                                                P.leaf_vcnt + v, pts, surf, W, res);
+}
+
+// All leaves: partition by variant, then one launch per variant the table uses.
 template <typename T>
 void leaf_launch(const Plan &P, const LeafCtx &C, const typename Vec4<T>::type *pts, const T *surf,
                  const LeafW<T> &W, double4 *res, cudaStream_t s) {
-    const unsigned g = (unsigned)((P.n_leaves + kLW - 1) / kLW);
-    ++g_launches, k_leaf_all<T, true><<<g, 32 * kLW, 0, s>>>(C, P.n_leaves, P.leaves, pts, surf, W, res);
-    ++g_launches, k_leaf_all<T, false><<<g, 32 * kLW, 0, s>>>(C, P.n_leaves, P.leaves, pts, surf, W, res);
+    if (P.n_leaves == 0) return;
+    cudaMemsetAsync(P.leaf_vcnt, 0, sizeof(int32_t) * kLeafTiles, s);
+    ++g_launches, k_leaf_partition<<<(unsigned)((P.n_leaves + 255) / 256), 256, 0, s>>>(
+                      P.n_leaves, P.leaves, P.cnt, C.tile, P.list_cap, P.leaf_vlist, P.leaf_vcnt);
+    bool used[kLeafTiles] = {false};
+    for (int i = 0; i < kLeafBuckets; ++i) used[C.tile.get(i)] = true;
+    if (used[0]) leaf_launch_variant<T, 1, 4>(P, C, 0, pts, surf, W, res, s);
+    if (used[1]) leaf_launch_variant<T, 2, 4>(P, C, 1, pts, surf, W, res, s);
+    if (used[2]) leaf_launch_variant<T, 1, 2>(P, C, 2, pts, surf, W, res, s);
+    if (used[3]) leaf_launch_variant<T, 2, 2>(P, C, 3, pts, surf, W, res, s);
+    if (used[4]) leaf_launch_variant<T, 1, 1>(P, C, 4, pts, surf, W, res, s);
+    if (used[5]) leaf_launch_variant<T, 2, 1>(P, C, 5, pts, surf, W, res, s);
 }
 
 // Scatter to caller order with 1/(4 pi), coef and physical units.
@@ -759,7 +873,7 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     stage_end(P, KIFMM_STAGE_LEAF, s);
     stage_begin(P, KIFMM_STAGE_P2P, s);
     LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns,
-              split_mean ? P.dbar : nullptr, P.leaf_tile};
+              split_mean ? P.dbar : nullptr, P.leaf_tile, P.status};
     const LeafW<T> W{(const T *)P.dn_dens, 1, (const T *)P.up_dens, 1, nullptr};
     if (!P.tuned_leaf && tuning_wanted(P, s)) {
         // time every candidate table on this tree; keep the fastest
@@ -885,7 +999,7 @@ cudaError_t backward_t(Plan &P, const void *w_user, const void *grad_user, void 
                          P.part_start[3].data() + 8 * l, 8, 1, ub, ub, 1, s);
     // P2M^T (own UC surface, u-bar), P2L^T (W boxes' DC surfaces, d-bar), P2P^T (weights w)
     LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns, nullptr,
-              P.leaf_tile};
+              P.leaf_tile, P.status};
     const LeafW<T> W{ub, 0, db, 0, ws};
     leaf_launch<T>(P, C, pts, surf, W, res, s);
     if (P.io_f64)

@@ -18,27 +18,27 @@ constexpr int kVSlots = 189;        // V-list slots per octant class (6^3 - 3^3)
 constexpr int kMaxCoarse = 26;      // coarser-or-equal adjacent leaves of a box
 constexpr int kColl = 27;           // colleague slots (3^3, centre = self)
 
-// Leaf-kernel tiles: id -> (targets per lane TPL, source groups G); a tile
-// covers (32 / G) TPL targets.  The table maps the number of targets still
-// to cover, in buckets of 8 (the last bucket: more than 120), to a tile.
-constexpr int kLeafTiles = 12;
+// Leaf-kernel tiles (variants): id -> (targets per lane TPL, source groups
+// G); a pass covers (32 / G) TPL targets.  The table maps a leaf's target
+// count, in buckets of 8 (the last bucket: more than 120), to the variant
+// that covers the whole leaf in passes.
+constexpr int kLeafTiles = 6;
 constexpr int kLeafBuckets = 16;
-constexpr int kLeafTilingCandidates = 12;
-__host__ __device__ constexpr int leaf_tile_tpl(int id) { return id % 4 + 1; }
-__host__ __device__ constexpr int leaf_tile_groups(int id) { return id < 4 ? 4 : (id < 8 ? 2 : 1); }
+constexpr int kLeafTilingCandidates = 6;
+__host__ __device__ constexpr int leaf_tile_tpl(int id) { return id % 2 + 1; }
+__host__ __device__ constexpr int leaf_tile_groups(int id) { return id < 2 ? 4 : (id < 4 ? 2 : 1); }
 struct LeafTiling {
     unsigned long long packed;  // 4 bits per bucket
-    int small_class;            // 1: leaves with <= 2 targets per lane go to the low-register kernel
     __host__ __device__ int get(int bucket) const { return (int)((packed >> (4 * bucket)) & 15ULL); }
     __host__ __device__ int for_targets(int r) const { return get((r - 1) >> 3 < kLeafBuckets ? (r - 1) >> 3 : kLeafBuckets - 1); }
     void set(int bucket, int id) {
         packed = (packed & ~(15ULL << (4 * bucket))) | ((unsigned long long)id << (4 * bucket));
     }
 };
+__host__ __device__ inline int leaf_variant(const LeafTiling &t, int n) { return t.for_targets(n > 0 ? n : 1); }
 // Candidate c of the tuner (c = 0 is the default): up to 32 targets use
-// g_small source groups, up to 64 use g_mid, beyond that one group, each with
-// the fewest targets per lane that cover the bucket; odd c keep every leaf
-// in the general kernel.
+// g_small source groups, up to 64 use g_mid, beyond that one group, each
+// with the fewest targets per lane (at most 2) that cover the bucket.
 LeafTiling leaf_tiling_candidate(int c);
 
 struct DevBuf {
@@ -135,6 +135,8 @@ struct Plan {
     int64_t m2l_class_start[9] = {0};
     int32_t *leaves = nullptr;       // [nb] leaf indices
     int64_t n_leaves = 0;
+    int32_t *leaf_vlist = nullptr;   // [kLeafTiles][list_cap] leaves of each leaf-kernel variant
+    int32_t *leaf_vcnt = nullptr;    // [8] leaves per variant
     int32_t *wsrc_flag = nullptr;    // [nb] 1 if the box is in some W list
     uint32_t *part_counts = nullptr; // [4][256]
     unsigned long long *list_totals = nullptr;  // [4] V and X list sizes

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             src_next[i] = (tg[i] >= 0) ? a.vdense[(size_t)tg[i] * kVSlots] : -1;
         }
         const bool leader = threadIdx.x == 0;
-        int o_cur = 0, last_it = -1;
+        int o_cur = 0, o_next = leader ? a.slot_off[cls * kVSlots] : 0, last_it = -1;
         for (int it = 0; it < iters; ++it) {
             const int stage = it % NS;
             const int s = it / kblocks, kb = it - s * kblocks;
@@ -143,7 +143,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
                     src[i] = src_next[i];
                     if (s + 1 < kVSlots) src_next[i] = (tg[i] >= 0) ? a.vdense[(size_t)tg[i] * kVSlots + s + 1] : -1;
                 }
-                if (leader) o_cur = a.slot_off[cls * kVSlots + s];
+                if (leader) {
+                    o_cur = o_next;
+                    if (s + 1 < kVSlots) o_next = a.slot_off[cls * kVSlots + s + 1];
+                }
             }
             if (!mbar_wait(smem_u32(&empty_bar[stage]), ((it / NS) & 1) ^ 1, &abort_s)) {
                 set_status(a.status, KIFMM_ERR_TIMEOUT);
@@ -415,7 +418,7 @@ cudaError_t m2l_tensor_setup(Plan &P) {
     S.np = S.nt * S.ncb;
     S.kp = round_up(ns, kKBlock);
     const size_t stage = 2 * (size_t)kTcRows * kRowBytes + 2 * (size_t)S.nt * kRowBytes;
-    S.nstages = (int)std::min<size_t>(16, (200 * 1024) / stage);
+    S.nstages = (int)std::min<size_t>(16, (227 * 1024 - 4096) / stage);
     if (S.nstages < 2 || S.nt > 160) return cudaErrorNotSupported;
     S.nstages_max = S.nstages;
     S.stage_bytes = stage;

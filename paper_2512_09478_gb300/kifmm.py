@@ -50,7 +50,7 @@ class ProfileT(ctypes.Structure):
 
 class TuningT(ctypes.Structure):
     _fields_ = [("tuned", ctypes.c_int), ("m2l_stages", ctypes.c_int), ("leaf_tpl", ctypes.c_int * 16),
-                ("leaf_groups", ctypes.c_int * 16), ("leaf_small_kernel", ctypes.c_int)]
+                ("leaf_groups", ctypes.c_int * 16)]
 
 
 class PeaksT(ctypes.Structure):
@@ -227,8 +227,7 @@ class Plan:
         t = TuningT()
         _check(load().kifmm_get_tuning(self._h, ctypes.byref(t)), "kifmm_get_tuning")
         return {"tuned_leaf": bool(t.tuned & 1), "tuned_m2l": bool(t.tuned & 2), "m2l_stages": t.m2l_stages,
-                "leaf_tiles": [(t.leaf_tpl[i], t.leaf_groups[i]) for i in range(16)],
-                "leaf_small_kernel": bool(t.leaf_small_kernel)}
+                "leaf_tiles": [(t.leaf_tpl[i], t.leaf_groups[i]) for i in range(16)]}
 
     def profile_read(self) -> dict:
         """Per-stage device milliseconds and bracket counts since the last
