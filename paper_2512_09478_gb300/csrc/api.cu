@@ -264,6 +264,7 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {(void **)&P.keys_user, sizeof(uint64_t) * n}, {(void **)&P.perm, sizeof(uint32_t) * n},
         {&P.pts, esz * 4 * n},                         {(void **)&P.res, sizeof(double) * 4 * n},
         {&P.w_sorted, esz * n},
+        {&P.gemm_part, esz * 8 * kSplitTargets * (size_t)(P.ns + 1)},
         {(void **)&P.sys_off_d, sizeof(int64_t) * (P.sys_cap + 1)},
         {(void **)&P.lo_side, sizeof(double) * 4 * P.sys_cap},
         {(void **)&P.bbox_ord, sizeof(unsigned long long) * 6 * P.sys_cap},

@@ -209,10 +209,16 @@ struct GatherSelf {
 // dbar[t] (FP64, plus the functor's mean_base) instead of out.
 // Tile: NTY warps; thread (tx, ty) owns targets RT ty .. RT ty + RT-1 and
 // outputs tx + 32 c (c < RC): TT = NTY RT targets by TJ = 32 RC outputs.
-template <typename T, class G, int NTY, int RT, int RC>
+// SPLIT: blockIdx.z = slot * ncb + column block; the block writes that
+// slot's partial product to part ([slot][target position][ld]) and
+// k_ggemm_sum adds the slots in order (the same arithmetic as the unsplit
+// form; used when few targets leave most SMs idle, e.g. the coarse levels of
+// M2M, whose latency is otherwise 8 slots x n_s / 16 dependent steps).
+template <typename T, class G, int NTY, int RT, int RC, bool SPLIT>
 __global__ void __launch_bounds__(32 * NTY) k_ggemm(G g, const int32_t *__restrict__ targets, ClassRanges cr,
                                                     int nslots, int ns, int ld, const T *__restrict__ in,
-                                                    T *__restrict__ out, int accumulate, double *dbar) {
+                                                    T *__restrict__ out, int accumulate, double *dbar, int ncb,
+                                                    T *__restrict__ part) {
     constexpr int TT = NTY * RT, TJ = 32 * RC, NT = 32 * NTY;
     __shared__ __align__(16) T Us[kGK][TT];
     __shared__ __align__(16) T Ms[kGK][TJ];
@@ -220,7 +226,8 @@ __global__ void __launch_bounds__(32 * NTY) k_ggemm(G g, const int32_t *__restri
     __shared__ int32_t src[TT];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int cls = blockIdx.y;
-    const int j0 = blockIdx.z * TJ;  // output columns [j0, j0 + TJ)
+    const int j0 = (SPLIT ? (int)blockIdx.z % ncb : (int)blockIdx.z) * TJ;  // output columns [j0, j0 + TJ)
+    const int s_lo = SPLIT ? (int)blockIdx.z / ncb : 0, s_hi = SPLIT ? s_lo + 1 : nslots;
     int64_t t_begin = 0, t_end = 0;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(32 * NTY) k_ggemm(G g, const int32_t *__restri
         for (int c = 0; c < RC; ++c) acc[a][c] = run[a][c] = T(0);
     const int nk = (ns + kGK - 1) / kGK;
     __syncthreads();
-    for (int s = 0; s < nslots; ++s) {
+    for (int s = s_lo; s < s_hi; ++s) {
         if (threadIdx.x < TT) {
             const int32_t t = tgt[threadIdx.x];
             src[threadIdx.x] = (t >= 0) ? g.src(t, s, cls) : -1;
@@ -316,13 +323,36 @@ __global__ void __launch_bounds__(32 * NTY) k_ggemm(G g, const int32_t *__restri
         for (int c = 0; c < RC; ++c) {
             const int j = j0 + tx + 32 * c;
             const T v = kTwoLevel ? run[a][c] : acc[a][c];
-            if (j < ns) {
+            if constexpr (SPLIT) {
+                if (j < ld)
+                    part[((size_t)s_lo * (size_t)(cr.b[gridDim.y] - cr.b[0]) + (size_t)(t0 + RT * ty + a - cr.b[0])) * ld +
+                         j] = v;
+            } else if (j < ns) {
                 T *o = out + (size_t)t * ns + j;
                 *o = accumulate ? *o + v : v;
             } else if (j == ns && dbar) {
                 dbar[t] = (accumulate ? dbar[t] : 0.0) + (double)v + g.mean_base(t, dbar);
             }
         }
+    }
+}
+
+// Slot-split form: out = the in-order sum of the slots' partial products.
+template <typename T, class G>
+__global__ void k_ggemm_sum(G g, const int32_t *__restrict__ targets, int64_t t_first, int64_t n_t, int nslots, int ns,
+                            int ld, const T *__restrict__ part, T *__restrict__ out, int accumulate, double *dbar) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_t * ld) return;
+    const int64_t i = idx / ld;
+    const int j = (int)(idx - i * ld);
+    T v = T(0);
+    for (int s = 0; s < nslots; ++s) v += part[((size_t)s * n_t + i) * ld + j];
+    const int32_t t = targets[t_first + i];
+    if (j < ns) {
+        T *o = out + (size_t)t * ns + j;
+        *o = accumulate ? *o + v : v;
+    } else if (j == ns && dbar) {
+        dbar[t] = (accumulate ? dbar[t] : 0.0) + (double)v + g.mean_base(t, dbar);
     }
 }
 
@@ -794,17 +824,31 @@ void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *s
     if (most <= 0) return;
     if (ld == 0) ld = P.ns;
     // 64 x 160 tiles while they fill the GPU twice over; else 16 x 32 tiles
-    // (the coarse levels of M2M / L2L and small trees are latency-bound).
+    // (the coarse levels of M2M / L2L and small trees are latency-bound),
+    // with up to 8 slots split over blocks when even those leave SMs idle.
     const int64_t big_blocks = grid_for(total, 64) * grid_for(ld, 160);
     if (big_blocks >= 2 * P.num_sms) {
         dim3 grid(grid_for(most, 64), ncls, grid_for(ld, 160));
-        ++g_launches, k_ggemm<T, G, 8, 8, 5><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,
-                                                                   accumulate, dbar);
-    } else {
-        dim3 grid(grid_for(most, 16), ncls, grid_for(ld, 32));
-        ++g_launches, k_ggemm<T, G, 4, 4, 1><<<grid, 128, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,
-                                                                   accumulate, dbar);
+        ++g_launches, k_ggemm<T, G, 8, 8, 5, false><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,
+                                                                          accumulate, dbar, 1, nullptr);
+        return;
     }
+    const int ncb = (int)grid_for(ld, 32);
+    int64_t small_blocks = 0;
+    for (int c = 0; c < ncls; ++c) small_blocks += grid_for(starts[c + 1] - starts[c], 16);
+    small_blocks *= ncb;
+    if (nslots > 1 && nslots <= 8 && total <= kSplitTargets && small_blocks < P.num_sms) {
+        T *part = (T *)P.gemm_part;
+        dim3 grid(grid_for(most, 16), ncls, ncb * nslots);
+        ++g_launches, k_ggemm<T, G, 4, 4, 1, true><<<grid, 128, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,
+                                                                         accumulate, dbar, ncb, part);
+        ++g_launches, k_ggemm_sum<T, G><<<grid_for(total * ld, 256), 256, 0, s>>>(
+                          g, targets, cr.b[0], total, nslots, P.ns, ld, part, out, accumulate, dbar);
+        return;
+    }
+    dim3 grid(grid_for(most, 16), ncls, ncb);
+    ++g_launches, k_ggemm<T, G, 4, 4, 1, false><<<grid, 128, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,
+                                                                      accumulate, dbar, ncb, nullptr);
 }
 
 template <typename T, class G>

@@ -17,6 +17,7 @@ constexpr int kNumM2L = 316;        // offsets in {-3..3}^3 minus {-1..1}^3
 constexpr int kVSlots = 189;        // V-list slots per octant class (6^3 - 3^3)
 constexpr int kMaxCoarse = 26;      // coarser-or-equal adjacent leaves of a box
 constexpr int kColl = 27;           // colleague slots (3^3, centre = self)
+constexpr int kSplitTargets = 640;  // targets of a gathered GEMM the slot-split form may take (up to 8 slots)
 
 // Leaf-kernel tiles (variants): id -> (targets per lane TPL, source groups
 // G); a pass covers (32 / G) TPL targets.  The table maps a leaf's target
@@ -149,6 +150,7 @@ struct Plan {
     std::vector<int64_t> part_start[4];  // host: exclusive prefix of the key counts (257 entries)
     int32_t *child8 = nullptr;       // [nb][8] child in each octant, -1 if none
     void *tmp_chk = nullptr;         // [nb][ns] pseudo-inverse scratch
+    void *gemm_part = nullptr;       // [8][kSplitTargets][ns + 1] slot partials of the slot-split gathered GEMM
     void *dn_dens = nullptr;         // [nb][ns] normalised downward densities of leaves
     int64_t list_cap = 0;            // boxes the per-box list/expansion arrays hold
 
