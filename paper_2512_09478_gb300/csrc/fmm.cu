@@ -212,8 +212,8 @@ struct GatherSelf {
 // SPLIT: blockIdx.z = slot * ncb + column block; the block writes that
 // slot's partial product to part ([slot][target position][ld]) and
 // k_ggemm_sum adds the slots in order (the same arithmetic as the unsplit
-// form; used when few targets leave most SMs idle, e.g. the coarse levels of
-// M2M, whose latency is otherwise 8 slots x n_s / 16 dependent steps).
+// form; used for the small-tile M2M levels, whose latency is otherwise
+// 8 slots x n_s / 16 dependent steps per block).
 template <typename T, class G, int NTY, int RT, int RC, bool SPLIT>
 __global__ void __launch_bounds__(32 * NTY) k_ggemm(G g, const int32_t *__restrict__ targets, ClassRanges cr,
                                                     int nslots, int ns, int ld, const T *__restrict__ in,
@@ -825,7 +825,7 @@ void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *s
     if (ld == 0) ld = P.ns;
     // 64 x 160 tiles while they fill the GPU twice over; else 16 x 32 tiles
     // (the coarse levels of M2M / L2L and small trees are latency-bound),
-    // with up to 8 slots split over blocks when even those leave SMs idle.
+    // with up to 8 slots split over blocks for up to kSplitTargets targets.
     const int64_t big_blocks = grid_for(total, 64) * grid_for(ld, 160);
     if (big_blocks >= 2 * P.num_sms) {
         dim3 grid(grid_for(most, 64), ncls, grid_for(ld, 160));
@@ -837,7 +837,7 @@ void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *s
     int64_t small_blocks = 0;
     for (int c = 0; c < ncls; ++c) small_blocks += grid_for(starts[c + 1] - starts[c], 16);
     small_blocks *= ncb;
-    if (nslots > 1 && nslots <= 8 && total <= kSplitTargets && small_blocks < P.num_sms) {
+    if (nslots > 1 && nslots <= 8 && total <= kSplitTargets && small_blocks < 16 * P.num_sms) {
         T *part = (T *)P.gemm_part;
         dim3 grid(grid_for(most, 16), ncls, ncb * nslots);
         ++g_launches, k_ggemm<T, G, 4, 4, 1, true><<<grid, 128, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,

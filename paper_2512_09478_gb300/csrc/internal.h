@@ -17,7 +17,7 @@ constexpr int kNumM2L = 316;        // offsets in {-3..3}^3 minus {-1..1}^3
 constexpr int kVSlots = 189;        // V-list slots per octant class (6^3 - 3^3)
 constexpr int kMaxCoarse = 26;      // coarser-or-equal adjacent leaves of a box
 constexpr int kColl = 27;           // colleague slots (3^3, centre = self)
-constexpr int kSplitTargets = 640;  // targets of a gathered GEMM the slot-split form may take (up to 8 slots)
+constexpr int kSplitTargets = 4096; // targets of a gathered GEMM the slot-split form may take (up to 8 slots)
 
 // Leaf-kernel tiles (variants): id -> (targets per lane TPL, source groups
 // G); a pass covers (32 / G) TPL targets.  The table maps a leaf's target
