@@ -243,10 +243,11 @@ kifmm_status kifmm_profile_read(kifmm_plan *plan, kifmm_profile_t *out);
 /* Tile shapes in use (no counterpart in the paper: the benchmark spec asks for
  * M2L/P2P tile shapes chosen by an autotuner).  tuned: bit 0 leaf kernel,
  * bit 1 tensor-core M2L.  m2l_stages: shared-memory pipeline depth of the
- * tensor-core M2L (0 when the plan has none).  Leaf kernel: a leaf with
- * r targets is evaluated by the variant of bucket min((r - 1) / 8, 15):
- * leaf_tpl targets per lane and leaf_groups source groups, in passes of
- * 32 / groups * tpl targets; each variant is its own kernel.
+ * tensor-core M2L (0 when the plan has none).  Leaf kernel: a leaf is
+ * covered by passes; with r of its targets still to cover, bucket
+ * min((r - 1) / 8, 15) selects leaf_tpl targets per lane and leaf_groups
+ * source groups for the next pass, which covers 32 / groups * tpl targets;
+ * each (tpl, groups) variant is its own kernel.
  * Host memory; no device work. */
 typedef struct {
     int tuned;

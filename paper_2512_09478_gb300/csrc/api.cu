@@ -58,15 +58,12 @@ static cudaError_t profile_collect(Plan &P) {
 }
 
 LeafTiling leaf_tiling_candidate(int c) {
-    static const int fam[kLeafTilingCandidates][2] = {{4, 2}, {2, 2}, {4, 1}, {2, 1}, {1, 1}, {1, 2}};
-    const int gs = fam[c][0], gm = fam[c][1];
+    // variants: 0 = (1, 4), 1 = (2, 4), 2 = (1, 2), 3 = (2, 2), 4 = (1, 1), 5 = (2, 1) as (TPL, G)
+    static const int fam[kLeafTilingCandidates][6] = {
+        {0, 1, 4, 4, 4, 4}, {0, 2, 4, 4, 4, 5}, {0, 1, 3, 3, 5, 5},
+        {0, 1, 4, 4, 5, 5}, {4, 4, 4, 4, 4, 4}, {2, 2, 4, 4, 4, 4}};
     LeafTiling t{};
-    for (int i = 0; i < kLeafBuckets; ++i) {
-        const int r = (i == kLeafBuckets - 1) ? 128 : 8 * (i + 1);
-        const int g = (r <= 32) ? gs : (r <= 64 ? gm : 1);
-        const int tpl = std::min(2, std::max(1, (r * g + 31) / 32));
-        t.set(i, (g == 4 ? 0 : g == 2 ? 2 : 4) + tpl - 1);
-    }
+    for (int i = 0; i < kLeafBuckets; ++i) t.set(i, fam[c][i < 4 ? i : (i < 8 ? 4 : 5)]);
     return t;
 }
 
@@ -166,11 +163,12 @@ static cudaError_t ensure_box_arrays(Plan &P) {
         {&P.tmp_chk, esz * P.ns * cap},
         {&P.dn_dens, esz * P.ns * cap},
         {(void **)&P.dbar, sizeof(double) * cap},
-        {(void **)&P.leaf_vlist, sizeof(int32_t) * kLeafTiles * cap},
+        {(void **)&P.leaf_vlist, sizeof(int2) * kLeafTiles * (cap + P.desc.n_max / 8 + 64)},
         {(void **)&P.leaf_vcnt, sizeof(int32_t) * 8},
     };
     for (const A &a : arrs) KIFMM_CUDA_TRY(plan_alloc(P, a.p, a.bytes));
     P.list_cap = cap;
+    P.leaf_item_cap = cap + P.desc.n_max / 8 + 64;
     return cudaSuccess;
 }
 

@@ -661,43 +661,49 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
         }
     }
 }
-// Leaf variants: the tile of a leaf is the plan table's entry for its
-// target count (leaf_variant); one kernel per variant, so each runs with the
-// registers its tile needs.  A leaf is covered in passes of (32 / G) TPL
-// targets.  k_leaf_partition lists the leaves of each variant (order within
-// a list is immaterial: leaves are independent).
+// Leaf work items: a leaf is covered greedily by passes (leaf, first
+// target); the pass over r remaining targets uses the plan table's variant
+// for r (bucket (r - 1) / 8) and covers (32 / G) TPL of them, so e.g. 40
+// targets become a 32-target pass and an 8-target pass with four source
+// groups, keeping every lane busy.  One kernel per variant, each with the
+// registers its tile needs; k_leaf_partition lists the items of each
+// variant (order within a list is immaterial: passes are independent).
 __global__ void k_leaf_partition(int64_t n_leaves, const int32_t *__restrict__ leaves,
                                  const int32_t *__restrict__ cnt, LeafTiling tile, int64_t cap,
-                                 int32_t *__restrict__ lists, int32_t *__restrict__ counts) {
+                                 int2 *__restrict__ lists, int32_t *__restrict__ counts) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool valid = i < n_leaves;
     const int b = valid ? leaves[i] : -1;
-    const int v = valid ? leaf_variant(tile, cnt[b]) : -1;
+    const int n = valid ? cnt[b] : 0;
+    int t0 = 0;
+    while (__any_sync(0xffffffffu, t0 < n)) {
+        const int v = (t0 < n) ? leaf_variant(tile, n - t0) : -1;
 #pragma unroll
-    for (int u = 0; u < kLeafTiles; ++u) {
-        const unsigned m = __ballot_sync(0xffffffffu, v == u);
-        if (m == 0) continue;
-        const int leader = __ffs(m) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&counts[u], __popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (v == u) lists[(int64_t)u * cap + base + __popc(m & ((1u << lane) - 1))] = b;
+        for (int u = 0; u < kLeafTiles; ++u) {
+            const unsigned m = __ballot_sync(0xffffffffu, v == u);
+            if (m == 0) continue;
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&counts[u], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (v == u) lists[(int64_t)u * cap + base + __popc(m & ((1u << lane) - 1))] = make_int2(b, t0);
+        }
+        if (v >= 0) t0 += (32 / leaf_tile_groups(v)) * leaf_tile_tpl(v);
     }
 }
 
 template <typename T, int TPL, int G>
 __global__ void __launch_bounds__(32 * kLW, sizeof(T) == 4 ? (TPL == 1 ? 6 : 5) : 2)
-    k_leaf_all(LeafCtx C, const int32_t *__restrict__ list, const int32_t *__restrict__ count,
+    k_leaf_all(LeafCtx C, const int2 *__restrict__ list, const int32_t *__restrict__ count,
                const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, LeafW<T> W,
                double4 *__restrict__ res) {
     __shared__ LeafSmem<T> bufs[kLW];
     const int warp = threadIdx.x >> 5;
     const int nl = *count;
     for (int li = blockIdx.x * kLW + warp; li < nl; li += gridDim.x * kLW) {
-        const int b = list[li];
-        const int n = C.cnt[b];
-        for (int t0 = 0; t0 < n; t0 += (32 / G) * TPL) leaf_pass<T, TPL, G>(C, b, t0, pts, surf, W, bufs[warp], res);
+        const int2 it = list[li];
+        leaf_pass<T, TPL, G>(C, it.x, it.y, pts, surf, W, bufs[warp], res);
     }
 }
 
@@ -707,18 +713,18 @@ void leaf_launch_variant(const Plan &P, const LeafCtx &C, int v, const typename 
     constexpr int occ = sizeof(T) == 4 ? (TPL == 1 ? 6 : 5) : 2;
     const int64_t want = (P.n_leaves + kLW - 1) / kLW;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P.num_sms * occ));
-    ++g_launches, k_leaf_all<T, TPL, G><<<g, 32 * kLW, 0, s>>>(C, P.leaf_vlist + (int64_t)v * P.list_cap,
+    ++g_launches, k_leaf_all<T, TPL, G><<<g, 32 * kLW, 0, s>>>(C, P.leaf_vlist + (int64_t)v * P.leaf_item_cap,
                                                                 P.leaf_vcnt + v, pts, surf, W, res);
 }
 
-// All leaves: partition by variant, then one launch per variant the table uses.
+// All leaves: work items by variant, then one launch per variant the table uses.
 template <typename T>
 void leaf_launch(const Plan &P, const LeafCtx &C, const typename Vec4<T>::type *pts, const T *surf,
                  const LeafW<T> &W, double4 *res, cudaStream_t s) {
     if (P.n_leaves == 0) return;
     cudaMemsetAsync(P.leaf_vcnt, 0, sizeof(int32_t) * kLeafTiles, s);
     ++g_launches, k_leaf_partition<<<(unsigned)((P.n_leaves + 255) / 256), 256, 0, s>>>(
-                      P.n_leaves, P.leaves, P.cnt, C.tile, P.list_cap, P.leaf_vlist, P.leaf_vcnt);
+                      P.n_leaves, P.leaves, P.cnt, C.tile, P.leaf_item_cap, P.leaf_vlist, P.leaf_vcnt);
     bool used[kLeafTiles] = {false};
     for (int i = 0; i < kLeafBuckets; ++i) used[C.tile.get(i)] = true;
     if (used[0]) leaf_launch_variant<T, 1, 4>(P, C, 0, pts, surf, W, res, s);

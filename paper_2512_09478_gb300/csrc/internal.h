@@ -20,9 +20,9 @@ constexpr int kColl = 27;           // colleague slots (3^3, centre = self)
 constexpr int kSplitTargets = 4096; // targets of a gathered GEMM the slot-split form may take (up to 8 slots)
 
 // Leaf-kernel tiles (variants): id -> (targets per lane TPL, source groups
-// G); a pass covers (32 / G) TPL targets.  The table maps a leaf's target
-// count, in buckets of 8 (the last bucket: more than 120), to the variant
-// that covers the whole leaf in passes.
+// G); a pass covers (32 / G) TPL targets.  The table maps the number of
+// targets still to cover, in buckets of 8 (the last bucket: more than 120),
+// to the variant of the next pass.
 constexpr int kLeafTiles = 6;
 constexpr int kLeafBuckets = 16;
 constexpr int kLeafTilingCandidates = 6;
@@ -37,9 +37,8 @@ struct LeafTiling {
     }
 };
 __host__ __device__ inline int leaf_variant(const LeafTiling &t, int n) { return t.for_targets(n > 0 ? n : 1); }
-// Candidate c of the tuner (c = 0 is the default): up to 32 targets use
-// g_small source groups, up to 64 use g_mid, beyond that one group, each
-// with the fewest targets per lane (at most 2) that cover the bucket.
+// Candidate c of the tuner (c = 0 is the default): the variant for up to 8,
+// 16, 24, 32, 64 and more remaining targets.
 LeafTiling leaf_tiling_candidate(int c);
 
 struct DevBuf {
@@ -136,8 +135,9 @@ struct Plan {
     int64_t m2l_class_start[9] = {0};
     int32_t *leaves = nullptr;       // [nb] leaf indices
     int64_t n_leaves = 0;
-    int32_t *leaf_vlist = nullptr;   // [kLeafTiles][list_cap] leaves of each leaf-kernel variant
-    int32_t *leaf_vcnt = nullptr;    // [8] leaves per variant
+    int2 *leaf_vlist = nullptr;      // [kLeafTiles][leaf_item_cap] (leaf, first target) passes per variant
+    int32_t *leaf_vcnt = nullptr;    // [8] passes per variant
+    int64_t leaf_item_cap = 0;       // bound on passes: every pass but a leaf's last covers >= 8 targets
     int32_t *wsrc_flag = nullptr;    // [nb] 1 if the box is in some W list
     uint32_t *part_counts = nullptr; // [4][256]
     unsigned long long *list_totals = nullptr;  // [4] V and X list sizes
