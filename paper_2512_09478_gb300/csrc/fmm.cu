@@ -38,13 +38,17 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-// P2M: u(b)_j = (1/h) sum_i q_i / |2.95 S_j - (x_i - c_b)/h|
+// P2M: u(b)_j = (1/h) sum_i q_i / |2.95 S_j - (x_i - c_b)/h|.  One block
+// per leaf with a thread per check point (blockDim = n_s rounded up to a
+// warp); particles staged through shared memory in chunks of blockDim.  The
+// check surface lies outside the leaf, so no distance is zero.
 template <typename T>
 __global__ void k_p2m(const int32_t *__restrict__ leaves, const int32_t *__restrict__ lvl,
                       const int32_t *__restrict__ first, const int32_t *__restrict__ cnt,
                       const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, int ns,
                       T *__restrict__ u, const T *__restrict__ wts = nullptr, int adj = 0) {
-    __shared__ T sx[kLeafThreads], sy[kLeafThreads], sz[kLeafThreads], sq[kLeafThreads];
+    extern __shared__ __align__(16) unsigned char p2m_sm[];
+    T *sx = (T *)p2m_sm, *sy = sx + blockDim.x, *sz = sy + blockDim.x, *sq = sz + blockDim.x;
     const int b = leaves[blockIdx.x];
     const T h = box_half<T>(lvl[b]), hinv = T(1) / h;
     const int n = cnt[b], f = first[b];
@@ -58,7 +62,7 @@ __global__ void k_p2m(const int32_t *__restrict__ leaves, const int32_t *__restr
             pz = a * surf[3 * j + 2];
         }
         T acc = 0;
-        for (int c0 = 0; c0 < n; c0 += kLeafThreads) {
+        for (int c0 = 0; c0 < n; c0 += blockDim.x) {
             __syncthreads();
             if (c0 + threadIdx.x < n) {
                 const auto v = pts[f + c0 + threadIdx.x];
@@ -68,8 +72,12 @@ __global__ void k_p2m(const int32_t *__restrict__ leaves, const int32_t *__restr
                 sq[threadIdx.x] = wts ? wts[f + c0 + threadIdx.x] : v.w;
             }
             __syncthreads();
-            const int m = min(kLeafThreads, n - c0);
-            for (int i = 0; i < m; ++i) acc += sq[i] * lap_pot<T>(px - sx[i], py - sy[i], pz - sz[i]);
+            const int m = min((int)blockDim.x, n - c0);
+#pragma unroll 4
+            for (int i = 0; i < m; ++i) {
+                const T rx = px - sx[i], ry = py - sy[i], rz = pz - sz[i];
+                acc += sq[i] * rsqrt_t<T>(rx * rx + ry * ry + rz * rz);
+            }
         }
         // forward: u = sum q / |UC - x| (1/h from the unit surface); adjoint of
         // L2P: h * sum w / |DE - x| with the same unit geometry
@@ -816,6 +824,11 @@ __global__ void k_clump(int64_t nc, const int64_t *__restrict__ off, const TO *_
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// k_p2m launch shape: a thread per check point, four staged values per thread.
+inline int p2m_threads(const Plan &P) { return (P.ns + 31) / 32 * 32; }
+template <typename T>
+inline size_t p2m_smem(const Plan &P) { return 4 * sizeof(T) * (size_t)p2m_threads(P); }
+
 // Classes c < ncls own targets [starts[c], starts[c + 1]); one launch.
 template <typename T, class G>
 void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *starts, int ncls, int nslots,
@@ -875,7 +888,7 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     double4 *res = (double4 *)P.res;
     // upward pass
     stage_begin(P, KIFMM_STAGE_P2M, s);
-    ++g_launches, k_p2m<T><<<(unsigned)P.n_leaves, kLeafThreads, 0, s>>>(P.leaves, P.lvl, P.first, P.cnt, pts,
+    ++g_launches, k_p2m<T><<<(unsigned)P.n_leaves, p2m_threads(P), p2m_smem<T>(P), s>>>(P.leaves, P.lvl, P.first, P.cnt, pts,
                                                                         surf, ns, u);
     stage_end(P, KIFMM_STAGE_P2M, s);
     stage_begin(P, KIFMM_STAGE_M2M, s);
@@ -1024,7 +1037,7 @@ cudaError_t backward_t(Plan &P, const void *w_user, const void *grad_user, void 
     // L2P^T: h * sum w / |DE - x| at each leaf, then d-bar = W_dn^T V_dn^T (.)
     KIFMM_CUDA_TRY(cudaMemsetAsync(db, 0, sizeof(T) * (size_t)P.nb * ns, s));
     KIFMM_CUDA_TRY(cudaMemsetAsync(ub, 0, sizeof(T) * (size_t)P.nb * ns, s));
-    ++g_launches, k_p2m<T><<<(unsigned)P.n_leaves, kLeafThreads, 0, s>>>(P.leaves, P.lvl, P.first, P.cnt, pts, surf,
+    ++g_launches, k_p2m<T><<<(unsigned)P.n_leaves, p2m_threads(P), p2m_smem<T>(P), s>>>(P.leaves, P.lvl, P.first, P.cnt, pts, surf,
                                                                         ns, e1, ws, 1);
     ggemm<T>(P, GatherSelf<T>{adjp + 3 * nn}, P.leaves, 0, P.n_leaves, 1, e1, tmp, 0, s);
     ggemm<T>(P, GatherSelf<T>{adjp + 2 * nn}, P.leaves, 0, P.n_leaves, 1, tmp, db, 0, s);

@@ -171,15 +171,61 @@ __global__ void k_rs_hist(int64_t n, const uint64_t *__restrict__ keys, const ui
     for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * nblk + blockIdx.x] = h[d];
 }
 
+// Per digit (one block each): exclusive scan over the tiles' counts of that
+// digit, in place ([digit][tile] layout), and the digit's total.
+__global__ void __launch_bounds__(256) k_rs_dscan(uint32_t *hist, int nblk, uint32_t *dtot) {
+    __shared__ uint32_t ws[8];
+    uint32_t *h = hist + (int64_t)blockIdx.x * nblk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (int c0 = 0; c0 < nblk; c0 += 256) {
+        const int i = c0 + threadIdx.x;
+        const uint32_t v = (i < nblk) ? h[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[warp] = x;
+        __syncthreads();
+        uint32_t wb = 0, tot = 0;
+        for (int w = 0; w < 8; ++w) {
+            wb += (w < warp) ? ws[w] : 0u;
+            tot += ws[w];
+        }
+        if (i < nblk) h[i] = carry + wb + x - v;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
+}
+
 // Scatter with ranks stable in input order: rounds of 256 consecutive items,
-// warp-level peer ranking, per-warp digit counts scanned across warps.
+// warp-level peer ranking, per-warp digit counts scanned across warps.  The
+// digit bases are the exclusive scan of the digit totals plus this tile's
+// offset within each digit.
 __global__ void k_rs_scatter(int64_t n, const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                              uint64_t *kout, uint32_t *vout, int mode, int shift, const int64_t *off, int S,
-                             const uint32_t *__restrict__ hist_scan, int nblk) {
+                             const uint32_t *__restrict__ hist_scan, const uint32_t *__restrict__ dtot, int nblk) {
+    static_assert(kBlock == 256, "one thread per digit");
     __shared__ uint32_t base_d[256];
     __shared__ uint32_t wcnt[kBlock / 32][256];
+    __shared__ uint32_t ws8[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < 256; d += kBlock) base_d[d] = hist_scan[(int64_t)d * nblk + blockIdx.x];
+    {
+        const int d = threadIdx.x;
+        const uint32_t v = dtot[d];
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws8[warp] = x;
+        __syncthreads();
+        uint32_t wb = 0;
+        for (int w = 0; w < warp; ++w) wb += ws8[w];
+        base_d[d] = wb + x - v + hist_scan[(int64_t)d * nblk + blockIdx.x];
+    }
     const int64_t tile0 = (int64_t)blockIdx.x * kTile;
     for (int r = 0; r < kItems; ++r) {
         for (int i = threadIdx.x; i < (kBlock / 32) * 256; i += kBlock) (&wcnt[0][0])[i] = 0;
@@ -757,10 +803,10 @@ static cudaError_t radix_pass(Plan &P, const uint64_t *kin, const uint32_t *vin,
         KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.scan_tmp, sizeof(uint32_t) * P.scan_tmp_elems));
     }
     ++g_launches, k_rs_hist<<<nblk, kBlock, 0, s>>>(n, kin, vin, mode, shift, P.sys_off_d, P.n_sys, P.hist, nblk);
-    KIFMM_CUDA_TRY(exclusive_scan_u32(P.hist, P.hist + (size_t)256 * nblk, (int64_t)256 * nblk, nullptr,
-                                      P.scan_tmp, P.scan_tmp_elems - 1, s));
+    uint32_t *dtot = P.hist + (size_t)256 * nblk;
+    ++g_launches, k_rs_dscan<<<256, 256, 0, s>>>(P.hist, nblk, dtot);
     ++g_launches, k_rs_scatter<<<nblk, kBlock, 0, s>>>(n, kin, vin, kout, vout, mode, shift, P.sys_off_d, P.n_sys,
-                                         P.hist + (size_t)256 * nblk, nblk);
+                                                       P.hist, dtot, nblk);
     return cudaGetLastError();
 }
 
