@@ -59,9 +59,7 @@ WORKLOADS["c2"]["compare"] = "fp32"
 # captured (sha256); otherwise the roofline's traffic is null.
 TRAFFIC = {
     ("dem-coulomb-rsa-1M", "m2l"): ("paper_2512_09478_gb300/csrc/m2l_tc.cu",
-                                    "d99250b3ce6a2051498f5002f0010cf8ea40c5e97d251ff79622c3de24ffc63e", 118.86e6),
-    ("dem-coulomb-rsa-1M", "p2p"): ("paper_2512_09478_gb300/csrc/fmm.cu",
-                                    "a156cf11cb8d7a44382c28c272dd49ae92a791b4b60a0ff8c277c15d4a165e7d", 42.03e6),
+                                    "df1cc98e7e8f86dc26583416384f2c2aceda1b6f866c8c7dd78bb749f569dfdc", 117.33e6),
 }
 
 
