@@ -222,8 +222,11 @@ struct GatherSelf {
 // k_ggemm_sum adds the slots in order (the same arithmetic as the unsplit
 // form; used for the small-tile M2M levels, whose latency is otherwise
 // 8 slots x n_s / 16 dependent steps per block).
-template <typename T, class G, int NTY, int RT, int RC, bool SPLIT>
-__global__ void __launch_bounds__(32 * NTY) k_ggemm(G g, const int32_t *__restrict__ targets, ClassRanges cr,
+// MULTI: more than one slot per block (FP32 then keeps per-slot partials and
+// running sums); single-slot launches need half the accumulator registers
+// and run two 256-thread blocks per SM.
+template <typename T, class G, int NTY, int RT, int RC, bool SPLIT, bool MULTI>
+__global__ void __launch_bounds__(32 * NTY, (sizeof(T) == 4 && NTY == 8 && !MULTI) ? 2 : 1) k_ggemm(G g, const int32_t *__restrict__ targets, ClassRanges cr,
                                                     int nslots, int ns, int ld, const T *__restrict__ in,
                                                     T *__restrict__ out, int accumulate, double *dbar, int ncb,
                                                     T *__restrict__ part) {
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(32 * NTY) k_ggemm(G g, const int32_t *__restri
     if (threadIdx.x < TT) tgt[threadIdx.x] = (t0 + threadIdx.x < t_end) ? targets[t0 + threadIdx.x] : -1;
     // FP32: each slot sums into a fresh partial that is then added to the
     // running total, so no rounding chain is longer than one slot's n_s terms.
-    constexpr bool kTwoLevel = sizeof(T) == 4;
+    constexpr bool kTwoLevel = sizeof(T) == 4 && MULTI;
     T acc[RT][RC], run[RT][RC];
 #pragma unroll
     for (int a = 0; a < RT; ++a)
@@ -848,8 +851,12 @@ void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *s
     const int64_t big_blocks = grid_for(total, 64) * grid_for(ld, 160);
     if (big_blocks >= 2 * P.num_sms) {
         dim3 grid(grid_for(most, 64), ncls, grid_for(ld, 160));
-        ++g_launches, k_ggemm<T, G, 8, 8, 5, false><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,
-                                                                          accumulate, dbar, 1, nullptr);
+        if (nslots > 1)
+            ++g_launches, k_ggemm<T, G, 8, 8, 5, false, true><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld,
+                                                                                  in, out, accumulate, dbar, 1, nullptr);
+        else
+            ++g_launches, k_ggemm<T, G, 8, 8, 5, false, false><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld,
+                                                                                   in, out, accumulate, dbar, 1, nullptr);
         return;
     }
     const int ncb = (int)grid_for(ld, 32);
@@ -859,15 +866,15 @@ void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *s
     if (nslots > 1 && nslots <= 8 && total <= kSplitTargets && small_blocks < 16 * P.num_sms) {
         T *part = (T *)P.gemm_part;
         dim3 grid(grid_for(most, 16), ncls, ncb * nslots);
-        ++g_launches, k_ggemm<T, G, 4, 4, 1, true><<<grid, 128, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,
-                                                                         accumulate, dbar, ncb, part);
+        ++g_launches, k_ggemm<T, G, 4, 4, 1, true, false><<<grid, 128, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in,
+                                                                                out, accumulate, dbar, ncb, part);
         ++g_launches, k_ggemm_sum<T, G><<<grid_for(total * ld, 256), 256, 0, s>>>(
                           g, targets, cr.b[0], total, nslots, P.ns, ld, part, out, accumulate, dbar);
         return;
     }
     dim3 grid(grid_for(most, 16), ncls, ncb);
-    ++g_launches, k_ggemm<T, G, 4, 4, 1, false><<<grid, 128, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in, out,
-                                                                      accumulate, dbar, ncb, nullptr);
+    ++g_launches, k_ggemm<T, G, 4, 4, 1, false, true><<<grid, 128, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in,
+                                                                            out, accumulate, dbar, ncb, nullptr);
 }
 
 template <typename T, class G>
