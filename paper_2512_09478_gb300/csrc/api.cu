@@ -274,6 +274,11 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     };
     for (const A &a : arrs)
         if (plan_alloc(P, a.p, a.bytes) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    if (cudaEventCreateWithFlags(&P.leaf_fork, cudaEventDisableTiming) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    for (int v = 0; v < kLeafTiles; ++v)
+        if (cudaStreamCreateWithFlags(&P.leaf_streams[v], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P.leaf_join[v], cudaEventDisableTiming) != cudaSuccess)
+            return fail(KIFMM_ERR_CUDA);
     const int64_t box0 = 12 * (n / (d.leaf_cap + 1)) + 64LL * P.sys_cap + 1024;
     if (grow_tree_arrays(P, box0, 0) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
     P.scan_tmp_elems = std::max(P.scan_tmp_elems, scan_tmp_needed((int64_t)256 * nblk) + 8);
@@ -292,6 +297,11 @@ kifmm_status kifmm_plan_destroy(kifmm_plan *pl) {
     for (auto &b : pl->P.owned) cudaFree(b.ptr);
     pl->P.owned.clear();
     for (cudaEvent_t e : pl->P.ev_pool) cudaEventDestroy(e);
+    if (pl->P.leaf_fork) cudaEventDestroy(pl->P.leaf_fork);
+    for (int v = 0; v < kLeafTiles; ++v) {
+        if (pl->P.leaf_join[v]) cudaEventDestroy(pl->P.leaf_join[v]);
+        if (pl->P.leaf_streams[v]) cudaStreamDestroy(pl->P.leaf_streams[v]);
+    }
     delete pl;
     return KIFMM_OK;
 }

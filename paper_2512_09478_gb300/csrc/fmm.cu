@@ -720,15 +720,22 @@ __global__ void __launch_bounds__(32 * kLW, sizeof(T) == 4 ? (TPL == 1 ? 6 : 5) 
 
 template <typename T, int TPL, int G>
 void leaf_launch_variant(const Plan &P, const LeafCtx &C, int v, const typename Vec4<T>::type *pts, const T *surf,
-                         const LeafW<T> &W, double4 *res, cudaStream_t s) {
+                         const LeafW<T> &W, double4 *res, cudaStream_t caller) {
+    // on the variant's own stream, after the partition; joined back below
+    cudaStream_t s = P.leaf_streams[v];
+    cudaStreamWaitEvent(s, P.leaf_fork, 0);
     constexpr int occ = sizeof(T) == 4 ? (TPL == 1 ? 6 : 5) : 2;
     const int64_t want = (P.n_leaves + kLW - 1) / kLW;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P.num_sms * occ));
     ++g_launches, k_leaf_all<T, TPL, G><<<g, 32 * kLW, 0, s>>>(C, P.leaf_vlist + (int64_t)v * P.leaf_item_cap,
                                                                 P.leaf_vcnt + v, pts, surf, W, res);
+    cudaEventRecord(P.leaf_join[v], s);
+    cudaStreamWaitEvent(caller, P.leaf_join[v], 0);
 }
 
-// All leaves: work items by variant, then one launch per variant the table uses.
+// All leaves: work items by variant, then one launch per variant the table
+// uses, each on its own stream so that the short variants' tails (a pass of
+// one warp over a leaf's whole source list) overlap the long one.
 template <typename T>
 void leaf_launch(const Plan &P, const LeafCtx &C, const typename Vec4<T>::type *pts, const T *surf,
                  const LeafW<T> &W, double4 *res, cudaStream_t s) {
@@ -736,6 +743,7 @@ void leaf_launch(const Plan &P, const LeafCtx &C, const typename Vec4<T>::type *
     cudaMemsetAsync(P.leaf_vcnt, 0, sizeof(int32_t) * kLeafTiles, s);
     ++g_launches, k_leaf_partition<<<(unsigned)((P.n_leaves + 255) / 256), 256, 0, s>>>(
                       P.n_leaves, P.leaves, P.cnt, C.tile, P.leaf_item_cap, P.leaf_vlist, P.leaf_vcnt);
+    cudaEventRecord(P.leaf_fork, s);
     bool used[kLeafTiles] = {false};
     for (int i = 0; i < kLeafBuckets; ++i) used[C.tile.get(i)] = true;
     if (used[0]) leaf_launch_variant<T, 1, 4>(P, C, 0, pts, surf, W, res, s);

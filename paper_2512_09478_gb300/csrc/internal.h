@@ -138,6 +138,10 @@ struct Plan {
     int2 *leaf_vlist = nullptr;      // [kLeafTiles][leaf_item_cap] (leaf, first target) passes per variant
     int32_t *leaf_vcnt = nullptr;    // [8] passes per variant
     int64_t leaf_item_cap = 0;       // bound on passes: every pass but a leaf's last covers >= 8 targets
+    // the leaf-kernel variants run concurrently: forked from the caller's
+    // stream onto these and joined back (event-ordered, so capturable)
+    cudaStream_t leaf_streams[kLeafTiles] = {};
+    cudaEvent_t leaf_fork = nullptr, leaf_join[kLeafTiles] = {};
     int32_t *wsrc_flag = nullptr;    // [nb] 1 if the box is in some W list
     uint32_t *part_counts = nullptr; // [4][256]
     unsigned long long *list_totals = nullptr;  // [4] V and X list sizes
