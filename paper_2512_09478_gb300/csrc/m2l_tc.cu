@@ -13,17 +13,19 @@
 // for all operators); the product keeps hi*hi + hi*lo + lo*hi (the lo*lo term
 // is below 2^-22 of the product) and the epilogue divides by sigma_A sigma_B.
 //
-// Pipeline (per CTA, 160 threads):
-//   warps 0-3  producers: cp.async (16 B, four threads per 64-byte row) of the
+// Pipeline (per CTA, 352 threads):
+//   warps 0-1  producers: cp.async (16 B, four threads per 64-byte row) of the
 //              gathered A rows into a ring of shared-memory stages laid out in
 //              the 64-byte swizzled K-major form; the slot's B block is stored
 //              in global memory already in that form and arrives by one bulk
 //              (TMA) copy per operand half.  Completion is tracked by the
-//              stage's "full" mbarrier (cp.async.mbarrier.arrive.noinc plus the
-//              bulk copies' byte count).
-//   warp 4     allocates TMEM; one thread issues tcgen05.mma for each stage
+//              stage's "full" mbarrier (cp.async.mbarrier.arrive.noinc of the
+//              64 producer threads plus the bulk copies' byte count; fewer
+//              producer threads mean fewer arrivals per stage).
+//   warp 2     allocates TMEM; one thread issues tcgen05.mma for each stage
 //              and frees the stage with tcgen05.commit on its "empty" barrier.
-//   warps 0-3  epilogue: tcgen05.ld of their 32 TMEM lanes, unscale, store.
+//   warps 3-10 drain: each V slot's partial accumulator is added in IEEE FP32
+//              to running sums held in registers, then unscaled and stored.
 // Every wait is bounded; on time-out the CTA records KIFMM_ERR_TIMEOUT, drains
 // its own copies and MMAs (bounded), frees TMEM and returns.
 #include <cuda_fp16.h>
@@ -41,8 +43,11 @@ namespace kifmm {
 namespace {
 
 constexpr int kDrainWarps = 8;
-constexpr int kTcThreads = 32 * (5 + kDrainWarps);  // 4 producer warps, 1 MMA warp, 8 drain warps
 constexpr int kAccBufs = 3;         // per-slot partial accumulators in TMEM
+constexpr int kProdWarps = 2;       // warps gathering the A rows (each stage waits for their cp.async arrivals)
+constexpr int kRowsPerThread = kTcRows / (8 * kProdWarps);
+constexpr int kMmaWarp = kProdWarps;  // then the MMA warp, then the drain warps
+constexpr int kTcThreads = 32 * (kProdWarps + 1 + kDrainWarps);
 constexpr int kKBlock = 32;         // FP16 elements per stage row (64 bytes)
 constexpr int kRowBytes = 64;
 
@@ -94,7 +99,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
         abort_s = 0;
         abort_zero = 0;
         for (int s = 0; s < NS; ++s) {
-            mbar_init(smem_u32(&full_bar[s]), kTcRows + 1);  // 128 cp.async arrivals + the bulk-copy leader
+            mbar_init(smem_u32(&full_bar[s]), 32 * kProdWarps + 1);  // producer cp.async arrivals + the bulk-copy leader
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
         mbar_init(smem_u32(&done_bar), 1);
@@ -107,7 +112,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
     // TMEM columns: kAccBufs partial accumulators of NT columns each.
     constexpr uint32_t tmem_cols = (kAccBufs * NT <= 128) ? 128 : (kAccBufs * NT <= 256) ? 256 : 512;
     static_assert(kAccBufs * NT <= 512, "partial accumulators exceed TMEM");
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
                      "r"(tmem_cols)
                      : "memory");
@@ -120,15 +125,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
     const int kblocks = kp / kKBlock;
     const int iters = kVSlots * kblocks;
 
-    if (warp < 4) {
+    if (warp < kProdWarps) {
         // ---------------- producers ----------------
-        // Thread t copies 16-byte chunk (t & 3) of rows (t >> 2) + 32 i, so
-        // each warp instruction reads eight whole 64-byte rows.
+        // Thread t copies 16-byte chunk (t & 3) of rows (t >> 2) + 8 P i
+        // (P producer warps), so each warp instruction reads eight whole
+        // 64-byte rows; few producer threads keep the stage barrier's
+        // arrival count low.
         const int ch = threadIdx.x & 3, r0 = threadIdx.x >> 2;
-        int32_t tg[4], src[4], src_next[4];
+        int32_t tg[kRowsPerThread], src[kRowsPerThread], src_next[kRowsPerThread];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            tg[i] = tgt_s[r0 + 32 * i];
+        for (int i = 0; i < kRowsPerThread; ++i) {
+            tg[i] = tgt_s[r0 + 8 * kProdWarps * i];
             src[i] = -1;
             src_next[i] = (tg[i] >= 0) ? a.vdense[(size_t)tg[i] * kVSlots] : -1;
         }
@@ -139,7 +146,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             const int s = it / kblocks, kb = it - s * kblocks;
             if (kb == 0) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < kRowsPerThread; ++i) {
                     src[i] = src_next[i];
                     if (s + 1 < kVSlots) src_next[i] = (tg[i] >= 0) ? a.vdense[(size_t)tg[i] * kVSlots + s + 1] : -1;
                 }
@@ -165,8 +172,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             }
             const size_t koff = (size_t)kb * kKBlock + 8 * ch;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = r0 + 32 * i;
+            for (int i = 0; i < kRowsPerThread; ++i) {
+                const int r = r0 + 8 * kProdWarps * i;
                 const size_t g = (size_t)(src[i] >= 0 ? src[i] : 0) * kp + koff;
                 const uint32_t nbytes = (src[i] >= 0) ? 16u : 0u;
                 cp_async16(sA + swz64(r, ch), a.uh + g, nbytes);
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             // producers stopped before arriving on that stage
             (void)mbar_wait(smem_u32(&full_bar[last_it % NS]), (last_it / NS) & 1, &abort_zero);
         }
-    } else if (warp == 4) {
+    } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------
         // Slot s accumulates into partial buffer s % kAccBufs (fresh
         // accumulator: the tensor core's FP32 accumulation rounds toward
@@ -228,12 +235,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
             mma_commit(smem_u32(&done_bar));
         }
         __syncwarp();
-    } else {
-        // ---------------- drain warps (5..12) ----------------
+    } else if (warp > kMmaWarp) {
+        // ---------------- drain warps ----------------
         // Warp w may read TMEM lanes 32 (w % 4) .. +31; two warps share each
         // lane quadrant and split the NT columns in halves.  The running sums
         // stay in registers (IEEE FP32 adds of the per-slot partials).
-        const int q = warp & 3, h = (warp - 5) >> 2;
+        const int q = warp & 3, h = (warp - kMmaWarp - 1) >> 2;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const int c_base = h * (NT / 2);
         float acc[NT / 2];
@@ -277,7 +284,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         if (abort_s) {
             // bounded drain of in-flight MMAs (the done barrier completes when they do)
             for (long long i = 0; i < kWaitIters; ++i)
