@@ -867,11 +867,23 @@ void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *s
                                                                                    in, out, accumulate, dbar, 1, nullptr);
         return;
     }
+    const bool splittable = nslots > 1 && nslots <= 8 && total <= kSplitTargets;
+    if (splittable && big_blocks * nslots >= 2 * P.num_sms) {
+        // big tiles, one slot per block (single-slot registers: two blocks per SM)
+        T *part = (T *)P.gemm_part;
+        const int ncb_big = (int)grid_for(ld, 160);
+        dim3 grid(grid_for(most, 64), ncls, ncb_big * nslots);
+        ++g_launches, k_ggemm<T, G, 8, 8, 5, true, false><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in,
+                                                                                out, accumulate, dbar, ncb_big, part);
+        ++g_launches, k_ggemm_sum<T, G><<<grid_for(total * ld, 256), 256, 0, s>>>(
+                          g, targets, cr.b[0], total, nslots, P.ns, ld, part, out, accumulate, dbar);
+        return;
+    }
     const int ncb = (int)grid_for(ld, 32);
     int64_t small_blocks = 0;
     for (int c = 0; c < ncls; ++c) small_blocks += grid_for(starts[c + 1] - starts[c], 16);
     small_blocks *= ncb;
-    if (nslots > 1 && nslots <= 8 && total <= kSplitTargets && small_blocks < 16 * P.num_sms) {
+    if (splittable && small_blocks < 16 * P.num_sms) {
         T *part = (T *)P.gemm_part;
         dim3 grid(grid_for(most, 16), ncls, ncb * nslots);
         ++g_launches, k_ggemm<T, G, 4, 4, 1, true, false><<<grid, 128, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in,
