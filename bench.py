@@ -59,7 +59,10 @@ WORKLOADS["c2"]["compare"] = "fp32"
 # captured (sha256); otherwise the roofline's traffic is null.
 TRAFFIC = {
     ("dem-coulomb-rsa-1M", "m2l"): ("paper_2512_09478_gb300/csrc/m2l_tc.cu",
-                                    "df1cc98e7e8f86dc26583416384f2c2aceda1b6f866c8c7dd78bb749f569dfdc", 117.33e6),
+                                    "17c0fcead92f151c6905234c76a369604c820bbb95aacdf8d76d0f7897befc2a", 120.58e6),
+    # the leaf stage: all tile variants of one evaluate together
+    ("dem-coulomb-rsa-1M", "p2p"): ("paper_2512_09478_gb300/csrc/fmm.cu",
+                                    "695c004fb6af7e3b702b10f6ddf5c356bc142fc16d559b48d398982c47c8e244", 67.81e6),
 }
 
 
