@@ -61,7 +61,8 @@ LeafTiling leaf_tiling_candidate(int c) {
     // variants: 0 = (1, 4), 1 = (2, 4), 2 = (1, 2), 3 = (2, 2), 4 = (1, 1), 5 = (2, 1) as (TPL, G)
     static const int fam[kLeafTilingCandidates][6] = {
         {0, 1, 4, 4, 4, 4}, {0, 2, 4, 4, 4, 5}, {0, 1, 3, 3, 5, 5},
-        {0, 1, 4, 4, 5, 5}, {4, 4, 4, 4, 4, 4}, {2, 2, 4, 4, 4, 4}};
+        {0, 1, 4, 4, 5, 5}, {4, 4, 4, 4, 4, 4}, {2, 2, 4, 4, 4, 4},
+        {0, 2, 2, 4, 4, 4}, {0, 1, 2, 4, 4, 4}};
     LeafTiling t{};
     for (int i = 0; i < kLeafBuckets; ++i) t.set(i, fam[c][i < 4 ? i : (i < 8 ? 4 : 5)]);
     return t;

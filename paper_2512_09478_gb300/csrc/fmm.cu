@@ -525,15 +525,20 @@ __device__ __forceinline__ void leaf_fetch(const LeafSmem<T> &S, int c, int tota
                                            const T *__restrict__ surf, const LeafW<T> &W,
                                            typename Vec4<T>::type (&raw)[kLK], int (&rs)[kLK]) {
     const int lane = threadIdx.x & 31;
+    // the lane's entries increase with i: one binary search, then linear steps
+    int s = 0;
 #pragma unroll
     for (int i = 0; i < kLK; ++i) {
         const int j = c * kLChunk + lane + 32 * i;
         rs[i] = -1;
         if (j < total) {
-            int s = 0;
+            if (i == 0) {
 #pragma unroll
-            for (int step = kLSeg / 2; step > 0; step >>= 1)
-                if (s + step < nb && S.start[s + step] <= j) s += step;
+                for (int step = kLSeg / 2; step > 0; step >>= 1)
+                    if (s + step < nb && S.start[s + step] <= j) s += step;
+            } else {
+                while (s + 1 < nb && S.start[s + 1] <= j) ++s;
+            }
             const int k = j - S.start[s];
             const int kind = S.seg[s].kind, base = S.seg[s].base;
             rs[i] = s;

@@ -25,7 +25,7 @@ constexpr int kSplitTargets = 4096; // targets of a gathered GEMM the slot-split
 // to the variant of the next pass.
 constexpr int kLeafTiles = 6;
 constexpr int kLeafBuckets = 16;
-constexpr int kLeafTilingCandidates = 6;
+constexpr int kLeafTilingCandidates = 8;
 __host__ __device__ constexpr int leaf_tile_tpl(int id) { return id % 2 + 1; }
 __host__ __device__ constexpr int leaf_tile_groups(int id) { return id < 2 ? 4 : (id < 4 ? 2 : 1); }
 struct LeafTiling {
