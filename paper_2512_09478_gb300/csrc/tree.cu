@@ -16,7 +16,7 @@ namespace kifmm {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kItems = 16;
+constexpr int kItems = 4;
 constexpr int kTile = kBlock * kItems;  // radix-sort tile
 
 __device__ __forceinline__ unsigned long long ord_of(double v) {
