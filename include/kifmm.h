@@ -139,6 +139,29 @@ kifmm_status kifmm_set_sources(kifmm_plan *plan, int n_systems, const int64_t *s
 kifmm_status kifmm_update_sources(kifmm_plan *plan, const void *xyz, const void *q, kifmm_stream_t stream);
 
 /*
+ * Refresh with a validity test: keep the tree when it still fits, rebuild it
+ * when it does not (the tree reuse between long-range evaluations of Sec. 2.4
+ * and Eq. 2, with a Verlet-style skin).  The test runs on the device: every
+ * particle, taken in the last set_sources' root cube, must lie inside its leaf
+ * grown on every side by skin times the half-width of the finest leaf level
+ * in the plan.  That bound keeps each particle inside the 1.05 h surfaces of
+ * its own leaf for skin <= 0.05 and keeps the separation of every V, W and X
+ * pair, so a reused tree has the accuracy of a fresh one (the default 0.05).
+ * If the test passes, this is kifmm_update_sources; otherwise it is
+ * kifmm_set_sources with the same systems (a new root cube and tree).
+ * xyz (device, [N,3]) and q (device, [N]): the same particles in the same
+ *   order as the last set_sources, in the plan's dtype.
+ * skin: in [0, 1]; 0 requires every particle inside its own leaf.
+ * reused (host, may be NULL): set to 1 if the tree was kept, else 0.
+ * Synchronises the stream once (the decision is taken on the host), so it is
+ * not capturable in a CUDA graph.  A non-finite coordinate fails the test and
+ * the rebuild returns KIFMM_ERR_NONFINITE.  Returns KIFMM_ERR_STATE before
+ * the first set_sources and KIFMM_ERR_ARG for a skin outside [0, 1].
+ */
+kifmm_status kifmm_refresh_sources(kifmm_plan *plan, const void *xyz, const void *q, double skin, int *reused,
+                                   kifmm_stream_t stream);
+
+/*
  * Evaluate the long-range field on every particle (Sec. 2.2 passes; Sec. 2.4
  * per-step evaluation): P2M, M2M, M2L (V list), P2L (X list), L2L, L2P,
  * M2P (W list), P2P (U list).

@@ -269,6 +269,7 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {(void **)&P.bbox_ord, sizeof(unsigned long long) * 6 * P.sys_cap},
         {(void **)&P.hist, sizeof(uint32_t) * P.hist_elems},
         {(void **)&P.status, sizeof(int)},
+        {(void **)&P.moved, sizeof(int)},
         {(void **)&P.part_counts, sizeof(uint32_t) * 4 * 256},
         {(void **)&P.list_totals, sizeof(unsigned long long) * 4},
         {(void **)&P.energy_chunk_start, sizeof(int32_t) * (P.sys_cap + 1)},
@@ -427,6 +428,35 @@ kifmm_status kifmm_update_sources(kifmm_plan *pl, const void *xyz, const void *q
     stage_end(P, KIFMM_STAGE_TREE, s);
     P.launches += g_launches - l0;
     return from_cuda(e);
+}
+
+kifmm_status kifmm_refresh_sources(kifmm_plan *pl, const void *xyz, const void *q, double skin, int *reused,
+                                   kifmm_stream_t stream) {
+    if (!pl || !xyz || !q || !(skin >= 0.0 && skin <= 1.0)) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!P.has_sources) return KIFMM_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    P.last_stream = s;
+    const long long l0 = g_launches;
+    stage_begin(P, KIFMM_STAGE_TREE, s);
+    int moved = 1;
+    kifmm_status rc = KIFMM_OK;
+    cudaError_t e = check_leaves(P, xyz, skin, P.moved, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&moved, P.moved, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        rc = from_cuda(e);
+    } else if (!moved) {
+        rc = from_cuda(gather_particles(P, xyz, q, s));
+    } else {
+        // same systems, new tree: the full set_sources pass
+        P.has_sources = false;
+        rc = set_sources_impl(P, xyz, q, s);
+    }
+    stage_end(P, KIFMM_STAGE_TREE, s);
+    P.launches += g_launches - l0;
+    if (reused) *reused = (rc == KIFMM_OK && !moved) ? 1 : 0;
+    return rc;
 }
 
 kifmm_status kifmm_get_device_status(kifmm_plan *pl, int *code) {

@@ -182,6 +182,7 @@ struct Plan {
 
     // ---- status ----
     int *status = nullptr;   // device status word
+    int *moved = nullptr;    // device flag of the tree reuse test
     cudaStream_t last_stream = nullptr;
     bool has_sources = false;
 
@@ -212,6 +213,9 @@ size_t scan_tmp_needed(int64_t n);
 cudaError_t build_operators(Plan &P, std::string &err);
 
 // ---- m2l_tc.cu (mixed modes) ----
+// tree.cu: *moved_dev = 1 if some particle lies outside its leaf by more than
+// skin half-widths of the finest level (refresh_sources' reuse test); enqueues only.
+cudaError_t check_leaves(Plan &P, const void *xyz, double skin, int *moved_dev, cudaStream_t s);
 cudaError_t m2l_tensor_setup(Plan &P);
 cudaError_t m2l_tensor_tiles(Plan &P, cudaStream_t s);
 cudaError_t m2l_tensor(Plan &P, cudaStream_t s);

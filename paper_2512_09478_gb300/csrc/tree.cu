@@ -433,6 +433,37 @@ __global__ void k_gather(int64_t n_leaves, const int32_t *__restrict__ leaves, c
     }
 }
 
+// Tree reuse test: one warp per leaf; every particle's leaf-relative offset
+// (the FP64 formula of k_gather, in units of the root side) must lie within
+// the leaf's half-width plus `margin` of its centre on every axis; otherwise
+// (or for a non-finite coordinate) *moved is set.
+template <typename TI>
+__global__ void k_leaf_check(int64_t n_leaves, const int32_t *__restrict__ leaves, const int32_t *__restrict__ first,
+                             const int32_t *__restrict__ cnt, const int32_t *__restrict__ lvl,
+                             const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                             const int32_t *__restrict__ cz, const int32_t *__restrict__ sys,
+                             const double *__restrict__ lo_side, const uint32_t *__restrict__ perm,
+                             const TI *__restrict__ xyz, double margin, int *moved) {
+    const int64_t li = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (li >= n_leaves) return;
+    const int b = leaves[li];
+    const int s = sys[b];
+    const double side = lo_side[s * 4 + 3];
+    const double lo[3] = {lo_side[s * 4], lo_side[s * 4 + 1], lo_side[s * 4 + 2]};
+    const double w = ldexp(1.0, -lvl[b]);
+    const double c[3] = {(cx[b] + 0.5) * w, (cy[b] + 0.5) * w, (cz[b] + 0.5) * w};
+    const double lim = 0.5 * w + margin;
+    bool bad = false;
+    for (int k = threadIdx.x & 31; k < cnt[b]; k += 32) {
+        const uint32_t j = perm[first[b] + k];
+        for (int d = 0; d < 3; ++d) {
+            const double r = ((double)xyz[3 * j + d] - lo[d]) / side - c[d];
+            bad = bad || !(fabs(r) <= lim);  // also catches NaN
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(moved, 1);
+}
+
 // ---------------------------------------------------------------------------
 // Lists
 // ---------------------------------------------------------------------------
@@ -934,6 +965,25 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
 
 // Leaf-relative particle records in the compute type (also used to refresh
 // positions and charges with the tree frozen).
+cudaError_t check_leaves(Plan &P, const void *xyz, double skin, int *moved_dev, cudaStream_t s) {
+    KIFMM_CUDA_TRY(cudaMemsetAsync(moved_dev, 0, sizeof(int), s));
+    if (P.n_leaves == 0) return cudaSuccess;
+    // the margin is skin half-widths of the finest level in the plan, so no
+    // particle comes closer to any box of its lists than that box's own
+    // surfaces allow for (a W-list box may be many levels finer than the leaf)
+    const double margin = skin * ldexp(0.5, -P.max_level);
+    const unsigned g = (unsigned)((P.n_leaves + 7) / 8);
+    if (P.io_f64)
+        ++g_launches, k_leaf_check<double><<<g, 256, 0, s>>>(P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx,
+                                                             P.cy, P.cz, P.sys, P.lo_side, P.perm,
+                                                             (const double *)xyz, margin, moved_dev);
+    else
+        ++g_launches, k_leaf_check<float><<<g, 256, 0, s>>>(P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx,
+                                                            P.cy, P.cz, P.sys, P.lo_side, P.perm,
+                                                            (const float *)xyz, margin, moved_dev);
+    return cudaGetLastError();
+}
+
 cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream_t s) {
     if (P.f64) {
         if (P.io_f64)

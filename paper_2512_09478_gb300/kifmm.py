@@ -64,7 +64,7 @@ EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifm
            "kifmm_clump_reduce", "kifmm_backward", "kifmm_get_device_status", "kifmm_status_string",
            "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
            "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources",
-           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_measure_peaks"]
+           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_measure_peaks", "kifmm_refresh_sources"]
 
 
 def load(path: str = LIB_PATH):
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
     lib.kifmm_profile_read.argtypes = [P, ctypes.POINTER(ProfileT)]
     lib.kifmm_copy_expansions.argtypes = [P, P, P, P]
     lib.kifmm_update_sources.argtypes = [P, P, P, P]
+    lib.kifmm_refresh_sources.argtypes = [P, P, P, D, ctypes.POINTER(I), P]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int if name != "kifmm_status_string" else ctypes.c_char_p
     _LIB = lib
@@ -172,9 +173,20 @@ class Plan:
     def update_sources(self, xyz: torch.Tensor, q: torch.Tensor, stream=None):
         """New positions/charges for the same particles, tree and lists frozen."""
         assert xyz.is_cuda and q.is_cuda and xyz.dtype == self.dtype and q.dtype == self.dtype
-        assert xyz.shape[0] == self.n
+        assert self.n == 0 or xyz.shape[0] == self.n  # n == 0: the library reports the state error
         _check(load().kifmm_update_sources(self._h, _ptr(xyz.contiguous()), _ptr(q.contiguous()),
                                            _stream(stream)), "kifmm_update_sources")
+
+    def refresh_sources(self, xyz: torch.Tensor, q: torch.Tensor, skin: float = 0.05, stream=None) -> bool:
+        """update_sources if every particle is still within its leaf (grown by
+        `skin` finest-level half-widths), else a full rebuild with the same
+        systems.  Returns True if the tree was kept.  Synchronises."""
+        assert xyz.is_cuda and q.is_cuda and xyz.dtype == self.dtype and q.dtype == self.dtype
+        assert self.n == 0 or xyz.shape[0] == self.n  # n == 0: the library reports the state error
+        reused = ctypes.c_int(0)
+        _check(load().kifmm_refresh_sources(self._h, _ptr(xyz.contiguous()), _ptr(q.contiguous()), float(skin),
+                                            ctypes.byref(reused), _stream(stream)), "kifmm_refresh_sources")
+        return bool(reused.value)
 
     def evaluate(self, pot=None, grad=None, energy=None, want_pot=True, want_grad=True, want_energy=False,
                  stream=None):
