@@ -232,6 +232,19 @@ kifmm_status kifmm_get_device_status(kifmm_plan *plan, int *code);
 /* Static description of a status code. */
 const char *kifmm_status_string(kifmm_status status);
 
+/*
+ * Long-range force computation stride (Eq. 2): S ~ sqrt(k_DEM / k_LR), the
+ * number of DEM time steps over which one long-range evaluation may be
+ * reused, since the Rayleigh time step scales with the square root of the
+ * stiffness.  The forces must be recomputed at least once every S steps, so
+ * the approximation is rounded down: S = max(1, floor(sqrt(k_dem / k_lr))).
+ * k_dem: the largest contact stiffness; k_lr: the largest stiffness of the
+ * long-range interaction (both > 0 and finite, same units).  stride (host)
+ * receives S.  Host only: needs no device and no plan.  KIFMM_ERR_ARG for a
+ * non-positive or non-finite stiffness or a NULL stride.
+ */
+kifmm_status kifmm_lr_stride(double k_dem, double k_lr, int64_t *stride);
+
 /* ------------------------------------------------------------------------
  * Profiling.  When enabled, every stage of set_sources / evaluate is
  * bracketed by CUDA events recorded on the call's stream (no extra

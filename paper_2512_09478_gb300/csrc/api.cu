@@ -208,6 +208,14 @@ const char *kifmm_status_string(kifmm_status s) {
     return "unknown status";
 }
 
+kifmm_status kifmm_lr_stride(double k_dem, double k_lr, int64_t *stride) {
+    if (!stride || !(k_dem > 0.0) || !(k_lr > 0.0) || !std::isfinite(k_dem) || !std::isfinite(k_lr))
+        return KIFMM_ERR_ARG;
+    const double r = std::sqrt(k_dem / k_lr);  // may overflow to inf for extreme ratios
+    *stride = (r >= 9.0e18) ? (int64_t)9000000000000000000LL : std::max<int64_t>(1, (int64_t)std::floor(r));
+    return KIFMM_OK;
+}
+
 kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     if (!desc || !out) return KIFMM_ERR_ARG;
     *out = nullptr;

@@ -963,8 +963,6 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
     return cudaGetLastError();  // the particle records follow once the leaves are listed
 }
 
-// Leaf-relative particle records in the compute type (also used to refresh
-// positions and charges with the tree frozen).
 cudaError_t check_leaves(Plan &P, const void *xyz, double skin, int *moved_dev, cudaStream_t s) {
     KIFMM_CUDA_TRY(cudaMemsetAsync(moved_dev, 0, sizeof(int), s));
     if (P.n_leaves == 0) return cudaSuccess;
@@ -984,6 +982,8 @@ cudaError_t check_leaves(Plan &P, const void *xyz, double skin, int *moved_dev, 
     return cudaGetLastError();
 }
 
+// Leaf-relative particle records in the compute type (also used to refresh
+// positions and charges with the tree frozen).
 cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream_t s) {
     if (P.f64) {
         if (P.io_f64)

@@ -64,7 +64,7 @@ EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifm
            "kifmm_clump_reduce", "kifmm_backward", "kifmm_get_device_status", "kifmm_status_string",
            "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
            "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources",
-           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_measure_peaks", "kifmm_refresh_sources"]
+           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_measure_peaks", "kifmm_refresh_sources", "kifmm_lr_stride"]
 
 
 def load(path: str = LIB_PATH):
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
     lib.kifmm_copy_expansions.argtypes = [P, P, P, P]
     lib.kifmm_update_sources.argtypes = [P, P, P, P]
     lib.kifmm_refresh_sources.argtypes = [P, P, P, D, ctypes.POINTER(I), P]
+    lib.kifmm_lr_stride.argtypes = [D, D, ctypes.POINTER(I64)]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int if name != "kifmm_status_string" else ctypes.c_char_p
     _LIB = lib
@@ -296,6 +297,15 @@ class Plan:
         _check(load().kifmm_copy_list(self._h, LIST_KINDS[kind], ptr.ctypes.data_as(ctypes.c_void_p),
                                       idx.ctypes.data_as(ctypes.c_void_p)), "kifmm_copy_list")
         return ptr, idx[:int(ptr[-1])]
+
+
+def lr_stride(k_dem: float, k_lr: float) -> int:
+    """Long-range force computation stride S = max(1, floor(sqrt(k_dem / k_lr)))
+    (Eq. 2): evaluate the long-range forces at least once every S DEM steps.
+    Host only (no device needed)."""
+    s = ctypes.c_int64(0)
+    _check(load().kifmm_lr_stride(float(k_dem), float(k_lr), ctypes.byref(s)), "kifmm_lr_stride")
+    return s.value
 
 
 def energy_noalloc(q: torch.Tensor, pot: torch.Tensor, out: torch.Tensor = None, stream=None) -> torch.Tensor:
