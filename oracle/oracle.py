@@ -32,6 +32,14 @@ Sec. 2.2) and fixed as follows:
 * Lists: U, V, W, X of the adaptive KIFMM, classified from their definitions;
   a W/X interaction whose finer box is a leaf with at most n_s points is
   summed directly (moved to U), the original KIFMM's cost rule.
+* Compressed M2L (optional; the operators are matrices computed from the
+  kernel, Sec. 2.2, so a low-rank form of them is another such matrix): the
+  316 M2L matrices share a left basis (the leading left singular vectors of
+  their mean-free forms side by side) and a right basis (the leading right
+  singular vectors of the full matrices stacked), truncated at eps * sigma_0
+  with the ranks rounded up to fill 32-wide tiles (the left rank leaves one
+  slot for the mean) and lowered off any cluster of equal singular values;
+  each matrix is replaced by its projection (U U^T K0 + 1 m^T) V V^T.
 
 Parity status: every function here is pinned by tests under tests/ against
 closed forms, invariants or brute force (see the test module docstrings).
@@ -366,6 +374,46 @@ def operators(p: int, eps: float = 1e-12):
                            for o in range(8)])
     ops["m2l"] = np.stack([kernel_matrix(ALPHA_DC * S, 2.0 * d + ALPHA_UE * S) for d in m2l_offsets()])
     return ops
+
+
+M2L_GAP = 1.001
+
+
+def compress_rank(sig, eps: float, tile: int = 32, mean_slot: int = 0) -> int:
+    """Rank kept from descending singular values ``sig``: the count above
+    eps * sig[0], rounded up so that rank + mean_slot is a multiple of
+    ``tile`` (at most len(sig)), then lowered while the cut would split a
+    cluster of equal values (sig[r-1] <= M2L_GAP * sig[r])."""
+    sig = np.asarray(sig, dtype=np.float64)
+    n = sig.shape[0]
+    r0 = int(np.sum(sig > eps * sig[0]))
+    r = min(n, tile * ((r0 + mean_slot + tile - 1) // tile) - mean_slot)
+    while 1 < r < n and sig[r - 1] <= M2L_GAP * sig[r]:
+        r -= 1
+    return r
+
+
+def compress_m2l(ops, eps: float, tile: int = 32):
+    """Operators with every M2L matrix K_o (DC <- UE + 2 d_o, on equivalent
+    densities) replaced by its projection onto the shared bases:
+    K_o -> (U U^T K0_o + 1 m_o^T) V V^T, where m_o is the mean of K_o over its
+    outputs (rows), K0_o = K_o - 1 m_o^T, U = leading left singular vectors of
+    [K0_1 ... K0_316] (rank r_L, mean_slot 1) and V = leading right singular
+    vectors of [K_1; ...; K_316] (rank r_R).  Returns (ops', info) with the
+    ranks and both singular value lists."""
+    K = np.asarray(ops["m2l"], dtype=np.float64)
+    m = K.mean(axis=1)
+    K0 = K - m[:, None, :]
+    u_l, s_l, _ = np.linalg.svd(np.concatenate(list(K0), axis=1), full_matrices=False)
+    _, s_r, vh_r = np.linalg.svd(np.concatenate(list(K), axis=0), full_matrices=False)
+    r_l = compress_rank(s_l, eps, tile, 1)
+    r_r = compress_rank(s_r, eps, tile, 0)
+    U = u_l[:, :r_l]
+    V = vh_r[:r_r].T
+    Kh = (np.einsum("ij,ojk->oik", U @ U.T, K0) + np.ones((1, K.shape[1], 1)) * m[:, None, :]) @ (V @ V.T)
+    out = dict(ops)
+    out["m2l"] = np.ascontiguousarray(Kh)
+    return out, {"r_l": r_l, "r_r": r_r, "s_l": s_l, "s_r": s_r, "U": U, "V": V}
 
 
 # ---------------------------------------------------------------------------
