@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed tile shapes (default: the library tunes them on the first, untimed, evaluate)")
+    ap.add_argument("--m2l-eps-compare", type=float, default=1e-5,
+                    help="also time the same step with the compressed M2L at this eps (0: skip)")
     ap.add_argument("--compare", default="auto",
                     help="also time this precision on the same workload (auto: the workload's comparison "
                          "path, none: skip)")
@@ -615,6 +617,10 @@ def run_ours(args, rank, world, local_rank):
     if cmp_prec and cmp_prec != args.precision:
         out["compare"] = compare_leg(args, w, cmp_prec, xt, qt, offsets, coef, n, n / (ms_per_step * 1e-3) / 1e6, stream, flush,
                                      clumps, (coff, cref) if clumps else None, ref, q)
+    if args.m2l_eps_compare > 0 and args.precision == "mixed_fp16":
+        out["m2l_compressed"] = compare_leg(args, w, "mixed_fp16", xt, qt, offsets, coef, n,
+                                            n / (ms_per_step * 1e-3) / 1e6, stream, flush, clumps,
+                                            (coff, cref) if clumps else None, ref, q, m2l_eps=args.m2l_eps_compare)
     print(json.dumps(out), flush=True)
 
 
@@ -635,15 +641,17 @@ def accuracy_of(ref, q, coef, pot, grad, force=None, torque=None):
     return acc
 
 
-def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, clumps, cl, ref, q):
+def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, clumps, cl, ref, q, m2l_eps=0.0):
     """The same step with another precision of the library (plain FP32 SIMT
-    M2L for the DEM workload, the FP64 path for gravity): its throughput,
-    the speedup of the benchmarked precision over it, and its accuracy."""
+    M2L for the DEM workload, the FP64 path for gravity), or with the
+    compressed M2L (m2l_eps > 0): its throughput, the speedup of the
+    benchmarked configuration over it, and its accuracy."""
     import torch
     from paper_2512_09478_gb300 import Plan
     dt = torch.float64 if prec == "fp64" else torch.float32
     plan = Plan(p=w["p"], leaf_cap=w["leaf_cap"], max_depth=w["max_depth"], precision=prec, coef=coef,
-                n_max=n, n_systems_max=len(offsets) - 1, dtype=dt, autotune=not args.no_autotune)
+                n_max=n, n_systems_max=len(offsets) - 1, dtype=dt, autotune=not args.no_autotune,
+                m2l_eps=m2l_eps)
     x2, q2 = xt.to(dt), qt.to(dt)
     pot = torch.empty(n, dtype=dt, device=xt.device)
     grad = torch.empty(n, 3, dtype=dt, device=xt.device)
@@ -675,6 +683,9 @@ def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, c
     v = n / (ms / k * 1e-3) / 1e6
     res = {"precision": prec, "value": v, "unit": UNIT, "ms_per_step": ms / k, "steps": k,
            "speedup_of_benchmarked": value / v, "io_dtype": "f64" if prec == "fp64" else "f32"}
+    if m2l_eps > 0:
+        res["m2l_eps"] = m2l_eps
+        res["m2l_ranks_out_in"] = list(plan.tuning()["m2l_ranks"])
     if ref is not None:
         res["accuracy"] = accuracy_of(ref, q, coef, pot, grad, force if clumps else None,
                                       torque if clumps else None)

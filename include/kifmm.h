@@ -90,6 +90,22 @@ typedef struct {
                             U-list (P2P) entry: the original KIFMM's cost rule
                             for the adaptive lists (Sec. 2.2).  0 selects n_s;
                             a negative value keeps every W/X interaction.      */
+    double m2l_eps;      /* compressed M2L (tensor-core modes only; 0: dense).
+                            The 316 M2L matrices K_o (downward check surface
+                            from the source's upward equivalent surface, Sec.
+                            2.2's operators computed from the kernel) are
+                            replaced by low-rank forms on two shared bases: U,
+                            the leading left singular vectors of their
+                            mean-free forms side by side, and V, the leading
+                            right singular vectors of the matrices stacked.
+                            Ranks: the singular values above m2l_eps * sigma_0,
+                            rounded up to fill 32-wide tensor-core tiles (the
+                            left rank leaves one column for the mean), then
+                            lowered while the cut would split a cluster of
+                            equal values (within a factor 1.001).  Each M2L is
+                            then (U U^T K0_o + 1 m_o^T) V V^T.  A value >= 1
+                            or not finite is KIFMM_ERR_ARG, as is any nonzero
+                            value in the FP64 and FP32 modes.               */
 } kifmm_plan_desc;
 
 typedef struct kifmm_plan kifmm_plan;
@@ -283,13 +299,17 @@ kifmm_status kifmm_profile_read(kifmm_plan *plan, kifmm_profile_t *out);
  * covered by passes; with r of its targets still to cover, bucket
  * min((r - 1) / 8, 15) selects leaf_tpl targets per lane and leaf_groups
  * source groups for the next pass, which covers 32 / groups * tpl targets;
- * each (tpl, groups) variant is its own kernel.
+ * each (tpl, groups) variant is its own kernel.  m2l_rank_out/in: the ranks
+ * a compressed M2L (desc.m2l_eps) chose at plan creation.
  * Host memory; no device work. */
 typedef struct {
     int tuned;
     int m2l_stages;
     int leaf_tpl[16];
     int leaf_groups[16];
+    int m2l_rank_out;    /* compressed M2L: left rank (outputs, without the
+                            mean column); 0 for a dense M2L               */
+    int m2l_rank_in;     /* compressed M2L: right rank (inputs); 0 if dense  */
 } kifmm_tuning_t;
 kifmm_status kifmm_get_tuning(kifmm_plan *plan, kifmm_tuning_t *out);
 

@@ -164,6 +164,8 @@ static cudaError_t ensure_box_arrays(Plan &P) {
         {&P.tmp_chk, esz * P.ns * cap},
         {&P.dn_dens, esz * P.ns * cap},
         {(void **)&P.dbar, sizeof(double) * cap},
+        {&P.u_c, sizeof(float) * (size_t)P.m2l_rr * cap},
+        {&P.d_c, sizeof(float) * (size_t)P.m2l_rl * cap},
         {(void **)&P.leaf_vlist, sizeof(int2) * kLeafTiles * (cap + P.desc.n_max / 8 + 64)},
         {(void **)&P.leaf_vcnt, sizeof(int32_t) * 8},
     };
@@ -225,6 +227,8 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     if (d.n_max < 1 || d.n_max > (int64_t)0x7fffffff || d.n_systems_max < 1) return KIFMM_ERR_ARG;
     if (d.dtype != KIFMM_DTYPE_F32 && d.dtype != KIFMM_DTYPE_F64) return KIFMM_ERR_ARG;
     if (!(d.pinv_eps >= 0.0) || d.pinv_eps >= 1.0) return KIFMM_ERR_ARG;
+    if (!(d.m2l_eps >= 0.0) || d.m2l_eps >= 1.0) return KIFMM_ERR_ARG;
+    if (d.m2l_eps > 0.0 && d.precision != KIFMM_MIXED_FP16) return KIFMM_ERR_ARG;
     kifmm_plan *pl = new (std::nothrow) kifmm_plan();
     if (!pl) return KIFMM_ERR_CUDA;
     Plan &P = pl->P;
@@ -506,6 +510,8 @@ kifmm_status kifmm_get_tuning(kifmm_plan *pl, kifmm_tuning_t *out) {
     const Plan &P = pl->P;
     out->tuned = (P.tuned_leaf ? 1 : 0) | (P.tuned_m2l ? 2 : 0);
     out->m2l_stages = m2l_tensor_stages(P);
+    out->m2l_rank_out = P.m2l_rl;
+    out->m2l_rank_in = P.m2l_rr;
     for (int i = 0; i < kLeafBuckets; ++i) {
         out->leaf_tpl[i] = leaf_tile_tpl(P.leaf_tile.get(i));
         out->leaf_groups[i] = leaf_tile_groups(P.leaf_tile.get(i));

@@ -87,6 +87,13 @@ struct Plan {
     void *m2l_tc = nullptr;     // layout owned by the tensor-core kernel
     float *m2l_tc_scale = nullptr;
     int *slot_off = nullptr;    // [8][189] V slot -> M2L offset index (-1 unused)
+    // Compressed M2L (desc.m2l_eps > 0, tensor-core mode): d = U C_o W u with
+    // C_o = U^T K0_o V (plus the mean row m_o^T V), W = V^T P_up.
+    int m2l_rl = 0, m2l_rr = 0; // left rank (outputs, mean excluded), right rank (inputs)
+    float *m2l_c = nullptr;     // [316][rr][rl + 1] C_o^T with the mean row in column rl
+    float *m2l_wc = nullptr;    // [rr][ns] W: check potential -> compressed input
+    float *m2l_ul = nullptr;    // [ns][rl] U: compressed output -> mean-free check potential
+    void *u_c = nullptr, *d_c = nullptr;  // [box cap][rr], [box cap][rl]
 
     // ---- capacities ----
     int64_t n_cap = 0, box_cap = 0, u_cap = 0, w_cap = 0;

@@ -322,6 +322,60 @@ __global__ void k_level_scale(int nlev, const unsigned *__restrict__ level_max, 
     level_unscale[l] = 1.f / (s * sigma_b);
 }
 
+// Compressed M2L projections: out[row][j] = sum_k in[row][k] M[j][k] for the
+// rows listed in `rows` (all rows 0..nrows-1 when null).  M row-major
+// [n_out][n_in].  A 64 x 64 output tile per block of 256 threads (4 x 4 per
+// thread), K staged in shared memory 32 at a time.
+__global__ void __launch_bounds__(256) k_rowmat(int64_t nrows, const int32_t *__restrict__ rows,
+                                                const float *__restrict__ in, int ld_in, int n_in,
+                                                const float *__restrict__ M, float *__restrict__ out, int ld_out,
+                                                int n_out) {
+    __shared__ float As[32][65], Bs[32][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int c0 = blockIdx.y * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < n_in; k0 += 32) {
+        for (int e = tid; e < 64 * 32; e += 256) {
+            const int r = e >> 5, k = e & 31;
+            const int64_t rr = r0 + r;
+            float v = 0.f;
+            if (rr < nrows && k0 + k < n_in) {
+                const int64_t row = rows ? rows[rr] : rr;
+                v = in[row * ld_in + k0 + k];
+            }
+            As[k][r] = v;
+            const int c = c0 + r;
+            Bs[k][r] = (c < n_out && k0 + k < n_in) ? M[(size_t)c * n_in + k0 + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t rr = r0 + ty + 16 * i;
+        if (rr >= nrows) continue;
+        const int64_t row = rows ? rows[rr] : rr;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = c0 + tx + 16 * j;
+            if (c < n_out) out[row * ld_out + c] = acc[i][j];
+        }
+    }
+}
+
 // hi/lo FP16 split of the scaled expansions, K padded with zeros.
 __global__ void k_split_u(int64_t nb, int ns, int kp, const float *__restrict__ u, const int32_t *__restrict__ lvl,
                           const float *__restrict__ level_sigma, __half *__restrict__ uh, __half *__restrict__ ul) {
@@ -396,6 +450,7 @@ struct TcState {
     int64_t tiles_cap = 0;
     std::vector<int4> tiles_h;
     size_t smem = 0;
+    int n_in = 0, n_out = 0, ld = 0;  // operator inputs, outputs (mean excluded), stored columns
 };
 
 static TcState &tc_state(Plan &P) {
@@ -415,15 +470,21 @@ void m2l_tensor_release(Plan &P) {
 // Plan time: FP16 hi/lo operators with one power-of-two scale.
 cudaError_t m2l_tensor_setup(Plan &P) {
     TcState &S = tc_state(P);
-    const int ns = P.ns;
+    // Dense: u (ns values) -> d (ns values + the mean row).  Compressed: the
+    // rr-value projection of u -> rl values + the mean row.
+    const bool comp = P.m2l_rl > 0;
+    const float *ops = comp ? P.m2l_c : (const float *)P.m2l_t;
+    S.n_in = comp ? P.m2l_rr : P.ns;
+    S.n_out = comp ? P.m2l_rl : P.ns;
+    S.ld = comp ? P.m2l_rl + 1 : P.op_ld;
     // Output columns per CTA: at most 160 (three partial accumulators fit
     // TMEM; the drain warps keep 80 running sums each in registers); larger
     // surfaces (p >= 7) are split into column blocks over blockIdx.y.
-    const int np0 = round_up(ns + 1, 32);  // room for the mean row (FP32-based modes)
+    const int np0 = round_up(S.n_out + 1, 32);  // room for the mean row (FP32-based modes)
     S.ncb = (np0 + 159) / 160;
     S.nt = round_up((np0 + S.ncb - 1) / S.ncb, 32);
     S.np = S.nt * S.ncb;
-    S.kp = round_up(ns, kKBlock);
+    S.kp = round_up(S.n_in, kKBlock);
     const size_t stage = 2 * (size_t)kTcRows * kRowBytes + 2 * (size_t)S.nt * kRowBytes;
     S.nstages = (int)std::min<size_t>(16, (227 * 1024 - 4096) / stage);
     if (S.nstages < 2 || S.nt > 160) return cudaErrorNotSupported;
@@ -433,8 +494,8 @@ cudaError_t m2l_tensor_setup(Plan &P) {
     unsigned *dmax = nullptr;
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&dmax, sizeof(unsigned)));
     KIFMM_CUDA_TRY(cudaMemset(dmax, 0, sizeof(unsigned)));
-    const int64_t nm = (int64_t)kNumM2L * ns * P.op_ld;
-    ++g_launches, k_absmax_f32<<<256, 256>>>(nm, (const float *)P.m2l_t, dmax);
+    const int64_t nm = (int64_t)kNumM2L * S.n_in * S.ld;
+    ++g_launches, k_absmax_f32<<<256, 256>>>(nm, ops, dmax);
     unsigned mbits = 0;
     KIFMM_CUDA_TRY(cudaMemcpy(&mbits, dmax, sizeof(unsigned), cudaMemcpyDeviceToHost));
     float mx;
@@ -445,7 +506,7 @@ cudaError_t m2l_tensor_setup(Plan &P) {
     const size_t nb = (size_t)kNumM2L * S.np * S.kp;
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.bh, sizeof(__half) * nb));
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.bl, sizeof(__half) * nb));
-    ++g_launches, k_split_ops<<<(unsigned)((nb + 255) / 256), 256>>>(kNumM2L, ns, P.op_ld, S.np, S.kp, (const float *)P.m2l_t,
+    ++g_launches, k_split_ops<<<(unsigned)((nb + 255) / 256), 256>>>(kNumM2L, S.n_in, S.ld, S.np, S.kp, ops,
                                                                      S.sigma_b, S.bh, S.bl);
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.level_max, sizeof(unsigned) * 32));
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.level_sigma, sizeof(float) * 32));
@@ -480,13 +541,19 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {
     TcState &S = tc_state(P);
     if (S.tiles_h.empty()) return cudaSuccess;
     const int nlev = P.max_level + 1;
+    const bool comp = P.m2l_rl > 0;
+    const float *u = (const float *)P.u_chk;
+    if (comp) {  // project every box's check potential onto the right basis
+        ++g_launches, k_rowmat<<<dim3((unsigned)((P.nb + 63) / 64), (unsigned)((S.n_in + 63) / 64)), 256, 0, s>>>(
+            P.nb, nullptr, u, P.ns, P.ns, P.m2l_wc, (float *)P.u_c, S.n_in, S.n_in);
+        u = (const float *)P.u_c;
+    }
     KIFMM_CUDA_TRY(cudaMemsetAsync(S.level_max, 0, sizeof(unsigned) * 32, s));
-    ++g_launches, k_level_absmax<<<(unsigned)((P.nb + 7) / 8), 256, 0, s>>>(P.nb, P.ns, (const float *)P.u_chk, P.lvl,
-                                                                            S.level_max);
+    ++g_launches, k_level_absmax<<<(unsigned)((P.nb + 7) / 8), 256, 0, s>>>(P.nb, S.n_in, u, P.lvl, S.level_max);
     ++g_launches, k_level_scale<<<1, 32, 0, s>>>(nlev, S.level_max, S.sigma_b, S.level_sigma, S.level_unscale);
     const int64_t tot = P.nb * S.kp;
-    ++g_launches, k_split_u<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.nb, P.ns, S.kp, (const float *)P.u_chk,
-                                                                          P.lvl, S.level_sigma, S.uh, S.ul);
+    ++g_launches, k_split_u<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.nb, S.n_in, S.kp, u, P.lvl,
+                                                                          S.level_sigma, S.uh, S.ul);
     TileArgs a;
     a.targets = P.m2l_targets;
     a.tiles = S.tiles;
@@ -498,9 +565,9 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {
     a.bl = S.bl;
     a.lvl = P.lvl;
     a.level_unscale = S.level_unscale;
-    a.d = (float *)P.d_chk;
-    a.dbar = (P.op_ld > P.ns) ? P.dbar : nullptr;
-    a.ns = P.ns;
+    a.d = comp ? (float *)P.d_c : (float *)P.d_chk;
+    a.dbar = (S.ld > S.n_out) ? P.dbar : nullptr;
+    a.ns = S.n_out;
     a.kp = S.kp;
     a.np = S.np;
     a.status = P.status;
@@ -537,7 +604,13 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {
         S.nstages = pick;
         P.tuned_m2l = true;
     }
-    return launch(S.nstages);
+    KIFMM_CUDA_TRY(launch(S.nstages));
+    if (comp) {  // back to the mean-free check potential of every target
+        const int64_t nt = P.m2l_class_start[8];
+        ++g_launches, k_rowmat<<<dim3((unsigned)((nt + 63) / 64), (unsigned)((P.ns + 63) / 64)), 256, 0, s>>>(
+            nt, P.m2l_targets, (const float *)P.d_c, S.n_out, S.n_out, P.m2l_ul, (float *)P.d_chk, P.ns, P.ns);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace kifmm

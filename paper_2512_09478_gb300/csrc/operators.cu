@@ -15,6 +15,7 @@
 // Jacobi (Hestenes) iteration in FP64 on the GPU with a cyclic round-robin
 // pair order (Brent & Luk); products are formed as ((K V) diag(sinv)) U^T so
 // the large entries of P never appear explicitly.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -172,6 +173,41 @@ __global__ void k_make_wt(int n, const double *Ut, const double *sinv, double *W
     Wt[idx] = sinv[m] * Ut[(size_t)m * n + j];
 }
 
+// G[i][l] = sum_b sum_m A_b[m][i] A_b[m][l]: the Gram matrix of nb row-major
+// n x n blocks stacked vertically.  One thread per (i, l).
+__global__ void k_gram(int n, int nb, const double *__restrict__ A, double *__restrict__ G) {
+    const int i = blockIdx.y, l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        const double *Ab = A + (size_t)b * n * n;
+        for (int m = 0; m < n; ++m) acc += Ab[(size_t)m * n + i] * Ab[(size_t)m * n + l];
+    }
+    G[(size_t)i * n + l] = acc;
+}
+
+// out[b][c] = sum_k mean[b][k] V[k][c] (V row-major n x n, columns >= r zero).
+__global__ void k_mean_proj(int n, int nb, const double *__restrict__ mean, const double *__restrict__ V,
+                            double *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nb * n) return;
+    const int b = (int)(t / n), c = (int)(t % n);
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc += mean[(size_t)b * n + k] * V[(size_t)k * n + c];
+    out[t] = acc;
+}
+
+// FP32 [nb][rr][rl + 1]: Bt[b][c][i] for i < rl, the mean row mh[b][c] at i = rl.
+__global__ void k_pack_compressed(int n, int nb, int rr, int rl, const double *__restrict__ Bt,
+                                  const double *__restrict__ mh, float *__restrict__ out) {
+    const int64_t ld = rl + 1;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nb * rr * ld) return;
+    const int b = (int)(t / (rr * ld));
+    const int c = (int)((t / ld) % rr), i = (int)(t % ld);
+    out[t] = (float)((i < rl) ? Bt[((size_t)b * n + c) * n + i] : mh[(size_t)b * n + c]);
+}
+
 std::vector<double> unit_surface(int p) {
     std::vector<double> s;
     for (int i = 0; i < p; ++i)
@@ -219,6 +255,120 @@ std::vector<int> m2l_offset_list() {
                 out.push_back(c);
             }
     return out;
+}
+
+// Rank from descending singular values: the count above eps * sig[0],
+// rounded up so that rank + mean_slot fills 32-wide tiles (at most n), then
+// lowered while the cut would split a cluster (sig[r-1] <= 1.001 sig[r]).
+static int compress_rank(const std::vector<double> &sig, double eps, int mean_slot) {
+    const int n = (int)sig.size();
+    int r0 = 0;
+    for (int i = 0; i < n; ++i) r0 += (sig[i] > eps * sig[0]) ? 1 : 0;
+    int r = std::min(n, 32 * ((r0 + mean_slot + 31) / 32) - mean_slot);
+    while (r > 1 && r < n && sig[r - 1] <= 1.001 * sig[r]) --r;
+    return r;
+}
+
+// Compressed M2L on shared bases.  K (device): the 316 raw M2L blocks,
+// row-major [j][k] (output DC point j, input UE point k).  U: leading
+// eigenvectors of sum_o K0_o K0_o^T (K0 = K minus its mean over j); V: of
+// sum_o K_o^T K_o; both from the FP64 Jacobi SVD of the symmetric Gram
+// matrices (singular values = eigenvalues; the accumulated rotations are the
+// eigenvectors).  Builds m2l_c (C_o^T = (U^T K0_o V)^T with the mean row
+// m_o^T V in column rl), m2l_wc = V^T P_up and m2l_ul = U, all FP32.
+static cudaError_t build_m2l_compressed(Plan &P, const double *dK, const double *Ut_up, const double *Vt_up,
+                                        const double *sinv_up, std::string &err) {
+    const int n = P.ns;
+    const size_t nn = (size_t)n * n;
+    const int nb = kNumM2L;
+    double *T = nullptr, *mean = nullptr, *K0 = nullptr, *G = nullptr, *Gv = nullptr, *Gs = nullptr;
+    int *sw = nullptr;
+    KIFMM_CUDA_TRY(cudaMalloc(&T, sizeof(double) * nb * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&K0, sizeof(double) * nb * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&mean, sizeof(double) * nb * n));
+    KIFMM_CUDA_TRY(cudaMalloc(&G, sizeof(double) * 2 * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&Gv, sizeof(double) * 2 * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&Gs, sizeof(double) * 2 * n));
+    KIFMM_CUDA_TRY(cudaMalloc(&sw, sizeof(int) * 2));
+    const size_t tot = nn * nb;
+    // T = K^T ([k][j]); centre each row over j: T0 = K0^T and the means m_o[k]
+    k_transpose_blocks<<<(unsigned)((tot + 255) / 256), 256>>>(n, nb, 0, dK, T);
+    k_center_rows<<<(unsigned)((nb * n + 255) / 256), 256>>>(n, nb, T, mean);
+    // G_L = sum T0^T T0 = sum K0 K0^T; G_R = sum K^T K
+    k_gram<<<dim3((n + 127) / 128, n), 128>>>(n, nb, T, G);
+    k_gram<<<dim3((n + 127) / 128, n), 128>>>(n, nb, dK, G + nn);
+    k_jacobi_svd<<<2, kSvdThreads>>>(n, G, Gv, Gs, 60, 1e-15, sw);
+    KIFMM_CUDA_TRY(cudaGetLastError());
+    std::vector<double> lam(2 * n), vt(2 * nn);
+    int sweeps[2];
+    KIFMM_CUDA_TRY(cudaMemcpy(lam.data(), Gs, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
+    KIFMM_CUDA_TRY(cudaMemcpy(vt.data(), Gv, sizeof(double) * 2 * nn, cudaMemcpyDeviceToHost));
+    KIFMM_CUDA_TRY(cudaMemcpy(sweeps, sw, sizeof(int) * 2, cudaMemcpyDeviceToHost));
+    if (sweeps[0] >= 60 || sweeps[1] >= 60) {
+        err = "Jacobi eigensolver of the M2L Gram matrices did not converge";
+        return cudaErrorUnknown;
+    }
+    // sort each spectrum (descending) and pick the ranks
+    int rank[2];
+    std::vector<int> order[2];
+    for (int m = 0; m < 2; ++m) {
+        order[m].resize(n);
+        for (int i = 0; i < n; ++i) order[m][i] = i;
+        std::stable_sort(order[m].begin(), order[m].end(),
+                         [&](int a, int b) { return lam[m * n + a] > lam[m * n + b]; });
+        std::vector<double> sig(n);
+        for (int i = 0; i < n; ++i) sig[i] = std::sqrt(std::fmax(lam[m * n + order[m][i]], 0.0));
+        rank[m] = compress_rank(sig, P.desc.m2l_eps, m == 0 ? 1 : 0);
+    }
+    const int rl = rank[0], rr = rank[1];
+    // bases, zero-padded to n x n: Up[j][i] = u_i[j] (i < rl); Vp[k][c] = v_c[k] (c < rr)
+    std::vector<double> Up(nn, 0.0), Vp(nn, 0.0), VpT(nn, 0.0);
+    for (int i = 0; i < rl; ++i)
+        for (int j = 0; j < n; ++j) Up[(size_t)j * n + i] = vt[(size_t)order[0][i] * n + j];
+    for (int c = 0; c < rr; ++c)
+        for (int k = 0; k < n; ++k) {
+            Vp[(size_t)k * n + c] = vt[nn + (size_t)order[1][c] * n + k];
+            VpT[(size_t)c * n + k] = Vp[(size_t)k * n + c];
+        }
+    double *dUp = nullptr, *dVp = nullptr, *dVpT = nullptr, *KVt = nullptr, *Bt = nullptr, *mh = nullptr,
+           *Y = nullptr, *Wc = nullptr;
+    KIFMM_CUDA_TRY(cudaMalloc(&dUp, sizeof(double) * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&dVp, sizeof(double) * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&dVpT, sizeof(double) * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&KVt, sizeof(double) * nb * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&Bt, sizeof(double) * nb * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&mh, sizeof(double) * nb * n));
+    KIFMM_CUDA_TRY(cudaMalloc(&Y, sizeof(double) * nn));
+    KIFMM_CUDA_TRY(cudaMalloc(&Wc, sizeof(double) * nn));
+    KIFMM_CUDA_TRY(cudaMemcpy(dUp, Up.data(), sizeof(double) * nn, cudaMemcpyHostToDevice));
+    KIFMM_CUDA_TRY(cudaMemcpy(dVp, Vp.data(), sizeof(double) * nn, cudaMemcpyHostToDevice));
+    KIFMM_CUDA_TRY(cudaMemcpy(dVpT, VpT.data(), sizeof(double) * nn, cudaMemcpyHostToDevice));
+    const dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16, nb), grd1((n + 15) / 16, (n + 15) / 16, 1);
+    // K0 row-major, then (K0 V)^T, then Bt = (K0 V)^T U = C^T ([c][i])
+    k_transpose_blocks<<<(unsigned)((tot + 255) / 256), 256>>>(n, nb, 0, T, K0);
+    k_dgemm<<<grd, blk>>>(n, K0, nn, dVp, nullptr, 0, 1.0, KVt, nn, 1);
+    k_dgemm<<<grd, blk>>>(n, KVt, nn, dUp, nullptr, 0, 1.0, Bt, nn, 0);
+    k_mean_proj<<<(unsigned)((nb * n + 255) / 256), 256>>>(n, nb, mean, dVp, mh);
+    // W = V^T P_up = (V^T V_up) diag(sinv) U_up^T
+    k_dgemm<<<grd1, blk>>>(n, dVpT, 0, Vt_up, nullptr, 1, 1.0, Y, 0, 0);
+    k_dgemm<<<grd1, blk>>>(n, Y, 0, Ut_up, sinv_up, 0, 1.0, Wc, 0, 0);
+    KIFMM_CUDA_TRY(cudaGetLastError());
+    const size_t nc = (size_t)nb * rr * (rl + 1);
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.m2l_c, sizeof(float) * nc));
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.m2l_wc, sizeof(float) * (size_t)rr * n));
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.m2l_ul, sizeof(float) * (size_t)n * rl));
+    k_pack_compressed<<<(unsigned)((nc + 255) / 256), 256>>>(n, nb, rr, rl, Bt, mh, P.m2l_c);
+    k_to_f32<<<(unsigned)(((size_t)rr * n + 255) / 256), 256>>>(Wc, P.m2l_wc, (size_t)rr * n);  // rows < rr
+    std::vector<float> ul((size_t)n * rl);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < rl; ++i) ul[(size_t)j * rl + i] = (float)Up[(size_t)j * n + i];
+    KIFMM_CUDA_TRY(cudaMemcpy(P.m2l_ul, ul.data(), sizeof(float) * ul.size(), cudaMemcpyHostToDevice));
+    KIFMM_CUDA_TRY(cudaDeviceSynchronize());
+    P.m2l_rl = rl;
+    P.m2l_rr = rr;
+    for (double *q : {T, K0, mean, G, Gv, Gs, dUp, dVp, dVpT, KVt, Bt, mh, Y, Wc}) cudaFree(q);
+    cudaFree(sw);
+    return cudaGetLastError();
 }
 
 cudaError_t build_operators(Plan &P, std::string &err) {
@@ -392,6 +542,7 @@ cudaError_t build_operators(Plan &P, std::string &err) {
         KIFMM_CUDA_TRY(cudaDeviceSynchronize());
         cudaFree(dMean);
     }
+    if (P.desc.m2l_eps > 0.0) KIFMM_CUDA_TRY(build_m2l_compressed(P, dK + 16 * nn, Ut_up, Vt_up, sinv_up, err));
     // surfaces
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf64, sizeof(double) * 3 * n));
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf32, sizeof(float) * 3 * n));

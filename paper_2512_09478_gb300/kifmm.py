@@ -31,7 +31,7 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("precision", ctypes.c_int), ("coef", ctypes.c_double), ("n_max", ctypes.c_int64),
                 ("n_systems_max", ctypes.c_int), ("dtype", ctypes.c_int), ("pinv_eps", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("direct_max", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("direct_max", ctypes.c_int), ("m2l_eps", ctypes.c_double)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -50,7 +50,7 @@ class ProfileT(ctypes.Structure):
 
 class TuningT(ctypes.Structure):
     _fields_ = [("tuned", ctypes.c_int), ("m2l_stages", ctypes.c_int), ("leaf_tpl", ctypes.c_int * 16),
-                ("leaf_groups", ctypes.c_int * 16)]
+                ("leaf_groups", ctypes.c_int * 16), ("m2l_rank_out", ctypes.c_int), ("m2l_rank_in", ctypes.c_int)]
 
 
 class PeaksT(ctypes.Structure):
@@ -130,14 +130,15 @@ class Plan:
     def __init__(self, p: int = 6, leaf_cap: int = 128, max_depth: int = 20, precision: str = "fp32",
                  coef: float = 1.0, n_max: int = 1 << 20, n_systems_max: int = 1,
                  dtype: torch.dtype = torch.float32, pinv_eps: float = 0.0, autotune: bool = False,
-                 direct_max: int = 0):
+                 direct_max: int = 0, m2l_eps: float = 0.0):
         lib = load()
         self.dtype = dtype
         self.precision = precision
         self.coef = coef
         d = PlanDesc(p=p, leaf_cap=leaf_cap, max_depth=max_depth, precision=PRECISIONS[precision], coef=coef,
                      n_max=n_max, n_systems_max=n_systems_max,
-                     dtype=1 if dtype == torch.float64 else 0, pinv_eps=pinv_eps, autotune=int(autotune), direct_max=direct_max)
+                     dtype=1 if dtype == torch.float64 else 0, pinv_eps=pinv_eps, autotune=int(autotune), direct_max=direct_max,
+                     m2l_eps=m2l_eps)
         h = ctypes.c_void_p()
         _check(lib.kifmm_plan_create(ctypes.byref(d), ctypes.byref(h)), "kifmm_plan_create")
         self._h = h
@@ -240,7 +241,8 @@ class Plan:
         t = TuningT()
         _check(load().kifmm_get_tuning(self._h, ctypes.byref(t)), "kifmm_get_tuning")
         return {"tuned_leaf": bool(t.tuned & 1), "tuned_m2l": bool(t.tuned & 2), "m2l_stages": t.m2l_stages,
-                "leaf_tiles": [(t.leaf_tpl[i], t.leaf_groups[i]) for i in range(16)]}
+                "leaf_tiles": [(t.leaf_tpl[i], t.leaf_groups[i]) for i in range(16)],
+                "m2l_ranks": (t.m2l_rank_out, t.m2l_rank_in)}
 
     def profile_read(self) -> dict:
         """Per-stage device milliseconds and bracket counts since the last
