@@ -123,6 +123,7 @@ struct Plan {
     std::vector<int64_t> level_start;  // host: level l owns [level_start[l], level_start[l+1])
     int64_t nb = 0, n = 0;
     int n_sys = 0, max_level = 0;
+    int sort_passes = 8;  // 8-bit key digits the last build sorted (from the top)
     std::vector<int64_t> sys_off_h;
 
     // ---- lists ----

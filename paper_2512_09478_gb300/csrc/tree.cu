@@ -2,10 +2,11 @@
 // at most M points per leaf; third step: the interaction lists).
 //
 //   per-system bounding cube -> 63-bit Morton keys -> stable LSD radix sort
-//   (8-bit digits) -> octree level by level (binary search of the octant
-//   boundaries inside each split node's key range) -> colleagues, coarse
-//   adjacent leaves, U/V/W/X lists.
+//   of the key digits the octree reads (8-bit digits) -> octree level by
+//   level (binary search of the octant boundaries inside each split node's
+//   key range) -> colleagues, coarse adjacent leaves, U/V/W/X lists.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "common.cuh"
@@ -877,11 +878,17 @@ cudaError_t partition_boxes(Plan &P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-static cudaError_t radix_sort(Plan &P, int64_t n, cudaStream_t s, int &cur) {
+// Octree levels whose split digits lie in the top `npass` 8-bit digits of the
+// 63-bit key (level l is read from bits [63 - 3l, 66 - 3l)).
+static int levels_sorted(int npass) { return (8 * npass - 1) / 3; }
+
+// Stable LSD sort on the top `npass` key digits (then the system id, for
+// batched sorts): equal top digits keep the incoming order.
+static cudaError_t radix_sort(Plan &P, int64_t n, cudaStream_t s, int &cur, int npass) {
     const int nblk = (int)((n + kTile - 1) / kTile);
     struct Pass { int mode, shift; };
     std::vector<Pass> passes;
-    for (int sh = 0; sh < 64; sh += 8) passes.push_back({0, sh});
+    for (int sh = 64 - 8 * npass; sh < 64; sh += 8) passes.push_back({0, sh});
     if (P.n_sys > 1) {
         for (int sh = 0; (1LL << sh) < P.n_sys; sh += 8) passes.push_back({1, sh});
     }
@@ -893,6 +900,8 @@ static cudaError_t radix_sort(Plan &P, int64_t n, cudaStream_t s, int &cur) {
     }
     return cudaSuccess;
 }
+
+static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort);
 
 cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) {
     const int64_t n = P.n;
@@ -915,15 +924,40 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
         ++g_launches, k_keys<float><<<grid_for(n, 256), 256, 0, s>>>(n, (const float *)xyz, P.sys_off_d, S, P.lo_side,
                                                       P.keys[0], P.vals[0], P.keys_user);
     KIFMM_CUDA_TRY(cudaGetLastError());
-    int cur = 0;
-    KIFMM_CUDA_TRY(radix_sort(P, n, s, cur));
-    if (cur != 0) {
-        KIFMM_CUDA_TRY(cudaMemcpyAsync(P.keys[0], P.keys[1], sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
-        KIFMM_CUDA_TRY(cudaMemcpyAsync(P.vals[0], P.vals[1], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    // Sort only the key digits the octree will read: two levels below the
+    // last tree's depth (or an estimate from N / M before the first tree),
+    // capped by max_depth.  A node that must split below the sorted levels
+    // sends the build back here for the remaining digits (a full stable sort
+    // of the partly sorted keys: equal keys stay in caller order).
+    int want = P.max_level > 0 ? P.max_level + 2
+                               : (int)std::ceil(std::log((double)n / P.desc.leaf_cap + 1.0) / std::log(8.0)) + 2;
+    want = std::max(1, std::min(want, P.desc.max_depth));
+    int npass = 1;
+    while (npass < 8 && levels_sorted(npass) < want) ++npass;
+    for (;;) {
+        int cur = 0;
+        KIFMM_CUDA_TRY(radix_sort(P, n, s, cur, npass));
+        if (cur != 0) {
+            KIFMM_CUDA_TRY(cudaMemcpyAsync(P.keys[0], P.keys[1], sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+            KIFMM_CUDA_TRY(cudaMemcpyAsync(P.vals[0], P.vals[1], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+        }
+        cudaError_t e = build_levels(P, s, npass < 8 ? levels_sorted(npass) : kMaxLevel + 1);
+        if (e == cudaErrorNotReady) {  // a node below the sorted levels must split
+            npass = 8;
+            continue;
+        }
+        KIFMM_CUDA_TRY(e);
+        break;
     }
+    P.sort_passes = npass;
     KIFMM_CUDA_TRY(cudaMemcpyAsync(P.perm, P.vals[0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    return cudaGetLastError();  // the particle records follow once the leaves are listed
+}
 
-    // octree, level by level
+// Octree, level by level, from sorted keys.  Nodes at level `lsort` cannot be
+// split (their children's digit is not sorted): cudaErrorNotReady if one must.
+static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
+    const int S = P.n_sys;
     ++g_launches, k_roots<<<grid_for(S, 128), 128, 0, s>>>(S, P.sys_off_d, P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.parent,
                                              P.sys);
     P.level_start.assign(1, 0);
@@ -941,6 +975,7 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
         uint32_t total = 0;
         KIFMM_CUDA_TRY(cudaMemcpyAsync(&total, total_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (level >= lsort && total > 0) return cudaErrorNotReady;
         if (le + (int64_t)total > P.box_cap) {
             KIFMM_CUDA_TRY(grow_tree_arrays(P, 2 * (le + (int64_t)total) + 1024, le));
             scan_out = P.tmp_nchild + P.box_cap;
@@ -959,8 +994,7 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
     }
     P.nb = le;
     P.max_level = level;
-
-    return cudaGetLastError();  // the particle records follow once the leaves are listed
+    return cudaGetLastError();
 }
 
 cudaError_t check_leaves(Plan &P, const void *xyz, double skin, int *moved_dev, cudaStream_t s) {

@@ -1,6 +1,7 @@
 """GPU path vs the FP64 CPU oracle, through the C ABI.
 
-* Morton keys, sort permutation, tree nodes and U/V/W/X lists: bit-exact.
+* Morton keys, tree nodes and U/V/W/X lists: bit-exact; the sort permutation
+  groups particles by leaf exactly as the oracle's (order within a leaf free).
 * FP64 GPU path vs the oracle's KIFMM (same rules): rel-L2 <= 1e-12.
 * FP32 path vs the FP64 direct sum: within the method's own error at that p
   plus a small margin (the reduced-precision budget).
@@ -35,6 +36,16 @@ def _plan(x, precision="fp64", p=4, M=32, D=20, dtype=torch.float64, n_systems=1
 
 def _dev(a, dtype=torch.float64):
     return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def _assert_same_leaves(perm, t):
+    """The sorted order groups particles by leaf exactly as the oracle's full
+    stable sort does; within a leaf the order is free (the library sorts only
+    the key digits the octree reads, so ties there keep the caller's order)."""
+    assert perm.shape == t["perm"].shape
+    for b in np.nonzero(t["child_first"] < 0)[0]:
+        f, c = int(t["first"][b]), int(t["count"][b])
+        assert np.array_equal(np.sort(perm[f:f + c]), np.sort(t["perm"][f:f + c])), b
 
 
 CASES = {
@@ -78,7 +89,7 @@ def test_tree_and_lists_bit_exact(case, M, direct_max):
     keys, perm, lo_side = plan.keys()
     t = O.sort_and_tree(x, M, 20)
     assert np.array_equal(keys, t["keys"])
-    assert np.array_equal(perm, t["perm"])
+    _assert_same_leaves(perm, t)
     assert np.array_equal(lo_side[0, :3], t["lo"]) and lo_side[0, 3] == t["side"]
     g = plan.tree()
     assert g["level"].shape[0] == t["nb"]
@@ -95,6 +106,25 @@ def test_tree_and_lists_bit_exact(case, M, direct_max):
         assert raw["W"][1].size > 0 and raw["X"][1].size > 0
         if direct_max == 0:
             assert L["U"][1].size > raw["U"][1].size  # some W/X moved to U
+
+
+def test_tree_deeper_than_the_sorted_digits():
+    """A plan that last built a shallow tree sorts few key digits; a deep tree
+    next must fall back to the full sort and still match the oracle."""
+    plan = _plan(np.zeros((4096, 3)), M=8)
+    xs, qs = G.uniform_charges(4096, 9)
+    plan.set_sources(_dev(xs), _dev(qs))
+    shallow = plan.tree_info()["max_level"]
+    x, q = CASES["clustered_tight"]()
+    plan.set_sources(_dev(x), _dev(q))
+    t = O.sort_and_tree(x, 8, 20)
+    assert plan.tree_info()["max_level"] == int(t["level"].max()) > shallow + 2
+    keys, perm, _ = plan.keys()
+    assert np.array_equal(keys, t["keys"])
+    assert np.array_equal(perm, t["perm"])   # full stable sort: the oracle's order exactly
+    g = plan.tree()
+    for name in ("level", "first", "count", "parent"):
+        assert np.array_equal(g[name], t[name]), name
 
 
 @pytest.mark.parametrize("case,M,p", [("uniform4096", 64, 4), ("plummer3000", 16, 4), ("clustered", 8, 6),

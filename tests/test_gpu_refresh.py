@@ -149,7 +149,13 @@ def test_large_motion_rebuilds_like_set_sources():
     assert plan.tree_info() == fresh.tree_info()
     k1, p1, l1 = plan.keys()
     k2, p2, l2 = fresh.keys()
-    assert np.array_equal(k1, k2) and np.array_equal(p1, p2) and np.array_equal(l1, l2)
+    assert np.array_equal(k1, k2) and np.array_equal(l1, l2)
+    # same particles per leaf (the order inside a leaf depends on how many key
+    # digits each plan sorted)
+    g = plan.tree()
+    isleaf = ~np.isin(np.arange(len(g["level"])), g["parent"])
+    for f, c in zip(g["first"][isleaf], g["count"][isleaf]):
+        assert np.array_equal(np.sort(p1[f:f + c]), np.sort(p2[f:f + c]))
     assert O.rel_l2(pot_r.cpu().numpy(), pot_f.cpu().numpy()) <= 1e-14
     assert O.rel_l2(grad_r.cpu().numpy(), grad_f.cpu().numpy()) <= 1e-14
     # and the new tree is the oracle's
