@@ -278,6 +278,8 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {&P.gemm_part, esz * 8 * kSplitTargets * (size_t)(P.ns + 1)},
         {(void **)&P.sys_off_d, sizeof(int64_t) * (P.sys_cap + 1)},
         {(void **)&P.lo_side, sizeof(double) * 4 * P.sys_cap},
+        {(void **)&P.key_scale, sizeof(double) * P.sys_cap},
+        {(void **)&P.out_scale, sizeof(double) * 2 * P.sys_cap},
         {(void **)&P.bbox_ord, sizeof(unsigned long long) * 6 * P.sys_cap},
         {(void **)&P.hist, sizeof(uint32_t) * P.hist_elems},
         {(void **)&P.status, sizeof(int)},

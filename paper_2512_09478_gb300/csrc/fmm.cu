@@ -762,7 +762,7 @@ void leaf_launch(const Plan &P, const LeafCtx &C, const typename Vec4<T>::type *
 // Scatter to caller order with 1/(4 pi), coef and physical units.
 template <typename TO>
 __global__ void k_finalize(int64_t n, const double4 *__restrict__ res, const uint32_t *__restrict__ perm,
-                           const int64_t *__restrict__ off, int S, const double *__restrict__ lo_side, double coef,
+                           const int64_t *__restrict__ off, int S, const double *__restrict__ out_scale,
                            TO *pot, TO *grad) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -772,8 +772,7 @@ __global__ void k_finalize(int64_t n, const double4 *__restrict__ res, const uin
         const int mid = (lo + hi + 1) >> 1;
         if (off[mid] <= (int64_t)j) lo = mid; else hi = mid - 1;
     }
-    const double side = lo_side[lo * 4 + 3];
-    const double c1 = coef * kInv4Pi / side, c2 = c1 / side;
+    const double c1 = out_scale[2 * lo], c2 = out_scale[2 * lo + 1];  // coef / (4 pi side), / side^2
     const double4 r = res[i];
     if (pot) pot[j] = (TO)(c1 * r.x);
     if (grad) {
@@ -998,11 +997,11 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     if (pot || grad) {
         if (P.io_f64)
             ++g_launches, k_finalize<double><<<grid_for(P.n, 256), 256, 0, s>>>(
-                              P.n, res, P.perm, P.sys_off_d, P.n_sys, P.lo_side, P.coef, (double *)pot,
+                              P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, (double *)pot,
                               (double *)grad);
         else
             ++g_launches, k_finalize<float><<<grid_for(P.n, 256), 256, 0, s>>>(
-                              P.n, res, P.perm, P.sys_off_d, P.n_sys, P.lo_side, P.coef, (float *)pot,
+                              P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, (float *)pot,
                               (float *)grad);
     }
     if (energy) {
@@ -1025,7 +1024,7 @@ __global__ void k_gather_w(int64_t n, const uint32_t *__restrict__ perm, const T
 // dq = c1 psi, dx = w grad + c1 / side * q grad(psi), c1 = coef / (4 pi side).
 template <typename TO, typename T>
 __global__ void k_finalize_adj(int64_t n, const double4 *__restrict__ res, const uint32_t *__restrict__ perm,
-                               const int64_t *__restrict__ off, int S, const double *__restrict__ lo_side, double coef,
+                               const int64_t *__restrict__ off, int S, const double *__restrict__ out_scale,
                                const typename Vec4<T>::type *__restrict__ pts, const TO *__restrict__ w,
                                const TO *__restrict__ grad, TO *dq, TO *dx) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1036,8 +1035,7 @@ __global__ void k_finalize_adj(int64_t n, const double4 *__restrict__ res, const
         const int mid = (lo + hi + 1) >> 1;
         if (off[mid] <= (int64_t)j) lo = mid; else hi = mid - 1;
     }
-    const double side = lo_side[lo * 4 + 3];
-    const double c1 = coef * kInv4Pi / side, c2 = c1 / side;
+    const double c1 = out_scale[2 * lo], c2 = out_scale[2 * lo + 1];  // coef / (4 pi side), / side^2
     const double4 r = res[i];
     const double q = (double)pts[i].w;
     if (dq) dq[j] = (TO)(c1 * r.x);
@@ -1099,11 +1097,11 @@ cudaError_t backward_t(Plan &P, const void *w_user, const void *grad_user, void 
     leaf_launch<T>(P, C, pts, surf, W, res, s);
     if (P.io_f64)
         ++g_launches, k_finalize_adj<double, T><<<grid_for(P.n, 256), 256, 0, s>>>(
-                          P.n, res, P.perm, P.sys_off_d, P.n_sys, P.lo_side, P.coef, pts, (const double *)w_user,
+                          P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, pts, (const double *)w_user,
                           (const double *)grad_user, (double *)dq, (double *)dx);
     else
         ++g_launches, k_finalize_adj<float, T><<<grid_for(P.n, 256), 256, 0, s>>>(
-                          P.n, res, P.perm, P.sys_off_d, P.n_sys, P.lo_side, P.coef, pts, (const float *)w_user,
+                          P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, pts, (const float *)w_user,
                           (const float *)grad_user, (float *)dq, (float *)dx);
     return cudaGetLastError();
 }

@@ -108,6 +108,8 @@ struct Plan {
     double *near_pot = nullptr;     // scratch accumulators (FP64 final sums)
     int64_t *sys_off_d = nullptr;   // [S+1]
     double *lo_side = nullptr;      // [S][4]
+    double *key_scale = nullptr;    // [S] 2^21 / side
+    double *out_scale = nullptr;    // [S][2] coef / (4 pi side), coef / (4 pi side^2)
     unsigned long long *bbox_ord = nullptr;  // [S][6]
     uint32_t *scan_tmp = nullptr;   // scan scratch
     size_t scan_tmp_elems = 0;

@@ -103,7 +103,8 @@ __global__ void k_bbox(int64_t n, const T *__restrict__ xyz, const T *__restrict
 }
 
 // Root cube per system: lo = per-axis minimum, side = largest extent (1 if 0).
-__global__ void k_bbox_final(const unsigned long long *bb, int S, double *lo_side) {
+__global__ void k_bbox_final(const unsigned long long *bb, int S, double *lo_side, double *key_scale, double coef,
+                             double *out_scale) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     double side = 0.0;
@@ -112,7 +113,13 @@ __global__ void k_bbox_final(const unsigned long long *bb, int S, double *lo_sid
         lo_side[s * 4 + d] = lo;
         side = fmax(side, hi - lo);
     }
-    lo_side[s * 4 + 3] = (side > 0.0) ? side : 1.0;
+    side = (side > 0.0) ? side : 1.0;
+    lo_side[s * 4 + 3] = side;
+    key_scale[s] = __ddiv_rn(2097152.0, side);  // once per system: FP64 division is slow
+    // output scales of the unit-root results: potential coef / (4 pi side), gradient / side^2
+    const double c1 = coef * kInv4Pi / side;
+    out_scale[2 * s] = c1;
+    out_scale[2 * s + 1] = c1 / side;
 }
 
 __device__ __forceinline__ uint64_t spread3(uint64_t x) {
@@ -126,16 +133,15 @@ __device__ __forceinline__ uint64_t spread3(uint64_t x) {
 }
 
 // 21-bit quantisation in FP64 without contraction: k = min(floor((x-lo)*s), 2^21-1),
-// s = 2^21 / side; bits interleaved x-highest.
+// s = 2^21 / side (key_scale, correctly rounded); bits interleaved x-highest.
 template <typename T>
 __global__ void k_keys(int64_t n, const T *__restrict__ xyz, const int64_t *__restrict__ off, int S,
-                       const double *__restrict__ lo_side, uint64_t *keys, uint32_t *vals,
-                       uint64_t *keys_user) {
+                       const double *__restrict__ lo_side, const double *__restrict__ key_scale, uint64_t *keys,
+                       uint32_t *vals, uint64_t *keys_user) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int s = find_sys(off, S, i);
-    const double side = lo_side[s * 4 + 3];
-    const double sc = __ddiv_rn(2097152.0, side);
+    const double sc = key_scale[s];
     uint64_t k[3];
     for (int d = 0; d < 3; ++d) {
         double t = __dmul_rn(__dsub_rn((double)xyz[3 * i + d], lo_side[s * 4 + d]), sc);
@@ -435,7 +441,7 @@ __global__ void k_gather(int64_t n_leaves, const int32_t *__restrict__ leaves, c
 }
 
 // Tree reuse test: one warp per leaf; every particle's leaf-relative offset
-// (the FP64 formula of k_gather, in units of the root side) must lie within
+// (in FP64, in units of the root side) must lie within
 // the leaf's half-width plus `margin` of its centre on every axis; otherwise
 // (or for a non-finite coordinate) *moved is set.
 template <typename TI>
@@ -449,7 +455,7 @@ __global__ void k_leaf_check(int64_t n_leaves, const int32_t *__restrict__ leave
     if (li >= n_leaves) return;
     const int b = leaves[li];
     const int s = sys[b];
-    const double side = lo_side[s * 4 + 3];
+    const double inv_side = 1.0 / lo_side[s * 4 + 3];  // a tolerance test: no exact quotient needed
     const double lo[3] = {lo_side[s * 4], lo_side[s * 4 + 1], lo_side[s * 4 + 2]};
     const double w = ldexp(1.0, -lvl[b]);
     const double c[3] = {(cx[b] + 0.5) * w, (cy[b] + 0.5) * w, (cz[b] + 0.5) * w};
@@ -458,7 +464,7 @@ __global__ void k_leaf_check(int64_t n_leaves, const int32_t *__restrict__ leave
     for (int k = threadIdx.x & 31; k < cnt[b]; k += 32) {
         const uint32_t j = perm[first[b] + k];
         for (int d = 0; d < 3; ++d) {
-            const double r = ((double)xyz[3 * j + d] - lo[d]) / side - c[d];
+            const double r = ((double)xyz[3 * j + d] - lo[d]) * inv_side - c[d];
             bad = bad || !(fabs(r) <= lim);  // also catches NaN
         }
     }
@@ -916,13 +922,14 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
     else
         ++g_launches, k_bbox<float><<<nt, kBlock, 0, s>>>(n, (const float *)xyz, (const float *)q, P.sys_off_d, S,
                                             P.bbox_ord, P.status);
-    ++g_launches, k_bbox_final<<<grid_for(S, 128), 128, 0, s>>>(P.bbox_ord, S, P.lo_side);
+    ++g_launches, k_bbox_final<<<grid_for(S, 128), 128, 0, s>>>(P.bbox_ord, S, P.lo_side, P.key_scale, P.coef,
+                                                                P.out_scale);
     if (P.io_f64)
         ++g_launches, k_keys<double><<<grid_for(n, 256), 256, 0, s>>>(n, (const double *)xyz, P.sys_off_d, S, P.lo_side,
-                                                       P.keys[0], P.vals[0], P.keys_user);
+                                                       P.key_scale, P.keys[0], P.vals[0], P.keys_user);
     else
         ++g_launches, k_keys<float><<<grid_for(n, 256), 256, 0, s>>>(n, (const float *)xyz, P.sys_off_d, S, P.lo_side,
-                                                      P.keys[0], P.vals[0], P.keys_user);
+                                                      P.key_scale, P.keys[0], P.vals[0], P.keys_user);
     KIFMM_CUDA_TRY(cudaGetLastError());
     // Sort only the key digits the octree will read: two levels below the
     // last tree's depth (or an estimate from N / M before the first tree),
