@@ -359,8 +359,9 @@ static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cu
     API_CUDA(partition_boxes(P, s));
     API_CUDA(gather_particles(P, xyz, q, s));
     if (P.desc.precision == KIFMM_MIXED_FP16) API_CUDA(m2l_tensor_tiles(P, s));
-    // energy chunks (sorted order never mixes systems)
-    {
+    // energy chunks (sorted order never mixes systems; they depend on the
+    // system offsets only)
+    if (P.energy_off_h != P.sys_off_h) {
         std::vector<int64_t> ch;
         std::vector<int32_t> start(n_systems + 1, 0);
         for (int sy = 0; sy < n_systems; ++sy) {
@@ -380,6 +381,7 @@ static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cu
         API_CUDA(cudaMemcpyAsync(P.energy_chunks, ch.data(), sizeof(int64_t) * ch.size(), cudaMemcpyHostToDevice, s));
         API_CUDA(cudaMemcpyAsync(P.energy_chunk_start, start.data(), sizeof(int32_t) * start.size(),
                                  cudaMemcpyHostToDevice, s));
+        P.energy_off_h = P.sys_off_h;
     }
     int st = 0;
     API_CUDA(cudaMemcpyAsync(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -127,6 +127,10 @@ struct Plan {
     int n_sys = 0, max_level = 0;
     int sort_passes = 8;  // 8-bit key digits the last build sorted (from the top)
     std::vector<int64_t> sys_off_h;
+    // Offsets already on the device and those the energy chunks were built
+    // for: unchanged systems skip both uploads (a pageable copy would stall
+    // the stream).
+    std::vector<int64_t> sys_off_dev_h, energy_off_h;
 
     // ---- lists ----
     int32_t *coll = nullptr;         // [nb][27]

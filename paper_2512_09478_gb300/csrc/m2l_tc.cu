@@ -451,6 +451,11 @@ struct TcState {
     std::vector<int4> tiles_h;
     size_t smem = 0;
     int n_in = 0, n_out = 0, ld = 0;  // operator inputs, outputs (mean excluded), stored columns
+    int4 *tiles_pin = nullptr;        // pinned staging of tiles_h (a pageable copy stalls the stream)
+    size_t tiles_pin_cap = 0;
+    ~TcState() {
+        if (tiles_pin) cudaFreeHost(tiles_pin);
+    }
 };
 
 static TcState &tc_state(Plan &P) {
@@ -526,15 +531,25 @@ cudaError_t m2l_tensor_tiles(Plan &P, cudaStream_t s) {
         S.tiles_cap = (int64_t)S.tiles_h.size() + 64;
         KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.tiles, sizeof(int4) * S.tiles_cap));
     }
+    if (S.tiles_h.size() > S.tiles_pin_cap) {
+        if (S.tiles_pin) cudaFreeHost(S.tiles_pin);
+        S.tiles_pin = nullptr;
+        S.tiles_pin_cap = 0;
+        KIFMM_CUDA_TRY(cudaMallocHost((void **)&S.tiles_pin, sizeof(int4) * (S.tiles_h.size() + 64)));
+        S.tiles_pin_cap = S.tiles_h.size() + 64;
+    }
+    std::copy(S.tiles_h.begin(), S.tiles_h.end(), S.tiles_pin);
     if (!S.tiles_h.empty())
-        KIFMM_CUDA_TRY(cudaMemcpyAsync(S.tiles, S.tiles_h.data(), sizeof(int4) * S.tiles_h.size(),
+        KIFMM_CUDA_TRY(cudaMemcpyAsync(S.tiles, S.tiles_pin, sizeof(int4) * S.tiles_h.size(),
                                        cudaMemcpyHostToDevice, s));
     if (P.nb > S.u_cap) {
         S.u_cap = P.list_cap;
         KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.uh, sizeof(__half) * S.u_cap * S.kp));
         KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.ul, sizeof(__half) * S.u_cap * S.kp));
     }
-    return cudaGetLastError();  // the tile list is a member: the staged copy needs no wait
+    // pinned: the copy runs asynchronously; set_sources synchronises before it
+    // returns, so the staging buffer is free again by the next call
+    return cudaGetLastError();
 }
 
 cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {

@@ -912,8 +912,11 @@ static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort);
 cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) {
     const int64_t n = P.n;
     const int S = P.n_sys;
-    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.sys_off_d, P.sys_off_h.data(), sizeof(int64_t) * (S + 1),
-                                   cudaMemcpyHostToDevice, s));
+    if (P.sys_off_dev_h != P.sys_off_h) {
+        KIFMM_CUDA_TRY(cudaMemcpyAsync(P.sys_off_d, P.sys_off_h.data(), sizeof(int64_t) * (S + 1),
+                                       cudaMemcpyHostToDevice, s));
+        P.sys_off_dev_h = P.sys_off_h;
+    }
     ++g_launches, k_bbox_init<double><<<grid_for(S * 6, 128), 128, 0, s>>>(P.bbox_ord, S);
     const unsigned nt = grid_for(n, kTile);
     if (P.io_f64)

@@ -212,3 +212,23 @@ def test_refresh_errors():
     with pytest.raises(KifmmError) as e:
         plan.evaluate()
     assert e.value.code == 6                      # and the plan holds no sources
+
+
+def test_changed_system_offsets_are_uploaded():
+    """A plan reuses the uploaded system offsets (and energy chunks) while they
+    are unchanged; new offsets must reach the device: the same particles split
+    differently give each system's energy as a fresh plan does."""
+    from paper_2512_09478_gb300 import Plan
+    x, q = G.uniform_charges(4000, 91)
+    mk = lambda: Plan(p=4, leaf_cap=32, max_depth=20, precision="fp64", n_max=len(x), n_systems_max=3,
+                      dtype=torch.float64)
+    plan = mk()
+    for off in ([0, 1500, 4000], [0, 1500, 4000], [0, 2500, 4000], [0, 1000, 3000, 4000]):
+        plan.set_sources(_dev(x), _dev(q), sys_offsets=off)
+        pot, _, energy = plan.evaluate(want_energy=True)
+        fresh = mk()
+        fresh.set_sources(_dev(x), _dev(q), sys_offsets=off)
+        pot_f, _, energy_f = fresh.evaluate(want_energy=True)
+        assert energy.shape[0] == len(off) - 1
+        assert O.rel_l2(energy.cpu().numpy(), energy_f.cpu().numpy()) <= 1e-14, off
+        assert O.rel_l2(pot.cpu().numpy(), pot_f.cpu().numpy()) <= 1e-14, off
