@@ -127,8 +127,11 @@ kifmm_status kifmm_plan_destroy(kifmm_plan *plan);
 
 /*
  * Load particles and build the tree (Sec. 2.2, first and third steps): per
- * system bounding cube, 63-bit Morton keys, stable radix sort, adaptive
- * octree (split while count > leaf_cap and level < max_depth), U/V/W/X lists.
+ * system bounding cube, 63-bit Morton keys, stable radix sort of the key
+ * digits the octree reads (two levels below the previous tree's depth, all
+ * digits if the tree turns out deeper), adaptive octree (split while
+ * count > leaf_cap and level < max_depth), U/V/W/X lists.  Particles come out
+ * grouped by leaf in Morton order; within a leaf their order is unspecified.
  * n_systems: number of independent systems (1 <= n_systems <= n_systems_max).
  * sys_offsets (host): n_systems + 1 ascending int64 offsets, sys_offsets[0] = 0;
  *   system s owns particles [sys_offsets[s], sys_offsets[s+1]), at least one.
@@ -348,7 +351,8 @@ typedef struct {
 kifmm_status kifmm_tree_info(kifmm_plan *plan, kifmm_tree_info_t *info);
 
 /* keys (host, [N] uint64): Morton keys in the caller's order;
- * perm (host, [N] int64): perm[i] = caller index of the i-th sorted particle;
+ * perm (host, [N] int64): perm[i] = caller index of the i-th sorted particle
+ *   (grouped by leaf; the order within a leaf is unspecified);
  * lo_side (host, [n_systems, 4] double): root cube lo xyz and side. */
 kifmm_status kifmm_copy_keys(kifmm_plan *plan, uint64_t *keys, int64_t *perm, double *lo_side);
 

@@ -90,3 +90,39 @@ def test_compressed_m2l_argument_rules():
             Plan(p=6, leaf_cap=32, precision=prec, n_max=100,
                  dtype=torch.float64 if prec == "fp64" else torch.float32, m2l_eps=eps)
         assert e.value.code == 1
+
+
+def test_compressed_plan_with_systems_refresh_and_backward():
+    """The compressed M2L composes with the rest of the plan: two systems,
+    a kept tree after a small motion (refresh_sources), and the adjoint (which
+    keeps the dense transposed operators, so dq differs from the dense plan's by
+    the compression's own size only)."""
+    from paper_2512_09478_gb300 import Plan
+    x1, q1 = G.uniform_charges(2000, 601)
+    x2, q2 = G.uniform_charges(3000, 602)
+    x = np.concatenate([x1, x2 + 3.0])
+    q = np.concatenate([q1, q2])
+    off = [0, 2000, 5000]
+    dev = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    plans = {}
+    for eps in (0.0, 1e-5):
+        plan = Plan(p=6, leaf_cap=32, max_depth=20, precision="mixed_fp16", n_max=len(x), n_systems_max=2,
+                    dtype=torch.float32, m2l_eps=eps)
+        plan.set_sources(dev(x), dev(q), sys_offsets=off)
+        assert plan.refresh_sources(dev(x + 1e-9), dev(q)) is True
+        pot, grad, energy = plan.evaluate(want_energy=True)
+        w = torch.linspace(-1.0, 1.0, len(x), device="cuda", dtype=torch.float32)
+        dq, dx = plan.backward(w, grad)
+        torch.cuda.synchronize()
+        assert plan.device_status() == 0
+        plans[eps] = [t.double().cpu().numpy() for t in (pot, grad, energy, dq, dx)]
+    # each system against its own direct sum
+    pot_c = plans[1e-5][0]
+    for k in range(2):
+        a, b = off[k], off[k + 1]
+        xs = (x[a:b] + 1e-9).astype(np.float32).astype(np.float64)
+        pd, _ = O.direct(xs, q[a:b])
+        assert O.rel_l2(pot_c[a:b], pd) < 1e-5
+    # compressed vs dense: within the compression's effect at eps = 1e-5
+    for i, name in enumerate(("pot", "grad", "energy", "dq", "dx")):
+        assert O.rel_l2(plans[1e-5][i], plans[0.0][i]) < 1e-4, name
