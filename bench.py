@@ -59,10 +59,10 @@ WORKLOADS["c2"]["compare"] = "fp32"
 # captured (sha256); otherwise the roofline's traffic is null.
 TRAFFIC = {
     ("dem-coulomb-rsa-1M", "m2l"): ("paper_2512_09478_gb300/csrc/m2l_tc.cu",
-                                    "a90c6bca85e6aad59a733c14f5be4f9ecf2083693c83d22cd213636d53eec7ab", 119.92e6),
+                                    "fc2ef0192df1450006b0109cfdf28cc76494914810b024da3834043ca1fe2701", 119.80e6),
     # the leaf stage: all tile variants of one evaluate together
     ("dem-coulomb-rsa-1M", "p2p"): ("paper_2512_09478_gb300/csrc/fmm.cu",
-                                    "c537ce5831240dece0ac0da6f49b4839b7c7756a64dae03a8879d939117cef64", 67.97e6),
+                                    "c537ce5831240dece0ac0da6f49b4839b7c7756a64dae03a8879d939117cef64", 68.06e6),
 }
 
 
