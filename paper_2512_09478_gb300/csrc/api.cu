@@ -284,6 +284,8 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {(void **)&P.hist, sizeof(uint32_t) * P.hist_elems},
         {(void **)&P.status, sizeof(int)},
         {(void **)&P.moved, sizeof(int)},
+        {(void **)&P.spec_buf, sizeof(int64_t) * 32},
+        {(void **)&P.spec_fail, sizeof(int)},
         {(void **)&P.part_counts, sizeof(uint32_t) * 4 * 256},
         {(void **)&P.list_totals, sizeof(unsigned long long) * 4},
         {(void **)&P.energy_chunk_start, sizeof(int32_t) * (P.sys_cap + 1)},

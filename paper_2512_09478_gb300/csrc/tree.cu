@@ -338,13 +338,24 @@ __global__ void k_roots(int S, const int64_t *off, int32_t *lvl, int32_t *cx, in
 // non-empty octants if it splits (count > M and level < max depth).
 // One warp per node; lanes 0..7 search in parallel for the end of octant o
 // (first index in the node's range whose digit exceeds o).
-__global__ void k_split(int64_t ls, int64_t le, int level, int leaf_cap, int max_depth,
-                        const uint64_t *__restrict__ keys, const int32_t *__restrict__ first,
+// Nodes [ls, le) of one level, or, with `range`, the device-held range of a
+// level built without a host round trip; m_ub bounds the node count (the
+// grid covers m_ub warps; nodes past le report no children).
+__global__ void k_split(int64_t ls, int64_t le, const int64_t *range, int64_t m_ub, int level, int leaf_cap,
+                        int max_depth, const uint64_t *__restrict__ keys, const int32_t *__restrict__ first,
                         const int32_t *__restrict__ cnt, uint32_t *nchild_tmp, int32_t *rng) {
-    const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (range) {
+        ls = range[0];
+        le = range[1];
+    }
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (b >= le) return;
-    const int64_t j = b - ls;
+    if (j >= m_ub) return;
+    const int64_t b = ls + j;
+    if (b >= le) {
+        if (lane == 0) nchild_tmp[j] = 0u;
+        return;
+    }
     const bool split = cnt[b] > leaf_cap && level < max_depth;
     int64_t end = 0;
     const int64_t lo0 = first[b], hi0 = lo0 + cnt[b];
@@ -367,14 +378,19 @@ __global__ void k_split(int64_t ls, int64_t le, int level, int leaf_cap, int max
     if (lane == 0) nchild_tmp[j] = split ? (uint32_t)__popc(nonempty) : 0u;
 }
 
-__global__ void k_emit(int64_t ls, int64_t le, const uint32_t *__restrict__ nchild_tmp,
-                       const uint32_t *__restrict__ nchild_scan, const int32_t *__restrict__ rng,
-                       int32_t *lvl, int32_t *cx, int32_t *cy, int32_t *cz, int32_t *first, int32_t *cnt,
-                       int32_t *parent, int32_t *child_first, int32_t *nchild, int32_t *sys, int64_t cap,
-                       int *status) {
-    int64_t b = ls + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_emit(int64_t ls, int64_t le, const int64_t *range, int64_t m_ub,
+                       const uint32_t *__restrict__ nchild_tmp, const uint32_t *__restrict__ nchild_scan,
+                       const int32_t *__restrict__ rng, int32_t *lvl, int32_t *cx, int32_t *cy, int32_t *cz,
+                       int32_t *first, int32_t *cnt, int32_t *parent, int32_t *child_first, int32_t *nchild,
+                       int32_t *sys, int64_t cap, int *status) {
+    if (range) {
+        ls = range[0];
+        le = range[1];
+    }
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m_ub) return;
+    const int64_t b = ls + j;
     if (b >= le) return;
-    const int64_t j = b - ls;
     const uint32_t nc = nchild_tmp[j];
     nchild[b] = (int32_t)nc;
     if (nc == 0) {
@@ -400,6 +416,30 @@ __global__ void k_emit(int64_t ls, int64_t le, const uint32_t *__restrict__ nchi
         cnt[ch] = c;
         parent[ch] = (int32_t)b;
         sys[ch] = sys[b];
+    }
+}
+
+// Device-side level bookkeeping of the speculative build: the next level is
+// [le, le + total); its end goes to level_start[slot]; a count above m_ub_next
+// (the grid the host launched for it) flags the speculation as failed.
+__global__ void k_spec_init(int64_t *range, int64_t *level_start, int S, int *fail) {
+    if (threadIdx.x == 0) {
+        range[0] = 0;
+        range[1] = S;
+        level_start[0] = 0;
+        level_start[1] = S;
+        *fail = 0;
+    }
+}
+
+__global__ void k_next_range(int64_t *range, const uint32_t *__restrict__ total, int64_t *level_start, int slot,
+                             int64_t m_ub_next, int *fail) {
+    if (threadIdx.x == 0) {
+        const int64_t ls = range[1], le = range[1] + (int64_t)*total;
+        range[0] = ls;
+        range[1] = le;
+        level_start[slot] = le;
+        if (le - ls > m_ub_next) *fail = 1;
     }
 }
 
@@ -966,19 +1006,91 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
 
 // Octree, level by level, from sorted keys.  Nodes at level `lsort` cannot be
 // split (their children's digit is not sorted): cudaErrorNotReady if one must.
+//
+// Each level needs its node count on the host (grid sizes, capacity, the end
+// of the tree), i.e. a stream synchronisation per level.  When the previous
+// tree's level sizes are known, the levels it had are first built without
+// them: device-held ranges, grids sized for twice the previous count, and one
+// synchronisation at the end that checks every count against its grid (on a
+// miss the whole build is redone level by level).
 static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
     const int S = P.n_sys;
-    ++g_launches, k_roots<<<grid_for(S, 128), 128, 0, s>>>(S, P.sys_off_d, P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.parent,
-                                             P.sys);
-    P.level_start.assign(1, 0);
-    P.level_start.push_back(S);
+    const std::vector<int64_t> prev = P.level_start;  // the last build's level boundaries
+    uint32_t *total_dev = P.scan_tmp + P.scan_tmp_elems - 1;
+    const int lspec = std::min((int)prev.size() - 2, lsort);
+    std::vector<int64_t> m_ub;
+    if (lspec >= 2 && prev[1] == S) {
+        int64_t need = S;
+        for (int l = 0; l < lspec; ++l) {
+            m_ub.push_back(l == 0 ? S : 2 * (prev[l + 1] - prev[l]) + 64);
+            need += 8 * m_ub.back();
+        }
+        if (need > P.box_cap) {
+            KIFMM_CUDA_TRY(grow_tree_arrays(P, need + 1024, 0));
+            total_dev = P.scan_tmp + P.scan_tmp_elems - 1;
+        }
+    }
+    bool spec_done = false;
     int64_t ls = 0, le = S;
     int level = 0;
-    uint32_t *total_dev = P.scan_tmp + P.scan_tmp_elems - 1;
+    if (!m_ub.empty()) {
+        ++g_launches, k_roots<<<grid_for(S, 128), 128, 0, s>>>(S, P.sys_off_d, P.lvl, P.cx, P.cy, P.cz, P.first,
+                                                                P.cnt, P.parent, P.sys);
+        int64_t *range = P.spec_buf, *lsd = P.spec_buf + 2;
+        ++g_launches, k_spec_init<<<1, 32, 0, s>>>(range, lsd, S, P.spec_fail);
+        uint32_t *scan_out = P.tmp_nchild + P.box_cap;
+        for (int l = 0; l < lspec; ++l) {
+            const int64_t mu = m_ub[l];
+            ++g_launches, k_split<<<grid_for(mu, 4), 128, 0, s>>>(0, 0, range, mu, l, P.desc.leaf_cap,
+                                                                  P.desc.max_depth, P.keys[0], P.first, P.cnt,
+                                                                  P.tmp_nchild, P.child_rng);
+            KIFMM_CUDA_TRY(exclusive_scan_u32(P.tmp_nchild, scan_out, mu, total_dev, P.scan_tmp,
+                                              P.scan_tmp_elems - 1, s));
+            ++g_launches, k_emit<<<grid_for(mu, 128), 128, 0, s>>>(0, 0, range, mu, P.tmp_nchild, scan_out,
+                                                                   P.child_rng, P.lvl, P.cx, P.cy, P.cz, P.first,
+                                                                   P.cnt, P.parent, P.child_first, P.nchild, P.sys,
+                                                                   P.box_cap, P.status);
+            const int64_t next = (l + 1 < lspec) ? m_ub[l + 1] : INT64_MAX;
+            ++g_launches, k_next_range<<<1, 32, 0, s>>>(range, total_dev, lsd, l + 2, next, P.spec_fail);
+        }
+        KIFMM_CUDA_TRY(cudaGetLastError());
+        std::vector<int64_t> lsh(lspec + 2);
+        int fail = 0;
+        KIFMM_CUDA_TRY(cudaMemcpyAsync(lsh.data(), lsd, sizeof(int64_t) * lsh.size(), cudaMemcpyDeviceToHost, s));
+        KIFMM_CUDA_TRY(cudaMemcpyAsync(&fail, P.spec_fail, sizeof(int), cudaMemcpyDeviceToHost, s));
+        KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!fail) {
+            // keep the non-empty levels; an empty one ends the tree
+            int last = 0;
+            while (last + 1 <= lspec && lsh[last + 2] > lsh[last + 1]) ++last;
+            P.level_start.assign(lsh.begin(), lsh.begin() + last + 2);
+            level = last;
+            ls = lsh[last];
+            le = lsh[last + 1];
+            spec_done = (last < lspec);  // a level below lspec produced no children
+            if (spec_done) {
+                P.nb = le;
+                P.max_level = level;
+                return cudaGetLastError();
+            }
+        }
+        if (fail) {
+            level = 0;
+            ls = 0;
+            le = S;
+        }
+    }
+    if (m_ub.empty() || level == 0) {
+        ++g_launches, k_roots<<<grid_for(S, 128), 128, 0, s>>>(S, P.sys_off_d, P.lvl, P.cx, P.cy, P.cz, P.first,
+                                                                P.cnt, P.parent, P.sys);
+        P.level_start.assign(1, 0);
+        P.level_start.push_back(S);
+    }
     while (true) {
         const int64_t m = le - ls;
-        ++g_launches, k_split<<<grid_for(m, 4), 128, 0, s>>>(ls, le, level, P.desc.leaf_cap, P.desc.max_depth, P.keys[0],
-                                                 P.first, P.cnt, P.tmp_nchild, P.child_rng);
+        ++g_launches, k_split<<<grid_for(m, 4), 128, 0, s>>>(ls, le, nullptr, m, level, P.desc.leaf_cap,
+                                                             P.desc.max_depth, P.keys[0], P.first, P.cnt,
+                                                             P.tmp_nchild, P.child_rng);
         uint32_t *scan_out = P.tmp_nchild + P.box_cap;
         KIFMM_CUDA_TRY(exclusive_scan_u32(P.tmp_nchild, scan_out, m, total_dev, P.scan_tmp,
                                           P.scan_tmp_elems - 1, s));
@@ -989,12 +1101,14 @@ static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
         if (le + (int64_t)total > P.box_cap) {
             KIFMM_CUDA_TRY(grow_tree_arrays(P, 2 * (le + (int64_t)total) + 1024, le));
             scan_out = P.tmp_nchild + P.box_cap;
+            total_dev = P.scan_tmp + P.scan_tmp_elems - 1;
             KIFMM_CUDA_TRY(exclusive_scan_u32(P.tmp_nchild, scan_out, m, total_dev, P.scan_tmp,
                                               P.scan_tmp_elems - 1, s));
         }
-        ++g_launches, k_emit<<<grid_for(m, 128), 128, 0, s>>>(ls, le, P.tmp_nchild, scan_out, P.child_rng, P.lvl, P.cx, P.cy,
-                                                P.cz, P.first, P.cnt, P.parent, P.child_first, P.nchild, P.sys,
-                                                P.box_cap, P.status);
+        ++g_launches, k_emit<<<grid_for(m, 128), 128, 0, s>>>(ls, le, nullptr, m, P.tmp_nchild, scan_out,
+                                                              P.child_rng, P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt,
+                                                              P.parent, P.child_first, P.nchild, P.sys, P.box_cap,
+                                                              P.status);
         KIFMM_CUDA_TRY(cudaGetLastError());
         if (total == 0) break;
         ls = le;

@@ -127,6 +127,31 @@ def test_tree_deeper_than_the_sorted_digits():
         assert np.array_equal(g[name], t[name]), name
 
 
+def test_tree_rebuilt_across_shapes_on_one_plan():
+    """One plan builds a sequence of trees: the same data again (the levels the
+    last tree had are built from its sizes without host round trips), a deeper
+    tree, a shallower one (it ends inside those levels), a much larger one (its
+    levels outgrow the grids sized from the last tree, so the build is redone
+    level by level).  Every tree matches the oracle's."""
+    rng = np.random.default_rng(77)
+    seq = [G.uniform_charges(4096, 1)[0], G.uniform_charges(4096, 1)[0], CASES["clustered_tight"]()[0],
+           G.uniform_charges(1000, 2)[0], G.uniform_charges(20000, 3)[0], G.plummer(3000, 5)[0],
+           rng.uniform(0, 1, size=(20000, 3))]
+    plan = _plan(np.zeros((20000, 3)), M=16)
+    for x in seq:
+        q = np.ones(len(x))
+        plan.set_sources(_dev(x), _dev(q))
+        t = O.sort_and_tree(x, 16, 20)
+        g = plan.tree()
+        assert g["level"].shape[0] == t["nb"]
+        for name in ("level", "first", "count", "parent"):
+            assert np.array_equal(g[name], t[name]), name
+        assert np.array_equal(g["coord"], t["coord"])
+        _, perm, _ = plan.keys()
+        _assert_same_leaves(perm, t)
+        assert plan.tree_info()["max_level"] == int(t["level"].max())
+
+
 @pytest.mark.parametrize("case,M,p", [("uniform4096", 64, 4), ("plummer3000", 16, 4), ("clustered", 8, 6),
                                       ("plummer3000", 16, 7), ("uniform4096", 64, 8)])
 def test_fp64_matches_oracle(case, M, p):
