@@ -255,6 +255,28 @@ def test_mixed_fp16_tensor_m2l(case, M, p):
     assert e_pm < e_p64 + 4e-6
 
 
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_mixed_fp16_matches_fp32_on_a_deeper_tree(p):
+    """60k points, leaf cap 16 (levels of more than 1024 boxes): the mixed
+    mode's upward and downward check potentials agree with the FP32 SIMT
+    path's to FP32-level accuracy, and so do the outputs."""
+    x, q = G.uniform_charges(60000, 4242)
+    out = {}
+    for prec in ("fp32", "mixed_fp16"):
+        plan = _plan(x, precision=prec, p=p, M=16, dtype=torch.float32)
+        plan.set_sources(_dev(x, torch.float32), _dev(q, torch.float32))
+        pot, grad, _ = plan.evaluate()
+        assert plan.device_status() == 0
+        u, d, _ = plan.expansions()
+        out[prec] = (u, d, pot.double().cpu().numpy(), grad.double().cpu().numpy())
+    tree = plan.tree()
+    assert (np.bincount(tree["level"]) >= 1024).sum() >= 2
+    e = [O.rel_l2(out["mixed_fp16"][i], out["fp32"][i]) for i in range(4)]
+    print("p=%d mixed vs fp32: u %.2e d %.2e pot %.2e grad %.2e" % (p, *e))
+    assert e[0] < 4e-6 and e[1] < 4e-6
+    assert e[2] < 4e-6 and e[3] < 2e-5
+
+
 @pytest.mark.parametrize("prec", ["fp32", "mixed_fp16"])
 def test_reduced_precision_gains_from_higher_order(prec):
     """With the FP32-based modes' regularised pseudo-inverse (pinv_eps 1e-9),
