@@ -516,13 +516,11 @@ __global__ void k_leaf_check(int64_t n_leaves, const int32_t *__restrict__ leave
 // ---------------------------------------------------------------------------
 // One warp per box: lane k < 27 scans the children of the parent's colleague
 // k; every child adjacent to (or equal to) b lands in its own slot.
-__global__ void k_colleagues(int64_t ls, int64_t le, int level, const int32_t *__restrict__ parent,
-                             const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
-                             const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
-                             const int32_t *__restrict__ cz, int32_t *coll) {
-    const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= le) return;
+__device__ __forceinline__ void dev_colleagues(int64_t b, int lane, int level, const int32_t *__restrict__ parent,
+                                               const int32_t *__restrict__ child_first,
+                                               const int32_t *__restrict__ nchild, const int32_t *__restrict__ cx,
+                                               const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
+                                               int32_t *coll) {
     int32_t *cb = coll + b * kColl;
     // cb was set to -1 by a memset of the whole array before the first level
     if (level == 0) {
@@ -543,14 +541,12 @@ __global__ void k_colleagues(int64_t ls, int64_t le, int level, const int32_t *_
 // Coarser-or-equal-level leaves adjacent to b: those of the parent that touch
 // b (in the parent's order), then b's leaf colleagues (in slot order).  One
 // warp per box; ballots keep the order.
-__global__ void k_coarse(int64_t ls, int64_t le, int level, const int32_t *__restrict__ parent,
-                         const int32_t *__restrict__ nchild, const int32_t *__restrict__ lvl,
-                         const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
-                         const int32_t *__restrict__ cz, const int32_t *__restrict__ coll, int32_t *coarse,
-                         int32_t *ncoarse, int *status) {
-    const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= le) return;
+// (coll is written by the colleague pass of the same launch: no read-only path)
+__device__ __forceinline__ void dev_coarse(int64_t b, int lane, int level, const int32_t *__restrict__ parent,
+                                           const int32_t *__restrict__ nchild, const int32_t *__restrict__ lvl,
+                                           const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                                           const int32_t *__restrict__ cz, const int32_t *coll, int32_t *coarse,
+                                           int32_t *ncoarse, int *status) {
     const unsigned below = (1u << lane) - 1u;
     int n = 0;
     int32_t *out = coarse + b * kMaxCoarse;
@@ -619,17 +615,15 @@ __device__ __forceinline__ bool direct_box(const int32_t *nchild, const int32_t 
 // not to b; empty when b itself is a direct-sum leaf, see k_uw).  One warp
 // per box: lane k < 27 takes the parent's colleague k (each child has its
 // own slot); the X list keeps the parent's coarse order through a ballot.
-__global__ void k_vx(int64_t ls, int64_t le, int level, int thr, const int32_t *__restrict__ parent,
-                     const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
-                     const int32_t *__restrict__ cnt,
-                     const int32_t *__restrict__ lvl, const int32_t *__restrict__ cx,
-                     const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
-                     const int32_t *__restrict__ coll, const int32_t *__restrict__ coarse,
-                     const int32_t *__restrict__ ncoarse, int32_t *vdense, int32_t *nv, int32_t *xdense,
-                     int32_t *nx, unsigned long long *totals) {
-    const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= le) return;
+// (coll, coarse and ncoarse are written earlier in the same launch)
+__device__ __forceinline__ void dev_vx(int64_t b, int lane, int level, int thr, const int32_t *__restrict__ parent,
+                                       const int32_t *__restrict__ child_first,
+                                       const int32_t *__restrict__ nchild, const int32_t *__restrict__ cnt,
+                                       const int32_t *__restrict__ lvl, const int32_t *__restrict__ cx,
+                                       const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
+                                       const int32_t *coll, const int32_t *coarse, const int32_t *ncoarse,
+                                       int32_t *vdense, int32_t *nv, int32_t *xdense, int32_t *nx,
+                                       unsigned long long *totals) {
     int32_t *vb = vdense + b * kVSlots;  // preset to -1 by a memset
     int cntv = 0, cntx = 0;
     if (level > 0) {
@@ -1165,6 +1159,28 @@ cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream
     return cudaGetLastError();
 }
 
+// The list passes of one level, one warp per box: its colleagues, then its
+// coarse adjacent leaves (which read its own colleagues), then its V and X
+// lists (which read its own coarse list).  Everything else they read belongs
+// to the previous level, so the three need no grid-wide ordering.
+__global__ void k_lists_level(int64_t ls, int64_t le, int level, int thr, const int32_t *__restrict__ parent,
+                              const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
+                              const int32_t *__restrict__ cnt, const int32_t *__restrict__ lvl,
+                              const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                              const int32_t *__restrict__ cz, int32_t *coll, int32_t *coarse, int32_t *ncoarse,
+                              int32_t *vdense, int32_t *nv, int32_t *xdense, int32_t *nx,
+                              unsigned long long *totals, int *status) {
+    const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= le) return;
+    dev_colleagues(b, lane, level, parent, child_first, nchild, cx, cy, cz, coll);
+    __syncwarp();
+    dev_coarse(b, lane, level, parent, nchild, lvl, cx, cy, cz, coll, coarse, ncoarse, status);
+    __syncwarp();
+    dev_vx(b, lane, level, thr, parent, child_first, nchild, cnt, lvl, cx, cy, cz, coll, coarse, ncoarse, vdense,
+           nv, xdense, nx, totals);
+}
+
 cudaError_t build_lists(Plan &P, cudaStream_t s) {
     const int64_t nb = P.nb;
     KIFMM_CUDA_TRY(cudaMemsetAsync(P.coll, 0xFF, sizeof(int32_t) * kColl * nb, s));
@@ -1173,14 +1189,9 @@ cudaError_t build_lists(Plan &P, cudaStream_t s) {
     for (int l = 0; l <= P.max_level; ++l) {
         const int64_t ls = P.level_start[l], le = P.level_start[l + 1];
         const unsigned g = grid_for(le - ls, 8);  // warp per box, 8 per block
-        ++g_launches, k_colleagues<<<g, 256, 0, s>>>(ls, le, l, P.parent, P.child_first, P.nchild, P.cx, P.cy, P.cz,
-                                                     P.coll);
-        ++g_launches, k_coarse<<<g, 256, 0, s>>>(ls, le, l, P.parent, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll,
-                                                 P.coarse, P.ncoarse, P.status);
-        ++g_launches, k_vx<<<g, 256, 0, s>>>(ls, le, l, P.direct_thr, P.parent, P.child_first, P.nchild, P.cnt,
-                                             P.lvl, P.cx, P.cy, P.cz,
-                                             P.coll, P.coarse, P.ncoarse, P.vdense, P.nv, P.xdense, P.nx,
-                                             P.list_totals);
+        ++g_launches, k_lists_level<<<g, 256, 0, s>>>(ls, le, l, P.direct_thr, P.parent, P.child_first, P.nchild,
+                                                      P.cnt, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse, P.ncoarse,
+                                                      P.vdense, P.nv, P.xdense, P.nx, P.list_totals, P.status);
         KIFMM_CUDA_TRY(cudaGetLastError());
     }
     const unsigned g = grid_for(nb, 128);
