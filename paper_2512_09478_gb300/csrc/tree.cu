@@ -315,10 +315,6 @@ __global__ void k_scan_add(uint32_t *out, int64_t n, const uint32_t *__restrict_
         if (base + k < n) out[base + k] += add;
 }
 
-__global__ void k_write_total(const uint32_t *scan, const uint32_t *in, int64_t n, uint32_t *total) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *total = (n > 0) ? scan[n - 1] + in[n - 1] : 0u;
-}
-
 // ---------------------------------------------------------------------------
 // Octree
 // ---------------------------------------------------------------------------
@@ -378,14 +374,23 @@ __global__ void k_split(int64_t ls, int64_t le, const int64_t *range, int64_t m_
     if (lane == 0) nchild_tmp[j] = split ? (uint32_t)__popc(nonempty) : 0u;
 }
 
-__global__ void k_emit(int64_t ls, int64_t le, const int64_t *range, int64_t m_ub,
+// With `range` (the level's boundaries range[0], range[1]), one thread also
+// records the next level's end range[2] = le + children and flags a count
+// above m_ub_next (the grid the host sized for that level).
+__global__ void k_emit(int64_t ls, int64_t le, int64_t *range, int64_t m_ub,
                        const uint32_t *__restrict__ nchild_tmp, const uint32_t *__restrict__ nchild_scan,
                        const int32_t *__restrict__ rng, int32_t *lvl, int32_t *cx, int32_t *cy, int32_t *cz,
                        int32_t *first, int32_t *cnt, int32_t *parent, int32_t *child_first, int32_t *nchild,
-                       int32_t *sys, int64_t cap, int *status) {
+                       int32_t *sys, int64_t cap, int *status, const uint32_t *children, int64_t m_ub_next,
+                       int *fail) {
     if (range) {
         ls = range[0];
         le = range[1];
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const int64_t next = le + (int64_t)*children;
+            range[2] = next;
+            if (next - le > m_ub_next) *fail = 1;
+        }
     }
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m_ub) return;
@@ -419,27 +424,12 @@ __global__ void k_emit(int64_t ls, int64_t le, const int64_t *range, int64_t m_u
     }
 }
 
-// Device-side level bookkeeping of the speculative build: the next level is
-// [le, le + total); its end goes to level_start[slot]; a count above m_ub_next
-// (the grid the host launched for it) flags the speculation as failed.
-__global__ void k_spec_init(int64_t *range, int64_t *level_start, int S, int *fail) {
+// Device-side level boundaries of the speculative build: level 0 holds the S roots.
+__global__ void k_spec_init(int64_t *level_start, int S, int *fail) {
     if (threadIdx.x == 0) {
-        range[0] = 0;
-        range[1] = S;
         level_start[0] = 0;
         level_start[1] = S;
         *fail = 0;
-    }
-}
-
-__global__ void k_next_range(int64_t *range, const uint32_t *__restrict__ total, int64_t *level_start, int slot,
-                             int64_t m_ub_next, int *fail) {
-    if (threadIdx.x == 0) {
-        const int64_t ls = range[1], le = range[1] + (int64_t)*total;
-        range[0] = ls;
-        range[1] = le;
-        level_start[slot] = le;
-        if (le - ls > m_ub_next) *fail = 1;
     }
 }
 
@@ -765,13 +755,15 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uin
     }
     const int64_t nblk = (n + kScanTile - 1) / kScanTile;
     if ((size_t)nblk + 1 > tmp_elems) return cudaErrorInvalidValue;
+    if (nblk == 1) {  // one tile: its sum is the total
+        ++g_launches, k_scan_tiles<<<1, kScanBlock, 0, s>>>(in, out, n, total_dev ? total_dev : tmp);
+        return cudaGetLastError();
+    }
     uint32_t *sums = tmp;
     ++g_launches, k_scan_tiles<<<(unsigned)nblk, kScanBlock, 0, s>>>(in, out, n, sums);
-    if (nblk > 1) {
-        KIFMM_CUDA_TRY(exclusive_scan_u32(sums, sums, nblk, nullptr, tmp + nblk + 1, tmp_elems - nblk - 1, s));
-        ++g_launches, k_scan_add<<<(unsigned)nblk, kScanBlock, 0, s>>>(out, n, sums);
-    }
-    if (total_dev) ++g_launches, k_write_total<<<1, 32, 0, s>>>(out, in, n, total_dev);
+    // the tile sums' own scan yields the grand total
+    KIFMM_CUDA_TRY(exclusive_scan_u32(sums, sums, nblk, total_dev, tmp + nblk + 1, tmp_elems - nblk - 1, s));
+    ++g_launches, k_scan_add<<<(unsigned)nblk, kScanBlock, 0, s>>>(out, n, sums);
     return cudaGetLastError();
 }
 
@@ -1030,22 +1022,22 @@ static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
     if (!m_ub.empty()) {
         ++g_launches, k_roots<<<grid_for(S, 128), 128, 0, s>>>(S, P.sys_off_d, P.lvl, P.cx, P.cy, P.cz, P.first,
                                                                 P.cnt, P.parent, P.sys);
-        int64_t *range = P.spec_buf, *lsd = P.spec_buf + 2;
-        ++g_launches, k_spec_init<<<1, 32, 0, s>>>(range, lsd, S, P.spec_fail);
+        int64_t *lsd = P.spec_buf;  // lsd[l], lsd[l + 1]: level l's boxes
+        ++g_launches, k_spec_init<<<1, 32, 0, s>>>(lsd, S, P.spec_fail);
         uint32_t *scan_out = P.tmp_nchild + P.box_cap;
         for (int l = 0; l < lspec; ++l) {
             const int64_t mu = m_ub[l];
-            ++g_launches, k_split<<<grid_for(mu, 4), 128, 0, s>>>(0, 0, range, mu, l, P.desc.leaf_cap,
+            ++g_launches, k_split<<<grid_for(mu, 4), 128, 0, s>>>(0, 0, lsd + l, mu, l, P.desc.leaf_cap,
                                                                   P.desc.max_depth, P.keys[0], P.first, P.cnt,
                                                                   P.tmp_nchild, P.child_rng);
             KIFMM_CUDA_TRY(exclusive_scan_u32(P.tmp_nchild, scan_out, mu, total_dev, P.scan_tmp,
                                               P.scan_tmp_elems - 1, s));
-            ++g_launches, k_emit<<<grid_for(mu, 128), 128, 0, s>>>(0, 0, range, mu, P.tmp_nchild, scan_out,
+            const int64_t next = (l + 1 < lspec) ? m_ub[l + 1] : INT64_MAX;
+            ++g_launches, k_emit<<<grid_for(mu, 128), 128, 0, s>>>(0, 0, lsd + l, mu, P.tmp_nchild, scan_out,
                                                                    P.child_rng, P.lvl, P.cx, P.cy, P.cz, P.first,
                                                                    P.cnt, P.parent, P.child_first, P.nchild, P.sys,
-                                                                   P.box_cap, P.status);
-            const int64_t next = (l + 1 < lspec) ? m_ub[l + 1] : INT64_MAX;
-            ++g_launches, k_next_range<<<1, 32, 0, s>>>(range, total_dev, lsd, l + 2, next, P.spec_fail);
+                                                                   P.box_cap, P.status, total_dev, next,
+                                                                   P.spec_fail);
         }
         KIFMM_CUDA_TRY(cudaGetLastError());
         std::vector<int64_t> lsh(lspec + 2);
@@ -1102,7 +1094,7 @@ static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
         ++g_launches, k_emit<<<grid_for(m, 128), 128, 0, s>>>(ls, le, nullptr, m, P.tmp_nchild, scan_out,
                                                               P.child_rng, P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt,
                                                               P.parent, P.child_first, P.nchild, P.sys, P.box_cap,
-                                                              P.status);
+                                                              P.status, nullptr, 0, nullptr);
         KIFMM_CUDA_TRY(cudaGetLastError());
         if (total == 0) break;
         ls = le;
