@@ -1003,7 +1003,11 @@ static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
     const int S = P.n_sys;
     const std::vector<int64_t> prev = P.level_start;  // the last build's level boundaries
     uint32_t *total_dev = P.scan_tmp + P.scan_tmp_elems - 1;
-    const int lspec = std::min((int)prev.size() - 2, lsort);
+    // split levels 0 .. lspec - 1 without round trips: every level the last
+    // tree had, its deepest (leaf) level included, so that a tree of the same
+    // depth is complete at the one synchronisation; a node at level lsort
+    // cannot be split from the sorted digits
+    const int lspec = std::min((int)prev.size() - 1, lsort);
     std::vector<int64_t> m_ub;
     if (lspec >= 2 && prev[1] == S) {
         int64_t need = S;
