@@ -295,8 +295,8 @@ kifmm_status kifmm_profile_enable(kifmm_plan *plan, int enable);
 /* out (host): accumulated times since the last read; resets them. */
 kifmm_status kifmm_profile_read(kifmm_plan *plan, kifmm_profile_t *out);
 
-/* Tile shapes in use (no counterpart in the paper: the benchmark spec asks for
- * M2L/P2P tile shapes chosen by an autotuner).  tuned: bit 0 leaf kernel,
+/* Tile shapes in use (no counterpart in the paper: the M2L and P2P tile
+ * shapes are chosen by an autotuner on the live tree).  tuned: bit 0 leaf kernel,
  * bit 1 tensor-core M2L.  m2l_stages: shared-memory pipeline depth of the
  * tensor-core M2L (0 when the plan has none).  Leaf kernel: a leaf is
  * covered by passes; with r of its targets still to cover, bucket

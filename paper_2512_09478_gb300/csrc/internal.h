@@ -197,7 +197,7 @@ struct Plan {
     // ---- status ----
     int *status = nullptr;   // device status word
     int *moved = nullptr;    // device flag of the tree reuse test
-    int64_t *spec_buf = nullptr;  // [32] speculative octree build: range, level boundaries
+    int64_t *spec_buf = nullptr;  // [32] speculative octree build: level boundaries
     int *spec_fail = nullptr;     // a level outgrew the grid the host sized for it
     cudaStream_t last_stream = nullptr;
     bool has_sources = false;
