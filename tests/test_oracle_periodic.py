@@ -1,0 +1,124 @@
+"""Pins of the oracle's periodic Coulomb sum (Ewald summation with the
+conducting boundary; the cell must be neutral, Sec. 2.4).
+
+* Madelung constants of rock salt and caesium chloride (textbook values,
+  e.g. Kittel, Introduction to Solid State Physics, ch. 3: 1.747565 and
+  1.762675; here to 13 digits).
+* Independence of the splitting parameter alpha; invariance under a common
+  translation and under moving a particle by a lattice vector.
+* The plain image sum over growing spheres of cells (written out below, no
+  Ewald split): for a neutral cell without dipole moment its gradient
+  converges to Ewald's and its potential to Ewald's plus the constant
+  (2 pi / 3V) sum_j q_j |x_j - c|^2 (de Leeuw, Perram & Smith 1980, the paper's
+  reference for the neutrality condition), c the centre of the sphere.
+* The gradient is the derivative of the potential (central differences).
+* A charged cell is refused.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+M_NACL = 1.747564594633182   # per nearest-neighbour distance
+M_CSCL = 1.762674773070989
+
+
+def test_madelung_rock_salt():
+    na = [(0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+    cl = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 1)]
+    x = np.array(na + cl, dtype=float)          # cubic cell 2, nearest neighbours 1 apart
+    q = np.array([1.0] * 4 + [-1.0] * 4)
+    pot, grad = O.ewald(x, q, 2.0)
+    assert np.allclose(pot * 4 * np.pi, -q * M_NACL, rtol=0, atol=1e-12)
+    assert np.abs(grad).max() < 1e-12          # every ion sits at a centre of symmetry
+
+
+def test_madelung_caesium_chloride():
+    x = np.array([(0.0, 0.0, 0.0), (0.5, 0.5, 0.5)])
+    q = np.array([1.0, -1.0])
+    pot, grad = O.ewald(x, q, 1.0)
+    r0 = np.sqrt(3.0) / 2.0
+    assert np.allclose(pot * 4 * np.pi * r0, -q * M_CSCL, rtol=0, atol=1e-12)
+    assert np.abs(grad).max() < 1e-12
+
+
+def _neutral(n, seed, L=1.0):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, L, size=(n, 3))
+    q = rng.normal(size=n)
+    q -= q.mean()
+    return x, q
+
+
+def test_splitting_parameter_does_not_matter():
+    x, q = _neutral(12, 5)
+    ref = O.ewald(x, q, 1.0, alpha=6.0)
+    for a in (4.5, 8.0):
+        pot, grad = O.ewald(x, q, 1.0, alpha=a)
+        assert O.rel_l2(pot, ref[0]) < 1e-12 and O.rel_l2(grad, ref[1]) < 1e-12, a
+
+
+def test_translation_and_lattice_shifts():
+    x, q = _neutral(10, 6, L=2.5)
+    pot, grad = O.ewald(x, q, 2.5)
+    t = np.array([0.37, -1.1, 2.2])
+    p2, g2 = O.ewald(np.mod(x + t, 2.5), q, 2.5)
+    assert O.rel_l2(p2, pot) < 1e-12 and O.rel_l2(g2, grad) < 1e-12
+    y = x.copy()
+    y[3] += np.array([2.5, 0.0, -2.5])
+    p3, g3 = O.ewald(y, q, 2.5)
+    assert O.rel_l2(p3, pot) < 1e-12 and O.rel_l2(g3, grad) < 1e-12
+
+
+def _sphere_sum(x, q, L, R):
+    """sum_j q_j / (4 pi |x_i - x_j + L s|) over cells s with |s| <= R (self excluded)."""
+    n = int(np.ceil(R))
+    r = np.arange(-n, n + 1)
+    S = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3).astype(float)
+    S = S[np.linalg.norm(S, axis=1) <= R]
+    pot = np.zeros(len(x))
+    grad = np.zeros((len(x), 3))
+    for i in range(len(x)):
+        d = x[i][None, None, :] - x[None, :, :] + L * S[:, None, :]
+        rr = np.linalg.norm(d, axis=-1)
+        rr[np.all(S == 0, axis=1), i] = np.inf
+        pot[i] = np.sum(q[None, :] / rr)
+        grad[i] = -np.sum((q[None, :] / rr ** 3)[:, :, None] * d, axis=(0, 1))
+    return pot / (4 * np.pi), grad / (4 * np.pi)
+
+
+def test_sphere_of_images_converges_to_ewald():
+    rng = np.random.default_rng(3)
+    L = 1.0
+    c = np.full(3, 0.5 * L)
+    h = rng.uniform(0, L, size=(4, 3))
+    x = np.concatenate([h, 2 * c - h])           # inversion pairs: zero dipole
+    q = np.array([1.0, -1.0, 2.0, -2.0] * 2)
+    pe, ge = O.ewald(x, q, L)
+    shift = (2 * np.pi / (3 * L ** 3)) * np.sum(q * np.sum((x - c) ** 2, axis=1)) / (4 * np.pi)
+    errs = []
+    for R in (8, 16):
+        ps, gs = _sphere_sum(x, q, L, R)
+        errs.append(O.rel_l2(gs, ge))
+        assert O.rel_l2(ps, pe - shift) < 2e-4, R
+    assert errs[1] < errs[0] / 8 and errs[1] < 1e-5, errs
+
+
+def test_gradient_is_the_derivative_of_the_potential():
+    x, q = _neutral(8, 11)
+    _, grad = O.ewald(x, q, 1.0)
+    h = 1e-5
+    for i in (0, 5):
+        for d in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, d] += h
+            xm[i, d] -= h
+            fd = (O.ewald(xp, q, 1.0)[0][i] - O.ewald(xm, q, 1.0)[0][i]) / (2 * h)
+            assert abs(fd - grad[i, d]) <= 1e-7 * (1.0 + abs(grad[i, d])), (i, d)
+
+
+def test_charged_cell_is_refused():
+    x = np.array([(0.1, 0.2, 0.3), (0.6, 0.5, 0.4)])
+    with pytest.raises(O.NotNeutralError):
+        O.ewald(x, np.array([1.0, -0.5]), 1.0)
+    O.check_neutral(np.array([1.0, -1.0, 0.5, -0.5]))
