@@ -40,6 +40,10 @@ Sec. 2.2) and fixed as follows:
   with the ranks rounded up to fill 32-wide tiles (the left rank leaves one
   slot for the mean) and lowered off any cluster of equal singular values;
   each matrix is replaced by its projection (U U^T K0 + 1 m^T) V V^T.
+* Tensor kernel: the direct sum of Stokeslets (point forces in Stokes flow),
+  the kind of vector/tensor kernel Eq. 1 admits, and the KIFMM with it (the
+  same tree, lists, surfaces and regularised pseudo-inverses; 3-vector
+  densities).
 * Periodic sums (Sec. 2.4): a neutral cubic cell repeated over Z^3, summed
   by Ewald's split with the conducting boundary (the mean potential of the
   cell is zero); a charged cell is refused, the paper's neutrality condition.
@@ -542,6 +546,115 @@ def clump_reduce(x, q, grad, offsets, ref, coef: float = 1.0):
             F[c] += f[k]
             T[c] += np.cross(x[k] - ref[c], f[k])
     return F, T
+
+
+# ---------------------------------------------------------------------------
+# Tensor kernel (Eq. 1 allows vector and tensor kernels; Stokes flow is the
+# paper's example of one with its own periodic constraints, Sec. 2.4)
+# ---------------------------------------------------------------------------
+def stokeslet_direct(x, f, targets=None, mu: float = 1.0):
+    """Velocity u(t) = sum_j G(t - x_j) f_j of point forces f_j at x_j, with the
+    Stokeslet G(r) = (I / |r| + r r^T / |r|^3) / (8 pi mu); pairs at zero
+    distance excluded.  x [N,3], f [N,3]; targets default to the sources."""
+    x = _f64(x).reshape(-1, 3)
+    f = _f64(f).reshape(-1, 3)
+    t = x if targets is None else _f64(targets).reshape(-1, 3)
+    u = np.zeros((t.shape[0], 3))
+    for i in range(t.shape[0]):
+        d = t[i][None, :] - x                      # [N, 3]
+        r2 = np.sum(d * d, axis=1)
+        ok = r2 > 0.0
+        r = np.sqrt(r2[ok])
+        dd, ff = d[ok], f[ok]
+        u[i] = np.sum(ff / r[:, None], axis=0) + np.sum(dd * (np.sum(dd * ff, axis=1) / r ** 3)[:, None], axis=0)
+    return u / (8.0 * np.pi * mu)
+
+
+def stokeslet_matrix(targets, sources, mu: float = 1.0):
+    """[3 nt, 3 ns] matrix of the Stokeslet: block (i, j) is G(t_i - s_j)
+    (zero at zero distance); row 3 i + a, column 3 j + b."""
+    t = _f64(targets).reshape(-1, 3)
+    s = _f64(sources).reshape(-1, 3)
+    d = t[:, None, :] - s[None, :, :]
+    r2 = np.sum(d * d, axis=-1)
+    ok = r2 > 0.0
+    r = np.sqrt(np.where(ok, r2, 1.0))
+    g = np.eye(3)[None, None, :, :] / r[:, :, None, None] + d[:, :, :, None] * d[:, :, None, :] / \
+        (r ** 3)[:, :, None, None]
+    g = np.where(ok[:, :, None, None], g, 0.0) / (8.0 * np.pi * mu)
+    return g.transpose(0, 2, 1, 3).reshape(3 * t.shape[0], 3 * s.shape[0])
+
+
+def kifmm_stokes(x, f, p: int = 6, leaf_cap: int = 64, max_depth: int = 20, eps: float = 1e-12,
+                 mu: float = 1.0, direct_max: int = 0):
+    """Velocities u_i = sum_{j != i} G(x_i - x_j) f_j by the KIFMM with the
+    Stokeslet (Sec. 2.2's method for a tensor kernel of Eq. 1): the tree and
+    lists of the Laplace oracle; every surface point carries a 3-vector
+    density (3 n_s unknowns); the operators are Stokeslet matrices between
+    the same surfaces, with the same regularised pseudo-inverses.  The
+    Stokeslet is homogeneous of degree -1 like 1/r, so unit-box operators
+    scale by 1/h.  The passes follow the Laplace oracle: P2M and M2M into
+    upward check velocities and densities, M2L (V) and P2L (X) into downward
+    check velocities, L2L, then L2P, M2P (W) and P2P (U) at the leaves."""
+    x = _f64(x).reshape(-1, 3)
+    f = _f64(f).reshape(-1, 3)
+    tree = sort_and_tree(x, leaf_cap, max_depth)
+    S = surface(p)
+    ns = S.shape[0]
+    lst = effective_lists(tree, lists(tree), direct_threshold(ns, direct_max))
+    K = lambda t, s: stokeslet_matrix(t, s, mu)
+    up = svd_pinv_factors(K(ALPHA_UC * S, ALPHA_UE * S), eps)
+    dn = svd_pinv_factors(K(ALPHA_DC * S, ALPHA_DE * S), eps)
+    pinv = lambda fac: fac[2] @ np.diag(fac[1]) @ fac[0].T
+    P_up, P_dn = pinv(up), pinv(dn)
+    m2m = [K(ALPHA_UC * S, child_offset(o) + 0.5 * ALPHA_UE * S) for o in range(8)]
+    l2l = [K(child_offset(o) + 0.5 * ALPHA_DC * S, ALPHA_DE * S) for o in range(8)]
+    offs = m2l_offsets()
+    m2l = {tuple(d): K(ALPHA_DC * S, 2.0 * d + ALPHA_UE * S) for d in offs}
+    perm = tree["perm"]
+    xs, fs = x[perm], f[perm]
+    nb = tree["nb"]
+    level, coord, first, count = tree["level"], tree["coord"], tree["first"], tree["count"]
+    w = tree["side"] / 2.0 ** level
+    centre = tree["lo"][None, :] + (coord + 0.5) * w[:, None]
+    half = 0.5 * w
+    octant = 4 * (coord[:, 0] & 1) + 2 * (coord[:, 1] & 1) + (coord[:, 2] & 1)
+    isleaf = tree["child_first"] < 0
+    pts = lambda b: slice(int(first[b]), int(first[b] + count[b]))
+    q_up = np.zeros((nb, 3 * ns))
+    d_chk = np.zeros((nb, 3 * ns))
+    q_dn = np.zeros((nb, 3 * ns))
+    for lev in range(int(level.max()), -1, -1):           # upward
+        for b in np.nonzero(level == lev)[0]:
+            if isleaf[b]:
+                chk = K(centre[b] + ALPHA_UC * half[b] * S, xs[pts(b)]) @ fs[pts(b)].ravel()
+            else:
+                chk = np.zeros(3 * ns)
+                for c in range(int(tree["child_first"][b]), int(tree["child_first"][b] + tree["nchild"][b])):
+                    chk += m2m[octant[c]] @ q_up[c] / half[b]
+            q_up[b] = half[b] * (P_up @ chk)
+    V, X, W, U = (lst[k] for k in "VXWU")
+    for b in range(nb):                                     # M2L, P2L
+        for a in V[1][V[0][b]:V[0][b + 1]]:
+            d_chk[b] += m2l[tuple(coord[a] - coord[b])] @ q_up[a] / half[b]
+        for a in X[1][X[0][b]:X[0][b + 1]]:
+            d_chk[b] += K(centre[b] + ALPHA_DC * half[b] * S, xs[pts(a)]) @ fs[pts(a)].ravel()
+    for lev in range(int(level.max()) + 1):                 # downward
+        for b in np.nonzero(level == lev)[0]:
+            pb = tree["parent"][b]
+            if pb >= 0:
+                d_chk[b] += l2l[octant[b]] @ q_dn[pb] / half[pb]
+            q_dn[b] = half[b] * (P_dn @ d_chk[b])
+    u = np.zeros((x.shape[0], 3))
+    for b in np.nonzero(isleaf)[0]:                         # L2P, M2P, P2P
+        xt = xs[pts(b)]
+        ub = K(xt, centre[b] + ALPHA_DE * half[b] * S) @ q_dn[b]
+        for a in W[1][W[0][b]:W[0][b + 1]]:
+            ub += K(xt, centre[a] + ALPHA_UE * half[a] * S) @ q_up[a]
+        for a in U[1][U[0][b]:U[0][b + 1]]:
+            ub += K(xt, xs[pts(a)]) @ fs[pts(a)].ravel()
+        u[perm[pts(b)]] = ub.reshape(-1, 3)
+    return u
 
 
 # ---------------------------------------------------------------------------
