@@ -13,6 +13,9 @@ conducting boundary; the cell must be neutral, Sec. 2.4).
   reference for the neutrality condition), c the centre of the sphere.
 * The gradient is the derivative of the potential (central differences).
 * A charged cell is refused.
+* The periodic KIFMM (cell as the root, lists over the 26 neighbouring
+  images, one far-image operator, the second-moment trace correction)
+  converges to the Ewald sum as p grows, on uniform and clustered cells.
 """
 import numpy as np
 import pytest
@@ -122,3 +125,48 @@ def test_charged_cell_is_refused():
     with pytest.raises(O.NotNeutralError):
         O.ewald(x, np.array([1.0, -0.5]), 1.0)
     O.check_neutral(np.array([1.0, -1.0, 0.5, -0.5]))
+
+
+# ---------------------------------------------------------------------------
+# The periodic KIFMM (oracle.kifmm_periodic) against the Ewald sum
+# ---------------------------------------------------------------------------
+def test_periodic_kifmm_converges_to_ewald():
+    x, q = _neutral(300, 1)
+    pe, ge = O.ewald(x, q, 1.0)
+    e = {}
+    for p in (4, 6):
+        pp, gp = O.kifmm_periodic(x, q, 1.0, p=p, leaf_cap=32)
+        e[p] = (O.rel_l2(pp, pe), O.rel_l2(gp, ge))
+    assert max(e[4]) < 2e-3 and max(e[6]) < 3e-5, e
+    assert e[6][0] < e[4][0] / 10 and e[6][1] < e[4][1] / 10, e
+    # a single leaf: the 27 nearest images directly, the rest through the
+    # far-image operator alone
+    pp, gp = O.kifmm_periodic(x, q, 1.0, p=6, leaf_cap=400)
+    assert O.rel_l2(pp, pe) < 3e-5 and O.rel_l2(gp, ge) < 3e-5
+
+
+def test_periodic_kifmm_adaptive_tree_with_images():
+    from workloads import generators as G
+    xp, _ = G.plummer(400, 3)
+    x = np.mod(0.5 + 0.05 * xp, 1.0)               # a cluster in the cell, wrapped
+    q = np.random.default_rng(12).normal(size=400)
+    q -= q.mean()
+    lo = np.zeros(3)
+    keys = O.morton(x, lo, 1.0)
+    perm = np.argsort(keys, kind="stable")
+    tree = O.build_tree(keys[perm], 16, 20)
+    lst, shifts = O.periodic_lists(tree)
+    assert sum(len(w) for w in lst["W"]) > 0 and sum(len(v) for v in lst["X"]) > 0
+    assert any((u[:, 1] != 13).any() for u in lst["U"] if len(u))   # image neighbours occur
+    for kind in "UVWX":                                             # no entry twice
+        for e in lst[kind]:
+            assert len({(int(a), int(n)) for a, n in e}) == len(e)
+    pe, ge = O.ewald(x, q, 1.0)
+    pp, gp = O.kifmm_periodic(x, q, 1.0, p=6, leaf_cap=16)
+    assert O.rel_l2(pp, pe) < 3e-5 and O.rel_l2(gp, ge) < 5e-5
+
+
+def test_periodic_kifmm_refuses_a_charged_cell():
+    x = np.array([(0.1, 0.2, 0.3), (0.6, 0.5, 0.4)])
+    with pytest.raises(O.NotNeutralError):
+        O.kifmm_periodic(x, np.array([1.0, 0.5]), 1.0, p=4)
