@@ -59,3 +59,51 @@ def test_lr_stride_closed_forms():
         with pytest.raises(KifmmError) as e:
             lr_stride(*bad)
         assert e.value.code == 1
+
+
+def test_host_side_argument_checks():
+    """Argument errors are reported before any CUDA call, so they hold without
+    a GPU: plan descriptors out of range, null plans and pointers, a skin
+    outside [0, 1], unknown list kinds, and the status strings."""
+    import ctypes as C
+    from paper_2512_09478_gb300 import build as B, kifmm
+    lib = C.CDLL(B.build())
+    kifmm._LIB = None
+    P = C.c_void_p
+    lib.kifmm_plan_create.argtypes = [C.POINTER(kifmm.PlanDesc), C.POINTER(P)]
+    lib.kifmm_status_string.restype = C.c_char_p
+    lib.kifmm_status_string.argtypes = [C.c_int]
+
+    def desc(**kw):
+        d = dict(p=6, leaf_cap=64, max_depth=20, precision=kifmm.PRECISIONS["mixed_fp16"], coef=1.0,
+                 n_max=1000, n_systems_max=1, dtype=0, pinv_eps=0.0, autotune=0, direct_max=0, m2l_eps=0.0)
+        d.update(kw)
+        return kifmm.PlanDesc(**d)
+
+    bad = [dict(p=1), dict(p=11), dict(leaf_cap=0), dict(max_depth=0), dict(max_depth=21), dict(precision=7),
+           dict(n_max=0), dict(n_systems_max=0), dict(dtype=2), dict(pinv_eps=-1.0), dict(pinv_eps=1.0),
+           dict(m2l_eps=-1e-5), dict(m2l_eps=1.0), dict(m2l_eps=float("nan")),
+           dict(m2l_eps=1e-5, precision=kifmm.PRECISIONS["fp32"]),
+           dict(m2l_eps=1e-5, precision=kifmm.PRECISIONS["fp64"])]
+    for kw in bad:
+        h = P()
+        d = desc(**kw)
+        assert lib.kifmm_plan_create(C.byref(d), C.byref(h)) == 1, kw
+        assert not h.value
+    assert lib.kifmm_plan_create(None, None) == 1
+    null = P()
+    buf = (C.c_double * 8)()
+    for name, args in [("kifmm_plan_destroy", [null]),
+                       ("kifmm_evaluate", [null, None, None, None, None]),
+                       ("kifmm_update_sources", [null, buf, buf, None]),
+                       ("kifmm_refresh_sources", [null, buf, buf, C.c_double(0.05), None, None]),
+                       ("kifmm_backward", [null, buf, buf, None, None, None]),
+                       ("kifmm_get_device_status", [null, None]),
+                       ("kifmm_profile_enable", [null, 1]),
+                       ("kifmm_tree_info", [null, None]),
+                       ("kifmm_copy_list", [null, 0, buf, None])]:
+        assert getattr(lib, name)(*args) == 1, name
+    names = {k: lib.kifmm_status_string(k).decode() for k in range(7)}
+    assert names[0] == "ok" and names[1] == "invalid argument" and names[6] == "call out of order"
+    assert len(set(names.values())) == 7
+    assert lib.kifmm_status_string(99).decode() == "unknown status"
