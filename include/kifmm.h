@@ -264,6 +264,27 @@ const char *kifmm_status_string(kifmm_status status);
  */
 kifmm_status kifmm_lr_stride(double k_dem, double k_lr, int64_t *stride);
 
+/*
+ * Far-image operator of a periodic cell (Sec. 2.4: periodic boundary
+ * conditions, which the paper allows for neutral cells only), the plan-time
+ * building block of a periodic evaluation.  With the cell of side `cell` as
+ * the root box (half-width h = cell / 2), T[j][k] is the potential, with the
+ * kernel 1/(4 pi r) of Eq. 3, at the root's downward check point
+ * 1.05 h S_j due to a unit charge at its upward equivalent point
+ * 1.05 h S_k repeated over every image cell n with max |n_i| >= 2 (the
+ * images a periodic evaluation's lists, which run over the cell and its 26
+ * neighbours, do not reach).  S is the unit surface of order p (n_s =
+ * 6 (p - 1)^2 + 2 points, lexicographic, as everywhere in this library).
+ * The sum converges only conditionally; it is taken as Ewald's sum with the
+ * conducting boundary minus the 27 nearest images, so applied to a density
+ * that sums to zero (a neutral cell) it is the conducting-boundary far
+ * field.  T (host, [n_s][n_s] row-major doubles) receives the matrix.
+ * Host only, FP64, about a second at p = 6: needs no device and no plan.
+ * KIFMM_ERR_ARG for p outside 2..10, a non-positive or non-finite cell, or
+ * a NULL T.
+ */
+kifmm_status kifmm_far_image_operator(int p, double cell, double *T);
+
 /* ------------------------------------------------------------------------
  * Profiling.  When enabled, every stage of set_sources / evaluate is
  * bracketed by CUDA events recorded on the call's stream (no extra

@@ -227,6 +227,8 @@ size_t scan_tmp_needed(int64_t n);
 
 // ---- operators.cu ----
 cudaError_t build_operators(Plan &P, std::string &err);
+// operators.cu: unit-cube surface points [n_s][3], lexicographic.
+std::vector<double> unit_surface(int p);
 
 // ---- m2l_tc.cu (mixed modes) ----
 // tree.cu: *moved_dev = 1 if some particle lies outside its leaf by more than

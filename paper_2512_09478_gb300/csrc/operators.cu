@@ -208,19 +208,6 @@ __global__ void k_pack_compressed(int n, int nb, int rr, int rl, const double *_
     out[t] = (float)((i < rl) ? Bt[((size_t)b * n + c) * n + i] : mh[(size_t)b * n + c]);
 }
 
-std::vector<double> unit_surface(int p) {
-    std::vector<double> s;
-    for (int i = 0; i < p; ++i)
-        for (int j = 0; j < p; ++j)
-            for (int k = 0; k < p; ++k) {
-                if (i == 0 || i == p - 1 || j == 0 || j == p - 1 || k == 0 || k == p - 1) {
-                    s.push_back(-1.0 + 2.0 * i / (p - 1));
-                    s.push_back(-1.0 + 2.0 * j / (p - 1));
-                    s.push_back(-1.0 + 2.0 * k / (p - 1));
-                }
-            }
-    return s;
-}
 
 // K[i][k] = 1 / |(ct + at S_i) - (cs + as S_k)|
 void kernel_block(const std::vector<double> &S, int n, const double ct[3], double at, const double cs[3],
@@ -243,6 +230,22 @@ void child_center(int o, double c[3]) {
 }
 
 }  // namespace
+
+// Unit-cube surface grid (half-width 1): p points per edge, the boundary
+// points of the p^3 lattice in lexicographic order, n_s = 6 (p - 1)^2 + 2.
+std::vector<double> unit_surface(int p) {
+    std::vector<double> s;
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j)
+            for (int k = 0; k < p; ++k) {
+                if (i == 0 || i == p - 1 || j == 0 || j == p - 1 || k == 0 || k == p - 1) {
+                    s.push_back(-1.0 + 2.0 * i / (p - 1));
+                    s.push_back(-1.0 + 2.0 * j / (p - 1));
+                    s.push_back(-1.0 + 2.0 * k / (p - 1));
+                }
+            }
+    return s;
+}
 
 std::vector<int> m2l_offset_list() {
     std::vector<int> out;

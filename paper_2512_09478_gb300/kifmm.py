@@ -64,7 +64,7 @@ EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifm
            "kifmm_clump_reduce", "kifmm_backward", "kifmm_get_device_status", "kifmm_status_string",
            "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
            "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources",
-           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_measure_peaks", "kifmm_refresh_sources", "kifmm_lr_stride"]
+           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_measure_peaks", "kifmm_refresh_sources", "kifmm_lr_stride", "kifmm_far_image_operator"]
 
 
 def load(path: str = LIB_PATH):
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.kifmm_update_sources.argtypes = [P, P, P, P]
     lib.kifmm_refresh_sources.argtypes = [P, P, P, D, ctypes.POINTER(I), P]
     lib.kifmm_lr_stride.argtypes = [D, D, ctypes.POINTER(I64)]
+    lib.kifmm_far_image_operator.argtypes = [I, D, P]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int if name != "kifmm_status_string" else ctypes.c_char_p
     _LIB = lib
@@ -308,6 +309,16 @@ def lr_stride(k_dem: float, k_lr: float) -> int:
     s = ctypes.c_int64(0)
     _check(load().kifmm_lr_stride(float(k_dem), float(k_lr), ctypes.byref(s)), "kifmm_lr_stride")
     return s.value
+
+
+def far_image_operator(p: int, cell: float) -> np.ndarray:
+    """[n_s, n_s] far-image operator of a periodic cell of side `cell`
+    (see kifmm_far_image_operator).  Host only."""
+    ns = 6 * (p - 1) ** 2 + 2
+    T = np.empty((ns, ns), dtype=np.float64)
+    _check(load().kifmm_far_image_operator(int(p), float(cell), T.ctypes.data_as(ctypes.c_void_p)),
+           "kifmm_far_image_operator")
+    return T
 
 
 def energy_noalloc(q: torch.Tensor, pot: torch.Tensor, out: torch.Tensor = None, stream=None) -> torch.Tensor:

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -107,3 +108,24 @@ def test_host_side_argument_checks():
     assert names[0] == "ok" and names[1] == "invalid argument" and names[6] == "call out of order"
     assert len(set(names.values())) == 7
     assert lib.kifmm_status_string(99).decode() == "unknown status"
+
+
+def test_far_image_operator_matches_the_oracle():
+    """The library's host-side far-image operator (C++, FP64) against the
+    oracle's own (numpy): the same definition, written twice, at p = 3 and 4
+    and two cell sides; it also scales as 1 / cell (the kernel's degree)."""
+    from paper_2512_09478_gb300 import build as B, kifmm
+    from oracle import oracle as O
+    B.build()
+    kifmm._LIB = None
+    for p in (3, 4):
+        for L in (1.0, 2.5):
+            T = kifmm.far_image_operator(p, L)
+            To = O.far_image_operator(p, L)
+            assert np.abs(T - To).max() <= 1e-12 * np.abs(To).max(), (p, L)
+    T1, T3 = kifmm.far_image_operator(4, 1.0), kifmm.far_image_operator(4, 3.0)
+    assert np.abs(T3 - T1 / 3.0).max() <= 1e-12 * np.abs(T1).max()
+    from paper_2512_09478_gb300 import KifmmError
+    for bad in ((1, 1.0), (4, 0.0), (4, float("inf"))):
+        with pytest.raises(KifmmError):
+            kifmm.far_image_operator(*bad)
