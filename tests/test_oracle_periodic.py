@@ -16,6 +16,8 @@ conducting boundary; the cell must be neutral, Sec. 2.4).
 * The periodic KIFMM (cell as the root, lists over the 26 neighbouring
   images, one far-image operator, the second-moment trace correction)
   converges to the Ewald sum as p grows, on uniform and clustered cells.
+* Its lists cover every (target leaf, source leaf, neighbouring image) pair
+  exactly once (brute-force count), on uniform, clustered and one-leaf trees.
 """
 import numpy as np
 import pytest
@@ -170,3 +172,53 @@ def test_periodic_kifmm_refuses_a_charged_cell():
     x = np.array([(0.1, 0.2, 0.3), (0.6, 0.5, 0.4)])
     with pytest.raises(O.NotNeutralError):
         O.kifmm_periodic(x, np.array([1.0, 0.5]), 1.0, p=4)
+
+
+def _periodic_tree(x, M):
+    lo = np.zeros(3)
+    keys = O.morton(x, lo, 1.0)
+    perm = np.argsort(keys, kind="stable")
+    return O.build_tree(keys[perm], M, 20)
+
+
+@pytest.mark.parametrize("shape,n,M", [("uniform", 400, 8), ("cluster", 500, 6), ("one_leaf", 50, 64)])
+def test_periodic_lists_cover_every_image_pair_exactly_once(shape, n, M):
+    """Every (target leaf B in the cell, source leaf A, image shift s with
+    s in {-1, 0, 1}^3) is accounted for exactly once: by U(B), by a W(B) box
+    whose image holds A's image, or by V/X of an ancestor-or-self of B; images
+    farther away belong to the far-image operator alone."""
+    rng = np.random.default_rng(31)
+    if shape == "cluster":
+        from workloads import generators as G
+        xp, _ = G.plummer(n, 4)
+        x = np.mod(0.3 + 0.04 * xp, 1.0)
+    else:
+        x = rng.uniform(0, 1, size=(n, 3))
+    t = _periodic_tree(x, M)
+    lst, _ = O.periodic_lists(t)
+    leaves = np.nonzero(t["isleaf"])[0]
+    pos = {int(b): i for i, b in enumerate(leaves)}
+
+    def desc(b):
+        if t["isleaf"][b]:
+            return [int(b)]
+        out = []
+        for c in range(t["child_first"][b], t["child_first"][b] + t["nchild"][b]):
+            out += desc(c)
+        return out
+
+    for B in leaves:
+        cover = np.zeros((len(leaves), 27), dtype=np.int64)
+        for A, s in lst["U"][B]:
+            cover[pos[int(A)], s] += 1
+        for A, s in lst["W"][B]:
+            for a in desc(A):
+                cover[pos[a], s] += 1
+        b = int(B)
+        while b >= 0:
+            for kind in ("V", "X"):
+                for A, s in lst[kind][b]:
+                    for a in desc(A):
+                        cover[pos[a], s] += 1
+            b = int(t["parent"][b])
+        assert np.all(cover == 1), (int(B), np.argwhere(cover != 1)[:5])
