@@ -38,7 +38,10 @@ EPS0 = 8.8541878128e-12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 
 WORKLOADS = {
-    "c2": dict(kind="rsa", name="dem-coulomb-rsa-1M", n=1_000_000, p=6, leaf_cap=128, max_depth=20, seed=1001),
+    # p_accurate: the lowest surface order whose FP64 KIFMM meets rel-L2 <= 1e-5
+    # on forces on this packing (4.0e-6 at p = 7 against 3.0e-5 at p = 6)
+    "c2": dict(kind="rsa", name="dem-coulomb-rsa-1M", n=1_000_000, p=6, leaf_cap=128, max_depth=20, seed=1001,
+               p_accurate=7),
     # 1/8 of C2: the same leaf occupancy (about 30 points) one level higher
     "c2-small": dict(kind="rsa", name="dem-coulomb-rsa-125k", n=125_000, p=6, leaf_cap=128, max_depth=20, seed=1001),
     "c2-64k": dict(kind="rsa", name="dem-coulomb-rsa-64k", n=65_536, p=6, leaf_cap=128, max_depth=20, seed=1001),
@@ -47,7 +50,7 @@ WORKLOADS = {
     "c4": dict(kind="plummer", name="gravity-plummer-4M", n=4_000_000, p=8, leaf_cap=128, max_depth=12, seed=1003,
                oracle_frac=0.03, ref_frac=0.005, compare="fp64"),
     "c5": dict(kind="batched", name="batched-64-systems-10k-200k", systems=64, p=6, leaf_cap=64, max_depth=20,
-               seed=1004),
+               seed=1004, ref_frac=0.1),
 }
 WORKLOADS["c2"]["compare"] = "fp32"
 
@@ -194,8 +197,10 @@ def algorithmic_work(plan, w, n):
     # per W-list box for M2P
     wptr, _ = plan.list("W")
     leaf_pairs = pairs + ns * float(n) + ns * float(np.sum(cnt * np.diff(wptr)))
-    # tree: bbox read 16 B, keys read 12 B + write 16 B, 8 sort passes x (read 12 + 12 + write 12) B, gather 36 B
-    tree_bytes = n * (16 + 28 + 8 * 36 + 36)
+    # tree: bbox read 16 B, keys read 12 B + write 16 B, each radix pass the
+    # library ran x (read 12 B for the histogram + read 12 B and write 12 B in
+    # the scatter), gather 36 B
+    tree_bytes = n * (16 + 28 + info["sort_passes"] * 36 + 36)
     return {"m2l_flops": m2l_flops, "p2p_pairs": pairs, "leaf_pairs": leaf_pairs, "tree_bytes": float(tree_bytes),
             "info": info}
 
@@ -206,10 +211,10 @@ def roofline_for(stage, ms_per_call, work, precision, peaks):
         flops = work["m2l_flops"]
         ach = flops / (ms_per_call * 1e-3) / 1e12
         if precision.startswith("mixed"):
-            peak = bf16_s if precision == "mixed_fp16" else bf16_s / 2
-            return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            # a ~1 ms kernel timed on its own launch: the burst peak (FP16 runs at the BF16 rate)
+            return {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
                     "traffic": None, "kernel": "k_m2l_tc",
-                    "peak_source": f"{kind} bf16 sustained (fp16 same rate); 3 split products, 1 counted"}
+                    "peak_source": f"{kind} bf16 burst (fp16 same rate); 3 split products, 1 counted"}
         return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "k_ggemm<GatherM2L>",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
@@ -308,15 +313,17 @@ def cpu_baseline_leg(x, q, meta, w, n_targets, seed=0, frac=None):
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle, as it stands, on a bounded sample of
-    the same workload per step (rank 0 only)."""
+    """Reference arm: the FP64 CPU oracle, as it stands, on the same workload
+    per step (rank 0 only): the whole workload for the DEM and clump cases
+    (about 7 s per step on 16 cores at 1M), a bounded sample where that would
+    take minutes per step (4M gravity, 64 batched systems)."""
     if rank != 0:
         return
     from oracle import oracle as O
     O.build()
     w = WORKLOADS[args.workload]
     x, q, meta = make_inputs(w)
-    parts, what = _oracle_sample(x, q, meta, w, w.get("ref_frac", 0.1))
+    parts, what = _oracle_sample(x, q, meta, w, w.get("ref_frac", 1.0))
     ops = O.operators(w["p"])
     n_s = sum(p[0].shape[0] for p in parts)
 
@@ -337,8 +344,9 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w["name"], "n": int(x.shape[0]), "p": w["p"], "leaf_cap": w["leaf_cap"],
-                      "parallelism": "host cores (OpenMP)"},
+           "config": {"workload": w["name"], "n": int(x.shape[0]), "systems": len(meta["offsets"]) - 1,
+                      "p": w["p"], "leaf_cap": w["leaf_cap"], "parallelism": "host cores (OpenMP)",
+                      "same_workload": n_s == int(x.shape[0])},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"{what}: {n_s} of {x.shape[0]} particles per step"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -579,11 +587,6 @@ def run_ours(args, rank, world, local_rank):
     dominant = max((k for k in per_call if k in ("m2l", "p2p")), key=lambda k: prof["ms"][k])
     peaks = measured_peaks()
     roof = roofline_for(dominant, per_call[dominant], work, args.precision, peaks)
-    try:
-        from paper_2512_09478_gb300.kifmm import measure_peaks
-        unit_peaks = measure_peaks()  # this device's FMA / rsqrt / tcgen05 rates, for context
-    except Exception as e:  # reported, never fatal for the benchmark line
-        unit_peaks = {"error": str(e)}
     other = {s: roofline_for(s, per_call[s], work, args.precision, peaks) for s in ("m2l", "p2p", "tree")
              if s in per_call}
     for s_name, r in list(other.items()) + [(dominant, roof)]:
@@ -609,8 +612,7 @@ def run_ours(args, rank, world, local_rank):
            "roofline": roof, "stage_rooflines": other,
            "stages_ms": {k: round(v / max(calls[k], 1) * (calls[k] / args.steps), 4)
                          for k, v in prof["ms"].items() if calls[k] > 0},
-           "stages_note": prof_note, "gpu_launches": launches, "clocks": clk, "e2e": e2e, "tree_reuse": reuse,
-           "unit_peaks_measured": unit_peaks}
+           "stages_note": prof_note, "gpu_launches": launches, "clocks": clk, "e2e": e2e, "tree_reuse": reuse}
     ref = None
     if not args.no_cpu_baseline:
         base, ref = cpu_baseline_leg(x, q, meta, w, args.accuracy_targets)
@@ -621,6 +623,23 @@ def run_ours(args, rank, world, local_rank):
     if cmp_prec and cmp_prec != args.precision:
         out["compare"] = compare_leg(args, w, cmp_prec, xt, qt, offsets, coef, n, n / (ms_per_step * 1e-3) / 1e6, stream, flush,
                                      clumps, (coff, cref) if clumps else None, ref, q)
+    if w.get("p_accurate") and args.precision == "mixed_fp16":
+        # the lowest surface order whose FP64 method error on this packing meets
+        # the metric's rel-L2 <= 1e-5 for forces: the benchmarked path and the
+        # plain FP32 path at that order, with their accuracy
+        pa = w["p_accurate"]
+        mixed_a = compare_leg(args, w, "mixed_fp16", xt, qt, offsets, coef, n, 0.0, stream, flush, clumps,
+                              (coff, cref) if clumps else None, ref, q, p=pa)
+        fp32_a = compare_leg(args, w, "fp32", xt, qt, offsets, coef, n, 0.0, stream, flush, clumps,
+                             (coff, cref) if clumps else None, ref, q, p=pa)
+        for leg in (mixed_a, fp32_a):
+            leg.pop("speedup_of_benchmarked", None)
+            leg.pop("m2l_ms", None)
+        out["at_accuracy"] = {"p": pa, "value": mixed_a["value"], "unit": UNIT,
+                              "ms_per_step": mixed_a["ms_per_step"], "precision": "mixed_fp16",
+                              "accuracy": mixed_a.get("accuracy"), "fp32": fp32_a,
+                              "speedup_vs_fp32": mixed_a["value"] / fp32_a["value"],
+                              "step": "set_sources + evaluate"}
     if args.m2l_eps_compare > 0 and args.precision == "mixed_fp16":
         out["m2l_compressed"] = compare_leg(args, w, "mixed_fp16", xt, qt, offsets, coef, n,
                                             n / (ms_per_step * 1e-3) / 1e6, stream, flush, clumps,
@@ -645,7 +664,8 @@ def accuracy_of(ref, q, coef, pot, grad, force=None, torque=None):
     return acc
 
 
-def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, clumps, cl, ref, q, m2l_eps=0.0):
+def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, clumps, cl, ref, q, m2l_eps=0.0,
+                p=None):
     """The same step with another precision of the library (plain FP32 SIMT
     M2L for the DEM workload, the FP64 path for gravity), or with the
     compressed M2L (m2l_eps > 0): its throughput, the speedup of the
@@ -653,7 +673,8 @@ def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, c
     import torch
     from paper_2512_09478_gb300 import Plan
     dt = torch.float64 if prec == "fp64" else torch.float32
-    plan = Plan(p=w["p"], leaf_cap=w["leaf_cap"], max_depth=w["max_depth"], precision=prec, coef=coef,
+    p = w["p"] if p is None else p
+    plan = Plan(p=p, leaf_cap=w["leaf_cap"], max_depth=w["max_depth"], precision=prec, coef=coef,
                 n_max=n, n_systems_max=len(offsets) - 1, dtype=dt, autotune=not args.no_autotune,
                 m2l_eps=m2l_eps)
     x2, q2 = xt.to(dt), qt.to(dt)
@@ -685,7 +706,7 @@ def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, c
         torch.cuda.synchronize()
         ms += a.elapsed_time(b)
     v = n / (ms / k * 1e-3) / 1e6
-    res = {"precision": prec, "value": v, "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+    res = {"precision": prec, "p": p, "value": v, "unit": UNIT, "ms_per_step": ms / k, "steps": k,
            "speedup_of_benchmarked": value / v, "io_dtype": "f64" if prec == "fp64" else "f32"}
     if m2l_eps > 0:
         res["m2l_eps"] = m2l_eps

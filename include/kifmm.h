@@ -52,10 +52,14 @@ typedef enum {
     KIFMM_ERR_STATE = 6      /* call out of order (e.g. evaluate before set_sources) */
 } kifmm_status;
 
+/* Value 2 is not a precision: a 3xTF32 tensor-core M2L would give the same
+ * accuracy as the 3xFP16 one (both operand halves carry 11 significant bits)
+ * at half the tensor rate, and single TF32 or BF16 operands (or a BF16 split)
+ * do not reach the FP32 path's accuracy, so only the 3xFP16 split is offered.
+ * plan_create returns KIFMM_ERR_ARG for 2. */
 typedef enum {
     KIFMM_FP64 = 0,       /* every stage in double precision (parity path) */
     KIFMM_FP32 = 1,       /* single precision, SIMT M2L ("plain FP32")         */
-    KIFMM_MIXED_TF32 = 2, /* M2L on tensor cores, 3xTF32 split, FP32 accumulate */
     KIFMM_MIXED_FP16 = 3  /* M2L on tensor cores, 3xFP16 split with power-of-two
                              scaling, FP32 accumulate                         */
 } kifmm_precision;
@@ -225,10 +229,16 @@ kifmm_status kifmm_backward(kifmm_plan *plan, const void *dL_dpot, const void *g
  * allocate device memory where they need the energy — a DEM step recorded into
  * a CUDA graph (cudaMalloc cannot be captured), an application whose device
  * memory belongs to its own pool, a time-critical loop that must not enter an
- * allocator.  It runs the same deterministic chunked reduction as the energy
- * output of kifmm_evaluate, with its partial sums in a fixed array of 16384
- * doubles (128 KiB) that lives in the library's device image; every GPU that
- * loads the library keeps that array until the process exits.
+ * allocator.  It sums q_i pot_i over all n entries in the caller's order with
+ * a fixed-chunk two-stage scheme (FP64 partial sums of 4096 entries, then one
+ * ordered sum of the partials), so its result is deterministic and equal to
+ * the energy output of kifmm_evaluate up to rounding (evaluate sums FP64
+ * internal potentials per system; this call sums the pot it is given, so in
+ * FP32 the two differ at the level of FP32 rounding of pot).  Given the
+ * particles of several systems it returns their total energy.  The partial
+ * sums live in a fixed array of 16384 doubles (128 KiB) in the library's
+ * device image; every GPU that loads the library keeps that array until the
+ * process exits.
  * n: number of particles, at most 67,108,864 (16384 chunks of 4096); larger n
  *   returns KIFMM_ERR_CAPACITY without launching anything.
  * dtype: kifmm_dtype of q and pot.  q, pot (device, [n]): charges and the
@@ -337,25 +347,6 @@ typedef struct {
 } kifmm_tuning_t;
 kifmm_status kifmm_get_tuning(kifmm_plan *plan, kifmm_tuning_t *out);
 
-/* Peak rates of the units the hot path uses, measured on the current device
- * (no counterpart in the paper: roofline denominators).  FP32 and FP64 FMA
- * (2 flop each), FP32 reciprocal square roots per second (rsqrt.approx), and
- * the tcgen05 kind::f16 MMA in the M2L kernel's shape (M = 128, K = 16,
- * 64-byte swizzled K-major operands) for N = 160 and 256.  Runs for a few
- * tens of milliseconds on `stream` and synchronises; allocates 68 bytes of
- * scratch.  Errors: KIFMM_ERR_ARG (out NULL), KIFMM_ERR_CUDA,
- * KIFMM_ERR_TIMEOUT (an MMA wait ran out; the device stays usable). */
-typedef struct {
-    double fp32_fma_tflops;
-    double fp64_fma_tflops;
-    double rsqrt_per_s;
-    double f16_mma_n160_tflops;
-    double f16_mma_n256_tflops;
-    int sms;
-    double clock_mhz;
-} kifmm_peaks_t;
-kifmm_status kifmm_measure_peaks(kifmm_peaks_t *out, kifmm_stream_t stream);
-
 /* ------------------------------------------------------------------------
  * Introspection (tests and tools).  All outputs are host buffers sized by
  * the caller from kifmm_tree_info; nodes are in canonical order (system,
@@ -367,6 +358,8 @@ typedef struct {
     int max_level;
     int n_systems;
     int64_t n_u, n_v, n_w, n_x; /* total list entries */
+    int sort_passes;            /* 8-bit key digits the last build's radix sort
+                                   processed (from the most significant one) */
 } kifmm_tree_info_t;
 
 kifmm_status kifmm_tree_info(kifmm_plan *plan, kifmm_tree_info_t *info);

@@ -387,6 +387,32 @@ def operators(p: int, eps: float = 1e-12):
     return ops
 
 
+def operators_perturbed(p: int, seed: int, eps: float = 1e-12):
+    """The operators of ``operators(p, eps)`` recomputed as another correct
+    FP64 implementation might: every pseudo-inverse from its check-from-
+    equivalent matrix plus a random perturbation of norm 2^-53 ||K|| (the
+    backward error of any backward-stable SVD), every translation matrix
+    with each entry moved by up to one unit in its last place (the rounding
+    of one kernel evaluation).  Running the KIFMM with these and with the
+    unperturbed operators measures the rounding floor of the method itself:
+    how far two correct FP64 evaluations of it can lie apart."""
+    rng = np.random.default_rng(seed)
+    ops = dict(operators(p, eps))
+    S = ops["surf"]
+    unit = 2.0 ** -53
+
+    def pert(k):
+        e = rng.standard_normal(k.shape)
+        return k + unit * np.linalg.norm(k, 2) * e / np.linalg.norm(e, 2)
+
+    ops["up"] = svd_pinv_factors(pert(kernel_matrix(ALPHA_UC * S, ALPHA_UE * S)), eps)
+    ops["dn"] = svd_pinv_factors(pert(kernel_matrix(ALPHA_DC * S, ALPHA_DE * S)), eps)
+    for k in ("m2m", "l2l", "m2l"):
+        a = np.asarray(ops[k])
+        ops[k] = a * (1.0 + 2.0 * unit * rng.uniform(-1.0, 1.0, size=a.shape))
+    return ops
+
+
 M2L_GAP = 1.001
 
 

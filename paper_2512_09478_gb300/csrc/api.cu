@@ -223,7 +223,8 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     *out = nullptr;
     const kifmm_plan_desc &d = *desc;
     if (d.p < 2 || d.p > 10 || d.leaf_cap < 1 || d.max_depth < 1 || d.max_depth > kMaxLevel) return KIFMM_ERR_ARG;
-    if (d.precision < KIFMM_FP64 || d.precision > KIFMM_MIXED_FP16) return KIFMM_ERR_ARG;
+    if (d.precision != KIFMM_FP64 && d.precision != KIFMM_FP32 && d.precision != KIFMM_MIXED_FP16)
+        return KIFMM_ERR_ARG;
     if (d.n_max < 1 || d.n_max > (int64_t)0x7fffffff || d.n_systems_max < 1) return KIFMM_ERR_ARG;
     if (d.dtype != KIFMM_DTYPE_F32 && d.dtype != KIFMM_DTYPE_F64) return KIFMM_ERR_ARG;
     if (!(d.pinv_eps >= 0.0) || d.pinv_eps >= 1.0) return KIFMM_ERR_ARG;
@@ -255,7 +256,6 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     cudaError_t e = build_operators(P, err);
     if (e == cudaErrorInvalidValue) return fail(KIFMM_ERR_ARG);
     if (e != cudaSuccess) return fail(KIFMM_ERR_CUDA);
-    if (d.precision == KIFMM_MIXED_TF32) return fail(KIFMM_ERR_ARG);  // not built yet
     if (d.precision == KIFMM_MIXED_FP16) {
         e = m2l_tensor_setup(P);
         if (e == cudaErrorNotSupported) return fail(KIFMM_ERR_ARG);
@@ -537,6 +537,7 @@ kifmm_status kifmm_tree_info(kifmm_plan *pl, kifmm_tree_info_t *info) {
     info->n_v = P.n_v;
     info->n_w = P.n_w;
     info->n_x = P.n_x;
+    info->sort_passes = P.sort_passes;
     return KIFMM_OK;
 }
 

@@ -933,7 +933,7 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     KIFMM_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(T) * (size_t)P.nb * ns, s));
     const bool split_mean = !P.f64;  // FP32-based modes: d = dbar (FP64) + mean-free FP32 vector
     if (split_mean) KIFMM_CUDA_TRY(cudaMemsetAsync(P.dbar, 0, sizeof(double) * (size_t)P.nb, s));
-    const bool tensor = (P.desc.precision == KIFMM_MIXED_TF32 || P.desc.precision == KIFMM_MIXED_FP16);
+    const bool tensor = (P.desc.precision == KIFMM_MIXED_FP16);
     if (tensor) {
         KIFMM_CUDA_TRY(m2l_tensor(P, s));
     } else {

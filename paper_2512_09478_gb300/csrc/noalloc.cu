@@ -5,11 +5,11 @@
 // cannot call cudaMalloc during capture; a host application that hands all
 // device memory to its own pool may forbid allocations by libraries; a
 // time-critical integration loop may not afford a trip through an allocator.
-// kifmm_energy_noalloc computes U = 1/2 sum_i q_i pot_i with the same
-// deterministic two-stage reduction (fixed 4096-particle chunks, then one
-// ordered sum of the chunk partials) that kifmm_evaluate uses for its energy
-// output, but keeps the partials in a fixed array that is part of the
-// library's device image, not in plan workspace.
+// kifmm_energy_noalloc computes U = 1/2 sum_i q_i pot_i with a deterministic
+// two-stage reduction (fixed 4096-particle chunks, then one ordered sum of the
+// chunk partials), the scheme kifmm_evaluate uses for its energy output, and
+// equal to that output up to rounding; it keeps the partials in a fixed array
+// that is part of the library's device image, not in plan workspace.
 #include <mutex>
 
 #include "common.cuh"

@@ -1,6 +1,6 @@
 // Inline-PTX helpers for the Blackwell tensor-core kernels (tcgen05, TMEM,
-// mbarrier, cp.async / bulk copies), shared by the M2L kernel and the peak
-// microbenchmarks.  Every wait is bounded (kWaitIters polls).
+// mbarrier, cp.async / bulk copies) of the M2L kernel.  Every wait is bounded
+// (kWaitIters polls).
 #pragma once
 #include <cstdint>
 

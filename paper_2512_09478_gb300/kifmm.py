@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libkifmm.so")
 
 OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
-PRECISIONS = {"fp64": 0, "fp32": 1, "mixed_tf32": 2, "mixed_fp16": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed_fp16": 3}
 LIST_KINDS = {"U": 0, "V": 1, "W": 2, "X": 3}
 
 
@@ -37,7 +37,7 @@ class PlanDesc(ctypes.Structure):
 class TreeInfo(ctypes.Structure):
     _fields_ = [("n_particles", ctypes.c_int64), ("n_boxes", ctypes.c_int64), ("max_level", ctypes.c_int),
                 ("n_systems", ctypes.c_int), ("n_u", ctypes.c_int64), ("n_v", ctypes.c_int64),
-                ("n_w", ctypes.c_int64), ("n_x", ctypes.c_int64)]
+                ("n_w", ctypes.c_int64), ("n_x", ctypes.c_int64), ("sort_passes", ctypes.c_int)]
 
 
 STAGES = ["tree", "p2m", "m2m", "m2l", "p2l", "l2l", "leaf", "p2p", "out"]
@@ -53,18 +53,12 @@ class TuningT(ctypes.Structure):
                 ("leaf_groups", ctypes.c_int * 16), ("m2l_rank_out", ctypes.c_int), ("m2l_rank_in", ctypes.c_int)]
 
 
-class PeaksT(ctypes.Structure):
-    _fields_ = [("fp32_fma_tflops", ctypes.c_double), ("fp64_fma_tflops", ctypes.c_double),
-                ("rsqrt_per_s", ctypes.c_double), ("f16_mma_n160_tflops", ctypes.c_double),
-                ("f16_mma_n256_tflops", ctypes.c_double), ("sms", ctypes.c_int), ("clock_mhz", ctypes.c_double)]
-
-
 _LIB = None
 EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifmm_evaluate",
            "kifmm_clump_reduce", "kifmm_backward", "kifmm_get_device_status", "kifmm_status_string",
            "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
            "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources",
-           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_measure_peaks", "kifmm_refresh_sources", "kifmm_lr_stride", "kifmm_far_image_operator"]
+           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_refresh_sources", "kifmm_lr_stride", "kifmm_far_image_operator"]
 
 
 def load(path: str = LIB_PATH):
@@ -147,6 +141,9 @@ class Plan:
         self.n = 0
         self.n_systems = 0
         self._offsets = None
+        # bumped whenever the plan's sources change: an autograd backward
+        # checks that the plan still holds the sources of its forward
+        self.generation = 0
 
     def close(self):
         if getattr(self, "_h", None):
@@ -172,6 +169,7 @@ class Plan:
         self.n = n
         self.n_systems = len(off) - 1
         self._offsets = off
+        self.generation += 1
 
     def update_sources(self, xyz: torch.Tensor, q: torch.Tensor, stream=None):
         """New positions/charges for the same particles, tree and lists frozen."""
@@ -179,6 +177,7 @@ class Plan:
         assert self.n == 0 or xyz.shape[0] == self.n  # n == 0: the library reports the state error
         _check(load().kifmm_update_sources(self._h, _ptr(xyz.contiguous()), _ptr(q.contiguous()),
                                            _stream(stream)), "kifmm_update_sources")
+        self.generation += 1
 
     def refresh_sources(self, xyz: torch.Tensor, q: torch.Tensor, skin: float = 0.05, stream=None) -> bool:
         """update_sources if every particle is still within its leaf (grown by
@@ -189,6 +188,7 @@ class Plan:
         reused = ctypes.c_int(0)
         _check(load().kifmm_refresh_sources(self._h, _ptr(xyz.contiguous()), _ptr(q.contiguous()), float(skin),
                                             ctypes.byref(reused), _stream(stream)), "kifmm_refresh_sources")
+        self.generation += 1
         return bool(reused.value)
 
     def evaluate(self, pot=None, grad=None, energy=None, want_pot=True, want_grad=True, want_energy=False,
@@ -323,20 +323,34 @@ def far_image_operator(p: int, cell: float) -> np.ndarray:
 
 def energy_noalloc(q: torch.Tensor, pot: torch.Tensor, out: torch.Tensor = None, stream=None) -> torch.Tensor:
     """U = 1/2 sum q pot through kifmm_energy_noalloc (the library allocates
-    nothing; ``out`` is a one-element float64 device tensor, created here if
-    not given)."""
+    nothing; ``out`` is a float64 device tensor whose first element receives
+    U, created here if not given).  q and pot: float32 or float64 (the same),
+    on one CUDA device; the call runs with that device current."""
     lib = load()
     if not hasattr(lib, "_noalloc_typed"):
         lib.kifmm_energy_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p]
         lib.kifmm_energy_noalloc.restype = ctypes.c_int
         lib._noalloc_typed = True
-    assert q.is_cuda and pot.is_cuda and q.dtype == pot.dtype and q.numel() == pot.numel()
+    if not (q.is_cuda and pot.is_cuda and q.device == pot.device):
+        raise ValueError("q and pot must be CUDA tensors on one device")
+    if q.dtype not in (torch.float32, torch.float64) or pot.dtype != q.dtype:
+        raise TypeError("q and pot must both be float32 or both float64")
+    if q.numel() != pot.numel():
+        raise ValueError("q and pot differ in size")
     if out is None:
         out = torch.empty(1, dtype=torch.float64, device=q.device)
+    if out.dtype != torch.float64 or out.device != q.device or out.numel() < 1 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 tensor of at least one element on q's device")
     dt = 1 if q.dtype == torch.float64 else 0
-    _check(lib.kifmm_energy_noalloc(q.numel(), dt, _ptr(q.contiguous()), _ptr(pot.contiguous()), _ptr(out),
-                                    _stream(stream)), "kifmm_energy_noalloc")
+    with torch.cuda.device(q.device):
+        qc, pc = q.contiguous(), pot.contiguous()
+        if stream is not None:
+            # the temporaries (if any) are read on `stream`: keep them alive until it has
+            qc.record_stream(stream)
+            pc.record_stream(stream)
+        _check(lib.kifmm_energy_noalloc(q.numel(), dt, _ptr(qc), _ptr(pc), _ptr(out), _stream(stream)),
+               "kifmm_energy_noalloc")
     return out
 
 
@@ -355,6 +369,7 @@ class KifmmPotential(torch.autograd.Function):
             plan.update_sources(x.detach(), q.detach())
         pot, grad, _ = plan.evaluate()
         ctx.plan = plan
+        ctx.generation = plan.generation
         ctx.save_for_backward(grad)
         ctx.mark_non_differentiable(grad)
         return pot, grad
@@ -362,6 +377,9 @@ class KifmmPotential(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g_pot, g_grad):
         (grad,) = ctx.saved_tensors
+        if ctx.plan.generation != ctx.generation:
+            raise RuntimeError("the plan's sources changed after this forward: backward needs the plan to "
+                               "hold the forward's sources (one plan per differentiated evaluation)")
         if g_grad is not None and torch.any(g_grad != 0):
             raise NotImplementedError("losses on the gradient output are not differentiated")
         dq, dx = ctx.plan.backward(g_pot, grad)
@@ -377,12 +395,3 @@ def potential(x, q, plan, rebuild=True):
 def energy(x, q, plan, rebuild=True):
     """Differentiable long-range energy U = 1/2 sum_i q_i pot_i (Sec. 2.4)."""
     return 0.5 * torch.dot(q, potential(x, q, plan, rebuild))
-
-
-def measure_peaks() -> dict:
-    """Peak rates of the FP32/FP64 FMA, rsqrt and tcgen05 f16 MMA units of the
-    current device (kifmm_measure_peaks)."""
-    out = PeaksT()
-    _check(load().kifmm_measure_peaks(ctypes.byref(out), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
-           "kifmm_measure_peaks")
-    return {f: getattr(out, f) for f, _ in PeaksT._fields_}

@@ -146,7 +146,9 @@ def test_large_motion_rebuilds_like_set_sources():
     fresh = _plan(len(x), M=M)
     fresh.set_sources(_dev(x2), _dev(q))
     pot_f, grad_f, _ = fresh.evaluate()
-    assert plan.tree_info() == fresh.tree_info()
+    # the same tree (the sorted digit count may differ: it follows each plan's last depth)
+    strip = lambda d: {k: v for k, v in d.items() if k != "sort_passes"}
+    assert strip(plan.tree_info()) == strip(fresh.tree_info())
     k1, p1, l1 = plan.keys()
     k2, p2, l2 = fresh.keys()
     assert np.array_equal(k1, k2) and np.array_equal(l1, l2)
@@ -187,7 +189,9 @@ def test_refresh_with_several_systems():
                  dtype=torch.float64)
     fresh.set_sources(_dev(xm), _dev(q), sys_offsets=off)
     pot_f, _, energy_f = fresh.evaluate(want_energy=True)
-    assert plan.tree_info() == fresh.tree_info()
+    # the same tree (the sorted digit count may differ: it follows each plan's last depth)
+    strip = lambda d: {k: v for k, v in d.items() if k != "sort_passes"}
+    assert strip(plan.tree_info()) == strip(fresh.tree_info())
     assert O.rel_l2(pot.cpu().numpy(), pot_f.cpu().numpy()) <= 1e-14
     assert O.rel_l2(energy.cpu().numpy(), energy_f.cpu().numpy()) <= 1e-14
 

@@ -134,3 +134,27 @@ def test_clump_reduce_brute_force():
     # total torque about the origin: sum_c (T_c + X_c x F_c) = sum_k x_k x F_k = 0
     Ttot = T.sum(axis=0) + np.cross(centres, F).sum(axis=0)
     assert np.linalg.norm(Ttot) < 1e-10 * scale * np.abs(x).max()
+
+
+def test_perturbed_operators_are_rounding_level():
+    """operators_perturbed (the parity tests' rounding floor) moves every
+    translation entry by about one unit in the last place, keeps the
+    pseudo-inverse factors those of a matrix within 2^-53 ||K|| of K (the
+    truncated rank is unchanged), and moves the KIFMM output far less than
+    the method's own error: a rounding floor, not a different method."""
+    p = 6
+    a, b = O.operators(p), O.operators_perturbed(p, 1)
+    for k in ("m2m", "l2l", "m2l"):
+        rel = np.abs(b[k] - a[k]) / np.abs(a[k])
+        # the drawn relative move (at most 2^-52) plus the rounding of the product
+        assert rel.max() <= 2.0 ** -52 + 2.0 ** -53 and rel.max() > 0
+    for k in ("up", "dn"):
+        assert np.count_nonzero(a[k][1]) == np.count_nonzero(b[k][1])
+        assert np.allclose(b[k][3], a[k][3], rtol=0, atol=1e-14 * a[k][3][0])
+    x, q = G.uniform_charges(1500, 5)
+    p0, g0, _ = O.kifmm(x, q, p=p, leaf_cap=32)
+    p1, g1, _ = O.kifmm(x, q, p=p, leaf_cap=32, ops=b)
+    pd, gd = O.direct(x, q)
+    floor_p, floor_g = O.rel_l2(p1, p0), O.rel_l2(g1, g0)
+    assert 0 < floor_p < 1e-12 and 0 < floor_g < 1e-12
+    assert floor_p < 1e-6 * O.rel_l2(p0, pd) and floor_g < 1e-6 * O.rel_l2(g0, gd)

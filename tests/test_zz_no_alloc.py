@@ -50,8 +50,33 @@ def test_noalloc_energy_matches_evaluate_twice():
     assert energy_noalloc(qa, pa).item() == first
 
 
+def test_noalloc_fp32_matches_evaluate_within_rounding():
+    """FP32 q and pot: the call sums the FP32 pot it is given, evaluate sums its
+    FP64 internal potentials, so the two agree to FP32 rounding of pot (2^-24
+    relative per term; the bound below is that times sum |q pot| / |sum q pot|)."""
+    from paper_2512_09478_gb300 import Plan
+    from paper_2512_09478_gb300.kifmm import energy_noalloc
+    x, q = G.uniform_charges(9000, 83)
+    plan = Plan(p=4, leaf_cap=32, precision="fp32", n_max=len(x), dtype=torch.float32)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    qt = torch.tensor(q, dtype=torch.float32, device="cuda")
+    plan.set_sources(xt, qt)
+    pot, _, energy = plan.evaluate(want_grad=False, want_energy=True)
+    for _ in range(2):
+        got = energy_noalloc(qt, pot).item()
+        e = energy.item()
+        terms = 0.5 * torch.sum(torch.abs(qt.double() * pot.double())).item()
+        assert abs(got - e) <= 2.0 ** -23 * terms + 1e-12 * abs(e)
+
+
+def test_noalloc_rejects_bad_dtype_on_the_host():
+    from paper_2512_09478_gb300.kifmm import energy_noalloc
+    q = torch.zeros(8, dtype=torch.float16, device="cuda")
+    with pytest.raises(TypeError):
+        energy_noalloc(q, q)
+
+
 def test_noalloc_rejects_oversize_without_work():
-    from paper_2512_09478_gb300 import KifmmError
     from paper_2512_09478_gb300.kifmm import load
     import ctypes
     lib = load()
@@ -59,7 +84,10 @@ def test_noalloc_rejects_oversize_without_work():
     q = torch.zeros(1, dtype=torch.float64, device="cuda")
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     energy_noalloc(q, q, out)
+    out.fill_(12345.0)  # sentinel: a refused call must leave it untouched
+    torch.cuda.synchronize()
     code = lib.kifmm_energy_noalloc(16384 * 4096 + 1, 1, ctypes.c_void_p(q.data_ptr()),
                                     ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(out.data_ptr()), None)
+    torch.cuda.synchronize()
     assert code == 2  # KIFMM_ERR_CAPACITY
-    assert KifmmError is not None
+    assert out.item() == 12345.0
