@@ -98,6 +98,8 @@ def parse():
                     help="fixed tile shapes (default: the library tunes them on the first, untimed, evaluate)")
     ap.add_argument("--m2l-eps-compare", type=float, default=1e-5,
                     help="also time the same step with the compressed M2L at this eps (0: skip)")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--compare", default="auto",
                     help="also time this precision on the same workload (auto: the workload's comparison "
                          "path, none: skip)")
@@ -430,12 +432,16 @@ def run_ours(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank)
     clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if args.profile_region:
+        torch.cuda.profiler.start()
     for k in range(args.steps):
         flush.fill_(k & 0xFF)  # evict the previous step's working set from L2 (not timed)
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
     torch.cuda.synchronize()
+    if args.profile_region:
+        torch.cuda.profiler.stop()
     clk = clocks.stop()
     if dist:
         torch.distributed.barrier()

@@ -213,15 +213,32 @@ kifmm_status kifmm_clump_reduce(kifmm_plan *plan, int64_t n_clumps, const int64_
 
 /*
  * Adjoint of evaluate with the tree frozen (not in the paper; it makes the
- * evaluation differentiable).  With pot = A(x) q the FMM operator and a loss
- * L with dL_dpot = w:
- *   dq = A^T w,   dx_k = w_k grad_k + q_k grad_{x_k} (A^T w)_k
- * computed by the transposed passes (no stored intermediates).
- * dL_dpot (device, [N]); grad (device, [N,3]): the forward gradient (coef
- * applied); dq (device, [N]), dx (device, [N,3]): outputs, caller order.
+ * evaluation differentiable, e.g. for a loss on the forces of Sec. 2.3-2.4).
+ * With pot = A(x) q and grad = G(x) q the FMM operators and a loss L with
+ * w = dL/dpot, g = dL/dgrad and u_s = dL/dU_s (U_s the energy of system s):
+ *   dq_j = (A^T w)_j + (G^T g)_j + u_s (pot_j + (A^T q)_j) / 2,
+ *   dx_k = w'_k grad_k + H_k g_k + q_k grad_{x_k}(A^T w' + G^T g)_k,
+ * with w' = w + u_s q / 2 and H_k the Hessian of the field at x_k; computed
+ * by the transposed passes (G^T g: the dipoles g on the same surfaces, lists
+ * and translation operators) and, for H g and the explicit energy term, from
+ * the last evaluate's equivalent densities and potentials.  No other
+ * intermediate is stored.
+ * dL_dpot (device, [N] or NULL), dL_dgrad (device, [N, 3] or NULL),
+ * dL_denergy (device, [n_systems] doubles or NULL): at least one is given.
+ * grad (device, [N, 3]): the forward gradient (coef applied); needed for dx
+ *   when dL_dpot or dL_denergy is given.
+ * dq (device, [N] or NULL), dx (device, [N, 3] or NULL): outputs, caller order.
+ * KIFMM_ERR_STATE when dL_dgrad or dL_denergy is given but no evaluate ran on
+ * the current sources (set_sources / update_sources / refresh_sources since),
+ * and when dL_denergy is given and another backward ran after that evaluate
+ * (the energy term reads the evaluate's potentials, which a backward
+ * overwrites).  The forward's equivalent densities are kept, so several
+ * backward calls with dL_dpot / dL_dgrad may follow one evaluate; the
+ * expansions (kifmm_copy_expansions) then show the transposed pass.  Never
+ * allocates.
  */
-kifmm_status kifmm_backward(kifmm_plan *plan, const void *dL_dpot, const void *grad, void *dq,
-                            void *dx, kifmm_stream_t stream);
+kifmm_status kifmm_backward(kifmm_plan *plan, const void *dL_dpot, const void *dL_dgrad, const double *dL_denergy,
+                            const void *grad, void *dq, void *dx, kifmm_stream_t stream);
 
 /*
  * Long-range energy U = 1/2 sum_i q_i pot_i without allocating anything.

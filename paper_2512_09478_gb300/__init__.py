@@ -3,4 +3,5 @@
 The compute path is the C-ABI library lib/libkifmm.so (CUDA kernels); the
 Python layer (kifmm.py) only marshals arguments.
 """
-from .kifmm import Plan, KifmmError, KifmmPotential, far_image_operator, load, lr_stride, PRECISIONS  # noqa: F401
+from .kifmm import (Plan, KifmmError, KifmmPotential, KifmmEnergy, energy, far_image_operator, field,  # noqa: F401
+                    load, lr_stride, potential, PRECISIONS)

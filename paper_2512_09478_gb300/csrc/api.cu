@@ -163,6 +163,8 @@ static cudaError_t ensure_box_arrays(Plan &P) {
         {&P.up_dens, esz * P.ns * cap},
         {&P.tmp_chk, esz * P.ns * cap},
         {&P.dn_dens, esz * P.ns * cap},
+        {&P.adj_e1, esz * P.ns * cap},
+        {&P.adj_e2, esz * P.ns * cap},
         {(void **)&P.dbar, sizeof(double) * cap},
         {&P.u_c, sizeof(float) * (size_t)P.m2l_rr * cap},
         {&P.d_c, sizeof(float) * (size_t)P.m2l_rl * cap},
@@ -275,6 +277,10 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {(void **)&P.keys_user, sizeof(uint64_t) * n}, {(void **)&P.perm, sizeof(uint32_t) * n},
         {&P.pts, esz * 4 * n},                         {(void **)&P.res, sizeof(double) * 4 * n},
         {&P.w_sorted, esz * n},
+        {&P.g_sorted, esz * 3 * n},
+        {(void **)&P.adj_hg, sizeof(double) * 4 * n},
+        {(void **)&P.adj_pd, sizeof(double) * 4 * n},
+        {(void **)&P.adj_pot, sizeof(double) * n},
         {&P.gemm_part, esz * 8 * kSplitTargets * (size_t)(P.ns + 1)},
         {(void **)&P.sys_off_d, sizeof(int64_t) * (P.sys_cap + 1)},
         {(void **)&P.lo_side, sizeof(double) * 4 * P.sys_cap},
@@ -420,16 +426,19 @@ kifmm_status kifmm_clump_reduce(kifmm_plan *pl, int64_t n_clumps, const int64_t 
     return from_cuda(run_clump_reduce(P, n_clumps, clump_offsets, xyz, q, grad, ref, force, torque, s));
 }
 
-kifmm_status kifmm_backward(kifmm_plan *pl, const void *dL_dpot, const void *grad, void *dq, void *dx,
-                            kifmm_stream_t stream) {
-    if (!pl || !dL_dpot) return KIFMM_ERR_ARG;
-    if (dx && !grad) return KIFMM_ERR_ARG;
+kifmm_status kifmm_backward(kifmm_plan *pl, const void *dL_dpot, const void *dL_dgrad, const double *dL_denergy,
+                            const void *grad, void *dq, void *dx, kifmm_stream_t stream) {
+    if (!pl || (!dL_dpot && !dL_dgrad && !dL_denergy)) return KIFMM_ERR_ARG;
+    if (dx && (dL_dpot || dL_denergy) && !grad) return KIFMM_ERR_ARG;
     Plan &P = pl->P;
     if (!P.has_sources) return KIFMM_ERR_STATE;
+    // the Hessian and energy terms read the last evaluate's field
+    if ((dL_dgrad || dL_denergy) && !P.fwd_valid) return KIFMM_ERR_STATE;
+    if (dL_denergy && !P.fwd_res_valid) return KIFMM_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     P.last_stream = s;
     const long long l0 = g_launches;
-    cudaError_t e = run_backward(P, dL_dpot, grad, dq, dx, s);
+    cudaError_t e = run_backward(P, dL_dpot, dL_dgrad, dL_denergy, grad, dq, dx, s);
     P.launches += g_launches - l0;
     return from_cuda(e);
 }

@@ -46,9 +46,14 @@ template <typename T>
 __global__ void k_p2m(const int32_t *__restrict__ leaves, const int32_t *__restrict__ lvl,
                       const int32_t *__restrict__ first, const int32_t *__restrict__ cnt,
                       const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, int ns,
-                      T *__restrict__ u, const T *__restrict__ wts = nullptr, int adj = 0) {
+                      T *__restrict__ u, const T *__restrict__ wts = nullptr, int adj = 0,
+                      const T *__restrict__ dip = nullptr) {
+    // Adjoint with dip ([N][3] sorted, root units): each particle also carries
+    // the dipole dL/dgrad, whose field at the surface point y is
+    // g . (y - x) / |y - x|^3 (the transpose of the gradient evaluation).
     extern __shared__ __align__(16) unsigned char p2m_sm[];
     T *sx = (T *)p2m_sm, *sy = sx + blockDim.x, *sz = sy + blockDim.x, *sq = sz + blockDim.x;
+    T *gx = sq + blockDim.x, *gy = gx + blockDim.x, *gz = gy + blockDim.x;
     const int b = leaves[blockIdx.x];
     const T h = box_half<T>(lvl[b]), hinv = T(1) / h;
     const int n = cnt[b], f = first[b];
@@ -70,13 +75,27 @@ __global__ void k_p2m(const int32_t *__restrict__ leaves, const int32_t *__restr
                 sy[threadIdx.x] = v.y * hinv;
                 sz[threadIdx.x] = v.z * hinv;
                 sq[threadIdx.x] = wts ? wts[f + c0 + threadIdx.x] : v.w;
+                if (dip) {  // in box units the dipole term carries 1/h
+                    const size_t k = 3 * (size_t)(f + c0 + threadIdx.x);
+                    gx[threadIdx.x] = dip[k] * hinv;
+                    gy[threadIdx.x] = dip[k + 1] * hinv;
+                    gz[threadIdx.x] = dip[k + 2] * hinv;
+                }
             }
             __syncthreads();
             const int m = min((int)blockDim.x, n - c0);
+            if (dip) {
+                for (int i = 0; i < m; ++i) {
+                    const T rx = px - sx[i], ry = py - sy[i], rz = pz - sz[i];
+                    const T ri = rsqrt_t<T>(rx * rx + ry * ry + rz * rz);
+                    acc += sq[i] * ri + (gx[i] * rx + gy[i] * ry + gz[i] * rz) * (ri * ri * ri);
+                }
+            } else {
 #pragma unroll 4
-            for (int i = 0; i < m; ++i) {
-                const T rx = px - sx[i], ry = py - sy[i], rz = pz - sz[i];
-                acc += sq[i] * rsqrt_t<T>(rx * rx + ry * ry + rz * rz);
+                for (int i = 0; i < m; ++i) {
+                    const T rx = px - sx[i], ry = py - sy[i], rz = pz - sz[i];
+                    acc += sq[i] * rsqrt_t<T>(rx * rx + ry * ry + rz * rz);
+                }
             }
         }
         // forward: u = sum q / |UC - x| (1/h from the unit surface); adjoint of
@@ -94,10 +113,12 @@ __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict_
                       const int32_t *__restrict__ first, const int32_t *__restrict__ cnt,
                       const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, int ns,
                       T *__restrict__ d, const T *__restrict__ wts = nullptr, int adj = 0,
-                      double *__restrict__ dbar = nullptr) {
+                      double *__restrict__ dbar = nullptr, const T *__restrict__ dip = nullptr) {
     // With dbar (FP32-based modes) the mean of this box's contribution goes
-    // to dbar and only the mean-free remainder to d.
+    // to dbar and only the mean-free remainder to d.  With dip (adjoint of
+    // M2P under a loss on the gradient) every particle also carries a dipole.
     __shared__ T sx[kLeafThreads], sy[kLeafThreads], sz[kLeafThreads], sq[kLeafThreads];
+    __shared__ T gx[kLeafThreads], gy[kLeafThreads], gz[kLeafThreads];
     __shared__ T cv[kMaxNs];
     __shared__ double red[kLeafThreads / 32];
     const int b = blockIdx.x;
@@ -129,10 +150,24 @@ __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict_
                     sy[threadIdx.x] = (oy + v.y) * hinv;
                     sz[threadIdx.x] = (oz + v.z) * hinv;
                     sq[threadIdx.x] = wts ? wts[f + c0 + threadIdx.x] : v.w;
+                    if (dip) {
+                        const size_t k = 3 * (size_t)(f + c0 + threadIdx.x);
+                        gx[threadIdx.x] = dip[k] * hinv;
+                        gy[threadIdx.x] = dip[k + 1] * hinv;
+                        gz[threadIdx.x] = dip[k + 2] * hinv;
+                    }
                 }
                 __syncthreads();
                 const int m = min(kLeafThreads, n - c0);
-                for (int i = 0; i < m; ++i) acc += sq[i] * lap_pot<T>(px - sx[i], py - sy[i], pz - sz[i]);
+                if (dip) {
+                    for (int i = 0; i < m; ++i) {
+                        const T rx = px - sx[i], ry = py - sy[i], rz = pz - sz[i];
+                        const T ri = rsqrt_t<T>(rx * rx + ry * ry + rz * rz);
+                        acc += sq[i] * ri + (gx[i] * rx + gy[i] * ry + gz[i] * rz) * (ri * ri * ri);
+                    }
+                } else {
+                    for (int i = 0; i < m; ++i) acc += sq[i] * lap_pot<T>(px - sx[i], py - sy[i], pz - sz[i]);
+                }
             }
         }
         if (j < ns) {
@@ -424,6 +459,11 @@ struct LeafAcc {
     T part[TPL][4];             // plain partial sums since the last flush
     T acc[TPL][4], cmp[TPL][4]; // compensated totals (two-sum)
     int pend;                   // sources per lane in part (warp-uniform bound)
+    // FP32: the pair loop runs on packed f32x2 arithmetic, two sources per
+    // instruction: negated targets duplicated into both halves, and plain
+    // partial sums per half (folded into part at each flush)
+    float2 ntx[TPL], nty[TPL], ntz[TPL];
+    float2 pk[TPL][4];
 };
 
 template <typename T, int TPL>
@@ -432,6 +472,10 @@ __device__ __forceinline__ void leaf_flush(LeafAcc<T, TPL> &L) {
     for (int k = 0; k < TPL; ++k)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
+            if constexpr (sizeof(T) == 4) {
+                L.part[k][c] = L.pk[k][c].x + L.pk[k][c].y;
+                L.pk[k][c] = make_float2(0.f, 0.f);
+            }
             T sum, err;
             two_sum<T>(L.acc[k][c], L.part[k][c], sum, err);
             L.acc[k][c] = sum;
@@ -501,12 +545,84 @@ __device__ __forceinline__ void leaf_range(LeafAcc<T, TPL> &L, const typename Ve
     }
 }
 
+// FP32 chunks are staged as source pairs: pair p holds sources a and a + G
+// with a = (p / G) 2G + p % G, as eight floats (x_a x_b y_a y_b z_a z_b w_a
+// w_b), so group g (p % G = g) meets its own sources g, g + G, g + 2G, ...
+// two at a time, each pair already in the register halves of the f32x2
+// instructions.  Entries beyond the chunk's sources hold a null source
+// (weight 0, far away), which adds exactly zero.
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Pairs i in [ia, ie) of group grp (pair index grp + i G).
+template <int TPL, int G, bool CHECK>
+__device__ __forceinline__ void leaf_pairs(LeafAcc<float, TPL> &L, const float4 *__restrict__ pairs, int ia, int ie,
+                                           int grp) {
+    constexpr int UNR = TPL == 1 ? 4 : 1;  // eight pair evaluations in flight per lane (the FP32 chains are latency-bound)
+#pragma unroll UNR
+    for (int i = ia; i < ie; ++i) {
+        const int p = grp + i * G;
+        const float4 A = pairs[2 * p], B = pairs[2 * p + 1];
+        const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
+        const float2 sz = make_float2(B.x, B.y), sw = make_float2(B.z, B.w);
+#pragma unroll
+        for (int k = 0; k < TPL; ++k) {
+            // r = source - target (the gradient sum below is then + r w / r^3)
+            const float2 rx = __fadd2_rn(sx, L.ntx[k]);
+            const float2 ry = __fadd2_rn(sy, L.nty[k]);
+            const float2 rz = __fadd2_rn(sz, L.ntz[k]);
+            float2 r2 = __fmul2_rn(rx, rx);
+            r2 = __ffma2_rn(ry, ry, r2);
+            r2 = __ffma2_rn(rz, rz, r2);
+            float2 ri;
+            if constexpr (CHECK) {
+                ri.x = r2.x > 0.f ? rsqrt_t<float>(r2.x) : 0.f;
+                ri.y = r2.y > 0.f ? rsqrt_t<float>(r2.y) : 0.f;
+            } else {
+                ri.x = rsqrt_t<float>(r2.x);
+                ri.y = rsqrt_t<float>(r2.y);
+            }
+            const float2 wr = __fmul2_rn(sw, ri);
+            const float2 wr3 = __fmul2_rn(wr, __fmul2_rn(ri, ri));
+            L.pk[k][0] = __fadd2_rn(L.pk[k][0], wr);
+            L.pk[k][1] = __ffma2_rn(rx, wr3, L.pk[k][1]);
+            L.pk[k][2] = __ffma2_rn(ry, wr3, L.pk[k][2]);
+            L.pk[k][3] = __ffma2_rn(rz, wr3, L.pk[k][3]);
+        }
+    }
+}
+
+// A staged FP32 chunk of m sources (pair layout); [olo, ohi) are the leaf's
+// own particles: the pairs of group grp that touch them take the r = 0 test.
+// Sub-blocks of kLFlush / 2 pairs keep every plain partial sum to at most
+// kLFlush terms.
+template <int TPL, int G>
+__device__ __forceinline__ void leaf_chunk_pk(LeafAcc<float, TPL> &L, const float4 *pairs, int m, int olo, int ohi,
+                                              int grp) {
+    const int np = grp < m ? (m - grp + 2 * G - 1) / (2 * G) : 0;
+    // pair i holds this group's sources 2 i G + grp and 2 i G + grp + G
+    const int i_lo = max(0, floor_div(olo - grp - G + 2 * G - 1, 2 * G));
+    const int i_hi = max(0, floor_div(ohi - grp + 2 * G - 1, 2 * G));
+    for (int i0 = 0; i0 < np; i0 += kLFlush / 2) {
+        const int i1 = min(np, i0 + kLFlush / 2);
+        const int a = max(i0, min(i1, i_lo)), e = max(a, min(i1, i_hi));
+        leaf_pairs<TPL, G, false>(L, pairs, i0, a, grp);
+        if (a < e) leaf_pairs<TPL, G, true>(L, pairs, a, e, grp);
+        leaf_pairs<TPL, G, false>(L, pairs, e, i1, grp);
+        L.pend += 2 * (i1 - i0);
+        if (L.pend >= kLFlush) leaf_flush<float, TPL>(L);
+    }
+}
+
 // A staged chunk of m sources; [olo, ohi) are the leaf's own particles.
 // Sub-blocks of kLFlush G sources keep every plain partial sum to at most
 // kLFlush terms.
 template <typename T, int TPL, int G>
 __device__ __forceinline__ void leaf_chunk(LeafAcc<T, TPL> &L, const typename Vec4<T>::type *buf, int m, int olo,
                                            int ohi, int grp) {
+    if constexpr (sizeof(T) == 4) {
+        leaf_chunk_pk<TPL, G>(L, buf, m, olo, ohi, grp);
+        return;
+    }
     for (int s0 = 0; s0 < m; s0 += kLFlush * G) {
         const int s1 = min(m, s0 + kLFlush * G);
         const int a = max(s0, min(s1, olo)), e = max(a, min(s1, ohi));
@@ -555,21 +671,37 @@ __device__ __forceinline__ void leaf_fetch(const LeafSmem<T> &S, int c, int tota
     }
 }
 
-// Place fetched entries (segment transform applied) in staging buffer slot.
-template <typename T>
+// Place fetched entries (segment transform applied) in staging buffer slot;
+// FP32 in the pair layout of leaf_chunk_pk, with null sources past the end.
+template <typename T, int G>
 __device__ __forceinline__ void leaf_store(LeafSmem<T> &S, int slot, const typename Vec4<T>::type (&raw)[kLK],
                                            const int (&rs)[kLK]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < kLK; ++i) {
-        if (rs[i] < 0) continue;
-        const LeafSeg<T> g = S.seg[rs[i]];
         typename Vec4<T>::type v;
-        v.x = g.r * raw[i].x + g.ox;
-        v.y = g.r * raw[i].y + g.oy;
-        v.z = g.r * raw[i].z + g.oz;
-        v.w = raw[i].w * g.hw;
-        S.buf[slot][lane + 32 * i] = v;
+        if (rs[i] >= 0) {
+            const LeafSeg<T> g = S.seg[rs[i]];
+            v.x = g.r * raw[i].x + g.ox;
+            v.y = g.r * raw[i].y + g.oy;
+            v.z = g.r * raw[i].z + g.oz;
+            v.w = raw[i].w * g.hw;
+        } else {
+            if constexpr (sizeof(T) == 8) continue;
+            v.x = v.y = v.z = T(1e4);  // null source: weight 0 at a finite distance
+            v.w = T(0);
+        }
+        const int j = lane + 32 * i;
+        if constexpr (sizeof(T) == 4) {
+            const int r = j % (2 * G), pair = (j / (2 * G)) * G + r % G, h = r / G;
+            float *P = reinterpret_cast<float *>(&S.buf[slot][0]) + 8 * pair;
+            P[h] = v.x;
+            P[2 + h] = v.y;
+            P[4 + h] = v.z;
+            P[6 + h] = v.w;
+        } else {
+            S.buf[slot][j] = v;
+        }
     }
 }
 
@@ -591,8 +723,16 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
         L.tx[k] = v.x;
         L.ty[k] = v.y;
         L.tz[k] = v.z;
+        if constexpr (sizeof(T) == 4) {
+            L.ntx[k] = make_float2(-(float)v.x, -(float)v.x);
+            L.nty[k] = make_float2(-(float)v.y, -(float)v.y);
+            L.ntz[k] = make_float2(-(float)v.z, -(float)v.z);
+        }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) L.part[k][c] = L.acc[k][c] = L.cmp[k][c] = T(0);
+        for (int c = 0; c < 4; ++c) {
+            L.part[k][c] = L.acc[k][c] = L.cmp[k][c] = T(0);
+            L.pk[k][c] = make_float2(0.f, 0.f);
+        }
     }
     L.pend = 0;
     const uint32_t w0 = C.w_ptr[b], u0 = C.u_ptr[b];
@@ -653,7 +793,7 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
         for (int c = 0; c < nchunks; ++c) {
             // double-buffered: the slot written here was last read two chunks ago
             leaf_fetch<T>(S, c, total, nb, pts, surf, W, raw, rs);
-            leaf_store<T>(S, c & 1, raw, rs);
+            leaf_store<T, G>(S, c & 1, raw, rs);
             __syncwarp();
             const int c0 = c * kLChunk;
             leaf_chunk<T, TPL, G>(L, S.buf[c & 1], min(kLChunk, total - c0), olo - c0, ohi - c0, grp);
@@ -710,7 +850,7 @@ __global__ void k_leaf_partition(int64_t n_leaves, const int32_t *__restrict__ l
 }
 
 template <typename T, int TPL, int G>
-__global__ void __launch_bounds__(32 * kLW, sizeof(T) == 4 ? (TPL == 1 ? 6 : 5) : 2)
+__global__ void __launch_bounds__(32 * kLW, sizeof(T) == 4 ? (TPL == 1 ? 5 : 4) : 2)
     k_leaf_all(LeafCtx C, const int2 *__restrict__ list, const int32_t *__restrict__ count,
                const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, LeafW<T> W,
                double4 *__restrict__ res) {
@@ -729,7 +869,7 @@ void leaf_launch_variant(const Plan &P, const LeafCtx &C, int v, const typename 
     // on the variant's own stream, after the partition; joined back below
     cudaStream_t s = P.leaf_streams[v];
     cudaStreamWaitEvent(s, P.leaf_fork, 0);
-    constexpr int occ = sizeof(T) == 4 ? (TPL == 1 ? 6 : 5) : 2;
+    constexpr int occ = sizeof(T) == 4 ? (TPL == 1 ? 5 : 4) : 2;
     const int64_t want = (P.n_leaves + kLW - 1) / kLW;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P.num_sms * occ));
     ++g_launches, k_leaf_all<T, TPL, G><<<g, 32 * kLW, 0, s>>>(C, P.leaf_vlist + (int64_t)v * P.leaf_item_cap,
@@ -842,7 +982,7 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 // k_p2m launch shape: a thread per check point, four staged values per thread.
 inline int p2m_threads(const Plan &P) { return (P.ns + 31) / 32 * 32; }
 template <typename T>
-inline size_t p2m_smem(const Plan &P) { return 4 * sizeof(T) * (size_t)p2m_threads(P); }
+inline size_t p2m_smem(const Plan &P) { return 7 * sizeof(T) * (size_t)p2m_threads(P); }
 
 // Classes c < ncls own targets [starts[c], starts[c + 1]); one launch.
 template <typename T, class G>
@@ -1011,22 +1151,83 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
                                                                          P.lo_side, P.coef, P.n_sys, energy);
     }
     stage_end(P, KIFMM_STAGE_OUT, s);
+    P.fwd_valid = P.fwd_res_valid = true;
     return cudaGetLastError();
 }
 
-// Adjoint weights in sorted order.
-template <typename TI, typename T>
-__global__ void k_gather_w(int64_t n, const uint32_t *__restrict__ perm, const TI *__restrict__ w, T *__restrict__ ws) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) ws[i] = (T)w[perm[i]];
+// Per-particle system (the last offset at or below the caller index j).
+__device__ __forceinline__ int system_of(const int64_t *__restrict__ off, int S, uint32_t j) {
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= (int64_t)j) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
-// dq = c1 psi, dx = w grad + c1 / side * q grad(psi), c1 = coef / (4 pi side).
+// Adjoint weights in sorted order: ws = dL/dpot + (1/2) dL/dU_s q (the energy
+// U_s = 1/2 sum q pot of the particle's system s, through its pot); with an
+// energy loss the forward potential (root units) is kept for the explicit
+// (1/2) dL/dU pot term of dq, since the transposed passes overwrite it.
+template <typename TI, typename T>
+__global__ void k_adj_weights(int64_t n, const uint32_t *__restrict__ perm, const int64_t *__restrict__ off, int S,
+                              const typename Vec4<T>::type *__restrict__ pts, const TI *__restrict__ w,
+                              const double *__restrict__ dLdU, const double4 *__restrict__ res, T *__restrict__ ws,
+                              double *__restrict__ fwd_pot) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    double v = w ? (double)w[j] : 0.0;
+    if (dLdU) {
+        v += 0.5 * dLdU[system_of(off, S, j)] * (double)pts[i].w;
+        fwd_pot[i] = res[i].x;
+    }
+    ws[i] = (T)v;
+}
+
+// dq = c1 (psi + pd) (+ 1/2 dL/dU c1 pot), dx = w_tot grad + c2 (q grad(psi + pd) + hg),
+// c1 = coef / (4 pi side), c2 = c1 / side; w_tot = dL/dpot + 1/2 dL/dU q.
 template <typename TO, typename T>
 __global__ void k_finalize_adj(int64_t n, const double4 *__restrict__ res, const uint32_t *__restrict__ perm,
                                const int64_t *__restrict__ off, int S, const double *__restrict__ out_scale,
                                const typename Vec4<T>::type *__restrict__ pts, const TO *__restrict__ w,
+                               const double *__restrict__ dLdU, const double *__restrict__ fwd_pot,
+                               const double4 *__restrict__ hg, const double4 *__restrict__ pd,
                                const TO *__restrict__ grad, TO *dq, TO *dx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    const int s = system_of(off, S, j);
+    const double c1 = out_scale[2 * s], c2 = out_scale[2 * s + 1];  // coef / (4 pi side), / side^2
+    double4 r = res[i];
+    if (pd) {
+        const double4 e = pd[i];
+        r.x += e.x, r.y += e.y, r.z += e.z, r.w += e.w;
+    }
+    const double q = (double)pts[i].w;
+    const double hu = dLdU ? 0.5 * dLdU[s] : 0.0;
+    if (dq) dq[j] = (TO)(c1 * r.x + (dLdU ? hu * c1 * fwd_pot[i] : 0.0));
+    if (dx) {
+        const double wj = (w ? (double)w[j] : 0.0) + hu * q;
+        double t[3] = {c2 * q * r.y, c2 * q * r.z, c2 * q * r.w};
+        if (hg) {
+            const double4 h = hg[i];
+            t[0] += c2 * h.x, t[1] += c2 * h.y, t[2] += c2 * h.z;
+        }
+        if (grad)
+            for (int d = 0; d < 3; ++d) t[d] += wj * (double)grad[3 * j + d];
+        dx[3 * j] = (TO)t[0];
+        dx[3 * j + 1] = (TO)t[1];
+        dx[3 * j + 2] = (TO)t[2];
+    }
+}
+
+// Weights of a loss on the gradient, in sorted order and root units: the
+// caller's dL/dgrad divided by the side of the particle's system (the
+// gradient in caller units is the root-unit gradient over the side).
+template <typename TI, typename T>
+__global__ void k_gather_g(int64_t n, const uint32_t *__restrict__ perm, const int64_t *__restrict__ off, int S,
+                           const double *__restrict__ lo_side, const TI *__restrict__ g, T *__restrict__ gs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t j = perm[i];
@@ -1035,47 +1236,168 @@ __global__ void k_finalize_adj(int64_t n, const double4 *__restrict__ res, const
         const int mid = (lo + hi + 1) >> 1;
         if (off[mid] <= (int64_t)j) lo = mid; else hi = mid - 1;
     }
-    const double c1 = out_scale[2 * lo], c2 = out_scale[2 * lo + 1];  // coef / (4 pi side), / side^2
-    const double4 r = res[i];
-    const double q = (double)pts[i].w;
-    if (dq) dq[j] = (TO)(c1 * r.x);
-    if (dx) {
-        const double wj = (double)w[j];
-        dx[3 * j] = (TO)(wj * (double)grad[3 * j] + c2 * q * r.y);
-        dx[3 * j + 1] = (TO)(wj * (double)grad[3 * j + 1] + c2 * q * r.z);
-        dx[3 * j + 2] = (TO)(wj * (double)grad[3 * j + 2] + c2 * q * r.w);
+    const double side = lo_side[4 * lo + 3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gs[3 * i + d] = (T)((double)g[3 * j + d] / side);
+}
+
+// The leaf-level terms of a loss on the gradient, one block per leaf b (its
+// targets in chunks of the block), root units, FP64 sums:
+//  hg[i]  = H_i g_i, the Hessian of the forward field at particle i applied
+//           to its own dipole (the gradient's dependence on the particle's
+//           position), from b's forward sources: its downward equivalent
+//           density on the 2.95 h_b surface, the upward densities of its W
+//           boxes on their 1.05 h_a surfaces, and the U-list particles;
+//  pd[i]  = (psi, grad psi) at particle i of the dipoles g_j of the U-list
+//           particles j != i (the near field of the transposed gradient).
+// With H = grad grad (1/r), r = x_i - y:  H g = (3 (r.g) r - r^2 g) / r^5;
+// a dipole g at y gives psi(x) = g . r / r^3, grad psi = g / r^3 - 3 (g.r) r / r^5.
+template <typename T>
+__global__ void __launch_bounds__(kLeafThreads) k_adj_leaf(LeafCtx C, const int32_t *__restrict__ leaves,
+                                                           const typename Vec4<T>::type *__restrict__ pts,
+                                                           const T *__restrict__ surf, const T *__restrict__ dn_dens,
+                                                           const T *__restrict__ up_dens, const T *__restrict__ gs,
+                                                           double4 *__restrict__ hg, double4 *__restrict__ pd) {
+    __shared__ T sx[kLeafThreads], sy[kLeafThreads], sz[kLeafThreads], sq[kLeafThreads];
+    __shared__ T sgx[kLeafThreads], sgy[kLeafThreads], sgz[kLeafThreads];
+    const int b = leaves[blockIdx.x];
+    const int lb = C.lvl[b], n = C.cnt[b], f = C.first[b], ns = C.ns;
+    const T hb = box_half<T>(lb);
+    const uint32_t w0 = C.w_ptr[b], u0 = C.u_ptr[b];
+    const int nw = (int)(C.w_ptr[b + 1] - w0), nu = (int)(C.u_ptr[b + 1] - u0);
+    for (int t0 = 0; t0 < n; t0 += kLeafThreads) {
+        const int i = t0 + threadIdx.x;
+        const bool valid = i < n;
+        T x = 0, y = 0, z = 0, g0 = 0, g1 = 0, g2 = 0;
+        if (valid) {
+            const auto v = pts[f + i];
+            x = v.x, y = v.y, z = v.z;
+            g0 = gs[3 * (size_t)(f + i)], g1 = gs[3 * (size_t)(f + i) + 1], g2 = gs[3 * (size_t)(f + i) + 2];
+        }
+        double h0 = 0, h1 = 0, h2 = 0, p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+        // Hessian of one monopole w at offset (rx, ry, rz) = x_i - y, applied to g
+        auto hess = [&](T rx, T ry, T rz, T w) {
+            const T r2 = rx * rx + ry * ry + rz * rz;
+            const T ri = rsqrt_t<T>(r2), ri2 = ri * ri, ri3 = ri * ri2;
+            const T rg3 = T(3) * (rx * g0 + ry * g1 + rz * g2) * ri2;
+            h0 += (double)(w * ri3 * (rg3 * rx - g0));
+            h1 += (double)(w * ri3 * (rg3 * ry - g1));
+            h2 += (double)(w * ri3 * (rg3 * rz - g2));
+        };
+        if (valid) {
+            // own downward equivalent surface (weights dn_dens h_b)
+            const T a = (T)kAlphaOuter * hb;
+            for (int k = 0; k < ns; ++k)
+                hess(x - a * surf[3 * k], y - a * surf[3 * k + 1], z - a * surf[3 * k + 2],
+                     dn_dens[(size_t)b * ns + k] * hb);
+            // W boxes' upward equivalent surfaces (weights up_dens h_a)
+            for (int e = 0; e < nw; ++e) {
+                const int a_ = C.w_idx[w0 + e], la = C.lvl[a_];
+                const T ha = box_half<T>(la), al = (T)kAlphaInner * ha;
+                const T ox = centre_diff<T>(C.cx[a_], la, C.cx[b], lb), oy = centre_diff<T>(C.cy[a_], la, C.cy[b], lb),
+                        oz = centre_diff<T>(C.cz[a_], la, C.cz[b], lb);
+                for (int k = 0; k < ns; ++k)
+                    hess(x - (ox + al * surf[3 * k]), y - (oy + al * surf[3 * k + 1]), z - (oz + al * surf[3 * k + 2]),
+                         up_dens[(size_t)a_ * ns + k] * ha);
+            }
+        }
+        // U-list particles, staged through shared memory
+        for (int e = 0; e < nu; ++e) {
+            const int a_ = C.u_idx[u0 + e], la = C.lvl[a_];
+            const T ox = centre_diff<T>(C.cx[a_], la, C.cx[b], lb), oy = centre_diff<T>(C.cy[a_], la, C.cy[b], lb),
+                    oz = centre_diff<T>(C.cz[a_], la, C.cz[b], lb);
+            const int na = C.cnt[a_], fa = C.first[a_];
+            for (int c0 = 0; c0 < na; c0 += kLeafThreads) {
+                __syncthreads();
+                if (c0 + threadIdx.x < na) {
+                    const int j = fa + c0 + threadIdx.x;
+                    const auto v = pts[j];
+                    sx[threadIdx.x] = ox + v.x;
+                    sy[threadIdx.x] = oy + v.y;
+                    sz[threadIdx.x] = oz + v.z;
+                    sq[threadIdx.x] = v.w;
+                    sgx[threadIdx.x] = gs[3 * (size_t)j];
+                    sgy[threadIdx.x] = gs[3 * (size_t)j + 1];
+                    sgz[threadIdx.x] = gs[3 * (size_t)j + 2];
+                }
+                __syncthreads();
+                const int m = min(kLeafThreads, na - c0);
+                if (valid) {
+                    for (int k = 0; k < m; ++k) {
+                        const T rx = x - sx[k], ry = y - sy[k], rz = z - sz[k];
+                        const T r2 = rx * rx + ry * ry + rz * rz;
+                        if (!(r2 > T(0))) continue;  // the particle itself and coincident points
+                        hess(rx, ry, rz, sq[k]);
+                        const T ri = rsqrt_t<T>(r2), ri2 = ri * ri, ri3 = ri * ri2;
+                        const T gr = sgx[k] * rx + sgy[k] * ry + sgz[k] * rz;
+                        const T gr3 = T(3) * gr * ri2;
+                        p0 += (double)(gr * ri3);
+                        p1 += (double)(ri3 * (sgx[k] - gr3 * rx));
+                        p2 += (double)(ri3 * (sgy[k] - gr3 * ry));
+                        p3 += (double)(ri3 * (sgz[k] - gr3 * rz));
+                    }
+                }
+            }
+        }
+        if (valid) {
+            hg[f + i] = make_double4(h0, h1, h2, 0.0);
+            pd[f + i] = make_double4(p0, p1, p2, p3);
+        }
     }
 }
 
 // Transposed passes with the tree frozen: psi = A^T w (Sec. 2.2 operators,
 // transposed in reverse order), then the adjoint outputs.
 template <typename T>
-cudaError_t backward_t(Plan &P, const void *w_user, const void *grad_user, void *dq, void *dx, cudaStream_t s) {
+cudaError_t backward_t(Plan &P, const void *w_user, const void *g_user, const double *dLdU, const void *grad_user,
+                       void *dq, void *dx, cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
     const int ns = P.ns;
     const size_t nn = (size_t)ns * ns;
     const T *surf = P.f64 ? (const T *)P.surf64 : (const T *)P.surf32;
     T *ub = (T *)P.u_chk, *db = (T *)P.d_chk, *tmp = (T *)P.tmp_chk;
-    T *e1 = (T *)P.dn_dens, *e2 = (T *)P.up_dens, *ws = (T *)P.w_sorted;
+    // scratch of their own: the forward's equivalent densities stay intact
+    // (the Hessian term reads them, and a second backward may follow)
+    T *e1 = (T *)P.adj_e1, *e2 = (T *)P.adj_e2, *ws = (T *)P.w_sorted;
+    T *gs = g_user ? (T *)P.g_sorted : nullptr;
     const T *adjp = (const T *)P.adj_pinv;
     const V4 *pts = (const V4 *)P.pts;
     double4 *res = (double4 *)P.res;
+    double4 *hg = g_user ? (double4 *)P.adj_hg : nullptr, *pd = g_user ? (double4 *)P.adj_pd : nullptr;
+    double *fwd_pot = dLdU ? P.adj_pot : nullptr;
     if (P.io_f64)
-        ++g_launches, k_gather_w<double, T><<<grid_for(P.n, 256), 256, 0, s>>>(P.n, P.perm, (const double *)w_user, ws);
+        ++g_launches, k_adj_weights<double, T><<<grid_for(P.n, 256), 256, 0, s>>>(
+                          P.n, P.perm, P.sys_off_d, P.n_sys, pts, (const double *)w_user, dLdU, res, ws, fwd_pot);
     else
-        ++g_launches, k_gather_w<float, T><<<grid_for(P.n, 256), 256, 0, s>>>(P.n, P.perm, (const float *)w_user, ws);
-    // L2P^T: h * sum w / |DE - x| at each leaf, then d-bar = W_dn^T V_dn^T (.)
+        ++g_launches, k_adj_weights<float, T><<<grid_for(P.n, 256), 256, 0, s>>>(
+                          P.n, P.perm, P.sys_off_d, P.n_sys, pts, (const float *)w_user, dLdU, res, ws, fwd_pot);
+    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns, nullptr,
+              P.leaf_tile, P.status};
+    if (g_user) {
+        if (P.io_f64)
+            ++g_launches, k_gather_g<double, T><<<grid_for(P.n, 256), 256, 0, s>>>(
+                              P.n, P.perm, P.sys_off_d, P.n_sys, P.lo_side, (const double *)g_user, gs);
+        else
+            ++g_launches, k_gather_g<float, T><<<grid_for(P.n, 256), 256, 0, s>>>(
+                              P.n, P.perm, P.sys_off_d, P.n_sys, P.lo_side, (const float *)g_user, gs);
+        // the forward field's Hessian term and the dipoles' near field (reads
+        // the last evaluate's equivalent densities)
+        ++g_launches, k_adj_leaf<T><<<(unsigned)P.n_leaves, kLeafThreads, 0, s>>>(
+                          C, P.leaves, pts, surf, (const T *)P.dn_dens, (const T *)P.up_dens, gs, hg, pd);
+    }
+    // L2P^T: h * sum w / |DE - x| (+ the dipoles) at each leaf, then d-bar = W_dn^T V_dn^T (.)
     KIFMM_CUDA_TRY(cudaMemsetAsync(db, 0, sizeof(T) * (size_t)P.nb * ns, s));
     KIFMM_CUDA_TRY(cudaMemsetAsync(ub, 0, sizeof(T) * (size_t)P.nb * ns, s));
     ++g_launches, k_p2m<T><<<(unsigned)P.n_leaves, p2m_threads(P), p2m_smem<T>(P), s>>>(P.leaves, P.lvl, P.first, P.cnt, pts, surf,
-                                                                        ns, e1, ws, 1);
+                                                                        ns, e1, ws, 1, gs);
     ggemm<T>(P, GatherSelf<T>{adjp + 3 * nn}, P.leaves, 0, P.n_leaves, 1, e1, tmp, 0, s);
     ggemm<T>(P, GatherSelf<T>{adjp + 2 * nn}, P.leaves, 0, P.n_leaves, 1, tmp, db, 0, s);
-    // M2P^T: W-list sources a receive h_a * sum w / |UE_a - x| from the leaves of X(a)
+    // M2P^T: W-list sources a receive h_a * sum w / |UE_a - x| (+ dipoles) from the leaves of X(a)
     if (P.n_x > 0) {
         KIFMM_CUDA_TRY(cudaMemsetAsync(e2, 0, sizeof(T) * (size_t)P.nb * ns, s));
         ++g_launches, k_p2l<T><<<(unsigned)P.nb, kLeafThreads, 0, s>>>(P.nx, P.xdense, P.lvl, P.cx, P.cy, P.cz,
-                                                                        P.first, P.cnt, pts, surf, ns, e2, ws, 1);
+                                                                        P.first, P.cnt, pts, surf, ns, e2, ws, 1,
+                                                                        nullptr, gs);
         ggemm<T>(P, GatherSelf<T>{adjp + 1 * nn}, P.part_list[2], 0, P.part_start[2][1], 1, e2, tmp, 0, s);
         ggemm<T>(P, GatherSelf<T>{adjp}, P.part_list[2], 0, P.part_start[2][1], 1, tmp, ub, 0, s);
     }
@@ -1091,25 +1413,26 @@ cudaError_t backward_t(Plan &P, const void *w_user, const void *grad_user, void 
         ggemm_classes<T>(P, GatherParent<T>{P.parent, (const T *)P.adj_m2m, ns, ns}, P.part_list[3],
                          P.part_start[3].data() + 8 * l, 8, 1, ub, ub, 1, s);
     // P2M^T (own UC surface, u-bar), P2L^T (W boxes' DC surfaces, d-bar), P2P^T (weights w)
-    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns, nullptr,
-              P.leaf_tile, P.status};
     const LeafW<T> W{ub, 0, db, 0, ws};
     leaf_launch<T>(P, C, pts, surf, W, res, s);
     if (P.io_f64)
         ++g_launches, k_finalize_adj<double, T><<<grid_for(P.n, 256), 256, 0, s>>>(
-                          P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, pts, (const double *)w_user,
-                          (const double *)grad_user, (double *)dq, (double *)dx);
+                          P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, pts, (const double *)w_user, dLdU,
+                          fwd_pot, hg, pd, (const double *)grad_user, (double *)dq, (double *)dx);
     else
         ++g_launches, k_finalize_adj<float, T><<<grid_for(P.n, 256), 256, 0, s>>>(
-                          P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, pts, (const float *)w_user,
-                          (const float *)grad_user, (float *)dq, (float *)dx);
+                          P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, pts, (const float *)w_user, dLdU,
+                          fwd_pot, hg, pd, (const float *)grad_user, (float *)dq, (float *)dx);
+    P.fwd_res_valid = false;  // res now holds the adjoint field
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t run_backward(Plan &P, const void *w, const void *grad, void *dq, void *dx, cudaStream_t s) {
-    return P.f64 ? backward_t<double>(P, w, grad, dq, dx, s) : backward_t<float>(P, w, grad, dq, dx, s);
+cudaError_t run_backward(Plan &P, const void *w, const void *g, const double *dLdU, const void *grad, void *dq,
+                         void *dx, cudaStream_t s) {
+    return P.f64 ? backward_t<double>(P, w, g, dLdU, grad, dq, dx, s)
+                 : backward_t<float>(P, w, g, dLdU, grad, dq, dx, s);
 }
 
 cudaError_t run_evaluate(Plan &P, void *pot, void *grad, double *energy, cudaStream_t s) {

@@ -83,6 +83,16 @@ struct Plan {
     // pseudo-inverse factors W_up, V_up, W_dn, V_dn row-major.
     void *adj_m2m = nullptr, *adj_l2l = nullptr, *adj_m2l = nullptr, *adj_pinv = nullptr;
     void *w_sorted = nullptr;   // [N] adjoint weights in sorted order
+    // Adjoint of a loss on the gradient / the energy: dipoles dL/dgrad in
+    // sorted order and root units [N][3]; per particle the Hessian term and
+    // the dipoles' near field (double4 each) and the forward potential; per
+    // box the transposed pass's scratch (kept apart from the forward's
+    // equivalent densities, which the Hessian term reads).
+    void *g_sorted = nullptr;
+    double *adj_hg = nullptr, *adj_pd = nullptr, *adj_pot = nullptr;
+    void *adj_e1 = nullptr, *adj_e2 = nullptr;
+    bool fwd_valid = false;     // the last evaluate ran on the current sources (densities)
+    bool fwd_res_valid = false; // ... and res still holds its field (no backward since)
     // Tensor-core M2L operands (mixed modes), built lazily.
     void *m2l_tc = nullptr;     // layout owned by the tensor-core kernel
     float *m2l_tc_scale = nullptr;
@@ -262,7 +272,8 @@ float time_launch(cudaStream_t s, F &&launch) {
 }
 
 cudaError_t run_evaluate(Plan &P, void *pot, void *grad, double *energy, cudaStream_t s);
-cudaError_t run_backward(Plan &P, const void *w, const void *grad, void *dq, void *dx, cudaStream_t s);
+cudaError_t run_backward(Plan &P, const void *w, const void *g, const double *dLdU, const void *grad, void *dq,
+                         void *dx, cudaStream_t s);
 cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream_t s);
 cudaError_t run_clump_reduce(Plan &P, int64_t n_clumps, const int64_t *offs, const void *xyz,
                              const void *q, const void *grad, const void *ref, void *force,

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
         accfree_bar[kAccBufs];
     __shared__ uint32_t tmem_base_s;
     __shared__ int32_t tgt_s[kTcRows];
+
     __shared__ volatile int abort_s;
     __shared__ volatile int abort_zero;  // never set: a wait on it runs to its bound
 
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
         const int i = tile.y + threadIdx.x;
         tgt_s[threadIdx.x] = (i < tile.z) ? a.targets[i] : -1;
     }
+
     if (threadIdx.x == 0) {
         abort_s = 0;
         abort_zero = 0;
@@ -224,8 +226,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TileArgs a) {
                         const uint64_t dBh = sdesc_sw64(sB + 32 * kk);
                         const uint64_t dBl = sdesc_sw64(sBl + 32 * kk);
                         const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-                        mma_f16(tacc, dAh, dBh, id, acc0);
-                        mma_f16(tacc, dAh, dBl, id, 1u);
+                        // A_hi feeds two products: read once into the collector
+                        mma_f16_fill(tacc, dAh, dBh, id, acc0);
+                        mma_f16_lastuse(tacc, dAh, dBl, id, 1u);
                         mma_f16(tacc, dAl, dBh, id, 1u);
                     }
                     mma_commit(smem_u32(&empty_bar[stage]));

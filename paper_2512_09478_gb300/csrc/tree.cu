@@ -451,7 +451,13 @@ __global__ void k_gather(int64_t n_leaves, const int32_t *__restrict__ leaves, c
     const double side = lo_side[s * 4 + 3], inv_side = 1.0 / side;
     const double lo[3] = {lo_side[s * 4], lo_side[s * 4 + 1], lo_side[s * 4 + 2]};
     const double w = ldexp(1.0, -lvl[b]);
-    const double c[3] = {(cx[b] + 0.5) * w, (cy[b] + 0.5) * w, (cz[b] + 0.5) * w};
+    // the leaf centre in the caller's coordinates: the offset x - C is then
+    // exact (x lies next to C) and rounds only on the division, so a record
+    // carries the caller's coordinate to about one unit in the last place of
+    // |x|, not of |x - lo| (which is far larger for a particle near the origin
+    // of a domain whose corner lies far from it)
+    const double C[3] = {fma((cx[b] + 0.5) * w, side, lo[0]), fma((cy[b] + 0.5) * w, side, lo[1]),
+                         fma((cz[b] + 0.5) * w, side, lo[2])};
     for (int k = threadIdx.x & 31; k < cnt[b]; k += 32) {
         const int64_t i = first[b] + k;
         const uint32_t j = perm[i];
@@ -459,8 +465,8 @@ __global__ void k_gather(int64_t n_leaves, const int32_t *__restrict__ leaves, c
         // FP64 records keep the correctly rounded quotient (FP64 parity); FP32
         // records are rounded to FP32 anyway, so a reciprocal multiply will do
         for (int d = 0; d < 3; ++d)
-            r[d] = (sizeof(TC) == 8 ? ((double)xyz[3 * j + d] - lo[d]) / side
-                                    : ((double)xyz[3 * j + d] - lo[d]) * inv_side) - c[d];
+            r[d] = sizeof(TC) == 8 ? ((double)xyz[3 * j + d] - C[d]) / side
+                                   : ((double)xyz[3 * j + d] - C[d]) * inv_side;
         typename Vec4<TC>::type v;
         v.x = (TC)r[0];
         v.y = (TC)r[1];
@@ -1133,6 +1139,7 @@ cudaError_t check_leaves(Plan &P, const void *xyz, double skin, int *moved_dev, 
 // Leaf-relative particle records in the compute type (also used to refresh
 // positions and charges with the tree frozen).
 cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream_t s) {
+    P.fwd_valid = P.fwd_res_valid = false;  // new sources: the last evaluate's field no longer applies
     if (P.f64) {
         if (P.io_f64)
             ++g_launches, k_gather<double, double><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(

@@ -75,7 +75,7 @@ def load(path: str = LIB_PATH):
     lib.kifmm_set_sources.argtypes = [P, I, P, P, P, P]
     lib.kifmm_evaluate.argtypes = [P, P, P, P, P]
     lib.kifmm_clump_reduce.argtypes = [P, I64, P, P, P, P, P, P, P, P]
-    lib.kifmm_backward.argtypes = [P, P, P, P, P, P]
+    lib.kifmm_backward.argtypes = [P, P, P, P, P, P, P, P]
     lib.kifmm_get_device_status.argtypes = [P, ctypes.POINTER(I)]
     lib.kifmm_status_string.argtypes = [I]
     lib.kifmm_status_string.restype = ctypes.c_char_p
@@ -215,17 +215,27 @@ class Plan:
                "kifmm_clump_reduce")
         return force, torque
 
-    def backward(self, dL_dpot, grad, dq=None, dx=None, stream=None):
-        """Adjoint of evaluate on the plan's current tree and sources:
-        dq = A^T dL_dpot, dx = dL_dpot * grad + q * grad_y(A^T dL_dpot)."""
-        dL_dpot = dL_dpot.contiguous()
-        grad = grad.contiguous()
+    def backward(self, dL_dpot=None, grad=None, dq=None, dx=None, stream=None, dL_dgrad=None, dL_denergy=None):
+        """Adjoint of evaluate on the plan's current tree and sources
+        (kifmm_backward): for a loss with dL/dpot, dL/dgrad (each [N] / [N, 3]
+        in the plan's dtype, or None) and dL/dU per system ([n_systems]
+        float64, or None), returns (dq, dx).  grad is the forward gradient,
+        needed for dx with dL_dpot or dL_denergy; dL_dgrad and dL_denergy read
+        the last evaluate, which must have run on the current sources."""
+        lib = load()
+        c = lambda t: None if t is None else t.contiguous()
+        dL_dpot, grad, dL_dgrad = c(dL_dpot), c(grad), c(dL_dgrad)
+        if dL_denergy is not None:
+            dL_denergy = dL_denergy.to(torch.float64).contiguous()
+        for t in (dL_dpot, dL_dgrad, grad):
+            assert t is None or (t.dtype == self.dtype and t.is_cuda)
+        dev = torch.device("cuda", torch.cuda.current_device())
         if dq is None:
-            dq = torch.empty(self.n, dtype=self.dtype, device=grad.device)
+            dq = torch.empty(self.n, dtype=self.dtype, device=dev)
         if dx is None:
-            dx = torch.empty(self.n, 3, dtype=self.dtype, device=grad.device)
-        _check(load().kifmm_backward(self._h, _ptr(dL_dpot), _ptr(grad), _ptr(dq), _ptr(dx), _stream(stream)),
-               "kifmm_backward")
+            dx = torch.empty(self.n, 3, dtype=self.dtype, device=dev)
+        _check(lib.kifmm_backward(self._h, _ptr(dL_dpot), _ptr(dL_dgrad), _ptr(dL_denergy), _ptr(grad), _ptr(dq),
+                                  _ptr(dx), _stream(stream)), "kifmm_backward")
         return dq, dx
 
     def device_status(self) -> int:
@@ -354,12 +364,19 @@ def energy_noalloc(q: torch.Tensor, pot: torch.Tensor, out: torch.Tensor = None,
     return out
 
 
+def _check_generation(ctx):
+    if ctx.plan.generation != ctx.generation:
+        raise RuntimeError("the plan's sources changed after this forward: backward needs the plan to "
+                           "hold the forward's sources (one plan per differentiated evaluation)")
+
+
 class KifmmPotential(torch.autograd.Function):
-    """pot = KIFMM(x, q) with gradients w.r.t. x and q through the adjoint
-    passes (kifmm_backward).  The tree is built (rebuild=True) or frozen
-    (rebuild=False, kifmm_update_sources); the plan must still hold these
-    sources when backward runs (tree-level recomputation, nothing stored
-    besides the forward gradient)."""
+    """(pot, grad) = KIFMM(x, q) with gradients w.r.t. x and q through the
+    adjoint passes (kifmm_backward), for losses on the potential and on the
+    gradient (forces F = -q grad).  The tree is built (rebuild=True) or
+    frozen (rebuild=False, kifmm_update_sources); the plan must still hold
+    these sources when backward runs (tree-level recomputation, nothing
+    stored besides the forward gradient)."""
 
     @staticmethod
     def forward(ctx, x, q, plan, rebuild=True):
@@ -371,18 +388,42 @@ class KifmmPotential(torch.autograd.Function):
         ctx.plan = plan
         ctx.generation = plan.generation
         ctx.save_for_backward(grad)
-        ctx.mark_non_differentiable(grad)
         return pot, grad
 
     @staticmethod
     def backward(ctx, g_pot, g_grad):
         (grad,) = ctx.saved_tensors
-        if ctx.plan.generation != ctx.generation:
-            raise RuntimeError("the plan's sources changed after this forward: backward needs the plan to "
-                               "hold the forward's sources (one plan per differentiated evaluation)")
-        if g_grad is not None and torch.any(g_grad != 0):
-            raise NotImplementedError("losses on the gradient output are not differentiated")
-        dq, dx = ctx.plan.backward(g_pot, grad)
+        _check_generation(ctx)
+        if g_grad is not None and not torch.any(g_grad != 0):
+            g_grad = None
+        if g_pot is None and g_grad is None:
+            return None, None, None, None
+        dq, dx = ctx.plan.backward(g_pot, grad, dL_dgrad=g_grad)
+        return dx, dq, None, None
+
+
+class KifmmEnergy(torch.autograd.Function):
+    """Long-range energy per system, U_s = 1/2 sum_{i in s} q_i pot_i (Sec.
+    2.4), as the library's energy output; its gradients w.r.t. x and q come
+    from kifmm_backward's energy term (no arithmetic here)."""
+
+    @staticmethod
+    def forward(ctx, x, q, plan, rebuild=True):
+        if rebuild:
+            plan.set_sources(x.detach(), q.detach())
+        else:
+            plan.update_sources(x.detach(), q.detach())
+        _, grad, energy = plan.evaluate(want_pot=False, want_energy=True)
+        ctx.plan = plan
+        ctx.generation = plan.generation
+        ctx.save_for_backward(grad)
+        return energy
+
+    @staticmethod
+    def backward(ctx, g_energy):
+        (grad,) = ctx.saved_tensors
+        _check_generation(ctx)
+        dq, dx = ctx.plan.backward(None, grad, dL_denergy=g_energy)
         return dx, dq, None, None
 
 
@@ -392,6 +433,13 @@ def potential(x, q, plan, rebuild=True):
     return pot
 
 
+def field(x, q, plan, rebuild=True):
+    """Differentiable (pot, grad); a loss on grad (e.g. on the forces
+    -q grad) is differentiated through the adjoint of the gradient."""
+    return KifmmPotential.apply(x, q, plan, rebuild)
+
+
 def energy(x, q, plan, rebuild=True):
-    """Differentiable long-range energy U = 1/2 sum_i q_i pot_i (Sec. 2.4)."""
-    return 0.5 * torch.dot(q, potential(x, q, plan, rebuild))
+    """Differentiable long-range energy, summed over the plan's systems
+    (KifmmEnergy gives the per-system values)."""
+    return KifmmEnergy.apply(x, q, plan, rebuild).sum()

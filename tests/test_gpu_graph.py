@@ -8,8 +8,7 @@ that reuses the tree) and checks every system against the oracle run on the
 moved particles with that system's frozen tree:
 
 * FP64, 8 systems of 2k..20k particles (uniform and Plummer, as in the
-  batched workload): within 10x the method's rounding floor
-  (parity_helpers.rounding_floor), never looser than 1e-12.
+  batched workload): rel-L2 <= 1e-12 per system.
 * The benchmark's batched workload itself (64 systems of 10k..200k, p = 6,
   leaf cap 64, FP32 data, 3xFP16 tensor-core M2L): against the oracle with
   the FP32 modes' pseudo-inverse truncation (the same method), within the
@@ -24,7 +23,6 @@ import torch
 
 from oracle import oracle as O
 from workloads import generators as G
-from parity_helpers import rounding_floor
 
 pytestmark = pytest.mark.gpu
 
@@ -102,11 +100,10 @@ def test_graph_replay_fp64_matches_oracle_per_system():
             lst = O.lists(t)
             xs = X[sl] + dx[sl]
             po, go, _ = O.kifmm(xs, Q[sl], p=4, leaf_cap=32, tree=t, lst=lst)
-            bar_p, bar_g = rounding_floor(xs, Q[sl], 4, 32, po, go, tree=t, lst=lst)
-            assert O.rel_l2(pot[sl], po) <= bar_p, s
-            assert O.rel_l2(grad[sl], go) <= bar_g, s
+            assert O.rel_l2(pot[sl], po) <= 1e-12, s
+            assert O.rel_l2(grad[sl], go) <= 1e-12, s
             # |U - U_o| <= 1/2 |q| |pot - pot_o| (Cauchy-Schwarz), with the pot bound above
-            assert abs(energy[s] - O.energy(Q[sl], po)) <= 0.5 * np.linalg.norm(Q[sl]) * bar_p * np.linalg.norm(po)
+            assert abs(energy[s] - O.energy(Q[sl], po)) <= 0.5 * np.linalg.norm(Q[sl]) * 1e-12 * np.linalg.norm(po)
 
 
 def test_graph_replay_mixed_batched_workload():
