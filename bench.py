@@ -56,17 +56,11 @@ WORKLOADS["c2"]["compare"] = "fp32"
 
 
 # DRAM bytes (read + write) per launch of the dominant kernels on the 1M DEM
-# packing, from one ncu capture (summary in
-# profiles/k_m2l_tc_k_leaf_all_c2_dem_coulomb_1M.md).  A figure is reported
-# only while the kernel's translation unit is byte-identical to the one
-# captured (sha256); otherwise the roofline's traffic is null.
-TRAFFIC = {
-    ("dem-coulomb-rsa-1M", "m2l"): ("paper_2512_09478_gb300/csrc/m2l_tc.cu",
-                                    "fc2ef0192df1450006b0109cfdf28cc76494914810b024da3834043ca1fe2701", 119.80e6),
-    # the leaf stage: all tile variants of one evaluate together
-    ("dem-coulomb-rsa-1M", "p2p"): ("paper_2512_09478_gb300/csrc/fmm.cu",
-                                    "c537ce5831240dece0ac0da6f49b4839b7c7756a64dae03a8879d939117cef64", 68.06e6),
-}
+# packing, from an ncu capture of the full-size launch with the DRAM byte
+# counters only (one pass; summary in profiles/).  A figure is reported only
+# while the kernel's translation unit is byte-identical to the one captured
+# (sha256); otherwise the roofline's traffic is null.
+TRAFFIC = {}
 
 
 def traffic_for(workload, stage):
