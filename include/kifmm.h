@@ -110,6 +110,27 @@ typedef struct {
                             then (U U^T K0_o + 1 m_o^T) V V^T.  A value >= 1
                             or not finite is KIFMM_ERR_ARG, as is any nonzero
                             value in the FP64 and FP32 modes.               */
+    double cell;         /* 0: free space.  > 0: periodic boundary conditions
+                            (Sec. 2.4): the particles live in the cubic cell
+                            [0, cell)^3 (positions outside are wrapped into
+                            it), repeated over Z^3.  The cell is the root box;
+                            the lists run over the cell and its 26 nearest
+                            images (entries carry an image shift), farther
+                            images act on the root through one far-image
+                            operator (kifmm_far_image_operator), and the
+                            potential gets the uniform second-moment term of
+                            the conducting-boundary lattice sum.  The cell
+                            must be neutral (|sum q| <= 1e-12 sum |q| for
+                            double charges, 2^-24 sum |q| for float ones: a
+                            neutral set rounded to float; else set_sources
+                            returns KIFMM_ERR_ARG); one system
+                            per plan (n_systems_max = 1); kifmm_backward is
+                            not available (KIFMM_ERR_ARG).  In the FP32-based
+                            modes that uniform term carries the FP32 error of
+                            the root's upward expansion amplified by the
+                            pseudo-inverse (a constant offset of every
+                            potential; gradients, forces and the energy of a
+                            neutral cell do not depend on it).              */
 } kifmm_plan_desc;
 
 typedef struct kifmm_plan kifmm_plan;
@@ -402,6 +423,12 @@ kifmm_status kifmm_copy_expansions(kifmm_plan *plan, double *u, double *d, doubl
  * ptr (host, [n_boxes + 1]), idx (host, [n_kind]); sources of each node are
  * sorted ascending. */
 kifmm_status kifmm_copy_list(kifmm_plan *plan, int kind, int64_t *ptr, int64_t *idx);
+
+/* The same with the image of every entry (periodic plans; all 13 in free
+ * space): img (host, [n_kind]) receives (n_x + 1) 9 + (n_y + 1) 3 + (n_z + 1)
+ * for the image shift n in {-1, 0, 1}^3 of the source box; entries sorted by
+ * (box, image).  ptr, idx as kifmm_copy_list. */
+kifmm_status kifmm_copy_list_images(kifmm_plan *plan, int kind, int64_t *ptr, int64_t *idx, int64_t *img);
 
 #ifdef __cplusplus
 }

@@ -866,7 +866,20 @@ def far_image_operator(p: int, L: float, alpha: float = None, real_shells: int =
     return T / (4.0 * np.pi)
 
 
-def kifmm_periodic(x, q, L: float, p: int = 6, leaf_cap: int = 64, max_depth: int = 20, eps: float = 1e-12):
+def periodic_tree(x, L: float, leaf_cap: int, max_depth: int):
+    """The tree of a periodic cell [0, L)^3: the same rules as sort_and_tree
+    with the cell itself as the root cube (x already wrapped into it)."""
+    x = _f64(x).reshape(-1, 3)
+    lo = np.zeros(3)
+    keys = morton(x, lo, L)
+    perm = np.argsort(keys, kind="stable")
+    tree = build_tree(keys[perm], leaf_cap, max_depth)
+    tree.update(lo=lo, side=float(L), keys=keys, perm=perm)
+    return tree
+
+
+def kifmm_periodic(x, q, L: float, p: int = 6, leaf_cap: int = 64, max_depth: int = 20, eps: float = 1e-12,
+                   ops=None):
     """Potential and gradient (Eq. 3 units) of a neutral cubic cell [0, L)^3
     repeated over Z^3 by the KIFMM: the tree's root is the cell; the lists run
     over the cell and its 26 neighbouring images (periodic_lists); the images
@@ -877,12 +890,10 @@ def kifmm_periodic(x, q, L: float, p: int = 6, leaf_cap: int = 64, max_depth: in
     x = np.mod(_f64(x).reshape(-1, 3), L)
     q = _f64(q).reshape(-1)
     check_neutral(q)
-    lo = np.zeros(3)
-    keys = morton(x, lo, L)
-    perm = np.argsort(keys, kind="stable")
-    tree = build_tree(keys[perm], leaf_cap, max_depth)
-    tree.update(lo=lo, side=float(L), keys=keys, perm=perm)
-    ops = operators(p, eps)
+    tree = periodic_tree(x, L, leaf_cap, max_depth)
+    perm = tree["perm"]
+    if ops is None:
+        ops = operators(p, eps)
     S, ns = ops["surf"], ops["ns"]
     uu, us, uv, _ = ops["up"]
     du, ds, dv, _ = ops["dn"]

@@ -172,6 +172,12 @@ static cudaError_t ensure_box_arrays(Plan &P) {
         {(void **)&P.leaf_vcnt, sizeof(int32_t) * 8},
     };
     for (const A &a : arrs) KIFMM_CUDA_TRY(plan_alloc(P, a.p, a.bytes));
+    if (P.periodic) {
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.coll_sh, (size_t)kColl * cap));
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.coarse_sh, (size_t)kMaxCoarse * cap));
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.x_sh, (size_t)kMaxCoarse * cap));
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.leaf_q2, sizeof(double) * cap));
+    }
     P.list_cap = cap;
     P.leaf_item_cap = cap + P.desc.n_max / 8 + 64;
     return cudaSuccess;
@@ -232,6 +238,8 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     if (!(d.pinv_eps >= 0.0) || d.pinv_eps >= 1.0) return KIFMM_ERR_ARG;
     if (!(d.m2l_eps >= 0.0) || d.m2l_eps >= 1.0) return KIFMM_ERR_ARG;
     if (d.m2l_eps > 0.0 && d.precision != KIFMM_MIXED_FP16) return KIFMM_ERR_ARG;
+    if (!(d.cell >= 0.0) || !std::isfinite(d.cell)) return KIFMM_ERR_ARG;
+    if (d.cell > 0.0 && d.n_systems_max != 1) return KIFMM_ERR_ARG;  // one periodic cell per plan
     kifmm_plan *pl = new (std::nothrow) kifmm_plan();
     if (!pl) return KIFMM_ERR_CUDA;
     Plan &P = pl->P;
@@ -247,6 +255,8 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     P.eps = (d.pinv_eps != 0.0) ? d.pinv_eps : (P.f64 ? 1e-12 : 1e-9);
     P.direct_thr = (d.direct_max < 0) ? -1 : (d.direct_max == 0 ? P.ns : d.direct_max);
     P.leaf_tile = leaf_tiling_candidate(0);
+    P.periodic = d.cell > 0.0;
+    P.cell = d.cell;
     auto fail = [&](kifmm_status st) {
         kifmm_plan_destroy(pl);
         (void)cudaGetLastError();
@@ -295,6 +305,8 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {(void **)&P.part_counts, sizeof(uint32_t) * 4 * 256},
         {(void **)&P.list_totals, sizeof(unsigned long long) * 4},
         {(void **)&P.energy_chunk_start, sizeof(int32_t) * (P.sys_cap + 1)},
+        {(void **)&P.qsum, sizeof(double) * 2},
+        {(void **)&P.pshift, sizeof(double)},
     };
     for (const A &a : arrs)
         if (plan_alloc(P, a.p, a.bytes) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
@@ -429,6 +441,7 @@ kifmm_status kifmm_clump_reduce(kifmm_plan *pl, int64_t n_clumps, const int64_t 
 kifmm_status kifmm_backward(kifmm_plan *pl, const void *dL_dpot, const void *dL_dgrad, const double *dL_denergy,
                             const void *grad, void *dq, void *dx, kifmm_stream_t stream) {
     if (!pl || (!dL_dpot && !dL_dgrad && !dL_denergy)) return KIFMM_ERR_ARG;
+    if (pl->P.periodic) return KIFMM_ERR_ARG;  // the adjoint of the periodic terms is not built
     if (dx && (dL_dpot || dL_denergy) && !grad) return KIFMM_ERR_ARG;
     Plan &P = pl->P;
     if (!P.has_sources) return KIFMM_ERR_STATE;
@@ -620,44 +633,83 @@ kifmm_status kifmm_copy_expansions(kifmm_plan *pl, double *u, double *d, double 
     return KIFMM_OK;
 }
 
-kifmm_status kifmm_copy_list(kifmm_plan *pl, int kind, int64_t *ptr, int64_t *idx) {
-    if (!pl || !ptr || kind < 0 || kind > 3) return KIFMM_ERR_ARG;
-    Plan &P = pl->P;
-    if (!P.has_sources) return KIFMM_ERR_STATE;
+// Lists as (box, image) pairs per node, sorted; the image of a V-list entry
+// follows from its slot's offset (the slot table stores the box only).
+static kifmm_status list_pairs(Plan &P, int kind, std::vector<std::vector<std::pair<int64_t, int>>> &lists) {
     API_CUDA(cudaDeviceSynchronize());
     const int64_t nb = P.nb;
-    std::vector<std::vector<int64_t>> lists(nb);
+    lists.assign(nb, {});
     if (kind == 0 || kind == 2) {
         std::vector<uint32_t> p(nb + 1);
         const int64_t tot = (kind == 0) ? P.n_u : P.n_w;
         std::vector<int32_t> ix(std::max<int64_t>(tot, 1));
+        std::vector<int8_t> sh(std::max<int64_t>(tot, 1), 13);
         API_CUDA(cudaMemcpy(p.data(), kind == 0 ? P.u_ptr : P.w_ptr, sizeof(uint32_t) * (nb + 1),
                             cudaMemcpyDeviceToHost));
-        if (tot) API_CUDA(cudaMemcpy(ix.data(), kind == 0 ? P.u_idx : P.w_idx, sizeof(int32_t) * tot,
-                                     cudaMemcpyDeviceToHost));
+        if (tot) {
+            API_CUDA(cudaMemcpy(ix.data(), kind == 0 ? P.u_idx : P.w_idx, sizeof(int32_t) * tot,
+                                cudaMemcpyDeviceToHost));
+            const int8_t *dsh = kind == 0 ? P.u_sh : P.w_sh;
+            if (P.periodic) API_CUDA(cudaMemcpy(sh.data(), dsh, tot, cudaMemcpyDeviceToHost));
+        }
         for (int64_t b = 0; b < nb; ++b)
-            for (uint32_t e = p[b]; e < p[b + 1]; ++e) lists[b].push_back(ix[e]);
+            for (uint32_t e = p[b]; e < p[b + 1]; ++e) lists[b].push_back({ix[e], sh[e]});
     } else if (kind == 1) {
-        std::vector<int32_t> v((size_t)nb * kVSlots);
+        std::vector<int32_t> v((size_t)nb * kVSlots), slot(8 * kVSlots), lv(nb), c3(3 * (size_t)nb);
         API_CUDA(cudaMemcpy(v.data(), P.vdense, sizeof(int32_t) * v.size(), cudaMemcpyDeviceToHost));
+        API_CUDA(cudaMemcpy(slot.data(), P.slot_off, sizeof(int32_t) * slot.size(), cudaMemcpyDeviceToHost));
+        API_CUDA(cudaMemcpy(lv.data(), P.lvl, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
+        API_CUDA(cudaMemcpy(c3.data(), P.cx, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
+        API_CUDA(cudaMemcpy(c3.data() + nb, P.cy, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
+        API_CUDA(cudaMemcpy(c3.data() + 2 * nb, P.cz, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
+        const std::vector<int> offs = m2l_offset_list();
         for (int64_t b = 0; b < nb; ++b)
-            for (int sl = 0; sl < kVSlots; ++sl)
-                if (v[(size_t)b * kVSlots + sl] >= 0) lists[b].push_back(v[(size_t)b * kVSlots + sl]);
+            for (int sl = 0; sl < kVSlots; ++sl) {
+                const int32_t a = v[(size_t)b * kVSlots + sl];
+                if (a < 0) continue;
+                const int cls = ((c3[b] & 1) << 2) | ((c3[nb + b] & 1) << 1) | (c3[2 * nb + b] & 1);
+                const int o = slot[cls * kVSlots + sl];
+                int img = 0;
+                for (int d = 0; d < 3; ++d) {
+                    const int64_t diff = (int64_t)c3[d * nb + b] + offs[3 * o + d] - c3[d * nb + a];
+                    img = 3 * img + (int)(diff >> lv[b]) + 1;  // the image shift, in cells
+                }
+                lists[b].push_back({a, img});
+            }
     } else {
         std::vector<int32_t> x((size_t)nb * kMaxCoarse), nx(nb);
+        std::vector<int8_t> xs((size_t)nb * kMaxCoarse, 13);
         API_CUDA(cudaMemcpy(x.data(), P.xdense, sizeof(int32_t) * x.size(), cudaMemcpyDeviceToHost));
         API_CUDA(cudaMemcpy(nx.data(), P.nx, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
+        if (P.periodic) API_CUDA(cudaMemcpy(xs.data(), P.x_sh, xs.size(), cudaMemcpyDeviceToHost));
         for (int64_t b = 0; b < nb; ++b)
-            for (int k = 0; k < nx[b]; ++k) lists[b].push_back(x[(size_t)b * kMaxCoarse + k]);
+            for (int k = 0; k < nx[b]; ++k)
+                lists[b].push_back({x[(size_t)b * kMaxCoarse + k], xs[(size_t)b * kMaxCoarse + k]});
     }
+    for (auto &l : lists) std::sort(l.begin(), l.end());
+    return KIFMM_OK;
+}
+
+kifmm_status kifmm_copy_list_images(kifmm_plan *pl, int kind, int64_t *ptr, int64_t *idx, int64_t *img) {
+    if (!pl || !ptr || kind < 0 || kind > 3) return KIFMM_ERR_ARG;
+    Plan &P = pl->P;
+    if (!P.has_sources) return KIFMM_ERR_STATE;
+    std::vector<std::vector<std::pair<int64_t, int>>> lists;
+    const kifmm_status st = list_pairs(P, kind, lists);
+    if (st != KIFMM_OK) return st;
     ptr[0] = 0;
-    for (int64_t b = 0; b < nb; ++b) {
-        std::sort(lists[b].begin(), lists[b].end());
+    for (int64_t b = 0; b < P.nb; ++b) {
         ptr[b + 1] = ptr[b] + (int64_t)lists[b].size();
-        if (idx)
-            for (size_t k = 0; k < lists[b].size(); ++k) idx[ptr[b] + k] = lists[b][k];
+        for (size_t k = 0; k < lists[b].size(); ++k) {
+            if (idx) idx[ptr[b] + k] = lists[b][k].first;
+            if (img) img[ptr[b] + k] = lists[b][k].second;
+        }
     }
     return KIFMM_OK;
+}
+
+kifmm_status kifmm_copy_list(kifmm_plan *pl, int kind, int64_t *ptr, int64_t *idx) {
+    return kifmm_copy_list_images(pl, kind, ptr, idx, nullptr);
 }
 
 }  // extern "C"

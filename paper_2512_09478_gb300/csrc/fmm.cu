@@ -31,6 +31,16 @@ __device__ __forceinline__ T box_center(int c, int level) {
     return (T)(ldexp((double)(2 * c + 1), -(level + 1)));
 }
 
+// Offset of image s (13: the cell itself) in root units: the periodic cell is
+// the root box, of side 1.
+template <typename T>
+__device__ __forceinline__ void image_offset(int s, T &x, T &y, T &z) {
+    x = (T)(s / 9 - 1);
+    y = (T)((s / 3) % 3 - 1);
+    z = (T)(s % 3 - 1);
+}
+
+
 template <typename T>
 __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
     s = a + b;
@@ -113,7 +123,8 @@ __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict_
                       const int32_t *__restrict__ first, const int32_t *__restrict__ cnt,
                       const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, int ns,
                       T *__restrict__ d, const T *__restrict__ wts = nullptr, int adj = 0,
-                      double *__restrict__ dbar = nullptr, const T *__restrict__ dip = nullptr) {
+                      double *__restrict__ dbar = nullptr, const T *__restrict__ dip = nullptr,
+                      const int8_t *__restrict__ x_sh = nullptr) {
     // With dbar (FP32-based modes) the mean of this box's contribution goes
     // to dbar and only the mean-free remainder to d.  With dip (adjoint of
     // M2P under a loss on the gradient) every particle also carries a dipole.
@@ -139,8 +150,13 @@ __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict_
         for (int e = 0; e < nx[b]; ++e) {
             const int a = xdense[(size_t)b * kMaxCoarse + e];
             const int la = lvl[a];
-            const T ox = box_center<T>(cx[a], la) - cbx, oy = box_center<T>(cy[a], la) - cby,
-                    oz = box_center<T>(cz[a], la) - cbz;
+            T ox = box_center<T>(cx[a], la) - cbx, oy = box_center<T>(cy[a], la) - cby,
+              oz = box_center<T>(cz[a], la) - cbz;
+            if (x_sh) {  // the source leaf's image (periodic cell)
+                T ix, iy, iz;
+                image_offset<T>(x_sh[(size_t)b * kMaxCoarse + e], ix, iy, iz);
+                ox += ix, oy += iy, oz += iz;
+            }
             const int n = cnt[a], f = first[a];
             for (int c0 = 0; c0 < n; c0 += kLeafThreads) {
                 __syncthreads();
@@ -510,7 +526,9 @@ struct LeafCtx {
     const double *dbar;  // per-box mean of the downward check potential, or nullptr
     LeafTiling tile;     // tile id per remaining-target bucket
     int *status;         // device status word
+    const int8_t *u_sh, *w_sh;  // image shifts of the U and W entries (periodic cell), or null
 };
+
 
 // Source weights of the leaf stage.  Forward: own surface dn_dens * h_b,
 // W surfaces up_dens * h_a, particles q.  Adjoint (same geometry): own
@@ -754,6 +772,11 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
             d.ox = centre_diff<T>(C.cx[a], la, bx, lb);
             d.oy = centre_diff<T>(C.cy[a], la, by, lb);
             d.oz = centre_diff<T>(C.cz[a], la, bz, lb);
+            if (C.w_sh) {
+                T ix, iy, iz;
+                image_offset<T>(C.w_sh[w0 + e - 1], ix, iy, iz);
+                d.ox += ix, d.oy += iy, d.oz += iz;
+            }
             d.r = (T)kAlphaInner * pow2<T>(-(la + 1));
             d.hw = W.wl_h ? pow2<T>(-(la + 1)) : T(1);
             d.base = a * ns;
@@ -764,9 +787,15 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
             d.ox = centre_diff<T>(C.cx[a], la, bx, lb);
             d.oy = centre_diff<T>(C.cy[a], la, by, lb);
             d.oz = centre_diff<T>(C.cz[a], la, bz, lb);
+            const int sa = C.u_sh ? (int)C.u_sh[u0 + e - 1 - nw] : 13;
+            if (sa != 13) {
+                T ix, iy, iz;
+                image_offset<T>(sa, ix, iy, iz);
+                d.ox += ix, d.oy += iy, d.oz += iz;
+            }
             d.base = C.first[a];
             cnt = C.cnt[a];
-            own = (a == b);
+            own = (a == b) && sa == 13;  // another image of the leaf is not its own particles
         }
         int incl = cnt;
 #pragma unroll
@@ -1048,6 +1077,90 @@ void ggemm(Plan &P, const G &g, const int32_t *targets, int64_t a, int64_t e, in
     ggemm_classes<T, G>(P, g, targets, st, 1, nslots, in, out, accumulate, s);
 }
 
+// Periodic cell (Sec. 2.4): the images beyond the 26 nearest act on the
+// root's downward check potential, d(root) += F u(root), with F the
+// far-image composite; FP64 sums, one block.  With dbar (FP32-based modes)
+// the mean goes to dbar and the mean-free rest to d.
+template <typename T>
+__global__ void k_far_root(int ns, const double *__restrict__ Ft, const double *__restrict__ u, T *__restrict__ d,
+                           double *__restrict__ dbar) {
+    __shared__ double v[kMaxNs];
+    __shared__ double red[32];
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < ns; ++k) acc += Ft[(size_t)k * ns + j] * u[k];
+        v[j] = acc;
+    }
+    __syncthreads();
+    double mean = 0.0;
+    if (dbar) {
+        double sum = 0.0;
+        for (int j = threadIdx.x; j < ns; j += blockDim.x) sum += v[j];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        mean = tot / ns;
+        if (threadIdx.x == 0) dbar[0] += mean;
+    }
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) d[j] += (T)(v[j] - mean);
+}
+
+// Periodic cell: the uniform potential term of the conducting-boundary
+// lattice sum that the root's equivalent density does not carry, (2 pi / 3)
+// (Q2 of the particles - Q2 of the density) for the unit cell (V = 1), Q2 the
+// trace of the second moment about the cell centre.  The particles' Q2 is
+// the sum of the per-leaf sums in leaf order, the density's is g . u(root).
+// One block, fixed summation order.
+__global__ void k_moment_term(int64_t nl, const double *__restrict__ leaf_q2, int ns, const double *__restrict__ g,
+                              const double *__restrict__ u_root, double *pshift) {
+    __shared__ double red[2][32];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < nl; i += blockDim.x) a += leaf_q2[i];
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) b += g[j] * u_root[j];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a;
+        red[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double qa = 0.0, qb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) qa += red[0][w], qb += red[1][w];
+        *pshift = (2.0 * 3.14159265358979323846 / 3.0) * (qa - qb);
+    }
+}
+
+// FP32-based periodic plans: the root's upward check potential in FP64 from
+// its children's (M2M composites in FP64, stored [k][j]); a root that is a
+// leaf keeps its own.  One block.
+__global__ void k_root_up64(int ns, const int32_t *__restrict__ child8, const int32_t *__restrict__ nchild,
+                            const double *__restrict__ m2m64, const float *__restrict__ u, double *__restrict__ u64) {
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+        double acc = 0.0;
+        if (nchild[0] == 0) {
+            acc = (double)u[j];
+        } else {
+            for (int c = 0; c < 8; ++c) {
+                const int32_t ch = child8[c];
+                if (ch < 0) continue;
+                const double *M = m2m64 + (size_t)c * ns * ns;
+                for (int k = 0; k < ns; ++k) acc += M[(size_t)k * ns + j] * (double)u[(size_t)ch * ns + k];
+            }
+        }
+        u64[j] = acc;
+    }
+}
+
+__global__ void k_add_shift(int64_t n, const double *__restrict__ pshift, double4 *__restrict__ res) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) res[i].x += *pshift;
+}
+
 template <typename T>
 cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
@@ -1085,8 +1198,21 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
         stage_begin(P, KIFMM_STAGE_P2L, s);
         ++g_launches, k_p2l<T><<<(unsigned)P.nb, kLeafThreads, 0, s>>>(P.nx, P.xdense, P.lvl, P.cx, P.cy, P.cz,
                                                                         P.first, P.cnt, pts, surf, ns, d, nullptr,
-                                                                        0, split_mean ? P.dbar : nullptr);
+                                                                        0, split_mean ? P.dbar : nullptr, nullptr,
+                                                                        P.periodic ? P.x_sh : nullptr);
         stage_end(P, KIFMM_STAGE_P2L, s);
+    }
+    // the root's upward check potential in FP64 (periodic cell)
+    const double *u_root = nullptr;
+    if (P.periodic) {
+        if constexpr (sizeof(T) == 8) {
+            u_root = (const double *)u;
+        } else {
+            ++g_launches, k_root_up64<<<1, 256, 0, s>>>(ns, P.child8, P.nchild, P.m2m64, u, P.u_root64);
+            u_root = P.u_root64;
+        }
+        // the far images, on the root (box 0) before the downward pass
+        ++g_launches, k_far_root<T><<<1, 256, 0, s>>>(ns, P.far_t, u_root, d, split_mean ? P.dbar : nullptr);
     }
     // downward pass: per level, per octant class of the child
     stage_begin(P, KIFMM_STAGE_L2L, s);
@@ -1107,7 +1233,8 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     stage_end(P, KIFMM_STAGE_LEAF, s);
     stage_begin(P, KIFMM_STAGE_P2P, s);
     LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns,
-              split_mean ? P.dbar : nullptr, P.leaf_tile, P.status};
+              split_mean ? P.dbar : nullptr, P.leaf_tile, P.status, P.periodic ? P.u_sh : nullptr,
+              P.periodic ? P.w_sh : nullptr};
     const LeafW<T> W{(const T *)P.dn_dens, 1, (const T *)P.up_dens, 1, nullptr};
     if (!P.tuned_leaf && tuning_wanted(P, s)) {
         // time every candidate table on this tree; keep the fastest
@@ -1130,6 +1257,10 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
         P.tuned_leaf = true;
     }
     leaf_launch<T>(P, C, pts, surf, W, res, s);
+    if (P.periodic) {
+        ++g_launches, k_moment_term<<<1, 256, 0, s>>>(P.n_leaves, P.leaf_q2, ns, P.far_g, u_root, P.pshift);
+        ++g_launches, k_add_shift<<<grid_for(P.n, 256), 256, 0, s>>>(P.n, P.pshift, res);
+    }
     stage_end(P, KIFMM_STAGE_P2P, s);
     KIFMM_CUDA_TRY(cudaGetLastError());
     // outputs
@@ -1372,7 +1503,7 @@ cudaError_t backward_t(Plan &P, const void *w_user, const void *g_user, const do
         ++g_launches, k_adj_weights<float, T><<<grid_for(P.n, 256), 256, 0, s>>>(
                           P.n, P.perm, P.sys_off_d, P.n_sys, pts, (const float *)w_user, dLdU, res, ws, fwd_pot);
     LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns, nullptr,
-              P.leaf_tile, P.status};
+              P.leaf_tile, P.status, nullptr, nullptr};
     if (g_user) {
         if (P.io_f64)
             ++g_launches, k_gather_g<double, T><<<grid_for(P.n, 256), 256, 0, s>>>(

@@ -91,6 +91,22 @@ struct Plan {
     void *g_sorted = nullptr;
     double *adj_hg = nullptr, *adj_pd = nullptr, *adj_pot = nullptr;
     void *adj_e1 = nullptr, *adj_e2 = nullptr;
+    // Periodic cell (desc.cell > 0): image shifts of the list entries
+    // (int8, (n_x + 1) 9 + (n_y + 1) 3 + (n_z + 1), 13 = the cell itself),
+    // the far-image operator on the root (compute type, stored [k][j] like
+    // the other composites), the root's second-moment functional g (FP64:
+    // the trace of the root's equivalent density's second moment is g . u),
+    // the per-leaf particle second moments and the uniform potential term.
+    bool periodic = false;
+    double cell = 0.0;
+    int8_t *coll_sh = nullptr, *coarse_sh = nullptr, *x_sh = nullptr, *u_sh = nullptr, *w_sh = nullptr;
+    double *far_t = nullptr;     // FP64 in every mode
+    double *far_g = nullptr;
+    double *m2m64 = nullptr;     // FP32-based periodic plans: FP64 copy of the M2M composites
+    double *u_root64 = nullptr;  // ... and the root's upward check potential from them, FP64
+    double *leaf_q2 = nullptr;   // [leaf cap]
+    double *qsum = nullptr;      // [2]: sum q, sum |q| (neutrality)
+    double *pshift = nullptr;    // [1]: uniform potential term (root units)
     bool fwd_valid = false;     // the last evaluate ran on the current sources (densities)
     bool fwd_res_valid = false; // ... and res still holds its field (no backward since)
     // Tensor-core M2L operands (mixed modes), built lazily.
@@ -239,6 +255,10 @@ size_t scan_tmp_needed(int64_t n);
 cudaError_t build_operators(Plan &P, std::string &err);
 // operators.cu: unit-cube surface points [n_s][3], lexicographic.
 std::vector<double> unit_surface(int p);
+// operators.cu: the 316 M2L offsets d (3 ints each), {-3..3}^3 minus {-1..1}^3.
+std::vector<int> m2l_offset_list();
+// periodic.cu: far-image matrix of a periodic cell of side L (host FP64).
+cudaError_t far_image_operator(int p, double L, double *T);
 
 // ---- m2l_tc.cu (mixed modes) ----
 // tree.cu: *moved_dev = 1 if some particle lies outside its leaf by more than

@@ -546,6 +546,58 @@ cudaError_t build_operators(Plan &P, std::string &err) {
         cudaFree(dMean);
     }
     if (P.desc.m2l_eps > 0.0) KIFMM_CUDA_TRY(build_m2l_compressed(P, dK + 16 * nn, Ut_up, Vt_up, sinv_up, err));
+    if (P.periodic) {
+        // Periodic cell (Sec. 2.4).  Far images on the root: K_far is the
+        // far-image matrix (root DC <- root UE over the images beyond the 26
+        // nearest) for the unit box (half-width 1, cell side 2) in this
+        // library's kernel 1/r; the composite F = K_far V diag(sinv) U^T maps
+        // the root's upward check potential to its downward one, like an M2L
+        // block, and is stored transposed ([k][j]) in the compute type.
+        std::vector<double> T(nn);
+        KIFMM_CUDA_TRY(far_image_operator(p, 2.0, T.data()));
+        for (double &v : T) v *= 4.0 * 3.14159265358979323846;
+        double *dKf = nullptr, *dKfV = nullptr, *dF = nullptr;
+        KIFMM_CUDA_TRY(cudaMalloc(&dKf, sizeof(double) * nn));
+        KIFMM_CUDA_TRY(cudaMalloc(&dKfV, sizeof(double) * nn));
+        KIFMM_CUDA_TRY(cudaMalloc(&dF, sizeof(double) * nn));
+        KIFMM_CUDA_TRY(cudaMemcpy(dKf, T.data(), sizeof(double) * nn, cudaMemcpyHostToDevice));
+        gemm(dKf, 1, Vt_up, nullptr, 1, 1.0, dKfV, 0);
+        gemm(dKfV, 1, Ut_up, sinv_up, 0, 1.0, dF, 1);
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.far_t, sizeof(double) * nn));
+        KIFMM_CUDA_TRY(cudaMemcpy(P.far_t, dF, sizeof(double) * nn, cudaMemcpyDeviceToDevice));
+        if (!P.f64) {
+            // FP32-based modes: the root sums the whole neutral cell, whose
+            // contributions cancel; its upward check potential is formed in
+            // FP64 from the level-1 boxes (M2M composites kept in FP64)
+            KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.m2m64, sizeof(double) * 8 * nn));
+            KIFMM_CUDA_TRY(cudaMemcpy(P.m2m64, dOut, sizeof(double) * 8 * nn, cudaMemcpyDeviceToDevice));
+            KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.u_root64, sizeof(double) * n));
+        }
+        // Second-moment functional of the root: the root's equivalent density
+        // (half-width h = 1/2 of the unit root) is h P u with P = V diag(sinv)
+        // U^T, on the points 1.05 h S_k, so the trace of its second moment
+        // about the centre is g . u with g_j = h (1.05 h)^2 sum_k P[k][j] |S_k|^2.
+        std::vector<double> Vt(nn), Ut(nn), si(n);
+        KIFMM_CUDA_TRY(cudaMemcpy(Vt.data(), Vt_up, sizeof(double) * nn, cudaMemcpyDeviceToHost));
+        KIFMM_CUDA_TRY(cudaMemcpy(Ut.data(), Ut_up, sizeof(double) * nn, cudaMemcpyDeviceToHost));
+        KIFMM_CUDA_TRY(cudaMemcpy(si.data(), sinv_up, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        std::vector<double> am(n, 0.0), g(n, 0.0);
+        for (int m = 0; m < n; ++m)  // a_m = sum_k V[k][m] |S_k|^2, V[k][m] = Vt[m][k]
+            for (int k = 0; k < n; ++k)
+                am[m] += Vt[(size_t)m * n + k] * (S[3 * k] * S[3 * k] + S[3 * k + 1] * S[3 * k + 1] + S[3 * k + 2] * S[3 * k + 2]);
+        const double h = 0.5, rz = kAlphaInner * h;
+        for (int j = 0; j < n; ++j) {  // U[j][m] = Ut[m][j]
+            double acc = 0.0;
+            for (int m = 0; m < n; ++m) acc += si[m] * Ut[(size_t)m * n + j] * am[m];
+            g[j] = h * rz * rz * acc;
+        }
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.far_g, sizeof(double) * n));
+        KIFMM_CUDA_TRY(cudaMemcpy(P.far_g, g.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        KIFMM_CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(dKf);
+        cudaFree(dKfV);
+        cudaFree(dF);
+    }
     // surfaces
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf64, sizeof(double) * 3 * n));
     KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf32, sizeof(float) * 3 * n));

@@ -122,6 +122,48 @@ __global__ void k_bbox_final(const unsigned long long *bb, int S, double *lo_sid
     out_scale[2 * s + 1] = c1 / side;
 }
 
+// Periodic cell [0, cell)^3: a coordinate wrapped into it (identity for a
+// free-space plan, cell = 0).
+__device__ __forceinline__ double wrap_cell(double x, double cell) {
+    return cell > 0.0 ? x - cell * floor(x / cell) : x;
+}
+
+// The root cube of a periodic plan is the cell itself.
+__global__ void k_periodic_root(double cell, double *lo_side, double *key_scale, double coef, double *out_scale) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    lo_side[0] = lo_side[1] = lo_side[2] = 0.0;
+    lo_side[3] = cell;
+    key_scale[0] = __ddiv_rn(2097152.0, cell);
+    const double c1 = coef * kInv4Pi / cell;
+    out_scale[0] = c1;
+    out_scale[1] = c1 / cell;
+}
+
+// Neutrality of a periodic cell (Sec. 2.4: the Coulomb lattice sum converges
+// only for a neutral cell): qsum[0] += sum q, qsum[1] += sum |q|.
+template <typename T>
+__global__ void k_charge_sums(int64_t n, const T *__restrict__ q, double *qsum) {
+    double a = 0.0, b = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)q[i];
+        a += v;
+        b += fabs(v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&qsum[0], a);
+        atomicAdd(&qsum[1], b);
+    }
+}
+// rtol: 1e-12 for FP64 charges; 2^-24 for FP32 ones (a neutral set rounded
+// to FP32 sums to at most that fraction of sum |q|).
+__global__ void k_charge_check(const double *qsum, double rtol, int *status) {
+    if (threadIdx.x == 0 && !(fabs(qsum[0]) <= rtol * qsum[1])) set_status(status, KIFMM_ERR_ARG);
+}
+
 __device__ __forceinline__ uint64_t spread3(uint64_t x) {
     x &= 0x1fffffULL;
     x = (x | (x << 32)) & 0x1f00000000ffffULL;
@@ -137,14 +179,14 @@ __device__ __forceinline__ uint64_t spread3(uint64_t x) {
 template <typename T>
 __global__ void k_keys(int64_t n, const T *__restrict__ xyz, const int64_t *__restrict__ off, int S,
                        const double *__restrict__ lo_side, const double *__restrict__ key_scale, uint64_t *keys,
-                       uint32_t *vals, uint64_t *keys_user) {
+                       uint32_t *vals, uint64_t *keys_user, double cell) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int s = find_sys(off, S, i);
     const double sc = key_scale[s];
     uint64_t k[3];
     for (int d = 0; d < 3; ++d) {
-        double t = __dmul_rn(__dsub_rn((double)xyz[3 * i + d], lo_side[s * 4 + d]), sc);
+        double t = __dmul_rn(__dsub_rn(wrap_cell((double)xyz[3 * i + d], cell), lo_side[s * 4 + d]), sc);
         double f = floor(t);
         k[d] = (f >= 2097151.0) ? 2097151ULL : (uint64_t)(f > 0.0 ? f : 0.0);
     }
@@ -442,7 +484,7 @@ __global__ void k_gather(int64_t n_leaves, const int32_t *__restrict__ leaves, c
                          const int32_t *__restrict__ cz, const int32_t *__restrict__ sys,
                          const double *__restrict__ lo_side, const uint32_t *__restrict__ perm,
                          const TI *__restrict__ xyz, const TI *__restrict__ q,
-                         typename Vec4<TC>::type *pts) {
+                         typename Vec4<TC>::type *pts, double cell, double *leaf_q2) {
     // one warp per leaf
     const int64_t li = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (li >= n_leaves) return;
@@ -458,21 +500,32 @@ __global__ void k_gather(int64_t n_leaves, const int32_t *__restrict__ leaves, c
     // of a domain whose corner lies far from it)
     const double C[3] = {fma((cx[b] + 0.5) * w, side, lo[0]), fma((cy[b] + 0.5) * w, side, lo[1]),
                          fma((cz[b] + 0.5) * w, side, lo[2])};
+    double q2 = 0.0;  // periodic cell: sum q |x - c_cell|^2 of the leaf, root units
     for (int k = threadIdx.x & 31; k < cnt[b]; k += 32) {
         const int64_t i = first[b] + k;
         const uint32_t j = perm[i];
         double r[3];
         // FP64 records keep the correctly rounded quotient (FP64 parity); FP32
         // records are rounded to FP32 anyway, so a reciprocal multiply will do
-        for (int d = 0; d < 3; ++d)
-            r[d] = sizeof(TC) == 8 ? ((double)xyz[3 * j + d] - C[d]) / side
-                                   : ((double)xyz[3 * j + d] - C[d]) * inv_side;
+        for (int d = 0; d < 3; ++d) {
+            const double x = wrap_cell((double)xyz[3 * j + d], cell);
+            r[d] = sizeof(TC) == 8 ? (x - C[d]) / side : (x - C[d]) * inv_side;
+        }
         typename Vec4<TC>::type v;
         v.x = (TC)r[0];
         v.y = (TC)r[1];
         v.z = (TC)r[2];
         v.w = (TC)q[j];
         pts[i] = v;
+        if (leaf_q2) {
+            const double ex = (cx[b] + 0.5) * w + r[0] - 0.5, ey = (cy[b] + 0.5) * w + r[1] - 0.5,
+                         ez = (cz[b] + 0.5) * w + r[2] - 0.5;
+            q2 += (double)q[j] * (ex * ex + ey * ey + ez * ez);
+        }
+    }
+    if (leaf_q2) {
+        for (int o = 16; o > 0; o >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, o);
+        if ((threadIdx.x & 31) == 0) leaf_q2[li] = q2;
     }
 }
 
@@ -486,7 +539,7 @@ __global__ void k_leaf_check(int64_t n_leaves, const int32_t *__restrict__ leave
                              const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
                              const int32_t *__restrict__ cz, const int32_t *__restrict__ sys,
                              const double *__restrict__ lo_side, const uint32_t *__restrict__ perm,
-                             const TI *__restrict__ xyz, double margin, int *moved) {
+                             const TI *__restrict__ xyz, double margin, int *moved, double cell) {
     const int64_t li = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (li >= n_leaves) return;
     const int b = leaves[li];
@@ -500,7 +553,7 @@ __global__ void k_leaf_check(int64_t n_leaves, const int32_t *__restrict__ leave
     for (int k = threadIdx.x & 31; k < cnt[b]; k += 32) {
         const uint32_t j = perm[first[b] + k];
         for (int d = 0; d < 3; ++d) {
-            const double r = ((double)xyz[3 * j + d] - lo[d]) * inv_side - c[d];
+            const double r = (wrap_cell((double)xyz[3 * j + d], cell) - lo[d]) * inv_side - c[d];
             bad = bad || !(fabs(r) <= lim);  // also catches NaN
         }
     }
@@ -510,27 +563,62 @@ __global__ void k_leaf_check(int64_t n_leaves, const int32_t *__restrict__ leave
 // ---------------------------------------------------------------------------
 // Lists
 // ---------------------------------------------------------------------------
+// Periodic cell (Sec. 2.4): a list entry is a box plus the image it is taken
+// in, an image shift n in {-1, 0, 1}^3 stored as (n_x + 1) 9 + (n_y + 1) 3 +
+// (n_z + 1) (13: the cell itself).  Shift arrays are null for a free-space
+// plan, whose entries are all in the cell.
+struct ListShifts {
+    int8_t *coll, *coarse, *x, *u, *w;  // parallel to coll, coarse, xdense, u_idx, w_idx
+};
+__device__ __forceinline__ int shift_of(const int8_t *sh, int64_t i) { return sh ? (int)sh[i] : 13; }
+// The shift of image s in boxes of `level` along each axis.
+__device__ __forceinline__ void shift_boxes(int s, int level, int &ox, int &oy, int &oz) {
+    ox = (s / 9 - 1) << level;
+    oy = ((s / 3) % 3 - 1) << level;
+    oz = (s % 3 - 1) << level;
+}
+// adjacent(box a in image sa, box at (lb, bx, by, bz))
+__device__ __forceinline__ bool adjacent_img(int la, int ax, int ay, int az, int sa, int lb, int bx, int by, int bz) {
+    int ox, oy, oz;
+    shift_boxes(sa, la, ox, oy, oz);
+    return boxes_adjacent(la, ax + ox, ay + oy, az + oz, lb, bx, by, bz);
+}
+
 // One warp per box: lane k < 27 scans the children of the parent's colleague
-// k; every child adjacent to (or equal to) b lands in its own slot.
+// k (in that colleague's image); every child adjacent to (or equal to) b
+// lands in its own slot.  In a periodic cell the root's colleagues are its 27
+// images (itself included).
 __device__ __forceinline__ void dev_colleagues(int64_t b, int lane, int level, const int32_t *__restrict__ parent,
                                                const int32_t *__restrict__ child_first,
                                                const int32_t *__restrict__ nchild, const int32_t *__restrict__ cx,
                                                const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
-                                               int32_t *coll) {
+                                               int32_t *coll, const ListShifts &sh) {
     int32_t *cb = coll + b * kColl;
     // cb was set to -1 by a memset of the whole array before the first level
     if (level == 0) {
-        if (lane == 0) cb[13] = (int32_t)b;
+        if (sh.coll) {
+            if (lane < kColl) {
+                cb[lane] = (int32_t)b;
+                sh.coll[b * kColl + lane] = (int8_t)lane;
+            }
+        } else if (lane == 0) {
+            cb[13] = (int32_t)b;
+        }
         return;
     }
     if (lane >= kColl) return;
     const int32_t c = coll[(int64_t)parent[b] * kColl + lane];
     if (c < 0) return;
+    const int sc = shift_of(sh.coll, (int64_t)parent[b] * kColl + lane);
+    int ox, oy, oz;
+    shift_boxes(sc, level, ox, oy, oz);
     const int bx = cx[b], by = cy[b], bz = cz[b];
     for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
-        const int dx = cx[ch] - bx, dy = cy[ch] - by, dz = cz[ch] - bz;
+        const int dx = cx[ch] + ox - bx, dy = cy[ch] + oy - by, dz = cz[ch] + oz - bz;
         if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
-        cb[(dx + 1) * 9 + (dy + 1) * 3 + (dz + 1)] = ch;
+        const int slot = (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
+        cb[slot] = ch;
+        if (sh.coll) sh.coll[b * kColl + slot] = (int8_t)sc;
     }
 }
 
@@ -542,7 +630,7 @@ __device__ __forceinline__ void dev_coarse(int64_t b, int lane, int level, const
                                            const int32_t *__restrict__ nchild, const int32_t *__restrict__ lvl,
                                            const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
                                            const int32_t *__restrict__ cz, const int32_t *coll, int32_t *coarse,
-                                           int32_t *ncoarse, int *status) {
+                                           int32_t *ncoarse, int *status, const ListShifts &sh) {
     const unsigned below = (1u << lane) - 1u;
     int n = 0;
     int32_t *out = coarse + b * kMaxCoarse;
@@ -550,28 +638,38 @@ __device__ __forceinline__ void dev_coarse(int64_t b, int lane, int level, const
         const int32_t P = parent[b];
         const int np = ncoarse[P];  // <= kMaxCoarse < 32
         int32_t a = -1;
+        int sa = 13;
         bool keep = false;
         if (lane < np) {
             a = coarse[(int64_t)P * kMaxCoarse + lane];
-            keep = boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], level, cx[b], cy[b], cz[b]);
+            sa = shift_of(sh.coarse, (int64_t)P * kMaxCoarse + lane);
+            keep = adjacent_img(lvl[a], cx[a], cy[a], cz[a], sa, level, cx[b], cy[b], cz[b]);
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (keep) {
             const int pos = __popc(m & below);
-            if (pos < kMaxCoarse) out[pos] = a;
+            if (pos < kMaxCoarse) {
+                out[pos] = a;
+                if (sh.coarse) sh.coarse[b * kMaxCoarse + pos] = (int8_t)sa;
+            }
         }
         n = __popc(m);
     }
     int32_t c = -1;
+    int sc = 13;
     bool keep = false;
     if (lane < kColl && lane != 13) {
         c = coll[b * kColl + lane];
         keep = c >= 0 && nchild[c] == 0;
+        if (keep) sc = shift_of(sh.coll, b * kColl + lane);
     }
     const unsigned m = __ballot_sync(0xffffffffu, keep);
     if (keep) {
         const int pos = n + __popc(m & below);
-        if (pos < kMaxCoarse) out[pos] = c;
+        if (pos < kMaxCoarse) {
+            out[pos] = c;
+            if (sh.coarse) sh.coarse[b * kMaxCoarse + pos] = (int8_t)sc;
+        }
     }
     n += __popc(m);
     if (lane == 0) {
@@ -619,7 +717,9 @@ __device__ __forceinline__ void dev_vx(int64_t b, int lane, int level, int thr, 
                                        const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
                                        const int32_t *coll, const int32_t *coarse, const int32_t *ncoarse,
                                        int32_t *vdense, int32_t *nv, int32_t *xdense, int32_t *nx,
-                                       unsigned long long *totals) {
+                                       unsigned long long *totals, const ListShifts &sh) {
+    // (a V-list slot fixes the source's offset, so the slot table needs no
+    // image shift: the source's expansion is the same in every image)
     int32_t *vb = vdense + b * kVSlots;  // preset to -1 by a memset
     int cntv = 0, cntx = 0;
     if (level > 0) {
@@ -629,8 +729,10 @@ __device__ __forceinline__ void dev_vx(int64_t b, int lane, int level, int thr, 
         if (lane < kColl) {
             const int32_t c = coll[(int64_t)P * kColl + lane];
             if (c >= 0) {
+                int sx, sy, sz;
+                shift_boxes(shift_of(sh.coll, (int64_t)P * kColl + lane), level, sx, sy, sz);
                 for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
-                    const int dx = cx[ch] - bx, dy = cy[ch] - by, dz = cz[ch] - bz;
+                    const int dx = cx[ch] + sx - bx, dy = cy[ch] + sy - by, dz = cz[ch] + sz - bz;
                     if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
                     const int sl = v_slot(ox, oy, oz, dx, dy, dz);
                     if (sl < 0) continue;  // unreachable: children of parent colleagues lie in the class window
@@ -644,13 +746,19 @@ __device__ __forceinline__ void dev_vx(int64_t b, int lane, int level, int thr, 
         if (!direct_box(nchild, cnt, thr, (int32_t)b)) {
             const int np = ncoarse[P];
             int32_t a = -1;
+            int sa = 13;
             bool keep = false;
             if (lane < np) {
                 a = coarse[(int64_t)P * kMaxCoarse + lane];
-                keep = !boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], level, bx, by, bz);
+                sa = shift_of(sh.coarse, (int64_t)P * kMaxCoarse + lane);
+                keep = !adjacent_img(lvl[a], cx[a], cy[a], cz[a], sa, level, bx, by, bz);
             }
             const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (keep) xdense[b * kMaxCoarse + __popc(m & ((1u << lane) - 1u))] = a;
+            if (keep) {
+                const int pos = __popc(m & ((1u << lane) - 1u));
+                xdense[b * kMaxCoarse + pos] = a;
+                if (sh.x) sh.x[b * kMaxCoarse + pos] = (int8_t)sa;
+            }
             cntx = __popc(m);
         }
     }
@@ -675,7 +783,8 @@ __global__ void k_uw(int64_t nb, int pass, int thr, const int32_t *__restrict__ 
                      const int32_t *__restrict__ cz, const int32_t *__restrict__ coll,
                      const int32_t *__restrict__ coarse, const int32_t *__restrict__ ncoarse,
                      uint32_t *u_cnt, uint32_t *w_cnt, const uint32_t *__restrict__ u_ptr,
-                     const uint32_t *__restrict__ w_ptr, int32_t *u_idx, int32_t *w_idx, int *status) {
+                     const uint32_t *__restrict__ w_ptr, int32_t *u_idx, int32_t *w_idx, int *status,
+                     ListShifts sh) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     if (nchild[b] != 0) {
@@ -685,33 +794,43 @@ __global__ void k_uw(int64_t nb, int pass, int thr, const int32_t *__restrict__ 
     const int lb = lvl[b], bx = cx[b], by = cy[b], bz = cz[b];
     uint32_t nu = 0, nw = 0;
     const uint32_t u0 = pass ? u_ptr[b] : 0, w0 = pass ? w_ptr[b] : 0;
-    if (pass) u_idx[u0 + nu] = (int32_t)b;
-    ++nu;
-    for (int k = 0; k < ncoarse[b]; ++k) {
-        if (pass) u_idx[u0 + nu] = coarse[b * kMaxCoarse + k];
+    auto put_u = [&](int32_t a, int sa) {
+        if (pass) {
+            u_idx[u0 + nu] = a;
+            if (sh.u) sh.u[u0 + nu] = (int8_t)sa;
+        }
         ++nu;
-    }
+    };
+    auto put_w = [&](int32_t a, int sa) {
+        if (pass) {
+            w_idx[w0 + nw] = a;
+            if (sh.w) sh.w[w0 + nw] = (int8_t)sa;
+        }
+        ++nw;
+    };
+    put_u((int32_t)b, 13);
+    for (int k = 0; k < ncoarse[b]; ++k) put_u(coarse[b * kMaxCoarse + k], shift_of(sh.coarse, b * kMaxCoarse + k));
     if (lb > 0 && direct_box(nchild, cnt, thr, (int32_t)b)) {
         const int32_t P = parent[b];
         for (int k = 0; k < ncoarse[P]; ++k) {
             const int32_t a = coarse[(int64_t)P * kMaxCoarse + k];
-            if (boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], lb, bx, by, bz)) continue;
-            if (pass) u_idx[u0 + nu] = a;
-            ++nu;
+            const int sa = shift_of(sh.coarse, (int64_t)P * kMaxCoarse + k);
+            if (adjacent_img(lvl[a], cx[a], cy[a], cz[a], sa, lb, bx, by, bz)) continue;
+            put_u(a, sa);
         }
     }
     int32_t stack[8 * (kMaxLevel + 1)];
     for (int k = 0; k < kColl; ++k) {
         const int32_t c = coll[b * kColl + k];
         if (k == 13 || c < 0 || nchild[c] == 0) continue;
+        const int sc = shift_of(sh.coll, b * kColl + k);  // every descendant is taken in this image
         int sp = 0;
         for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) stack[sp++] = ch;
         while (sp > 0) {
             const int32_t a = stack[--sp];
-            if (boxes_adjacent(lvl[a], cx[a], cy[a], cz[a], lb, bx, by, bz)) {
+            if (adjacent_img(lvl[a], cx[a], cy[a], cz[a], sc, lb, bx, by, bz)) {
                 if (nchild[a] == 0) {
-                    if (pass) u_idx[u0 + nu] = a;
-                    ++nu;
+                    put_u(a, sc);
                 } else {
                     if (sp + nchild[a] > 8 * (kMaxLevel + 1)) {
                         set_status(status, KIFMM_ERR_CAPACITY);
@@ -720,11 +839,9 @@ __global__ void k_uw(int64_t nb, int pass, int thr, const int32_t *__restrict__ 
                     for (int32_t ch = child_first[a]; ch < child_first[a] + nchild[a]; ++ch) stack[sp++] = ch;
                 }
             } else if (direct_box(nchild, cnt, thr, a)) {
-                if (pass) u_idx[u0 + nu] = a;
-                ++nu;
+                put_u(a, sc);
             } else {
-                if (pass) w_idx[w0 + nw] = a;
-                ++nw;
+                put_w(a, sc);
             }
         }
     }
@@ -957,14 +1074,25 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
     else
         ++g_launches, k_bbox<float><<<nt, kBlock, 0, s>>>(n, (const float *)xyz, (const float *)q, P.sys_off_d, S,
                                             P.bbox_ord, P.status);
-    ++g_launches, k_bbox_final<<<grid_for(S, 128), 128, 0, s>>>(P.bbox_ord, S, P.lo_side, P.key_scale, P.coef,
-                                                                P.out_scale);
+    if (P.periodic) {
+        // the root is the cell; the cell must be neutral
+        ++g_launches, k_periodic_root<<<1, 32, 0, s>>>(P.cell, P.lo_side, P.key_scale, P.coef, P.out_scale);
+        KIFMM_CUDA_TRY(cudaMemsetAsync(P.qsum, 0, 2 * sizeof(double), s));
+        if (P.io_f64)
+            ++g_launches, k_charge_sums<double><<<std::min<unsigned>(nt, 1024), 256, 0, s>>>(n, (const double *)q, P.qsum);
+        else
+            ++g_launches, k_charge_sums<float><<<std::min<unsigned>(nt, 1024), 256, 0, s>>>(n, (const float *)q, P.qsum);
+        ++g_launches, k_charge_check<<<1, 32, 0, s>>>(P.qsum, P.io_f64 ? 1e-12 : 0x1p-24, P.status);
+    } else {
+        ++g_launches, k_bbox_final<<<grid_for(S, 128), 128, 0, s>>>(P.bbox_ord, S, P.lo_side, P.key_scale, P.coef,
+                                                                    P.out_scale);
+    }
     if (P.io_f64)
         ++g_launches, k_keys<double><<<grid_for(n, 256), 256, 0, s>>>(n, (const double *)xyz, P.sys_off_d, S, P.lo_side,
-                                                       P.key_scale, P.keys[0], P.vals[0], P.keys_user);
+                                                       P.key_scale, P.keys[0], P.vals[0], P.keys_user, P.cell);
     else
         ++g_launches, k_keys<float><<<grid_for(n, 256), 256, 0, s>>>(n, (const float *)xyz, P.sys_off_d, S, P.lo_side,
-                                                      P.key_scale, P.keys[0], P.vals[0], P.keys_user);
+                                                      P.key_scale, P.keys[0], P.vals[0], P.keys_user, P.cell);
     KIFMM_CUDA_TRY(cudaGetLastError());
     // Sort only the key digits the octree will read: two levels below the
     // last tree's depth (or an estimate from N / M before the first tree),
@@ -1128,11 +1256,11 @@ cudaError_t check_leaves(Plan &P, const void *xyz, double skin, int *moved_dev, 
     if (P.io_f64)
         ++g_launches, k_leaf_check<double><<<g, 256, 0, s>>>(P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx,
                                                              P.cy, P.cz, P.sys, P.lo_side, P.perm,
-                                                             (const double *)xyz, margin, moved_dev);
+                                                             (const double *)xyz, margin, moved_dev, P.cell);
     else
         ++g_launches, k_leaf_check<float><<<g, 256, 0, s>>>(P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx,
                                                             P.cy, P.cz, P.sys, P.lo_side, P.perm,
-                                                            (const float *)xyz, margin, moved_dev);
+                                                            (const float *)xyz, margin, moved_dev, P.cell);
     return cudaGetLastError();
 }
 
@@ -1144,20 +1272,20 @@ cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream
         if (P.io_f64)
             ++g_launches, k_gather<double, double><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
                 P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
-                (const double *)xyz, (const double *)q, (double4 *)P.pts);
+                (const double *)xyz, (const double *)q, (double4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
         else
             ++g_launches, k_gather<float, double><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
                 P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
-                (const float *)xyz, (const float *)q, (double4 *)P.pts);
+                (const float *)xyz, (const float *)q, (double4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
     } else {
         if (P.io_f64)
             ++g_launches, k_gather<double, float><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
                 P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
-                (const double *)xyz, (const double *)q, (float4 *)P.pts);
+                (const double *)xyz, (const double *)q, (float4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
         else
             ++g_launches, k_gather<float, float><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
                 P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
-                (const float *)xyz, (const float *)q, (float4 *)P.pts);
+                (const float *)xyz, (const float *)q, (float4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
     }
     return cudaGetLastError();
 }
@@ -1172,16 +1300,21 @@ __global__ void k_lists_level(int64_t ls, int64_t le, int level, int thr, const 
                               const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
                               const int32_t *__restrict__ cz, int32_t *coll, int32_t *coarse, int32_t *ncoarse,
                               int32_t *vdense, int32_t *nv, int32_t *xdense, int32_t *nx,
-                              unsigned long long *totals, int *status) {
+                              unsigned long long *totals, int *status, ListShifts sh) {
     const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= le) return;
-    dev_colleagues(b, lane, level, parent, child_first, nchild, cx, cy, cz, coll);
+    dev_colleagues(b, lane, level, parent, child_first, nchild, cx, cy, cz, coll, sh);
     __syncwarp();
-    dev_coarse(b, lane, level, parent, nchild, lvl, cx, cy, cz, coll, coarse, ncoarse, status);
+    dev_coarse(b, lane, level, parent, nchild, lvl, cx, cy, cz, coll, coarse, ncoarse, status, sh);
     __syncwarp();
     dev_vx(b, lane, level, thr, parent, child_first, nchild, cnt, lvl, cx, cy, cz, coll, coarse, ncoarse, vdense,
-           nv, xdense, nx, totals);
+           nv, xdense, nx, totals, sh);
+}
+
+static ListShifts list_shifts(const Plan &P) {
+    if (!P.periodic) return ListShifts{nullptr, nullptr, nullptr, nullptr, nullptr};
+    return ListShifts{P.coll_sh, P.coarse_sh, P.x_sh, P.u_sh, P.w_sh};
 }
 
 cudaError_t build_lists(Plan &P, cudaStream_t s) {
@@ -1194,12 +1327,14 @@ cudaError_t build_lists(Plan &P, cudaStream_t s) {
         const unsigned g = grid_for(le - ls, 8);  // warp per box, 8 per block
         ++g_launches, k_lists_level<<<g, 256, 0, s>>>(ls, le, l, P.direct_thr, P.parent, P.child_first, P.nchild,
                                                       P.cnt, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse, P.ncoarse,
-                                                      P.vdense, P.nv, P.xdense, P.nx, P.list_totals, P.status);
+                                                      P.vdense, P.nv, P.xdense, P.nx, P.list_totals, P.status,
+                                                      list_shifts(P));
         KIFMM_CUDA_TRY(cudaGetLastError());
     }
     const unsigned g = grid_for(nb, 128);
     ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 0, P.direct_thr, P.parent, P.cnt, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse,
-                                         P.ncoarse, P.u_cnt, P.w_cnt, nullptr, nullptr, nullptr, nullptr, P.status);
+                                         P.ncoarse, P.u_cnt, P.w_cnt, nullptr, nullptr, nullptr, nullptr, P.status,
+                                         list_shifts(P));
     // two scans, totals in the last two scratch words; one synchronisation for all list sizes
     uint32_t *tot_u = P.scan_tmp + P.scan_tmp_elems - 1, *tot_w = P.scan_tmp + P.scan_tmp_elems - 2;
     KIFMM_CUDA_TRY(exclusive_scan_u32(P.u_cnt, P.u_ptr, nb, tot_u, P.scan_tmp, P.scan_tmp_elems - 2, s));
@@ -1221,14 +1356,17 @@ cudaError_t build_lists(Plan &P, cudaStream_t s) {
         if (P.n_u > P.u_cap) {
             P.u_cap = P.n_u + P.n_u / 4 + 1024;
             KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.u_idx, sizeof(int32_t) * P.u_cap));
+            if (P.periodic) KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.u_sh, P.u_cap));
         }
         if (P.n_w > P.w_cap) {
             P.w_cap = P.n_w + P.n_w / 4 + 1024;
             KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.w_idx, sizeof(int32_t) * P.w_cap));
+            if (P.periodic) KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.w_sh, P.w_cap));
         }
     }
     ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 1, P.direct_thr, P.parent, P.cnt, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse,
-                                         P.ncoarse, P.u_cnt, P.w_cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, P.status);
+                                         P.ncoarse, P.u_cnt, P.w_cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, P.status,
+                                         list_shifts(P));
     KIFMM_CUDA_TRY(cudaMemsetAsync(P.wsrc_flag, 0, sizeof(int32_t) * nb, s));
     if (P.n_w > 0) ++g_launches, k_mark_w<<<grid_for(P.n_w, 256), 256, 0, s>>>(P.n_w, P.w_idx, P.wsrc_flag);
     KIFMM_CUDA_TRY(cudaGetLastError());

@@ -31,7 +31,8 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("precision", ctypes.c_int), ("coef", ctypes.c_double), ("n_max", ctypes.c_int64),
                 ("n_systems_max", ctypes.c_int), ("dtype", ctypes.c_int), ("pinv_eps", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("direct_max", ctypes.c_int), ("m2l_eps", ctypes.c_double)]
+                ("autotune", ctypes.c_int), ("direct_max", ctypes.c_int), ("m2l_eps", ctypes.c_double),
+                ("cell", ctypes.c_double)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -58,7 +59,8 @@ EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifm
            "kifmm_clump_reduce", "kifmm_backward", "kifmm_get_device_status", "kifmm_status_string",
            "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
            "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources",
-           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_refresh_sources", "kifmm_lr_stride", "kifmm_far_image_operator"]
+           "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_refresh_sources", "kifmm_lr_stride", "kifmm_far_image_operator",
+           "kifmm_copy_list_images"]
 
 
 def load(path: str = LIB_PATH):
@@ -90,6 +92,7 @@ def load(path: str = LIB_PATH):
     lib.kifmm_refresh_sources.argtypes = [P, P, P, D, ctypes.POINTER(I), P]
     lib.kifmm_lr_stride.argtypes = [D, D, ctypes.POINTER(I64)]
     lib.kifmm_far_image_operator.argtypes = [I, D, P]
+    lib.kifmm_copy_list_images.argtypes = [P, I, P, P, P]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int if name != "kifmm_status_string" else ctypes.c_char_p
     _LIB = lib
@@ -125,7 +128,7 @@ class Plan:
     def __init__(self, p: int = 6, leaf_cap: int = 128, max_depth: int = 20, precision: str = "fp32",
                  coef: float = 1.0, n_max: int = 1 << 20, n_systems_max: int = 1,
                  dtype: torch.dtype = torch.float32, pinv_eps: float = 0.0, autotune: bool = False,
-                 direct_max: int = 0, m2l_eps: float = 0.0):
+                 direct_max: int = 0, m2l_eps: float = 0.0, cell: float = 0.0):
         lib = load()
         self.dtype = dtype
         self.precision = precision
@@ -133,7 +136,7 @@ class Plan:
         d = PlanDesc(p=p, leaf_cap=leaf_cap, max_depth=max_depth, precision=PRECISIONS[precision], coef=coef,
                      n_max=n_max, n_systems_max=n_systems_max,
                      dtype=1 if dtype == torch.float64 else 0, pinv_eps=pinv_eps, autotune=int(autotune), direct_max=direct_max,
-                     m2l_eps=m2l_eps)
+                     m2l_eps=m2l_eps, cell=cell)
         h = ctypes.c_void_p()
         _check(lib.kifmm_plan_create(ctypes.byref(d), ctypes.byref(h)), "kifmm_plan_create")
         self._h = h
@@ -299,6 +302,20 @@ class Plan:
         c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         _check(lib.kifmm_copy_expansions(self._h, c(u), c(d), c(res)), "kifmm_copy_expansions")
         return u, d, res
+
+    def list_images(self, kind: str):
+        """(ptr, idx, img): one list kind as CSR with the image of every entry
+        ((n_x + 1) 9 + (n_y + 1) 3 + (n_z + 1), 13 = the cell itself), sorted
+        by (box, image) (see kifmm_copy_list_images)."""
+        nb = self.tree_info()["n_boxes"]
+        ptr = np.empty(nb + 1, dtype=np.int64)
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(load().kifmm_copy_list_images(self._h, LIST_KINDS[kind], c(ptr), None, None), "kifmm_copy_list_images")
+        idx = np.empty(max(int(ptr[-1]), 1), dtype=np.int64)
+        img = np.empty(max(int(ptr[-1]), 1), dtype=np.int64)
+        _check(load().kifmm_copy_list_images(self._h, LIST_KINDS[kind], c(ptr), c(idx), c(img)),
+               "kifmm_copy_list_images")
+        return ptr, idx[:int(ptr[-1])], img[:int(ptr[-1])]
 
     def list(self, kind: str):
         info = self.tree_info()

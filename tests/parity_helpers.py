@@ -37,3 +37,24 @@ def rounding_floor(x, q, p, M, pot_o, grad_o, **kw):
         fp = max(fp, O.rel_l2(a * po, pot_o))
         fg = max(fg, O.rel_l2(a * a * go, grad_o))
     return max(1e-12, 10 * fp), max(1e-12, 10 * fg)
+
+
+def periodic_rounding_floor(x, q, L, p, M, pot_o, grad_o):
+    """The same for the periodic method (oracle.kifmm_periodic): its change
+    under the operator perturbation (two seeds) and under a scaling of the
+    whole cell, x -> a x and L -> a L (a translation would move particles
+    across the cell boundary, which changes the tree, not just the rounding).
+    The periodic potential reads the root's equivalent density through the
+    far-image operator and the second-moment term, so it inherits the
+    pseudo-inverse's conditioning: at p = 6 two correct FP64 evaluations
+    differ by ~1e-8 in the potential and ~2e-10 in the gradient."""
+    fp = fg = 0.0
+    for seed in (1, 2):
+        po, go = O.kifmm_periodic(x, q, L, p=p, leaf_cap=M, ops=O.operators_perturbed(p, seed))
+        fp = max(fp, O.rel_l2(po, pot_o))
+        fg = max(fg, O.rel_l2(go, grad_o))
+    for a in (3.0, 0.7):
+        po, go = O.kifmm_periodic(a * x, q, a * L, p=p, leaf_cap=M)
+        fp = max(fp, O.rel_l2(a * po, pot_o))
+        fg = max(fg, O.rel_l2(a * a * go, grad_o))
+    return max(1e-12, 10 * fp), max(1e-12, 10 * fg)
