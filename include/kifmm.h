@@ -131,7 +131,20 @@ typedef struct {
                             pseudo-inverse (a constant offset of every
                             potential; gradients, forces and the energy of a
                             neutral cell do not depend on it).              */
+    int kernel;          /* kifmm_kernel: the kernel of the sum of Eq. 1      */
 } kifmm_plan_desc;
+
+/* Kernels of Eq. 1.  The Laplace kernel is the default (1/(4 pi r) times
+ * coef, Eq. 3; scalar charges; outputs potential, gradient, energy).  The
+ * Stokeslet, G(r) = (I / |r| + r r^T / |r|^3) / (8 pi) times coef (coef =
+ * 1 / mu: the velocity of point forces in Stokes flow, Sec. 2.4), is the
+ * tensor-kernel form Eq. 1 admits: set_sources takes forces [N, 3] in place
+ * of q, evaluate writes velocities [N, 3] to pot (grad and energy must be
+ * NULL).  Same tree, lists, surfaces and pseudo-inverse rules, with 3-vector
+ * densities on the surfaces.  Stokeslet plans run in KIFMM_FP64 or
+ * KIFMM_FP32, free space, with no compressed M2L, clump reduce or adjoint
+ * (KIFMM_ERR_ARG). */
+typedef enum { KIFMM_KERNEL_LAPLACE = 0, KIFMM_KERNEL_STOKESLET = 1 } kifmm_kernel;
 
 typedef struct kifmm_plan kifmm_plan;
 

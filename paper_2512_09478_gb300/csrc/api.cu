@@ -239,13 +239,19 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     if (!(d.m2l_eps >= 0.0) || d.m2l_eps >= 1.0) return KIFMM_ERR_ARG;
     if (d.m2l_eps > 0.0 && d.precision != KIFMM_MIXED_FP16) return KIFMM_ERR_ARG;
     if (!(d.cell >= 0.0) || !std::isfinite(d.cell)) return KIFMM_ERR_ARG;
+    if (d.kernel != KIFMM_KERNEL_LAPLACE && d.kernel != KIFMM_KERNEL_STOKESLET) return KIFMM_ERR_ARG;
+    if (d.kernel == KIFMM_KERNEL_STOKESLET &&
+        (d.precision == KIFMM_MIXED_FP16 || d.m2l_eps != 0.0 || d.cell != 0.0 || d.p > 8))
+        return KIFMM_ERR_ARG;
     if (d.cell > 0.0 && d.n_systems_max != 1) return KIFMM_ERR_ARG;  // one periodic cell per plan
     kifmm_plan *pl = new (std::nothrow) kifmm_plan();
     if (!pl) return KIFMM_ERR_CUDA;
     Plan &P = pl->P;
     P.desc = d;
     P.p = d.p;
-    P.ns = 6 * (d.p - 1) * (d.p - 1) + 2;
+    P.nsurf = 6 * (d.p - 1) * (d.p - 1) + 2;
+    P.stokes = d.kernel == KIFMM_KERNEL_STOKESLET;
+    P.ns = P.stokes ? 3 * P.nsurf : P.nsurf;
     P.f64 = (d.precision == KIFMM_FP64);
     P.io_f64 = (d.dtype == KIFMM_DTYPE_F64);
     P.coef = (d.coef == 0.0) ? 1.0 : d.coef;
@@ -253,7 +259,7 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     // them only inflates the composite operators (at p = 8 their entries grow
     // ~30x and so does the FP32 rounding of every translation).
     P.eps = (d.pinv_eps != 0.0) ? d.pinv_eps : (P.f64 ? 1e-12 : 1e-9);
-    P.direct_thr = (d.direct_max < 0) ? -1 : (d.direct_max == 0 ? P.ns : d.direct_max);
+    P.direct_thr = (d.direct_max < 0) ? -1 : (d.direct_max == 0 ? P.nsurf : d.direct_max);
     P.leaf_tile = leaf_tiling_candidate(0);
     P.periodic = d.cell > 0.0;
     P.cell = d.cell;
@@ -306,6 +312,7 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {(void **)&P.list_totals, sizeof(unsigned long long) * 4},
         {(void **)&P.energy_chunk_start, sizeof(int32_t) * (P.sys_cap + 1)},
         {(void **)&P.qsum, sizeof(double) * 2},
+        {&P.frc, P.stokes ? esz * 3 * n : 8},
         {(void **)&P.pshift, sizeof(double)},
     };
     for (const A &a : arrs)
@@ -414,6 +421,7 @@ static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cu
 kifmm_status kifmm_evaluate(kifmm_plan *pl, void *pot, void *grad, double *energy, kifmm_stream_t stream) {
     if (!pl) return KIFMM_ERR_ARG;
     Plan &P = pl->P;
+    if (P.stokes && (grad || energy)) return KIFMM_ERR_ARG;  // Stokeslet: velocities in pot only
     if (!P.has_sources) return KIFMM_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     P.last_stream = s;
@@ -433,6 +441,7 @@ kifmm_status kifmm_clump_reduce(kifmm_plan *pl, int64_t n_clumps, const int64_t 
     if (!pl || n_clumps < 0) return KIFMM_ERR_ARG;
     if (n_clumps > 0 && (!clump_offsets || !xyz || !q || !grad || !ref || !force || !torque)) return KIFMM_ERR_ARG;
     Plan &P = pl->P;
+    if (P.stokes) return KIFMM_ERR_ARG;  // forces from charges: the Laplace kernel only
     cudaStream_t s = (cudaStream_t)stream;
     P.last_stream = s;
     return from_cuda(run_clump_reduce(P, n_clumps, clump_offsets, xyz, q, grad, ref, force, torque, s));
@@ -441,7 +450,7 @@ kifmm_status kifmm_clump_reduce(kifmm_plan *pl, int64_t n_clumps, const int64_t 
 kifmm_status kifmm_backward(kifmm_plan *pl, const void *dL_dpot, const void *dL_dgrad, const double *dL_denergy,
                             const void *grad, void *dq, void *dx, kifmm_stream_t stream) {
     if (!pl || (!dL_dpot && !dL_dgrad && !dL_denergy)) return KIFMM_ERR_ARG;
-    if (pl->P.periodic) return KIFMM_ERR_ARG;  // the adjoint of the periodic terms is not built
+    if (pl->P.periodic || pl->P.stokes) return KIFMM_ERR_ARG;  // not built for these plans
     if (dx && (dL_dpot || dL_denergy) && !grad) return KIFMM_ERR_ARG;
     Plan &P = pl->P;
     if (!P.has_sources) return KIFMM_ERR_STATE;

@@ -1353,6 +1353,270 @@ __global__ void k_finalize_adj(int64_t n, const double4 *__restrict__ res, const
     }
 }
 
+// ---------------------------------------------------------------------------
+// The Stokeslet (the tensor kernel Eq. 1 admits; Stokes flow, Sec. 2.4):
+// G(r) = I / |r| + r r^T / |r|^3, the 1 / (8 pi) and coef applied at the
+// output.  Sources carry forces, surfaces 3-vector densities (expansion
+// vectors of 3 n_s values, point-major), targets receive velocities.  The
+// same homogeneity as 1/r (degree -1), so the box-unit scalings carry over.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void stokes_acc(T rx, T ry, T rz, T fx, T fy, T fz, T &ux, T &uy, T &uz) {
+    const T ri = rsqrt_t<T>(rx * rx + ry * ry + rz * rz);
+    const T rf = (rx * fx + ry * fy + rz * fz) * (ri * ri * ri);
+    ux += fx * ri + rx * rf;
+    uy += fy * ri + ry * rf;
+    uz += fz * ri + rz * rf;
+}
+
+// P2M: u(b)_{3j+a} = sum_i G_a.(UC_j - x_i) f_i, box units then 1/h; one
+// block per leaf, a thread per check point, forces staged through shared memory.
+template <typename T>
+__global__ void k_p2m_stokes(const int32_t *__restrict__ leaves, const int32_t *__restrict__ lvl,
+                             const int32_t *__restrict__ first, const int32_t *__restrict__ cnt,
+                             const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ frc,
+                             const T *__restrict__ surf, int npt, T *__restrict__ u) {
+    __shared__ T sx[kLeafThreads], sy[kLeafThreads], sz[kLeafThreads], sfx[kLeafThreads], sfy[kLeafThreads],
+        sfz[kLeafThreads];
+    const int b = leaves[blockIdx.x];
+    const T h = box_half<T>(lvl[b]), hinv = T(1) / h;
+    const int n = cnt[b], f = first[b];
+    const T a = (T)kAlphaOuter;
+    for (int j0 = 0; j0 < npt; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        T px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0;
+        if (j < npt) px = a * surf[3 * j], py = a * surf[3 * j + 1], pz = a * surf[3 * j + 2];
+        for (int c0 = 0; c0 < n; c0 += kLeafThreads) {
+            __syncthreads();
+            for (int k = threadIdx.x; k < kLeafThreads && c0 + k < n; k += blockDim.x) {
+                const auto v = pts[f + c0 + k];
+                sx[k] = v.x * hinv, sy[k] = v.y * hinv, sz[k] = v.z * hinv;
+                const size_t o = 3 * (size_t)(f + c0 + k);
+                sfx[k] = frc[o], sfy[k] = frc[o + 1], sfz[k] = frc[o + 2];
+            }
+            __syncthreads();
+            const int m = min(kLeafThreads, n - c0);
+            for (int i = 0; i < m; ++i) stokes_acc<T>(px - sx[i], py - sy[i], pz - sz[i], sfx[i], sfy[i], sfz[i], ux, uy, uz);
+        }
+        if (j < npt) {
+            T *o = u + (size_t)b * 3 * npt + 3 * j;
+            o[0] = ux * hinv, o[1] = uy * hinv, o[2] = uz * hinv;
+        }
+    }
+}
+
+// P2L: d(b) += the forces of the leaves of X(b) on b's downward check surface.
+template <typename T>
+__global__ void k_p2l_stokes(const int32_t *__restrict__ nx, const int32_t *__restrict__ xdense,
+                             const int32_t *__restrict__ lvl, const int32_t *__restrict__ cx,
+                             const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
+                             const int32_t *__restrict__ first, const int32_t *__restrict__ cnt,
+                             const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ frc,
+                             const T *__restrict__ surf, int npt, T *__restrict__ d) {
+    __shared__ T sx[kLeafThreads], sy[kLeafThreads], sz[kLeafThreads], sfx[kLeafThreads], sfy[kLeafThreads],
+        sfz[kLeafThreads];
+    const int b = blockIdx.x;
+    if (nx[b] == 0) return;
+    const int lb = lvl[b];
+    const T hb = box_half<T>(lb), hinv = T(1) / hb;
+    const T al = (T)kAlphaInner;
+    for (int j0 = 0; j0 < npt; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        T px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0;
+        if (j < npt) px = al * surf[3 * j], py = al * surf[3 * j + 1], pz = al * surf[3 * j + 2];
+        for (int e = 0; e < nx[b]; ++e) {
+            const int a = xdense[(size_t)b * kMaxCoarse + e], la = lvl[a];
+            const T ox = centre_diff<T>(cx[a], la, cx[b], lb), oy = centre_diff<T>(cy[a], la, cy[b], lb),
+                    oz = centre_diff<T>(cz[a], la, cz[b], lb);
+            const int n = cnt[a], f = first[a];
+            for (int c0 = 0; c0 < n; c0 += kLeafThreads) {
+                __syncthreads();
+                for (int k = threadIdx.x; k < kLeafThreads && c0 + k < n; k += blockDim.x) {
+                    const auto v = pts[f + c0 + k];
+                    sx[k] = (ox + v.x) * hinv, sy[k] = (oy + v.y) * hinv, sz[k] = (oz + v.z) * hinv;
+                    const size_t o = 3 * (size_t)(f + c0 + k);
+                    sfx[k] = frc[o], sfy[k] = frc[o + 1], sfz[k] = frc[o + 2];
+                }
+                __syncthreads();
+                const int m = min(kLeafThreads, n - c0);
+                for (int i = 0; i < m; ++i)
+                    stokes_acc<T>(px - sx[i], py - sy[i], pz - sz[i], sfx[i], sfy[i], sfz[i], ux, uy, uz);
+            }
+        }
+        if (j < npt) {
+            T *o = d + (size_t)b * 3 * npt + 3 * j;
+            o[0] += ux * hinv, o[1] += uy * hinv, o[2] += uz * hinv;
+        }
+    }
+}
+
+// Leaves: L2P (own downward density on the 2.95 h_b surface), M2P (the W
+// boxes' upward densities on their 1.05 h_a surfaces) and P2P (the U-list
+// particles' forces, r = 0 skipped); root units, FP64 sums; one block per
+// leaf, a thread per target.
+template <typename T>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf_stokes(LeafCtx C, const int32_t *__restrict__ leaves,
+                                                              const typename Vec4<T>::type *__restrict__ pts,
+                                                              const T *__restrict__ frc, const T *__restrict__ surf,
+                                                              int npt, const T *__restrict__ dn_dens,
+                                                              const T *__restrict__ up_dens, double4 *__restrict__ res) {
+    __shared__ T sx[kLeafThreads], sy[kLeafThreads], sz[kLeafThreads], sfx[kLeafThreads], sfy[kLeafThreads],
+        sfz[kLeafThreads];
+    const int b = leaves[blockIdx.x];
+    const int lb = C.lvl[b], n = C.cnt[b], f = C.first[b];
+    const T hb = box_half<T>(lb);
+    const uint32_t w0 = C.w_ptr[b], u0 = C.u_ptr[b];
+    const int nw = (int)(C.w_ptr[b + 1] - w0), nu = (int)(C.u_ptr[b + 1] - u0);
+    for (int t0 = 0; t0 < n; t0 += kLeafThreads) {
+        const int i = t0 + threadIdx.x;
+        const bool valid = i < n;
+        T x = 0, y = 0, z = 0;
+        if (valid) {
+            const auto v = pts[f + i];
+            x = v.x, y = v.y, z = v.z;
+        }
+        double vx = 0, vy = 0, vz = 0;
+        auto add = [&](T rx, T ry, T rz, T fx, T fy, T fz) {
+            T ux = 0, uy = 0, uz = 0;
+            stokes_acc<T>(rx, ry, rz, fx, fy, fz, ux, uy, uz);
+            vx += (double)ux, vy += (double)uy, vz += (double)uz;
+        };
+        if (valid) {
+            const T a = (T)kAlphaOuter * hb;
+            for (int k = 0; k < npt; ++k) {
+                const T *w = dn_dens + (size_t)b * 3 * npt + 3 * k;
+                add(x - a * surf[3 * k], y - a * surf[3 * k + 1], z - a * surf[3 * k + 2], w[0] * hb, w[1] * hb,
+                    w[2] * hb);
+            }
+            for (int e = 0; e < nw; ++e) {
+                const int a_ = C.w_idx[w0 + e], la = C.lvl[a_];
+                const T ha = box_half<T>(la), al = (T)kAlphaInner * ha;
+                const T ox = centre_diff<T>(C.cx[a_], la, C.cx[b], lb), oy = centre_diff<T>(C.cy[a_], la, C.cy[b], lb),
+                        oz = centre_diff<T>(C.cz[a_], la, C.cz[b], lb);
+                for (int k = 0; k < npt; ++k) {
+                    const T *w = up_dens + (size_t)a_ * 3 * npt + 3 * k;
+                    add(x - (ox + al * surf[3 * k]), y - (oy + al * surf[3 * k + 1]), z - (oz + al * surf[3 * k + 2]),
+                        w[0] * ha, w[1] * ha, w[2] * ha);
+                }
+            }
+        }
+        for (int e = 0; e < nu; ++e) {
+            const int a_ = C.u_idx[u0 + e], la = C.lvl[a_];
+            const T ox = centre_diff<T>(C.cx[a_], la, C.cx[b], lb), oy = centre_diff<T>(C.cy[a_], la, C.cy[b], lb),
+                    oz = centre_diff<T>(C.cz[a_], la, C.cz[b], lb);
+            const int na = C.cnt[a_], fa = C.first[a_];
+            for (int c0 = 0; c0 < na; c0 += kLeafThreads) {
+                __syncthreads();
+                if (c0 + threadIdx.x < na) {
+                    const int j = fa + c0 + threadIdx.x;
+                    const auto v = pts[j];
+                    sx[threadIdx.x] = ox + v.x, sy[threadIdx.x] = oy + v.y, sz[threadIdx.x] = oz + v.z;
+                    sfx[threadIdx.x] = frc[3 * (size_t)j], sfy[threadIdx.x] = frc[3 * (size_t)j + 1],
+                    sfz[threadIdx.x] = frc[3 * (size_t)j + 2];
+                }
+                __syncthreads();
+                const int m = min(kLeafThreads, na - c0);
+                if (valid)
+                    for (int k = 0; k < m; ++k) {
+                        const T rx = x - sx[k], ry = y - sy[k], rz = z - sz[k];
+                        if (!(rx * rx + ry * ry + rz * rz > T(0))) continue;  // the particle itself, coincident points
+                        add(rx, ry, rz, sfx[k], sfy[k], sfz[k]);
+                    }
+            }
+        }
+        if (valid) {
+            res[f + i] = make_double4(vx, vy, vz, 0.0);
+            if (!isfinite(vx + vy + vz)) set_status(C.status, KIFMM_ERR_NONFINITE);
+        }
+    }
+}
+
+// Velocities in the caller's order: coef / (8 pi side) times the root-unit sums.
+template <typename TO>
+__global__ void k_finalize_stokes(int64_t n, const double4 *__restrict__ res, const uint32_t *__restrict__ perm,
+                                  const int64_t *__restrict__ off, int S, const double *__restrict__ out_scale,
+                                  TO *__restrict__ vel) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= (int64_t)j) lo = mid; else hi = mid - 1;
+    }
+    const double c = 0.5 * out_scale[2 * lo];  // coef / (4 pi side) / 2
+    const double4 r = res[i];
+    vel[3 * (size_t)j] = (TO)(c * r.x);
+    vel[3 * (size_t)j + 1] = (TO)(c * r.y);
+    vel[3 * (size_t)j + 2] = (TO)(c * r.z);
+}
+
+template <typename T>
+cudaError_t evaluate_stokes_t(Plan &P, void *vel, cudaStream_t s) {
+    using V4 = typename Vec4<T>::type;
+    const int ns = P.ns, npt = P.nsurf;
+    const T *surf = P.f64 ? (const T *)P.surf64 : (const T *)P.surf32;
+    T *u = (T *)P.u_chk, *d = (T *)P.d_chk, *tmp = (T *)P.tmp_chk;
+    const V4 *pts = (const V4 *)P.pts;
+    const T *frc = (const T *)P.frc;
+    double4 *res = (double4 *)P.res;
+    const unsigned thr = (unsigned)std::min(kLeafThreads, (npt + 31) / 32 * 32);
+    stage_begin(P, KIFMM_STAGE_P2M, s);
+    ++g_launches, k_p2m_stokes<T><<<(unsigned)P.n_leaves, thr, 0, s>>>(P.leaves, P.lvl, P.first, P.cnt, pts, frc,
+                                                                       surf, npt, u);
+    stage_end(P, KIFMM_STAGE_P2M, s);
+    stage_begin(P, KIFMM_STAGE_M2M, s);
+    for (int l = P.max_level - 1; l >= 0; --l)
+        ggemm<T>(P, GatherChild<T>{P.child8, (const T *)P.m2m_t, ns}, P.part_list[1],
+                 P.part_start[1][1 + l], P.part_start[1][2 + l], 8, u, u, 0, s);
+    stage_end(P, KIFMM_STAGE_M2M, s);
+    stage_begin(P, KIFMM_STAGE_M2L, s);
+    KIFMM_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(T) * (size_t)P.nb * ns, s));
+    ggemm_classes<T>(P, GatherM2L<T>{P.vdense, P.slot_off, (const T *)P.m2l_t, ns, P.op_ld}, P.part_list[0],
+                     P.part_start[0].data(), 8, kVSlots, u, d, 0, s, P.op_ld, nullptr);
+    stage_end(P, KIFMM_STAGE_M2L, s);
+    if (P.n_x > 0) {
+        stage_begin(P, KIFMM_STAGE_P2L, s);
+        ++g_launches, k_p2l_stokes<T><<<(unsigned)P.nb, thr, 0, s>>>(P.nx, P.xdense, P.lvl, P.cx, P.cy, P.cz,
+                                                                       P.first, P.cnt, pts, frc, surf, npt, d);
+        stage_end(P, KIFMM_STAGE_P2L, s);
+    }
+    stage_begin(P, KIFMM_STAGE_L2L, s);
+    for (int l = 1; l <= P.max_level; ++l)
+        ggemm_classes<T>(P, GatherParent<T>{P.parent, (const T *)P.l2l_t, ns, P.op_ld}, P.part_list[3],
+                         P.part_start[3].data() + 8 * l, 8, 1, d, d, 1, s, P.op_ld, nullptr);
+    stage_end(P, KIFMM_STAGE_L2L, s);
+    KIFMM_CUDA_TRY(cudaGetLastError());
+    stage_begin(P, KIFMM_STAGE_LEAF, s);
+    if (P.n_w > 0) {
+        ggemm<T>(P, GatherSelf<T>{(const T *)P.up_w_t}, P.part_list[2], 0, P.part_start[2][1], 1, u, tmp, 0, s);
+        ggemm<T>(P, GatherSelf<T>{(const T *)P.up_v_t}, P.part_list[2], 0, P.part_start[2][1], 1, tmp,
+                 (T *)P.up_dens, 0, s);
+    }
+    ggemm<T>(P, GatherSelf<T>{(const T *)P.dn_w_t}, P.leaves, 0, P.n_leaves, 1, d, tmp, 0, s);
+    ggemm<T>(P, GatherSelf<T>{(const T *)P.dn_v_t}, P.leaves, 0, P.n_leaves, 1, tmp, (T *)P.dn_dens, 0, s);
+    stage_end(P, KIFMM_STAGE_LEAF, s);
+    stage_begin(P, KIFMM_STAGE_P2P, s);
+    LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns, nullptr,
+              P.leaf_tile, P.status, nullptr, nullptr};
+    ++g_launches, k_leaf_stokes<T><<<(unsigned)P.n_leaves, kLeafThreads, 0, s>>>(
+                      C, P.leaves, pts, frc, surf, npt, (const T *)P.dn_dens, (const T *)P.up_dens, res);
+    stage_end(P, KIFMM_STAGE_P2P, s);
+    stage_begin(P, KIFMM_STAGE_OUT, s);
+    if (vel) {
+        if (P.io_f64)
+            ++g_launches, k_finalize_stokes<double><<<grid_for(P.n, 256), 256, 0, s>>>(
+                              P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, (double *)vel);
+        else
+            ++g_launches, k_finalize_stokes<float><<<grid_for(P.n, 256), 256, 0, s>>>(
+                              P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, (float *)vel);
+    }
+    stage_end(P, KIFMM_STAGE_OUT, s);
+    P.fwd_valid = P.fwd_res_valid = true;
+    return cudaGetLastError();
+}
+
+
 // Weights of a loss on the gradient, in sorted order and root units: the
 // caller's dL/dgrad divided by the side of the particle's system (the
 // gradient in caller units is the root-unit gradient over the side).
@@ -1567,6 +1831,7 @@ cudaError_t run_backward(Plan &P, const void *w, const void *g, const double *dL
 }
 
 cudaError_t run_evaluate(Plan &P, void *pot, void *grad, double *energy, cudaStream_t s) {
+    if (P.stokes) return P.f64 ? evaluate_stokes_t<double>(P, pot, s) : evaluate_stokes_t<float>(P, pot, s);
     return P.f64 ? evaluate_t<double>(P, pot, grad, energy, s) : evaluate_t<float>(P, pot, grad, energy, s);
 }
 

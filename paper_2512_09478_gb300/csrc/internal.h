@@ -50,7 +50,10 @@ struct DevBuf {
 struct Plan {
     kifmm_plan_desc desc{};
     int device = 0;
-    int p = 0, ns = 0;        // surface order, surface points
+    int p = 0, ns = 0;        // surface order, expansion length (surface points x components)
+    int nsurf = 0;            // surface points, 6 (p - 1)^2 + 2
+    bool stokes = false;      // Stokeslet kernel: 3-vector sources, densities and outputs
+    void *frc = nullptr;      // Stokeslet: [N][3] forces in sorted order, compute type
     bool f64 = false;         // compute type is double (FP64 mode)
     int io_f64 = 0;           // caller dtype is double
     double coef = 1.0;

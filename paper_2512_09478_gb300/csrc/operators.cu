@@ -223,6 +223,27 @@ void kernel_block(const std::vector<double> &S, int n, const double ct[3], doubl
         }
 }
 
+// The Stokeslet block of the same surfaces (the tensor kernel of Eq. 1, Sec.
+// 2.4's Stokes flow): [3 n][3 n], row 3 i + a, column 3 k + b holds
+// G_ab(r) = delta_ab / |r| + r_a r_b / |r|^3 (the 1 / (8 pi mu) is applied
+// with coef), r = target_i - source_k; zero at r = 0.
+void stokes_block(const std::vector<double> &S, int n, const double ct[3], double at, const double cs[3], double as,
+                  double *K) {
+    const size_t ld = 3 * (size_t)n;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            double r[3], r2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                r[d] = (ct[d] + at * S[3 * i + d]) - (cs[d] + as * S[3 * k + d]);
+                r2 += r[d] * r[d];
+            }
+            const double ri = (r2 > 0.0) ? 1.0 / std::sqrt(r2) : 0.0, ri3 = ri * ri * ri;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    K[(3 * (size_t)i + a) * ld + 3 * k + b] = (a == b ? ri : 0.0) + r[a] * r[b] * ri3;
+        }
+}
+
 void child_center(int o, double c[3]) {
     c[0] = ((o >> 2) & 1) ? 0.5 : -0.5;
     c[1] = ((o >> 1) & 1) ? 0.5 : -0.5;
@@ -375,11 +396,18 @@ static cudaError_t build_m2l_compressed(Plan &P, const double *dK, const double 
 }
 
 cudaError_t build_operators(Plan &P, std::string &err) {
-    const int p = P.p, n = P.ns;
+    // n: length of a box's expansion vector (n_s for the Laplace kernel, 3 n_s
+    // for the Stokeslet's 3-vector densities); ns_pts: surface points
+    const int p = P.p, n = P.ns, ns_pts = P.nsurf;
     const std::vector<double> S = unit_surface(p);
     const double zero[3] = {0, 0, 0};
     const size_t nn = (size_t)n * n;
     const double ai = kAlphaInner, ao = kAlphaOuter;
+    auto kernel_block = [&](const std::vector<double> &S_, int, const double ct[3], double at, const double cs[3],
+                            double as, double *K) {
+        if (P.stokes) stokes_block(S_, ns_pts, ct, at, cs, as, K);
+        else kifmm::kernel_block(S_, ns_pts, ct, at, cs, as, K);
+    };
 
     // check-from-equivalent matrices, transposed for the column-wise Jacobi
     std::vector<double> Kchk(2 * nn), tmp(nn);
@@ -491,6 +519,7 @@ cudaError_t build_operators(Plan &P, std::string &err) {
         else
             k_to_f32<<<(unsigned)((c.cnt + 255) / 256), 256>>>(c.src, (float *)c.dst, c.cnt);
     }
+    if (!P.stokes) {
     // Adjoint operators (the transposed passes use the same gathered GEMM, which
     // reads operators as [k][j]; for Op^T that is Op itself, row-major):
     //   M2M^T, L2L^T: blocks of m2m_t / l2l_t transposed back;
@@ -525,8 +554,9 @@ cudaError_t build_operators(Plan &P, std::string &err) {
     }
     KIFMM_CUDA_TRY(cudaDeviceSynchronize());
     cudaFree(dT);
+    }  // adjoint operators (Laplace)
     P.op_ld = n;
-    if (!P.f64) {
+    if (!P.f64 && !P.stokes) {
         // FP32-based modes carry the downward check potential as a per-box
         // mean (FP64 scalar) plus a mean-free FP32 vector: the L2L and M2L
         // blocks are stored mean-free, [k][n + 1] with the mean row in
@@ -599,11 +629,11 @@ cudaError_t build_operators(Plan &P, std::string &err) {
         cudaFree(dF);
     }
     // surfaces
-    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf64, sizeof(double) * 3 * n));
-    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf32, sizeof(float) * 3 * n));
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf64, sizeof(double) * 3 * ns_pts));
+    KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.surf32, sizeof(float) * 3 * ns_pts));
     std::vector<float> S32(S.begin(), S.end());
-    KIFMM_CUDA_TRY(cudaMemcpy(P.surf64, S.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
-    KIFMM_CUDA_TRY(cudaMemcpy(P.surf32, S32.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice));
+    KIFMM_CUDA_TRY(cudaMemcpy(P.surf64, S.data(), sizeof(double) * 3 * ns_pts, cudaMemcpyHostToDevice));
+    KIFMM_CUDA_TRY(cudaMemcpy(P.surf32, S32.data(), sizeof(float) * 3 * ns_pts, cudaMemcpyHostToDevice));
     // V slot -> offset index tables
     std::vector<int> slot(8 * kVSlots, -1);
     for (int cls = 0; cls < 8; ++cls) {

@@ -59,7 +59,7 @@ __global__ void k_bbox(int64_t n, const T *__restrict__ xyz, const T *__restrict
     for (int64_t i = base + threadIdx.x; i < end; i += kBlock) {
         double v[3];
         for (int d = 0; d < 3; ++d) v[d] = (double)xyz[3 * i + d];
-        if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || !isfinite((double)q[i])) {
+        if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || (q && !isfinite((double)q[i]))) {
             bad = true;
             continue;
         }
@@ -515,12 +515,12 @@ __global__ void k_gather(int64_t n_leaves, const int32_t *__restrict__ leaves, c
         v.x = (TC)r[0];
         v.y = (TC)r[1];
         v.z = (TC)r[2];
-        v.w = (TC)q[j];
+        v.w = q ? (TC)q[j] : TC(0);
         pts[i] = v;
         if (leaf_q2) {
             const double ex = (cx[b] + 0.5) * w + r[0] - 0.5, ey = (cy[b] + 0.5) * w + r[1] - 0.5,
                          ez = (cz[b] + 0.5) * w + r[2] - 0.5;
-            q2 += (double)q[j] * (ex * ex + ey * ey + ez * ez);
+            q2 += (double)v.w * (ex * ex + ey * ey + ez * ez);
         }
     }
     if (leaf_q2) {
@@ -1069,10 +1069,12 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
     ++g_launches, k_bbox_init<double><<<grid_for(S * 6, 128), 128, 0, s>>>(P.bbox_ord, S);
     const unsigned nt = grid_for(n, kTile);
     if (P.io_f64)
-        ++g_launches, k_bbox<double><<<nt, kBlock, 0, s>>>(n, (const double *)xyz, (const double *)q, P.sys_off_d, S,
+        ++g_launches, k_bbox<double><<<nt, kBlock, 0, s>>>(n, (const double *)xyz,
+                                             P.stokes ? nullptr : (const double *)q, P.sys_off_d, S,
                                              P.bbox_ord, P.status);
     else
-        ++g_launches, k_bbox<float><<<nt, kBlock, 0, s>>>(n, (const float *)xyz, (const float *)q, P.sys_off_d, S,
+        ++g_launches, k_bbox<float><<<nt, kBlock, 0, s>>>(n, (const float *)xyz,
+                                            P.stokes ? nullptr : (const float *)q, P.sys_off_d, S,
                                             P.bbox_ord, P.status);
     if (P.periodic) {
         // the root is the cell; the cell must be neutral
@@ -1264,9 +1266,42 @@ cudaError_t check_leaves(Plan &P, const void *xyz, double skin, int *moved_dev, 
     return cudaGetLastError();
 }
 
+// Stokeslet: the forces in sorted order, compute type; non-finite ones flagged.
+template <typename TI, typename TC>
+__global__ void k_gather_frc(int64_t n, const uint32_t *__restrict__ perm, const TI *__restrict__ f,
+                             TC *__restrict__ frc, int *status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    bool bad = false;
+    for (int d = 0; d < 3; ++d) {
+        const double v = (double)f[3 * (size_t)j + d];
+        bad = bad || !isfinite(v);
+        frc[3 * i + d] = (TC)v;
+    }
+    if (bad) set_status(status, KIFMM_ERR_NONFINITE);
+}
+
 // Leaf-relative particle records in the compute type (also used to refresh
 // positions and charges with the tree frozen).
-cudaError_t gather_particles(Plan &P, const void *xyz, const void *q, cudaStream_t s) {
+cudaError_t gather_particles(Plan &P, const void *xyz, const void *q_in, cudaStream_t s) {
+    // Stokeslet plans: q_in holds forces [N][3], gathered on their own; the
+    // records' weight is unused
+    const void *q = P.stokes ? nullptr : q_in;
+    if (P.stokes) {
+        if (P.f64 && P.io_f64)
+            ++g_launches, k_gather_frc<double, double><<<grid_for(P.n, 256), 256, 0, s>>>(
+                              P.n, P.perm, (const double *)q_in, (double *)P.frc, P.status);
+        else if (P.f64)
+            ++g_launches, k_gather_frc<float, double><<<grid_for(P.n, 256), 256, 0, s>>>(
+                              P.n, P.perm, (const float *)q_in, (double *)P.frc, P.status);
+        else if (P.io_f64)
+            ++g_launches, k_gather_frc<double, float><<<grid_for(P.n, 256), 256, 0, s>>>(
+                              P.n, P.perm, (const double *)q_in, (float *)P.frc, P.status);
+        else
+            ++g_launches, k_gather_frc<float, float><<<grid_for(P.n, 256), 256, 0, s>>>(
+                              P.n, P.perm, (const float *)q_in, (float *)P.frc, P.status);
+    }
     P.fwd_valid = P.fwd_res_valid = false;  // new sources: the last evaluate's field no longer applies
     if (P.f64) {
         if (P.io_f64)

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libkifmm.so")
 
 OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
 PRECISIONS = {"fp64": 0, "fp32": 1, "mixed_fp16": 3}
+KERNELS = {"laplace": 0, "stokeslet": 1}
 LIST_KINDS = {"U": 0, "V": 1, "W": 2, "X": 3}
 
 
@@ -32,7 +33,7 @@ class PlanDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("coef", ctypes.c_double), ("n_max", ctypes.c_int64),
                 ("n_systems_max", ctypes.c_int), ("dtype", ctypes.c_int), ("pinv_eps", ctypes.c_double),
                 ("autotune", ctypes.c_int), ("direct_max", ctypes.c_int), ("m2l_eps", ctypes.c_double),
-                ("cell", ctypes.c_double)]
+                ("cell", ctypes.c_double), ("kernel", ctypes.c_int)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -128,7 +129,7 @@ class Plan:
     def __init__(self, p: int = 6, leaf_cap: int = 128, max_depth: int = 20, precision: str = "fp32",
                  coef: float = 1.0, n_max: int = 1 << 20, n_systems_max: int = 1,
                  dtype: torch.dtype = torch.float32, pinv_eps: float = 0.0, autotune: bool = False,
-                 direct_max: int = 0, m2l_eps: float = 0.0, cell: float = 0.0):
+                 direct_max: int = 0, m2l_eps: float = 0.0, cell: float = 0.0, kernel: str = "laplace"):
         lib = load()
         self.dtype = dtype
         self.precision = precision
@@ -136,11 +137,12 @@ class Plan:
         d = PlanDesc(p=p, leaf_cap=leaf_cap, max_depth=max_depth, precision=PRECISIONS[precision], coef=coef,
                      n_max=n_max, n_systems_max=n_systems_max,
                      dtype=1 if dtype == torch.float64 else 0, pinv_eps=pinv_eps, autotune=int(autotune), direct_max=direct_max,
-                     m2l_eps=m2l_eps, cell=cell)
+                     m2l_eps=m2l_eps, cell=cell, kernel=KERNELS[kernel])
         h = ctypes.c_void_p()
         _check(lib.kifmm_plan_create(ctypes.byref(d), ctypes.byref(h)), "kifmm_plan_create")
         self._h = h
-        self._ns = 6 * (p - 1) ** 2 + 2
+        self.kernel = kernel
+        self._ns = (6 * (p - 1) ** 2 + 2) * (3 if kernel == "stokeslet" else 1)  # expansion length
         self.n = 0
         self.n_systems = 0
         self._offsets = None
@@ -196,7 +198,16 @@ class Plan:
 
     def evaluate(self, pot=None, grad=None, energy=None, want_pot=True, want_grad=True, want_energy=False,
                  stream=None):
+        """(pot [N], grad [N, 3], energy [n_systems] float64), None where not
+        wanted.  A Stokeslet plan returns (velocity [N, 3], None, None)."""
         dev = torch.device("cuda", torch.cuda.current_device())
+        if self.kernel == "stokeslet":
+            if pot is None:
+                pot = torch.empty(self.n, 3, dtype=self.dtype, device=dev)
+            # grad / energy, if given, are refused by the library
+            _check(load().kifmm_evaluate(self._h, _ptr(pot), _ptr(grad), _ptr(energy), _stream(stream)),
+                   "kifmm_evaluate")
+            return pot, None, None
         if pot is None and want_pot:
             pot = torch.empty(self.n, dtype=self.dtype, device=dev)
         if grad is None and want_grad:
