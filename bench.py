@@ -384,11 +384,21 @@ def run_ours(args, rank, world, local_rank):
         force = torch.empty(len(meta["centres"]), 3, dtype=torch.float32, device=dev)
         torque = torch.empty_like(force)
 
-    def eager_step():
-        plan.set_sources(xt, qt, offsets)
+    # Every timed step runs the whole path (tree, lists, evaluation) on new
+    # positions: the steps alternate the packing and its mirror image
+    # (x -> lo + hi - x, the same workload).  The plan builds its lists on
+    # every set_sources; keeping them when the boxes are unchanged
+    # (reuse_lists) is timed on its own below.
+    lo, hi = xt.min(0).values, xt.max(0).values
+    xs_alt = (xt, (lo + hi) - xt)
+    cref_alt = (cref, (lo + hi) - cref) if clumps else (None, None)
+
+    def eager_step(k=0):
+        xk = xs_alt[k & 1]
+        plan.set_sources(xk, qt, offsets)
         plan.evaluate(pot, grad)
         if clumps:
-            plan.clump_reduce(coff, xt, qt, grad, cref, force, torque)
+            plan.clump_reduce(coff, xk, qt, grad, cref_alt[k & 1], force, torque)
 
     graph = None
     if w["kind"] == "batched":
@@ -408,13 +418,13 @@ def run_ours(args, rank, world, local_rank):
             plan.evaluate(pot, grad)
         launches_per_replay = plan.profile_read()["launches"]
 
-        def step():
+        def step(k=0):
             graph.replay()
     else:
         step = eager_step
 
-    for _ in range(max(args.warmup, 3)):
-        step()
+    for k in range(max(args.warmup, 3)):
+        step(k)
     torch.cuda.synchronize()
     work = algorithmic_work(plan, w, n)
     if graph is None:
@@ -431,7 +441,7 @@ def run_ours(args, rank, world, local_rank):
     for k in range(args.steps):
         flush.fill_(k & 0xFF)  # evict the previous step's working set from L2 (not timed)
         evs[k][0].record(stream)
-        step()
+        step(k)
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     if args.profile_region:
@@ -445,6 +455,13 @@ def run_ours(args, rank, world, local_rank):
         plan.profile(False)
         launches = int(prof["launches"])
         prof_note = "stage events recorded in the timed steps"
+        # untimed: both halves of the alternation built their lists, and the
+        # outputs (checked for accuracy below) are the packing's own
+        rebuilt = []
+        for k in (1, 0):
+            eager_step(k)
+            rebuilt.append(plan.tree_info()["lists_reused"] == 0)
+        torch.cuda.synchronize()
     else:
         launches = int(launches_per_replay) * args.steps
         # stage split from an uncaptured pass of the same evaluate (events cannot be read per replay)
@@ -468,25 +485,25 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the public API: pinned host inputs -> device -> step -> host outputs
     e2e = None
     if not args.no_e2e:
-        hx = torch.tensor(x, dtype=torch.float32).pin_memory()
+        hxs = (xt.cpu().pin_memory(), xs_alt[1].cpu().pin_memory())   # the packing and its mirror image
         hq = torch.tensor(q, dtype=torch.float32).pin_memory()
         hpot = torch.empty(n, dtype=torch.float32).pin_memory()
         hgrad = torch.empty(n, 3, dtype=torch.float32).pin_memory()
         dx = torch.empty_like(xt)
         dq = torch.empty_like(qt)
 
-        def e2e_step():
-            dx.copy_(hx, non_blocking=True)
+        def e2e_step(k):
+            dx.copy_(hxs[k & 1], non_blocking=True)
             dq.copy_(hq, non_blocking=True)
             plan.set_sources(dx, dq, offsets)
             plan.evaluate(pot, grad)
             if clumps:
-                plan.clump_reduce(coff, dx, dq, grad, cref, force, torque)
+                plan.clump_reduce(coff, dx, dq, grad, cref_alt[k & 1], force, torque)
             hpot.copy_(pot, non_blocking=True)
             hgrad.copy_(grad, non_blocking=True)
 
-        for _ in range(2):
-            e2e_step()
+        for k in range(2):
+            e2e_step(k)
         torch.cuda.synchronize()
         ke = max(3, min(args.steps, 10))
         e_ms = 0.0
@@ -494,7 +511,7 @@ def run_ours(args, rank, world, local_rank):
             flush.fill_(k & 0xFF)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            e2e_step()
+            e2e_step(k)
             b.record(stream)
             torch.cuda.synchronize()
             e_ms += a.elapsed_time(b)
@@ -503,7 +520,7 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e_ms = t.item()
         e2e = {"value": units / (e_ms / ke * 1e-3) / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": int(hx.numel() * 4 + hq.numel() * 4),
+               "h2d_bytes_per_step": int(hxs[0].numel() * 4 + hq.numel() * 4),
                "d2h_bytes_per_step": int(hpot.numel() * 4 + hgrad.numel() * 4),
                "step": "set_sources + evaluate" + (" + clump_reduce" if clumps else "")}
 
@@ -511,6 +528,8 @@ def run_ours(args, rank, world, local_rank):
     # the long-range stride / reuse case; same L2 flush and events
     reuse = None
     if graph is None:
+        eager_step(0)   # untimed: the tree of the packing itself (e2e may end on its mirror image)
+
         def reuse_step():
             plan.update_sources(xt, qt)
             plan.evaluate(pot, grad)
@@ -579,6 +598,48 @@ def run_ours(args, rank, world, local_rank):
                             "steps": kr, "tree_kept": kept_timed,
                             "step": "refresh_sources (skin 0.05, jitter 1e-6 of the domain) + evaluate"}
 
+        # fourth number: set_sources on the same jittered alternation with a
+        # reuse_lists plan; the tree is rebuilt every step and its lists are
+        # kept when the boxes came out the same (own outputs: the accuracy
+        # check below reads the benchmarked plan's)
+        lplan = Plan(p=w["p"], leaf_cap=w["leaf_cap"], max_depth=w["max_depth"], precision=args.precision,
+                     coef=coef, n_max=n, n_systems_max=n_sys, dtype=torch.float32, autotune=not args.no_autotune,
+                     reuse_lists=True)
+        pot_l, grad_l = torch.empty_like(pot), torch.empty_like(grad)
+        if clumps:
+            force_l, torque_l = torch.empty_like(force), torch.empty_like(torque)
+
+        def lists_step(k):
+            xk = xj if k & 1 else xt
+            lplan.set_sources(xk, qt, offsets)
+            lplan.evaluate(pot_l, grad_l)
+            if clumps:
+                lplan.clump_reduce(coff, xk, qt, grad_l, cref, force_l, torque_l)
+
+        for k in range(3):
+            lists_step(k)
+        torch.cuda.synchronize()
+        l_ms, kept_l = 0.0, 0
+        for k in range(kr):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lists_step(k)
+            b.record(stream)
+            kept_l += lplan.tree_info()["lists_reused"]
+            torch.cuda.synchronize()
+            l_ms += a.elapsed_time(b)
+        if dist:
+            t = torch.tensor([l_ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            l_ms = t.item()
+        torch.cuda.synchronize()
+        lplan.close()
+        reuse["lists_kept"] = {"value": units / (l_ms / kr * 1e-3) / 1e6, "unit": UNIT,
+                               "ms_per_step": l_ms / kr, "steps": kr, "lists_kept": kept_l,
+                               "step": "set_sources (reuse_lists plan; jitter 1e-6 of the domain, alternating) "
+                                       "+ evaluate"}
+
     if rank != 0:
         return
     calls = prof["calls"]
@@ -600,6 +661,9 @@ def run_ours(args, rank, world, local_rank):
            "max_level": work["info"]["max_level"],
            "step": ("graph replay of update_sources + evaluate (tree frozen)" if graph is not None else
                     "set_sources + evaluate" + (" + clump_reduce" if clumps else ""))}
+    if graph is None:
+        cfg["positions"] = "steps alternate the packing and its mirror image (x -> lo + hi - x)"
+        cfg["lists_rebuilt_every_step"] = all(rebuilt)
     if "solid_fraction" in meta:
         cfg["rsa_solid_fraction"] = round(meta["solid_fraction"], 4)
     tun = plan.tuning()
@@ -686,14 +750,19 @@ def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, c
         force = torch.empty(cref.shape[0], 3, dtype=dt, device=xt.device)
         torque = torch.empty_like(force)
 
-    def step():
-        plan.set_sources(x2, q2, offsets)
+    # the packing and its mirror image in turn, as in the benchmarked step
+    lo, hi = x2.min(0).values, x2.max(0).values
+    xs_alt = (x2, (lo + hi) - x2)
+    cref_alt = (cref, (lo + hi) - cref) if clumps else (None, None)
+
+    def step(i):
+        plan.set_sources(xs_alt[i & 1], q2, offsets)
         plan.evaluate(pot, grad)
         if clumps:
-            plan.clump_reduce(coff, x2, q2, grad, cref, force, torque)
+            plan.clump_reduce(coff, xs_alt[i & 1], q2, grad, cref_alt[i & 1], force, torque)
 
-    for _ in range(3):
-        step()
+    for i in range(3):
+        step(i)
     torch.cuda.synchronize()
     k = 3 if prec == "fp64" else max(3, min(args.steps, 10))
     ms = 0.0
@@ -701,10 +770,12 @@ def compare_leg(args, w, prec, xt, qt, offsets, coef, n, value, stream, flush, c
         flush.fill_(i & 0xFF)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step()
+        step(i)
         b.record(stream)
         torch.cuda.synchronize()
         ms += a.elapsed_time(b)
+    step(0)   # untimed: the packing's own outputs for the accuracy check
+    torch.cuda.synchronize()
     v = n / (ms / k * 1e-3) / 1e6
     res = {"precision": prec, "p": p, "value": v, "unit": UNIT, "ms_per_step": ms / k, "steps": k,
            "speedup_of_benchmarked": value / v, "io_dtype": "f64" if prec == "fp64" else "f32"}

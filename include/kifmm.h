@@ -132,6 +132,14 @@ typedef struct {
                             potential; gradients, forces and the energy of a
                             neutral cell do not depend on it).              */
     int kernel;          /* kifmm_kernel: the kernel of the sum of Eq. 1      */
+    int reuse_lists;     /* 0: every set_sources builds the U/V/W/X lists and
+                            box partitions.  1: set_sources compares the boxes
+                            of the new tree (level, integer coordinates,
+                            parent, child range, small-leaf flag) with those
+                            the lists were last built for and keeps the lists
+                            when they are equal (the lists are a function of
+                            the boxes alone, so the outputs are bit-identical
+                            to a rebuild); kifmm_tree_info reports which.   */
 } kifmm_plan_desc;
 
 /* Kernels of Eq. 1.  The Laplace kernel is the default (1/(4 pi r) times
@@ -411,6 +419,10 @@ typedef struct {
     int64_t n_u, n_v, n_w, n_x; /* total list entries */
     int sort_passes;            /* 8-bit key digits the last build's radix sort
                                    processed (from the most significant one) */
+    int lists_reused;           /* 1: the last set_sources found the boxes its
+                                   lists were built for (reuse_lists plans
+                                   only) and kept the lists and box
+                                   partitions; 0: built them                   */
 } kifmm_tree_info_t;
 
 kifmm_status kifmm_tree_info(kifmm_plan *plan, kifmm_tree_info_t *info);

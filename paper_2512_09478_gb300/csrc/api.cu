@@ -240,6 +240,7 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     if (d.m2l_eps > 0.0 && d.precision != KIFMM_MIXED_FP16) return KIFMM_ERR_ARG;
     if (!(d.cell >= 0.0) || !std::isfinite(d.cell)) return KIFMM_ERR_ARG;
     if (d.kernel != KIFMM_KERNEL_LAPLACE && d.kernel != KIFMM_KERNEL_STOKESLET) return KIFMM_ERR_ARG;
+    if (d.reuse_lists != 0 && d.reuse_lists != 1) return KIFMM_ERR_ARG;
     if (d.kernel == KIFMM_KERNEL_STOKESLET &&
         (d.precision == KIFMM_MIXED_FP16 || d.m2l_eps != 0.0 || d.cell != 0.0 || d.p > 8))
         return KIFMM_ERR_ARG;
@@ -314,6 +315,7 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {(void **)&P.qsum, sizeof(double) * 2},
         {&P.frc, P.stokes ? esz * 3 * n : 8},
         {(void **)&P.pshift, sizeof(double)},
+        {(void **)&P.tree_differs, sizeof(int)},
     };
     for (const A &a : arrs)
         if (plan_alloc(P, a.p, a.bytes) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
@@ -382,8 +384,20 @@ static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cu
     // build regardless; the status is read once at the end.
     API_CUDA(build_tree(P, xyz, q, s));
     API_CUDA(ensure_box_arrays(P));
-    API_CUDA(build_lists(P, s));
-    API_CUDA(partition_boxes(P, s));
+    // the lists (and the box partitions) depend on the boxes alone: when the
+    // new tree has the boxes the lists were built for, they are kept
+    P.lists_reused = false;
+    if (P.desc.reuse_lists && P.prev_nb == P.nb && P.prev_sys_off == P.sys_off_h) {
+        int differs = 1;
+        API_CUDA(same_boxes(P, &differs, s));
+        P.lists_reused = (differs == 0);
+    }
+    if (!P.lists_reused) {
+        P.prev_nb = -1;  // recorded below once the build has succeeded
+        API_CUDA(build_lists(P, s));
+        API_CUDA(partition_boxes(P, s));
+        if (P.desc.reuse_lists) API_CUDA(save_boxes(P, s));
+    }
     API_CUDA(gather_particles(P, xyz, q, s));
     if (P.desc.precision == KIFMM_MIXED_FP16) API_CUDA(m2l_tensor_tiles(P, s));
     // energy chunks (sorted order never mixes systems; they depend on the
@@ -414,6 +428,10 @@ static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cu
     API_CUDA(cudaMemcpyAsync(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     API_CUDA(cudaStreamSynchronize(s));
     if (st != 0) return (kifmm_status)st;
+    if (!P.lists_reused) {
+        P.prev_nb = P.nb;
+        P.prev_sys_off = P.sys_off_h;
+    }
     P.has_sources = true;
     return KIFMM_OK;
 }
@@ -569,6 +587,7 @@ kifmm_status kifmm_tree_info(kifmm_plan *pl, kifmm_tree_info_t *info) {
     info->n_w = P.n_w;
     info->n_x = P.n_x;
     info->sort_passes = P.sort_passes;
+    info->lists_reused = P.lists_reused ? 1 : 0;
     return KIFMM_OK;
 }
 

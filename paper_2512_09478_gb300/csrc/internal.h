@@ -155,6 +155,14 @@ struct Plan {
     int64_t nb = 0, n = 0;
     int n_sys = 0, max_level = 0;
     int sort_passes = 8;  // 8-bit key digits the last build sorted (from the top)
+    // The boxes the lists were last built for: level, coordinates, parent,
+    // child range and direct-sum flag per box ([8][prev_cap] int32).  A new
+    // tree with the same boxes has the same lists, so set_sources keeps them.
+    int32_t *prev_tree = nullptr;
+    int64_t prev_nb = -1, prev_cap = 0;
+    std::vector<int64_t> prev_sys_off;
+    int *tree_differs = nullptr;
+    bool lists_reused = false;
     std::vector<int64_t> sys_off_h;
     // Offsets already on the device and those the energy chunks were built
     // for: unchanged systems skip both uploads (a pageable copy would stall
@@ -250,6 +258,10 @@ inline void count_launch(Plan &P, int64_t k = 1) { P.launches += k; }
 cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s);
 cudaError_t build_lists(Plan &P, cudaStream_t s);
 cudaError_t partition_boxes(Plan &P, cudaStream_t s);
+// tree.cu: *differs = 0 when the current boxes equal the saved ones
+// (synchronises the stream); save_boxes records the current boxes.
+cudaError_t same_boxes(Plan &P, int *differs, cudaStream_t s);
+cudaError_t save_boxes(Plan &P, cudaStream_t s);
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total_dev,
                                uint32_t *tmp, size_t tmp_elems, cudaStream_t s);
 size_t scan_tmp_needed(int64_t n);

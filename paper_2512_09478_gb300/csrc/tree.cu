@@ -1033,6 +1033,65 @@ cudaError_t partition_boxes(Plan &P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The fields of a box the lists depend on: level, coordinates, parent,
+// child range, and whether it is a leaf summed directly (the small-leaf rule).
+__device__ __forceinline__ void box_fields(int64_t b, int thr, const int32_t *lvl, const int32_t *cx,
+                                           const int32_t *cy, const int32_t *cz, const int32_t *parent,
+                                           const int32_t *nchild, const int32_t *child_first, const int32_t *cnt,
+                                           int32_t (&f)[8]) {
+    f[0] = lvl[b], f[1] = cx[b], f[2] = cy[b], f[3] = cz[b], f[4] = parent[b], f[5] = nchild[b],
+    f[6] = child_first[b], f[7] = (nchild[b] == 0 && thr >= 0 && cnt[b] <= thr) ? 1 : 0;
+}
+__global__ void k_boxes_differ(int64_t nb, int thr, const int32_t *__restrict__ lvl, const int32_t *__restrict__ cx,
+                               const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
+                               const int32_t *__restrict__ parent, const int32_t *__restrict__ nchild,
+                               const int32_t *__restrict__ child_first, const int32_t *__restrict__ cnt,
+                               const int32_t *__restrict__ prev, int64_t cap, int *differs) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int32_t f[8];
+    box_fields(b, thr, lvl, cx, cy, cz, parent, nchild, child_first, cnt, f);
+    bool same = true;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) same = same && (f[k] == prev[k * cap + b]);
+    if (!same) *differs = 1;
+}
+__global__ void k_boxes_save(int64_t nb, int thr, const int32_t *__restrict__ lvl, const int32_t *__restrict__ cx,
+                             const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
+                             const int32_t *__restrict__ parent, const int32_t *__restrict__ nchild,
+                             const int32_t *__restrict__ child_first, const int32_t *__restrict__ cnt,
+                             int32_t *__restrict__ prev, int64_t cap) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int32_t f[8];
+    box_fields(b, thr, lvl, cx, cy, cz, parent, nchild, child_first, cnt, f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) prev[k * cap + b] = f[k];
+}
+
+cudaError_t same_boxes(Plan &P, int *differs, cudaStream_t s) {
+    KIFMM_CUDA_TRY(cudaMemsetAsync(P.tree_differs, 0, sizeof(int), s));
+    if (P.nb > 0)
+        ++g_launches, k_boxes_differ<<<grid_for(P.nb, 256), 256, 0, s>>>(
+                          P.nb, P.direct_thr, P.lvl, P.cx, P.cy, P.cz, P.parent, P.nchild, P.child_first, P.cnt,
+                          P.prev_tree, P.prev_cap, P.tree_differs);
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(differs, P.tree_differs, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t save_boxes(Plan &P, cudaStream_t s) {
+    if (P.nb > P.prev_cap) {
+        const int64_t cap = P.nb + P.nb / 4 + 256;
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.prev_tree, sizeof(int32_t) * 8 * cap));
+        P.prev_cap = cap;
+    }
+    if (P.nb > 0)
+        ++g_launches, k_boxes_save<<<grid_for(P.nb, 256), 256, 0, s>>>(P.nb, P.direct_thr, P.lvl, P.cx, P.cy, P.cz,
+                                                                       P.parent, P.nchild, P.child_first, P.cnt,
+                                                                       P.prev_tree, P.prev_cap);
+    return cudaGetLastError();
+}
+
 // Octree levels whose split digits lie in the top `npass` 8-bit digits of the
 // 63-bit key (level l is read from bits [63 - 3l, 66 - 3l)).
 static int levels_sorted(int npass) { return (8 * npass - 1) / 3; }

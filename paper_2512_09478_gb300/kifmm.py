@@ -33,13 +33,14 @@ class PlanDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("coef", ctypes.c_double), ("n_max", ctypes.c_int64),
                 ("n_systems_max", ctypes.c_int), ("dtype", ctypes.c_int), ("pinv_eps", ctypes.c_double),
                 ("autotune", ctypes.c_int), ("direct_max", ctypes.c_int), ("m2l_eps", ctypes.c_double),
-                ("cell", ctypes.c_double), ("kernel", ctypes.c_int)]
+                ("cell", ctypes.c_double), ("kernel", ctypes.c_int), ("reuse_lists", ctypes.c_int)]
 
 
 class TreeInfo(ctypes.Structure):
     _fields_ = [("n_particles", ctypes.c_int64), ("n_boxes", ctypes.c_int64), ("max_level", ctypes.c_int),
                 ("n_systems", ctypes.c_int), ("n_u", ctypes.c_int64), ("n_v", ctypes.c_int64),
-                ("n_w", ctypes.c_int64), ("n_x", ctypes.c_int64), ("sort_passes", ctypes.c_int)]
+                ("n_w", ctypes.c_int64), ("n_x", ctypes.c_int64), ("sort_passes", ctypes.c_int),
+                ("lists_reused", ctypes.c_int)]
 
 
 STAGES = ["tree", "p2m", "m2m", "m2l", "p2l", "l2l", "leaf", "p2p", "out"]
@@ -129,7 +130,8 @@ class Plan:
     def __init__(self, p: int = 6, leaf_cap: int = 128, max_depth: int = 20, precision: str = "fp32",
                  coef: float = 1.0, n_max: int = 1 << 20, n_systems_max: int = 1,
                  dtype: torch.dtype = torch.float32, pinv_eps: float = 0.0, autotune: bool = False,
-                 direct_max: int = 0, m2l_eps: float = 0.0, cell: float = 0.0, kernel: str = "laplace"):
+                 direct_max: int = 0, m2l_eps: float = 0.0, cell: float = 0.0, kernel: str = "laplace",
+                 reuse_lists: bool = False):
         lib = load()
         self.dtype = dtype
         self.precision = precision
@@ -137,7 +139,7 @@ class Plan:
         d = PlanDesc(p=p, leaf_cap=leaf_cap, max_depth=max_depth, precision=PRECISIONS[precision], coef=coef,
                      n_max=n_max, n_systems_max=n_systems_max,
                      dtype=1 if dtype == torch.float64 else 0, pinv_eps=pinv_eps, autotune=int(autotune), direct_max=direct_max,
-                     m2l_eps=m2l_eps, cell=cell, kernel=KERNELS[kernel])
+                     m2l_eps=m2l_eps, cell=cell, kernel=KERNELS[kernel], reuse_lists=int(reuse_lists))
         h = ctypes.c_void_p()
         _check(lib.kifmm_plan_create(ctypes.byref(d), ctypes.byref(h)), "kifmm_plan_create")
         self._h = h

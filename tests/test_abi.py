@@ -85,7 +85,7 @@ def test_host_side_argument_checks():
            dict(n_max=0), dict(n_systems_max=0), dict(dtype=2), dict(pinv_eps=-1.0), dict(pinv_eps=1.0),
            dict(m2l_eps=-1e-5), dict(m2l_eps=1.0), dict(m2l_eps=float("nan")),
            dict(m2l_eps=1e-5, precision=kifmm.PRECISIONS["fp32"]),
-           dict(m2l_eps=1e-5, precision=kifmm.PRECISIONS["fp64"])]
+           dict(m2l_eps=1e-5, precision=kifmm.PRECISIONS["fp64"]), dict(reuse_lists=2), dict(reuse_lists=-1)]
     for kw in bad:
         h = P()
         d = desc(**kw)

@@ -7,6 +7,8 @@
 * Accuracy after small motions: within the method's error of a fresh tree,
   against the FP64 direct sum.
 * Non-finite input and argument errors are reported.
+* set_sources keeps the lists when the rebuilt tree has the same boxes: the
+  outputs and lists equal a fresh plan's bit for bit; other boxes rebuild them.
 """
 import numpy as np
 import pytest
@@ -29,9 +31,9 @@ def _lib():
     torch.cuda.set_device(0)
 
 
-def _plan(n, precision="fp64", p=4, M=32, dtype=torch.float64):
+def _plan(n, precision="fp64", p=4, M=32, dtype=torch.float64, reuse_lists=False):
     from paper_2512_09478_gb300 import Plan
-    return Plan(p=p, leaf_cap=M, max_depth=20, precision=precision, n_max=n, dtype=dtype)
+    return Plan(p=p, leaf_cap=M, max_depth=20, precision=precision, n_max=n, dtype=dtype, reuse_lists=reuse_lists)
 
 
 def _dev(a, dtype=torch.float64):
@@ -147,7 +149,7 @@ def test_large_motion_rebuilds_like_set_sources():
     fresh.set_sources(_dev(x2), _dev(q))
     pot_f, grad_f, _ = fresh.evaluate()
     # the same tree (the sorted digit count may differ: it follows each plan's last depth)
-    strip = lambda d: {k: v for k, v in d.items() if k != "sort_passes"}
+    strip = lambda d: {k: v for k, v in d.items() if k not in ("sort_passes", "lists_reused")}
     assert strip(plan.tree_info()) == strip(fresh.tree_info())
     k1, p1, l1 = plan.keys()
     k2, p2, l2 = fresh.keys()
@@ -190,7 +192,7 @@ def test_refresh_with_several_systems():
     fresh.set_sources(_dev(xm), _dev(q), sys_offsets=off)
     pot_f, _, energy_f = fresh.evaluate(want_energy=True)
     # the same tree (the sorted digit count may differ: it follows each plan's last depth)
-    strip = lambda d: {k: v for k, v in d.items() if k != "sort_passes"}
+    strip = lambda d: {k: v for k, v in d.items() if k not in ("sort_passes", "lists_reused")}
     assert strip(plan.tree_info()) == strip(fresh.tree_info())
     assert O.rel_l2(pot.cpu().numpy(), pot_f.cpu().numpy()) <= 1e-14
     assert O.rel_l2(energy.cpu().numpy(), energy_f.cpu().numpy()) <= 1e-14
@@ -236,3 +238,44 @@ def test_changed_system_offsets_are_uploaded():
         assert energy.shape[0] == len(off) - 1
         assert O.rel_l2(energy.cpu().numpy(), energy_f.cpu().numpy()) <= 1e-14, off
         assert O.rel_l2(pot.cpu().numpy(), pot_f.cpu().numpy()) <= 1e-14, off
+
+
+@pytest.mark.parametrize("precision,dtype", [("fp64", torch.float64), ("mixed_fp16", torch.float32)])
+def test_set_sources_keeps_lists_of_unchanged_boxes(precision, dtype):
+    """With reuse_lists, a rebuilt tree with the same boxes (level,
+    coordinates, parent, children, small-leaf flag) keeps its lists and box
+    partitions; the outputs are then bit-identical to a fresh plan's.  A tree
+    whose boxes changed builds them again; a plan without the flag always
+    does."""
+    x, q = G.uniform_charges(6000, 91)
+    M = 32
+    jitter = np.random.default_rng(92).uniform(-1e-9, 1e-9, size=x.shape)
+    plain = _plan(len(x), precision=precision, M=M, dtype=dtype)
+    for _ in range(2):
+        plain.set_sources(_dev(x, dtype), _dev(q, dtype))
+        assert plain.tree_info()["lists_reused"] == 0
+    plan = _plan(len(x), precision=precision, M=M, dtype=dtype, reuse_lists=True)
+    plan.set_sources(_dev(x, dtype), _dev(q, dtype))
+    assert plan.tree_info()["lists_reused"] == 0          # the first build
+    for xs, reused in ((x + jitter, 1), (x, 1)):
+        plan.set_sources(_dev(xs, dtype), _dev(q, dtype))
+        assert plan.tree_info()["lists_reused"] == reused
+        pot, grad, _ = plan.evaluate()
+        fresh = _plan(len(x), precision=precision, M=M, dtype=dtype)
+        fresh.set_sources(_dev(xs, dtype), _dev(q, dtype))
+        pf, gf, _ = fresh.evaluate()
+        assert torch.equal(pot, pf) and torch.equal(grad, gf)
+        for kind in "UVWX":
+            a, b = plan.list(kind), fresh.list(kind)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # a particle moved across the domain: other boxes, lists built again
+    x2 = x.copy()
+    x2[:200] = np.random.default_rng(93).uniform(0, 0.2, size=(200, 3))
+    plan.set_sources(_dev(x2, dtype), _dev(q, dtype))
+    assert plan.tree_info()["lists_reused"] == 0
+    pot, grad, _ = plan.evaluate()
+    fresh = _plan(len(x), precision=precision, M=M, dtype=dtype)
+    fresh.set_sources(_dev(x2, dtype), _dev(q, dtype))
+    pf, gf, _ = fresh.evaluate()
+    assert torch.equal(pot, pf) and torch.equal(grad, gf)
+    assert plan.device_status() == 0
