@@ -668,6 +668,7 @@ def run_ours(args, rank, world, local_rank):
         cfg["rsa_solid_fraction"] = round(meta["solid_fraction"], 4)
     tun = plan.tuning()
     cfg["tiles"] = {"autotuned": tun["tuned_leaf"], "m2l_stages": tun["m2l_stages"],
+                    "m2l_producer_warps": tun["m2l_producers"], "m2l_tiles_per_cta": tun["m2l_tiles"],
                     "leaf_tpl_x_groups_per_8_targets": ["%dx%d" % t for t in tun["leaf_tiles"]]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

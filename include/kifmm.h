@@ -403,8 +403,20 @@ typedef struct {
     int m2l_rank_out;    /* compressed M2L: left rank (outputs, without the
                             mean column); 0 for a dense M2L               */
     int m2l_rank_in;     /* compressed M2L: right rank (inputs); 0 if dense  */
+    int m2l_producers;   /* tensor-core M2L: warps gathering the source rows
+                            (0 when the plan has none)                      */
+    int m2l_tiles;       /* tensor-core M2L: tiles of 128 targets per CTA that
+                            share each operator block (1 or 2; 0: none)     */
 } kifmm_tuning_t;
 kifmm_status kifmm_get_tuning(kifmm_plan *plan, kifmm_tuning_t *out);
+
+/* Pins the tensor-core M2L variant instead of tuning it (a known-good choice
+ * replayed, or each variant tested): producers 2 or 4 warps, tiles 1 or 2
+ * (two tiles take two producer warps), stages 2 .. the shared-memory
+ * maximum for that tile count.  Every variant computes bit-identical
+ * results.  KIFMM_ERR_ARG for other values or a plan without the
+ * tensor-core M2L (FP64, FP32, Stokeslet).  Host only; no device work. */
+kifmm_status kifmm_set_m2l_tuning(kifmm_plan *plan, int producers, int tiles, int stages);
 
 /* ------------------------------------------------------------------------
  * Introspection (tests and tools).  All outputs are host buffers sized by

@@ -560,11 +560,18 @@ kifmm_status kifmm_profile_read(kifmm_plan *pl, kifmm_profile_t *out) {
     return KIFMM_OK;
 }
 
+kifmm_status kifmm_set_m2l_tuning(kifmm_plan *pl, int producers, int tiles, int stages) {
+    if (!pl) return KIFMM_ERR_ARG;
+    return m2l_tensor_pin(pl->P, producers, tiles, stages) ? KIFMM_OK : KIFMM_ERR_ARG;
+}
+
 kifmm_status kifmm_get_tuning(kifmm_plan *pl, kifmm_tuning_t *out) {
     if (!pl || !out) return KIFMM_ERR_ARG;
     const Plan &P = pl->P;
     out->tuned = (P.tuned_leaf ? 1 : 0) | (P.tuned_m2l ? 2 : 0);
     out->m2l_stages = m2l_tensor_stages(P);
+    out->m2l_producers = m2l_tensor_producers(P);
+    out->m2l_tiles = m2l_tensor_tiles_per_cta(P);
     out->m2l_rank_out = P.m2l_rl;
     out->m2l_rank_in = P.m2l_rr;
     for (int i = 0; i < kLeafBuckets; ++i) {

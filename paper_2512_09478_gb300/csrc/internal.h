@@ -288,6 +288,9 @@ void m2l_tensor_release(Plan &P);
 // Autotuning: true when desc.autotune asks for it, something is still
 // untuned and the stream is not being captured (tuning synchronises).
 bool tuning_wanted(const Plan &P, cudaStream_t s);
+bool m2l_tensor_pin(Plan &P, int producers, int tiles, int stages);  // false: no such variant
+int m2l_tensor_tiles_per_cta(const Plan &P);  // its target tiles per CTA (0: none)
+int m2l_tensor_producers(const Plan &P);  // its producer warps (0: none)
 int m2l_tensor_stages(const Plan &P);  // current pipeline depth of the tensor-core M2L (0: none)
 // Device time of one launch sequence on stream s, in ms (synchronises).
 template <class F>

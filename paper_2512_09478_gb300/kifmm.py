@@ -53,7 +53,8 @@ class ProfileT(ctypes.Structure):
 
 class TuningT(ctypes.Structure):
     _fields_ = [("tuned", ctypes.c_int), ("m2l_stages", ctypes.c_int), ("leaf_tpl", ctypes.c_int * 16),
-                ("leaf_groups", ctypes.c_int * 16), ("m2l_rank_out", ctypes.c_int), ("m2l_rank_in", ctypes.c_int)]
+                ("leaf_groups", ctypes.c_int * 16), ("m2l_rank_out", ctypes.c_int), ("m2l_rank_in", ctypes.c_int),
+                ("m2l_producers", ctypes.c_int), ("m2l_tiles", ctypes.c_int)]
 
 
 _LIB = None
@@ -62,7 +63,7 @@ EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifm
            "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
            "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources",
            "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_refresh_sources", "kifmm_lr_stride", "kifmm_far_image_operator",
-           "kifmm_copy_list_images"]
+           "kifmm_copy_list_images", "kifmm_set_m2l_tuning"]
 
 
 def load(path: str = LIB_PATH):
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.kifmm_refresh_sources.argtypes = [P, P, P, D, ctypes.POINTER(I), P]
     lib.kifmm_lr_stride.argtypes = [D, D, ctypes.POINTER(I64)]
     lib.kifmm_far_image_operator.argtypes = [I, D, P]
+    lib.kifmm_set_m2l_tuning.argtypes = [P, I, I, I]
     lib.kifmm_copy_list_images.argtypes = [P, I, P, P, P]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int if name != "kifmm_status_string" else ctypes.c_char_p
@@ -269,7 +271,12 @@ class Plan:
         _check(load().kifmm_get_tuning(self._h, ctypes.byref(t)), "kifmm_get_tuning")
         return {"tuned_leaf": bool(t.tuned & 1), "tuned_m2l": bool(t.tuned & 2), "m2l_stages": t.m2l_stages,
                 "leaf_tiles": [(t.leaf_tpl[i], t.leaf_groups[i]) for i in range(16)],
-                "m2l_ranks": (t.m2l_rank_out, t.m2l_rank_in)}
+                "m2l_ranks": (t.m2l_rank_out, t.m2l_rank_in), "m2l_producers": t.m2l_producers,
+                "m2l_tiles": t.m2l_tiles}
+
+    def set_m2l_tuning(self, producers: int, tiles: int, stages: int):
+        """Pin the tensor-core M2L variant (see kifmm_set_m2l_tuning)."""
+        _check(load().kifmm_set_m2l_tuning(self._h, producers, tiles, stages), "kifmm_set_m2l_tuning")
 
     def profile_read(self) -> dict:
         """Per-stage device milliseconds and bracket counts since the last
