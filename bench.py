@@ -94,6 +94,8 @@ def parse():
                     help="also time the same step with the compressed M2L at this eps (0: skip)")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--m2l-variant", default=None,
+                    help="pin the tensor-core M2L variant as producers,tiles,stages (e.g. 2,2,3) instead of tuning it")
     ap.add_argument("--compare", default="auto",
                     help="also time this precision on the same workload (auto: the workload's comparison "
                          "path, none: skip)")
@@ -373,6 +375,8 @@ def run_ours(args, rank, world, local_rank):
     qt = torch.tensor(q, dtype=torch.float32, device=dev)
     plan = Plan(p=w["p"], leaf_cap=w["leaf_cap"], max_depth=w["max_depth"], precision=args.precision, coef=coef,
                 n_max=n, n_systems_max=n_sys, dtype=torch.float32, autotune=not args.no_autotune)
+    if args.m2l_variant:
+        plan.set_m2l_tuning(*[int(v) for v in args.m2l_variant.split(",")])
     pot = torch.empty(n, dtype=torch.float32, device=dev)
     grad = torch.empty(n, 3, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -526,10 +530,13 @@ def run_ours(args, rank, world, local_rank):
 
     # second number: the tree reused across steps (update_sources + evaluate),
     # the long-range stride / reuse case; same L2 flush and events
+    # untimed: the packing's own tree and outputs again (e2e may end on the
+    # mirror image; a captured graph was recorded on this tree)
+    eager_step(0)
+    torch.cuda.synchronize()
+
     reuse = None
     if graph is None:
-        eager_step(0)   # untimed: the tree of the packing itself (e2e may end on its mirror image)
-
         def reuse_step():
             plan.update_sources(xt, qt)
             plan.evaluate(pot, grad)

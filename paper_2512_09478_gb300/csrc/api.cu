@@ -330,6 +330,7 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
     if (plan_alloc(P, (void **)&P.scan_tmp, sizeof(uint32_t) * P.scan_tmp_elems) != cudaSuccess)
         return fail(KIFMM_ERR_CUDA);
     if (cudaMemset(P.status, 0, sizeof(int)) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    if (cudaMallocHost((void **)&P.rb, sizeof(Plan::Readback)) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(KIFMM_ERR_CUDA);
     *out = pl;
     return KIFMM_OK;
@@ -341,6 +342,7 @@ kifmm_status kifmm_plan_destroy(kifmm_plan *pl) {
     m2l_tensor_release(pl->P);
     for (auto &b : pl->P.owned) cudaFree(b.ptr);
     pl->P.owned.clear();
+    if (pl->P.rb) cudaFreeHost(pl->P.rb);
     for (cudaEvent_t e : pl->P.ev_pool) cudaEventDestroy(e);
     if (pl->P.leaf_fork) cudaEventDestroy(pl->P.leaf_fork);
     for (int v = 0; v < kLeafTiles; ++v) {
@@ -399,7 +401,6 @@ static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cu
         if (P.desc.reuse_lists) API_CUDA(save_boxes(P, s));
     }
     API_CUDA(gather_particles(P, xyz, q, s));
-    if (P.desc.precision == KIFMM_MIXED_FP16) API_CUDA(m2l_tensor_tiles(P, s));
     // energy chunks (sorted order never mixes systems; they depend on the
     // system offsets only)
     if (P.energy_off_h != P.sys_off_h) {
@@ -424,10 +425,23 @@ static kifmm_status set_sources_impl(Plan &P, const void *xyz, const void *q, cu
                                  cudaMemcpyHostToDevice, s));
         P.energy_off_h = P.sys_off_h;
     }
-    int st = 0;
-    API_CUDA(cudaMemcpyAsync(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // the one synchronisation after the octree levels: the status word and,
+    // for new lists, their sizes and the partition counts
+    API_CUDA(cudaMemcpyAsync(&P.rb->status, P.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     API_CUDA(cudaStreamSynchronize(s));
+    const int st = P.rb->status;
+    if (!P.lists_reused) {
+        if (!lists_finish(P)) {
+            // a U or W list outgrew its storage: grow it and build again
+            // (the totals of this build bound the next one exactly)
+            API_CUDA(grow_lists(P));
+            return set_sources_impl(P, xyz, q, s);
+        }
+        partition_finish(P);
+    }
     if (st != 0) return (kifmm_status)st;
+    // tiles of the tensor-core M2L (kept lists: the same tiles)
+    if (P.desc.precision == KIFMM_MIXED_FP16 && !P.lists_reused) API_CUDA(m2l_tensor_tiles(P, s));
     if (!P.lists_reused) {
         P.prev_nb = P.nb;
         P.prev_sys_off = P.sys_off_h;

@@ -195,6 +195,14 @@ struct Plan {
     cudaEvent_t leaf_fork = nullptr, leaf_join[kLeafTiles] = {};
     int32_t *wsrc_flag = nullptr;    // [nb] 1 if the box is in some W list
     uint32_t *part_counts = nullptr; // [4][256]
+    // What set_sources reads back at its final synchronisation (pinned host
+    // memory): the status word, the list sizes and the partition counts.
+    struct Readback {
+        int status;
+        uint32_t uw[2];                 // U and W list entries
+        unsigned long long vx[4];       // V and X list entries
+        uint32_t part_counts[4][256];
+    } *rb = nullptr;
     unsigned long long *list_totals = nullptr;  // [4] V and X list sizes
     // Box lists grouped by a small key (stable, canonical order within a key):
     //   0: octant class of boxes with a V list (8 = none)
@@ -258,6 +266,12 @@ inline void count_launch(Plan &P, int64_t k = 1) { P.launches += k; }
 cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s);
 cudaError_t build_lists(Plan &P, cudaStream_t s);
 cudaError_t partition_boxes(Plan &P, cudaStream_t s);
+// after the final synchronisation of set_sources: list sizes and partition
+// offsets from the read-back counts; false when a list outgrew its storage
+// (grown here; the caller builds the lists again)
+bool lists_finish(Plan &P);
+cudaError_t grow_lists(Plan &P);
+void partition_finish(Plan &P);
 // tree.cu: *differs = 0 when the current boxes equal the saved ones
 // (synchronises the stream); save_boxes records the current boxes.
 cudaError_t same_boxes(Plan &P, int *differs, cudaStream_t s);

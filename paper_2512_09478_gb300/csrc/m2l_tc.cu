@@ -511,7 +511,12 @@ struct TcState {
     int n_in = 0, n_out = 0, ld = 0;  // operator inputs, outputs (mean excluded), stored columns
     int4 *tiles_pin = nullptr;        // pinned staging of tiles_h (a pageable copy stalls the stream)
     size_t tiles_pin_cap = 0;
+    cudaEvent_t tiles_copied = nullptr;  // the last upload from tiles_pin
     ~TcState() {
+        if (tiles_copied) {
+            cudaEventSynchronize(tiles_copied);
+            cudaEventDestroy(tiles_copied);
+        }
         if (tiles_pin) cudaFreeHost(tiles_pin);
     }
 };
@@ -606,6 +611,10 @@ cudaError_t m2l_tensor_tiles(Plan &P, cudaStream_t s) {
         S.tiles_cap = (int64_t)S.tiles_h.size() + 64;
         KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.tiles, sizeof(int4) * S.tiles_cap));
     }
+    // the staging buffer may still feed the previous upload (set_sources on
+    // another stream)
+    if (S.tiles_copied) KIFMM_CUDA_TRY(cudaEventSynchronize(S.tiles_copied));
+    else KIFMM_CUDA_TRY(cudaEventCreateWithFlags(&S.tiles_copied, cudaEventDisableTiming));
     if (S.tiles_h.size() > S.tiles_pin_cap) {
         if (S.tiles_pin) cudaFreeHost(S.tiles_pin);
         S.tiles_pin = nullptr;
@@ -614,16 +623,16 @@ cudaError_t m2l_tensor_tiles(Plan &P, cudaStream_t s) {
         S.tiles_pin_cap = S.tiles_h.size() + 64;
     }
     std::copy(S.tiles_h.begin(), S.tiles_h.end(), S.tiles_pin);
-    if (!S.tiles_h.empty())
+    if (!S.tiles_h.empty()) {
         KIFMM_CUDA_TRY(cudaMemcpyAsync(S.tiles, S.tiles_pin, sizeof(int4) * S.tiles_h.size(),
                                        cudaMemcpyHostToDevice, s));
+        KIFMM_CUDA_TRY(cudaEventRecord(S.tiles_copied, s));
+    }
     if (P.nb > S.u_cap) {
         S.u_cap = P.list_cap;
         KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.uh, sizeof(__half) * S.u_cap * S.kp));
         KIFMM_CUDA_TRY(plan_alloc(P, (void **)&S.ul, sizeof(__half) * S.u_cap * S.kp));
     }
-    // pinned: the copy runs asynchronously; set_sources synchronises before it
-    // returns, so the staging buffer is free again by the next call
     return cudaGetLastError();
 }
 

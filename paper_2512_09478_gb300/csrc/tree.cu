@@ -478,16 +478,18 @@ __global__ void k_spec_init(int64_t *level_start, int S, int *fail) {
 // Leaf-relative particle records {x - c_leaf, y - c_leaf, z - c_leaf, q} in
 // root-normalised units (root side = 1), computed in FP64.
 template <typename TI, typename TC>
-__global__ void k_gather(int64_t n_leaves, const int32_t *__restrict__ leaves, const int32_t *__restrict__ first,
+__global__ void k_gather(int64_t max_leaves, const uint32_t *__restrict__ n_leaves,
+                         const int32_t *__restrict__ leaves, const int32_t *__restrict__ first,
                          const int32_t *__restrict__ cnt, const int32_t *__restrict__ lvl,
                          const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
                          const int32_t *__restrict__ cz, const int32_t *__restrict__ sys,
                          const double *__restrict__ lo_side, const uint32_t *__restrict__ perm,
                          const TI *__restrict__ xyz, const TI *__restrict__ q,
                          typename Vec4<TC>::type *pts, double cell, double *leaf_q2) {
-    // one warp per leaf
+    // one warp per leaf; the leaf count is read on the device (the grid
+    // covers max_leaves)
     const int64_t li = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (li >= n_leaves) return;
+    if (li >= max_leaves || li >= (int64_t)*n_leaves) return;
     const int b = leaves[li];
     const int s = sys[b];
     const double side = lo_side[s * 4 + 3], inv_side = 1.0 / side;
@@ -783,8 +785,8 @@ __global__ void k_uw(int64_t nb, int pass, int thr, const int32_t *__restrict__ 
                      const int32_t *__restrict__ cz, const int32_t *__restrict__ coll,
                      const int32_t *__restrict__ coarse, const int32_t *__restrict__ ncoarse,
                      uint32_t *u_cnt, uint32_t *w_cnt, const uint32_t *__restrict__ u_ptr,
-                     const uint32_t *__restrict__ w_ptr, int32_t *u_idx, int32_t *w_idx, int *status,
-                     ListShifts sh) {
+                     const uint32_t *__restrict__ w_ptr, int32_t *u_idx, int32_t *w_idx, int64_t u_cap,
+                     int64_t w_cap, int *status, ListShifts sh) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     if (nchild[b] != 0) {
@@ -794,15 +796,17 @@ __global__ void k_uw(int64_t nb, int pass, int thr, const int32_t *__restrict__ 
     const int lb = lvl[b], bx = cx[b], by = cy[b], bz = cz[b];
     uint32_t nu = 0, nw = 0;
     const uint32_t u0 = pass ? u_ptr[b] : 0, w0 = pass ? w_ptr[b] : 0;
+    // pass 1 writes only inside the storage; the host sees a list that
+    // outgrew it from the totals and builds the lists again
     auto put_u = [&](int32_t a, int sa) {
-        if (pass) {
+        if (pass && (int64_t)u0 + nu < u_cap) {
             u_idx[u0 + nu] = a;
             if (sh.u) sh.u[u0 + nu] = (int8_t)sa;
         }
         ++nu;
     };
     auto put_w = [&](int32_t a, int sa) {
-        if (pass) {
+        if (pass && (int64_t)w0 + nw < w_cap) {
             w_idx[w0 + nw] = a;
             if (sh.w) sh.w[w0 + nw] = (int8_t)sa;
         }
@@ -851,9 +855,12 @@ __global__ void k_uw(int64_t nb, int pass, int thr, const int32_t *__restrict__ 
     }
 }
 
-__global__ void k_mark_w(int64_t nw, const int32_t *__restrict__ w_idx, int32_t *flag) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nw) flag[w_idx[i]] = 1;
+// W-list sources: the entry count is read on the device (w_ptr[nb]), capped
+// by the storage.
+__global__ void k_mark_w(int64_t cap, const uint32_t *__restrict__ w_total, const int32_t *__restrict__ w_idx,
+                         int32_t *flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cap && i < (int64_t)*w_total) flag[w_idx[i]] = 1;
 }
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
@@ -1018,19 +1025,22 @@ cudaError_t partition_boxes(Plan &P, cudaStream_t s) {
     ++g_launches, k_part_scatter<<<grid, kBlock, 0, s>>>(nb, nblk, P.nv, P.nchild, P.lvl, P.wsrc_flag, P.cx, P.cy,
                                                          P.cz, P.hist + nh, P.part_list[0], P.part_list[1],
                                                          P.part_list[2], P.part_list[3]);
-    // one synchronisation for the four key histograms
-    uint32_t counts[4][256];
-    KIFMM_CUDA_TRY(cudaMemcpyAsync(counts, P.part_counts, sizeof(counts), cudaMemcpyDeviceToHost, s));
-    KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    // the four key histograms come back with set_sources' final
+    // synchronisation (the gather reads the leaf count on the device)
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.rb->part_counts, P.part_counts, sizeof(P.rb->part_counts),
+                                   cudaMemcpyDeviceToHost, s));
+    P.m2l_targets = P.part_list[0];
+    P.leaves = P.part_list[1];
+    return cudaGetLastError();
+}
+
+void partition_finish(Plan &P) {
     for (int mode = 0; mode < 4; ++mode) {
         P.part_start[mode].assign(257, 0);
-        for (int k = 0; k < 256; ++k) P.part_start[mode][k + 1] = P.part_start[mode][k] + counts[mode][k];
+        for (int k = 0; k < 256; ++k) P.part_start[mode][k + 1] = P.part_start[mode][k] + P.rb->part_counts[mode][k];
     }
-    P.m2l_targets = P.part_list[0];
     for (int c = 0; c <= 8; ++c) P.m2l_class_start[c] = P.part_start[0][c];
-    P.leaves = P.part_list[1];
     P.n_leaves = P.part_start[1][1];
-    return cudaGetLastError();
 }
 
 // The fields of a box the lists depend on: level, coordinates, parent,
@@ -1364,21 +1374,21 @@ cudaError_t gather_particles(Plan &P, const void *xyz, const void *q_in, cudaStr
     P.fwd_valid = P.fwd_res_valid = false;  // new sources: the last evaluate's field no longer applies
     if (P.f64) {
         if (P.io_f64)
-            ++g_launches, k_gather<double, double><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
-                P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+            ++g_launches, k_gather<double, double><<<grid_for(P.nb, 8), 256, 0, s>>>(
+                P.nb, P.part_counts + 256, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
                 (const double *)xyz, (const double *)q, (double4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
         else
-            ++g_launches, k_gather<float, double><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
-                P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+            ++g_launches, k_gather<float, double><<<grid_for(P.nb, 8), 256, 0, s>>>(
+                P.nb, P.part_counts + 256, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
                 (const float *)xyz, (const float *)q, (double4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
     } else {
         if (P.io_f64)
-            ++g_launches, k_gather<double, float><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
-                P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+            ++g_launches, k_gather<double, float><<<grid_for(P.nb, 8), 256, 0, s>>>(
+                P.nb, P.part_counts + 256, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
                 (const double *)xyz, (const double *)q, (float4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
         else
-            ++g_launches, k_gather<float, float><<<grid_for(P.n_leaves, 8), 256, 0, s>>>(
-                P.n_leaves, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
+            ++g_launches, k_gather<float, float><<<grid_for(P.nb, 8), 256, 0, s>>>(
+                P.nb, P.part_counts + 256, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
                 (const float *)xyz, (const float *)q, (float4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
     }
     return cudaGetLastError();
@@ -1426,44 +1436,51 @@ cudaError_t build_lists(Plan &P, cudaStream_t s) {
         KIFMM_CUDA_TRY(cudaGetLastError());
     }
     const unsigned g = grid_for(nb, 128);
-    ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 0, P.direct_thr, P.parent, P.cnt, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse,
-                                         P.ncoarse, P.u_cnt, P.w_cnt, nullptr, nullptr, nullptr, nullptr, P.status,
-                                         list_shifts(P));
-    // two scans, totals in the last two scratch words; one synchronisation for all list sizes
+    ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 0, P.direct_thr, P.parent, P.cnt, P.child_first, P.nchild, P.lvl,
+                                         P.cx, P.cy, P.cz, P.coll, P.coarse, P.ncoarse, P.u_cnt, P.w_cnt, nullptr,
+                                         nullptr, nullptr, nullptr, 0, 0, P.status, list_shifts(P));
+    // two scans, totals in the last two scratch words, then appended to the
+    // offsets; the sizes come back to the host with set_sources' final
+    // synchronisation (no round trip here: the fill pass writes only inside
+    // the storage and flags a list that outgrew it)
     uint32_t *tot_u = P.scan_tmp + P.scan_tmp_elems - 1, *tot_w = P.scan_tmp + P.scan_tmp_elems - 2;
     KIFMM_CUDA_TRY(exclusive_scan_u32(P.u_cnt, P.u_ptr, nb, tot_u, P.scan_tmp, P.scan_tmp_elems - 2, s));
     KIFMM_CUDA_TRY(exclusive_scan_u32(P.w_cnt, P.w_ptr, nb, tot_w, P.scan_tmp, P.scan_tmp_elems - 2, s));
     KIFMM_CUDA_TRY(cudaMemcpyAsync(P.u_ptr + nb, tot_u, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     KIFMM_CUDA_TRY(cudaMemcpyAsync(P.w_ptr + nb, tot_w, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    uint32_t uw[2];
-    unsigned long long vx[4];
-    KIFMM_CUDA_TRY(cudaMemcpyAsync(&uw[0], tot_u, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    KIFMM_CUDA_TRY(cudaMemcpyAsync(&uw[1], tot_w, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    KIFMM_CUDA_TRY(cudaMemcpyAsync(vx, P.list_totals, sizeof(vx), cudaMemcpyDeviceToHost, s));
-    KIFMM_CUDA_TRY(cudaStreamSynchronize(s));
-    P.n_u = uw[0];
-    P.n_w = uw[1];
-    P.n_v = (int64_t)vx[0];
-    P.n_x = (int64_t)vx[1];
-    if (P.n_u > P.u_cap || P.n_w > P.w_cap) {
-        // grow the list storage (set_sources may allocate; evaluate never does)
-        if (P.n_u > P.u_cap) {
-            P.u_cap = P.n_u + P.n_u / 4 + 1024;
-            KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.u_idx, sizeof(int32_t) * P.u_cap));
-            if (P.periodic) KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.u_sh, P.u_cap));
-        }
-        if (P.n_w > P.w_cap) {
-            P.w_cap = P.n_w + P.n_w / 4 + 1024;
-            KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.w_idx, sizeof(int32_t) * P.w_cap));
-            if (P.periodic) KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.w_sh, P.w_cap));
-        }
-    }
-    ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 1, P.direct_thr, P.parent, P.cnt, P.child_first, P.nchild, P.lvl, P.cx, P.cy, P.cz, P.coll, P.coarse,
-                                         P.ncoarse, P.u_cnt, P.w_cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, P.status,
-                                         list_shifts(P));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(&P.rb->uw[0], tot_u, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(&P.rb->uw[1], tot_w, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    KIFMM_CUDA_TRY(cudaMemcpyAsync(P.rb->vx, P.list_totals, sizeof(P.rb->vx), cudaMemcpyDeviceToHost, s));
+    ++g_launches, k_uw<<<g, 128, 0, s>>>(nb, 1, P.direct_thr, P.parent, P.cnt, P.child_first, P.nchild, P.lvl,
+                                         P.cx, P.cy, P.cz, P.coll, P.coarse, P.ncoarse, P.u_cnt, P.w_cnt, P.u_ptr,
+                                         P.w_ptr, P.u_idx, P.w_idx, P.u_cap, P.w_cap, P.status, list_shifts(P));
     KIFMM_CUDA_TRY(cudaMemsetAsync(P.wsrc_flag, 0, sizeof(int32_t) * nb, s));
-    if (P.n_w > 0) ++g_launches, k_mark_w<<<grid_for(P.n_w, 256), 256, 0, s>>>(P.n_w, P.w_idx, P.wsrc_flag);
+    if (P.w_cap > 0)
+        ++g_launches, k_mark_w<<<grid_for(P.w_cap, 256), 256, 0, s>>>(P.w_cap, P.w_ptr + nb, P.w_idx, P.wsrc_flag);
     KIFMM_CUDA_TRY(cudaGetLastError());
+    return cudaSuccess;
+}
+
+bool lists_finish(Plan &P) {
+    P.n_u = P.rb->uw[0];
+    P.n_w = P.rb->uw[1];
+    P.n_v = (int64_t)P.rb->vx[0];
+    P.n_x = (int64_t)P.rb->vx[1];
+    return P.n_u <= P.u_cap && P.n_w <= P.w_cap;
+}
+
+cudaError_t grow_lists(Plan &P) {
+    // grow the list storage (set_sources may allocate; evaluate never does)
+    if (P.n_u > P.u_cap) {
+        P.u_cap = P.n_u + P.n_u / 4 + 1024;
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.u_idx, sizeof(int32_t) * P.u_cap));
+        if (P.periodic) KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.u_sh, P.u_cap));
+    }
+    if (P.n_w > P.w_cap) {
+        P.w_cap = P.n_w + P.n_w / 4 + 1024;
+        KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.w_idx, sizeof(int32_t) * P.w_cap));
+        if (P.periodic) KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.w_sh, P.w_cap));
+    }
     return cudaSuccess;
 }
 
