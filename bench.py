@@ -55,12 +55,20 @@ WORKLOADS = {
 WORKLOADS["c2"]["compare"] = "fp32"
 
 
-# DRAM bytes (read + write) per launch of the dominant kernels on the 1M DEM
-# packing, from an ncu capture of the full-size launch with the DRAM byte
-# counters only (one pass; summary in profiles/).  A figure is reported only
-# while the kernel's translation unit is byte-identical to the one captured
-# (sha256); otherwise the roofline's traffic is null.
-TRAFFIC = {}
+# DRAM bytes (read + write) of the dominant kernels per step on the 1M DEM
+# packing (M2L: its one launch; leaf kernel: its three tile variants), from an
+# ncu capture of the timed steps with the DRAM byte counters and the duration
+# only (profiles/dram_traffic_c2_dem_coulomb_1M.md).  A figure is reported
+# only while the kernel's sources are byte-identical to the ones captured
+# (sha256 over the listed files); otherwise the roofline's traffic is null.
+_M2L_SRC = ("paper_2512_09478_gb300/csrc/m2l_tc.cu", "paper_2512_09478_gb300/csrc/tc_ptx.cuh",
+            "paper_2512_09478_gb300/csrc/common.cuh", "paper_2512_09478_gb300/csrc/internal.h")
+_LEAF_SRC = ("paper_2512_09478_gb300/csrc/fmm.cu", "paper_2512_09478_gb300/csrc/common.cuh",
+             "paper_2512_09478_gb300/csrc/internal.h")
+TRAFFIC = {
+    ("dem-coulomb-rsa-1M", "m2l"): (_M2L_SRC, "811eec91d2852c8e70e175f45b89c0a12963a333b35aa9dbd385d854ca04e138", 96832000),
+    ("dem-coulomb-rsa-1M", "p2p"): (_LEAF_SRC, "5393445c80a78139f10d581984f295835eec72249f1e50bec8c576d776f04875", 66596096),
+}
 
 
 def traffic_for(workload, stage):
@@ -68,13 +76,15 @@ def traffic_for(workload, stage):
     ent = TRAFFIC.get((workload, stage))
     if ent is None:
         return None
-    path, sha, nbytes = ent
+    paths, sha, nbytes = ent
+    m = hashlib.sha256()
     try:
-        with open(os.path.join(ROOT, path), "rb") as f:
-            cur = hashlib.sha256(f.read()).hexdigest()
+        for path in paths:
+            with open(os.path.join(ROOT, path), "rb") as f:
+                m.update(f.read())
     except OSError:
         return None
-    return nbytes if cur == sha else None
+    return nbytes if m.hexdigest() == sha else None
 
 
 def parse():
