@@ -399,6 +399,141 @@ __global__ void __launch_bounds__(32 * NTY, (sizeof(T) == 4 && NTY == 8 && !MULT
     }
 }
 
+// FP32 big tiles with vector shared-memory reads: 64 targets x 160 outputs
+// per 320-thread block; thread (tn = t % 40, tm = t / 40) owns outputs
+// 4 tn .. 4 tn + 3 and targets 8 tm .. 8 tm + 7, so each k step reads one
+// float4 of the operator and two of the gathered inputs for 32 FMAs (the
+// scalar tile above reads 13 values for 40).  The sums run over k in the same
+// order, one fresh partial per slot, so the results equal the scalar form's
+// bit for bit.  VEC: the input rows are 16-byte aligned (n_s a multiple of 4)
+// and are read as float4.
+constexpr int kV4Threads = 320;
+template <class G, bool MULTI, bool VEC>
+__global__ void __launch_bounds__(kV4Threads, 2) k_ggemm_v4(G g, const int32_t *__restrict__ targets,
+                                                            ClassRanges cr, int nslots, int ns, int ld,
+                                                            const float *__restrict__ in, float *__restrict__ out,
+                                                            int accumulate, double *dbar) {
+    constexpr int TT = 64, TJ = 160;
+    __shared__ __align__(16) float Us[kGK][TT];
+    __shared__ __align__(16) float Ms[kGK][TJ];
+    __shared__ int32_t tgt[TT];
+    __shared__ int32_t src[TT];
+    const int tid = threadIdx.x;
+    const int tn = tid % 40, tm = tid / 40;
+    const int cls = blockIdx.y;
+    const int j0 = (int)blockIdx.z * TJ;
+    int64_t t_begin = 0, t_end = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (c == cls) {
+            t_begin = cr.b[c];
+            t_end = cr.b[c + 1];
+        }
+    const int64_t t0 = t_begin + (int64_t)blockIdx.x * TT;
+    if (t0 >= t_end) return;  // uniform for the block
+    if (tid < TT) tgt[tid] = (t0 + tid < t_end) ? targets[t0 + tid] : -1;
+    float acc[8][4], run[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = run[a][c] = 0.f;
+    const int nk = (ns + kGK - 1) / kGK;
+    __syncthreads();
+    for (int s = 0; s < nslots; ++s) {
+        if (tid < TT) {
+            const int32_t t = tgt[tid];
+            src[tid] = (t >= 0) ? g.src(t, s, cls) : -1;
+        }
+        const float *M = g.op(s, cls);
+        __syncthreads();
+        // staged values: inputs as (target = e % 64, k quad = e / 64), four
+        // k values each; operator rows as (k, j) with j fastest
+        constexpr int kRM = kGK * TJ / kV4Threads;  // 8
+        float4 ru = make_float4(0.f, 0.f, 0.f, 0.f);
+        float rm[kRM];
+        auto load = [&](int kc) {
+            const int k0 = kc * kGK;
+            if (tid < TT * (kGK / 4)) {
+                const int t = tid % TT, k = 4 * (tid / TT);
+                const int32_t sb = src[t];
+                ru = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (sb >= 0) {
+                    const float *row = in + (size_t)sb * ns + k0 + k;
+                    if (VEC && k0 + k + 3 < ns) {
+                        ru = *reinterpret_cast<const float4 *>(row);
+                    } else {
+                        if (k0 + k < ns) ru.x = row[0];
+                        if (k0 + k + 1 < ns) ru.y = row[1];
+                        if (k0 + k + 2 < ns) ru.z = row[2];
+                        if (k0 + k + 3 < ns) ru.w = row[3];
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kRM; ++r) {
+                const int e = tid + kV4Threads * r;
+                const int k = e / TJ, j = e - k * TJ;
+                rm[r] = (k0 + k < ns && j0 + j < ld) ? M[(size_t)(k0 + k) * ld + j0 + j] : 0.f;
+            }
+        };
+        load(0);
+        for (int kc = 0; kc < nk; ++kc) {
+            if (tid < TT * (kGK / 4)) {
+                const int t = tid % TT, k = 4 * (tid / TT);
+                Us[k][t] = ru.x;
+                Us[k + 1][t] = ru.y;
+                Us[k + 2][t] = ru.z;
+                Us[k + 3][t] = ru.w;
+            }
+#pragma unroll
+            for (int r = 0; r < kRM; ++r) {
+                const int e = tid + kV4Threads * r;
+                Ms[e / TJ][e % TJ] = rm[r];
+            }
+            __syncthreads();
+            if (kc + 1 < nk) load(kc + 1);
+#pragma unroll
+            for (int k = 0; k < kGK; ++k) {
+                const float4 u0 = *reinterpret_cast<const float4 *>(&Us[k][8 * tm]);
+                const float4 u1 = *reinterpret_cast<const float4 *>(&Us[k][8 * tm + 4]);
+                const float4 m = *reinterpret_cast<const float4 *>(&Ms[k][4 * tn]);
+                const float uv[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                const float mv[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][c] += uv[a] * mv[c];
+            }
+            __syncthreads();
+        }
+        if constexpr (MULTI) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    run[a][c] += acc[a][c];
+                    acc[a][c] = 0.f;
+                }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int32_t t = tgt[8 * tm + a];
+        if (t < 0) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = j0 + 4 * tn + c;
+            const float v = MULTI ? run[a][c] : acc[a][c];
+            if (j < ns) {
+                float *o = out + (size_t)t * ns + j;
+                *o = accumulate ? *o + v : v;
+            } else if (j == ns && dbar) {
+                dbar[t] = (accumulate ? dbar[t] : 0.0) + (double)v + g.mean_base(t, dbar);
+            }
+        }
+    }
+}
+
 // Slot-split form: out = the in-order sum of the slots' partial products.
 template <typename T, class G>
 __global__ void k_ggemm_sum(G g, const int32_t *__restrict__ targets, int64_t t_first, int64_t n_t, int nslots, int ns,
@@ -1032,6 +1167,22 @@ void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *s
     const int64_t big_blocks = grid_for(total, 64) * grid_for(ld, 160);
     if (big_blocks >= 2 * P.num_sms) {
         dim3 grid(grid_for(most, 64), ncls, grid_for(ld, 160));
+        if constexpr (sizeof(T) == 4) {
+            const bool vec = P.ns % 4 == 0;
+            if (nslots > 1 && vec)
+                ++g_launches, k_ggemm_v4<G, true, true><<<grid, kV4Threads, 0, s>>>(g, targets, cr, nslots, P.ns, ld,
+                                                                                   in, out, accumulate, dbar);
+            else if (nslots > 1)
+                ++g_launches, k_ggemm_v4<G, true, false><<<grid, kV4Threads, 0, s>>>(g, targets, cr, nslots, P.ns,
+                                                                                    ld, in, out, accumulate, dbar);
+            else if (vec)
+                ++g_launches, k_ggemm_v4<G, false, true><<<grid, kV4Threads, 0, s>>>(g, targets, cr, nslots, P.ns,
+                                                                                    ld, in, out, accumulate, dbar);
+            else
+                ++g_launches, k_ggemm_v4<G, false, false><<<grid, kV4Threads, 0, s>>>(g, targets, cr, nslots, P.ns,
+                                                                                     ld, in, out, accumulate, dbar);
+            return;
+        }
         if (nslots > 1)
             ++g_launches, k_ggemm<T, G, 8, 8, 5, false, true><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld,
                                                                                   in, out, accumulate, dbar, 1, nullptr);

@@ -337,14 +337,24 @@ __global__ void __launch_bounds__(tc_threads(PW, TL), 1) k_m2l_tc(TileArgs a) {
 }
 
 // max |u| per level, as float bits (non-negative floats order like integers).
+// A warp per box; the block's maxima meet in shared memory first, so the
+// few per-level words take one global atomic per block and level, not one
+// per box.
 __global__ void k_level_absmax(int64_t nb, int ns, const float *__restrict__ u, const int32_t *__restrict__ lvl,
                                unsigned *__restrict__ level_max) {
+    __shared__ unsigned blk[kMaxLevel + 1];
+    for (int l = threadIdx.x; l <= kMaxLevel; l += blockDim.x) blk[l] = 0u;
+    __syncthreads();
     const int64_t b = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (b >= nb) return;
-    float m = 0.f;
-    for (int k = threadIdx.x & 31; k < ns; k += 32) m = fmaxf(m, fabsf(u[(size_t)b * ns + k]));
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&level_max[lvl[b]], __float_as_uint(m));
+    if (b < nb) {
+        float m = 0.f;
+        for (int k = threadIdx.x & 31; k < ns; k += 32) m = fmaxf(m, fabsf(u[(size_t)b * ns + k]));
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&blk[lvl[b]], __float_as_uint(m));
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l <= kMaxLevel; l += blockDim.x)
+        if (blk[l]) atomicMax(&level_max[l], blk[l]);
 }
 
 __device__ __forceinline__ float pow2_scale_for(float maxabs) {

@@ -53,37 +53,40 @@ __global__ void k_bbox(int64_t n, const T *__restrict__ xyz, const T *__restrict
     if (base >= n) return;
     const int64_t end = min(n, base + (int64_t)kTile);
     const int s0 = find_sys(off, S, base), s1 = find_sys(off, S, end - 1);
-    double mn[3] = {1e308, 1e308, 1e308}, mx[3] = {-1e308, -1e308, -1e308};
+    // minima and maxima are exact in the input type (FP32 inputs need no FP64
+    // arithmetic, which this GPU runs at a small fraction of the FP32 rate)
+    T mn[3], mx[3];
+    for (int d = 0; d < 3; ++d) mn[d] = mx[d] = T(0);
     int cur = -1;
     bool bad = false;
     for (int64_t i = base + threadIdx.x; i < end; i += kBlock) {
-        double v[3];
-        for (int d = 0; d < 3; ++d) v[d] = (double)xyz[3 * i + d];
-        if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || (q && !isfinite((double)q[i]))) {
+        T v[3];
+        for (int d = 0; d < 3; ++d) v[d] = xyz[3 * i + d];
+        if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || (q && !isfinite(q[i]))) {
             bad = true;
             continue;
         }
         if (s0 != s1) {
             int s = find_sys(off, S, i);
             for (int d = 0; d < 3; ++d) {
-                atomicMin(&bb[s * 6 + d], ord_of(v[d]));
-                atomicMax(&bb[s * 6 + 3 + d], ord_of(v[d]));
+                atomicMin(&bb[s * 6 + d], ord_of((double)v[d]));
+                atomicMax(&bb[s * 6 + 3 + d], ord_of((double)v[d]));
             }
             continue;
         }
-        cur = s0;
         for (int d = 0; d < 3; ++d) {
-            mn[d] = fmin(mn[d], v[d]);
-            mx[d] = fmax(mx[d], v[d]);
+            mn[d] = (cur < 0 || v[d] < mn[d]) ? v[d] : mn[d];
+            mx[d] = (cur < 0 || v[d] > mx[d]) ? v[d] : mx[d];
         }
+        cur = s0;
     }
     if (bad) set_status(status, KIFMM_ERR_NONFINITE);
     if (s0 != s1) return;
     // block reduction (single system)
     unsigned long long o[6];
     for (int d = 0; d < 3; ++d) {
-        o[d] = (cur >= 0) ? ord_of(mn[d]) : ~0ULL;
-        o[3 + d] = (cur >= 0) ? ord_of(mx[d]) : 0ULL;
+        o[d] = (cur >= 0) ? ord_of((double)mn[d]) : ~0ULL;
+        o[3 + d] = (cur >= 0) ? ord_of((double)mx[d]) : 0ULL;
     }
     for (int k = 0; k < 6; ++k) {
         unsigned long long v = o[k];
@@ -767,8 +770,6 @@ __device__ __forceinline__ void dev_vx(int64_t b, int lane, int level, int thr, 
     if (lane == 0) {
         nv[b] = cntv;
         nx[b] = cntx;
-        if (cntv) atomicAdd(&totals[0], (unsigned long long)cntv);
-        if (cntx) atomicAdd(&totals[1], (unsigned long long)cntx);
     }
 }
 
@@ -1407,13 +1408,25 @@ __global__ void k_lists_level(int64_t ls, int64_t le, int level, int thr, const 
                               unsigned long long *totals, int *status, ListShifts sh) {
     const int64_t b = ls + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (b >= le) return;
-    dev_colleagues(b, lane, level, parent, child_first, nchild, cx, cy, cz, coll, sh);
-    __syncwarp();
-    dev_coarse(b, lane, level, parent, nchild, lvl, cx, cy, cz, coll, coarse, ncoarse, status, sh);
-    __syncwarp();
-    dev_vx(b, lane, level, thr, parent, child_first, nchild, cnt, lvl, cx, cy, cz, coll, coarse, ncoarse, vdense,
-           nv, xdense, nx, totals, sh);
+    __shared__ unsigned long long blk_tot[2];
+    if (threadIdx.x < 2) blk_tot[threadIdx.x] = 0;
+    __syncthreads();
+    if (b < le) {
+        dev_colleagues(b, lane, level, parent, child_first, nchild, cx, cy, cz, coll, sh);
+        __syncwarp();
+        dev_coarse(b, lane, level, parent, nchild, lvl, cx, cy, cz, coll, coarse, ncoarse, status, sh);
+        __syncwarp();
+        dev_vx(b, lane, level, thr, parent, child_first, nchild, cnt, lvl, cx, cy, cz, coll, coarse, ncoarse, vdense,
+               nv, xdense, nx, totals, sh);
+        // V and X list totals: one global atomic per block, not per box (a
+        // single address taking an atomic from every box serialises)
+        if (lane == 0) {
+            atomicAdd(&blk_tot[0], (unsigned long long)nv[b]);
+            atomicAdd(&blk_tot[1], (unsigned long long)nx[b]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 && blk_tot[threadIdx.x]) atomicAdd(&totals[threadIdx.x], blk_tot[threadIdx.x]);
 }
 
 static ListShifts list_shifts(const Plan &P) {
