@@ -169,7 +169,7 @@ static cudaError_t ensure_box_arrays(Plan &P) {
         {&P.u_c, sizeof(float) * (size_t)P.m2l_rr * cap},
         {&P.d_c, sizeof(float) * (size_t)P.m2l_rl * cap},
         {(void **)&P.leaf_vlist, sizeof(int2) * kLeafTiles * (cap + P.desc.n_max / 8 + 64)},
-        {(void **)&P.leaf_vcnt, sizeof(int32_t) * 8},
+        {(void **)&P.leaf_vcnt, sizeof(int32_t) * 16},
     };
     for (const A &a : arrs) KIFMM_CUDA_TRY(plan_alloc(P, a.p, a.bytes));
     if (P.periodic) {

@@ -1013,15 +1013,23 @@ __global__ void k_leaf_partition(int64_t n_leaves, const int32_t *__restrict__ l
     }
 }
 
+// Each warp takes the next pass from a shared counter as it finishes one
+// (passes differ in length by their source lists; a fixed stride left the
+// last warps running alone).  Every pass writes only its own targets, so the
+// order passes are taken in does not change any result.
 template <typename T, int TPL, int G>
 __global__ void __launch_bounds__(32 * kLW, sizeof(T) == 4 ? (TPL == 1 ? 5 : 4) : 2)
-    k_leaf_all(LeafCtx C, const int2 *__restrict__ list, const int32_t *__restrict__ count,
+    k_leaf_all(LeafCtx C, const int2 *__restrict__ list, const int32_t *__restrict__ count, int32_t *next,
                const typename Vec4<T>::type *__restrict__ pts, const T *__restrict__ surf, LeafW<T> W,
                double4 *__restrict__ res) {
     __shared__ LeafSmem<T> bufs[kLW];
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nl = *count;
-    for (int li = blockIdx.x * kLW + warp; li < nl; li += gridDim.x * kLW) {
+    while (true) {
+        int li = 0;
+        if (lane == 0) li = atomicAdd(next, 1);
+        li = __shfl_sync(0xffffffffu, li, 0);
+        if (li >= nl) break;
         const int2 it = list[li];
         leaf_pass<T, TPL, G>(C, it.x, it.y, pts, surf, W, bufs[warp], res);
     }
@@ -1037,7 +1045,8 @@ void leaf_launch_variant(const Plan &P, const LeafCtx &C, int v, const typename 
     const int64_t want = (P.n_leaves + kLW - 1) / kLW;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P.num_sms * occ));
     ++g_launches, k_leaf_all<T, TPL, G><<<g, 32 * kLW, 0, s>>>(C, P.leaf_vlist + (int64_t)v * P.leaf_item_cap,
-                                                                P.leaf_vcnt + v, pts, surf, W, res);
+                                                                P.leaf_vcnt + v, P.leaf_vcnt + 8 + v, pts, surf,
+                                                                W, res);
     cudaEventRecord(P.leaf_join[v], s);
     cudaStreamWaitEvent(caller, P.leaf_join[v], 0);
 }
@@ -1049,7 +1058,7 @@ template <typename T>
 void leaf_launch(const Plan &P, const LeafCtx &C, const typename Vec4<T>::type *pts, const T *surf,
                  const LeafW<T> &W, double4 *res, cudaStream_t s) {
     if (P.n_leaves == 0) return;
-    cudaMemsetAsync(P.leaf_vcnt, 0, sizeof(int32_t) * kLeafTiles, s);
+    cudaMemsetAsync(P.leaf_vcnt, 0, sizeof(int32_t) * 16, s);  // counts and next-pass counters
     ++g_launches, k_leaf_partition<<<(unsigned)((P.n_leaves + 255) / 256), 256, 0, s>>>(
                       P.n_leaves, P.leaves, P.cnt, C.tile, P.leaf_item_cap, P.leaf_vlist, P.leaf_vcnt);
     cudaEventRecord(P.leaf_fork, s);

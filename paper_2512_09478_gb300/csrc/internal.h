@@ -187,7 +187,7 @@ struct Plan {
     int32_t *leaves = nullptr;       // [nb] leaf indices
     int64_t n_leaves = 0;
     int2 *leaf_vlist = nullptr;      // [kLeafTiles][leaf_item_cap] (leaf, first target) passes per variant
-    int32_t *leaf_vcnt = nullptr;    // [8] passes per variant
+    int32_t *leaf_vcnt = nullptr;    // [16]: passes per variant [0, 8), then each variant's next-pass counter
     int64_t leaf_item_cap = 0;       // bound on passes: every pass but a leaf's last covers >= 8 targets
     // the leaf-kernel variants run concurrently: forked from the caller's
     // stream onto these and joined back (event-ordered, so capturable)
