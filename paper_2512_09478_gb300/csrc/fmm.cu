@@ -115,6 +115,65 @@ __global__ void k_p2m(const int32_t *__restrict__ leaves, const int32_t *__restr
 }
 
 
+// P2M, FP32 forward form: kP2mLeaves leaves per block (a leaf's ~n_s x 30
+// kernel evaluations are too little work for a block of their own) and the
+// particle loop on packed f32x2 arithmetic, two particles per instruction
+// (the chunk's odd tail padded with a null particle: weight 0, far away).
+constexpr int kP2mLeaves = 4;
+__global__ void k_p2m_f32(const int32_t *__restrict__ leaves, int64_t n_leaves, const int32_t *__restrict__ lvl,
+                          const int32_t *__restrict__ first, const int32_t *__restrict__ cnt,
+                          const float4 *__restrict__ pts, const float *__restrict__ surf, int ns,
+                          float *__restrict__ u) {
+    extern __shared__ __align__(16) unsigned char p2m_sm[];
+    const int nt = blockDim.x;  // a multiple of 32
+    float *sx = (float *)p2m_sm, *sy = sx + nt, *sz = sy + nt, *sq = sz + nt;
+    const float a = (float)kAlphaOuter;
+    const int64_t l0 = (int64_t)blockIdx.x * kP2mLeaves, l1 = min(n_leaves, l0 + kP2mLeaves);
+    for (int64_t li = l0; li < l1; ++li) {
+        const int b = leaves[li];
+        const float hinv = 1.f / box_half<float>(lvl[b]);
+        const int n = cnt[b], f = first[b];
+        for (int j0 = 0; j0 < ns; j0 += nt) {
+            const int j = j0 + threadIdx.x;
+            float px = 0.f, py = 0.f, pz = 0.f;
+            if (j < ns) {
+                px = a * surf[3 * j];
+                py = a * surf[3 * j + 1];
+                pz = a * surf[3 * j + 2];
+            }
+            const float2 npx = make_float2(-px, -px), npy = make_float2(-py, -py), npz = make_float2(-pz, -pz);
+            float2 acc = make_float2(0.f, 0.f);
+            for (int c0 = 0; c0 < n; c0 += nt) {
+                __syncthreads();
+                const int m = min(nt, n - c0);
+                if ((int)threadIdx.x < m) {
+                    const float4 v = pts[f + c0 + threadIdx.x];
+                    sx[threadIdx.x] = v.x * hinv;
+                    sy[threadIdx.x] = v.y * hinv;
+                    sz[threadIdx.x] = v.z * hinv;
+                    sq[threadIdx.x] = v.w;
+                } else if ((int)threadIdx.x == m) {  // m < nt: pad the odd tail
+                    sx[m] = sy[m] = sz[m] = 1e4f;
+                    sq[m] = 0.f;
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int i = 0; i < m; i += 2) {
+                    const float2 rx = __fadd2_rn(*reinterpret_cast<const float2 *>(sx + i), npx);
+                    const float2 ry = __fadd2_rn(*reinterpret_cast<const float2 *>(sy + i), npy);
+                    const float2 rz = __fadd2_rn(*reinterpret_cast<const float2 *>(sz + i), npz);
+                    float2 r2 = __fmul2_rn(rx, rx);
+                    r2 = __ffma2_rn(ry, ry, r2);
+                    r2 = __ffma2_rn(rz, rz, r2);
+                    const float2 ri = make_float2(rsqrt_t<float>(r2.x), rsqrt_t<float>(r2.y));
+                    acc = __ffma2_rn(*reinterpret_cast<const float2 *>(sq + i), ri, acc);
+                }
+            }
+            if (j < ns) u[(size_t)b * ns + j] = (acc.x + acc.y) * hinv;
+        }
+    }
+}
+
 // P2L: d(b)_j += (1/h_b) sum_{a in X(b)} sum_i q_i / |1.05 S_j - (x_i - c_b)/h_b|
 template <typename T>
 __global__ void k_p2l(const int32_t *__restrict__ nx, const int32_t *__restrict__ xdense,
@@ -1332,8 +1391,13 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     double4 *res = (double4 *)P.res;
     // upward pass
     stage_begin(P, KIFMM_STAGE_P2M, s);
-    ++g_launches, k_p2m<T><<<(unsigned)P.n_leaves, p2m_threads(P), p2m_smem<T>(P), s>>>(P.leaves, P.lvl, P.first, P.cnt, pts,
-                                                                        surf, ns, u);
+    if constexpr (sizeof(T) == 4)
+        ++g_launches, k_p2m_f32<<<(unsigned)((P.n_leaves + kP2mLeaves - 1) / kP2mLeaves), p2m_threads(P),
+                                  4 * sizeof(float) * (size_t)p2m_threads(P), s>>>(P.leaves, P.n_leaves, P.lvl,
+                                                                                   P.first, P.cnt, pts, surf, ns, u);
+    else
+        ++g_launches, k_p2m<T><<<(unsigned)P.n_leaves, p2m_threads(P), p2m_smem<T>(P), s>>>(
+                          P.leaves, P.lvl, P.first, P.cnt, pts, surf, ns, u);
     stage_end(P, KIFMM_STAGE_P2M, s);
     stage_begin(P, KIFMM_STAGE_M2M, s);
     for (int l = P.max_level - 1; l >= 0; --l)
