@@ -505,6 +505,33 @@ __global__ void k_gather(int64_t max_leaves, const uint32_t *__restrict__ n_leav
     // of a domain whose corner lies far from it)
     const double C[3] = {fma((cx[b] + 0.5) * w, side, lo[0]), fma((cy[b] + 0.5) * w, side, lo[1]),
                          fma((cz[b] + 0.5) * w, side, lo[2])};
+    if constexpr (sizeof(TC) == 4 && sizeof(TI) == 4) {
+        if (cell == 0.0 && !leaf_q2) {
+            // FP32 records from FP32 inputs in FP32 arithmetic (this GPU runs
+            // FP64 at a small fraction of the FP32 rate): the centre as an
+            // unevaluated sum C_hi + C_lo of two floats, x - C_hi exact for x
+            // next to C (Sterbenz), so a record is still the caller's
+            // coordinate to about an ulp of |x|
+            float ch[3], cl[3];
+            for (int d = 0; d < 3; ++d) {
+                ch[d] = (float)C[d];
+                cl[d] = (float)(C[d] - (double)ch[d]);
+            }
+            const float is = (float)inv_side;
+            const int n = cnt[b], f = first[b];
+            for (int k = threadIdx.x & 31; k < n; k += 32) {
+                const int64_t i = f + k;
+                const uint32_t j = perm[i];
+                float4 v;
+                v.x = (xyz[3 * j] - ch[0] - cl[0]) * is;
+                v.y = (xyz[3 * j + 1] - ch[1] - cl[1]) * is;
+                v.z = (xyz[3 * j + 2] - ch[2] - cl[2]) * is;
+                v.w = q ? (float)q[j] : 0.f;
+                pts[i] = v;
+            }
+            return;
+        }
+    }
     double q2 = 0.0;  // periodic cell: sum q |x - c_cell|^2 of the leaf, root units
     for (int k = threadIdx.x & 31; k < cnt[b]; k += 32) {
         const int64_t i = first[b] + k;
