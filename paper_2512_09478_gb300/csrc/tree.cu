@@ -187,11 +187,17 @@ __global__ void k_keys(int64_t n, const T *__restrict__ xyz, const int64_t *__re
     if (i >= n) return;
     const int s = find_sys(off, S, i);
     const double sc = key_scale[s];
+    const bool wrap = cell > 0.0;
     uint64_t k[3];
     for (int d = 0; d < 3; ++d) {
-        double t = __dmul_rn(__dsub_rn(wrap_cell((double)xyz[3 * i + d], cell), lo_side[s * 4 + d]), sc);
-        double f = floor(t);
-        k[d] = (f >= 2097151.0) ? 2097151ULL : (uint64_t)(f > 0.0 ? f : 0.0);
+        // few FP64 operations (this GPU runs FP64 at a small fraction of the
+        // FP32 rate): the floor comes with the conversion to an integer and
+        // the clamp is integer arithmetic; the values equal floor() then a
+        // clamp in FP64
+        const double x = (double)xyz[3 * i + d];
+        const double t = __dmul_rn(__dsub_rn(wrap ? wrap_cell(x, cell) : x, lo_side[s * 4 + d]), sc);
+        const long long f = __double2ll_rd(t);
+        k[d] = (f >= 2097151LL) ? 2097151ULL : (uint64_t)(f > 0LL ? f : 0LL);
     }
     uint64_t key = (spread3(k[0]) << 2) | (spread3(k[1]) << 1) | spread3(k[2]);
     keys[i] = key;
@@ -495,31 +501,33 @@ __global__ void k_gather(int64_t max_leaves, const uint32_t *__restrict__ n_leav
     if (li >= max_leaves || li >= (int64_t)*n_leaves) return;
     const int b = leaves[li];
     const int s = sys[b];
-    const double side = lo_side[s * 4 + 3], inv_side = 1.0 / side;
-    const double lo[3] = {lo_side[s * 4], lo_side[s * 4 + 1], lo_side[s * 4 + 2]};
-    const double w = ldexp(1.0, -lvl[b]);
-    // the leaf centre in the caller's coordinates: the offset x - C is then
-    // exact (x lies next to C) and rounds only on the division, so a record
-    // carries the caller's coordinate to about one unit in the last place of
-    // |x|, not of |x - lo| (which is far larger for a particle near the origin
-    // of a domain whose corner lies far from it)
-    const double C[3] = {fma((cx[b] + 0.5) * w, side, lo[0]), fma((cy[b] + 0.5) * w, side, lo[1]),
-                         fma((cz[b] + 0.5) * w, side, lo[2])};
     if constexpr (sizeof(TC) == 4 && sizeof(TI) == 4) {
         if (cell == 0.0 && !leaf_q2) {
-            // FP32 records from FP32 inputs in FP32 arithmetic (this GPU runs
-            // FP64 at a small fraction of the FP32 rate): the centre as an
-            // unevaluated sum C_hi + C_lo of two floats, x - C_hi exact for x
-            // next to C (Sterbenz), so a record is still the caller's
-            // coordinate to about an ulp of |x|
-            float ch[3], cl[3];
-            for (int d = 0; d < 3; ++d) {
-                ch[d] = (float)C[d];
-                cl[d] = (float)(C[d] - (double)ch[d]);
+            // FP32 records from FP32 inputs in FP32 arithmetic: this GPU runs
+            // FP64 at a small fraction of the FP32 rate, so lane 0 alone forms
+            // the leaf centre (FP64) and hands it over as an unevaluated sum
+            // C_hi + C_lo of two floats; x - C_hi is exact for x next to C
+            // (Sterbenz), so a record is still the caller's coordinate to
+            // about an ulp of |x|
+            const int lane = threadIdx.x & 31;
+            float ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f}, is = 0.f;
+            if (lane == 0) {
+                const double side = lo_side[s * 4 + 3], w = ldexp(1.0, -lvl[b]);
+                const int c3[3] = {cx[b], cy[b], cz[b]};
+                for (int d = 0; d < 3; ++d) {
+                    const double C = fma((c3[d] + 0.5) * w, side, lo_side[s * 4 + d]);
+                    ch[d] = (float)C;
+                    cl[d] = (float)(C - (double)ch[d]);
+                }
+                is = (float)(1.0 / side);
             }
-            const float is = (float)inv_side;
+            for (int d = 0; d < 3; ++d) {
+                ch[d] = __shfl_sync(0xffffffffu, ch[d], 0);
+                cl[d] = __shfl_sync(0xffffffffu, cl[d], 0);
+            }
+            is = __shfl_sync(0xffffffffu, is, 0);
             const int n = cnt[b], f = first[b];
-            for (int k = threadIdx.x & 31; k < n; k += 32) {
+            for (int k = lane; k < n; k += 32) {
                 const int64_t i = f + k;
                 const uint32_t j = perm[i];
                 float4 v;
@@ -532,6 +540,16 @@ __global__ void k_gather(int64_t max_leaves, const uint32_t *__restrict__ n_leav
             return;
         }
     }
+    const double side = lo_side[s * 4 + 3], inv_side = 1.0 / side;
+    const double lo[3] = {lo_side[s * 4], lo_side[s * 4 + 1], lo_side[s * 4 + 2]};
+    const double w = ldexp(1.0, -lvl[b]);
+    // the leaf centre in the caller's coordinates: the offset x - C is then
+    // exact (x lies next to C) and rounds only on the division, so a record
+    // carries the caller's coordinate to about one unit in the last place of
+    // |x|, not of |x - lo| (which is far larger for a particle near the origin
+    // of a domain whose corner lies far from it)
+    const double C[3] = {fma((cx[b] + 0.5) * w, side, lo[0]), fma((cy[b] + 0.5) * w, side, lo[1]),
+                         fma((cz[b] + 0.5) * w, side, lo[2])};
     double q2 = 0.0;  // periodic cell: sum q |x - c_cell|^2 of the leaf, root units
     for (int k = threadIdx.x & 31; k < cnt[b]; k += 32) {
         const int64_t i = first[b] + k;
