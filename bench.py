@@ -66,8 +66,8 @@ _M2L_SRC = ("paper_2512_09478_gb300/csrc/m2l_tc.cu", "paper_2512_09478_gb300/csr
 _LEAF_SRC = ("paper_2512_09478_gb300/csrc/fmm.cu", "paper_2512_09478_gb300/csrc/common.cuh",
              "paper_2512_09478_gb300/csrc/internal.h")
 TRAFFIC = {
-    ("dem-coulomb-rsa-1M", "m2l"): (_M2L_SRC, "811eec91d2852c8e70e175f45b89c0a12963a333b35aa9dbd385d854ca04e138", 96832000),
-    ("dem-coulomb-rsa-1M", "p2p"): (_LEAF_SRC, "5393445c80a78139f10d581984f295835eec72249f1e50bec8c576d776f04875", 66596096),
+    ("dem-coulomb-rsa-1M", "m2l"): (_M2L_SRC, "9727e4c4a438270595210dea8fdc0b7f45a9e9693551130fc53009e1da2b0e6f", 96929024),
+    ("dem-coulomb-rsa-1M", "p2p"): (_LEAF_SRC, "22dd75aae7d96f633705cc50e80f641b77531a2937c39ea88e0d8b3789a0c83d", 66722048),
 }
 
 
