@@ -418,6 +418,17 @@ kifmm_status kifmm_get_tuning(kifmm_plan *plan, kifmm_tuning_t *out);
  * tensor-core M2L (FP64, FP32, Stokeslet).  Host only; no device work. */
 kifmm_status kifmm_set_m2l_tuning(kifmm_plan *plan, int producers, int tiles, int stages);
 
+/* Bound, in polls, of every barrier wait of the tensor-core M2L's pipeline
+ * (0: the default, about 2^24).  Every wait of that kernel is bounded: on
+ * time-out its blocks record KIFMM_ERR_TIMEOUT in the device status
+ * (kifmm_get_device_status), wait for their own copies in flight (with the
+ * default bound), free their tensor memory and return, so that the context
+ * stays usable; that evaluate's outputs are then not valid.  A tiny bound
+ * makes the waits run out on purpose (the time-out path's test).
+ * KIFMM_ERR_ARG for a negative bound or a plan without the tensor-core M2L.
+ * Host only; no device work. */
+kifmm_status kifmm_set_m2l_wait_bound(kifmm_plan *plan, int64_t polls);
+
 /* ------------------------------------------------------------------------
  * Introspection (tests and tools).  All outputs are host buffers sized by
  * the caller from kifmm_tree_info; nodes are in canonical order (system,

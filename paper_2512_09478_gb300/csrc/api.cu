@@ -574,6 +574,13 @@ kifmm_status kifmm_profile_read(kifmm_plan *pl, kifmm_profile_t *out) {
     return KIFMM_OK;
 }
 
+kifmm_status kifmm_set_m2l_wait_bound(kifmm_plan *pl, int64_t polls) {
+    if (!pl || polls < 0) return KIFMM_ERR_ARG;
+    if (pl->P.desc.precision != KIFMM_MIXED_FP16) return KIFMM_ERR_ARG;
+    pl->P.m2l_wait_polls = polls;
+    return KIFMM_OK;
+}
+
 kifmm_status kifmm_set_m2l_tuning(kifmm_plan *pl, int producers, int tiles, int stages) {
     if (!pl) return KIFMM_ERR_ARG;
     return m2l_tensor_pin(pl->P, producers, tiles, stages) ? KIFMM_OK : KIFMM_ERR_ARG;

@@ -155,6 +155,7 @@ struct Plan {
     int64_t nb = 0, n = 0;
     int n_sys = 0, max_level = 0;
     int sort_passes = 8;  // 8-bit key digits the last build sorted (from the top)
+    long long m2l_wait_polls = 0;  // tensor-core M2L barrier-wait bound (0: the default)
     // The boxes the lists were last built for: level, coordinates, parent,
     // child range and direct-sum flag per box ([8][prev_cap] int32).  A new
     // tree with the same boxes has the same lists, so set_sources keeps them.

@@ -44,6 +44,11 @@ namespace kifmm {
 namespace {
 
 constexpr int kDrainWarps = 8;
+// After a time-out the leader waits this many polls for its last bulk copy
+// to land before the block's shared memory goes away (microseconds are
+// enough; the barrier itself may never complete when other producers
+// stopped before arriving).
+constexpr long long kDrainPolls = 1LL << 18;
 constexpr int kAccBufs = 3;         // per-slot partial accumulators in TMEM
 constexpr int kKBlock = 32;         // FP16 elements per stage row (64 bytes)
 constexpr int kRowBytes = 64;
@@ -64,6 +69,7 @@ struct TileArgs {
     double *dbar;             // [nb] output column ns (the mean row), or nullptr
     int ns, kp, np, nstages;  // np: operator rows (output columns) incl. padding
     int ncb;                  // column blocks (np = ncb NT)
+    long long wait_polls;     // bound of the pipeline's barrier waits (the clean-up waits keep kWaitIters)
     int *status;
 };
 
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(tc_threads(PW, TL), 1) k_m2l_tc(TileArgs a) {
                     if (s + 1 < kVSlots) o_next = a.slot_off[cls * kVSlots + s + 1];
                 }
             }
-            if (!mbar_wait(smem_u32(&empty_bar[stage]), ((it / NS) & 1) ^ 1, &abort_s)) {
+            if (!mbar_wait(smem_u32(&empty_bar[stage]), ((it / NS) & 1) ^ 1, &abort_s, a.wait_polls)) {
                 set_status(a.status, KIFMM_ERR_TIMEOUT);
                 abort_s = 1;
                 break;
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(tc_threads(PW, TL), 1) k_m2l_tc(TileArgs a) {
             // the last bulk copy must land before the CTA's shared memory
             // goes away; the bounded wait outlasts it even when other
             // producers stopped before arriving on that stage
-            (void)mbar_wait(smem_u32(&full_bar[last_it % NS]), (last_it / NS) & 1, &abort_zero);
+            (void)mbar_wait(smem_u32(&full_bar[last_it % NS]), (last_it / NS) & 1, &abort_zero, kDrainPolls);
         }
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(tc_threads(PW, TL), 1) k_m2l_tc(TileArgs a) {
                 for (int t = 0; t < ntl; ++t) {
                     const int u = s * ntl + t, buf = u % kAccBufs;
                     if (u >= kAccBufs &&
-                        !mbar_wait(smem_u32(&accfree_bar[buf]), ((u / kAccBufs) - 1) & 1, &abort_s)) {
+                        !mbar_wait(smem_u32(&accfree_bar[buf]), ((u / kAccBufs) - 1) & 1, &abort_s, a.wait_polls)) {
                         ok = false;
                         break;
                     }
@@ -234,7 +240,7 @@ __global__ void __launch_bounds__(tc_threads(PW, TL), 1) k_m2l_tc(TileArgs a) {
                 tc_fence_after();
                 for (int kb = 0; kb < kblocks; ++kb, ++it) {
                     const int stage = it % NS;
-                    if (!mbar_wait(smem_u32(&full_bar[stage]), (it / NS) & 1, &abort_s)) {
+                    if (!mbar_wait(smem_u32(&full_bar[stage]), (it / NS) & 1, &abort_s, a.wait_polls)) {
                         set_status(a.status, KIFMM_ERR_TIMEOUT);
                         abort_s = 1;
                         break;
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(tc_threads(PW, TL), 1) k_m2l_tc(TileArgs a) {
         if (t < ntl) {
             for (int s = 0; s < kVSlots; ++s) {
                 const int u = s * ntl + t, buf = u % kAccBufs;
-                ok = mbar_wait(smem_u32(&accfull_bar[buf]), (u / kAccBufs) & 1, &abort_s);
+                ok = mbar_wait(smem_u32(&accfull_bar[buf]), (u / kAccBufs) & 1, &abort_s, a.wait_polls);
                 ok = __all_sync(0xffffffffu, ok);  // warp-uniform: tcgen05.ld is .sync.aligned
                 if (!ok) {
                     set_status(a.status, KIFMM_ERR_TIMEOUT);
@@ -672,6 +678,7 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {
     a.ul = S.ul;
     a.bhl = S.bhl;
     a.ncb = S.ncb;
+    a.wait_polls = P.m2l_wait_polls > 0 ? P.m2l_wait_polls : kWaitIters;
     a.lvl = P.lvl;
     a.level_unscale = S.level_unscale;
     a.d = comp ? (float *)P.d_c : (float *)P.d_chk;

@@ -30,9 +30,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on one mbarrier phase; false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-    for (long long i = 0; i < kWaitIters; ++i) {
+// Bounded wait on one mbarrier phase (at most `polls` polls); false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          long long polls = kWaitIters) {
+    for (long long i = 0; i < polls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
     }

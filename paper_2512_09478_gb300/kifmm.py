@@ -63,7 +63,7 @@ EXPORTS = ["kifmm_plan_create", "kifmm_plan_destroy", "kifmm_set_sources", "kifm
            "kifmm_tree_info", "kifmm_copy_keys", "kifmm_copy_tree", "kifmm_copy_list",
            "kifmm_profile_enable", "kifmm_profile_read", "kifmm_copy_expansions", "kifmm_update_sources",
            "kifmm_get_tuning", "kifmm_energy_noalloc", "kifmm_refresh_sources", "kifmm_lr_stride", "kifmm_far_image_operator",
-           "kifmm_copy_list_images", "kifmm_set_m2l_tuning"]
+           "kifmm_copy_list_images", "kifmm_set_m2l_tuning", "kifmm_set_m2l_wait_bound"]
 
 
 def load(path: str = LIB_PATH):
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
     lib.kifmm_lr_stride.argtypes = [D, D, ctypes.POINTER(I64)]
     lib.kifmm_far_image_operator.argtypes = [I, D, P]
     lib.kifmm_set_m2l_tuning.argtypes = [P, I, I, I]
+    lib.kifmm_set_m2l_wait_bound.argtypes = [P, I64]
     lib.kifmm_copy_list_images.argtypes = [P, I, P, P, P]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int if name != "kifmm_status_string" else ctypes.c_char_p
@@ -273,6 +274,10 @@ class Plan:
                 "leaf_tiles": [(t.leaf_tpl[i], t.leaf_groups[i]) for i in range(16)],
                 "m2l_ranks": (t.m2l_rank_out, t.m2l_rank_in), "m2l_producers": t.m2l_producers,
                 "m2l_tiles": t.m2l_tiles}
+
+    def set_m2l_wait_bound(self, polls: int):
+        """Bound of the tensor-core M2L's barrier waits (see kifmm_set_m2l_wait_bound)."""
+        _check(load().kifmm_set_m2l_wait_bound(self._h, polls), "kifmm_set_m2l_wait_bound")
 
     def set_m2l_tuning(self, producers: int, tiles: int, stages: int):
         """Pin the tensor-core M2L variant (see kifmm_set_m2l_tuning)."""

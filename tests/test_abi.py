@@ -103,7 +103,8 @@ def test_host_side_argument_checks():
                        ("kifmm_profile_enable", [null, 1]),
                        ("kifmm_tree_info", [null, None]),
                        ("kifmm_copy_list", [null, 0, buf, None]),
-                       ("kifmm_set_m2l_tuning", [null, 2, 1, 4])]:
+                       ("kifmm_set_m2l_tuning", [null, 2, 1, 4]),
+                       ("kifmm_set_m2l_wait_bound", [null, C.c_int64(1)])]:
         assert getattr(lib, name)(*args) == 1, name
     names = {k: lib.kifmm_status_string(k).decode() for k in range(7)}
     assert names[0] == "ok" and names[1] == "invalid argument" and names[6] == "call out of order"

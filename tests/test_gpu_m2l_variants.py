@@ -69,3 +69,35 @@ def test_pinning_checks_its_arguments():
                      dtype=torch.float64 if prec == "fp64" else torch.float32)
         with pytest.raises(KifmmError):
             other.set_m2l_tuning(2, 1, 4)
+
+
+def test_bounded_waits_time_out_and_the_plan_recovers():
+    """The tensor-core M2L's barrier waits are bounded.  With a bound of one
+    poll they run out on purpose: the kernel returns, the device status reads
+    KIFMM_ERR_TIMEOUT, and with the default bound restored the same plan's
+    next evaluate equals a fresh plan's bit for bit (the context stays
+    usable; tensor memory was freed)."""
+    from paper_2512_09478_gb300 import KifmmError, Plan
+    x, q = G.uniform_charges(20000, 41)
+    x = x.astype(np.float32).astype(np.float64)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    qt = torch.tensor(q, dtype=torch.float32, device="cuda")
+    mk = lambda: Plan(p=4, leaf_cap=32, max_depth=20, precision="mixed_fp16", n_max=len(x), dtype=torch.float32)
+    plan = mk()
+    plan.set_sources(xt, qt)
+    plan.set_m2l_wait_bound(1)
+    plan.evaluate()
+    torch.cuda.synchronize()
+    assert plan.device_status() == 5          # KIFMM_ERR_TIMEOUT
+    plan.set_m2l_wait_bound(0)
+    pot, grad, _ = plan.evaluate()
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    fresh = mk()
+    fresh.set_sources(xt, qt)
+    pf, gf, _ = fresh.evaluate()
+    assert torch.equal(pot, pf) and torch.equal(grad, gf)
+    with pytest.raises(KifmmError):
+        plan.set_m2l_wait_bound(-1)
+    with pytest.raises(KifmmError):
+        Plan(p=4, leaf_cap=32, n_max=100, precision="fp32").set_m2l_wait_bound(1)
