@@ -66,8 +66,8 @@ _M2L_SRC = ("paper_2512_09478_gb300/csrc/m2l_tc.cu", "paper_2512_09478_gb300/csr
 _LEAF_SRC = ("paper_2512_09478_gb300/csrc/fmm.cu", "paper_2512_09478_gb300/csrc/common.cuh",
              "paper_2512_09478_gb300/csrc/internal.h")
 TRAFFIC = {
-    ("dem-coulomb-rsa-1M", "m2l"): (_M2L_SRC, "9727e4c4a438270595210dea8fdc0b7f45a9e9693551130fc53009e1da2b0e6f", 96929024),
-    ("dem-coulomb-rsa-1M", "p2p"): (_LEAF_SRC, "22dd75aae7d96f633705cc50e80f641b77531a2937c39ea88e0d8b3789a0c83d", 66722048),
+    ("dem-coulomb-rsa-1M", "m2l"): (_M2L_SRC, "feb3e37c924e51871e98a1b5331a2f163353762589066b6a0ee6904987129fe4", 95317248),
+    ("dem-coulomb-rsa-1M", "p2p"): (_LEAF_SRC, "c8e01d3a8668b09082bfecaa4c32acf9f6f66a78e23b4bd8158aa4bbf50118b9", 66681344),
 }
 
 

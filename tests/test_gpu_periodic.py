@@ -150,3 +150,26 @@ def test_periodic_reduced_precision_vs_ewald(precision):
     print("periodic %s vs Ewald: grad %.2e (fp64 method %.2e), pot-mean %.2e (%.2e)" % (precision, e_g, e_go, e_p, e_po))
     assert e_g <= 1.1 * e_go + 1e-6
     assert e_p <= 1.1 * e_po + 1e-6
+
+
+def test_periodic_lists_kept_with_reuse_lists():
+    """A periodic plan with reuse_lists keeps its image-shifted lists for a
+    tree with the same boxes; its lists and outputs equal those of a plan that
+    builds them every time and runs the same calls."""
+    from paper_2512_09478_gb300 import Plan
+    x, q = _neutral(1200, 12)
+    jitter = np.random.default_rng(13).uniform(-1e-9, 1e-9, size=x.shape)
+    mk = lambda reuse: Plan(p=4, leaf_cap=16, max_depth=20, precision="fp64", n_max=len(x), dtype=torch.float64,
+                            cell=1.0, direct_max=-1, reuse_lists=reuse)
+    plain, plan = mk(False), mk(True)
+    for xs, reused in ((x, 0), (np.mod(x + jitter, 1.0), 1)):
+        for pl in (plain, plan):
+            pl.set_sources(_dev(xs), _dev(q))
+        assert plan.tree_info()["lists_reused"] == reused
+        pot, grad, _ = plan.evaluate()
+        pp, gp, _ = plain.evaluate()
+        assert torch.equal(pot, pp) and torch.equal(grad, gp)
+        for kind in "UVWX":
+            a, b = plan.list_images(kind), plain.list_images(kind)
+            assert all(np.array_equal(u, v) for u, v in zip(a, b)), kind
+    assert plan.device_status() == 0

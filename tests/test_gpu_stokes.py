@@ -128,3 +128,23 @@ def test_stokes_refuses_what_it_does_not_support():
     with pytest.raises(KifmmError) as e:
         plan.backward(torch.ones(200, dtype=torch.float64, device="cuda"), u)
     assert e.value.code == 1
+
+
+def test_stokes_lists_kept_with_reuse_lists():
+    """A Stokeslet plan with reuse_lists keeps its lists for a tree with the
+    same boxes; its velocities equal those of a plan that builds them every
+    time and runs the same calls, bit for bit."""
+    from paper_2512_09478_gb300 import Plan
+    x, f = CASES["uniform"](1500)
+    jitter = np.random.default_rng(14).uniform(-1e-9, 1e-9, size=x.shape)
+    mk = lambda reuse: Plan(p=4, leaf_cap=32, max_depth=20, precision="fp64", n_max=len(x), dtype=torch.float64,
+                            kernel="stokeslet", reuse_lists=reuse)
+    plain, plan = mk(False), mk(True)
+    for xs, reused in ((x, 0), (x + jitter, 1)):
+        for pl in (plain, plan):
+            pl.set_sources(_dev(xs), _dev(f))
+        assert plan.tree_info()["lists_reused"] == reused
+        u, _, _ = plan.evaluate()
+        up, _, _ = plain.evaluate()
+        assert torch.equal(u, up)
+    assert plan.device_status() == 0
