@@ -447,3 +447,55 @@ def test_autotune_keeps_results(prec):
         out.append((pot2.double().cpu().numpy(), grad2.double().cpu().numpy()))
     tol = 1e-12 if prec == "fp64" else 1e-6
     assert O.rel_l2(out[1][0], out[0][0]) < tol and O.rel_l2(out[1][1], out[0][1]) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed_fp16"])
+def test_degenerate_inputs_reduced_precision(prec):
+    """The FP32-based paths (FP32 records, packed P2M, vector-tiled and
+    tensor-core contractions) on the degenerate cases: one particle (zero
+    field), two particles (the direct sum), coincident points (zero field),
+    a cloud held in one leaf (the direct sum), and a batch whose systems
+    hold one, two and many particles (each system on its own)."""
+    f32 = torch.float32
+    tol, gtol = 2e-6, 1e-5   # FP32 records and the hardware reciprocal square root
+    plan = _plan(np.zeros((1, 3)), precision=prec, M=4, p=6, dtype=f32)
+    plan.set_sources(_dev([[0.3, 0.2, 0.1]], f32), _dev([2.0], f32))
+    pot, grad, _ = plan.evaluate()
+    assert pot.item() == 0.0 and torch.all(grad == 0)
+    x = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    q = np.array([1.0, 2.0])
+    plan = _plan(x, precision=prec, M=1, p=6, dtype=f32)
+    plan.set_sources(_dev(x, f32), _dev(q, f32))
+    pot, grad, _ = plan.evaluate()
+    pd, gd = O.direct(x, q)
+    assert O.rel_l2(pot.double().cpu().numpy(), pd) <= tol and O.rel_l2(grad.double().cpu().numpy(), gd) <= gtol
+    x = np.ones((50, 3)) * 0.5
+    plan = _plan(x, precision=prec, M=4, D=3, p=6, dtype=f32)
+    plan.set_sources(_dev(x, f32), _dev(np.ones(50), f32))
+    pot, grad, _ = plan.evaluate()
+    assert torch.all(pot == 0) and torch.all(grad == 0)
+    x, q = G.uniform_charges(200, 17)
+    x32, q32 = x.astype(np.float32).astype(np.float64), q.astype(np.float32).astype(np.float64)
+    plan = _plan(x, precision=prec, M=256, p=6, dtype=f32)
+    plan.set_sources(_dev(x32, f32), _dev(q32, f32))
+    pot, grad, _ = plan.evaluate()
+    assert plan.tree_info()["n_boxes"] == 1
+    pd, gd = O.direct(x32, q32)
+    assert O.rel_l2(pot.double().cpu().numpy(), pd) <= tol and O.rel_l2(grad.double().cpu().numpy(), gd) <= gtol
+    # a batch of one, two and 3000 particles
+    xs = [np.array([[0.5, 0.5, 0.5]]), np.array([[0.0, 0.0, 0.0], [0.0, 2.0, 0.0]]), G.uniform_charges(3000, 18)[0]]
+    qs = [np.array([1.0]), np.array([1.0, -1.0]), G.uniform_charges(3000, 18)[1]]
+    X = np.concatenate(xs).astype(np.float32).astype(np.float64)
+    Q = np.concatenate(qs).astype(np.float32).astype(np.float64)
+    off = [0, 1, 3, len(X)]
+    plan = _plan(X, precision=prec, M=32, p=6, dtype=f32, n_systems=3)
+    plan.set_sources(_dev(X, f32), _dev(Q, f32), sys_offsets=off)
+    pot, grad, _ = plan.evaluate()
+    assert plan.device_status() == 0
+    pot, grad = pot.double().cpu().numpy(), grad.double().cpu().numpy()
+    assert pot[0] == 0.0 and np.all(grad[0] == 0.0)
+    for s in (1, 2):
+        sl = slice(off[s], off[s + 1])
+        pd, gd = O.direct(X[sl], Q[sl])
+        bound = (tol, gtol) if s == 1 else (5e-5, 5e-5)   # 3000 particles: within the p = 6 method's own error
+        assert O.rel_l2(pot[sl], pd) <= bound[0] and O.rel_l2(grad[sl], gd) <= bound[1], s
