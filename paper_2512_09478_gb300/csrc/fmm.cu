@@ -467,11 +467,14 @@ __global__ void __launch_bounds__(32 * NTY, (sizeof(T) == 4 && NTY == 8 && !MULT
 // bit for bit.  VEC: the input rows are 16-byte aligned (n_s a multiple of 4)
 // and are read as float4.
 constexpr int kV4Threads = 320;
-template <class G, bool MULTI, bool VEC>
+// SPLIT: blockIdx.z = slot * ncb + column block, the slot's partial product
+// to part ([slot][target position][ld]) as in the scalar tile's split form.
+template <class G, bool MULTI, bool VEC, bool SPLIT = false>
 __global__ void __launch_bounds__(kV4Threads, 2) k_ggemm_v4(G g, const int32_t *__restrict__ targets,
                                                             ClassRanges cr, int nslots, int ns, int ld,
                                                             const float *__restrict__ in, float *__restrict__ out,
-                                                            int accumulate, double *dbar) {
+                                                            int accumulate, double *dbar, int ncb = 1,
+                                                            float *__restrict__ part = nullptr) {
     constexpr int TT = 64, TJ = 160;
     __shared__ __align__(16) float Us[kGK][TT];
     __shared__ __align__(16) float Ms[kGK][TJ];
@@ -480,7 +483,8 @@ __global__ void __launch_bounds__(kV4Threads, 2) k_ggemm_v4(G g, const int32_t *
     const int tid = threadIdx.x;
     const int tn = tid % 40, tm = tid / 40;
     const int cls = blockIdx.y;
-    const int j0 = (int)blockIdx.z * TJ;
+    const int j0 = (SPLIT ? (int)blockIdx.z % ncb : (int)blockIdx.z) * TJ;
+    const int s_lo = SPLIT ? (int)blockIdx.z / ncb : 0, s_hi = SPLIT ? s_lo + 1 : nslots;
     int64_t t_begin = 0, t_end = 0;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(kV4Threads, 2) k_ggemm_v4(G g, const int32_t *
         for (int c = 0; c < 4; ++c) acc[a][c] = run[a][c] = 0.f;
     const int nk = (ns + kGK - 1) / kGK;
     __syncthreads();
-    for (int s = 0; s < nslots; ++s) {
+    for (int s = s_lo; s < s_hi; ++s) {
         if (tid < TT) {
             const int32_t t = tgt[tid];
             src[tid] = (t >= 0) ? g.src(t, s, cls) : -1;
@@ -583,7 +587,11 @@ __global__ void __launch_bounds__(kV4Threads, 2) k_ggemm_v4(G g, const int32_t *
         for (int c = 0; c < 4; ++c) {
             const int j = j0 + 4 * tn + c;
             const float v = MULTI ? run[a][c] : acc[a][c];
-            if (j < ns) {
+            if constexpr (SPLIT) {
+                if (j < ld)
+                    part[((size_t)s_lo * (size_t)(cr.b[gridDim.y] - cr.b[0]) + (size_t)(t0 + 8 * tm + a - cr.b[0])) *
+                             ld + j] = v;
+            } else if (j < ns) {
                 float *o = out + (size_t)t * ns + j;
                 *o = accumulate ? *o + v : v;
             } else if (j == ns && dbar) {
@@ -1265,8 +1273,18 @@ void ggemm_classes(Plan &P, const G &g, const int32_t *targets, const int64_t *s
         T *part = (T *)P.gemm_part;
         const int ncb_big = (int)grid_for(ld, 160);
         dim3 grid(grid_for(most, 64), ncls, ncb_big * nslots);
-        ++g_launches, k_ggemm<T, G, 8, 8, 5, true, false><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld, in,
-                                                                                out, accumulate, dbar, ncb_big, part);
+        if constexpr (sizeof(T) == 4) {
+            if (P.ns % 4 == 0)
+                ++g_launches, k_ggemm_v4<G, false, true, true><<<grid, kV4Threads, 0, s>>>(
+                                  g, targets, cr, nslots, P.ns, ld, in, out, accumulate, dbar, ncb_big, part);
+            else
+                ++g_launches, k_ggemm_v4<G, false, false, true><<<grid, kV4Threads, 0, s>>>(
+                                  g, targets, cr, nslots, P.ns, ld, in, out, accumulate, dbar, ncb_big, part);
+        } else {
+            ++g_launches, k_ggemm<T, G, 8, 8, 5, true, false><<<grid, 256, 0, s>>>(g, targets, cr, nslots, P.ns, ld,
+                                                                                    in, out, accumulate, dbar,
+                                                                                    ncb_big, part);
+        }
         ++g_launches, k_ggemm_sum<T, G><<<grid_for(total * ld, 256), 256, 0, s>>>(
                           g, targets, cr.b[0], total, nslots, P.ns, ld, part, out, accumulate, dbar);
         return;
