@@ -243,8 +243,10 @@ struct Plan {
     // ---- status ----
     int *status = nullptr;   // device status word
     int *moved = nullptr;    // device flag of the tree reuse test
-    int64_t *spec_buf = nullptr;  // [32] speculative octree build: level boundaries
-    int *spec_fail = nullptr;     // a level outgrew the grid the host sized for it
+    int64_t *spec_buf = nullptr;  // [32] all-levels octree build: level boundaries
+    int *spec_fail = nullptr;     // the speculative build outgrew the box arrays
+    uint32_t *os_cnt = nullptr;   // [levels][particle tiles] box counts, then box offsets
+    size_t os_cnt_elems = 0;
     cudaStream_t last_stream = nullptr;
     bool has_sources = false;
 

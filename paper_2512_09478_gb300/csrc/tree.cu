@@ -385,24 +385,14 @@ __global__ void k_roots(int S, const int64_t *off, int32_t *lvl, int32_t *cx, in
 // non-empty octants if it splits (count > M and level < max depth).
 // One warp per node; lanes 0..7 search in parallel for the end of octant o
 // (first index in the node's range whose digit exceeds o).
-// Nodes [ls, le) of one level, or, with `range`, the device-held range of a
-// level built without a host round trip; m_ub bounds the node count (the
-// grid covers m_ub warps; nodes past le report no children).
-__global__ void k_split(int64_t ls, int64_t le, const int64_t *range, int64_t m_ub, int level, int leaf_cap,
-                        int max_depth, const uint64_t *__restrict__ keys, const int32_t *__restrict__ first,
+// Nodes [ls, le) of one level.
+__global__ void k_split(int64_t ls, int64_t le, int level, int leaf_cap, int max_depth,
+                        const uint64_t *__restrict__ keys, const int32_t *__restrict__ first,
                         const int32_t *__restrict__ cnt, uint32_t *nchild_tmp, int32_t *rng) {
-    if (range) {
-        ls = range[0];
-        le = range[1];
-    }
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (j >= m_ub) return;
     const int64_t b = ls + j;
-    if (b >= le) {
-        if (lane == 0) nchild_tmp[j] = 0u;
-        return;
-    }
+    if (b >= le) return;
     const bool split = cnt[b] > leaf_cap && level < max_depth;
     int64_t end = 0;
     const int64_t lo0 = first[b], hi0 = lo0 + cnt[b];
@@ -425,26 +415,13 @@ __global__ void k_split(int64_t ls, int64_t le, const int64_t *range, int64_t m_
     if (lane == 0) nchild_tmp[j] = split ? (uint32_t)__popc(nonempty) : 0u;
 }
 
-// With `range` (the level's boundaries range[0], range[1]), one thread also
-// records the next level's end range[2] = le + children and flags a count
-// above m_ub_next (the grid the host sized for that level).
-__global__ void k_emit(int64_t ls, int64_t le, int64_t *range, int64_t m_ub,
-                       const uint32_t *__restrict__ nchild_tmp, const uint32_t *__restrict__ nchild_scan,
-                       const int32_t *__restrict__ rng, int32_t *lvl, int32_t *cx, int32_t *cy, int32_t *cz,
-                       int32_t *first, int32_t *cnt, int32_t *parent, int32_t *child_first, int32_t *nchild,
-                       int32_t *sys, int64_t cap, int *status, const uint32_t *children, int64_t m_ub_next,
-                       int *fail) {
-    if (range) {
-        ls = range[0];
-        le = range[1];
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            const int64_t next = le + (int64_t)*children;
-            range[2] = next;
-            if (next - le > m_ub_next) *fail = 1;
-        }
-    }
+// The children of the nodes [ls, le) of one level, numbered from le on in
+// node order (the scan of the child counts) and octant order.
+__global__ void k_emit(int64_t ls, int64_t le, const uint32_t *__restrict__ nchild_tmp,
+                       const uint32_t *__restrict__ nchild_scan, const int32_t *__restrict__ rng, int32_t *lvl,
+                       int32_t *cx, int32_t *cy, int32_t *cz, int32_t *first, int32_t *cnt, int32_t *parent,
+                       int32_t *child_first, int32_t *nchild, int32_t *sys, int64_t cap, int *status) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m_ub) return;
     const int64_t b = ls + j;
     if (b >= le) return;
     const uint32_t nc = nchild_tmp[j];
@@ -475,17 +452,253 @@ __global__ void k_emit(int64_t ls, int64_t le, int64_t *range, int64_t m_ub,
     }
 }
 
-// Device-side level boundaries of the speculative build: level 0 holds the S roots.
-__global__ void k_spec_init(int64_t *level_start, int S, int *fail) {
-    if (threadIdx.x == 0) {
-        level_start[0] = 0;
-        level_start[1] = S;
-        *fail = 0;
+// ---------------------------------------------------------------------------
+// Every level of the octree at once, from the sorted keys (the levels the
+// last tree had).  A box of level l >= 1 is a particle i that starts a level-l
+// key prefix (or its system's range) inside a level-(l-1) key segment of more
+// than M particles, with l - 1 below the maximum depth.  Segment counts only
+// shrink with the level, so every ancestor of that segment splits as well:
+// the box exists with no further look up the tree.  Boxes are numbered level
+// by level and, within a level, in particle order: the order of the
+// level-by-level build (children grouped by parent, in octant order).
+// Passes: counts per (level, particle tile); one block scans them into box
+// offsets and level boundaries; the emit pass writes each box's own fields;
+// the link pass finds parents and child ranges by binary search over the
+// first particles of the neighbouring levels.
+// ---------------------------------------------------------------------------
+constexpr int kOsPer = 16;                 // particles per thread
+constexpr int kOsTile = kBlock * kOsPer;   // particles per block
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {  // inverse of spread3
+    x &= 0x1249249249249249ULL;
+    x = (x | (x >> 2)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x >> 4)) & 0x100f00f00f00f00fULL;
+    x = (x | (x >> 8)) & 0x1f0000ff0000ffULL;
+    x = (x | (x >> 16)) & 0x1f00000000ffffULL;
+    x = (x | (x >> 32)) & 0x1fffffULL;
+    return (uint32_t)x;
+}
+
+// Shift of the level-l key prefix (the l leading octant digits).
+__device__ __forceinline__ int prefix_shift(int l) { return 3 * (kMaxLevel + 1 - l); }
+
+// Whether the level-(l-1) segment holding particle i (system range [s0, s1))
+// has more than M particles: its start a is found within M places below i
+// (or the segment already holds i - M .. i), then particle a + M decides.
+__device__ __forceinline__ bool os_parent_splits(const uint64_t *__restrict__ keys, int64_t i, int64_t s0,
+                                                 int64_t s1, int l, int M) {
+    if (l == 1) return s1 - s0 > M;  // the parent is the root
+    const int sh = prefix_shift(l - 1);
+    const uint64_t pp = keys[i] >> sh;
+    int64_t lo = max(s0, i - (int64_t)M), a;
+    if ((keys[lo] >> sh) == pp) {
+        if (i - lo >= M) return true;
+        a = lo;  // lo is the system's first particle
+    } else {
+        int64_t hi = i;  // keys[lo] outside the segment, keys[hi] inside
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((keys[mid] >> sh) == pp) hi = mid; else lo = mid;
+        }
+        a = hi;
+    }
+    const int64_t j = a + M;
+    return j < s1 && (keys[j] >> sh) == pp;
+}
+
+// Box flags of level l for the thread's particles i0 .. i0 + kOsPer - 1
+// (kp[e + 1] = keys[i0 + e], kp[0] = keys[i0 - 1]); bit e set if particle
+// i0 + e is a box of level l.
+__device__ __forceinline__ uint32_t os_flags(const uint64_t *__restrict__ keys, const uint64_t (&kp)[kOsPer + 1],
+                                             int64_t n, int64_t i0, const int64_t *__restrict__ off, int sy0,
+                                             int l, int M, int max_depth) {
+    if (l - 1 >= max_depth) return 0u;
+    const int sh = prefix_shift(l);
+    uint32_t f = 0;
+    int sy = sy0;
+#pragma unroll
+    for (int e = 0; e < kOsPer; ++e) {
+        const int64_t i = i0 + e;
+        if (i >= n) break;
+        while (i >= off[sy + 1]) ++sy;
+        const int64_t s0 = off[sy];
+        if (i > s0 && (kp[e + 1] >> sh) == (kp[e] >> sh)) continue;  // not a segment start
+        if (os_parent_splits(keys, i, s0, off[sy + 1], l, M)) f |= 1u << e;
+    }
+    return f;
+}
+
+__device__ __forceinline__ void os_load(const uint64_t *__restrict__ keys, int64_t n, int64_t i0,
+                                        uint64_t (&kp)[kOsPer + 1]) {
+    kp[0] = (i0 > 0 && i0 <= n) ? keys[i0 - 1] : 0ull;
+#pragma unroll
+    for (int e = 0; e < kOsPer; ++e) kp[e + 1] = (i0 + e < n) ? keys[i0 + e] : 0ull;
+}
+
+// Block-wide exclusive scan of one value per thread; *total gets the sum.
+__device__ __forceinline__ uint32_t os_block_scan(uint32_t v, uint32_t *ws, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();  // ws free from any previous use
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, tot = 0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+        before += (w < warp) ? ws[w] : 0u;
+        tot += ws[w];
+    }
+    *total = tot;
+    return before + x - v;
+}
+
+// Pass 1: boxes of levels 1 .. L per particle tile -> cnt[(l - 1) ntiles + tile].
+__global__ void __launch_bounds__(kBlock) k_os_count(int64_t n, const uint64_t *__restrict__ keys,
+                                                     const int64_t *__restrict__ off, int S, int L, int M,
+                                                     int max_depth, int ntiles, uint32_t *cnt) {
+    __shared__ uint32_t ws[kBlock / 32];
+    const int64_t i0 = (int64_t)blockIdx.x * kOsTile + (int64_t)threadIdx.x * kOsPer;
+    uint64_t kp[kOsPer + 1];
+    os_load(keys, n, i0, kp);
+    const int sy0 = i0 < n ? find_sys(off, S, i0) : 0;
+    for (int l = 1; l <= L; ++l) {
+        const uint32_t f = i0 < n ? os_flags(keys, kp, n, i0, off, sy0, l, M, max_depth) : 0u;
+        uint32_t tot;
+        (void)os_block_scan((uint32_t)__popc(f), ws, &tot);
+        if (threadIdx.x == 0) cnt[(size_t)(l - 1) * ntiles + blockIdx.x] = tot;
     }
 }
 
-// Leaf-relative particle records {x - c_leaf, y - c_leaf, z - c_leaf, q} in
-// root-normalised units (root side = 1), computed in FP64.
+// Pass 2 (one block): the counts become first box indices in place, level
+// boundaries go to lb[0 .. L + 1] (level 0: the S roots), and fail is set
+// when the boxes outgrow the arrays (then nothing else is written).
+__global__ void __launch_bounds__(1024) k_os_scan(int L, int ntiles, int S, int64_t cap, uint32_t *cnt, int64_t *lb,
+                                                  int *fail) {
+    __shared__ uint32_t ws[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t carry = S;
+    for (int l = 0; l < L; ++l) {
+        uint32_t *c = cnt + (size_t)l * ntiles;
+        for (int c0 = 0; c0 < ntiles; c0 += 1024) {
+            const int t = c0 + threadIdx.x;
+            const uint32_t v = t < ntiles ? c[t] : 0u;
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            __syncthreads();
+            if (lane == 31) ws[warp] = x;
+            __syncthreads();
+            uint32_t before = 0, tot = 0;
+            for (int w = 0; w < 32; ++w) {
+                before += (w < warp) ? ws[w] : 0u;
+                tot += ws[w];
+            }
+            if (t < ntiles) c[t] = (uint32_t)(carry + before + x - v);
+            carry += tot;
+        }
+        if (threadIdx.x == 0) lb[l + 2] = carry;
+    }
+    if (threadIdx.x == 0) {
+        lb[0] = 0;
+        lb[1] = S;
+        *fail = carry > cap || carry > (int64_t)INT32_MAX;
+    }
+}
+
+// Pass 3: each box's level, coordinates, particle range and system.
+__global__ void __launch_bounds__(kBlock) k_os_emit(int64_t n, const uint64_t *__restrict__ keys,
+                                                    const int64_t *__restrict__ off, int S, int L, int M,
+                                                    int max_depth, int ntiles, const uint32_t *__restrict__ base,
+                                                    const int *fail, int32_t *lvl, int32_t *cx, int32_t *cy,
+                                                    int32_t *cz, int32_t *first, int32_t *cnt, int32_t *sys) {
+    __shared__ uint32_t ws[kBlock / 32];
+    if (*fail) return;
+    const int64_t i0 = (int64_t)blockIdx.x * kOsTile + (int64_t)threadIdx.x * kOsPer;
+    uint64_t kp[kOsPer + 1];
+    os_load(keys, n, i0, kp);
+    const int sy0 = i0 < n ? find_sys(off, S, i0) : 0;
+    for (int l = 1; l <= L; ++l) {
+        uint32_t f = i0 < n ? os_flags(keys, kp, n, i0, off, sy0, l, M, max_depth) : 0u;
+        uint32_t tot;
+        int64_t b = (int64_t)base[(size_t)(l - 1) * ntiles + blockIdx.x] + os_block_scan((uint32_t)__popc(f), ws, &tot);
+        const int sh = prefix_shift(l);
+        int sy = sy0;
+        while (f) {
+            const int e = __ffs(f) - 1;
+            f &= f - 1;
+            const int64_t i = i0 + e;
+            while (i >= off[sy + 1]) ++sy;
+            const uint64_t p = keys[i] >> sh;  // (not kp[e + 1]: a dynamic index would spill kp)
+            // the segment's end: doubling steps, then bisection
+            const int64_t s1 = off[sy + 1];
+            int64_t lo = i, hi, step = 1;
+            while (true) {
+                hi = lo + step;
+                if (hi >= s1) {
+                    hi = s1;
+                    break;
+                }
+                if ((keys[hi] >> sh) != p) break;
+                lo = hi;
+                step <<= 1;
+            }
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) >> 1;
+                if ((keys[mid] >> sh) == p) lo = mid; else hi = mid;
+            }
+            lvl[b] = l;
+            cx[b] = (int32_t)compact3(p >> 2);
+            cy[b] = (int32_t)compact3(p >> 1);
+            cz[b] = (int32_t)compact3(p);
+            first[b] = (int32_t)i;
+            cnt[b] = (int32_t)(hi - i);
+            sys[b] = sy;
+            ++b;
+        }
+    }
+}
+
+// Index in [lo, hi) of the last a[k] <= x (lo - 1 if none).
+__device__ __forceinline__ int64_t last_le(const int32_t *__restrict__ a, int64_t lo, int64_t hi, int32_t x) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo - 1;
+}
+
+// Pass 4: parents (the last box of the level above whose first particle is
+// at or before the box's) and child ranges (the boxes of the level below
+// whose first particle lies in the box's range); the boxes of level L get
+// none here (the level-by-level build continues from them if one splits).
+__global__ void k_os_link(const int64_t *__restrict__ lb, int L, int M, int max_depth, const int *fail,
+                          const int32_t *__restrict__ lvl, const int32_t *__restrict__ first,
+                          const int32_t *__restrict__ cnt, int32_t *parent, int32_t *child_first, int32_t *nchild) {
+    if (*fail) return;
+    const int64_t nb = lb[L + 1];
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        const int l = lvl[b];
+        const int32_t f = first[b], c = cnt[b];
+        if (l >= 1) parent[b] = (int32_t)last_le(first, lb[l - 1], lb[l], f);
+        if (l < L && l < max_depth && c > M) {
+            const int64_t c0 = last_le(first, lb[l + 1], lb[l + 2], f - 1) + 1;
+            const int64_t c1 = last_le(first, lb[l + 1], lb[l + 2], f + c - 1) + 1;
+            child_first[b] = (int32_t)c0;
+            nchild[b] = (int32_t)(c1 - c0);
+        } else {
+            child_first[b] = -1;
+            nchild[b] = 0;
+        }
+    }
+}
+
 template <typename TI, typename TC>
 __global__ void k_gather(int64_t max_leaves, const uint32_t *__restrict__ n_leaves,
                          const int32_t *__restrict__ leaves, const int32_t *__restrict__ first,
@@ -634,17 +847,39 @@ __device__ __forceinline__ bool adjacent_img(int la, int ax, int ay, int az, int
     return boxes_adjacent(la, ax + ox, ay + oy, az + oz, lb, bx, by, bz);
 }
 
-// One warp per box: lane k < 27 scans the children of the parent's colleague
-// k (in that colleague's image); every child adjacent to (or equal to) b
-// lands in its own slot.  In a periodic cell the root's colleagues are its 27
-// images (itself included).
-__device__ __forceinline__ void dev_colleagues(int64_t b, int lane, int level, const int32_t *__restrict__ parent,
-                                               const int32_t *__restrict__ child_first,
-                                               const int32_t *__restrict__ nchild, const int32_t *__restrict__ cx,
-                                               const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
-                                               int32_t *coll, const ListShifts &sh) {
+// slot of offset d for octant class (ox,oy,oz): components range over
+// [-2-o, 3-o]; the inner [-1,1]^3 is excluded.
+// Closed form: lexicographic index in the 6^3 window minus the excluded inner
+// 3^3 cells (at window offset 1 + o per axis) that precede it.
+__device__ __forceinline__ int v_slot(int ox, int oy, int oz, int dx, int dy, int dz) {
+    const int a = dx + 2 + ox, b = dy + 2 + oy, c = dz + 2 + oz;  // 0..5
+    if (a < 0 || a > 5 || b < 0 || b > 5 || c < 0 || c > 5) return -1;
+    const int a0 = 1 + ox, b0 = 1 + oy, c0 = 1 + oz;
+    const bool ina = a >= a0 && a < a0 + 3, inb = b >= b0 && b < b0 + 3, inc = c >= c0 && c < c0 + 3;
+    if (ina && inb && inc) return -1;
+    int before = min(max(a - a0, 0), 3) * 9;
+    if (ina) {
+        before += min(max(b - b0, 0), 3) * 3;
+        if (inb) before += min(max(c - c0, 0), 3);
+    }
+    return a * 36 + b * 6 + c - before;
+}
+
+// Colleagues and V list of b in one pass.  One warp per box: lane k < 27
+// scans the children of the parent's colleague k (in that colleague's
+// image); a child adjacent to (or equal to) b lands in its colleague slot,
+// any other in its slot of b's octant-class table (V: children of the
+// parent's colleagues not adjacent to b; each child has its own slot, and a
+// slot fixes the source's offset, so the table needs no image shift).  In a
+// periodic cell the root's colleagues are its 27 images (itself included).
+// Returns the V count (the same on every lane).
+__device__ __forceinline__ int dev_colleagues_v(int64_t b, int lane, int level, const int32_t *__restrict__ parent,
+                                                const int32_t *__restrict__ child_first,
+                                                const int32_t *__restrict__ nchild, const int32_t *__restrict__ cx,
+                                                const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
+                                                int32_t *coll, int32_t *vdense, const ListShifts &sh) {
     int32_t *cb = coll + b * kColl;
-    // cb was set to -1 by a memset of the whole array before the first level
+    // cb and the V table were set to -1 by memsets of the whole arrays
     if (level == 0) {
         if (sh.coll) {
             if (lane < kColl) {
@@ -654,22 +889,34 @@ __device__ __forceinline__ void dev_colleagues(int64_t b, int lane, int level, c
         } else if (lane == 0) {
             cb[13] = (int32_t)b;
         }
-        return;
+        return 0;
     }
-    if (lane >= kColl) return;
-    const int32_t c = coll[(int64_t)parent[b] * kColl + lane];
-    if (c < 0) return;
-    const int sc = shift_of(sh.coll, (int64_t)parent[b] * kColl + lane);
-    int ox, oy, oz;
-    shift_boxes(sc, level, ox, oy, oz);
-    const int bx = cx[b], by = cy[b], bz = cz[b];
-    for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
-        const int dx = cx[ch] + ox - bx, dy = cy[ch] + oy - by, dz = cz[ch] + oz - bz;
-        if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
-        const int slot = (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
-        cb[slot] = ch;
-        if (sh.coll) sh.coll[b * kColl + slot] = (int8_t)sc;
+    int cntv = 0;
+    const int32_t c = (lane < kColl) ? coll[(int64_t)parent[b] * kColl + lane] : -1;
+    if (c >= 0) {
+        const int sc = shift_of(sh.coll, (int64_t)parent[b] * kColl + lane);
+        int ox, oy, oz;
+        shift_boxes(sc, level, ox, oy, oz);
+        const int bx = cx[b], by = cy[b], bz = cz[b];
+        const int px = bx & 1, py = by & 1, pz = bz & 1;
+        int32_t *vb = vdense + b * kVSlots;
+        for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
+            const int dx = cx[ch] + ox - bx, dy = cy[ch] + oy - by, dz = cz[ch] + oz - bz;
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) {
+                const int slot = (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
+                cb[slot] = ch;
+                if (sh.coll) sh.coll[b * kColl + slot] = (int8_t)sc;
+            } else {
+                const int sl = v_slot(px, py, pz, dx, dy, dz);
+                if (sl < 0) continue;  // unreachable: children of parent colleagues lie in the class window
+                vb[sl] = ch;
+                ++cntv;
+            }
+        }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cntv += __shfl_xor_sync(0xffffffffu, cntv, o);
+    return cntv;
 }
 
 // Coarser-or-equal-level leaves adjacent to b: those of the parent that touch
@@ -731,86 +978,40 @@ __device__ __forceinline__ void dev_coarse(int64_t b, int lane, int level, const
     }
 }
 
-// slot of offset d for octant class (ox,oy,oz): components range over
-// [-2-o, 3-o]; the inner [-1,1]^3 is excluded.
-// Closed form: lexicographic index in the 6^3 window minus the excluded inner
-// 3^3 cells (at window offset 1 + o per axis) that precede it.
-__device__ __forceinline__ int v_slot(int ox, int oy, int oz, int dx, int dy, int dz) {
-    const int a = dx + 2 + ox, b = dy + 2 + oy, c = dz + 2 + oz;  // 0..5
-    if (a < 0 || a > 5 || b < 0 || b > 5 || c < 0 || c > 5) return -1;
-    const int a0 = 1 + ox, b0 = 1 + oy, c0 = 1 + oz;
-    const bool ina = a >= a0 && a < a0 + 3, inb = b >= b0 && b < b0 + 3, inc = c >= c0 && c < c0 + 3;
-    if (ina && inb && inc) return -1;
-    int before = min(max(a - a0, 0), 3) * 9;
-    if (ina) {
-        before += min(max(b - b0, 0), 3) * 3;
-        if (inb) before += min(max(c - c0, 0), 3);
-    }
-    return a * 36 + b * 6 + c - before;
-}
-
 // A leaf holding at most thr points: its W/X interactions are summed directly.
 __device__ __forceinline__ bool direct_box(const int32_t *nchild, const int32_t *cnt, int thr, int32_t b) {
     return thr >= 0 && nchild[b] == 0 && cnt[b] <= thr;
 }
 
-// V list (children of the parent's colleagues not adjacent to b) into the
-// per-class slot table, and X list (coarser leaves adjacent to the parent but
-// not to b; empty when b itself is a direct-sum leaf, see k_uw).  One warp
-// per box: lane k < 27 takes the parent's colleague k (each child has its
-// own slot); the X list keeps the parent's coarse order through a ballot.
-// (coll, coarse and ncoarse are written earlier in the same launch)
-__device__ __forceinline__ void dev_vx(int64_t b, int lane, int level, int thr, const int32_t *__restrict__ parent,
-                                       const int32_t *__restrict__ child_first,
-                                       const int32_t *__restrict__ nchild, const int32_t *__restrict__ cnt,
-                                       const int32_t *__restrict__ lvl, const int32_t *__restrict__ cx,
-                                       const int32_t *__restrict__ cy, const int32_t *__restrict__ cz,
-                                       const int32_t *coll, const int32_t *coarse, const int32_t *ncoarse,
-                                       int32_t *vdense, int32_t *nv, int32_t *xdense, int32_t *nx,
-                                       unsigned long long *totals, const ListShifts &sh) {
-    // (a V-list slot fixes the source's offset, so the slot table needs no
-    // image shift: the source's expansion is the same in every image)
-    int32_t *vb = vdense + b * kVSlots;  // preset to -1 by a memset
-    int cntv = 0, cntx = 0;
-    if (level > 0) {
+// X list (coarser leaves adjacent to the parent but not to b; empty when b
+// itself is a direct-sum leaf, see k_uw) in the parent's coarse order (a
+// ballot), and the V and X counts.  One warp per box.
+// (coarse and ncoarse of the parent come from the previous level's launch)
+__device__ __forceinline__ void dev_x(int64_t b, int lane, int level, int thr, int cntv,
+                                      const int32_t *__restrict__ parent, const int32_t *__restrict__ nchild,
+                                      const int32_t *__restrict__ cnt, const int32_t *__restrict__ lvl,
+                                      const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                                      const int32_t *__restrict__ cz, const int32_t *coarse, const int32_t *ncoarse,
+                                      int32_t *nv, int32_t *xdense, int32_t *nx, const ListShifts &sh) {
+    int cntx = 0;
+    if (level > 0 && !direct_box(nchild, cnt, thr, (int32_t)b)) {
         const int32_t P = parent[b];
-        const int bx = cx[b], by = cy[b], bz = cz[b];
-        const int ox = bx & 1, oy = by & 1, oz = bz & 1;
-        if (lane < kColl) {
-            const int32_t c = coll[(int64_t)P * kColl + lane];
-            if (c >= 0) {
-                int sx, sy, sz;
-                shift_boxes(shift_of(sh.coll, (int64_t)P * kColl + lane), level, sx, sy, sz);
-                for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
-                    const int dx = cx[ch] + sx - bx, dy = cy[ch] + sy - by, dz = cz[ch] + sz - bz;
-                    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
-                    const int sl = v_slot(ox, oy, oz, dx, dy, dz);
-                    if (sl < 0) continue;  // unreachable: children of parent colleagues lie in the class window
-                    vb[sl] = ch;
-                    ++cntv;
-                }
-            }
+        const int np = ncoarse[P];
+        int32_t a = -1;
+        int sa = 13;
+        bool keep = false;
+        if (lane < np) {
+            a = coarse[(int64_t)P * kMaxCoarse + lane];
+            sa = shift_of(sh.coarse, (int64_t)P * kMaxCoarse + lane);
+            keep = !adjacent_img(lvl[a], cx[a], cy[a], cz[a], sa, level, cx[b], cy[b], cz[b]);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cntv += __shfl_xor_sync(0xffffffffu, cntv, o);
-        if (!direct_box(nchild, cnt, thr, (int32_t)b)) {
-            const int np = ncoarse[P];
-            int32_t a = -1;
-            int sa = 13;
-            bool keep = false;
-            if (lane < np) {
-                a = coarse[(int64_t)P * kMaxCoarse + lane];
-                sa = shift_of(sh.coarse, (int64_t)P * kMaxCoarse + lane);
-                keep = !adjacent_img(lvl[a], cx[a], cy[a], cz[a], sa, level, bx, by, bz);
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int pos = __popc(m & ((1u << lane) - 1u));
-                xdense[b * kMaxCoarse + pos] = a;
-                if (sh.x) sh.x[b * kMaxCoarse + pos] = (int8_t)sa;
-            }
-            cntx = __popc(m);
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int pos = __popc(m & ((1u << lane) - 1u));
+            xdense[b * kMaxCoarse + pos] = a;
+            if (sh.x) sh.x[b * kMaxCoarse + pos] = (int8_t)sa;
         }
+        cntx = __popc(m);
     }
     if (lane == 0) {
         nv[b] = cntv;
@@ -1241,31 +1442,29 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
     return cudaGetLastError();  // the particle records follow once the leaves are listed
 }
 
-// Octree, level by level, from sorted keys.  Nodes at level `lsort` cannot be
-// split (their children's digit is not sorted): cudaErrorNotReady if one must.
+// Octree from sorted keys.  Nodes at level `lsort` cannot be split (their
+// children's digit is not sorted): cudaErrorNotReady if one must.
 //
-// Each level needs its node count on the host (grid sizes, capacity, the end
-// of the tree), i.e. a stream synchronisation per level.  When the previous
-// tree's level sizes are known, the levels it had are first built without
-// them: device-held ranges, grids sized for twice the previous count, and one
-// synchronisation at the end that checks every count against its grid (on a
-// miss the whole build is redone level by level).
+// When the previous tree's level sizes are known, the levels it had are built
+// at once (k_os_*: four launches, one synchronisation for the level
+// boundaries); a deeper tree continues level by level from its last level.
+// Otherwise each level needs its node count on the host (grid sizes,
+// capacity, the end of the tree): a stream synchronisation per level.
 static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
     const int S = P.n_sys;
     const std::vector<int64_t> prev = P.level_start;  // the last build's level boundaries
     uint32_t *total_dev = P.scan_tmp + P.scan_tmp_elems - 1;
-    // split levels 0 .. lspec - 1 without round trips: every level the last
-    // tree had, its deepest (leaf) level included, so that a tree of the same
-    // depth is complete at the one synchronisation; a node at level lsort
-    // cannot be split from the sorted digits
+    // levels 1 .. lspec at once: every level the last tree had below its
+    // roots, so that a tree of the same depth is complete at the one
+    // synchronisation (a node at level lsort cannot be split from the sorted
+    // digits).  The box arrays are sized for eight times twice the last
+    // tree's level sizes; a tree that outgrows them is redone level by level.
     const int lspec = std::min((int)prev.size() - 1, lsort);
-    std::vector<int64_t> m_ub;
-    if (lspec >= 2 && prev[1] == S) {
-        int64_t need = S;
-        for (int l = 0; l < lspec; ++l) {
-            m_ub.push_back(l == 0 ? S : 2 * (prev[l + 1] - prev[l]) + 64);
-            need += 8 * m_ub.back();
-        }
+    const bool spec = lspec >= 2 && prev[1] == S;
+    int64_t need = S;
+    if (spec) {
+        for (int l = 1; l < lspec; ++l) need += 8 * (2 * (prev[l + 1] - prev[l]) + 64);
+        need += 8 * S;
         if (need > P.box_cap) {
             KIFMM_CUDA_TRY(grow_tree_arrays(P, need + 1024, 0));
             total_dev = P.scan_tmp + P.scan_tmp_elems - 1;
@@ -1274,26 +1473,30 @@ static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
     bool spec_done = false;
     int64_t ls = 0, le = S;
     int level = 0;
-    if (!m_ub.empty()) {
+    if (spec) {
         ++g_launches, k_roots<<<grid_for(S, 128), 128, 0, s>>>(S, P.sys_off_d, P.lvl, P.cx, P.cy, P.cz, P.first,
                                                                 P.cnt, P.parent, P.sys);
         int64_t *lsd = P.spec_buf;  // lsd[l], lsd[l + 1]: level l's boxes
-        ++g_launches, k_spec_init<<<1, 32, 0, s>>>(lsd, S, P.spec_fail);
-        uint32_t *scan_out = P.tmp_nchild + P.box_cap;
-        for (int l = 0; l < lspec; ++l) {
-            const int64_t mu = m_ub[l];
-            ++g_launches, k_split<<<grid_for(mu, 4), 128, 0, s>>>(0, 0, lsd + l, mu, l, P.desc.leaf_cap,
-                                                                  P.desc.max_depth, P.keys[0], P.first, P.cnt,
-                                                                  P.tmp_nchild, P.child_rng);
-            KIFMM_CUDA_TRY(exclusive_scan_u32(P.tmp_nchild, scan_out, mu, total_dev, P.scan_tmp,
-                                              P.scan_tmp_elems - 1, s));
-            const int64_t next = (l + 1 < lspec) ? m_ub[l + 1] : INT64_MAX;
-            ++g_launches, k_emit<<<grid_for(mu, 128), 128, 0, s>>>(0, 0, lsd + l, mu, P.tmp_nchild, scan_out,
-                                                                   P.child_rng, P.lvl, P.cx, P.cy, P.cz, P.first,
-                                                                   P.cnt, P.parent, P.child_first, P.nchild, P.sys,
-                                                                   P.box_cap, P.status, total_dev, next,
-                                                                   P.spec_fail);
+        const int64_t n = P.n;
+        const int ntiles = (int)((n + kOsTile - 1) / kOsTile);
+        const size_t need_cnt = (size_t)lspec * std::max(ntiles, 1);
+        if (need_cnt > P.os_cnt_elems) {
+            P.os_cnt_elems = need_cnt;
+            KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.os_cnt, sizeof(uint32_t) * P.os_cnt_elems));
         }
+        const int M = P.desc.leaf_cap, D = P.desc.max_depth;
+        if (ntiles > 0)
+            ++g_launches, k_os_count<<<ntiles, kBlock, 0, s>>>(n, P.keys[0], P.sys_off_d, S, lspec, M, D, ntiles,
+                                                               P.os_cnt);
+        ++g_launches, k_os_scan<<<1, 1024, 0, s>>>(lspec, ntiles, S, P.box_cap, P.os_cnt, lsd, P.spec_fail);
+        if (ntiles > 0)
+            ++g_launches, k_os_emit<<<ntiles, kBlock, 0, s>>>(n, P.keys[0], P.sys_off_d, S, lspec, M, D, ntiles,
+                                                              P.os_cnt, P.spec_fail, P.lvl, P.cx, P.cy, P.cz,
+                                                              P.first, P.cnt, P.sys);
+        ++g_launches, k_os_link<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(need, 256),
+                                                                                    (int64_t)P.num_sms * 8)),
+                                  256, 0, s>>>(lsd, lspec, M, D, P.spec_fail, P.lvl, P.first, P.cnt, P.parent,
+                                               P.child_first, P.nchild);
         KIFMM_CUDA_TRY(cudaGetLastError());
         std::vector<int64_t> lsh(lspec + 2);
         int fail = 0;
@@ -1321,7 +1524,7 @@ static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
             le = S;
         }
     }
-    if (m_ub.empty() || level == 0) {
+    if (!spec || level == 0) {
         ++g_launches, k_roots<<<grid_for(S, 128), 128, 0, s>>>(S, P.sys_off_d, P.lvl, P.cx, P.cy, P.cz, P.first,
                                                                 P.cnt, P.parent, P.sys);
         P.level_start.assign(1, 0);
@@ -1329,9 +1532,9 @@ static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
     }
     while (true) {
         const int64_t m = le - ls;
-        ++g_launches, k_split<<<grid_for(m, 4), 128, 0, s>>>(ls, le, nullptr, m, level, P.desc.leaf_cap,
-                                                             P.desc.max_depth, P.keys[0], P.first, P.cnt,
-                                                             P.tmp_nchild, P.child_rng);
+        ++g_launches, k_split<<<grid_for(m, 4), 128, 0, s>>>(ls, le, level, P.desc.leaf_cap, P.desc.max_depth,
+                                                             P.keys[0], P.first, P.cnt, P.tmp_nchild,
+                                                             P.child_rng);
         uint32_t *scan_out = P.tmp_nchild + P.box_cap;
         KIFMM_CUDA_TRY(exclusive_scan_u32(P.tmp_nchild, scan_out, m, total_dev, P.scan_tmp,
                                           P.scan_tmp_elems - 1, s));
@@ -1346,10 +1549,10 @@ static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
             KIFMM_CUDA_TRY(exclusive_scan_u32(P.tmp_nchild, scan_out, m, total_dev, P.scan_tmp,
                                               P.scan_tmp_elems - 1, s));
         }
-        ++g_launches, k_emit<<<grid_for(m, 128), 128, 0, s>>>(ls, le, nullptr, m, P.tmp_nchild, scan_out,
-                                                              P.child_rng, P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt,
-                                                              P.parent, P.child_first, P.nchild, P.sys, P.box_cap,
-                                                              P.status, nullptr, 0, nullptr);
+        ++g_launches, k_emit<<<grid_for(m, 128), 128, 0, s>>>(ls, le, P.tmp_nchild, scan_out, P.child_rng,
+                                                              P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.parent,
+                                                              P.child_first, P.nchild, P.sys, P.box_cap,
+                                                              P.status);
         KIFMM_CUDA_TRY(cudaGetLastError());
         if (total == 0) break;
         ls = le;
@@ -1440,10 +1643,11 @@ cudaError_t gather_particles(Plan &P, const void *xyz, const void *q_in, cudaStr
     return cudaGetLastError();
 }
 
-// The list passes of one level, one warp per box: its colleagues, then its
-// coarse adjacent leaves (which read its own colleagues), then its V and X
-// lists (which read its own coarse list).  Everything else they read belongs
-// to the previous level, so the three need no grid-wide ordering.
+// The list passes of one level, one warp per box: its colleagues and V list
+// (one scan of the parent's colleagues' children), then its coarse adjacent
+// leaves (which read its own colleagues), then its X list.  Everything else
+// they read belongs to the previous level, so the passes need no grid-wide
+// ordering.
 __global__ void k_lists_level(int64_t ls, int64_t le, int level, int thr, const int32_t *__restrict__ parent,
                               const int32_t *__restrict__ child_first, const int32_t *__restrict__ nchild,
                               const int32_t *__restrict__ cnt, const int32_t *__restrict__ lvl,
@@ -1457,12 +1661,11 @@ __global__ void k_lists_level(int64_t ls, int64_t le, int level, int thr, const 
     if (threadIdx.x < 2) blk_tot[threadIdx.x] = 0;
     __syncthreads();
     if (b < le) {
-        dev_colleagues(b, lane, level, parent, child_first, nchild, cx, cy, cz, coll, sh);
+        const int cntv =
+            dev_colleagues_v(b, lane, level, parent, child_first, nchild, cx, cy, cz, coll, vdense, sh);
         __syncwarp();
         dev_coarse(b, lane, level, parent, nchild, lvl, cx, cy, cz, coll, coarse, ncoarse, status, sh);
-        __syncwarp();
-        dev_vx(b, lane, level, thr, parent, child_first, nchild, cnt, lvl, cx, cy, cz, coll, coarse, ncoarse, vdense,
-               nv, xdense, nx, totals, sh);
+        dev_x(b, lane, level, thr, cntv, parent, nchild, cnt, lvl, cx, cy, cz, coarse, ncoarse, nv, xdense, nx, sh);
         // V and X list totals: one global atomic per block, not per box (a
         // single address taking an atomic from every box serialises)
         if (lane == 0) {

@@ -359,8 +359,12 @@ def test_depth_limit_leaves_exceed_cap():
     assert O.rel_l2(pot.cpu().numpy(), pot_o) <= 1e-12
 
 
-def test_batched_systems_match_per_system_oracle():
-    sizes = [1500, 333, 2711]
+@pytest.mark.parametrize("sizes", [[1500, 333, 2711], [1500, 10, 2711, 40]])
+def test_batched_systems_match_per_system_oracle(sizes):
+    """Three or four systems in one plan, each against the oracle on its own
+    (a system of one leaf among them).  The plan then rebuilds from the same
+    sources: that build takes every level at once from the last tree's level
+    sizes, and must give the same boxes and the same outputs bit for bit."""
     xs, qs = [], []
     for k, nk in enumerate(sizes):
         x, q = (G.uniform_charges(nk, 40 + k) if k % 2 == 0 else
@@ -369,12 +373,18 @@ def test_batched_systems_match_per_system_oracle():
         qs.append(q)
     off = np.concatenate([[0], np.cumsum(sizes)])
     X, Q = np.concatenate(xs), np.concatenate(qs)
-    plan = _plan(X, M=16, n_systems=3)
+    plan = _plan(X, M=16, n_systems=len(sizes))
     plan.set_sources(_dev(X), _dev(Q), sys_offsets=off)
     pot, grad, energy = plan.evaluate(want_energy=True)
     pot, grad = pot.cpu().numpy(), grad.cpu().numpy()
     g = plan.tree()
-    for k in range(3):
+    plan.set_sources(_dev(X), _dev(Q), sys_offsets=off)
+    g2 = plan.tree()
+    for name in g:
+        assert np.array_equal(g[name], g2[name]), name
+    pot2, grad2, _ = plan.evaluate()
+    assert np.array_equal(pot2.cpu().numpy(), pot) and np.array_equal(grad2.cpu().numpy(), grad)
+    for k in range(len(sizes)):
         sl = slice(off[k], off[k + 1])
         po, go, info = O.kifmm(xs[k], qs[k], p=4, leaf_cap=16)
         assert O.rel_l2(pot[sl], po) <= 1e-12 and O.rel_l2(grad[sl], go) <= 1e-12
