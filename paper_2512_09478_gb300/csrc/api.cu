@@ -158,6 +158,7 @@ static cudaError_t ensure_box_arrays(Plan &P) {
         {(void **)&P.part_list[3], sizeof(int32_t) * cap},
         {(void **)&P.child8, sizeof(int32_t) * 8 * cap},
         {(void **)&P.wsrc_flag, sizeof(int32_t) * cap},
+        {(void **)&P.leaf_ctr, sizeof(float2) * 3 * cap},
         {&P.u_chk, esz * P.ns * cap},
         {&P.d_chk, esz * P.ns * cap},
         {&P.up_dens, esz * P.ns * cap},
@@ -302,6 +303,7 @@ kifmm_status kifmm_plan_create(const kifmm_plan_desc *desc, kifmm_plan **out) {
         {(void **)&P.sys_off_d, sizeof(int64_t) * (P.sys_cap + 1)},
         {(void **)&P.lo_side, sizeof(double) * 4 * P.sys_cap},
         {(void **)&P.key_scale, sizeof(double) * P.sys_cap},
+        {(void **)&P.inv_side_f, sizeof(float) * P.sys_cap},
         {(void **)&P.out_scale, sizeof(double) * 2 * P.sys_cap},
         {(void **)&P.bbox_ord, sizeof(unsigned long long) * 6 * P.sys_cap},
         {(void **)&P.hist, sizeof(uint32_t) * P.hist_elems},

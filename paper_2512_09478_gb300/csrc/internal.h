@@ -138,6 +138,8 @@ struct Plan {
     int64_t *sys_off_d = nullptr;   // [S+1]
     double *lo_side = nullptr;      // [S][4]
     double *key_scale = nullptr;    // [S] 2^21 / side
+    float *inv_side_f = nullptr;    // [S] 1 / side (FP64 quotient rounded to FP32)
+    float2 *leaf_ctr = nullptr;     // [leaf][3] leaf centres (FP64) as unevaluated sums hi + lo of two floats
     double *out_scale = nullptr;    // [S][2] coef / (4 pi side), coef / (4 pi side^2)
     unsigned long long *bbox_ord = nullptr;  // [S][6]
     uint32_t *scan_tmp = nullptr;   // scan scratch
@@ -244,7 +246,7 @@ struct Plan {
     int *status = nullptr;   // device status word
     int *moved = nullptr;    // device flag of the tree reuse test
     int64_t *spec_buf = nullptr;  // [32] all-levels octree build: level boundaries
-    int *spec_fail = nullptr;     // the speculative build outgrew the box arrays
+    int *spec_fail = nullptr;     // the all-levels build outgrew the box arrays
     uint32_t *os_cnt = nullptr;   // [levels][particle tiles] box counts, then box offsets
     size_t os_cnt_elems = 0;
     cudaStream_t last_stream = nullptr;

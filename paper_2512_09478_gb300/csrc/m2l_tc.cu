@@ -433,17 +433,19 @@ __global__ void __launch_bounds__(256) k_rowmat(int64_t nrows, const int32_t *__
     }
 }
 
-// hi/lo FP16 split of the scaled expansions, K padded with zeros.
+// hi/lo FP16 split of the scaled expansions, K padded with zeros; a warp per
+// box (coalesced rows, no index division).
 __global__ void k_split_u(int64_t nb, int ns, int kp, const float *__restrict__ u, const int32_t *__restrict__ lvl,
                           const float *__restrict__ level_sigma, __half *__restrict__ uh, __half *__restrict__ ul) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nb * kp) return;
-    const int64_t b = idx / kp;
-    const int k = (int)(idx - b * kp);
-    const float x = (k < ns) ? u[(size_t)b * ns + k] * level_sigma[lvl[b]] : 0.f;
-    const __half h = __float2half_rn(x);
-    uh[idx] = h;
-    ul[idx] = __float2half_rn(x - __half2float(h));
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= nb) return;
+    const float sg = level_sigma[lvl[b]];
+    for (int k = threadIdx.x & 31; k < kp; k += 32) {
+        const float x = (k < ns) ? u[(size_t)b * ns + k] * sg : 0.f;
+        const __half h = __float2half_rn(x);
+        uh[(size_t)b * kp + k] = h;
+        ul[(size_t)b * kp + k] = __float2half_rn(x - __half2float(h));
+    }
 }
 
 // Operator B[j][k] = M_o[j][k] (m2l_t is stored transposed, [o][k][ld], with
@@ -666,9 +668,8 @@ cudaError_t m2l_tensor(Plan &P, cudaStream_t s) {
     KIFMM_CUDA_TRY(cudaMemsetAsync(S.level_max, 0, sizeof(unsigned) * 32, s));
     ++g_launches, k_level_absmax<<<(unsigned)((P.nb + 7) / 8), 256, 0, s>>>(P.nb, S.n_in, u, P.lvl, S.level_max);
     ++g_launches, k_level_scale<<<1, 32, 0, s>>>(nlev, S.level_max, S.sigma_b, S.level_sigma, S.level_unscale);
-    const int64_t tot = P.nb * S.kp;
-    ++g_launches, k_split_u<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.nb, S.n_in, S.kp, u, P.lvl,
-                                                                          S.level_sigma, S.uh, S.ul);
+    ++g_launches, k_split_u<<<(unsigned)((P.nb + 7) / 8), 256, 0, s>>>(P.nb, S.n_in, S.kp, u, P.lvl,
+                                                                       S.level_sigma, S.uh, S.ul);
     TileArgs a;
     a.targets = P.m2l_targets;
     a.tiles = S.tiles;

@@ -45,19 +45,20 @@ __global__ void k_bbox_init(unsigned long long *bb, int S) {
 }
 
 // Per-system min/max of the positions; non-finite inputs raise a status.
+// A block takes kBboxTile particles; minima and maxima are taken in the input
+// type (FP32 inputs need no FP64 arithmetic, which this GPU runs at a small
+// fraction of the FP32 rate) and become ordered 64-bit words once per warp.
+constexpr int kBboxTile = 1024;
 template <typename T>
 __global__ void k_bbox(int64_t n, const T *__restrict__ xyz, const T *__restrict__ q,
                        const int64_t *__restrict__ off, int S, unsigned long long *bb, int *status) {
     __shared__ unsigned long long red[6][kBlock / 32];
-    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const int64_t base = (int64_t)blockIdx.x * kBboxTile;
     if (base >= n) return;
-    const int64_t end = min(n, base + (int64_t)kTile);
+    const int64_t end = min(n, base + (int64_t)kBboxTile);
     const int s0 = find_sys(off, S, base), s1 = find_sys(off, S, end - 1);
-    // minima and maxima are exact in the input type (FP32 inputs need no FP64
-    // arithmetic, which this GPU runs at a small fraction of the FP32 rate)
-    T mn[3], mx[3];
-    for (int d = 0; d < 3; ++d) mn[d] = mx[d] = T(0);
-    int cur = -1;
+    const T inf = (T)INFINITY;
+    T mn[3] = {inf, inf, inf}, mx[3] = {-inf, -inf, -inf};
     bool bad = false;
     for (int64_t i = base + threadIdx.x; i < end; i += kBlock) {
         T v[3];
@@ -75,26 +76,25 @@ __global__ void k_bbox(int64_t n, const T *__restrict__ xyz, const T *__restrict
             continue;
         }
         for (int d = 0; d < 3; ++d) {
-            mn[d] = (cur < 0 || v[d] < mn[d]) ? v[d] : mn[d];
-            mx[d] = (cur < 0 || v[d] > mx[d]) ? v[d] : mx[d];
+            mn[d] = v[d] < mn[d] ? v[d] : mn[d];
+            mx[d] = v[d] > mx[d] ? v[d] : mx[d];
         }
-        cur = s0;
     }
     if (bad) set_status(status, KIFMM_ERR_NONFINITE);
     if (s0 != s1) return;
-    // block reduction (single system)
-    unsigned long long o[6];
+    // block reduction (single system): in T within each warp, then ordered words
     for (int d = 0; d < 3; ++d) {
-        o[d] = (cur >= 0) ? ord_of((double)mn[d]) : ~0ULL;
-        o[3 + d] = (cur >= 0) ? ord_of((double)mx[d]) : 0ULL;
-    }
-    for (int k = 0; k < 6; ++k) {
-        unsigned long long v = o[k];
-        for (int sh = 16; sh > 0; sh >>= 1) {
-            unsigned long long w = __shfl_xor_sync(0xffffffffu, v, sh);
-            v = (k < 3) ? (w < v ? w : v) : (w > v ? w : v);
+        for (int o = 16; o > 0; o >>= 1) {
+            const T a = __shfl_xor_sync(0xffffffffu, mn[d], o), c = __shfl_xor_sync(0xffffffffu, mx[d], o);
+            mn[d] = a < mn[d] ? a : mn[d];
+            mx[d] = c > mx[d] ? c : mx[d];
         }
-        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int d = 0; d < 3; ++d) {
+            red[d][threadIdx.x >> 5] = mn[d] < inf ? ord_of((double)mn[d]) : ~0ULL;
+            red[3 + d][threadIdx.x >> 5] = mx[d] > -inf ? ord_of((double)mx[d]) : 0ULL;
+        }
     }
     __syncthreads();
     if (threadIdx.x < 6) {
@@ -107,7 +107,7 @@ __global__ void k_bbox(int64_t n, const T *__restrict__ xyz, const T *__restrict
 
 // Root cube per system: lo = per-axis minimum, side = largest extent (1 if 0).
 __global__ void k_bbox_final(const unsigned long long *bb, int S, double *lo_side, double *key_scale, double coef,
-                             double *out_scale) {
+                             double *out_scale, float *inv_side_f) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     double side = 0.0;
@@ -119,6 +119,7 @@ __global__ void k_bbox_final(const unsigned long long *bb, int S, double *lo_sid
     side = (side > 0.0) ? side : 1.0;
     lo_side[s * 4 + 3] = side;
     key_scale[s] = __ddiv_rn(2097152.0, side);  // once per system: FP64 division is slow
+    inv_side_f[s] = (float)__ddiv_rn(1.0, side);
     // output scales of the unit-root results: potential coef / (4 pi side), gradient / side^2
     const double c1 = coef * kInv4Pi / side;
     out_scale[2 * s] = c1;
@@ -132,11 +133,13 @@ __device__ __forceinline__ double wrap_cell(double x, double cell) {
 }
 
 // The root cube of a periodic plan is the cell itself.
-__global__ void k_periodic_root(double cell, double *lo_side, double *key_scale, double coef, double *out_scale) {
+__global__ void k_periodic_root(double cell, double *lo_side, double *key_scale, double coef, double *out_scale,
+                                float *inv_side_f) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     lo_side[0] = lo_side[1] = lo_side[2] = 0.0;
     lo_side[3] = cell;
     key_scale[0] = __ddiv_rn(2097152.0, cell);
+    inv_side_f[0] = (float)__ddiv_rn(1.0, cell);
     const double c1 = coef * kInv4Pi / cell;
     out_scale[0] = c1;
     out_scale[1] = c1 / cell;
@@ -466,8 +469,7 @@ __global__ void k_emit(int64_t ls, int64_t le, const uint32_t *__restrict__ nchi
 // the link pass finds parents and child ranges by binary search over the
 // first particles of the neighbouring levels.
 // ---------------------------------------------------------------------------
-constexpr int kOsPer = 16;                 // particles per thread
-constexpr int kOsTile = kBlock * kOsPer;   // particles per block
+constexpr int kOsTile = 256;  // particles per block, one per thread
 
 __device__ __forceinline__ uint32_t compact3(uint64_t x) {  // inverse of spread3
     x &= 0x1249249249249249ULL;
@@ -506,162 +508,181 @@ __device__ __forceinline__ bool os_parent_splits(const uint64_t *__restrict__ ke
     return j < s1 && (keys[j] >> sh) == pp;
 }
 
-// Box flags of level l for the thread's particles i0 .. i0 + kOsPer - 1
-// (kp[e + 1] = keys[i0 + e], kp[0] = keys[i0 - 1]); bit e set if particle
-// i0 + e is a box of level l.
-__device__ __forceinline__ uint32_t os_flags(const uint64_t *__restrict__ keys, const uint64_t (&kp)[kOsPer + 1],
-                                             int64_t n, int64_t i0, const int64_t *__restrict__ off, int sy0,
-                                             int l, int M, int max_depth) {
-    if (l - 1 >= max_depth) return 0u;
+// The thread's particle: its key, its predecessor's and its system range.
+struct OsPoint {
+    bool valid;
+    int sy;
+    int64_t i, s0, s1;
+    uint64_t key, prev;
+};
+__device__ __forceinline__ OsPoint os_point(int64_t n, const uint64_t *__restrict__ keys,
+                                            const int64_t *__restrict__ off, int S) {
+    OsPoint p;
+    p.i = (int64_t)blockIdx.x * kOsTile + threadIdx.x;
+    p.valid = p.i < n;
+    p.key = p.valid ? keys[p.i] : 0ull;
+    p.prev = (p.valid && p.i > 0) ? keys[p.i - 1] : 0ull;
+    p.sy = p.valid ? find_sys(off, S, p.i) : 0;
+    p.s0 = p.valid ? off[p.sy] : 0;
+    p.s1 = p.valid ? off[p.sy + 1] : 0;
+    return p;
+}
+
+// Whether the particle is a box of level l.
+__device__ __forceinline__ bool os_is_box(const OsPoint &p, const uint64_t *__restrict__ keys, int l, int M,
+                                          int max_depth) {
+    if (!p.valid || l - 1 >= max_depth) return false;
     const int sh = prefix_shift(l);
+    if (p.i > p.s0 && (p.key >> sh) == (p.prev >> sh)) return false;  // not a segment start
+    return os_parent_splits(keys, p.i, p.s0, p.s1, l, M);
+}
+
+// Bit l - 1 set: the particle is a box of level l (L <= kMaxLevel + 1 < 32).
+// Every level's test first, with no barrier between them, so that the
+// threads' chains of dependent loads overlap.
+__device__ __forceinline__ uint32_t os_box_levels(const OsPoint &p, const uint64_t *__restrict__ keys, int L, int M,
+                                                  int max_depth) {
     uint32_t f = 0;
-    int sy = sy0;
-#pragma unroll
-    for (int e = 0; e < kOsPer; ++e) {
-        const int64_t i = i0 + e;
-        if (i >= n) break;
-        while (i >= off[sy + 1]) ++sy;
-        const int64_t s0 = off[sy];
-        if (i > s0 && (kp[e + 1] >> sh) == (kp[e] >> sh)) continue;  // not a segment start
-        if (os_parent_splits(keys, i, s0, off[sy + 1], l, M)) f |= 1u << e;
-    }
+    for (int l = 1; l <= L; ++l)
+        if (os_is_box(p, keys, l, M, max_depth)) f |= 1u << (l - 1);
     return f;
 }
 
-__device__ __forceinline__ void os_load(const uint64_t *__restrict__ keys, int64_t n, int64_t i0,
-                                        uint64_t (&kp)[kOsPer + 1]) {
-    kp[0] = (i0 > 0 && i0 <= n) ? keys[i0 - 1] : 0ull;
-#pragma unroll
-    for (int e = 0; e < kOsPer; ++e) kp[e + 1] = (i0 + e < n) ? keys[i0 + e] : 0ull;
+// Pass 1: boxes of levels 1 .. L per particle tile -> cnt[(l - 1) ntiles + tile].
+__global__ void __launch_bounds__(kOsTile) k_os_count(int64_t n, const uint64_t *__restrict__ keys,
+                                                      const int64_t *__restrict__ off, int S, int L, int M,
+                                                      int max_depth, int ntiles, uint32_t *cnt) {
+    const OsPoint p = os_point(n, keys, off, S);
+    const uint32_t f = os_box_levels(p, keys, L, M, max_depth);
+    for (int l = 1; l <= L; ++l) {
+        const int c = __syncthreads_count((f >> (l - 1)) & 1u);
+        if (threadIdx.x == 0) cnt[(size_t)(l - 1) * ntiles + blockIdx.x] = (uint32_t)c;
+    }
 }
 
-// Block-wide exclusive scan of one value per thread; *total gets the sum.
-__device__ __forceinline__ uint32_t os_block_scan(uint32_t v, uint32_t *ws, uint32_t *total) {
+// Pass 2 (one block): the counts cnt[(l - 1) ntiles + tile] become the first
+// box index of each (level, tile) in first_idx (one exclusive scan over the
+// level-major array: each warp sums a contiguous segment with coalesced loads,
+// the warps' sums are scanned, each warp rescans its segment 32 at a time);
+// level boundaries go to lb[0 .. L + 1] (level 0: the S roots), and fail is
+// set when the boxes outgrow the arrays (then nothing else is written).
+__global__ void __launch_bounds__(1024) k_os_scan(int L, int ntiles, int S, int64_t cap,
+                                                  const uint32_t *__restrict__ cnt, uint32_t *__restrict__ first_idx,
+                                                  int64_t *lb, int *fail) {
+    __shared__ uint32_t ws[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
+    const int64_t len = (int64_t)L * ntiles;
+    const int64_t seg = ((len + 32 * 32 - 1) / (32 * 32)) * 32;  // per warp, a multiple of 32
+    const int64_t w0 = min(len, warp * seg), w1 = min(len, w0 + seg);
+    uint32_t sum = 0;
+#pragma unroll 4
+    for (int64_t k = w0 + lane; k < w1; k += 32) sum += cnt[k];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    __syncthreads();  // ws free from any previous use
-    if (lane == 31) ws[warp] = x;
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) ws[warp] = sum;
     __syncthreads();
     uint32_t before = 0, tot = 0;
-    for (int w = 0; w < kBlock / 32; ++w) {
+    for (int w = 0; w < 32; ++w) {
         before += (w < warp) ? ws[w] : 0u;
         tot += ws[w];
     }
-    *total = tot;
-    return before + x - v;
-}
-
-// Pass 1: boxes of levels 1 .. L per particle tile -> cnt[(l - 1) ntiles + tile].
-__global__ void __launch_bounds__(kBlock) k_os_count(int64_t n, const uint64_t *__restrict__ keys,
-                                                     const int64_t *__restrict__ off, int S, int L, int M,
-                                                     int max_depth, int ntiles, uint32_t *cnt) {
-    __shared__ uint32_t ws[kBlock / 32];
-    const int64_t i0 = (int64_t)blockIdx.x * kOsTile + (int64_t)threadIdx.x * kOsPer;
-    uint64_t kp[kOsPer + 1];
-    os_load(keys, n, i0, kp);
-    const int sy0 = i0 < n ? find_sys(off, S, i0) : 0;
-    for (int l = 1; l <= L; ++l) {
-        const uint32_t f = i0 < n ? os_flags(keys, kp, n, i0, off, sy0, l, M, max_depth) : 0u;
-        uint32_t tot;
-        (void)os_block_scan((uint32_t)__popc(f), ws, &tot);
-        if (threadIdx.x == 0) cnt[(size_t)(l - 1) * ntiles + blockIdx.x] = tot;
-    }
-}
-
-// Pass 2 (one block): the counts become first box indices in place, level
-// boundaries go to lb[0 .. L + 1] (level 0: the S roots), and fail is set
-// when the boxes outgrow the arrays (then nothing else is written).
-__global__ void __launch_bounds__(1024) k_os_scan(int L, int ntiles, int S, int64_t cap, uint32_t *cnt, int64_t *lb,
-                                                  int *fail) {
-    __shared__ uint32_t ws[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int64_t carry = S;
-    for (int l = 0; l < L; ++l) {
-        uint32_t *c = cnt + (size_t)l * ntiles;
-        for (int c0 = 0; c0 < ntiles; c0 += 1024) {
-            const int t = c0 + threadIdx.x;
-            const uint32_t v = t < ntiles ? c[t] : 0u;
-            uint32_t x = v;
+    int64_t run = (int64_t)S + before;  // boxes before this warp's segment
+    for (int64_t k0 = w0; k0 < w1; k0 += 32) {
+        const int64_t k = k0 + lane;
+        const uint32_t v = k < w1 ? cnt[k] : 0u;
+        uint32_t x = v;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            __syncthreads();
-            if (lane == 31) ws[warp] = x;
-            __syncthreads();
-            uint32_t before = 0, tot = 0;
-            for (int w = 0; w < 32; ++w) {
-                before += (w < warp) ? ws[w] : 0u;
-                tot += ws[w];
-            }
-            if (t < ntiles) c[t] = (uint32_t)(carry + before + x - v);
-            carry += tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        if (threadIdx.x == 0) lb[l + 2] = carry;
+        if (k < w1) {
+            first_idx[k] = (uint32_t)(run + x - v);
+            if (k % ntiles == 0) lb[k / ntiles + 1] = run + x - v;  // level k / ntiles + 1 starts here
+        }
+        run += __shfl_sync(0xffffffffu, x, 31);
     }
     if (threadIdx.x == 0) {
+        const int64_t total = (int64_t)S + tot;
         lb[0] = 0;
-        lb[1] = S;
-        *fail = carry > cap || carry > (int64_t)INT32_MAX;
+        if (ntiles == 0)
+            for (int l = 1; l <= L; ++l) lb[l] = S;
+        lb[L + 1] = total;
+        *fail = total > cap || total > (int64_t)INT32_MAX;
     }
 }
 
-// Pass 3: each box's level, coordinates, particle range and system.
-__global__ void __launch_bounds__(kBlock) k_os_emit(int64_t n, const uint64_t *__restrict__ keys,
-                                                    const int64_t *__restrict__ off, int S, int L, int M,
-                                                    int max_depth, int ntiles, const uint32_t *__restrict__ base,
-                                                    const int *fail, int32_t *lvl, int32_t *cx, int32_t *cy,
-                                                    int32_t *cz, int32_t *first, int32_t *cnt, int32_t *sys) {
-    __shared__ uint32_t ws[kBlock / 32];
-    if (*fail) return;
-    const int64_t i0 = (int64_t)blockIdx.x * kOsTile + (int64_t)threadIdx.x * kOsPer;
-    uint64_t kp[kOsPer + 1];
-    os_load(keys, n, i0, kp);
-    const int sy0 = i0 < n ? find_sys(off, S, i0) : 0;
-    for (int l = 1; l <= L; ++l) {
-        uint32_t f = i0 < n ? os_flags(keys, kp, n, i0, off, sy0, l, M, max_depth) : 0u;
-        uint32_t tot;
-        int64_t b = (int64_t)base[(size_t)(l - 1) * ntiles + blockIdx.x] + os_block_scan((uint32_t)__popc(f), ws, &tot);
-        const int sh = prefix_shift(l);
-        int sy = sy0;
-        while (f) {
-            const int e = __ffs(f) - 1;
-            f &= f - 1;
-            const int64_t i = i0 + e;
-            while (i >= off[sy + 1]) ++sy;
-            const uint64_t p = keys[i] >> sh;  // (not kp[e + 1]: a dynamic index would spill kp)
-            // the segment's end: doubling steps, then bisection
-            const int64_t s1 = off[sy + 1];
-            int64_t lo = i, hi, step = 1;
-            while (true) {
-                hi = lo + step;
-                if (hi >= s1) {
-                    hi = s1;
-                    break;
-                }
-                if ((keys[hi] >> sh) != p) break;
-                lo = hi;
-                step <<= 1;
-            }
-            while (hi - lo > 1) {
-                const int64_t mid = (lo + hi) >> 1;
-                if ((keys[mid] >> sh) == p) lo = mid; else hi = mid;
-            }
-            lvl[b] = l;
-            cx[b] = (int32_t)compact3(p >> 2);
-            cy[b] = (int32_t)compact3(p >> 1);
-            cz[b] = (int32_t)compact3(p);
-            first[b] = (int32_t)i;
-            cnt[b] = (int32_t)(hi - i);
-            sys[b] = sy;
-            ++b;
+// End of the key segment that starts at particle i (prefix pf = keys[i] >> sh,
+// system end s1): the first j > i with j = s1 or another prefix.  The whole
+// warp probes 32 places per round, growing the stride 32-fold until a probe
+// leaves the segment, then shrinking it 32-fold; in-segment probes always form
+// a prefix of the lanes (sorted keys), so a ballot's count places the end.
+// A segment of c particles takes about 2 log32(c) rounds instead of 2 log2(c)
+// dependent loads.
+__device__ __forceinline__ int64_t warp_segment_end(const uint64_t *__restrict__ keys, int64_t i, int64_t s1,
+                                                   uint64_t pf, int sh, int lane) {
+    int64_t lo = i, step = 1;  // keys[lo] is in the segment
+    for (;;) {
+        const int64_t pos = lo + step * (lane + 1);
+        const bool in = pos < s1 && (keys[pos] >> sh) == pf;
+        const int c = __popc(__ballot_sync(0xffffffffu, in));
+        if (c < 32) {
+            lo += step * c;
+            break;
         }
+        lo += 32 * step;
+        step *= 32;
+    }
+    while (step > 1) {  // the end lies in (lo, lo + step]
+        step = (step + 31) / 32;
+        const int64_t pos = lo + step * (lane + 1);
+        const bool in = pos < s1 && (keys[pos] >> sh) == pf;
+        lo += step * __popc(__ballot_sync(0xffffffffu, in));
+    }
+    return lo + 1;
+}
+
+// Pass 3: each box's level, coordinates, particle range and system; its
+// index is the tile's first box of the level plus the boxes of the level
+// before it in the tile (ballots, then the warps' counts).
+__global__ void __launch_bounds__(kOsTile) k_os_emit(int64_t n, const uint64_t *__restrict__ keys,
+                                                     const int64_t *__restrict__ off, int S, int L, int M,
+                                                     int max_depth, int ntiles, const uint32_t *__restrict__ base_idx,
+                                                     const int *fail, int32_t *lvl, int32_t *cx, int32_t *cy,
+                                                     int32_t *cz, int32_t *first, int32_t *cnt, int32_t *sys) {
+    __shared__ uint32_t wc[kOsTile / 32];
+    if (*fail) return;
+    const OsPoint p = os_point(n, keys, off, S);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t f = os_box_levels(p, keys, L, M, max_depth);
+    for (int l = 1; l <= L; ++l) {
+        const bool box = (f >> (l - 1)) & 1u;
+        const unsigned m = __ballot_sync(0xffffffffu, box);
+        __syncthreads();  // wc free from the previous level
+        if (lane == 0) wc[warp] = (uint32_t)__popc(m);
+        __syncthreads();
+        const int sh = prefix_shift(l);
+        const uint64_t pf = p.key >> sh;
+        // the segments' ends, one box of the warp at a time, all lanes probing
+        int64_t hi = 0;
+        for (unsigned pend = m; pend; pend &= pend - 1) {
+            const int src = __ffs(pend) - 1;
+            const int64_t e = warp_segment_end(keys, __shfl_sync(0xffffffffu, p.i, src),
+                                               __shfl_sync(0xffffffffu, p.s1, src),
+                                               __shfl_sync(0xffffffffu, pf, src), sh, lane);
+            if (lane == src) hi = e;
+        }
+        if (!box) continue;
+        uint32_t before = (uint32_t)__popc(m & ((1u << lane) - 1u));
+        for (int w = 0; w < warp; ++w) before += wc[w];
+        const int64_t b = (int64_t)base_idx[(size_t)(l - 1) * ntiles + blockIdx.x] + before;
+        lvl[b] = l;
+        cx[b] = (int32_t)compact3(pf >> 2);
+        cy[b] = (int32_t)compact3(pf >> 1);
+        cz[b] = (int32_t)compact3(pf);
+        first[b] = (int32_t)p.i;
+        cnt[b] = (int32_t)(hi - p.i);
+        sys[b] = p.sy;
     }
 }
 
@@ -699,6 +720,27 @@ __global__ void k_os_link(const int64_t *__restrict__ lb, int L, int M, int max_
     }
 }
 
+// Leaf centres in the caller's coordinates, C = lo + (c + 1/2) 2^-level side
+// in FP64, as unevaluated sums C_hi + C_lo of two floats: one thread per
+// (leaf, axis), so the few FP64 operations fill whole warps (this GPU runs
+// FP64 at a small fraction of the FP32 rate, per warp instruction).
+__global__ void k_leaf_centres(int64_t max_leaves, const uint32_t *__restrict__ n_leaves,
+                               const int32_t *__restrict__ leaves, const int32_t *__restrict__ lvl,
+                               const int32_t *__restrict__ cx, const int32_t *__restrict__ cy,
+                               const int32_t *__restrict__ cz, const int32_t *__restrict__ sys,
+                               const double *__restrict__ lo_side, float2 *ctr) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t li = t / 3;
+    const int d = (int)(t - 3 * li);
+    if (li >= max_leaves || li >= (int64_t)*n_leaves) return;
+    const int b = leaves[li], s = sys[b];
+    const double w = ldexp(1.0, -lvl[b]);
+    const int c = d == 0 ? cx[b] : d == 1 ? cy[b] : cz[b];
+    const double C = fma((c + 0.5) * w, lo_side[s * 4 + 3], lo_side[s * 4 + d]);
+    const float hi = (float)C;
+    ctr[t] = make_float2(hi, (float)(C - (double)hi));
+}
+
 template <typename TI, typename TC>
 __global__ void k_gather(int64_t max_leaves, const uint32_t *__restrict__ n_leaves,
                          const int32_t *__restrict__ leaves, const int32_t *__restrict__ first,
@@ -707,7 +749,8 @@ __global__ void k_gather(int64_t max_leaves, const uint32_t *__restrict__ n_leav
                          const int32_t *__restrict__ cz, const int32_t *__restrict__ sys,
                          const double *__restrict__ lo_side, const uint32_t *__restrict__ perm,
                          const TI *__restrict__ xyz, const TI *__restrict__ q,
-                         typename Vec4<TC>::type *pts, double cell, double *leaf_q2) {
+                         typename Vec4<TC>::type *pts, double cell, double *leaf_q2,
+                         const float2 *__restrict__ ctr, const float *__restrict__ inv_side_f) {
     // one warp per leaf; the leaf count is read on the device (the grid
     // covers max_leaves)
     const int64_t li = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -716,29 +759,19 @@ __global__ void k_gather(int64_t max_leaves, const uint32_t *__restrict__ n_leav
     const int s = sys[b];
     if constexpr (sizeof(TC) == 4 && sizeof(TI) == 4) {
         if (cell == 0.0 && !leaf_q2) {
-            // FP32 records from FP32 inputs in FP32 arithmetic: this GPU runs
-            // FP64 at a small fraction of the FP32 rate, so lane 0 alone forms
-            // the leaf centre (FP64) and hands it over as an unevaluated sum
-            // C_hi + C_lo of two floats; x - C_hi is exact for x next to C
-            // (Sterbenz), so a record is still the caller's coordinate to
-            // about an ulp of |x|
+            // FP32 records from FP32 inputs in FP32 arithmetic: the leaf
+            // centre comes as an unevaluated sum C_hi + C_lo of two floats
+            // (k_leaf_centres); x - C_hi is exact for x next to C (Sterbenz),
+            // so a record is still the caller's coordinate to about an ulp of
+            // |x|
             const int lane = threadIdx.x & 31;
-            float ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f}, is = 0.f;
-            if (lane == 0) {
-                const double side = lo_side[s * 4 + 3], w = ldexp(1.0, -lvl[b]);
-                const int c3[3] = {cx[b], cy[b], cz[b]};
-                for (int d = 0; d < 3; ++d) {
-                    const double C = fma((c3[d] + 0.5) * w, side, lo_side[s * 4 + d]);
-                    ch[d] = (float)C;
-                    cl[d] = (float)(C - (double)ch[d]);
-                }
-                is = (float)(1.0 / side);
-            }
+            const float2 c2 = lane < 3 ? ctr[3 * li + lane] : make_float2(0.f, 0.f);
+            float ch[3], cl[3];
             for (int d = 0; d < 3; ++d) {
-                ch[d] = __shfl_sync(0xffffffffu, ch[d], 0);
-                cl[d] = __shfl_sync(0xffffffffu, cl[d], 0);
+                ch[d] = __shfl_sync(0xffffffffu, c2.x, d);
+                cl[d] = __shfl_sync(0xffffffffu, c2.y, d);
             }
-            is = __shfl_sync(0xffffffffu, is, 0);
+            const float is = inv_side_f[s];
             const int n = cnt[b], f = first[b];
             for (int k = lane; k < n; k += 32) {
                 const int64_t i = f + k;
@@ -900,7 +933,12 @@ __device__ __forceinline__ int dev_colleagues_v(int64_t b, int lane, int level, 
         const int bx = cx[b], by = cy[b], bz = cz[b];
         const int px = bx & 1, py = by & 1, pz = bz & 1;
         int32_t *vb = vdense + b * kVSlots;
-        for (int32_t ch = child_first[c]; ch < child_first[c] + nchild[c]; ++ch) {
+        const int32_t cf = child_first[c], nc = nchild[c];  // nc <= 8
+        // (a fixed trip count: the children's coordinates load together)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k >= nc) continue;
+            const int32_t ch = cf + k;
             const int dx = cx[ch] + ox - bx, dy = cy[ch] + oy - by, dz = cz[ch] + oz - bz;
             if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) {
                 const int slot = (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
@@ -1385,16 +1423,17 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
     ++g_launches, k_bbox_init<double><<<grid_for(S * 6, 128), 128, 0, s>>>(P.bbox_ord, S);
     const unsigned nt = grid_for(n, kTile);
     if (P.io_f64)
-        ++g_launches, k_bbox<double><<<nt, kBlock, 0, s>>>(n, (const double *)xyz,
+        ++g_launches, k_bbox<double><<<grid_for(n, kBboxTile), kBlock, 0, s>>>(n, (const double *)xyz,
                                              P.stokes ? nullptr : (const double *)q, P.sys_off_d, S,
                                              P.bbox_ord, P.status);
     else
-        ++g_launches, k_bbox<float><<<nt, kBlock, 0, s>>>(n, (const float *)xyz,
+        ++g_launches, k_bbox<float><<<grid_for(n, kBboxTile), kBlock, 0, s>>>(n, (const float *)xyz,
                                             P.stokes ? nullptr : (const float *)q, P.sys_off_d, S,
                                             P.bbox_ord, P.status);
     if (P.periodic) {
         // the root is the cell; the cell must be neutral
-        ++g_launches, k_periodic_root<<<1, 32, 0, s>>>(P.cell, P.lo_side, P.key_scale, P.coef, P.out_scale);
+        ++g_launches, k_periodic_root<<<1, 32, 0, s>>>(P.cell, P.lo_side, P.key_scale, P.coef, P.out_scale,
+                                                       P.inv_side_f);
         KIFMM_CUDA_TRY(cudaMemsetAsync(P.qsum, 0, 2 * sizeof(double), s));
         if (P.io_f64)
             ++g_launches, k_charge_sums<double><<<std::min<unsigned>(nt, 1024), 256, 0, s>>>(n, (const double *)q, P.qsum);
@@ -1403,7 +1442,7 @@ cudaError_t build_tree(Plan &P, const void *xyz, const void *q, cudaStream_t s) 
         ++g_launches, k_charge_check<<<1, 32, 0, s>>>(P.qsum, P.io_f64 ? 1e-12 : 0x1p-24, P.status);
     } else {
         ++g_launches, k_bbox_final<<<grid_for(S, 128), 128, 0, s>>>(P.bbox_ord, S, P.lo_side, P.key_scale, P.coef,
-                                                                    P.out_scale);
+                                                                    P.out_scale, P.inv_side_f);
     }
     if (P.io_f64)
         ++g_launches, k_keys<double><<<grid_for(n, 256), 256, 0, s>>>(n, (const double *)xyz, P.sys_off_d, S, P.lo_side,
@@ -1479,19 +1518,21 @@ static cudaError_t build_levels(Plan &P, cudaStream_t s, int lsort) {
         int64_t *lsd = P.spec_buf;  // lsd[l], lsd[l + 1]: level l's boxes
         const int64_t n = P.n;
         const int ntiles = (int)((n + kOsTile - 1) / kOsTile);
-        const size_t need_cnt = (size_t)lspec * std::max(ntiles, 1);
+        const size_t need_cnt = 2 * (size_t)lspec * std::max(ntiles, 1);  // counts, then first indices
         if (need_cnt > P.os_cnt_elems) {
             P.os_cnt_elems = need_cnt;
             KIFMM_CUDA_TRY(plan_alloc(P, (void **)&P.os_cnt, sizeof(uint32_t) * P.os_cnt_elems));
         }
         const int M = P.desc.leaf_cap, D = P.desc.max_depth;
         if (ntiles > 0)
-            ++g_launches, k_os_count<<<ntiles, kBlock, 0, s>>>(n, P.keys[0], P.sys_off_d, S, lspec, M, D, ntiles,
+            ++g_launches, k_os_count<<<ntiles, kOsTile, 0, s>>>(n, P.keys[0], P.sys_off_d, S, lspec, M, D, ntiles,
                                                                P.os_cnt);
-        ++g_launches, k_os_scan<<<1, 1024, 0, s>>>(lspec, ntiles, S, P.box_cap, P.os_cnt, lsd, P.spec_fail);
+        uint32_t *first_idx = P.os_cnt + (size_t)lspec * std::max(ntiles, 1);
+        ++g_launches, k_os_scan<<<1, 1024, 0, s>>>(lspec, ntiles, S, P.box_cap, P.os_cnt, first_idx, lsd,
+                                                   P.spec_fail);
         if (ntiles > 0)
-            ++g_launches, k_os_emit<<<ntiles, kBlock, 0, s>>>(n, P.keys[0], P.sys_off_d, S, lspec, M, D, ntiles,
-                                                              P.os_cnt, P.spec_fail, P.lvl, P.cx, P.cy, P.cz,
+            ++g_launches, k_os_emit<<<ntiles, kOsTile, 0, s>>>(n, P.keys[0], P.sys_off_d, S, lspec, M, D, ntiles,
+                                                              first_idx, P.spec_fail, P.lvl, P.cx, P.cy, P.cz,
                                                               P.first, P.cnt, P.sys);
         ++g_launches, k_os_link<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(need, 256),
                                                                                     (int64_t)P.num_sms * 8)),
@@ -1625,20 +1666,25 @@ cudaError_t gather_particles(Plan &P, const void *xyz, const void *q_in, cudaStr
         if (P.io_f64)
             ++g_launches, k_gather<double, double><<<grid_for(P.nb, 8), 256, 0, s>>>(
                 P.nb, P.part_counts + 256, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
-                (const double *)xyz, (const double *)q, (double4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
+                (const double *)xyz, (const double *)q, (double4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr, nullptr, nullptr);
         else
             ++g_launches, k_gather<float, double><<<grid_for(P.nb, 8), 256, 0, s>>>(
                 P.nb, P.part_counts + 256, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
-                (const float *)xyz, (const float *)q, (double4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
+                (const float *)xyz, (const float *)q, (double4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr, nullptr, nullptr);
     } else {
         if (P.io_f64)
             ++g_launches, k_gather<double, float><<<grid_for(P.nb, 8), 256, 0, s>>>(
                 P.nb, P.part_counts + 256, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
-                (const double *)xyz, (const double *)q, (float4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
-        else
+                (const double *)xyz, (const double *)q, (float4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr, nullptr, nullptr);
+        else {
+            if (!P.periodic)  // the FP32 path's leaf centres
+                ++g_launches, k_leaf_centres<<<grid_for(3 * P.nb, 256), 256, 0, s>>>(
+                    P.nb, P.part_counts + 256, P.leaves, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.leaf_ctr);
             ++g_launches, k_gather<float, float><<<grid_for(P.nb, 8), 256, 0, s>>>(
                 P.nb, P.part_counts + 256, P.leaves, P.first, P.cnt, P.lvl, P.cx, P.cy, P.cz, P.sys, P.lo_side, P.perm,
-                (const float *)xyz, (const float *)q, (float4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr);
+                (const float *)xyz, (const float *)q, (float4 *)P.pts, P.cell, P.periodic ? P.leaf_q2 : nullptr,
+                P.leaf_ctr, P.inv_side_f);
+        }
     }
     return cudaGetLastError();
 }
