@@ -66,8 +66,8 @@ _M2L_SRC = ("paper_2512_09478_gb300/csrc/m2l_tc.cu", "paper_2512_09478_gb300/csr
 _LEAF_SRC = ("paper_2512_09478_gb300/csrc/fmm.cu", "paper_2512_09478_gb300/csrc/common.cuh",
              "paper_2512_09478_gb300/csrc/internal.h")
 TRAFFIC = {
-    ("dem-coulomb-rsa-1M", "m2l"): (_M2L_SRC, "feb3e37c924e51871e98a1b5331a2f163353762589066b6a0ee6904987129fe4", 95317248),
-    ("dem-coulomb-rsa-1M", "p2p"): (_LEAF_SRC, "c8e01d3a8668b09082bfecaa4c32acf9f6f66a78e23b4bd8158aa4bbf50118b9", 66681344),
+    ("dem-coulomb-rsa-1M", "m2l"): (_M2L_SRC, "2930bb808ea1995153aa528a283826ff0089836c0692b1a886b3579915bdf02c", 96189952),
+    ("dem-coulomb-rsa-1M", "p2p"): (_LEAF_SRC, "69640af591874b528bd1b952f786be219fbd6907e55ce1c25cd9d0760c31f96b", 66811648),
 }
 
 

@@ -528,23 +528,21 @@ __device__ __forceinline__ OsPoint os_point(int64_t n, const uint64_t *__restric
     return p;
 }
 
-// Whether the particle is a box of level l.
-__device__ __forceinline__ bool os_is_box(const OsPoint &p, const uint64_t *__restrict__ keys, int l, int M,
-                                          int max_depth) {
-    if (!p.valid || l - 1 >= max_depth) return false;
-    const int sh = prefix_shift(l);
-    if (p.i > p.s0 && (p.key >> sh) == (p.prev >> sh)) return false;  // not a segment start
-    return os_parent_splits(keys, p.i, p.s0, p.s1, l, M);
-}
-
 // Bit l - 1 set: the particle is a box of level l (L <= kMaxLevel + 1 < 32).
-// Every level's test first, with no barrier between them, so that the
-// threads' chains of dependent loads overlap.
+// A particle that starts a level-l segment whose level-(l-1) segment holds at
+// most M particles lies in a leaf of level l - 1 or coarser: no finer level
+// can hold a box starting with it (its segments only shrink), so the levels
+// below are not tested.
 __device__ __forceinline__ uint32_t os_box_levels(const OsPoint &p, const uint64_t *__restrict__ keys, int L, int M,
                                                   int max_depth) {
     uint32_t f = 0;
-    for (int l = 1; l <= L; ++l)
-        if (os_is_box(p, keys, l, M, max_depth)) f |= 1u << (l - 1);
+    if (!p.valid) return f;
+    for (int l = 1; l <= L && l - 1 < max_depth; ++l) {
+        const int sh = prefix_shift(l);
+        if (p.i > p.s0 && (p.key >> sh) == (p.prev >> sh)) continue;  // not a segment start
+        if (!os_parent_splits(keys, p.i, p.s0, p.s1, l, M)) break;
+        f |= 1u << (l - 1);
+    }
     return f;
 }
 
