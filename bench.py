@@ -67,7 +67,7 @@ _LEAF_SRC = ("paper_2512_09478_gb300/csrc/fmm.cu", "paper_2512_09478_gb300/csrc/
              "paper_2512_09478_gb300/csrc/internal.h")
 TRAFFIC = {
     ("dem-coulomb-rsa-1M", "m2l"): (_M2L_SRC, "2930bb808ea1995153aa528a283826ff0089836c0692b1a886b3579915bdf02c", 96189952),
-    ("dem-coulomb-rsa-1M", "p2p"): (_LEAF_SRC, "69640af591874b528bd1b952f786be219fbd6907e55ce1c25cd9d0760c31f96b", 66811648),
+    ("dem-coulomb-rsa-1M", "p2p"): (_LEAF_SRC, "878cc63175916d94552a1ff20aace24ffec7bd61c66ecd4b34b2f350e9ae4b9d", 76453120),
 }
 
 

@@ -729,6 +729,15 @@ struct LeafCtx {
     LeafTiling tile;     // tile id per remaining-target bucket
     int *status;         // device status word
     const int8_t *u_sh, *w_sh;  // image shifts of the U and W entries (periodic cell), or null
+    // Forward evaluate of a free-space plan: the outputs in caller order with
+    // the physical scales (coef / (4 pi side), / side^2 of the particle's
+    // system), written by the pass itself next to its FP64 results; null
+    // elsewhere (the results are scattered by k_finalize).
+    const uint32_t *perm = nullptr;
+    const int32_t *sys = nullptr;
+    const double *out_scale = nullptr;
+    void *pot = nullptr, *grad = nullptr;
+    int out_f64 = 0;
 };
 
 
@@ -1045,6 +1054,28 @@ __device__ void leaf_pass(const LeafCtx &C, int b, int tbase, const typename Vec
         if (grp == 0 && i < n) {
             res[f + i] = make_double4(tot[0], tot[1], tot[2], tot[3]);
             if (!isfinite(tot[0] + tot[1] + tot[2] + tot[3])) set_status(C.status, KIFMM_ERR_NONFINITE);
+            if (C.pot || C.grad) {  // the finalisation, as k_finalize does it
+                const uint32_t j = C.perm[f + i];
+                const int sy = C.sys[b];
+                const double c1 = C.out_scale[2 * sy], c2 = C.out_scale[2 * sy + 1];
+                if (C.out_f64) {
+                    if (C.pot) ((double *)C.pot)[j] = c1 * tot[0];
+                    if (C.grad) {
+                        double *g = (double *)C.grad + 3 * (size_t)j;
+                        g[0] = c2 * tot[1];
+                        g[1] = c2 * tot[2];
+                        g[2] = c2 * tot[3];
+                    }
+                } else {
+                    if (C.pot) ((float *)C.pot)[j] = (float)(c1 * tot[0]);
+                    if (C.grad) {
+                        float *g = (float *)C.grad + 3 * (size_t)j;
+                        g[0] = (float)(c2 * tot[1]);
+                        g[1] = (float)(c2 * tot[2]);
+                        g[2] = (float)(c2 * tot[3]);
+                    }
+                }
+            }
         }
     }
 }
@@ -1477,6 +1508,17 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     LeafCtx C{P.lvl, P.cx, P.cy, P.cz, P.first, P.cnt, P.u_ptr, P.w_ptr, P.u_idx, P.w_idx, ns,
               split_mean ? P.dbar : nullptr, P.leaf_tile, P.status, P.periodic ? P.u_sh : nullptr,
               P.periodic ? P.w_sh : nullptr};
+    // free space: the leaf pass writes the outputs itself (a periodic cell
+    // adds the uniform shift to the results afterwards, then k_finalize)
+    const bool fused_out = !P.periodic && (pot || grad);
+    if (fused_out) {
+        C.perm = P.perm;
+        C.sys = P.sys;
+        C.out_scale = P.out_scale;
+        C.pot = pot;
+        C.grad = grad;
+        C.out_f64 = P.io_f64 ? 1 : 0;
+    }
     const LeafW<T> W{(const T *)P.dn_dens, 1, (const T *)P.up_dens, 1, nullptr};
     if (!P.tuned_leaf && tuning_wanted(P, s)) {
         // time every candidate table on this tree; keep the fastest
@@ -1507,7 +1549,7 @@ cudaError_t evaluate_t(Plan &P, void *pot, void *grad, double *energy, cudaStrea
     KIFMM_CUDA_TRY(cudaGetLastError());
     // outputs
     stage_begin(P, KIFMM_STAGE_OUT, s);
-    if (pot || grad) {
+    if ((pot || grad) && !fused_out) {
         if (P.io_f64)
             ++g_launches, k_finalize<double><<<grid_for(P.n, 256), 256, 0, s>>>(
                               P.n, res, P.perm, P.sys_off_d, P.n_sys, P.out_scale, (double *)pot,
