@@ -206,3 +206,49 @@ def test_lists_duality(thr):
     offs = {tuple(d) for d in O.m2l_offsets()}
     for b, a in V:
         assert tuple(t["coord"][a] - t["coord"][b]) in offs
+
+
+def _boxes_by_segments(keys, M, D):
+    """The octree's boxes read off the sorted keys level by level, with no
+    recursion: a box of level l >= 1 starts where the level-l key prefix
+    changes, inside a level-(l-1) run of equal prefixes longer than M, at a
+    level l - 1 below the maximum depth D (runs only shrink with the level,
+    so every coarser run around it is longer than M too).  Returns the
+    (level, first, count) of every box in level-major, then key order."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    n = keys.size
+    out = [(0, 0, n)]
+
+    def runs(p):
+        start = np.ones(n, dtype=bool)
+        start[1:] = p[1:] != p[:-1]
+        first = np.flatnonzero(start)
+        length = np.diff(np.append(first, n))
+        return start, np.repeat(length, length)   # run length seen from every point
+
+    prev_len = np.full(n, n)
+    for l in range(1, O.BITS + 1):
+        p = keys >> np.uint64(3 * (O.BITS - l))
+        start, length = runs(p)
+        box = start & (prev_len > M) & (l - 1 < D)
+        if not box.any():
+            break
+        out += [(l, int(i), int(length[i])) for i in np.flatnonzero(box)]
+        prev_len = length
+    return out
+
+
+@pytest.mark.parametrize("case", ["uniform", "plummer", "clustered"])
+@pytest.mark.parametrize("M,D", [(1, 20), (8, 20), (32, 4), (200, 20)])
+def test_tree_equals_the_segment_rule(case, M, D):
+    """The oracle's level-by-level octree (split while more than M points and
+    above depth D) has exactly the boxes of the segment rule, in the same
+    order, with the same counts."""
+    rng = np.random.default_rng(11)
+    x = {"uniform": lambda: G.uniform_charges(3000, 3)[0],
+         "plummer": lambda: G.plummer(3000, 4)[0],
+         "clustered": lambda: np.concatenate([rng.normal(0, 1e-4, (600, 3)), rng.uniform(-1, 1, (600, 3))])}[case]()
+    t = O.sort_and_tree(x, M, D)
+    want = _boxes_by_segments(t["keys"][t["perm"]], M, D)
+    got = list(zip(t["level"].tolist(), t["first"].tolist(), t["count"].tolist()))
+    assert got == want
