@@ -129,12 +129,46 @@ def test_tree_deeper_than_the_sorted_digits():
         assert np.array_equal(g[name], t[name]), name
 
 
+def test_tree_outgrowing_the_all_levels_build():
+    """The all-levels build sizes the box arrays from the last tree's level
+    sizes.  After three points (a close pair and a far point: a chain of one
+    or two boxes per level down to level 19), 2048 such close pairs spread
+    over a 16^3 grid have a chain each: far more boxes within those levels
+    than the arrays hold, so the build gives up before writing a box and the
+    tree is built level by level (more launches).  It matches the oracle's,
+    and a rebuild of the same points takes the all-levels path (fewer
+    launches, the same tree)."""
+    d = 2.0 ** -19
+    few = np.array([[0.5 - d / 2, 0.5, 0.5], [0.5 + d / 2, 0.5, 0.5], [0.0, 0.0, 0.0]])
+    g = (np.arange(16) + 0.5) / 16
+    cells = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)[:2048]
+    pairs = np.concatenate([cells - [d / 2, 0, 0], cells + [d / 2, 0, 0]])
+    q = np.ones(len(pairs))
+    plan = _plan(pairs, M=1)
+    for _ in range(2):
+        plan.set_sources(_dev(few), _dev(np.ones(3)))
+    assert plan.tree_info()["max_level"] >= 15
+    plan.profile_read()
+    t = O.sort_and_tree(pairs, 1, 20)
+    counts = []
+    for _ in range(2):
+        plan.set_sources(_dev(pairs), _dev(q))
+        counts.append(plan.profile_read()["launches"])
+        gt = plan.tree()
+        assert gt["level"].shape[0] == t["nb"]
+        for name in ("level", "first", "count", "parent"):
+            assert np.array_equal(gt[name], t[name]), name
+        assert np.array_equal(gt["coord"], t["coord"])
+    assert counts[0] > counts[1], counts
+
+
 def test_tree_rebuilt_across_shapes_on_one_plan():
     """One plan builds a sequence of trees: the same data again (the levels the
-    last tree had are built from its sizes without host round trips), a deeper
-    tree, a shallower one (it ends inside those levels), a much larger one (its
-    levels outgrow the grids sized from the last tree, so the build is redone
-    level by level).  Every tree matches the oracle's."""
+    last tree had are built at once from its level sizes), a deeper tree (it
+    continues level by level below them), a shallower one (it ends inside
+    them), a much larger one (its boxes outgrow the arrays sized from the last
+    tree, so the build is redone level by level).  Every tree matches the
+    oracle's."""
     rng = np.random.default_rng(77)
     seq = [G.uniform_charges(4096, 1)[0], G.uniform_charges(4096, 1)[0], CASES["clustered_tight"]()[0],
            G.uniform_charges(1000, 2)[0], G.uniform_charges(20000, 3)[0], G.plummer(3000, 5)[0],
