@@ -457,7 +457,8 @@ __global__ void k_emit(int64_t ls, int64_t le, const uint32_t *__restrict__ nchi
 
 // ---------------------------------------------------------------------------
 // Every level of the octree at once, from the sorted keys (the levels the
-// last tree had).  A box of level l >= 1 is a particle i that starts a level-l
+// last tree had).  The adaptive octree of Sec. 2.2 splits a box while it holds
+// more than M points; equivalently, a box of level l >= 1 is a particle i that starts a level-l
 // key prefix (or its system's range) inside a level-(l-1) key segment of more
 // than M particles, with l - 1 below the maximum depth.  Segment counts only
 // shrink with the level, so every ancestor of that segment splits as well:
