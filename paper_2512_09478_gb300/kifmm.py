@@ -182,11 +182,18 @@ class Plan:
         self.generation += 1
 
     def update_sources(self, xyz: torch.Tensor, q: torch.Tensor, stream=None):
-        """New positions/charges for the same particles, tree and lists frozen."""
+        """New positions/charges for the same particles, tree and lists frozen.
+        Asynchronous on `stream`: a contiguous copy made here is recorded on
+        that stream, so the allocator does not reuse it before the copy in is
+        done."""
         assert xyz.is_cuda and q.is_cuda and xyz.dtype == self.dtype and q.dtype == self.dtype
         assert self.n == 0 or xyz.shape[0] == self.n  # n == 0: the library reports the state error
-        _check(load().kifmm_update_sources(self._h, _ptr(xyz.contiguous()), _ptr(q.contiguous()),
-                                           _stream(stream)), "kifmm_update_sources")
+        xc, qc = xyz.contiguous(), q.contiguous()
+        if stream is not None:
+            for t, src in ((xc, xyz), (qc, q)):
+                if t.data_ptr() != src.data_ptr():
+                    t.record_stream(stream)
+        _check(load().kifmm_update_sources(self._h, _ptr(xc), _ptr(qc), _stream(stream)), "kifmm_update_sources")
         self.generation += 1
 
     def refresh_sources(self, xyz: torch.Tensor, q: torch.Tensor, skin: float = 0.05, stream=None) -> bool:
